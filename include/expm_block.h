@@ -1,0 +1,187 @@
+/*
+ * expm_block.h -- C ABI of the GB300 (sm_103a) preconditioned shifted block FOM library.
+ *
+ * Computes Z = r(tA) B, the Caratheodory-Fejer (CF) rational approximation of
+ * e^{tA} B (Wu, Pang, Sun, "Preconditioning the restarted and shifted block FOM
+ * algorithm for matrix exponential computation", arXiv:1405.0707):
+ *
+ *   r(x) = omega_0 + sum_{i=1..nu} omega_i / (x - tau_i)            (Section 2, eq. (11))
+ *
+ * The nu shifted systems (tA - tau_i I) X_i = B (eq. (3)) are solved together by the
+ * restarted shifted block FOM with the right preconditioner (tA)^{-1} common to every
+ * shift (Section 4.1, eq. (3188)): block Arnoldi on (tA)^{-1} (eq. (4.5)), projected
+ * systems (I - tau_i H_m) Z_i = E_1 R_i (eq. (3236)), residual norms by eq. (49),
+ * restart from V_{m+1} with the collinear residuals (Algorithm 2, k = 0).
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major with an explicit leading dimension (ld >= rows).
+ *   - "device" pointers are CUDA global-memory pointers on the plan's device; the
+ *     caller owns them and keeps them valid until the call's stream work completes.
+ *     "host" pointers are ordinary CPU memory, read or written before return.
+ *   - All device work is issued on the plan's stream (given at plan creation).  Calls
+ *     that return numbers to the host (info, residuals) synchronise that stream.
+ *   - No entry point calls exit/abort or prints; every failure is a status code.
+ *     After EXPM_CUDA_ERROR the plan should be destroyed.
+ *   - Only real data (A and B real); the conjugate poles are folded
+ *     (Section 2: "one only needs to solve nu/2 shifted linear systems").
+ */
+#ifndef EXPM_BLOCK_H
+#define EXPM_BLOCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EXPM_OK = 0,
+    EXPM_INVALID_ARG = 1,      /* bad size, pointer, descriptor or option            */
+    EXPM_NOT_CONVERGED = 2,    /* max_cycles reached; Z still written, info filled   */
+    EXPM_BREAKDOWN = 3,        /* block Arnoldi breakdown that is not an invariant
+                                  subspace (the paper is silent on this case)        */
+    EXPM_NUMERICAL = 4,        /* NaN/Inf, or a Cholesky pivot <= 0 in the block QR  */
+    EXPM_CUDA_ERROR = 5,       /* a CUDA runtime call or kernel launch failed         */
+    EXPM_NO_MEMORY = 6,        /* device allocation failed at plan creation           */
+    EXPM_INTERNAL = 7
+} expm_status;
+
+/* Operator families (the problem of Section 1: tA large, sparse, negative definite). */
+typedef enum {
+    /* t * (diff * Laplacian_h - vel . grad_h) on the unit interval/square/cube,
+     * N_d interior points per axis, h_d = 1/(N_d + 1), homogeneous Dirichlet boundary,
+     * second-order central differences, grid index x fastest.  Requires cell Peclet
+     * |vel_d| h_d / (2 diff) < 1 on every axis (then tA is diagonally similar to a
+     * symmetric negative definite matrix).  The 1-D case with vel = 0 and diff = 1 is
+     * (n+1)^2 tridiag(1, -2, 1); the 2-D Laplacian is the paper's Example 5.1 matrix. */
+    EXPM_OP_CONV_DIFF = 0
+} expm_op_kind;
+
+typedef struct {
+    int32_t kind;          /* expm_op_kind                                           */
+    int32_t ndim;          /* 1, 2 or 3                                              */
+    int32_t side[3];       /* interior grid points per axis (x, y, z); unused = 1    */
+    double  diff;          /* diffusion coefficient (> 0)                            */
+    double  vel[3];        /* convection velocity per axis                           */
+} expm_op_desc;
+
+typedef enum {
+    EXPM_PREC_FP64 = 0     /* every step in FP64 (the plain path)                    */
+} expm_precision;
+
+typedef struct {
+    int32_t m;             /* block Arnoldi steps per cycle (restart length), >= 1   */
+    int32_t max_cycles;    /* cap on restart cycles, >= 1                            */
+    double  tol;           /* stop when max_i ||R_i||_F <= tol ||B||_F  (eq. (49))   */
+    int32_t precision;     /* expm_precision                                         */
+    int32_t fixed_cycles;  /* > 0: run exactly this many cycles, ignoring tol        */
+} expm_opts;
+
+#define EXPM_MAX_POLES 16
+
+typedef struct {
+    int32_t cycles;              /* restart cycles run                               */
+    int32_t block_steps;         /* block applications of (tA)^{-1}                  */
+    int64_t matvecs;             /* p * block_steps: the paper's Mat-Vec count (Sec. 5) */
+    int32_t converged;           /* 1 if max_i resid[i] <= tol ||B||_F               */
+    int32_t breakdown;           /* 1 if a cycle ended on an invariant subspace      */
+    int32_t npoles;              /* nu/2 poles with Im tau > 0                        */
+    double  resid[EXPM_MAX_POLES]; /* eq. (49) norms ||R_i||_F after the last cycle   */
+    double  normB;               /* ||B||_F                                          */
+} expm_info;
+
+typedef struct expm_plan_s expm_plan;
+
+/* ---------------------------------------------------------------------------------
+ * expm_cf_coeffs -- the CF table of Section 2 for e^x on (-inf, 0].
+ *   nu          : even degree, 2 <= nu <= 2*EXPM_MAX_POLES (the paper uses 14, Sec. 5)
+ *   tau_re_im   : host, 2*(nu/2) doubles out: poles with Im tau > 0, (re, im) pairs,
+ *                 ordered by decreasing Im
+ *   omega_re_im : host, 2*(nu/2) doubles out: matching residues
+ *   omega0      : host, 1 double out: r(-inf)
+ *   sigma       : host, 1 double out (may be NULL): the CF error estimate (the
+ *                 (nu+1)-st Hankel singular value)
+ * Poles from the singular vector of the Hankel matrix of the Chebyshev coefficients of
+ * e^x transplanted to [-1, 1]; residues by a least-squares fit with those poles.
+ * Computed on the host in double-double arithmetic once per nu, then cached.
+ * Errors: EXPM_INVALID_ARG (nu, NULL pointer), EXPM_INTERNAL (construction failed).
+ * ------------------------------------------------------------------------------ */
+expm_status expm_cf_coeffs(int nu, double* tau_re_im, double* omega_re_im,
+                           double* omega0, double* sigma);
+
+/* ---------------------------------------------------------------------------------
+ * expm_plan_create -- "LU once and for all" (Section 4.1; Section 5): set up the exact
+ * inverse of A (without t: (tA)^{-1} = A^{-1}/t) and allocate the workspace for block
+ * width up to p_max and the options' m.
+ *   op      : host descriptor (read during the call)
+ *   p_max   : 1 <= p_max <= 32; m * p_max <= 512
+ *   opts    : host options (copied)
+ *   stream  : cudaStream_t (NULL = legacy default stream) used by every later call
+ *   out     : host, receives the plan; owned by the caller, free with expm_plan_destroy
+ * The plan owns all device memory it allocates (Krylov basis, Hessenberg matrix,
+ * preconditioner tables).  Errors: EXPM_INVALID_ARG, EXPM_NO_MEMORY, EXPM_CUDA_ERROR.
+ * ------------------------------------------------------------------------------ */
+expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts* opts,
+                             void* stream, expm_plan** out);
+
+void expm_plan_destroy(expm_plan* plan);
+
+/* ---------------------------------------------------------------------------------
+ * expm_block -- Z = r(tA) B by Algorithm 2 (PSBFOM, restart without deflation).
+ *   t      : time, t > 0 (t is folded into A as in Section 1)
+ *   dB     : device, n x p, leading dimension ldb >= n (not modified)
+ *   p      : 1 <= p <= p_max
+ *   dZ     : device, n x p out, leading dimension ldz >= n; must not alias dB
+ *   info   : host out (may be NULL)
+ * Per cycle: m block steps of W = (tA)^{-1} V_j, block classical Gram-Schmidt with one
+ * reorthogonalisation, Cholesky-QR of W; then the nu/2 projected systems of eq. (3236)
+ * in one launch, the eq. (49) norms, and the update Z += V_{m+1} sum_i 2 Re(omega_i
+ * H~_m Z_i), which equals sum_i 2 Re(omega_i (X_i - X_i^0)) because
+ * (tA)^{-1} V_m = V_{m+1} H~_m (eq. (4.5)) and X_i = (tA)^{-1} Y_i.
+ * Returns EXPM_NOT_CONVERGED (Z holds the last iterate) if max_cycles is reached.
+ * Synchronises the plan's stream once per cycle (residual norms to the host).
+ * ------------------------------------------------------------------------------ */
+expm_status expm_block(expm_plan* plan, double t, const double* dB, int64_t ldb, int p,
+                       double* dZ, int64_t ldz, expm_info* info);
+
+/* expm_block_host -- the same computation with HOST buffers: copies B (n x p, ldb) to
+ * the plan's device staging buffer, runs expm_block, copies Z back (n x p, ldz).
+ * B and Z are ordinary (preferably page-locked) host memory.  Same errors. */
+expm_status expm_block_host(expm_plan* plan, double t, const double* hB, int64_t ldb,
+                            int p, double* hZ, int64_t ldz, expm_info* info);
+
+/* ---------------------------------------------------------------------------------
+ * Component entry points (the hot path's kernels, exposed for parity tests and
+ * measurement).  All are stream-ordered on the plan's stream and do not synchronise.
+ *
+ * expm_op_apply   : W = tA V  (the operator of Algorithm 1 and of the residual
+ *                   B - (tA - tau I) X; Section 1 / eq. (3)).
+ * expm_prec_apply : W = (tA)^{-1} V, the exact inner solve that replaces the paper's
+ *                   sparse LU (Section 4.1, "U \ (L \ w)"): a transform along every
+ *                   axis but x with the axis' eigenvectors (diagonal similarity + DST-I),
+ *                   then tridiagonal solves along x for each transformed mode.
+ *   dV, dW : device, n x p (ld >= n), must not alias; 1 <= p <= p_max.
+ * Errors: EXPM_INVALID_ARG, EXPM_CUDA_ERROR (launch failure).
+ * ------------------------------------------------------------------------------ */
+expm_status expm_op_apply(expm_plan* plan, double t, const double* dV, int64_t ldv, int p,
+                          double* dW, int64_t ldw);
+expm_status expm_prec_apply(expm_plan* plan, double t, const double* dV, int64_t ldv, int p,
+                            double* dW, int64_t ldw);
+
+/* expm_arnoldi -- one block Arnoldi pass (eq. (4.5)) from an orthonormal V_1:
+ *   dV1 : device n x p (ldv1), orthonormal start block (copied into the basis)
+ *   dVout : device n x (m+1)p out (ldvo), the basis V_{m+1}
+ *   dHout : device (m+1)p x mp out (ldh), the band Hessenberg H~_m
+ * With Cholesky-QR the new blocks' R factors have a positive diagonal, so the basis
+ * equals Ruhe's variant's (Section 3) in exact arithmetic.  Synchronises the stream
+ * (breakdown flag).  Errors: EXPM_INVALID_ARG, EXPM_NUMERICAL, EXPM_CUDA_ERROR. */
+expm_status expm_arnoldi(expm_plan* plan, double t, const double* dV1, int64_t ldv1, int p,
+                         double* dVout, int64_t ldvo, double* dHout, int64_t ldh);
+
+const char* expm_status_str(expm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXPM_BLOCK_H */

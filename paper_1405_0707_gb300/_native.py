@@ -1,0 +1,157 @@
+"""ctypes binding of include/expm_block.h: the same names, argument marshalling only.
+
+Every step of the computation runs in the CUDA library; nothing here computes.  Loading
+fails loudly (RuntimeError) when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+EXPM_OK = 0
+EXPM_INVALID_ARG = 1
+EXPM_NOT_CONVERGED = 2
+EXPM_BREAKDOWN = 3
+EXPM_NUMERICAL = 4
+EXPM_CUDA_ERROR = 5
+EXPM_NO_MEMORY = 6
+EXPM_INTERNAL = 7
+EXPM_OP_CONV_DIFF = 0
+EXPM_PREC_FP64 = 0
+EXPM_MAX_POLES = 16
+
+# Every exported function the header declares (checked by the CPU test suite).
+EXPORTS = ("expm_cf_coeffs", "expm_plan_create", "expm_plan_destroy", "expm_block",
+           "expm_block_host", "expm_op_apply", "expm_prec_apply", "expm_arnoldi",
+           "expm_status_str")
+
+
+class expm_op_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("ndim", C.c_int32), ("side", C.c_int32 * 3),
+                ("diff", C.c_double), ("vel", C.c_double * 3)]
+
+
+class expm_opts(C.Structure):
+    _fields_ = [("m", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double),
+                ("precision", C.c_int32), ("fixed_cycles", C.c_int32)]
+
+
+class expm_info(C.Structure):
+    _fields_ = [("cycles", C.c_int32), ("block_steps", C.c_int32), ("matvecs", C.c_int64),
+                ("converged", C.c_int32), ("breakdown", C.c_int32), ("npoles", C.c_int32),
+                ("resid", C.c_double * EXPM_MAX_POLES), ("normB", C.c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libexpm_block.so (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run __graft_entry__.build() or python -m paper_1405_0707_gb300.build)")
+    lib = C.CDLL(path)
+    p, d, i32, i64 = C.c_void_p, C.c_double, C.c_int, C.c_int64
+    lib.expm_status_str.restype = C.c_char_p
+    lib.expm_status_str.argtypes = [C.c_int]
+    lib.expm_cf_coeffs.restype = C.c_int
+    lib.expm_cf_coeffs.argtypes = [C.c_int, C.POINTER(d), C.POINTER(d), C.POINTER(d), C.POINTER(d)]
+    lib.expm_plan_create.restype = C.c_int
+    lib.expm_plan_create.argtypes = [C.POINTER(expm_op_desc), C.c_int, C.POINTER(expm_opts), p,
+                                     C.POINTER(p)]
+    lib.expm_plan_destroy.restype = None
+    lib.expm_plan_destroy.argtypes = [p]
+    for name in ("expm_block", "expm_block_host"):
+        f = getattr(lib, name)
+        f.restype = C.c_int
+        f.argtypes = [p, d, p, i64, i32, p, i64, C.POINTER(expm_info)]
+    for name in ("expm_op_apply", "expm_prec_apply"):
+        f = getattr(lib, name)
+        f.restype = C.c_int
+        f.argtypes = [p, d, p, i64, i32, p, i64]
+    lib.expm_arnoldi.restype = C.c_int
+    lib.expm_arnoldi.argtypes = [p, d, p, i64, i32, p, i64, p, i64]
+    _lib = lib
+    return lib
+
+
+class ExpmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = load().expm_status_str(code).decode()
+        super().__init__(f"{where}: status {code} ({msg})")
+
+
+def check(code, where, allow=(EXPM_OK,)):
+    if code not in allow:
+        raise ExpmError(code, where)
+    return code
+
+
+# ---------------------------------------------------------------- thin wrappers (same names)
+def expm_cf_coeffs(nu=14):
+    lib = load()
+    k = nu // 2
+    tau = (C.c_double * (2 * k))()
+    om = (C.c_double * (2 * k))()
+    w0 = C.c_double()
+    sg = C.c_double()
+    check(lib.expm_cf_coeffs(nu, tau, om, C.byref(w0), C.byref(sg)), "expm_cf_coeffs")
+    taus = [complex(tau[2 * i], tau[2 * i + 1]) for i in range(k)]
+    oms = [complex(om[2 * i], om[2 * i + 1]) for i in range(k)]
+    return taus, oms, w0.value, sg.value
+
+
+def expm_plan_create(op: expm_op_desc, p_max: int, opts: expm_opts, stream: int = 0):
+    lib = load()
+    out = C.c_void_p()
+    check(lib.expm_plan_create(C.byref(op), p_max, C.byref(opts), C.c_void_p(stream), C.byref(out)),
+          "expm_plan_create")
+    return out
+
+
+def expm_plan_destroy(plan):
+    load().expm_plan_destroy(plan)
+
+
+def expm_block(plan, t, dB, ldb, p, dZ, ldz, allow_not_converged=True):
+    info = expm_info()
+    allow = (EXPM_OK, EXPM_NOT_CONVERGED) if allow_not_converged else (EXPM_OK,)
+    code = check(load().expm_block(plan, t, C.c_void_p(dB), ldb, p, C.c_void_p(dZ), ldz,
+                                   C.byref(info)), "expm_block", allow)
+    return code, info
+
+
+def expm_block_host(plan, t, hB, ldb, p, hZ, ldz, allow_not_converged=True):
+    info = expm_info()
+    allow = (EXPM_OK, EXPM_NOT_CONVERGED) if allow_not_converged else (EXPM_OK,)
+    code = check(load().expm_block_host(plan, t, C.c_void_p(hB), ldb, p, C.c_void_p(hZ), ldz,
+                                        C.byref(info)), "expm_block_host", allow)
+    return code, info
+
+
+def expm_op_apply(plan, t, dV, ldv, p, dW, ldw):
+    check(load().expm_op_apply(plan, t, C.c_void_p(dV), ldv, p, C.c_void_p(dW), ldw), "expm_op_apply")
+
+
+def expm_prec_apply(plan, t, dV, ldv, p, dW, ldw):
+    check(load().expm_prec_apply(plan, t, C.c_void_p(dV), ldv, p, C.c_void_p(dW), ldw),
+          "expm_prec_apply")
+
+
+def expm_arnoldi(plan, t, dV1, ldv1, p, dVout, ldvo, dHout, ldh):
+    check(load().expm_arnoldi(plan, t, C.c_void_p(dV1), ldv1, p, C.c_void_p(dVout), ldvo,
+                              C.c_void_p(dHout), ldh), "expm_arnoldi")

@@ -1,0 +1,118 @@
+"""User-facing wrapper: a plan per operator, torch tensors in and out.
+
+Matrices are column-major, as in the C ABI: an (n, p) torch tensor with stride (1, ld).
+``colmajor(n, p)`` allocates one.  All work is issued on the plan's CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _native as N
+
+
+def colmajor(n, p, device="cuda", dtype=None, ld=None):
+    import torch
+    dtype = dtype or torch.float64
+    ld = ld or n
+    return torch.empty((p, ld), dtype=dtype, device=device).T[:n]
+
+
+def _check_colmajor(X, n, p, name):
+    import torch
+    if X.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if X.dim() != 2 or X.shape[0] != n or X.shape[1] != p:
+        raise ValueError(f"{name} must have shape ({n}, {p}), got {tuple(X.shape)}")
+    if X.stride(0) != 1 and p > 1:
+        raise ValueError(f"{name} must be column-major (stride (1, ld))")
+    return X.stride(1) if p > 1 else max(n, X.stride(1) if X.dim() == 2 else n)
+
+
+def cf_coeffs(nu=14):
+    """(tau[nu/2], omega[nu/2], omega0, sigma) of the CF table computed by the library."""
+    return N.expm_cf_coeffs(nu)
+
+
+class Plan:
+    """A plan for tA = t (diff Laplacian_h - vel . grad_h) on a 1/2/3-D grid (x fastest)."""
+
+    def __init__(self, sides, diff, vel, p_max, m=10, tol=1e-10, max_cycles=200,
+                 fixed_cycles=0, stream=None):
+        import torch
+        sides = tuple(int(s) for s in sides)
+        vel = tuple(float(v) for v in vel)
+        if len(sides) != len(vel) or not 1 <= len(sides) <= 3:
+            raise ValueError("sides and vel must have the same length 1..3")
+        op = N.expm_op_desc()
+        op.kind = N.EXPM_OP_CONV_DIFF
+        op.ndim = len(sides)
+        for d in range(3):
+            op.side[d] = sides[d] if d < len(sides) else 1
+            op.vel[d] = vel[d] if d < len(vel) else 0.0
+        op.diff = float(diff)
+        opts = N.expm_opts()
+        opts.m, opts.max_cycles, opts.tol = int(m), int(max_cycles), float(tol)
+        opts.precision = N.EXPM_PREC_FP64
+        opts.fixed_cycles = int(fixed_cycles)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
+        self.n = 1
+        for s in sides:
+            self.n *= s
+        self._h = N.expm_plan_create(op, int(p_max), opts, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.expm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ entry points
+    def expm_block(self, t, B, Z=None):
+        """Z = r(tA) B on the device (Algorithm 2).  Returns (Z, info)."""
+        n, p = self.n, B.shape[1]
+        ldb = _check_colmajor(B, n, p, "B")
+        if Z is None:
+            Z = colmajor(n, p, device=B.device)
+        ldz = _check_colmajor(Z, n, p, "Z")
+        code, info = N.expm_block(self._h, float(t), B.data_ptr(), ldb, p, Z.data_ptr(), ldz)
+        return Z, info
+
+    def expm_block_host(self, t, hB, hZ):
+        """Host buffers (torch CPU float64, column-major, ideally pinned): copies inside."""
+        n, p = self.n, hB.shape[1]
+        ldb = _check_colmajor(hB, n, p, "B")
+        ldz = _check_colmajor(hZ, n, p, "Z")
+        code, info = N.expm_block_host(self._h, float(t), hB.data_ptr(), ldb, p, hZ.data_ptr(), ldz)
+        return hZ, info
+
+    def op_apply(self, t, V, W=None):
+        n, p = self.n, V.shape[1]
+        ldv = _check_colmajor(V, n, p, "V")
+        W = colmajor(n, p, device=V.device) if W is None else W
+        N.expm_op_apply(self._h, float(t), V.data_ptr(), ldv, p, W.data_ptr(), _check_colmajor(W, n, p, "W"))
+        return W
+
+    def prec_apply(self, t, V, W=None):
+        n, p = self.n, V.shape[1]
+        ldv = _check_colmajor(V, n, p, "V")
+        W = colmajor(n, p, device=V.device) if W is None else W
+        N.expm_prec_apply(self._h, float(t), V.data_ptr(), ldv, p, W.data_ptr(), _check_colmajor(W, n, p, "W"))
+        return W
+
+    def arnoldi(self, t, V1):
+        """One block Arnoldi pass from the orthonormal V1: returns (V_{m+1}, H~_m)."""
+        import torch
+        n, p = self.n, V1.shape[1]
+        ldv = _check_colmajor(V1, n, p, "V1")
+        m = self.m
+        V = colmajor(n, (m + 1) * p, device=V1.device)
+        H = torch.zeros(((m) * p, (m + 1) * p), dtype=torch.float64, device=V1.device).T
+        N.expm_arnoldi(self._h, float(t), V1.data_ptr(), ldv, p, V.data_ptr(), V.stride(1),
+                       H.data_ptr(), H.stride(1))
+        return V, H

@@ -1,0 +1,448 @@
+// api.cu -- C ABI entry points and the restart-cycle driver of Algorithm 2 (PSBFOM, k = 0).
+//
+// Host side of one call to expm_block:
+//   Step 1-2 (Algorithm 1, shared by Algorithm 2): X_i^0 = 0, R_i^0 = B = V_1 R  (Cholesky QR)
+//   per cycle:
+//     Step 3: m block steps W = (tA)^{-1} V_j -> CGS2 -> Cholesky QR -> V_{j+1}, H~_m (eq. (4.5))
+//     Step 4: all projected systems in one launch (eq. (3236)), norms by eq. (49),
+//             Z += V_{m+1} sum_i 2 Re(omega_i H~_m Z_i); restart V_1 <- V_{m+1}
+//     one device->host copy of the nu/2 residual norms + status flags, then the stop test
+//   Z = omega_0 B + Z_acc   (eq. (11) with the conjugate pairs folded)
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace expm;
+
+namespace {
+
+#define CK(call)                                          \
+    do {                                                  \
+        if ((call) != cudaSuccess) return EXPM_CUDA_ERROR; \
+    } while (0)
+
+constexpr int kNu = 14;
+constexpr int kStatDoubles = 32;   // res[0..15], normsq at [16], int flags at doubles [24..25]
+
+// small scratch map (in doubles)
+constexpr size_t kOffH = 0;                                        // h: kMaxMP x kMaxP
+constexpr size_t kOffR = kOffH + (size_t)kMaxMP * kMaxP;           // R
+constexpr size_t kOffRi = kOffR + kMaxP * kMaxP;                   // R^{-1}
+constexpr size_t kOffRt = kOffRi + kMaxP * kMaxP;                  // product of R factors
+constexpr size_t kOffWc = kOffRt + kMaxP * kMaxP;                  // (kMaxMP + kMaxP) x kMaxP
+constexpr size_t kOffTau = kOffWc + (size_t)(kMaxMP + kMaxP) * kMaxP;   // 4 x 16
+constexpr size_t kSmallDoubles = kOffTau + 4 * EXPM_MAX_POLES;
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int* flags_of(double* stat) { return reinterpret_cast<int*>(stat + 24); }
+
+double* sm(expm_plan* P, size_t off) { return P->small + off; }
+
+expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, int hrow, int hcol,
+                     double* normsq, bool gram_done) {
+    cudaStream_t s = P->stream;
+    const int64_t n = P->n, ld = P->ld;
+    const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * std::ldexp(1.0, -53);
+    int* flags = flags_of(P->stat);
+    if (!gram_done) CK(launch_proj_partial(P->W, ld, p, P->W, ld, p, n, P->part, P->nblk, s));
+    CK(launch_chol(P->part, P->nblk, p, shift, sm(P, kOffR), sm(P, kOffRi), sm(P, kOffRt), 1,
+                   nullptr, 0, 0, 0, normsq, flags, s));
+    CK(launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, s));
+    CK(launch_chol(P->part, P->nblk, p, 0.0, sm(P, kOffR), sm(P, kOffRi), sm(P, kOffRt), 0,
+                   nullptr, 0, 0, 0, nullptr, flags, s));
+    CK(launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, s));
+    CK(launch_chol(P->part, P->nblk, p, 0.0, sm(P, kOffR), sm(P, kOffRi), sm(P, kOffRt), 0,
+                   withH ? P->H : nullptr, P->ldH, hrow, hcol, nullptr, flags, s));
+    CK(launch_trsm(P->W, ld, p, n, sm(P, kOffRi), out, ldo, nullptr, P->nblk, 0, s));
+    return EXPM_OK;
+}
+
+expm_status prec_apply_internal(expm_plan* P, double t, const double* V, int64_t ldv, int p,
+                                double* W, int64_t ldw) {
+    cudaStream_t s = P->stream;
+    const double inv_t = 1.0 / t;
+    const int nx = P->ax[0].N, ny = P->ax[1].N, nz = P->ax[2].N;
+    const int64_t ld = P->ld;
+    const double lsub = P->ax[0].l;
+    if (P->ndim == 1) {
+        CK(launch_tridiag_lines(V, ldv, W, ldw, p, nx, 1, lsub, P->th_m, P->th_c, inv_t, s));
+        return EXPM_OK;
+    }
+    if (P->ndim == 2) {
+        GemmArgs g1{V, P->Qf[1], P->T1, nx, ny, ny, 1, nx, ldv, 0, ny, 1, ld, 0, ny, p, 1};
+        CK(launch_gemm(g1, s));
+        CK(launch_tridiag_lines(P->T1, ld, P->T1, ld, p, nx, ny, lsub, P->th_m, P->th_c, inv_t, s));
+        GemmArgs g2{P->T1, P->Qi[1], W, nx, ny, ny, ny, 1, ld, 0, 1, nx, ldw, 0, ny, p, 1};
+        CK(launch_gemm(g2, s));
+        return EXPM_OK;
+    }
+    const int64_t nxy = (int64_t)nx * ny;
+    GemmArgs g1{V, P->Qf[2], P->T2, (int)nxy, nz, nz, 1, nxy, ldv, 0, 1, nxy, ld, 0, nz, p, 1};
+    CK(launch_gemm(g1, s));
+    GemmArgs g2{P->T2, P->Qf[1], P->T1, nx, ny, ny, 1, nx, ld, nxy, (int64_t)ny * nz, 1, ld, ny, ny, p, nz};
+    CK(launch_gemm(g2, s));
+    CK(launch_tridiag_lines(P->T1, ld, P->T1, ld, p, nx, (int64_t)ny * nz, lsub, P->th_m, P->th_c,
+                            inv_t, s));
+    GemmArgs g3{P->T1, P->Qi[1], P->T2, nx, ny, ny, (int64_t)ny * nz, 1, ld, ny, 1, nx, ld, nxy, ny, p, nz};
+    CK(launch_gemm(g3, s));
+    GemmArgs g4{P->T2, P->Qi[2], W, (int)nxy, nz, nz, 1, nxy, ld, 0, 1, nxy, ldw, 0, nz, p, 1};
+    CK(launch_gemm(g4, s));
+    return EXPM_OK;
+}
+
+// Block step j (0-based): V_j -> W = (tA)^{-1} V_j -> V_{j+1}, H column block j.
+expm_status block_step(expm_plan* P, double t, int j, int p) {
+    cudaStream_t s = P->stream;
+    const int64_t n = P->n, ld = P->ld;
+    double* h = sm(P, kOffH);
+    expm_status st = prec_apply_internal(P, t, P->V + (int64_t)j * p * ld, ld, p, P->W, ld);
+    if (st != EXPM_OK) return st;
+    const int cols = (j + 1) * p;
+    CK(launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, P->nblk, s));
+    CK(launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
+    CK(launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s));
+    CK(launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
+    CK(launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 1, s));
+    return qr_block(P, p, P->V + (int64_t)(j + 1) * p * ld, ld, true, (j + 1) * p, j * p, nullptr, true);
+}
+
+expm_status check_flags(const double* hstat) {
+    const int* f = reinterpret_cast<const int*>(hstat + 24);
+    if (f[0]) return EXPM_NUMERICAL;
+    if (f[1]) return EXPM_BREAKDOWN;
+    return EXPM_OK;
+}
+
+expm_status validate_block_args(expm_plan* P, double t, const void* B, int64_t ldb, int p,
+                                const void* Z, int64_t ldz) {
+    if (!P || !B || !Z) return EXPM_INVALID_ARG;
+    if (!(t > 0.0) || !std::isfinite(t)) return EXPM_INVALID_ARG;
+    if (p < 1 || p > P->p_max) return EXPM_INVALID_ARG;
+    if (ldb < P->n || ldz < P->n) return EXPM_INVALID_ARG;
+    if (B == Z) return EXPM_INVALID_ARG;
+    return EXPM_OK;
+}
+
+expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int p, double* dZ,
+                      int64_t ldz, expm_info* info) {
+    cudaStream_t s = P->stream;
+    const int m = P->opts.m;
+    const int64_t n = P->n, ld = P->ld;
+    const int mp = m * p;
+    CK(cudaMemsetAsync(P->stat, 0, sizeof(double) * kStatDoubles, s));
+    CK(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)P->ldH * m * P->p_max, s));
+    CK(launch_zero(P->Zacc, ld, n, p, s));
+    // Steps 1-2: R_i^0 = B = V_1 R for every pole
+    CK(launch_copy(dB, ldb, P->W, ld, n, p, s));
+    expm_status st = qr_block(P, p, P->V, ld, false, 0, 0, P->stat + 16, false);
+    if (st != EXPM_OK) return st;
+    CK(launch_init_S(sm(P, kOffRt), p, P->npoles, P->S, s));
+    double* tau_re = sm(P, kOffTau);
+    int cycles = 0;
+    bool converged = false;
+    double normB = 0.0;
+    expm_status result = EXPM_OK;
+    while (true) {
+        ++cycles;
+        for (int j = 0; j < m; ++j) {
+            st = block_step(P, t, j, p);
+            if (st != EXPM_OK) return st;
+        }
+        CK(launch_poles(P->H, P->ldH, mp, p, P->npoles, tau_re, tau_re + EXPM_MAX_POLES,
+                        tau_re + 2 * EXPM_MAX_POLES, tau_re + 3 * EXPM_MAX_POLES, P->S, P->poles,
+                        P->Wc_slots, P->stat, flags_of(P->stat), s));
+        CK(launch_combine(P->Wc_slots, P->npoles, mp + p, p, sm(P, kOffWc), s));
+        CK(launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk));
+        CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        st = check_flags(P->hpin);
+        if (st != EXPM_OK) { result = st; break; }
+        normB = std::sqrt(P->hpin[16]);
+        double mx = 0.0;
+        for (int i = 0; i < P->npoles; ++i) mx = std::max(mx, P->hpin[i]);
+        converged = mx <= P->opts.tol * normB;
+        const bool done = (P->opts.fixed_cycles > 0) ? cycles >= P->opts.fixed_cycles
+                                                     : (converged || cycles >= P->opts.max_cycles);
+        if (done) break;
+    }
+    // Z = omega_0 B + Z_acc
+    CK(launch_axpby(P->omega0, dB, ldb, 1.0, P->Zacc, ld, dZ, ldz, n, p, s));
+    CK(cudaGetLastError());
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->cycles = cycles;
+        info->block_steps = cycles * m;
+        info->matvecs = (int64_t)cycles * m * p;
+        info->converged = converged ? 1 : 0;
+        info->npoles = P->npoles;
+        for (int i = 0; i < P->npoles; ++i) info->resid[i] = P->hpin[i];
+        info->normB = normB;
+    }
+    if (result != EXPM_OK) return result;
+    if (P->opts.fixed_cycles > 0) return EXPM_OK;
+    return converged ? EXPM_OK : EXPM_NOT_CONVERGED;
+}
+
+void free_plan(expm_plan* P) {
+    if (!P) return;
+    for (int d = 0; d < 3; ++d) {
+        cudaFree(P->Qf[d]);
+        cudaFree(P->Qi[d]);
+        cudaFree(P->lam[d]);
+    }
+    cudaFree(P->th_m);
+    cudaFree(P->th_c);
+    cudaFree(P->V);
+    cudaFree(P->W);
+    cudaFree(P->T1);
+    cudaFree(P->T2);
+    cudaFree(P->Zacc);
+    cudaFree(P->Bst);
+    cudaFree(P->Zst);
+    cudaFree(P->H);
+    cudaFree(P->part);
+    cudaFree(P->small);
+    cudaFree(P->poles);
+    cudaFree(P->S);
+    cudaFree(P->Wc_slots);
+    cudaFree(P->stat);
+    if (P->hpin) cudaFreeHost(P->hpin);
+    delete P;
+}
+
+template <class T>
+bool dalloc(T** p, size_t count) {
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* expm_status_str(expm_status s) {
+    switch (s) {
+        case EXPM_OK: return "ok";
+        case EXPM_INVALID_ARG: return "invalid argument";
+        case EXPM_NOT_CONVERGED: return "not converged within max_cycles";
+        case EXPM_BREAKDOWN: return "block Arnoldi breakdown";
+        case EXPM_NUMERICAL: return "numerical failure (NaN/Inf or non-positive Cholesky pivot)";
+        case EXPM_CUDA_ERROR: return "CUDA error";
+        case EXPM_NO_MEMORY: return "device allocation failed";
+        default: return "internal error";
+    }
+}
+
+expm_status expm_cf_coeffs(int nu, double* tau_re_im, double* omega_re_im, double* omega0,
+                           double* sigma) {
+    if (nu < 2 || nu > 2 * EXPM_MAX_POLES || (nu % 2) != 0) return EXPM_INVALID_ARG;
+    if (!tau_re_im || !omega_re_im || !omega0) return EXPM_INVALID_ARG;
+    std::vector<std::complex<double>> tau, om;
+    double w0 = 0, sg = 0;
+    if (!expm_internal_cf_table(nu, tau, om, w0, sg)) return EXPM_INTERNAL;
+    for (size_t i = 0; i < tau.size(); ++i) {
+        tau_re_im[2 * i] = tau[i].real();
+        tau_re_im[2 * i + 1] = tau[i].imag();
+        omega_re_im[2 * i] = om[i].real();
+        omega_re_im[2 * i + 1] = om[i].imag();
+    }
+    *omega0 = w0;
+    if (sigma) *sigma = sg;
+    return EXPM_OK;
+}
+
+expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts* opts,
+                             void* stream, expm_plan** out) {
+    if (!op || !opts || !out) return EXPM_INVALID_ARG;
+    *out = nullptr;
+    if (op->kind != EXPM_OP_CONV_DIFF) return EXPM_INVALID_ARG;
+    if (op->ndim < 1 || op->ndim > 3) return EXPM_INVALID_ARG;
+    if (!(op->diff > 0.0) || !std::isfinite(op->diff)) return EXPM_INVALID_ARG;
+    if (p_max < 1 || p_max > kMaxP) return EXPM_INVALID_ARG;
+    if (opts->m < 1 || (int64_t)opts->m * p_max > kMaxMP) return EXPM_INVALID_ARG;
+    if (opts->max_cycles < 1 || !(opts->tol >= 0.0)) return EXPM_INVALID_ARG;
+    if (opts->precision != EXPM_PREC_FP64) return EXPM_INVALID_ARG;
+    expm_plan* P = new (std::nothrow) expm_plan_s();
+    if (!P) return EXPM_NO_MEMORY;
+    P->op = *op;
+    P->opts = *opts;
+    P->ndim = op->ndim;
+    P->p_max = p_max;
+    P->stream = reinterpret_cast<cudaStream_t>(stream);
+    int64_t n = 1;
+    for (int d = 0; d < 3; ++d) {
+        Axis& a = P->ax[d];
+        if (d < op->ndim) {
+            const int N = op->side[d];
+            if (N < 1 || N > (1 << 20)) { delete P; return EXPM_INVALID_ARG; }
+            const double h = 1.0 / (N + 1);
+            a.N = N;
+            a.l = op->diff / (h * h) + op->vel[d] / (2.0 * h);
+            a.c = -2.0 * op->diff / (h * h);
+            a.u = op->diff / (h * h) - op->vel[d] / (2.0 * h);
+            if (!(a.l * a.u > 0.0)) { delete P; return EXPM_INVALID_ARG; }   // cell Peclet >= 1
+            n *= N;
+        } else {
+            a = Axis{};
+        }
+    }
+    if (op->ndim > 1 && (int64_t)P->ax[1].N * P->ax[2].N * P->ax[0].N != n) { delete P; return EXPM_INVALID_ARG; }
+    P->n = n;
+    P->ld = round_up(n, 32);
+    // CF table (Section 2), nu = 14 as in the paper's experiments (Section 5)
+    {
+        std::vector<std::complex<double>> tau, om;
+        double w0 = 0, sg = 0;
+        if (!expm_internal_cf_table(kNu, tau, om, w0, sg)) { delete P; return EXPM_INTERNAL; }
+        P->npoles = (int)tau.size();
+        for (int i = 0; i < P->npoles; ++i) {
+            P->tau_re[i] = tau[i].real();
+            P->tau_im[i] = tau[i].imag();
+            P->om_re[i] = om[i].real();
+            P->om_im[i] = om[i].imag();
+        }
+        P->omega0 = w0;
+    }
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete P;
+        return EXPM_CUDA_ERROR;
+    }
+    P->nblk = consistent_blocks(n, std::max(1, std::min<int>(2 * sms, (int)((n + 63) / 64))));
+    const int m = opts->m;
+    const int64_t ld = P->ld;
+    P->ldH = (m + 1) * p_max;
+    const int mpm = m * p_max;
+    bool ok = true;
+    ok = ok && dalloc(&P->V, (size_t)ld * (m + 1) * p_max);
+    ok = ok && dalloc(&P->W, (size_t)ld * p_max);
+    ok = ok && dalloc(&P->T1, (size_t)ld * p_max);
+    ok = ok && dalloc(&P->T2, (size_t)ld * p_max);
+    ok = ok && dalloc(&P->Zacc, (size_t)ld * p_max);
+    ok = ok && dalloc(&P->Bst, (size_t)ld * p_max);
+    ok = ok && dalloc(&P->Zst, (size_t)ld * p_max);
+    ok = ok && dalloc(&P->H, (size_t)P->ldH * mpm);
+    ok = ok && dalloc(&P->part, (size_t)P->nblk * std::max(mpm * p_max, p_max * p_max));
+    ok = ok && dalloc(&P->small, kSmallDoubles);
+    ok = ok && dalloc(&P->S, (size_t)P->npoles * p_max * p_max * 2);
+    ok = ok && dalloc(&P->Wc_slots, (size_t)P->npoles * (mpm + p_max) * p_max);
+    ok = ok && dalloc(&P->stat, kStatDoubles);
+    if (poles_smem_bytes(mpm, p_max) == 0)   // elimination does not fit in shared memory
+        ok = ok && dalloc(&P->poles, (size_t)P->npoles * ((size_t)mpm * mpm + (size_t)mpm * p_max) * 2);
+    ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hpin), sizeof(double) * kStatDoubles) == cudaSuccess;
+    // preconditioner tables: every axis but x is transformed
+    int64_t nmodes = 1;
+    for (int d = 1; d < P->ndim; ++d) {
+        const int N = P->ax[d].N;
+        ok = ok && dalloc(&P->Qf[d], (size_t)N * N) && dalloc(&P->Qi[d], (size_t)N * N) &&
+             dalloc(&P->lam[d], (size_t)N);
+        nmodes *= N;
+    }
+    P->nmodes = nmodes;
+    ok = ok && dalloc(&P->th_m, (size_t)P->ax[0].N * nmodes) && dalloc(&P->th_c, (size_t)P->ax[0].N * nmodes);
+    if (!ok) {
+        cudaGetLastError();
+        free_plan(P);
+        return EXPM_NO_MEMORY;
+    }
+    cudaStream_t s = P->stream;
+    bool cuda_ok = krylov_set_smem_limits() == cudaSuccess && poles_set_smem_limits() == cudaSuccess;
+    for (int d = 1; d < P->ndim && cuda_ok; ++d)
+        cuda_ok = launch_axis_setup(P->Qf[d], P->Qi[d], P->lam[d], P->ax[d].N, P->ax[d].l,
+                                    P->ax[d].c, P->ax[d].u, s) == cudaSuccess;
+    if (cuda_ok)
+        cuda_ok = launch_thomas_setup(P->th_m, P->th_c, P->ax[0].N, nmodes, P->ax[0].l, P->ax[0].c,
+                                      P->ax[0].u, P->ndim > 1 ? P->lam[1] : nullptr, P->ax[1].N,
+                                      P->ndim > 2 ? P->lam[2] : nullptr, P->ax[2].N, s) == cudaSuccess;
+    if (cuda_ok) {
+        double taus[4 * EXPM_MAX_POLES] = {0};
+        for (int i = 0; i < P->npoles; ++i) {
+            taus[i] = P->tau_re[i];
+            taus[EXPM_MAX_POLES + i] = P->tau_im[i];
+            taus[2 * EXPM_MAX_POLES + i] = P->om_re[i];
+            taus[3 * EXPM_MAX_POLES + i] = P->om_im[i];
+        }
+        cuda_ok = cudaMemcpyAsync(P->small + kOffTau, taus, sizeof(taus), cudaMemcpyHostToDevice, s) == cudaSuccess;
+    }
+    if (cuda_ok) cuda_ok = cudaStreamSynchronize(s) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    if (!cuda_ok) {
+        free_plan(P);
+        return EXPM_CUDA_ERROR;
+    }
+    *out = P;
+    return EXPM_OK;
+}
+
+void expm_plan_destroy(expm_plan* plan) {
+    if (plan && plan->stream) cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+}
+
+expm_status expm_block(expm_plan* plan, double t, const double* dB, int64_t ldb, int p,
+                       double* dZ, int64_t ldz, expm_info* info) {
+    expm_status st = validate_block_args(plan, t, dB, ldb, p, dZ, ldz);
+    if (st != EXPM_OK) return st;
+    return run_block(plan, t, dB, ldb, p, dZ, ldz, info);
+}
+
+expm_status expm_block_host(expm_plan* plan, double t, const double* hB, int64_t ldb, int p,
+                            double* hZ, int64_t ldz, expm_info* info) {
+    expm_status st = validate_block_args(plan, t, hB, ldb, p, hZ, ldz);
+    if (st != EXPM_OK) return st;
+    cudaStream_t s = plan->stream;
+    const int64_t n = plan->n, ld = plan->ld;
+    CK(cudaMemcpy2DAsync(plan->Bst, ld * sizeof(double), hB, ldb * sizeof(double), n * sizeof(double), p,
+                         cudaMemcpyHostToDevice, s));
+    st = run_block(plan, t, plan->Bst, ld, p, plan->Zst, ld, info);
+    if (st != EXPM_OK && st != EXPM_NOT_CONVERGED) return st;
+    CK(cudaMemcpy2DAsync(hZ, ldz * sizeof(double), plan->Zst, ld * sizeof(double), n * sizeof(double), p,
+                         cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
+expm_status expm_op_apply(expm_plan* plan, double t, const double* dV, int64_t ldv, int p,
+                          double* dW, int64_t ldw) {
+    expm_status st = validate_block_args(plan, t, dV, ldv, p, dW, ldw);
+    if (st != EXPM_OK) return st;
+    CK(launch_cd_apply(dV, ldv, dW, ldw, p, plan->ndim, plan->ax[0].N, plan->ax[1].N, plan->ax[2].N,
+                       plan->ax, t, plan->stream));
+    return EXPM_OK;
+}
+
+expm_status expm_prec_apply(expm_plan* plan, double t, const double* dV, int64_t ldv, int p,
+                            double* dW, int64_t ldw) {
+    expm_status st = validate_block_args(plan, t, dV, ldv, p, dW, ldw);
+    if (st != EXPM_OK) return st;
+    return prec_apply_internal(plan, t, dV, ldv, p, dW, ldw);
+}
+
+expm_status expm_arnoldi(expm_plan* plan, double t, const double* dV1, int64_t ldv1, int p,
+                         double* dVout, int64_t ldvo, double* dHout, int64_t ldh) {
+    expm_status st = validate_block_args(plan, t, dV1, ldv1, p, dVout, ldvo);
+    if (st != EXPM_OK) return st;
+    if (!dHout) return EXPM_INVALID_ARG;
+    const int m = plan->opts.m;
+    if (ldh < (int64_t)(m + 1) * p) return EXPM_INVALID_ARG;
+    cudaStream_t s = plan->stream;
+    const int64_t n = plan->n, ld = plan->ld;
+    CK(cudaMemsetAsync(plan->stat, 0, sizeof(double) * kStatDoubles, s));
+    CK(cudaMemsetAsync(plan->H, 0, sizeof(double) * (size_t)plan->ldH * m * plan->p_max, s));
+    CK(launch_copy(dV1, ldv1, plan->V, ld, n, p, s));
+    for (int j = 0; j < m; ++j) {
+        st = block_step(plan, t, j, p);
+        if (st != EXPM_OK) return st;
+    }
+    CK(launch_copy(plan->V, ld, dVout, ldvo, n, (m + 1) * p, s));
+    CK(cudaMemcpy2DAsync(dHout, ldh * sizeof(double), plan->H, plan->ldH * sizeof(double),
+                         (size_t)(m + 1) * p * sizeof(double), (size_t)m * p, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(plan->hpin, plan->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return check_flags(plan->hpin);
+}
+
+}  // extern "C"

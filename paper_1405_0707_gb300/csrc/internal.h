@@ -1,0 +1,133 @@
+// internal.h -- plan layout and kernel launchers shared by the library's CUDA sources.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <vector>
+
+#include "../../include/expm_block.h"
+
+namespace expm {
+
+constexpr int kMaxP = 32;          // block width limit
+constexpr int kMaxMP = 512;        // m * p limit
+constexpr int kProjThreads = 256;
+
+// One axis of the convection-diffusion operator (t = 1): tridiag(l, c, u).
+struct Axis {
+    int N = 1;
+    double l = 0, c = 0, u = 0;
+};
+
+// Strided, two-level batched real GEMM  C = A * B  (B row-major, shared by the batch).
+struct GemmArgs {
+    const double* A;
+    const double* B;
+    double* C;
+    int M, N, K;
+    int64_t a_rs, a_cs, a_b1, a_b2;
+    int64_t c_rs, c_cs, c_b1, c_b2;
+    int ldb;
+    int nb1, nb2;
+};
+
+}  // namespace expm
+
+struct expm_plan_s {
+    expm_op_desc op{};
+    expm_opts opts{};
+    int ndim = 1;
+    expm::Axis ax[3];
+    int64_t n = 0, ld = 0;
+    int p_max = 0;
+    cudaStream_t stream = nullptr;
+    // CF table (poles with Im > 0)
+    int npoles = 0;
+    double tau_re[EXPM_MAX_POLES], tau_im[EXPM_MAX_POLES];
+    double om_re[EXPM_MAX_POLES], om_im[EXPM_MAX_POLES];
+    double omega0 = 0;
+    // preconditioner tables (device)
+    double* Qf[3] = {nullptr, nullptr, nullptr};   // diag(rho^j) Q      (N x N, row-major)
+    double* Qi[3] = {nullptr, nullptr, nullptr};   // Q diag(rho^-j)     (N x N, row-major)
+    double* lam[3] = {nullptr, nullptr, nullptr};  // axis eigenvalues (t = 1)
+    double* th_m = nullptr;                          // Thomas 1/pivot, [x * nmodes + mode]
+    double* th_c = nullptr;                          // Thomas c',      [x * nmodes + mode]
+    int64_t nmodes = 1;
+    // workspace (device)
+    double* V = nullptr;       // ld x (m+1) p_max       Krylov basis
+    double* W = nullptr;       // ld x p_max
+    double* T1 = nullptr;      // ld x p_max             transform temporaries
+    double* T2 = nullptr;
+    double* Zacc = nullptr;    // ld x p_max
+    double* Bst = nullptr;     // ld x p_max             staging for the host entry point
+    double* H = nullptr;       // ldH x m p_max, ldH = (m+1) p_max
+    int ldH = 0;
+    double* part = nullptr;    // nblk x (m+1) p_max x p_max partial sums
+    int nblk = 0;
+    double* small = nullptr;   // small scratch (see api.cu for the map)
+    double* poles = nullptr;   // per-pole elimination workspace (global fallback)
+    double* S = nullptr;       // per-pole restart factors, npoles x p x p complex
+    double* Wc_slots = nullptr;// per-pole (m+1)p x p update coefficients
+    double* stat = nullptr;    // device status block: res[16], normsq, flags (ints)
+    double* hpin = nullptr;    // pinned host mirror of stat
+    double* Zst = nullptr;     // ld x p_max staging for the host entry point
+};
+
+// ---------------------------------------------------------------- launchers
+namespace expm {
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
+cudaError_t launch_tridiag_lines(const double* in, int64_t ld_in, double* out, int64_t ld_out,
+                                 int p, int L, int64_t nmodes, double l_sub, const double* th_m,
+                                 const double* th_c, double inv_t, cudaStream_t s);
+cudaError_t launch_thomas_setup(double* th_m, double* th_c, int L, int64_t nmodes,
+                                double l, double c, double u, const double* lam_y, int Ny,
+                                const double* lam_z, int Nz, cudaStream_t s);
+cudaError_t launch_axis_setup(double* Qf, double* Qi, double* lam, int N, double l, double c,
+                              double u, cudaStream_t s);
+cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw, int p,
+                            int ndim, int nx, int ny, int nz, const Axis* ax, double t,
+                            cudaStream_t s);
+
+// block Gram-Schmidt / Cholesky-QR pieces
+cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const double* W,
+                                int64_t ldw, int p, int64_t n, double* part, int nblk,
+                                cudaStream_t s);
+cudaError_t launch_reduce_h(const double* part, int nblk, int cols, int p, double* h,
+                            double* H, int ldH, int row0, int col0, int accumulate,
+                            cudaStream_t s);
+cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
+                               int p, int64_t n, const double* h, double* part, int nblk,
+                               int gram, cudaStream_t s);
+cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,
+                        double* Rinv, double* Rtot, int first, double* H, int ldH, int hrow,
+                        int hcol, double* normsq_out, int* flags, cudaStream_t s);
+cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* Rinv,
+                        double* out, int64_t ldo, double* part, int nblk, int gram,
+                        cudaStream_t s);
+// projected solves / update
+cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
+                         const double* tau_re, const double* tau_im, const double* om_re,
+                         const double* om_im, double* S, double* work, double* Wc_slots,
+                         double* res, int* flags, cudaStream_t s);
+cudaError_t launch_combine(const double* Wc_slots, int npoles, int rows, int p, double* Wc,
+                           cudaStream_t s);
+cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
+                            const double* Wc, double* Z, int64_t ldz, int restart_copy,
+                            cudaStream_t s, int nblk);
+int consistent_blocks(int64_t n, int requested);
+cudaError_t krylov_set_smem_limits();
+cudaError_t poles_set_smem_limits();
+size_t poles_smem_bytes(int mp, int p);
+cudaError_t launch_init_S(const double* R, int p, int npoles, double* S, cudaStream_t s);
+cudaError_t launch_axpby(double a, const double* X, int64_t ldx, double b, const double* Y,
+                         int64_t ldy, double* out, int64_t ldo, int64_t n, int p,
+                         cudaStream_t s);
+cudaError_t launch_copy(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n, int p,
+                        cudaStream_t s);
+cudaError_t launch_zero(double* X, int64_t ldx, int64_t n, int p, cudaStream_t s);
+}  // namespace expm
+
+bool expm_internal_cf_table(int nu, std::vector<std::complex<double>>& tau,
+                            std::vector<std::complex<double>>& omega, double& omega0,
+                            double& sigma);

@@ -1,0 +1,488 @@
+// k_krylov.cu -- block Arnoldi pieces (Section 3, eq. (2.1); Section 4.1, eq. (4.5)).
+//
+// One block step turns W = (tA)^{-1} V_j into V_{j+1}:
+//   block classical Gram-Schmidt, twice (CGS2):  h = V^T W,  W -= V h   (x2, h summed
+//   into H), then a Cholesky QR of W with a shifted first pass (three passes in all:
+//   G = W^T W (+ shift on pass 1), G = R^T R, W <- W R^{-1}); the product of the three
+//   R factors is H_{j+1,j}, upper triangular with a positive diagonal, so the basis is
+//   the one Ruhe's vector-wise variant builds in exact arithmetic.
+//
+// The tall-skinny passes split the n rows over `nblk` CTAs; each CTA stages 16-row tiles
+// of V and W in shared memory, and writes one partial (cols x p) product per CTA.  A
+// second tiny launch sums the partials in a fixed order (deterministic), so the
+// projections need no atomics.  The update of pass 1 is fused with the projection of
+// pass 2, and the update of pass 2 with the Gram matrix of the QR, so V_j is read three
+// times per block step instead of four.
+#include "internal.h"
+
+namespace expm {
+namespace {
+
+constexpr int TR = 16;      // rows per shared-memory tile
+constexpr int NT = 256;     // threads per CTA for the row passes
+
+__device__ inline int64_t rows_begin(int64_t rpb) { return (int64_t)blockIdx.x * rpb; }
+
+// Load a TR x cols tile of column-major X (rows r0.., ld) into S[rr * cs + a], zero-filled.
+__device__ inline void load_tile(const double* __restrict__ X, int64_t ld, int cols, int64_t r0,
+                                 int tr, double* S, int cs) {
+    for (int e = threadIdx.x; e < TR * cols; e += blockDim.x) {
+        const int rr = e % TR, a = e / TR;
+        S[rr * cs + a] = (rr < tr) ? X[(int64_t)a * ld + r0 + rr] : 0.0;
+    }
+}
+
+// partial[blk][a][c] = sum_{rows of blk} V[r, a] W[r, c]      (a < cols, c < p)
+template <int OPT>
+__global__ void __launch_bounds__(NT) k_proj(const double* __restrict__ V, int64_t ldv, int cols,
+                                             const double* __restrict__ W, int64_t ldw, int p,
+                                             int64_t n, int64_t rpb, double* __restrict__ part) {
+    extern __shared__ double sm[];
+    const int cs = cols | 1;
+    double* Vs = sm;
+    double* Ws = sm + TR * cs;
+    const int nout = cols * p;
+    double acc[OPT];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) acc[q] = 0.0;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r0 = rb; r0 < re; r0 += TR) {
+        const int tr = (int)min((int64_t)TR, re - r0);
+        load_tile(V, ldv, cols, r0, tr, Vs, cs);
+        load_tile(W, ldw, p, r0, tr, Ws, p);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) {
+            const int o = threadIdx.x + q * NT;
+            if (o < nout) {
+                const int a = o / p, c = o % p;
+                double s = 0.0;
+#pragma unroll
+                for (int rr = 0; rr < TR; ++rr) s = fma(Vs[rr * cs + a], Ws[rr * p + c], s);
+                acc[q] += s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+        const int o = threadIdx.x + q * NT;
+        if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+    }
+}
+
+// h[o] = sum_b part[b][o]; H[row0 + a, col0 + c] (+)= h[a][c]
+__global__ void k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p,
+                           double* __restrict__ h, double* H, int ldH, int row0, int col0,
+                           int accumulate) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nout = cols * p;
+    if (o >= nout) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * nout + o];
+    h[o] = s;
+    if (H) {
+        const int a = o / p, c = o % p;
+        double* dst = H + (int64_t)(col0 + c) * ldH + row0 + a;
+        *dst = accumulate ? *dst + s : s;
+    }
+}
+
+// W <- W - V h ; then partial of V^T W (gram = 0) or W^T W (gram = 1).
+template <int OPT>
+__global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int64_t ldv, int cols,
+                                               double* __restrict__ W, int64_t ldw, int p,
+                                               int64_t n, int64_t rpb,
+                                               const double* __restrict__ h,
+                                               double* __restrict__ part, int gram) {
+    extern __shared__ double sm[];
+    const int cs = cols | 1;
+    double* hs = sm;                      // cols x p
+    double* Vs = hs + cols * p;           // TR x cs
+    double* Ws = Vs + TR * cs;            // TR x p
+    for (int e = threadIdx.x; e < cols * p; e += blockDim.x) hs[e] = h[e];
+    const int nout = gram ? p * p : cols * p;
+    double acc[OPT];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) acc[q] = 0.0;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r0 = rb; r0 < re; r0 += TR) {
+        const int tr = (int)min((int64_t)TR, re - r0);
+        load_tile(V, ldv, cols, r0, tr, Vs, cs);
+        load_tile(W, ldw, p, r0, tr, Ws, p);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TR * p; e += blockDim.x) {
+            const int rr = e % TR, c = e / TR;
+            double w = Ws[rr * p + c];
+            for (int a = 0; a < cols; ++a) w = fma(-Vs[rr * cs + a], hs[a * p + c], w);
+            Ws[rr * p + c] = w;
+            if (rr < tr) W[(int64_t)c * ldw + r0 + rr] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) {
+            const int o = threadIdx.x + q * NT;
+            if (o < nout) {
+                double s = 0.0;
+                if (gram) {
+                    const int c1 = o / p, c2 = o % p;
+#pragma unroll
+                    for (int rr = 0; rr < TR; ++rr) s = fma(Ws[rr * p + c1], Ws[rr * p + c2], s);
+                } else {
+                    const int a = o / p, c = o % p;
+#pragma unroll
+                    for (int rr = 0; rr < TR; ++rr) s = fma(Vs[rr * cs + a], Ws[rr * p + c], s);
+                }
+                acc[q] += s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+        const int o = threadIdx.x + q * NT;
+        if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+    }
+}
+
+// One warp: G = sum of the p x p partials (+ shift_rel * trace on the first pass),
+// upper Cholesky G = R^T R, R^{-1}, Rtot = R Rtot (Rtot = R on the first pass).  The last
+// pass writes Rtot into H (rows hrow.., cols hcol..) and checks for breakdown against the
+// column norms of W before orthogonalisation (H column above + Rtot column).
+__global__ void k_chol(const double* __restrict__ part, int nblk, int p, double shift_rel,
+                       double* R, double* Rinv, double* Rtot, int first, double* H, int ldH,
+                       int hrow, int hcol, double* normsq_out, int* flags) {
+    __shared__ double G[kMaxP * kMaxP], Rs[kMaxP * kMaxP], Ri[kMaxP * kMaxP], Rt[kMaxP * kMaxP];
+    __shared__ int bad;
+    const int lane = threadIdx.x;   // blockDim.x == 32
+    const int pp = p * p;
+    for (int o = lane; o < pp; o += 32) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * pp + o];
+        G[o] = s;
+        Rs[o] = 0.0;
+        Ri[o] = 0.0;
+    }
+    if (lane == 0) bad = 0;
+    __syncwarp();
+    double tr = 0.0;
+    for (int c = 0; c < p; ++c) tr += G[c * p + c];
+    if (normsq_out && lane == 0) *normsq_out = tr;
+    if (first && lane < p) G[lane * p + lane] += shift_rel * tr;
+    __syncwarp();
+    // right-looking upper Cholesky on G (row-major, upper part used)
+    for (int j = 0; j < p; ++j) {
+        if (lane == 0) {
+            double d = G[j * p + j];
+            if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
+            Rs[j * p + j] = sqrt(d);
+        }
+        __syncwarp();
+        const double inv = 1.0 / Rs[j * p + j];
+        if (lane > j && lane < p) Rs[j * p + lane] = G[j * p + lane] * inv;
+        __syncwarp();
+        if (lane > j && lane < p) {
+            const double rb = Rs[j * p + lane];
+            for (int a = j + 1; a <= lane; ++a) G[a * p + lane] -= Rs[j * p + a] * rb;
+        }
+        __syncwarp();
+    }
+    // inverse of the upper triangular R, column `lane`
+    if (lane < p) {
+        const int c = lane;
+        Ri[c * p + c] = 1.0 / Rs[c * p + c];
+        for (int r = c - 1; r >= 0; --r) {
+            double s = 0.0;
+            for (int k = r + 1; k <= c; ++k) s += Rs[r * p + k] * Ri[k * p + c];
+            Ri[r * p + c] = -s / Rs[r * p + r];
+        }
+    }
+    __syncwarp();
+    // Rtot = R * Rtot_old (upper triangular product), column `lane`
+    if (lane < p) {
+        const int c = lane;
+        for (int r = 0; r < p; ++r) {
+            double s;
+            if (first) s = Rs[r * p + c];
+            else {
+                s = 0.0;
+                for (int k = r; k <= c; ++k) s += Rs[r * p + k] * Rtot[k * p + c];
+            }
+            Rt[r * p + c] = (r <= c) ? s : 0.0;
+        }
+    }
+    __syncwarp();
+    for (int o = lane; o < pp; o += 32) {
+        R[o] = Rs[o];
+        Rinv[o] = Ri[o];
+        Rtot[o] = Rt[o];
+        if (!isfinite(Rt[o])) bad = 1;
+    }
+    __syncwarp();
+    if (H) {
+        for (int o = lane; o < pp; o += 32) {
+            const int a = o / p, c = o % p;
+            H[(int64_t)(hcol + c) * ldH + hrow + a] = Rt[o];
+        }
+        if (lane < p) {
+            const int c = lane;
+            double n0 = 0.0;
+            for (int a = 0; a < hrow; ++a) {
+                const double v = H[(int64_t)(hcol + c) * ldH + a];
+                n0 += v * v;
+            }
+            for (int a = 0; a <= c; ++a) n0 += Rt[a * p + c] * Rt[a * p + c];
+            if (Rt[c * p + c] <= 1e-14 * sqrt(n0)) atomicOr(&flags[1], 1);
+        }
+    }
+    __syncwarp();
+    if (lane == 0 && bad) atomicOr(&flags[0], 1);
+}
+
+// W_out = W R^{-1} (row by row); gram: also partial of W_out^T W_out.
+template <int OPT>
+__global__ void __launch_bounds__(NT) k_trsm(double* __restrict__ W, int64_t ldw, int p, int64_t n,
+                                             int64_t rpb, const double* __restrict__ Rinv,
+                                             double* __restrict__ out, int64_t ldo,
+                                             double* __restrict__ part, int gram) {
+    __shared__ double Ri[kMaxP * kMaxP];
+    __shared__ double Ws[TR * kMaxP], Wn[TR * kMaxP];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ri[e] = Rinv[e];
+    const int nout = p * p;
+    double acc[OPT];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) acc[q] = 0.0;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r0 = rb; r0 < re; r0 += TR) {
+        const int tr = (int)min((int64_t)TR, re - r0);
+        load_tile(W, ldw, p, r0, tr, Ws, p);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TR * p; e += blockDim.x) {
+            const int rr = e % TR, c = e / TR;
+            double s = 0.0;
+            for (int a = 0; a <= c; ++a) s = fma(Ws[rr * p + a], Ri[a * p + c], s);
+            Wn[rr * p + c] = s;
+            if (rr < tr) out[(int64_t)c * ldo + r0 + rr] = s;
+        }
+        __syncthreads();
+        if (gram) {
+#pragma unroll
+            for (int q = 0; q < OPT; ++q) {
+                const int o = threadIdx.x + q * NT;
+                if (o < nout) {
+                    const int c1 = o / p, c2 = o % p;
+                    double s = 0.0;
+#pragma unroll
+                    for (int rr = 0; rr < TR; ++rr) s = fma(Wn[rr * p + c1], Wn[rr * p + c2], s);
+                    acc[q] += s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (gram) {
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) {
+            const int o = threadIdx.x + q * NT;
+            if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+        }
+    }
+}
+
+// Z[r, c] += sum_{a < cols} V[r, a] Wc[a][c]; restart: V[:, 0:p] <- V[:, cols-p:cols].
+__global__ void __launch_bounds__(NT) k_update_z(double* __restrict__ V, int64_t ldv, int cols,
+                                                 int p, int64_t n, int64_t rpb,
+                                                 const double* __restrict__ Wc,
+                                                 double* __restrict__ Z, int64_t ldz,
+                                                 int restart_copy) {
+    extern __shared__ double sm[];
+    const int cs = cols | 1;
+    double* ws = sm;                 // cols x p
+    double* Vs = ws + cols * p;      // TR x cs
+    for (int e = threadIdx.x; e < cols * p; e += blockDim.x) ws[e] = Wc[e];
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r0 = rb; r0 < re; r0 += TR) {
+        const int tr = (int)min((int64_t)TR, re - r0);
+        load_tile(V, ldv, cols, r0, tr, Vs, cs);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TR * p; e += blockDim.x) {
+            const int rr = e % TR, c = e / TR;
+            if (rr < tr) {
+                double s = 0.0;
+                for (int a = 0; a < cols; ++a) s = fma(Vs[rr * cs + a], ws[a * p + c], s);
+                Z[(int64_t)c * ldz + r0 + rr] += s;
+                if (restart_copy) V[(int64_t)c * ldv + r0 + rr] = Vs[rr * cs + cols - p + c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_combine(const double* __restrict__ slots, int npoles, int nout,
+                          double* __restrict__ Wc) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nout) return;
+    double s = 0.0;
+    for (int i = 0; i < npoles; ++i) s += slots[(int64_t)i * nout + o];
+    Wc[o] = s;
+}
+
+__global__ void k_init_S(const double* __restrict__ R, int p, int npoles, double* __restrict__ S) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= npoles * p * p) return;
+    S[2 * e] = R[e % (p * p)];
+    S[2 * e + 1] = 0.0;
+}
+
+__global__ void k_axpby(double a, const double* __restrict__ X, int64_t ldx, double b,
+                        const double* __restrict__ Y, int64_t ldy, double* __restrict__ out,
+                        int64_t ldo, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= n) return;
+    const double y = Y ? Y[c * ldy + i] : 0.0;
+    out[c * ldo + i] = a * X[c * ldx + i] + b * y;
+}
+
+__global__ void k_zero(double* __restrict__ X, int64_t ldx, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) X[blockIdx.y * ldx + i] = 0.0;
+}
+
+int64_t rows_per_block(int64_t n, int nblk) {
+    int64_t r = (n + nblk - 1) / nblk;
+    return (r + TR - 1) / TR * TR;
+}
+int blocks_for(int64_t n, int nblk) {
+    const int64_t rpb = rows_per_block(n, nblk);
+    return (int)((n + rpb - 1) / rpb);
+}
+
+}  // namespace
+
+// A CTA count that the row-pass launchers reproduce exactly (rows per CTA are rounded up
+// to whole tiles, which can lower the count); every partial-sum reduction uses it.
+int consistent_blocks(int64_t n, int requested) {
+    int nb = requested < 1 ? 1 : requested;
+    for (int it = 0; it < 64; ++it) {
+        const int g = blocks_for(n, nb);
+        if (g == nb) break;
+        nb = g;
+    }
+    return nb;
+}
+
+#define EXPM_OPT_DISPATCH(NOUT, CALL)                  \
+    do {                                               \
+        const int need_ = ((NOUT) + NT - 1) / NT;      \
+        if (need_ <= 1) { constexpr int O = 1; CALL; } \
+        else if (need_ <= 4) { constexpr int O = 4; CALL; } \
+        else if (need_ <= 16) { constexpr int O = 16; CALL; } \
+        else if (need_ <= 64) { constexpr int O = 64; CALL; } \
+        else return cudaErrorInvalidValue;             \
+    } while (0)
+
+cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const double* W,
+                                int64_t ldw, int p, int64_t n, double* part, int nblk,
+                                cudaStream_t s) {
+    const int64_t rpb = rows_per_block(n, nblk);
+    const int g = blocks_for(n, nblk);
+    const size_t shm = sizeof(double) * (TR * (cols | 1) + TR * p);
+    EXPM_OPT_DISPATCH(cols * p, (k_proj<O><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, part)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_h(const double* part, int nblk_req, int cols, int p, double* h,
+                            double* H, int ldH, int row0, int col0, int accumulate,
+                            cudaStream_t s) {
+    (void)nblk_req;
+    const int nout = cols * p;
+    k_reduce_h<<<(nout + 127) / 128, 128, 0, s>>>(part, nblk_req, cols, p, h, H, ldH, row0, col0,
+                                                  accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
+                               int p, int64_t n, const double* h, double* part, int nblk,
+                               int gram, cudaStream_t s) {
+    const int64_t rpb = rows_per_block(n, nblk);
+    const int g = blocks_for(n, nblk);
+    const size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1) + TR * p);
+    const int nout = gram ? p * p : cols * p;
+    EXPM_OPT_DISPATCH(nout, (k_update<O><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,
+                        double* Rinv, double* Rtot, int first, double* H, int ldH, int hrow,
+                        int hcol, double* normsq_out, int* flags, cudaStream_t s) {
+    k_chol<<<1, 32, 0, s>>>(part, nblk, p, shift_rel, R, Rinv, Rtot, first, H, ldH, hrow, hcol,
+                            normsq_out, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* Rinv,
+                        double* out, int64_t ldo, double* part, int nblk, int gram,
+                        cudaStream_t s) {
+    const int64_t rpb = rows_per_block(n, nblk);
+    const int g = blocks_for(n, nblk);
+    EXPM_OPT_DISPATCH(p * p, (k_trsm<O><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
+                            const double* Wc, double* Z, int64_t ldz, int restart_copy,
+                            cudaStream_t s, int nblk) {
+    const int64_t rpb = rows_per_block(n, nblk);
+    const int g = blocks_for(n, nblk);
+    const size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1));
+    k_update_z<<<g, NT, shm, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const double* Wc_slots, int npoles, int rows, int p, double* Wc,
+                           cudaStream_t s) {
+    const int nout = rows * p;
+    k_combine<<<(nout + 127) / 128, 128, 0, s>>>(Wc_slots, npoles, nout, Wc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_S(const double* R, int p, int npoles, double* S, cudaStream_t s) {
+    const int tot = npoles * p * p;
+    k_init_S<<<(tot + 127) / 128, 128, 0, s>>>(R, p, npoles, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double a, const double* X, int64_t ldx, double b, const double* Y,
+                         int64_t ldy, double* out, int64_t ldo, int64_t n, int p,
+                         cudaStream_t s) {
+    dim3 grid((unsigned)((n + 255) / 256), p);
+    k_axpby<<<grid, 256, 0, s>>>(a, X, ldx, b, Y, ldy, out, ldo, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n, int p,
+                        cudaStream_t s) {
+    return launch_axpby(1.0, X, ldx, 0.0, nullptr, 0, Y, ldy, n, p, s);
+}
+
+cudaError_t launch_zero(double* X, int64_t ldx, int64_t n, int p, cudaStream_t s) {
+    dim3 grid((unsigned)((n + 255) / 256), p);
+    k_zero<<<grid, 256, 0, s>>>(X, ldx, n);
+    return cudaGetLastError();
+}
+
+// Shared-memory opt-in for the launches whose dynamic size can pass 48 KB.
+cudaError_t krylov_set_smem_limits() {
+    const int big = 227 * 1024;   // k_update_z needs up to 209 KB at m p = 512, p = 32
+    cudaError_t e = cudaSuccess;
+#define EXPM_SET(K) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
+    EXPM_SET(k_proj<1>); EXPM_SET(k_proj<4>); EXPM_SET(k_proj<16>); EXPM_SET(k_proj<64>);
+    EXPM_SET(k_update<1>); EXPM_SET(k_update<4>); EXPM_SET(k_update<16>); EXPM_SET(k_update<64>);
+    EXPM_SET(k_update_z);
+#undef EXPM_SET
+    return e;
+}
+
+}  // namespace expm

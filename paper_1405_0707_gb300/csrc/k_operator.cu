@@ -1,0 +1,215 @@
+// k_operator.cu -- operator and exact-inverse kernels for the convection-diffusion family.
+//
+// W = (tA)^{-1} V replaces the paper's "LU once, then U \ (L \ w)" (Section 4.1,
+// Section 5) by an exact structured solve: tA = t (T_x (+) T_y (+) T_z) (Kronecker sum)
+// with T_d = D_d^{-1} Q Lambda_d Q D_d (diagonal similarity D_d = diag(rho^j),
+// rho = sqrt(u/l); Q the orthonormal DST-I, symmetric, Q Q = I).  Transform every axis
+// except x with (D_d, Q), solve one tridiagonal system along x per transformed mode with
+// the shift lambda_y + lambda_z, transform back.  The transforms are small dense GEMMs
+// (DST-I for N + 1 prime or odd has no cheap power-of-two FFT), the line solves use a
+// Thomas factorisation built once per mode at plan creation.
+#include "internal.h"
+
+namespace expm {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+// C = A * B, FP64.  256 threads, 4x4 outputs per thread.  CM selects the thread layout
+// so that the fastest-varying thread index walks C's contiguous dimension.
+template <bool CM>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs g) {
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN];
+    const int b1 = blockIdx.z % g.nb1, b2 = blockIdx.z / g.nb1;
+    const double* A = g.A + b1 * g.a_b1 + b2 * g.a_b2;
+    double* C = g.C + b1 * g.c_b1 + b2 * g.c_b2;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const bool a_mfast = (g.a_rs == 1);
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * 256;
+            int mm, kk;
+            if (a_mfast) { mm = e % BM; kk = e / BM; }
+            else { kk = e % BK; mm = e / BK; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < g.M && gk < g.K) ? A[(int64_t)gm * g.a_rs + (int64_t)gk * g.a_cs] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * 256;
+            const int nn = e % BN, kk = e / BN;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < g.N && gk < g.K) ? g.B[(int64_t)gk * g.ldb + gn] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][(CM ? tx : ty) + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][(CM ? ty : tx) + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + (CM ? tx : ty) + 16 * i, nn = n0 + (CM ? ty : tx) + 16 * j;
+            if (m < g.M && nn < g.N) C[(int64_t)m * g.c_rs + (int64_t)nn * g.c_cs] = acc[i][j];
+        }
+}
+
+// One thread per (mode, column): forward elimination and back substitution along x with
+// the precomputed Thomas factors of tridiag(l, c + lambda_mode, u).  in may equal out.
+__global__ void k_tridiag_lines(const double* in, int64_t ld_in, double* out, int64_t ld_out,
+                                int p, int L, int64_t nmodes, double l_sub,
+                                const double* __restrict__ thm, const double* __restrict__ thc,
+                                double inv_t) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= nmodes * p) return;
+    const int64_t k = gid % nmodes;
+    const int c = (int)(gid / nmodes);
+    const double* f = in + c * ld_in + k;
+    double* y = out + c * ld_out + k;
+    double prev = 0.0;
+    for (int x = 0; x < L; ++x) {
+        const int64_t o = (int64_t)x * nmodes;
+        const double v = (f[o] * inv_t - l_sub * prev) * thm[o + k];
+        y[o] = v;
+        prev = v;
+    }
+    double next = prev;
+    for (int x = L - 2; x >= 0; --x) {
+        const int64_t o = (int64_t)x * nmodes;
+        next = y[o] - thc[o + k] * next;
+        y[o] = next;
+    }
+}
+
+// Thomas factors for every mode (one thread per mode): pivots b - l c'_{x-1}, stored as
+// reciprocals, and c'_x = u / pivot_x.
+__global__ void k_thomas_setup(double* thm, double* thc, int L, int64_t nmodes, double l,
+                               double c, double u, const double* lam_y, int Ny,
+                               const double* lam_z, int Nz) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nmodes) return;
+    double shift = 0.0;
+    if (lam_y) shift += lam_y[k % Ny];
+    if (lam_z) shift += lam_z[k / Ny];
+    const double b = c + shift;
+    double cp = 0.0;
+    for (int x = 0; x < L; ++x) {
+        const double piv = b - (x > 0 ? l * cp : 0.0);
+        const double mi = 1.0 / piv;
+        cp = u * mi;
+        thm[(int64_t)x * nmodes + k] = mi;
+        thc[(int64_t)x * nmodes + k] = cp;
+    }
+}
+
+// Axis eigen-data: Q[j][k] = sqrt(2/(N+1)) sin(pi (j+1)(k+1)/(N+1)) (DST-I, exact
+// integer argument reduction), Qf = diag(rho^j) Q, Qi = Q diag(rho^-j),
+// lambda_k = c + 2 s cos(pi (k+1)/(N+1)), s = sign(l) sqrt(l u).
+__global__ void k_axis_setup(double* Qf, double* Qi, double* lam, int N, double l, double c,
+                             double u) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)N * N) return;
+    const int j = (int)(e / N), k = (int)(e % N);
+    const int64_t arg = ((int64_t)(j + 1) * (k + 1)) % (2 * (int64_t)(N + 1));
+    const double q = sqrt(2.0 / (N + 1)) * sinpi((double)arg / (double)(N + 1));
+    const double rho = sqrt(u / l);
+    Qf[e] = pow(rho, (double)j) * q;              // row j (grid index), column k (mode)
+    Qi[e] = q * pow(rho, -(double)k);             // row j (mode), column k (grid index)
+    if (j == 0) {
+        const double s = (l > 0 ? 1.0 : -1.0) * sqrt(l * u);
+        lam[k] = c + 2.0 * s * cospi((double)(k + 1) / (double)(N + 1));
+    }
+}
+
+// W = tA V, 3/5/7-point stencil with Dirichlet zeros outside the grid.
+__global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __restrict__ W,
+                           int64_t ldw, int ndim, int nx, int ny, int nz, Axis ax0, Axis ax1,
+                           Axis ax2, double t) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= n) return;
+    const double* v = V + c * ldv;
+    const int ix = (int)(i % nx);
+    const int iy = (int)((i / nx) % ny);
+    const int iz = (int)(i / ((int64_t)nx * ny));
+    const double ui = v[i];
+    double acc = (ax0.c + (ndim > 1 ? ax1.c : 0.0) + (ndim > 2 ? ax2.c : 0.0)) * ui;
+    if (ix > 0) acc += ax0.l * v[i - 1];
+    if (ix < nx - 1) acc += ax0.u * v[i + 1];
+    if (ndim > 1) {
+        if (iy > 0) acc += ax1.l * v[i - nx];
+        if (iy < ny - 1) acc += ax1.u * v[i + nx];
+    }
+    if (ndim > 2) {
+        const int64_t s = (int64_t)nx * ny;
+        if (iz > 0) acc += ax2.l * v[i - s];
+        if (iz < nz - 1) acc += ax2.u * v[i + s];
+    }
+    W[c * ldw + i] = t * acc;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
+    dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, g.nb1 * g.nb2);
+    if (g.c_rs == 1) k_gemm<true><<<grid, 256, 0, s>>>(g);
+    else k_gemm<false><<<grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_lines(const double* in, int64_t ld_in, double* out, int64_t ld_out,
+                                 int p, int L, int64_t nmodes, double l_sub, const double* th_m,
+                                 const double* th_c, double inv_t, cudaStream_t s) {
+    const int64_t tot = nmodes * p;
+    const int thr = 128;
+    k_tridiag_lines<<<(unsigned)((tot + thr - 1) / thr), thr, 0, s>>>(in, ld_in, out, ld_out, p, L,
+                                                                     nmodes, l_sub, th_m, th_c, inv_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thomas_setup(double* th_m, double* th_c, int L, int64_t nmodes, double l,
+                                double c, double u, const double* lam_y, int Ny,
+                                const double* lam_z, int Nz, cudaStream_t s) {
+    const int thr = 128;
+    k_thomas_setup<<<(unsigned)((nmodes + thr - 1) / thr), thr, 0, s>>>(th_m, th_c, L, nmodes, l, c, u,
+                                                                        lam_y, Ny, lam_z, Nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axis_setup(double* Qf, double* Qi, double* lam, int N, double l, double c,
+                              double u, cudaStream_t s) {
+    const int64_t tot = (int64_t)N * N;
+    k_axis_setup<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Qf, Qi, lam, N, l, c, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw, int p,
+                            int ndim, int nx, int ny, int nz, const Axis* ax, double t,
+                            cudaStream_t s) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    dim3 grid((unsigned)((n + 255) / 256), p);
+    k_cd_apply<<<grid, 256, 0, s>>>(V, ldv, W, ldw, ndim, nx, ny, nz, ax[0], ax[1], ax[2], t);
+    return cudaGetLastError();
+}
+
+}  // namespace expm

@@ -1,0 +1,38 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the CPU baseline.
+
+This module holds none of the method's arithmetic: operator parameters and random
+right-hand sides only.  Each side (the CUDA path and the oracle) builds its own operator
+from these parameters.  Random numbers: numpy Generator(PCG64(seed)), N(0, 1), laid out
+column by column (column c of B is one contiguous draw of n numbers), seed
+20140707 + workload index.
+
+Workloads (the paper's experiments use nu = 14 CF poles, Section 5; the block sizes, grid
+sizes and times below are the synthetic stand-ins described in the design doc):
+  tridiag-1d   A = t (n+1)^2 tridiag(1, -2, 1), n = 2000, t = 1, p = 4, m = 10, tol 1e-10
+  cd2d-256     t (0.1 Laplacian_h - (1, 1) . grad_h) on a 256 x 256 interior grid,
+               n = 65536, p = 8, t in {1e-3, 1e-2, 1e-1}, m = 10
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 20140707
+
+WORKLOADS = {
+    "tridiag-1d": dict(sides=(2000,), diff=1.0, vel=(0.0,), t=(1.0,), p=4, m=10, tol=1e-10,
+                       seed=SEED_BASE + 1),
+    "cd2d-256": dict(sides=(256, 256), diff=0.1, vel=(1.0, 1.0), t=(1e-3, 1e-2, 1e-1), p=8, m=10,
+                     tol=1e-10, seed=SEED_BASE + 2),
+}
+
+
+def rhs(n, p, seed):
+    """B (n x p), i.i.d. N(0, 1), returned as a Fortran-ordered (column-major) array."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.asfortranarray(rng.standard_normal((p, n)).T)
+
+
+def to_device_colmajor(B_np, device="cuda"):
+    """Copy a numpy (n, p) array to a column-major (stride (1, n)) CUDA float64 tensor."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(B_np.T)).to(device).T

@@ -1,0 +1,103 @@
+"""GPU parity of the whole path (Algorithm 2) through the C ABI.
+
+* against the oracle's literal Algorithm 2 run for the same number of cycles (the same
+  iterate, so the only difference is rounding, amplified by the partial-fraction
+  cancellation: tolerance max(1e-10, 20 x floor), floor = eps sum 2|omega_i| ||X_i|| / ||Z||);
+* against the closed-form r(tA) B and e^{tA} B at convergence;
+* edge cases: p = 1, p = p_max, ragged n, ld > n, NOT_CONVERGED, host buffers.
+"""
+import numpy as np
+import pytest
+
+from oracle import cf, operators as ops, psbfom as ps
+from paper_1405_0707_gb300 import inputs
+from tests.gpu_util import cancellation_floor, need_gpu, rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tab():
+    return cf.load_table()
+
+
+SMALL = [((300,), 1.0, (0.0,), 1.0, 3, 5),
+         ((37, 29), 0.1, (1.0, 1.0), 1e-1, 4, 4),
+         ((40, 33), 0.1, (1.0, 1.0), 1.0, 1, 6),
+         ((11, 9, 7), 1.0, (3.0, -2.0, 1.0), 0.3, 2, 5)]
+
+
+@pytest.mark.parametrize("sides,diff,vel,t,p,m", SMALL)
+def test_fixed_cycles_parity_with_oracle(tab, sides, diff, vel, t, p, m):
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n = int(np.prod(sides))
+    B = inputs.rhs(n, p, 31)
+    for cycles in (1, 3):
+        plan = Plan(sides, diff, vel, p_max=p, m=m, fixed_cycles=cycles)
+        Zg, info = plan.expm_block(t, to_dev(B))
+        Zg = to_np(Zg)
+        Zo, io = ps.psbfom(ps.lu_inverse(ops.cd_matrix(sides, diff, vel, t)), B, tab, m=m,
+                           fixed_cycles=cycles)
+        floor = cancellation_floor(tab, io["X"], Zo)
+        assert info.cycles == cycles
+        assert rel(Zg, Zo) <= max(1e-10, 20 * floor), (cycles, rel(Zg, Zo), floor)
+        # eq. (49) residual norms agree with the oracle's
+        ro = io["residuals"][-1]
+        rg = np.array([info.resid[i] for i in range(7)])
+        assert np.allclose(rg, ro, rtol=1e-6, atol=1e-12 * np.linalg.norm(B))
+
+
+@pytest.mark.parametrize("sides,diff,vel,t,p,m", SMALL)
+def test_converged_matches_closed_form(tab, sides, diff, vel, t, p, m):
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n = int(np.prod(sides))
+    B = inputs.rhs(n, p, 32)
+    plan = Plan(sides, diff, vel, p_max=p, m=m, tol=1e-12, max_cycles=300)
+    Zg, info = plan.expm_block(t, to_dev(B))
+    assert info.converged == 1
+    Zg = to_np(Zg)
+    ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+    _, io = ps.psbfom(ps.lu_inverse(ops.cd_matrix(sides, diff, vel, t)), B, tab, m=m, tol=1e-12,
+                      max_cycles=300)
+    floor = cancellation_floor(tab, io["X"], ref)
+    assert rel(Zg, ref) <= max(1e-10, 50 * floor)
+
+
+def test_edge_cases(tab):
+    need_gpu()
+    import torch
+    from paper_1405_0707_gb300 import Plan, colmajor
+    from paper_1405_0707_gb300 import _native as N
+    sides, diff, vel, t = (23, 19), 0.1, (1.0, 1.0), 0.5
+    n = 23 * 19
+    plan = Plan(sides, diff, vel, p_max=5, m=3, tol=1e-11, max_cycles=200)
+    ref_all = ops.exact_r_of_A_B(sides, diff, vel, t, tab, inputs.rhs(n, 5, 3))
+    # p = 1 and p = p_max against the closed form
+    for p in (1, 5):
+        B = inputs.rhs(n, 5, 3)[:, :p]
+        Zg, info = plan.expm_block(t, to_dev(B))
+        assert info.converged and rel(to_np(Zg), ref_all[:, :p]) < 1e-9
+    # leading dimensions larger than n
+    B = inputs.rhs(n, 5, 3)
+    Bd = colmajor(n, 5, ld=n + 7)
+    Bd.copy_(to_dev(B))
+    Zd = colmajor(n, 5, ld=n + 3)
+    plan.expm_block(t, Bd, Zd)
+    assert rel(to_np(Zd), ref_all) < 1e-9
+    # host-buffer entry point gives the same numbers
+    hB = torch.from_numpy(np.ascontiguousarray(B.T)).T.pin_memory() if False else torch.from_numpy(np.ascontiguousarray(B.T)).T
+    hZ = torch.empty((5, n), dtype=torch.float64).T
+    plan.expm_block_host(t, hB, hZ)
+    assert rel(hZ.numpy(), to_np(Zd)) < 1e-15
+    # NOT_CONVERGED with one cycle still writes Z and fills info
+    one = Plan(sides, diff, vel, p_max=5, m=1, tol=1e-14, max_cycles=1)
+    Zg, info = one.expm_block(t, to_dev(B))
+    assert info.cycles == 1 and info.converged == 0
+    assert np.all(np.isfinite(to_np(Zg)))
+    # bad arguments
+    with pytest.raises(N.ExpmError):
+        plan.expm_block(-1.0, to_dev(B))
+    with pytest.raises(ValueError):
+        plan.expm_block(t, to_dev(np.ones((n + 1, 2))))
