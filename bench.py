@@ -1,0 +1,474 @@
+"""Throughput of Z = r(tA) B (preconditioned shifted block FOM, Algorithm 2) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload cd2d-256|tridiag-1d]
+
+One step = one pass of the whole hot path over one batch: for the default workload
+(cd2d-256: 2-D convection-diffusion, 256 x 256 interior grid, n = 65536, p = 8 columns
+of N(0,1), m = 10, tol 1e-10) one expm_block call per time t in {1e-3, 1e-2, 1e-1},
+i.e. 24 right-hand-side columns.  The metric is RHS columns per second (higher is
+better).  Inputs are resident in HBM when the timed region starts; before every timed
+step a 512 MB buffer is written to flush the 129 MB L2 (the working set, about 60 MB,
+would otherwise stay L2-resident across steps), outside the event-timed interval.
+
+Multi-GPU: the path does not shard (the block Krylov space couples the p columns), so
+N > 1 runs N independent replicas, one per rank, each on its own seeded batch ("weak"
+scaling); the only collectives are the timing barrier and the max over ranks.
+
+--impl reference times the CPU oracle (oracle/, plain FP64 numpy/scipy, sparse LU and
+Ruhe's vector-wise block Arnoldi) on the host cores, on a bounded sample of the same
+workload, and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "e^{tA}B RHS-columns/sec at rel.err≤1e-8 vs plain FP64 GPU path; SpMM HBM GB/s"
+UNIT = "RHS-columns/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070   # SMs x FP64 FMA/clk/SM x flop/FMA x GHz = 1.259e3 GF/s
+L2_FLUSH_BYTES = 512 << 20
+KERNEL_OF = {"gemm": "k_gemm (DST-I transforms of the exact inverse, FP64)",
+             "cgs": "k_proj/k_update (block CGS2 row passes, FP64)",
+             "stencil": "k_cd_apply (stencil W = tA V, FP64)",
+             "update": "k_update_z (Z += V_{m+1} Wc, FP64)",
+             "tridiag": "k_tridiag_lines (Thomas line solves, FP64)",
+             "qr": "k_chol/k_trsm (Cholesky QR, FP64)"}
+
+
+def _hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0      # fallback figure of the profiling recipe
+
+
+HBM_PEAK_GBS = _hbm_peak()
+
+
+def algorithmic_work(sides, p, m, cycles, algs):
+    """(flops, bytes) per step of every kernel class, from the algorithm's own counts:
+    minimum traffic (each operand read once per pass, results written once)."""
+    n = 1
+    for s_ in sides:
+        n *= s_
+    nx = sides[0]
+    trans = 1
+    for s_ in sides[1:]:
+        trans *= s_
+    out = {k: [0.0, 0.0] for k in ("gemm", "cgs", "stencil", "update", "tridiag", "qr")}
+    for t, c in cycles.items():
+        alg = algs[t]
+        steps = c * m
+        sum_cols = p * m * (m + 1) / 2            # sum over block steps of (j+1) p
+        out["cgs"][0] += c * (8.0 * n * p * sum_cols + 2.0 * n * p * p * m)
+        out["cgs"][1] += c * 8.0 * (3.0 * n * sum_cols + 5.0 * n * p * m)
+        out["qr"][0] += steps * 5.0 * n * p * p
+        out["qr"][1] += steps * 8.0 * 6.0 * n * p
+        out["update"][0] += c * 2.0 * n * (m + 1) * p * p
+        out["update"][1] += c * 8.0 * (n * (m + 1) * p + 2.0 * n * p)
+        if alg == 2:
+            # per apply: forward + inverse transform along every axis but x (2-D case)
+            out["gemm"][0] += steps * 2 * 2.0 * nx * trans * (sum(sides[1:]) if len(sides) > 1 else 0) * p
+            out["gemm"][1] += steps * 2 * 8.0 * 2.0 * n * p
+            out["tridiag"][0] += steps * 5.0 * n * p
+            out["tridiag"][1] += steps * 8.0 * (2.0 * n * p + 2.0 * n)
+        else:
+            out["stencil"][0] += steps * 2.0 * (2 * len(sides) + 1) * n * p
+            out["stencil"][1] += steps * 8.0 * 2.0 * n * p
+    return {k: tuple(v) for k, v in out.items()}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cd2d-256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--component", default=None, choices=[None, "prec", "stencil", "expm"],
+                    help="time one entry point of the library on the workload's shapes "
+                         "(used for the ncu captures) instead of the full bench")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--t", type=float, default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (200 ms period)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1])]
+        mx = [num(r[2]) for r in self.rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        load = [s for s in sm if mx and s >= 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# --------------------------------------------------------------------------- our arm
+def traffic_record(kernel):
+    """ncu DRAM bytes per launch recorded in profiles/ncu_traffic.json, or None when the
+    kernel's source changed since the capture (sha256 of the source file)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+        src = os.path.join(ROOT, rec["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+            return None
+        return rec["bytes_per_launch_full"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1405_0707_gb300 import Plan, inputs
+    from paper_1405_0707_gb300 import _native as N
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    w = inputs.WORKLOADS[args.workload]
+    sides, p, m = w["sides"], w["p"], w["m"]
+    n = int(np.prod(sides))
+    times = w["t"]
+    N.load()
+    stream = torch.cuda.Stream(device=dev)
+    plan = Plan(sides, w["diff"], w["vel"], p_max=p, m=m, tol=w["tol"], max_cycles=200, stream=stream)
+    Bh = inputs.rhs(n, p, w["seed"] + 1000 * rank)
+    with torch.cuda.stream(stream):
+        B = inputs.to_device_colmajor(Bh, device=dev)
+        Z = torch.empty((p, n), dtype=torch.float64, device=dev).T
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    hB = torch.from_numpy(np.ascontiguousarray(Bh.T)).pin_memory().T
+    hZ = torch.empty((p, n), dtype=torch.float64).pin_memory().T
+    torch.cuda.synchronize()
+
+    def step():
+        infos = []
+        for t in times:
+            _, info = plan.expm_block(t, B, Z)
+            infos.append(info)
+        return infos
+
+    def step_host():
+        for t in times:
+            plan.expm_block_host(t, hB, hZ)
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(k):
+            with torch.cuda.stream(stream):
+                flush.fill_(i)
+                ev[i][0].record(stream)
+            fn()
+            with torch.cuda.stream(stream):
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if pg:
+            pg.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        return ms, wall
+
+    for _ in range(max(1, args.warmup)):
+        infos = step()
+    torch.cuda.synchronize()
+    cycles = [int(i.cycles) for i in infos]
+    algs = [int(i.algorithm) for i in infos]
+    conv = all(int(i.converged) for i in infos)
+    # main timed region (device time, CUDA events on the plan's stream) + clocks
+    plan.profile(False)
+    _, l0 = plan.get_profile()
+    with ClockSampler(local) as clk:
+        ms, wall = timed(step, args.steps)
+    _, l1 = plan.get_profile()
+    launches = l1 - l0
+    clocks = clk.summary()
+    # end to end through the public host-buffer entry point (H2D + D2H inside)
+    for _ in range(max(1, args.warmup // 2)):
+        step_host()
+    ms_e2e, _ = timed(step_host, args.steps)
+    # per-kernel-class timing pass (events around every launch inside the library)
+    plan.profile(True)
+    ms_prof, _ = timed(step, args.steps)
+    prof, _ = plan.get_profile()
+    plan.profile(False)
+    t_max = ms
+    t_e2e = ms_e2e
+    if pg:
+        import torch.distributed as dist
+        tt = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, t_e2e = float(tt[0]), float(tt[1])
+    cols = world * args.steps * len(times) * p
+    value = cols / (t_max / 1e3)
+    e2e = cols / (t_e2e / 1e3)
+    # rooflines: analytic algorithmic flops / bytes of every kernel class over the profiled
+    # pass, divided by its event-timed duration
+    alg_work = algorithmic_work(sides, p, m, dict(zip(times, cycles)), dict(zip(times, algs)))
+    roofs = {}
+    for k, (fl, by) in alg_work.items():
+        ms_k, n_k = prof.get(k, (0.0, 0))
+        if n_k == 0 or ms_k <= 0:
+            continue
+        sec = ms_k / 1e3
+        fl_s, by_s = fl * args.steps / sec, by * args.steps / sec
+        roofs[k] = {"launches_per_step": n_k // args.steps, "ms_per_step": ms_k / args.steps,
+                    "tflops": fl_s / 1e12, "gbs": by_s / 1e9,
+                    "frac_fp64_alu": fl_s / 1e12 / (FP64_PEAK_TFLOPS / 1e3),
+                    "frac_hbm": by_s / 1e9 / HBM_PEAK_GBS}
+    dom = max(roofs, key=lambda k: roofs[k]["ms_per_step"])
+    r = roofs[dom]
+    fl_launch = alg_work[dom][0] / max(1, r["launches_per_step"])
+    by_launch = alg_work[dom][1] / max(1, r["launches_per_step"])
+    if r["frac_fp64_alu"] >= r["frac_hbm"]:
+        roof = {"kernel": KERNEL_OF[dom], "bound": "alu", "achieved": round(r["tflops"], 4),
+                "peak": round(FP64_PEAK_TFLOPS / 1e3, 4), "unit": "TFLOP/s",
+                "frac": round(r["frac_fp64_alu"], 4)}
+    else:
+        roof = {"kernel": KERNEL_OF[dom], "bound": "hbm", "achieved": round(r["gbs"], 1),
+                "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": round(r["frac_hbm"], 4)}
+    roof.update({"traffic": traffic_record(dom), "flops_per_launch": fl_launch,
+                 "bytes_per_launch": by_launch,
+                 "launch_ms": r["ms_per_step"] / max(1, r["launches_per_step"]),
+                 "peak_note": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz (probe 1.26 TF/s); "
+                              "HBM: measured copy GB/s"})
+    stages = {k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] // args.steps}
+              for k, v in prof.items() if v[1]}
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded N(0,1) right-hand sides; operator from its definition)",
+        "config": {"workload": args.workload, "n": n, "grid": list(sides), "p": p, "m": m,
+                   "t": list(times), "tol": w["tol"], "nu": 14, "precision": "fp64",
+                   "columns_per_step": len(times) * p, "cycles_per_t": cycles,
+                   "algorithm_per_t": algs,
+                   "converged": conv, "l2": "flushed before every timed step (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e, 3), "unit": UNIT,
+                "h2d_bytes_per_step": len(times) * n * p * 8,
+                "d2h_bytes_per_step": len(times) * n * p * 8},
+        "gpu_launches": int(launches) * world,
+        "roofline": roof,
+        "rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                      for k, v in roofs.items()},
+        "stages": stages,
+        "clocks": clocks,
+        "wall_s_timed": round(wall, 3),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, dict(zip(times, algs)),
+                                            dict(zip(times, cycles)))
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    plan.close()
+    if pg:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- oracle arm
+def auto_algorithm(workload, t):
+    """The library's AUTO rule, restated on the host: Algorithm 2 iff the Gershgorin bound
+    of ||tA|| is >= 50 max|tau| (eq. (43)).  The pole modulus comes from the stored table."""
+    from oracle import cf
+    from paper_1405_0707_gb300 import inputs
+    w = inputs.WORKLOADS[workload]
+    bound = t * sum(4.0 * w["diff"] * (s + 1) ** 2 for s in w["sides"])
+    taumax = max(abs(z) for z in cf.load_table()["tau"])
+    return 2 if bound >= 50.0 * taumax else 1
+
+
+def oracle_sample(workload, t, alg):
+    """One complete oracle solve for one t: Algorithm 2 (sparse LU inner solve) or
+    Algorithm 1 (sparse matvec), literal, Ruhe's vector-wise block Arnoldi."""
+    import numpy as np
+
+    from oracle import cf, operators, psbfom
+    from paper_1405_0707_gb300 import inputs
+    w = inputs.WORKLOADS[workload]
+    n = int(np.prod(w["sides"]))
+    B = inputs.rhs(n, w["p"], w["seed"])
+    A = operators.cd_matrix(w["sides"], w["diff"], w["vel"], t)
+    t0 = time.perf_counter()
+    if alg == 2:
+        Z, info = psbfom.psbfom(psbfom.lu_inverse(A), B, cf.load_table(), m=w["m"], tol=w["tol"],
+                                max_cycles=200)
+    else:
+        Z, info = psbfom.sbfom(psbfom.matvec(A), B, cf.load_table(), m=w["m"], tol=w["tol"],
+                               max_cycles=400)
+    return time.perf_counter() - t0, w["p"], info
+
+
+def cpu_baseline(workload, algs, gpu_cycles, budget_s=32.0, sec_per_cycle=2.8):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload:
+    complete solves of its t values, cheapest first by an estimate (GPU cycle count x the
+    oracle's ~2.8 s per cycle at n = 65536), while the estimated total stays within
+    ~budget_s (at least one)."""
+    from paper_1405_0707_gb300 import inputs
+    w = inputs.WORKLOADS[workload]
+    tot, cols, done, est = 0.0, 0, [], 0.0
+    for t in sorted(w["t"], key=lambda x: gpu_cycles.get(x, 0)):
+        e = sec_per_cycle * gpu_cycles.get(t, 1) + 2.0
+        if done and est + e > budget_s:
+            continue
+        est += e
+        dt, p, info = oracle_sample(workload, t, algs.get(t, auto_algorithm(workload, t)))
+        tot += dt
+        cols += p
+        done.append({"t": t, "algorithm": algs.get(t), "s": round(dt, 2), "cycles": info["cycles"]})
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": round(cols / tot, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"complete oracle solves for t in {[d['t'] for d in done]} of "
+                      f"{list(w['t'])} (p = {w['p']} each; numpy/scipy with their default "
+                      f"threads): {done}"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1405_0707_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    t = min(w["t"])          # the cheapest solve of the workload keeps each step bounded
+    alg = auto_algorithm(args.workload, t)
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, t, alg)
+    tot, cols = 0.0, 0
+    for _ in range(args.steps):
+        dt, p, info = oracle_sample(args.workload, t, alg)
+        tot += dt
+        cols += p
+    value = cols / tot
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"one complete oracle solve per step at t = {t} (Algorithm {alg}, p = {w['p']}, "
+              f"grid {w['sides']}), the cheapest t of the workload")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * tot / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "t": [t], "p": w["p"]},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_component(args):
+    """Time one library entry point on the workload's shapes (for ncu captures)."""
+    import numpy as np
+    import torch
+
+    from paper_1405_0707_gb300 import Plan, inputs
+    w = inputs.WORKLOADS[args.workload]
+    n, p = int(np.prod(w["sides"])), w["p"]
+    t = args.t if args.t is not None else max(w["t"])
+    plan = Plan(w["sides"], w["diff"], w["vel"], p_max=p, m=w["m"], tol=w["tol"])
+    B = inputs.to_device_colmajor(inputs.rhs(n, p, w["seed"]))
+    Wd = torch.empty((p, n), dtype=torch.float64, device="cuda").T
+    fn = {"prec": lambda: plan.prec_apply(t, B, Wd), "stencil": lambda: plan.op_apply(t, B, Wd),
+          "expm": lambda: plan.expm_block(t, B, Wd)}[args.component]
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"component": args.component, "workload": args.workload, "t": t,
+                      "ms_per_call": e0.elapsed_time(e1) / args.reps}))
+    plan.close()
+
+
+def main():
+    args = parse()
+    if args.component:
+        run_component(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -69,12 +69,26 @@ typedef enum {
     EXPM_PREC_FP64 = 0     /* every step in FP64 (the plain path)                    */
 } expm_precision;
 
+/* Which of the paper's two algorithms runs.  Algorithm 2 (PSBFOM, Krylov operator
+ * (tA)^{-1}) pays off when ||tA|| >> |tau_i| (eq. (43), Example 5.2); Algorithm 1 (SBFOM,
+ * Krylov operator tA, Section 3) is the better choice when ||tA|| is comparable to the
+ * poles.  AUTO picks Algorithm 2 iff the Gershgorin bound of ||tA|| is at least
+ * EXPM_AUTO_RATIO * max_i |tau_i| (a build choice). */
+typedef enum {
+    EXPM_ALG_AUTO = 0,
+    EXPM_ALG_SBFOM = 1,     /* Algorithm 1 */
+    EXPM_ALG_PSBFOM = 2     /* Algorithm 2 */
+} expm_algorithm;
+#define EXPM_AUTO_RATIO 50.0
+
 typedef struct {
     int32_t m;             /* block Arnoldi steps per cycle (restart length), >= 1   */
     int32_t max_cycles;    /* cap on restart cycles, >= 1                            */
-    double  tol;           /* stop when max_i ||R_i||_F <= tol ||B||_F  (eq. (49))   */
+    double  tol;           /* stop when max_i ||R_i||_F <= tol ||B||_F  (eq. (49) /
+                              eq. (365) for Algorithm 1)                             */
     int32_t precision;     /* expm_precision                                         */
     int32_t fixed_cycles;  /* > 0: run exactly this many cycles, ignoring tol        */
+    int32_t algorithm;     /* expm_algorithm                                         */
 } expm_opts;
 
 #define EXPM_MAX_POLES 16
@@ -88,6 +102,8 @@ typedef struct {
     int32_t npoles;              /* nu/2 poles with Im tau > 0                        */
     double  resid[EXPM_MAX_POLES]; /* eq. (49) norms ||R_i||_F after the last cycle   */
     double  normB;               /* ||B||_F                                          */
+    int32_t algorithm;           /* 1 or 2: the algorithm that ran                   */
+    double  normA_bound;         /* Gershgorin bound of ||tA|| used by AUTO          */
 } expm_info;
 
 typedef struct expm_plan_s expm_plan;
@@ -127,7 +143,8 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
 void expm_plan_destroy(expm_plan* plan);
 
 /* ---------------------------------------------------------------------------------
- * expm_block -- Z = r(tA) B by Algorithm 2 (PSBFOM, restart without deflation).
+ * expm_block -- Z = r(tA) B by Algorithm 2 (PSBFOM, restart without deflation), or by
+ * Algorithm 1 (SBFOM) when opts.algorithm asks for it or AUTO selects it.
  *   t      : time, t > 0 (t is folded into A as in Section 1)
  *   dB     : device, n x p, leading dimension ldb >= n (not modified)
  *   p      : 1 <= p <= p_max
@@ -138,6 +155,8 @@ void expm_plan_destroy(expm_plan* plan);
  * in one launch, the eq. (49) norms, and the update Z += V_{m+1} sum_i 2 Re(omega_i
  * H~_m Z_i), which equals sum_i 2 Re(omega_i (X_i - X_i^0)) because
  * (tA)^{-1} V_m = V_{m+1} H~_m (eq. (4.5)) and X_i = (tA)^{-1} Y_i.
+ * Algorithm 1 instead applies W = tA V_j, solves (H_m - tau_i I) Z_i = E_1 S_i (eq. (3.3)),
+ * restarts from S_i = -H_{m+1,m} E_m^T Z_i (eq. (35)) and adds V_m sum_i 2 Re(omega_i Z_i).
  * Returns EXPM_NOT_CONVERGED (Z holds the last iterate) if max_cycles is reached.
  * Synchronises the plan's stream once per cycle (residual norms to the host).
  * ------------------------------------------------------------------------------ */
@@ -177,6 +196,31 @@ expm_status expm_prec_apply(expm_plan* plan, double t, const double* dV, int64_t
  * (breakdown flag).  Errors: EXPM_INVALID_ARG, EXPM_NUMERICAL, EXPM_CUDA_ERROR. */
 expm_status expm_arnoldi(expm_plan* plan, double t, const double* dV1, int64_t ldv1, int p,
                          double* dVout, int64_t ldvo, double* dHout, int64_t ldh);
+
+/* ---------------------------------------------------------------------------------
+ * Profiling (not part of the paper: measurement support).  Kernel launches are always
+ * counted; with profiling enabled, CUDA events on the plan's stream bracket every launch
+ * and their durations are accumulated per kernel class at each stream synchronisation.
+ * expm_plan_profile(plan, 1) resets the counters and enables timing, (plan, 0) disables.
+ * expm_plan_get_profile copies min(nstages, EXPM_NSTAGES) entries (host arrays, either may
+ * be NULL) and the total launch count.  Errors: EXPM_INVALID_ARG, EXPM_CUDA_ERROR.
+ * ------------------------------------------------------------------------------ */
+typedef enum {
+    EXPM_STAGE_GEMM = 0,      /* DST-I transforms of the exact inverse (batched FP64 GEMM) */
+    EXPM_STAGE_TRIDIAG = 1,   /* tridiagonal line solves of the exact inverse            */
+    EXPM_STAGE_CGS = 2,       /* block CGS2 row passes (projection / update)             */
+    EXPM_STAGE_REDUCE = 3,    /* partial-sum reductions of the projections                */
+    EXPM_STAGE_QR = 4,        /* Cholesky-QR (Gram/Cholesky/triangular solve)             */
+    EXPM_STAGE_POLES = 5,     /* projected shifted systems (eq. (3236)) + combination     */
+    EXPM_STAGE_UPDATE = 6,    /* Z += V_{m+1} Wc and restart copy                          */
+    EXPM_STAGE_OTHER = 7,     /* copies, initialisation, final Z = omega_0 B + Z_acc       */
+    EXPM_STAGE_STENCIL = 8,   /* W = tA V                                                  */
+    EXPM_NSTAGES = 9
+} expm_stage;
+
+expm_status expm_plan_profile(expm_plan* plan, int enable);
+expm_status expm_plan_get_profile(expm_plan* plan, double* stage_ms, int64_t* stage_launches,
+                                  int nstages, int64_t* total_launches);
 
 const char* expm_status_str(expm_status s);
 

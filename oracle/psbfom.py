@@ -71,7 +71,7 @@ def block_arnoldi_ruhe(op, V1, m, start_vectors=None, H0=None):
     Returns (V, H, m_done, breakdown): V is n x (m_done+1)p, H is (m_done+1)p x m_done p.
     """
     n, p = V1.shape if start_vectors is None else (start_vectors.shape[0], V1.shape[1])
-    V = np.zeros((n, (m + 1) * p))
+    V = np.zeros((n, (m + 1) * p), order="F")     # basis vectors are columns
     H = np.zeros(((m + 1) * p, m * p))
     if start_vectors is None:
         V[:, :p] = V1

@@ -20,12 +20,16 @@ EXPM_NO_MEMORY = 6
 EXPM_INTERNAL = 7
 EXPM_OP_CONV_DIFF = 0
 EXPM_PREC_FP64 = 0
+EXPM_ALG_AUTO = 0
+EXPM_ALG_SBFOM = 1
+EXPM_ALG_PSBFOM = 2
 EXPM_MAX_POLES = 16
 
 # Every exported function the header declares (checked by the CPU test suite).
 EXPORTS = ("expm_cf_coeffs", "expm_plan_create", "expm_plan_destroy", "expm_block",
            "expm_block_host", "expm_op_apply", "expm_prec_apply", "expm_arnoldi",
-           "expm_status_str")
+           "expm_plan_profile", "expm_plan_get_profile", "expm_status_str")
+STAGES = ("gemm", "tridiag", "cgs", "reduce", "qr", "poles", "update", "other", "stencil")
 
 
 class expm_op_desc(C.Structure):
@@ -35,13 +39,14 @@ class expm_op_desc(C.Structure):
 
 class expm_opts(C.Structure):
     _fields_ = [("m", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double),
-                ("precision", C.c_int32), ("fixed_cycles", C.c_int32)]
+                ("precision", C.c_int32), ("fixed_cycles", C.c_int32), ("algorithm", C.c_int32)]
 
 
 class expm_info(C.Structure):
     _fields_ = [("cycles", C.c_int32), ("block_steps", C.c_int32), ("matvecs", C.c_int64),
                 ("converged", C.c_int32), ("breakdown", C.c_int32), ("npoles", C.c_int32),
-                ("resid", C.c_double * EXPM_MAX_POLES), ("normB", C.c_double)]
+                ("resid", C.c_double * EXPM_MAX_POLES), ("normB", C.c_double),
+                ("algorithm", C.c_int32), ("normA_bound", C.c_double)]
 
 
 _lib = None
@@ -84,6 +89,11 @@ def load(build_if_missing: bool = False):
         f.argtypes = [p, d, p, i64, i32, p, i64]
     lib.expm_arnoldi.restype = C.c_int
     lib.expm_arnoldi.argtypes = [p, d, p, i64, i32, p, i64, p, i64]
+    lib.expm_plan_profile.restype = C.c_int
+    lib.expm_plan_profile.argtypes = [p, C.c_int]
+    lib.expm_plan_get_profile.restype = C.c_int
+    lib.expm_plan_get_profile.argtypes = [p, C.POINTER(d), C.POINTER(C.c_int64), C.c_int,
+                                          C.POINTER(C.c_int64)]
     _lib = lib
     return lib
 
@@ -155,3 +165,17 @@ def expm_prec_apply(plan, t, dV, ldv, p, dW, ldw):
 def expm_arnoldi(plan, t, dV1, ldv1, p, dVout, ldvo, dHout, ldh):
     check(load().expm_arnoldi(plan, t, C.c_void_p(dV1), ldv1, p, C.c_void_p(dVout), ldvo,
                               C.c_void_p(dHout), ldh), "expm_arnoldi")
+
+
+def expm_plan_profile(plan, enable):
+    check(load().expm_plan_profile(plan, int(enable)), "expm_plan_profile")
+
+
+def expm_plan_get_profile(plan):
+    """{stage: (ms, launches)}, total launches."""
+    k = len(STAGES)
+    ms = (C.c_double * k)()
+    nl = (C.c_int64 * k)()
+    tot = C.c_int64()
+    check(load().expm_plan_get_profile(plan, ms, nl, k, C.byref(tot)), "expm_plan_get_profile")
+    return {STAGES[i]: (ms[i], nl[i]) for i in range(k)}, tot.value

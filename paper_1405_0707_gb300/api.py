@@ -37,7 +37,7 @@ class Plan:
     """A plan for tA = t (diff Laplacian_h - vel . grad_h) on a 1/2/3-D grid (x fastest)."""
 
     def __init__(self, sides, diff, vel, p_max, m=10, tol=1e-10, max_cycles=200,
-                 fixed_cycles=0, stream=None):
+                 fixed_cycles=0, stream=None, algorithm=0):
         import torch
         sides = tuple(int(s) for s in sides)
         vel = tuple(float(v) for v in vel)
@@ -54,6 +54,7 @@ class Plan:
         opts.m, opts.max_cycles, opts.tol = int(m), int(max_cycles), float(tol)
         opts.precision = N.EXPM_PREC_FP64
         opts.fixed_cycles = int(fixed_cycles)
+        opts.algorithm = int(algorithm)        # 0 auto, 1 SBFOM (Algorithm 1), 2 PSBFOM (Algorithm 2)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
         self.n = 1
@@ -71,6 +72,14 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def profile(self, enable=True):
+        """Reset and enable (or disable) per-kernel-class event timing inside the library."""
+        N.expm_plan_profile(self._h, enable)
+
+    def get_profile(self):
+        """({stage: (ms, launches)}, total launches) since the last profile(True)."""
+        return N.expm_plan_get_profile(self._h)
 
     # ------------------------------------------------------------------ entry points
     def expm_block(self, t, B, Z=None):

@@ -41,22 +41,57 @@ inline int* flags_of(double* stat) { return reinterpret_cast<int*>(stat + 24); }
 
 double* sm(expm_plan* P, size_t off) { return P->small + off; }
 
+// ---- profiling: count every launch; with profiling on, bracket it with events
+constexpr int kEventPool = 2048;
+int prof_begin(expm_plan* P) {
+    if (!P->prof || P->ev_used + 2 > (int)P->ev.size()) return -1;
+    const int e = P->ev_used;
+    P->ev_used += 2;
+    cudaEventRecord(P->ev[e], P->stream);
+    return e;
+}
+void prof_end(expm_plan* P, int stage, int e, int nlaunch) {
+    P->launches += nlaunch;
+    P->stage_launches[stage] += nlaunch;
+    if (e < 0) return;
+    cudaEventRecord(P->ev[e + 1], P->stream);
+    P->pend_stage.push_back(stage);
+}
+// after a stream synchronisation: fold the pending event pairs into the stage totals
+void prof_flush(expm_plan* P) {
+    for (size_t k = 0; k < P->pend_stage.size(); ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P->ev[2 * k], P->ev[2 * k + 1]) == cudaSuccess)
+            P->stage_ms[P->pend_stage[k]] += ms;
+    }
+    P->pend_stage.clear();
+    P->ev_used = 0;
+}
+
+#define LAUNCH(stage, call)                          \
+    do {                                             \
+        const int e_ = prof_begin(P);                \
+        if ((call) != cudaSuccess) return EXPM_CUDA_ERROR; \
+        prof_end(P, (stage), e_, 1);                 \
+    } while (0)
+
 expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, int hrow, int hcol,
                      double* normsq, bool gram_done) {
     cudaStream_t s = P->stream;
     const int64_t n = P->n, ld = P->ld;
     const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * std::ldexp(1.0, -53);
     int* flags = flags_of(P->stat);
-    if (!gram_done) CK(launch_proj_partial(P->W, ld, p, P->W, ld, p, n, P->part, P->nblk, s));
-    CK(launch_chol(P->part, P->nblk, p, shift, sm(P, kOffR), sm(P, kOffRi), sm(P, kOffRt), 1,
-                   nullptr, 0, 0, 0, normsq, flags, s));
-    CK(launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, s));
-    CK(launch_chol(P->part, P->nblk, p, 0.0, sm(P, kOffR), sm(P, kOffRi), sm(P, kOffRt), 0,
-                   nullptr, 0, 0, 0, nullptr, flags, s));
-    CK(launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, s));
-    CK(launch_chol(P->part, P->nblk, p, 0.0, sm(P, kOffR), sm(P, kOffRi), sm(P, kOffRt), 0,
-                   withH ? P->H : nullptr, P->ldH, hrow, hcol, nullptr, flags, s));
-    CK(launch_trsm(P->W, ld, p, n, sm(P, kOffRi), out, ldo, nullptr, P->nblk, 0, s));
+    if (!gram_done) LAUNCH(EXPM_STAGE_QR, launch_proj_partial(P->W, ld, p, P->W, ld, p, n, P->part, P->nblk, s));
+    LAUNCH(EXPM_STAGE_QR, launch_chol(P->part, P->nblk, p, shift, sm(P, kOffR), sm(P, kOffRi),
+                                      sm(P, kOffRt), 1, nullptr, 0, 0, 0, normsq, flags, s));
+    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, s));
+    LAUNCH(EXPM_STAGE_QR, launch_chol(P->part, P->nblk, p, 0.0, sm(P, kOffR), sm(P, kOffRi),
+                                      sm(P, kOffRt), 0, nullptr, 0, 0, 0, nullptr, flags, s));
+    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, s));
+    LAUNCH(EXPM_STAGE_QR, launch_chol(P->part, P->nblk, p, 0.0, sm(P, kOffR), sm(P, kOffRi),
+                                      sm(P, kOffRt), 0, withH ? P->H : nullptr, P->ldH, hrow, hcol,
+                                      nullptr, flags, s));
+    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), out, ldo, nullptr, P->nblk, 0, s));
     return EXPM_OK;
 }
 
@@ -68,44 +103,51 @@ expm_status prec_apply_internal(expm_plan* P, double t, const double* V, int64_t
     const int64_t ld = P->ld;
     const double lsub = P->ax[0].l;
     if (P->ndim == 1) {
-        CK(launch_tridiag_lines(V, ldv, W, ldw, p, nx, 1, lsub, P->th_m, P->th_c, inv_t, s));
+        LAUNCH(EXPM_STAGE_TRIDIAG, launch_tridiag_lines(V, ldv, W, ldw, p, nx, 1, lsub, P->th_m, P->th_c, inv_t, s));
         return EXPM_OK;
     }
     if (P->ndim == 2) {
         GemmArgs g1{V, P->Qf[1], P->T1, nx, ny, ny, 1, nx, ldv, 0, ny, 1, ld, 0, ny, p, 1};
-        CK(launch_gemm(g1, s));
-        CK(launch_tridiag_lines(P->T1, ld, P->T1, ld, p, nx, ny, lsub, P->th_m, P->th_c, inv_t, s));
+        LAUNCH(EXPM_STAGE_GEMM, launch_gemm(g1, s));
+        LAUNCH(EXPM_STAGE_TRIDIAG, launch_tridiag_lines(P->T1, ld, P->T1, ld, p, nx, ny, lsub, P->th_m, P->th_c, inv_t, s));
         GemmArgs g2{P->T1, P->Qi[1], W, nx, ny, ny, ny, 1, ld, 0, 1, nx, ldw, 0, ny, p, 1};
-        CK(launch_gemm(g2, s));
+        LAUNCH(EXPM_STAGE_GEMM, launch_gemm(g2, s));
         return EXPM_OK;
     }
     const int64_t nxy = (int64_t)nx * ny;
     GemmArgs g1{V, P->Qf[2], P->T2, (int)nxy, nz, nz, 1, nxy, ldv, 0, 1, nxy, ld, 0, nz, p, 1};
-    CK(launch_gemm(g1, s));
+    LAUNCH(EXPM_STAGE_GEMM, launch_gemm(g1, s));
     GemmArgs g2{P->T2, P->Qf[1], P->T1, nx, ny, ny, 1, nx, ld, nxy, (int64_t)ny * nz, 1, ld, ny, ny, p, nz};
-    CK(launch_gemm(g2, s));
-    CK(launch_tridiag_lines(P->T1, ld, P->T1, ld, p, nx, (int64_t)ny * nz, lsub, P->th_m, P->th_c,
-                            inv_t, s));
+    LAUNCH(EXPM_STAGE_GEMM, launch_gemm(g2, s));
+    LAUNCH(EXPM_STAGE_TRIDIAG, launch_tridiag_lines(P->T1, ld, P->T1, ld, p, nx, (int64_t)ny * nz, lsub,
+                                                    P->th_m, P->th_c, inv_t, s));
     GemmArgs g3{P->T1, P->Qi[1], P->T2, nx, ny, ny, (int64_t)ny * nz, 1, ld, ny, 1, nx, ld, nxy, ny, p, nz};
-    CK(launch_gemm(g3, s));
+    LAUNCH(EXPM_STAGE_GEMM, launch_gemm(g3, s));
     GemmArgs g4{P->T2, P->Qi[2], W, (int)nxy, nz, nz, 1, nxy, ld, 0, 1, nxy, ldw, 0, nz, p, 1};
-    CK(launch_gemm(g4, s));
+    LAUNCH(EXPM_STAGE_GEMM, launch_gemm(g4, s));
     return EXPM_OK;
 }
 
-// Block step j (0-based): V_j -> W = (tA)^{-1} V_j -> V_{j+1}, H column block j.
-expm_status block_step(expm_plan* P, double t, int j, int p) {
+// Block step j (0-based): V_j -> W = Op V_j -> V_{j+1}, H column block j.
+// Op = (tA)^{-1} (Algorithm 2) or tA (Algorithm 1).
+expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     cudaStream_t s = P->stream;
     const int64_t n = P->n, ld = P->ld;
     double* h = sm(P, kOffH);
-    expm_status st = prec_apply_internal(P, t, P->V + (int64_t)j * p * ld, ld, p, P->W, ld);
-    if (st != EXPM_OK) return st;
+    const double* Vj = P->V + (int64_t)j * p * ld;
+    if (alg == 2) {
+        expm_status st = prec_apply_internal(P, t, Vj, ld, p, P->W, ld);
+        if (st != EXPM_OK) return st;
+    } else {
+        LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(Vj, ld, P->W, ld, p, P->ndim, P->ax[0].N, P->ax[1].N,
+                                                   P->ax[2].N, P->ax, t, s));
+    }
     const int cols = (j + 1) * p;
-    CK(launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, P->nblk, s));
-    CK(launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
-    CK(launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s));
-    CK(launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
-    CK(launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 1, s));
+    LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, P->nblk, s));
+    LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
+    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s));
+    LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
+    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 1, s));
     return qr_block(P, p, P->V + (int64_t)(j + 1) * p * ld, ld, true, (j + 1) * p, j * p, nullptr, true);
 }
 
@@ -126,20 +168,35 @@ expm_status validate_block_args(expm_plan* P, double t, const void* B, int64_t l
     return EXPM_OK;
 }
 
+// Gershgorin bound of ||tA||_inf for the convection-diffusion operator.
+double norm_bound(const expm_plan* P, double t) {
+    double s = 0.0;
+    for (int d = 0; d < P->ndim; ++d) s += std::fabs(P->ax[d].l) + std::fabs(P->ax[d].c) + std::fabs(P->ax[d].u);
+    return t * s;
+}
+
+int choose_algorithm(const expm_plan* P, double t) {
+    if (P->opts.algorithm == EXPM_ALG_SBFOM || P->opts.algorithm == EXPM_ALG_PSBFOM) return P->opts.algorithm;
+    double tmax = 0.0;
+    for (int i = 0; i < P->npoles; ++i) tmax = std::max(tmax, std::hypot(P->tau_re[i], P->tau_im[i]));
+    return norm_bound(P, t) >= EXPM_AUTO_RATIO * tmax ? EXPM_ALG_PSBFOM : EXPM_ALG_SBFOM;
+}
+
 expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int p, double* dZ,
                       int64_t ldz, expm_info* info) {
     cudaStream_t s = P->stream;
+    const int alg = choose_algorithm(P, t);
     const int m = P->opts.m;
     const int64_t n = P->n, ld = P->ld;
     const int mp = m * p;
     CK(cudaMemsetAsync(P->stat, 0, sizeof(double) * kStatDoubles, s));
     CK(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)P->ldH * m * P->p_max, s));
-    CK(launch_zero(P->Zacc, ld, n, p, s));
+    LAUNCH(EXPM_STAGE_OTHER, launch_zero(P->Zacc, ld, n, p, s));
     // Steps 1-2: R_i^0 = B = V_1 R for every pole
-    CK(launch_copy(dB, ldb, P->W, ld, n, p, s));
+    LAUNCH(EXPM_STAGE_OTHER, launch_copy(dB, ldb, P->W, ld, n, p, s));
     expm_status st = qr_block(P, p, P->V, ld, false, 0, 0, P->stat + 16, false);
     if (st != EXPM_OK) return st;
-    CK(launch_init_S(sm(P, kOffRt), p, P->npoles, P->S, s));
+    LAUNCH(EXPM_STAGE_OTHER, launch_init_S(sm(P, kOffRt), p, P->npoles, P->S, s));
     double* tau_re = sm(P, kOffTau);
     int cycles = 0;
     bool converged = false;
@@ -148,16 +205,18 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
     while (true) {
         ++cycles;
         for (int j = 0; j < m; ++j) {
-            st = block_step(P, t, j, p);
+            st = block_step(P, t, j, p, alg);
             if (st != EXPM_OK) return st;
         }
-        CK(launch_poles(P->H, P->ldH, mp, p, P->npoles, tau_re, tau_re + EXPM_MAX_POLES,
-                        tau_re + 2 * EXPM_MAX_POLES, tau_re + 3 * EXPM_MAX_POLES, P->S, P->poles,
-                        P->Wc_slots, P->stat, flags_of(P->stat), s));
-        CK(launch_combine(P->Wc_slots, P->npoles, mp + p, p, sm(P, kOffWc), s));
-        CK(launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk));
+        LAUNCH(EXPM_STAGE_POLES, launch_poles(P->H, P->ldH, mp, p, P->npoles, tau_re, tau_re + EXPM_MAX_POLES,
+                                              tau_re + 2 * EXPM_MAX_POLES, tau_re + 3 * EXPM_MAX_POLES,
+                                              P->S, P->poles, P->Wc_slots, P->stat, flags_of(P->stat),
+                                              alg, s));
+        LAUNCH(EXPM_STAGE_POLES, launch_combine(P->Wc_slots, P->npoles, mp + p, p, sm(P, kOffWc), s));
+        LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk));
         CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        prof_flush(P);
         st = check_flags(P->hpin);
         if (st != EXPM_OK) { result = st; break; }
         normB = std::sqrt(P->hpin[16]);
@@ -169,8 +228,7 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
         if (done) break;
     }
     // Z = omega_0 B + Z_acc
-    CK(launch_axpby(P->omega0, dB, ldb, 1.0, P->Zacc, ld, dZ, ldz, n, p, s));
-    CK(cudaGetLastError());
+    LAUNCH(EXPM_STAGE_OTHER, launch_axpby(P->omega0, dB, ldb, 1.0, P->Zacc, ld, dZ, ldz, n, p, s));
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->cycles = cycles;
@@ -180,6 +238,8 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
         info->npoles = P->npoles;
         for (int i = 0; i < P->npoles; ++i) info->resid[i] = P->hpin[i];
         info->normB = normB;
+        info->algorithm = alg;
+        info->normA_bound = norm_bound(P, t);
     }
     if (result != EXPM_OK) return result;
     if (P->opts.fixed_cycles > 0) return EXPM_OK;
@@ -210,6 +270,7 @@ void free_plan(expm_plan* P) {
     cudaFree(P->Wc_slots);
     cudaFree(P->stat);
     if (P->hpin) cudaFreeHost(P->hpin);
+    for (auto& e : P->ev) cudaEventDestroy(e);
     delete P;
 }
 
@@ -265,6 +326,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     if (opts->m < 1 || (int64_t)opts->m * p_max > kMaxMP) return EXPM_INVALID_ARG;
     if (opts->max_cycles < 1 || !(opts->tol >= 0.0)) return EXPM_INVALID_ARG;
     if (opts->precision != EXPM_PREC_FP64) return EXPM_INVALID_ARG;
+    if (opts->algorithm < EXPM_ALG_AUTO || opts->algorithm > EXPM_ALG_PSBFOM) return EXPM_INVALID_ARG;
     expm_plan* P = new (std::nothrow) expm_plan_s();
     if (!P) return EXPM_NO_MEMORY;
     P->op = *op;
@@ -409,8 +471,9 @@ expm_status expm_op_apply(expm_plan* plan, double t, const double* dV, int64_t l
                           double* dW, int64_t ldw) {
     expm_status st = validate_block_args(plan, t, dV, ldv, p, dW, ldw);
     if (st != EXPM_OK) return st;
-    CK(launch_cd_apply(dV, ldv, dW, ldw, p, plan->ndim, plan->ax[0].N, plan->ax[1].N, plan->ax[2].N,
-                       plan->ax, t, plan->stream));
+    expm_plan* P = plan;
+    LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(dV, ldv, dW, ldw, p, plan->ndim, plan->ax[0].N, plan->ax[1].N,
+                                               plan->ax[2].N, plan->ax, t, plan->stream));
     return EXPM_OK;
 }
 
@@ -432,17 +495,51 @@ expm_status expm_arnoldi(expm_plan* plan, double t, const double* dV1, int64_t l
     const int64_t n = plan->n, ld = plan->ld;
     CK(cudaMemsetAsync(plan->stat, 0, sizeof(double) * kStatDoubles, s));
     CK(cudaMemsetAsync(plan->H, 0, sizeof(double) * (size_t)plan->ldH * m * plan->p_max, s));
-    CK(launch_copy(dV1, ldv1, plan->V, ld, n, p, s));
+    expm_plan* P = plan;
+    LAUNCH(EXPM_STAGE_OTHER, launch_copy(dV1, ldv1, plan->V, ld, n, p, s));
     for (int j = 0; j < m; ++j) {
-        st = block_step(plan, t, j, p);
+        st = block_step(plan, t, j, p, EXPM_ALG_PSBFOM);
         if (st != EXPM_OK) return st;
     }
-    CK(launch_copy(plan->V, ld, dVout, ldvo, n, (m + 1) * p, s));
+    LAUNCH(EXPM_STAGE_OTHER, launch_copy(plan->V, ld, dVout, ldvo, n, (m + 1) * p, s));
     CK(cudaMemcpy2DAsync(dHout, ldh * sizeof(double), plan->H, plan->ldH * sizeof(double),
                          (size_t)(m + 1) * p * sizeof(double), (size_t)m * p, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(plan->hpin, plan->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    prof_flush(plan);
     return check_flags(plan->hpin);
+}
+
+expm_status expm_plan_profile(expm_plan* plan, int enable) {
+    if (!plan) return EXPM_INVALID_ARG;
+    if (plan->stream) CK(cudaStreamSynchronize(plan->stream));
+    prof_flush(plan);
+    if (enable && plan->ev.empty()) {
+        plan->ev.resize(kEventPool);
+        for (auto& e : plan->ev) CK(cudaEventCreate(&e));
+    }
+    if (enable) {
+        plan->launches = 0;
+        for (int k = 0; k < EXPM_NSTAGES; ++k) {
+            plan->stage_launches[k] = 0;
+            plan->stage_ms[k] = 0.0;
+        }
+    }
+    plan->prof = enable != 0;
+    return EXPM_OK;
+}
+
+expm_status expm_plan_get_profile(expm_plan* plan, double* stage_ms, int64_t* stage_launches,
+                                  int nstages, int64_t* total_launches) {
+    if (!plan || nstages < 0) return EXPM_INVALID_ARG;
+    if (plan->stream) CK(cudaStreamSynchronize(plan->stream));
+    prof_flush(plan);
+    for (int k = 0; k < nstages && k < EXPM_NSTAGES; ++k) {
+        if (stage_ms) stage_ms[k] = plan->stage_ms[k];
+        if (stage_launches) stage_launches[k] = plan->stage_launches[k];
+    }
+    if (total_launches) *total_launches = plan->launches;
+    return EXPM_OK;
 }
 
 }  // extern "C"

@@ -72,6 +72,14 @@ struct expm_plan_s {
     double* stat = nullptr;    // device status block: res[16], normsq, flags (ints)
     double* hpin = nullptr;    // pinned host mirror of stat
     double* Zst = nullptr;     // ld x p_max staging for the host entry point
+    // profiling: launch counts always, event timing when enabled
+    bool prof = false;
+    int64_t launches = 0;
+    int64_t stage_launches[EXPM_NSTAGES] = {};
+    double stage_ms[EXPM_NSTAGES] = {};
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> pend_stage;          // stage of pending event pair k (events 2k, 2k+1)
+    int ev_used = 0;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -109,7 +117,7 @@ cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* 
 cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          const double* tau_re, const double* tau_im, const double* om_re,
                          const double* om_im, double* S, double* work, double* Wc_slots,
-                         double* res, int* flags, cudaStream_t s);
+                         double* res, int* flags, int alg, cudaStream_t s);
 cudaError_t launch_combine(const double* Wc_slots, int npoles, int rows, int p, double* Wc,
                            cudaStream_t s);
 cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,

@@ -1,12 +1,14 @@
-// k_poles.cu -- the projected shifted systems of Algorithm 2, one CTA per pole.
+// k_poles.cu -- the projected shifted systems, one CTA per pole.
 //
-// For each pole tau_i (Im > 0) in one launch:
+// For each pole tau_i (Im > 0) in one launch, Algorithm 2:
 //   (I - tau_i H_m) Z_i = E_1 S_i                              eq. (3236)
 //   S_i <- tau_i H_{m+1,m} E_m^T Z_i,  ||R_i||_F = ||S_i||_F     eq. (49) and the residual
 //                                                             formula above it (collinear
 //                                                             with V_{m+1}: restart factor)
 //   Wc_i = 2 Re(omega_i H~_m Z_i)   ((m+1)p x p, real)          eq. (4.5): X_i - X_i^0 =
 //                                                             (tA)^{-1} V_m Z_i = V_{m+1} H~_m Z_i
+// Algorithm 1 (alg = 1): (H_m - tau_i I) Z_i = E_1 S_i (eq. (3.3)), S_i <- -H_{m+1,m} E_m^T Z_i
+// (eq. (35)), Wc_i = 2 Re(omega_i Z_i) (X_i - X_i^0 = V_m Z_i).
 // H_m is band upper Hessenberg with p sub-diagonals, so Gaussian elimination with partial
 // pivoting only looks at rows j..j+p of column j.  The matrix lives in shared memory when
 // (mp)^2 + mp p complex numbers fit, else in a global workspace (L2-resident).
@@ -37,7 +39,7 @@ __global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int
                                                const double* __restrict__ om_im,
                                                double* __restrict__ S, double* __restrict__ work,
                                                double* __restrict__ Wc_slots, double* res,
-                                               int* flags, int use_smem) {
+                                               int* flags, int use_smem, int alg) {
     extern __shared__ double sm[];
     __shared__ cplx f[kMaxP + 1];
     __shared__ int piv_s;
@@ -49,11 +51,13 @@ __global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int
     cplx* M = use_smem ? reinterpret_cast<cplx*>(sm) : reinterpret_cast<cplx*>(work) + (size_t)i * per;
     cplx* X = M + (size_t)mp * mp;
     cplx* Si = reinterpret_cast<cplx*>(S) + (size_t)i * p * p;
-    // M = I - tau H_m (row-major), X = E_1 S_i
+    // Algorithm 2: M = I - tau H_m (eq. (3236)); Algorithm 1: M = H_m - tau I (eq. (3.3));
+    // row-major.  X = E_1 S_i.
     for (int e = tid; e < mp * mp; e += nt) {
         const int r = e / mp, c = e % mp;
         const double h = H[(int64_t)c * ldH + r];
-        M[e] = cplx{(r == c ? 1.0 : 0.0) - tau.re * h, -tau.im * h};
+        const double d = (r == c ? 1.0 : 0.0);
+        M[e] = (alg == 2) ? cplx{d - tau.re * h, -tau.im * h} : cplx{h - d * tau.re, -d * tau.im};
     }
     for (int e = tid; e < mp * p; e += nt) {
         const int r = e / p, c = e % p;
@@ -126,7 +130,8 @@ __global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int
             s.re += h * x.re;
             s.im += h * x.im;
         }
-        const cplx snew = cmul(tau, s);
+        // Algorithm 2: tau H_{m+1,m} E_m^T Z_i (eq. (49)); Algorithm 1: -H_{m+1,m} E_m^T Z_i (eq. (35))
+        const cplx snew = (alg == 2) ? cmul(tau, s) : cplx{-s.re, -s.im};
         Si[e] = snew;
         ss += cabs2(snew);
     }
@@ -140,17 +145,22 @@ __global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int
         res[i] = sqrt(red[0]);
         if (!isfinite(red[0])) atomicOr(&flags[0], 4);
     }
-    // Wc_i = 2 Re(omega_i H~_m Z_i); H~ row r has non-zeros in columns >= r - p
+    // Algorithm 2: Wc_i = 2 Re(omega_i H~_m Z_i) (H~ row r has non-zeros in columns >= r - p);
+    // Algorithm 1: Wc_i = 2 Re(omega_i Z_i) on the first mp rows, 0 on the last p.
     const int rows = mp + p;
     double* Wi = Wc_slots + (size_t)i * rows * p;
     for (int e = tid; e < rows * p; e += nt) {
         const int r = e / p, c = e % p;
         cplx s{0.0, 0.0};
-        for (int k = max(0, r - p); k < mp; ++k) {
-            const double h = H[(int64_t)k * ldH + r];
-            const cplx x = X[(size_t)k * p + c];
-            s.re += h * x.re;
-            s.im += h * x.im;
+        if (alg == 2) {
+            for (int k = max(0, r - p); k < mp; ++k) {
+                const double h = H[(int64_t)k * ldH + r];
+                const cplx x = X[(size_t)k * p + c];
+                s.re += h * x.re;
+                s.im += h * x.im;
+            }
+        } else if (r < mp) {
+            s = X[(size_t)r * p + c];
         }
         Wi[e] = 2.0 * (om.re * s.re - om.im * s.im);
     }
@@ -166,10 +176,10 @@ size_t poles_smem_bytes(int mp, int p) {
 cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          const double* tau_re, const double* tau_im, const double* om_re,
                          const double* om_im, double* S, double* work, double* Wc_slots,
-                         double* res, int* flags, cudaStream_t s) {
+                         double* res, int* flags, int alg, cudaStream_t s) {
     const size_t shm = poles_smem_bytes(mp, p);
     k_poles<<<npoles, 256, shm, s>>>(H, ldH, mp, p, tau_re, tau_im, om_re, om_im, S, work,
-                                     Wc_slots, res, flags, shm > 0 ? 1 : 0);
+                                     Wc_slots, res, flags, shm > 0 ? 1 : 0, alg);
     return cudaGetLastError();
 }
 

@@ -101,3 +101,43 @@ def test_edge_cases(tab):
         plan.expm_block(-1.0, to_dev(B))
     with pytest.raises(ValueError):
         plan.expm_block(t, to_dev(np.ones((n + 1, 2))))
+
+
+@pytest.mark.parametrize("sides,diff,vel,t,p,m", [((300,), 1.0, (0.0,), 1e-3, 3, 5),
+                                                  ((37, 29), 0.1, (1.0, 1.0), 1e-2, 4, 4),
+                                                  ((11, 9, 7), 1.0, (3.0, -2.0, 1.0), 0.01, 2, 5)])
+def test_algorithm1_parity_with_oracle(tab, sides, diff, vel, t, p, m):
+    """Algorithm 1 (SBFOM, Krylov operator tA) against the oracle's literal Algorithm 1."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n = int(np.prod(sides))
+    B = inputs.rhs(n, p, 41)
+    for cycles in (1, 4):
+        plan = Plan(sides, diff, vel, p_max=p, m=m, fixed_cycles=cycles, algorithm=1)
+        Zg, info = plan.expm_block(t, to_dev(B))
+        Zo, io = ps.sbfom(ps.matvec(ops.cd_matrix(sides, diff, vel, t)), B, tab, m=m, fixed_cycles=cycles)
+        assert info.algorithm == 1 and info.cycles == cycles
+        floor = cancellation_floor(tab, io["X"], Zo)
+        assert rel(to_np(Zg), Zo) <= max(1e-10, 20 * floor)
+        rg = np.array([info.resid[i] for i in range(7)])
+        assert np.allclose(rg, io["residuals"][-1], rtol=1e-6, atol=1e-12 * np.linalg.norm(B))
+
+
+def test_auto_selection_follows_norm_ratio(tab):
+    """AUTO runs Algorithm 2 only when the Gershgorin bound of ||tA|| is >= 50 max|tau|
+    (eq. (43)); both choices converge to the closed form here."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    sides, diff, vel, p = (48, 40), 0.1, (1.0, 1.0), 2
+    n = 48 * 40
+    B = inputs.rhs(n, p, 5)
+    plan = Plan(sides, diff, vel, p_max=p, m=8, tol=1e-11, max_cycles=400)
+    taumax = np.abs(tab["tau"]).max()
+    for t in (1e-3, 3e-2, 1.0):
+        Zg, info = plan.expm_block(t, to_dev(B))
+        h2 = [1.0 / (s + 1) ** 2 for s in sides]
+        bound = t * sum(4 * diff / h for h in h2)
+        assert abs(info.normA_bound - bound) <= 1e-12 * bound
+        assert info.algorithm == (2 if bound >= 50 * taumax else 1)
+        ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+        assert info.converged == 1 and rel(to_np(Zg), ref) < 1e-9, (t, rel(to_np(Zg), ref))
