@@ -20,6 +20,7 @@ EXPM_NO_MEMORY = 6
 EXPM_INTERNAL = 7
 EXPM_OP_CONV_DIFF = 0
 EXPM_PREC_FP64 = 0
+EXPM_PREC_MIXED = 1
 EXPM_ALG_AUTO = 0
 EXPM_ALG_SBFOM = 1
 EXPM_ALG_PSBFOM = 2

@@ -95,9 +95,58 @@ expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, 
     return EXPM_OK;
 }
 
+// One FP32 application of (tA)^{-1} to R (FP64 in), written (acc = 0) or added (acc = 1)
+// to X (FP64).  Same transforms and layouts as the FP64 path.
+expm_status inv32_apply(expm_plan* P, double t, const double* R, int64_t ldr, int p, double* X,
+                        int64_t ldx, int acc) {
+    cudaStream_t s = P->stream;
+    const int nx = P->ax[0].N, ny = P->ax[1].N, nz = P->ax[2].N;
+    const int64_t ld = P->ld;
+    const float lsub = (float)P->ax[0].l, inv_t = (float)(1.0 / t);
+    if (P->ndim == 2) {
+        GemmArgsMixed g1{R, P->Qf32[1], P->T1f, nx, ny, ny, 1, nx, ldr, 0, ny, 1, ld, 0, ny, p, 1, 1, 0, 0};
+        LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g1, s));
+        LAUNCH(EXPM_STAGE_TRIDIAG, launch_tridiag_lines32(P->T1f, ld, p, nx, ny, lsub, P->th_m32, P->th_c32, inv_t, s));
+        GemmArgsMixed g2{P->T1f, P->Qi32[1], X, nx, ny, ny, ny, 1, ld, 0, 1, nx, ldx, 0, ny, p, 1, 0, 1, acc};
+        LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g2, s));
+        return EXPM_OK;
+    }
+    const int64_t nxy = (int64_t)nx * ny;
+    GemmArgsMixed g1{R, P->Qf32[2], P->T2f, (int)nxy, nz, nz, 1, nxy, ldr, 0, 1, nxy, ld, 0, nz, p, 1, 1, 0, 0};
+    LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g1, s));
+    GemmArgsMixed g2{P->T2f, P->Qf32[1], P->T1f, nx, ny, ny, 1, nx, ld, nxy, (int64_t)ny * nz, 1, ld, ny, ny, p, nz, 0, 0, 0};
+    LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g2, s));
+    LAUNCH(EXPM_STAGE_TRIDIAG, launch_tridiag_lines32(P->T1f, ld, p, nx, (int64_t)ny * nz, lsub, P->th_m32,
+                                                      P->th_c32, inv_t, s));
+    GemmArgsMixed g3{P->T1f, P->Qi32[1], P->T2f, nx, ny, ny, (int64_t)ny * nz, 1, ld, ny, 1, nx, ld, nxy, ny, p, nz, 0, 0, 0};
+    LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g3, s));
+    GemmArgsMixed g4{P->T2f, P->Qi32[2], X, (int)nxy, nz, nz, 1, nxy, ld, 0, 1, nxy, ldx, 0, nz, p, 1, 0, 1, acc};
+    LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g4, s));
+    return EXPM_OK;
+}
+
+// Mixed precision: W = (tA)^{-1} V to FP64 accuracy by iterative refinement of the FP32
+// inverse: x_0 = inv32(V), x_{k+1} = x_k + inv32(V - tA x_k) with the residual in FP64
+// (Theorem 4.3: the inverse's accuracy is what the shifted solutions inherit).  Each step
+// multiplies the backward error by about eps_32 * rho^-N (diagonal similarity).
+expm_status prec_apply_mixed(expm_plan* P, double t, const double* V, int64_t ldv, int p,
+                             double* W, int64_t ldw) {
+    cudaStream_t s = P->stream;
+    expm_status st = inv32_apply(P, t, V, ldv, p, W, ldw, 0);
+    if (st != EXPM_OK) return st;
+    for (int k = 0; k < P->refine; ++k) {
+        LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(W, ldw, P->R64, P->ld, p, P->ndim, P->ax[0].N, P->ax[1].N,
+                                                   P->ax[2].N, P->ax, -t, s, V, ldv, 1.0));
+        st = inv32_apply(P, t, P->R64, P->ld, p, W, ldw, 1);
+        if (st != EXPM_OK) return st;
+    }
+    return EXPM_OK;
+}
+
 expm_status prec_apply_internal(expm_plan* P, double t, const double* V, int64_t ldv, int p,
                                 double* W, int64_t ldw) {
     cudaStream_t s = P->stream;
+    if (P->opts.precision == EXPM_PREC_MIXED && P->ndim > 1) return prec_apply_mixed(P, t, V, ldv, p, W, ldw);
     const double inv_t = 1.0 / t;
     const int nx = P->ax[0].N, ny = P->ax[1].N, nz = P->ax[2].N;
     const int64_t ld = P->ld;
@@ -143,9 +192,10 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
                                                    P->ax[2].N, P->ax, t, s));
     }
     const int cols = (j + 1) * p;
-    LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, P->nblk, s));
+    const int f32 = P->opts.precision == EXPM_PREC_MIXED ? 1 : 0;
+    LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, P->nblk, s, f32));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
-    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s));
+    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s, f32));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
     LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 1, s));
     return qr_block(P, p, P->V + (int64_t)(j + 1) * p * ld, ld, true, (j + 1) * p, j * p, nullptr, true);
@@ -255,6 +305,15 @@ void free_plan(expm_plan* P) {
     }
     cudaFree(P->th_m);
     cudaFree(P->th_c);
+    for (int d = 0; d < 3; ++d) {
+        cudaFree(P->Qf32[d]);
+        cudaFree(P->Qi32[d]);
+    }
+    cudaFree(P->th_m32);
+    cudaFree(P->th_c32);
+    cudaFree(P->T1f);
+    cudaFree(P->T2f);
+    cudaFree(P->R64);
     cudaFree(P->V);
     cudaFree(P->W);
     cudaFree(P->T1);
@@ -325,7 +384,14 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     if (p_max < 1 || p_max > kMaxP) return EXPM_INVALID_ARG;
     if (opts->m < 1 || (int64_t)opts->m * p_max > kMaxMP) return EXPM_INVALID_ARG;
     if (opts->max_cycles < 1 || !(opts->tol >= 0.0)) return EXPM_INVALID_ARG;
-    if (opts->precision != EXPM_PREC_FP64) return EXPM_INVALID_ARG;
+    if (opts->precision != EXPM_PREC_FP64 && opts->precision != EXPM_PREC_MIXED) return EXPM_INVALID_ARG;
+    // shared memory of the fused update + FP32 projection at the largest block step
+    {
+        const size_t cols = (size_t)opts->m * p_max, cs = cols | 1;
+        size_t shm = 8 * (cols * p_max + 16 * cs + 16 * (size_t)p_max);
+        if (opts->precision == EXPM_PREC_MIXED) shm += 4 * (16 * cs + 16 * (size_t)p_max);
+        if (shm > 227 * 1024) return EXPM_INVALID_ARG;
+    }
     if (opts->algorithm < EXPM_ALG_AUTO || opts->algorithm > EXPM_ALG_PSBFOM) return EXPM_INVALID_ARG;
     expm_plan* P = new (std::nothrow) expm_plan_s();
     if (!P) return EXPM_NO_MEMORY;
@@ -406,6 +472,16 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     }
     P->nmodes = nmodes;
     ok = ok && dalloc(&P->th_m, (size_t)P->ax[0].N * nmodes) && dalloc(&P->th_c, (size_t)P->ax[0].N * nmodes);
+    const bool mixed = opts->precision == EXPM_PREC_MIXED;
+    if (mixed) {
+        for (int d = 1; d < P->ndim; ++d) {
+            const int N = P->ax[d].N;
+            ok = ok && dalloc(&P->Qf32[d], (size_t)N * N) && dalloc(&P->Qi32[d], (size_t)N * N);
+        }
+        ok = ok && dalloc(&P->th_m32, (size_t)P->ax[0].N * nmodes) && dalloc(&P->th_c32, (size_t)P->ax[0].N * nmodes);
+        ok = ok && dalloc(&P->T1f, (size_t)ld * p_max) && dalloc(&P->T2f, (size_t)ld * p_max);
+        ok = ok && dalloc(&P->R64, (size_t)ld * p_max);
+    }
     if (!ok) {
         cudaGetLastError();
         free_plan(P);
@@ -420,6 +496,17 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         cuda_ok = launch_thomas_setup(P->th_m, P->th_c, P->ax[0].N, nmodes, P->ax[0].l, P->ax[0].c,
                                       P->ax[0].u, P->ndim > 1 ? P->lam[1] : nullptr, P->ax[1].N,
                                       P->ndim > 2 ? P->lam[2] : nullptr, P->ax[2].N, s) == cudaSuccess;
+    if (cuda_ok && mixed) {
+        for (int d = 1; d < P->ndim && cuda_ok; ++d) {
+            const int64_t NN = (int64_t)P->ax[d].N * P->ax[d].N;
+            cuda_ok = launch_d2f(P->Qf[d], P->Qf32[d], NN, s) == cudaSuccess &&
+                      launch_d2f(P->Qi[d], P->Qi32[d], NN, s) == cudaSuccess;
+        }
+        const int64_t nt = (int64_t)P->ax[0].N * nmodes;
+        if (cuda_ok)
+            cuda_ok = launch_d2f(P->th_m, P->th_m32, nt, s) == cudaSuccess &&
+                      launch_d2f(P->th_c, P->th_c32, nt, s) == cudaSuccess;
+    }
     if (cuda_ok) {
         double taus[4 * EXPM_MAX_POLES] = {0};
         for (int i = 0; i < P->npoles; ++i) {

@@ -32,6 +32,20 @@ struct GemmArgs {
     int nb1, nb2;
 };
 
+// Mixed-precision variant: A and C may be FP64 or FP32 (a_f64 / c_f64), B is FP32,
+// arithmetic FP32; accumulate != 0 adds into C.
+struct GemmArgsMixed {
+    const void* A;
+    const float* B;
+    void* C;
+    int M, N, K;
+    int64_t a_rs, a_cs, a_b1, a_b2;
+    int64_t c_rs, c_cs, c_b1, c_b2;
+    int ldb;
+    int nb1, nb2;
+    int a_f64, c_f64, accumulate;
+};
+
 }  // namespace expm
 
 struct expm_plan_s {
@@ -54,6 +68,15 @@ struct expm_plan_s {
     double* th_m = nullptr;                          // Thomas 1/pivot, [x * nmodes + mode]
     double* th_c = nullptr;                          // Thomas c',      [x * nmodes + mode]
     int64_t nmodes = 1;
+    // mixed precision: FP32 copies of the tables and FP32 transform buffers
+    float* Qf32[3] = {nullptr, nullptr, nullptr};
+    float* Qi32[3] = {nullptr, nullptr, nullptr};
+    float* th_m32 = nullptr;
+    float* th_c32 = nullptr;
+    float* T1f = nullptr;      // ld x p_max
+    float* T2f = nullptr;      // ld x p_max
+    double* R64 = nullptr;     // ld x p_max   residual of the refined inverse
+    int refine = 2;            // FP64 refinement steps of the FP32 inverse
     // workspace (device)
     double* V = nullptr;       // ld x (m+1) p_max       Krylov basis
     double* W = nullptr;       // ld x p_max
@@ -95,18 +118,24 @@ cudaError_t launch_axis_setup(double* Qf, double* Qi, double* lam, int N, double
                               double u, cudaStream_t s);
 cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw, int p,
                             int ndim, int nx, int ny, int nz, const Axis* ax, double t,
-                            cudaStream_t s);
+                            cudaStream_t s, const double* Y = nullptr, int64_t ldy = 0,
+                            double beta = 0.0);
+cudaError_t launch_gemm32(const GemmArgsMixed& g, cudaStream_t s);
+cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t nmodes, float l_sub,
+                                   const float* th_m, const float* th_c, float inv_t,
+                                   cudaStream_t s);
+cudaError_t launch_d2f(const double* in, float* out, int64_t n, cudaStream_t s);
 
 // block Gram-Schmidt / Cholesky-QR pieces
 cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const double* W,
                                 int64_t ldw, int p, int64_t n, double* part, int nblk,
-                                cudaStream_t s);
+                                cudaStream_t s, int f32 = 0);
 cudaError_t launch_reduce_h(const double* part, int nblk, int cols, int p, double* h,
                             double* H, int ldH, int row0, int col0, int accumulate,
                             cudaStream_t s);
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
                                int p, int64_t n, const double* h, double* part, int nblk,
-                               int gram, cudaStream_t s);
+                               int gram, cudaStream_t s, int f32 = 0);
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,
                         double* Rinv, double* Rtot, int first, double* H, int ldH, int hrow,
                         int hcol, double* normsq_out, int* flags, cudaStream_t s);

@@ -23,24 +23,28 @@ constexpr int NT = 256;     // threads per CTA for the row passes
 
 __device__ inline int64_t rows_begin(int64_t rpb) { return (int64_t)blockIdx.x * rpb; }
 
-// Load a TR x cols tile of column-major X (rows r0.., ld) into S[rr * cs + a], zero-filled.
+// Load a TR x cols tile of column-major X (rows r0.., ld) into S[rr * cs + a], zero-filled,
+// converted to the tile's element type.
+template <typename T>
 __device__ inline void load_tile(const double* __restrict__ X, int64_t ld, int cols, int64_t r0,
-                                 int tr, double* S, int cs) {
+                                 int tr, T* S, int cs) {
     for (int e = threadIdx.x; e < TR * cols; e += blockDim.x) {
         const int rr = e % TR, a = e / TR;
-        S[rr * cs + a] = (rr < tr) ? X[(int64_t)a * ld + r0 + rr] : 0.0;
+        S[rr * cs + a] = (rr < tr) ? (T)X[(int64_t)a * ld + r0 + rr] : (T)0;
     }
 }
 
 // partial[blk][a][c] = sum_{rows of blk} V[r, a] W[r, c]      (a < cols, c < p)
-template <int OPT>
+// T = float: FP32 products over each 16-row tile (the mixed path's projections; only the
+// FP64 updates must be exact for the Arnoldi relation), FP64 accumulation across tiles.
+template <int OPT, typename T>
 __global__ void __launch_bounds__(NT) k_proj(const double* __restrict__ V, int64_t ldv, int cols,
                                              const double* __restrict__ W, int64_t ldw, int p,
                                              int64_t n, int64_t rpb, double* __restrict__ part) {
     extern __shared__ double sm[];
     const int cs = cols | 1;
-    double* Vs = sm;
-    double* Ws = sm + TR * cs;
+    T* Vs = reinterpret_cast<T*>(sm);
+    T* Ws = Vs + TR * cs;
     const int nout = cols * p;
     double acc[OPT];
 #pragma unroll
@@ -56,10 +60,10 @@ __global__ void __launch_bounds__(NT) k_proj(const double* __restrict__ V, int64
             const int o = threadIdx.x + q * NT;
             if (o < nout) {
                 const int a = o / p, c = o % p;
-                double s = 0.0;
+                T s = 0;
 #pragma unroll
                 for (int rr = 0; rr < TR; ++rr) s = fma(Vs[rr * cs + a], Ws[rr * p + c], s);
-                acc[q] += s;
+                acc[q] += (double)s;
             }
         }
         __syncthreads();
@@ -88,8 +92,9 @@ __global__ void k_reduce_h(const double* __restrict__ part, int nblk, int cols, 
     }
 }
 
-// W <- W - V h ; then partial of V^T W (gram = 0) or W^T W (gram = 1).
-template <int OPT>
+// W <- W - V h (FP64: keeps the Arnoldi relation exact); then partial of V^T W (gram = 0)
+// or W^T W (gram = 1).  F32: the projection's products in FP32 on FP32 copies of the tiles.
+template <int OPT, bool F32>
 __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int64_t ldv, int cols,
                                                double* __restrict__ W, int64_t ldw, int p,
                                                int64_t n, int64_t rpb,
@@ -100,6 +105,8 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
     double* hs = sm;                      // cols x p
     double* Vs = hs + cols * p;           // TR x cs
     double* Ws = Vs + TR * cs;            // TR x p
+    float* Vf = reinterpret_cast<float*>(Ws + TR * p);   // F32 copies (TR x cs, TR x p)
+    float* Wf = Vf + TR * cs;
     for (int e = threadIdx.x; e < cols * p; e += blockDim.x) hs[e] = h[e];
     const int nout = gram ? p * p : cols * p;
     double acc[OPT];
@@ -116,8 +123,14 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
             double w = Ws[rr * p + c];
             for (int a = 0; a < cols; ++a) w = fma(-Vs[rr * cs + a], hs[a * p + c], w);
             Ws[rr * p + c] = w;
+            if (F32) Wf[rr * p + c] = (float)w;
             if (rr < tr) W[(int64_t)c * ldw + r0 + rr] = w;
         }
+        if (F32 && !gram)
+            for (int e = threadIdx.x; e < TR * cols; e += blockDim.x) {
+                const int rr = e % TR, a = e / TR;
+                Vf[rr * cs + a] = (float)Vs[rr * cs + a];
+            }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < OPT; ++q) {
@@ -128,6 +141,12 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
                     const int c1 = o / p, c2 = o % p;
 #pragma unroll
                     for (int rr = 0; rr < TR; ++rr) s = fma(Ws[rr * p + c1], Ws[rr * p + c2], s);
+                } else if (F32) {
+                    const int a = o / p, c = o % p;
+                    float sf = 0.f;
+#pragma unroll
+                    for (int rr = 0; rr < TR; ++rr) sf = fmaf(Vf[rr * cs + a], Wf[rr * p + c], sf);
+                    s = (double)sf;
                 } else {
                     const int a = o / p, c = o % p;
 #pragma unroll
@@ -384,11 +403,14 @@ int consistent_blocks(int64_t n, int requested) {
 
 cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const double* W,
                                 int64_t ldw, int p, int64_t n, double* part, int nblk,
-                                cudaStream_t s) {
+                                cudaStream_t s, int f32) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
     const size_t shm = sizeof(double) * (TR * (cols | 1) + TR * p);
-    EXPM_OPT_DISPATCH(cols * p, (k_proj<O><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, part)));
+    if (f32)
+        EXPM_OPT_DISPATCH(cols * p, (k_proj<O, float><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, part)));
+    else
+        EXPM_OPT_DISPATCH(cols * p, (k_proj<O, double><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, part)));
     return cudaGetLastError();
 }
 
@@ -404,12 +426,16 @@ cudaError_t launch_reduce_h(const double* part, int nblk_req, int cols, int p, d
 
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
                                int p, int64_t n, const double* h, double* part, int nblk,
-                               int gram, cudaStream_t s) {
+                               int gram, cudaStream_t s, int f32) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
-    const size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1) + TR * p);
+    size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1) + TR * p);
+    if (f32) shm += sizeof(float) * (TR * (cols | 1) + TR * p);
     const int nout = gram ? p * p : cols * p;
-    EXPM_OPT_DISPATCH(nout, (k_update<O><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
+    if (f32)
+        EXPM_OPT_DISPATCH(nout, (k_update<O, true><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
+    else
+        EXPM_OPT_DISPATCH(nout, (k_update<O, false><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
     return cudaGetLastError();
 }
 
@@ -478,8 +504,12 @@ cudaError_t krylov_set_smem_limits() {
     cudaError_t e = cudaSuccess;
 #define EXPM_SET(K) \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
-    EXPM_SET(k_proj<1>); EXPM_SET(k_proj<4>); EXPM_SET(k_proj<16>); EXPM_SET(k_proj<64>);
-    EXPM_SET(k_update<1>); EXPM_SET(k_update<4>); EXPM_SET(k_update<16>); EXPM_SET(k_update<64>);
+    EXPM_SET((k_proj<1, double>)); EXPM_SET((k_proj<4, double>)); EXPM_SET((k_proj<16, double>));
+    EXPM_SET((k_proj<64, double>)); EXPM_SET((k_proj<1, float>)); EXPM_SET((k_proj<4, float>));
+    EXPM_SET((k_proj<16, float>)); EXPM_SET((k_proj<64, float>));
+    EXPM_SET((k_update<1, false>)); EXPM_SET((k_update<4, false>)); EXPM_SET((k_update<16, false>));
+    EXPM_SET((k_update<64, false>)); EXPM_SET((k_update<1, true>)); EXPM_SET((k_update<4, true>));
+    EXPM_SET((k_update<16, true>)); EXPM_SET((k_update<64, true>));
     EXPM_SET(k_update_z);
 #undef EXPM_SET
     return e;

@@ -140,10 +140,12 @@ __global__ void k_axis_setup(double* Qf, double* Qi, double* lam, int N, double 
     }
 }
 
-// W = tA V, 3/5/7-point stencil with Dirichlet zeros outside the grid.
+// W = t (A V) + beta Y, 3/5/7-point stencil with Dirichlet zeros outside the grid.
+// (beta = 0, Y = null: the operator apply; t -> -t, beta = 1: the residual Y - tA V.)
 __global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __restrict__ W,
                            int64_t ldw, int ndim, int nx, int ny, int nz, Axis ax0, Axis ax1,
-                           Axis ax2, double t) {
+                           Axis ax2, double t, const double* __restrict__ Y, int64_t ldy,
+                           double beta) {
     const int64_t n = (int64_t)nx * ny * nz;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
@@ -165,7 +167,98 @@ __global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __
         if (iz > 0) acc += ax2.l * v[i - s];
         if (iz < nz - 1) acc += ax2.u * v[i + s];
     }
-    W[c * ldw + i] = t * acc;
+    W[c * ldw + i] = t * acc + (Y ? beta * Y[c * ldy + i] : 0.0);
+}
+
+// ---------------------------------------------------------------- mixed precision
+// FP32 arithmetic for the DST-I transforms of the exact inverse; the result is refined
+// in FP64 by the caller (residual with the FP64 stencil, Theorem 4.3 bounds what an
+// inexact inverse costs).  TA / TC: element types of A and C; acc: C += A B.
+template <bool CM, typename TA, typename TC>
+__global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
+    __shared__ float As[BK][BM + 1];
+    __shared__ float Bs[BK][BN];
+    const int b1 = blockIdx.z % g.nb1, b2 = blockIdx.z / g.nb1;
+    const TA* A = reinterpret_cast<const TA*>(g.A) + b1 * g.a_b1 + b2 * g.a_b2;
+    TC* C = reinterpret_cast<TC*>(g.C) + b1 * g.c_b1 + b2 * g.c_b2;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const bool a_mfast = (g.a_rs == 1);
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * 256;
+            int mm, kk;
+            if (a_mfast) { mm = e % BM; kk = e / BM; }
+            else { kk = e % BK; mm = e / BK; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < g.M && gk < g.K) ? (float)A[(int64_t)gm * g.a_rs + (int64_t)gk * g.a_cs] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * 256;
+            const int nn = e % BN, kk = e / BN;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < g.N && gk < g.K) ? g.B[(int64_t)gk * g.ldb + gn] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][(CM ? tx : ty) + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][(CM ? ty : tx) + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + (CM ? tx : ty) + 16 * i, nn = n0 + (CM ? ty : tx) + 16 * j;
+            if (m < g.M && nn < g.N) {
+                TC* dst = C + (int64_t)m * g.c_rs + (int64_t)nn * g.c_cs;
+                *dst = g.accumulate ? (TC)(*dst + (TC)acc[i][j]) : (TC)acc[i][j];
+            }
+        }
+}
+
+__global__ void k_tridiag_lines32(float* y_io, int64_t ld, int p, int L, int64_t nmodes,
+                                  float l_sub, const float* __restrict__ thm,
+                                  const float* __restrict__ thc, float inv_t) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= nmodes * p) return;
+    const int64_t k = gid % nmodes;
+    const int c = (int)(gid / nmodes);
+    float* y = y_io + c * ld + k;
+    float prev = 0.f;
+    for (int x = 0; x < L; ++x) {
+        const int64_t o = (int64_t)x * nmodes;
+        const float v = (y[o] * inv_t - l_sub * prev) * thm[o + k];
+        y[o] = v;
+        prev = v;
+    }
+    float next = prev;
+    for (int x = L - 2; x >= 0; --x) {
+        const int64_t o = (int64_t)x * nmodes;
+        next = y[o] - thc[o + k] * next;
+        y[o] = next;
+    }
+}
+
+__global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
 }
 
 }  // namespace
@@ -205,10 +298,44 @@ cudaError_t launch_axis_setup(double* Qf, double* Qi, double* lam, int N, double
 
 cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw, int p,
                             int ndim, int nx, int ny, int nz, const Axis* ax, double t,
-                            cudaStream_t s) {
+                            cudaStream_t s, const double* Y, int64_t ldy, double beta) {
     const int64_t n = (int64_t)nx * ny * nz;
     dim3 grid((unsigned)((n + 255) / 256), p);
-    k_cd_apply<<<grid, 256, 0, s>>>(V, ldv, W, ldw, ndim, nx, ny, nz, ax[0], ax[1], ax[2], t);
+    k_cd_apply<<<grid, 256, 0, s>>>(V, ldv, W, ldw, ndim, nx, ny, nz, ax[0], ax[1], ax[2], t, Y,
+                                    ldy, beta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm32(const GemmArgsMixed& g, cudaStream_t s) {
+    dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, g.nb1 * g.nb2);
+    const bool cm = (g.c_rs == 1);
+    if (g.a_f64 && !g.c_f64) {
+        if (cm) k_gemm32<true, double, float><<<grid, 256, 0, s>>>(g);
+        else k_gemm32<false, double, float><<<grid, 256, 0, s>>>(g);
+    } else if (!g.a_f64 && !g.c_f64) {
+        if (cm) k_gemm32<true, float, float><<<grid, 256, 0, s>>>(g);
+        else k_gemm32<false, float, float><<<grid, 256, 0, s>>>(g);
+    } else if (!g.a_f64 && g.c_f64) {
+        if (cm) k_gemm32<true, float, double><<<grid, 256, 0, s>>>(g);
+        else k_gemm32<false, float, double><<<grid, 256, 0, s>>>(g);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t nmodes, float l_sub,
+                                   const float* th_m, const float* th_c, float inv_t,
+                                   cudaStream_t s) {
+    const int64_t tot = nmodes * p;
+    const int thr = 128;
+    k_tridiag_lines32<<<(unsigned)((tot + thr - 1) / thr), thr, 0, s>>>(y, ld, p, L, nmodes, l_sub,
+                                                                       th_m, th_c, inv_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_d2f(const double* in, float* out, int64_t n, cudaStream_t s) {
+    k_d2f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
 }
 

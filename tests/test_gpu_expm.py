@@ -34,7 +34,7 @@ def test_fixed_cycles_parity_with_oracle(tab, sides, diff, vel, t, p, m):
     n = int(np.prod(sides))
     B = inputs.rhs(n, p, 31)
     for cycles in (1, 3):
-        plan = Plan(sides, diff, vel, p_max=p, m=m, fixed_cycles=cycles)
+        plan = Plan(sides, diff, vel, p_max=p, m=m, fixed_cycles=cycles, algorithm=2)
         Zg, info = plan.expm_block(t, to_dev(B))
         Zg = to_np(Zg)
         Zo, io = ps.psbfom(ps.lu_inverse(ops.cd_matrix(sides, diff, vel, t)), B, tab, m=m,
