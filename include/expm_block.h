@@ -194,6 +194,25 @@ expm_status expm_op_apply(expm_plan* plan, double t, const double* dV, int64_t l
 expm_status expm_prec_apply(expm_plan* plan, double t, const double* dV, int64_t ldv, int p,
                             double* dW, int64_t ldw);
 
+/* expm_prec_apply_noalloc -- W = (tA)^{-1} V like expm_prec_apply, for callers that cannot
+ * call cudaMalloc (for example a host application whose own pool allocator owns all device
+ * memory and forbids raw allocations by libraries, or a latency-critical loop that must not
+ * enter the CUDA allocator).  The paper has no counterpart: this is a deployment variant.
+ * It needs no plan and allocates nothing: the transform tables, the Thomas factors and the
+ * transform temporary live in one fixed 8 MiB device array inside the library (held by every
+ * GPU that loads the library until the process exits).  Each call rebuilds what it reads.
+ *   op        : host descriptor, EXPM_OP_CONV_DIFF with ndim 1 or 2
+ *   dV, dW    : device, n x p (ld >= n), must not alias; 1 <= p <= 32
+ *   stream    : cudaStream_t (NULL = legacy default stream); the call is stream-ordered
+ * Size limit: 1-D needs 2n doubles, 2-D needs 2 N_y^2 + N_y + 2n + n p doubles (each
+ * region rounded up to 32) within 2^20 doubles; larger problems return EXPM_INVALID_ARG.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU (different streams or host threads on
+ * one device) race: order them.  Errors: EXPM_INVALID_ARG, EXPM_CUDA_ERROR. */
+expm_status expm_prec_apply_noalloc(const expm_op_desc* op, double t, const double* dV,
+                                    int64_t ldv, int p, double* dW, int64_t ldw, void* stream);
+
 /* expm_arnoldi -- one block Arnoldi pass (eq. (4.5)) from an orthonormal V_1:
  *   dV1 : device n x p (ldv1), orthonormal start block (copied into the basis)
  *   dVout : device n x (m+1)p out (ldvo), the basis V_{m+1}

@@ -29,7 +29,8 @@ EXPM_MAX_POLES = 16
 # Every exported function the header declares (checked by the CPU test suite).
 EXPORTS = ("expm_cf_coeffs", "expm_plan_create", "expm_plan_destroy", "expm_block",
            "expm_block_host", "expm_op_apply", "expm_prec_apply", "expm_arnoldi",
-           "expm_plan_profile", "expm_plan_get_profile", "expm_status_str")
+           "expm_plan_profile", "expm_plan_get_profile", "expm_status_str",
+           "expm_prec_apply_noalloc")
 STAGES = ("gemm", "tridiag", "cgs", "reduce", "qr", "poles", "update", "other", "stencil")
 
 
@@ -90,6 +91,8 @@ def load(build_if_missing: bool = False):
         f.argtypes = [p, d, p, i64, i32, p, i64]
     lib.expm_arnoldi.restype = C.c_int
     lib.expm_arnoldi.argtypes = [p, d, p, i64, i32, p, i64, p, i64]
+    lib.expm_prec_apply_noalloc.restype = C.c_int
+    lib.expm_prec_apply_noalloc.argtypes = [C.POINTER(expm_op_desc), d, p, i64, i32, p, i64, p]
     lib.expm_plan_profile.restype = C.c_int
     lib.expm_plan_profile.argtypes = [p, C.c_int]
     lib.expm_plan_get_profile.restype = C.c_int
@@ -180,3 +183,9 @@ def expm_plan_get_profile(plan):
     tot = C.c_int64()
     check(load().expm_plan_get_profile(plan, ms, nl, k, C.byref(tot)), "expm_plan_get_profile")
     return {STAGES[i]: (ms[i], nl[i]) for i in range(k)}, tot.value
+
+
+def expm_prec_apply_noalloc(op, t, dV, ldv, p, dW, ldw, stream=0):
+    """Allocation-free W = (tA)^{-1} V (no plan); see include/expm_block.h."""
+    check(load().expm_prec_apply_noalloc(C.byref(op), t, C.c_void_p(dV), ldv, p, C.c_void_p(dW), ldw,
+                                         C.c_void_p(stream)), "expm_prec_apply_noalloc")
