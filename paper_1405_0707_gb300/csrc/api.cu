@@ -232,6 +232,68 @@ int choose_algorithm(const expm_plan* P, double t) {
     return norm_bound(P, t) >= EXPM_AUTO_RATIO * tmax ? EXPM_ALG_PSBFOM : EXPM_ALG_SBFOM;
 }
 
+// One restart cycle: m block steps, the projected systems, the update and the restart copy,
+// then the device->host copy of the residual norms and flags (no synchronisation).
+expm_status issue_cycle(expm_plan* P, double t, int p, int alg) {
+    cudaStream_t s = P->stream;
+    const int m = P->opts.m, mp = m * p;
+    const int64_t n = P->n, ld = P->ld;
+    for (int j = 0; j < m; ++j) {
+        expm_status st = block_step(P, t, j, p, alg);
+        if (st != EXPM_OK) return st;
+    }
+    double* tau_re = sm(P, kOffTau);
+    LAUNCH(EXPM_STAGE_POLES, launch_poles(P->H, P->ldH, mp, p, P->npoles, tau_re, tau_re + EXPM_MAX_POLES,
+                                          tau_re + 2 * EXPM_MAX_POLES, tau_re + 3 * EXPM_MAX_POLES,
+                                          P->S, P->poles, P->Wc_slots, P->stat, flags_of(P->stat), alg, s));
+    LAUNCH(EXPM_STAGE_POLES, launch_combine2(P->H, P->ldH, mp, p, P->npoles, P->Wc_slots, sm(P, kOffWc), alg, s));
+    LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk));
+    CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
+    return EXPM_OK;
+}
+
+// Capture (once) and return the graph of one cycle for (alg, p, t); nullptr if capture is
+// not possible, in which case the caller launches directly.
+GraphEntry* graph_for(expm_plan* P, double t, int p, int alg) {
+    for (auto& g : P->graphs)
+        if (g.alg == alg && g.p == p && g.t == t) return &g;
+    if (P->graphs.size() >= 16) return nullptr;
+    cudaStream_t s = P->stream;
+    const int64_t l0 = P->launches;
+    int64_t sl0[EXPM_NSTAGES];
+    for (int k = 0; k < EXPM_NSTAGES; ++k) sl0[k] = P->stage_launches[k];
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    expm_status st = issue_cycle(P, t, p, alg);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    GraphEntry e;
+    e.alg = alg;
+    e.p = p;
+    e.t = t;
+    e.launches = P->launches - l0;
+    for (int k = 0; k < EXPM_NSTAGES; ++k) {
+        e.stage_launches[k] = P->stage_launches[k] - sl0[k];
+        P->stage_launches[k] = sl0[k];
+    }
+    P->launches = l0;
+    if (st != EXPM_OK || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    P->graphs.push_back(e);
+    return &P->graphs.back();
+}
+
 expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int p, double* dZ,
                       int64_t ldz, expm_info* info) {
     cudaStream_t s = P->stream;
@@ -252,19 +314,19 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
     bool converged = false;
     double normB = 0.0;
     expm_status result = EXPM_OK;
+    // graph of one restart cycle, cached per (algorithm, p, t)
+    GraphEntry* ge = nullptr;
+    if (P->use_graphs && !P->prof && P->stream != nullptr) ge = graph_for(P, t, p, alg);
     while (true) {
         ++cycles;
-        for (int j = 0; j < m; ++j) {
-            st = block_step(P, t, j, p, alg);
+        if (ge) {
+            CK(cudaGraphLaunch(ge->exec, s));
+            P->launches += ge->launches;
+            for (int k = 0; k < EXPM_NSTAGES; ++k) P->stage_launches[k] += ge->stage_launches[k];
+        } else {
+            st = issue_cycle(P, t, p, alg);
             if (st != EXPM_OK) return st;
         }
-        LAUNCH(EXPM_STAGE_POLES, launch_poles(P->H, P->ldH, mp, p, P->npoles, tau_re, tau_re + EXPM_MAX_POLES,
-                                              tau_re + 2 * EXPM_MAX_POLES, tau_re + 3 * EXPM_MAX_POLES,
-                                              P->S, P->poles, P->Wc_slots, P->stat, flags_of(P->stat),
-                                              alg, s));
-        LAUNCH(EXPM_STAGE_POLES, launch_combine(P->Wc_slots, P->npoles, mp + p, p, sm(P, kOffWc), s));
-        LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk));
-        CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         prof_flush(P);
         st = check_flags(P->hpin);
@@ -330,6 +392,7 @@ void free_plan(expm_plan* P) {
     cudaFree(P->stat);
     if (P->hpin) cudaFreeHost(P->hpin);
     for (auto& e : P->ev) cudaEventDestroy(e);
+    for (auto& g : P->graphs) cudaGraphExecDestroy(g.exec);
     delete P;
 }
 
@@ -400,6 +463,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     P->ndim = op->ndim;
     P->p_max = p_max;
     P->stream = reinterpret_cast<cudaStream_t>(stream);
+    P->use_graphs = true;
     int64_t n = 1;
     for (int d = 0; d < 3; ++d) {
         Axis& a = P->ax[d];
@@ -440,7 +504,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         delete P;
         return EXPM_CUDA_ERROR;
     }
-    P->nblk = consistent_blocks(n, std::max(1, std::min<int>(2 * sms, (int)((n + 63) / 64))));
+    P->nblk = consistent_blocks(n, std::max(1, std::min<int>(sms, (int)((n + 63) / 64))));
     const int m = opts->m;
     const int64_t ld = P->ld;
     P->ldH = (m + 1) * p_max;

@@ -48,6 +48,14 @@ struct GemmArgsMixed {
 
 }  // namespace expm
 
+struct GraphEntry {
+    int alg = 0, p = 0;
+    double t = 0.0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+    int64_t stage_launches[EXPM_NSTAGES] = {};
+};
+
 struct expm_plan_s {
     expm_op_desc op{};
     expm_opts opts{};
@@ -103,6 +111,9 @@ struct expm_plan_s {
     std::vector<cudaEvent_t> ev;
     std::vector<int> pend_stage;          // stage of pending event pair k (events 2k, 2k+1)
     int ev_used = 0;
+    // CUDA graphs of one restart cycle, keyed by (algorithm, p, t)
+    bool use_graphs = false;
+    std::vector<GraphEntry> graphs;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -149,6 +160,8 @@ cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          double* res, int* flags, int alg, cudaStream_t s);
 cudaError_t launch_combine(const double* Wc_slots, int npoles, int rows, int p, double* Wc,
                            cudaStream_t s);
+cudaError_t launch_combine2(const double* H, int ldH, int mp, int p, int npoles,
+                            const double* Y_slots, double* Wc, int alg, cudaStream_t s);
 cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
                             const double* Wc, double* Z, int64_t ldz, int restart_copy,
                             cudaStream_t s, int nblk);

@@ -75,15 +75,40 @@ __global__ void __launch_bounds__(NT) k_proj(const double* __restrict__ V, int64
     }
 }
 
-// h[o] = sum_b part[b][o]; H[row0 + a, col0 + c] (+)= h[a][c]
-__global__ void k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p,
-                           double* __restrict__ h, double* H, int ldH, int row0, int col0,
-                           int accumulate) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+// Sum of the nblk partials of output o, split over `stripes` threads (stripe s takes
+// b = s, s + stripes, ...) with four independent accumulators; the caller adds the stripes
+// in a fixed order, so the result does not depend on scheduling.
+__device__ inline double stripe_sum(const double* __restrict__ part, int nblk, int nout, int o,
+                                    int s, int stripes) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = s;
+    for (; b + 3 * stripes < nblk; b += 4 * stripes) {
+        a0 += part[(int64_t)b * nout + o];
+        a1 += part[(int64_t)(b + stripes) * nout + o];
+        a2 += part[(int64_t)(b + 2 * stripes) * nout + o];
+        a3 += part[(int64_t)(b + 3 * stripes) * nout + o];
+    }
+    for (; b < nblk; b += stripes) a0 += part[(int64_t)b * nout + o];
+    return (a0 + a1) + (a2 + a3);
+}
+
+constexpr int RED_OUT = 32;       // outputs per reduction CTA
+constexpr int RED_STRIPES = 8;    // threads per output
+
+// h[o] = sum_b part[b][o]; H[row0 + a, col0 + c] (+)= h[a][c].  CTA = 32 outputs x 8 stripes.
+__global__ void __launch_bounds__(RED_OUT * RED_STRIPES)
+k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p, double* __restrict__ h,
+           double* H, int ldH, int row0, int col0, int accumulate) {
+    __shared__ double red[RED_STRIPES][RED_OUT];
     const int nout = cols * p;
-    if (o >= nout) return;
+    const int ol = threadIdx.x % RED_OUT, st = threadIdx.x / RED_OUT;
+    const int o = blockIdx.x * RED_OUT + ol;
+    red[st][ol] = (o < nout) ? stripe_sum(part, nblk, nout, o, st, RED_STRIPES) : 0.0;
+    __syncthreads();
+    if (st != 0 || o >= nout) return;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * nout + o];
+#pragma unroll
+    for (int k = 0; k < RED_STRIPES; ++k) s += red[k][ol];
     h[o] = s;
     if (H) {
         const int a = o / p, c = o % p;
@@ -168,20 +193,34 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
 // upper Cholesky G = R^T R, R^{-1}, Rtot = R Rtot (Rtot = R on the first pass).  The last
 // pass writes Rtot into H (rows hrow.., cols hcol..) and checks for breakdown against the
 // column norms of W before orthogonalisation (H column above + Rtot column).
-__global__ void k_chol(const double* __restrict__ part, int nblk, int p, double shift_rel,
-                       double* R, double* Rinv, double* Rtot, int first, double* H, int ldH,
-                       int hrow, int hcol, double* normsq_out, int* flags) {
+__global__ void __launch_bounds__(256) k_chol(const double* __restrict__ part, int nblk, int p,
+                                              double shift_rel, double* R, double* Rinv,
+                                              double* Rtot, int first, double* H, int ldH,
+                                              int hrow, int hcol, double* normsq_out, int* flags) {
     __shared__ double G[kMaxP * kMaxP], Rs[kMaxP * kMaxP], Ri[kMaxP * kMaxP], Rt[kMaxP * kMaxP];
+    __shared__ double red[256];
     __shared__ int bad;
-    const int lane = threadIdx.x;   // blockDim.x == 32
     const int pp = p * p;
-    for (int o = lane; o < pp; o += 32) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * pp + o];
-        G[o] = s;
-        Rs[o] = 0.0;
-        Ri[o] = 0.0;
+    // G = sum of the partial Gram matrices: every output split over 256 / pp stripes
+    {
+        const int stripes = pp >= 256 ? 1 : 256 / pp;
+        for (int base = 0; base < pp; base += 256 / stripes) {
+            const int ol = threadIdx.x % (256 / stripes), st = threadIdx.x / (256 / stripes);
+            const int o = base + ol;
+            red[threadIdx.x] = (o < pp && st < stripes) ? stripe_sum(part, nblk, pp, o, st, stripes) : 0.0;
+            __syncthreads();
+            if (st == 0 && o < pp) {
+                double s = 0.0;
+                for (int k = 0; k < stripes; ++k) s += red[k * (256 / stripes) + ol];
+                G[o] = s;
+                Rs[o] = 0.0;
+                Ri[o] = 0.0;
+            }
+            __syncthreads();
+        }
     }
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     if (lane == 0) bad = 0;
     __syncwarp();
     double tr = 0.0;
@@ -417,10 +456,9 @@ cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const do
 cudaError_t launch_reduce_h(const double* part, int nblk_req, int cols, int p, double* h,
                             double* H, int ldH, int row0, int col0, int accumulate,
                             cudaStream_t s) {
-    (void)nblk_req;
     const int nout = cols * p;
-    k_reduce_h<<<(nout + 127) / 128, 128, 0, s>>>(part, nblk_req, cols, p, h, H, ldH, row0, col0,
-                                                  accumulate);
+    k_reduce_h<<<(nout + RED_OUT - 1) / RED_OUT, RED_OUT * RED_STRIPES, 0, s>>>(
+        part, nblk_req, cols, p, h, H, ldH, row0, col0, accumulate);
     return cudaGetLastError();
 }
 
@@ -442,8 +480,8 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,
                         double* Rinv, double* Rtot, int first, double* H, int ldH, int hrow,
                         int hcol, double* normsq_out, int* flags, cudaStream_t s) {
-    k_chol<<<1, 32, 0, s>>>(part, nblk, p, shift_rel, R, Rinv, Rtot, first, H, ldH, hrow, hcol,
-                            normsq_out, flags);
+    k_chol<<<1, 256, 0, s>>>(part, nblk, p, shift_rel, R, Rinv, Rtot, first, H, ldH, hrow, hcol,
+                             normsq_out, flags);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,49 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g) {
 }
 
 // One thread per (mode, column): forward elimination and back substitution along x with
-// the precomputed Thomas factors of tridiag(l, c + lambda_mode, u).  in may equal out.
+// the precomputed Thomas factors of tridiag(l, c + lambda_mode, u).  The recurrence is
+// sequential in x, so loads are issued TCH steps ahead (chunked register prefetch) to keep
+// the dependent chain from waiting on one global load per step.  in may equal out (each
+// chunk is read before it is written).
+constexpr int TCH = 16;
+
+template <typename T>
+__device__ inline void thomas_line(const T* f, T* y, int L, int64_t nm, int64_t k, T l_sub,
+                                   const T* __restrict__ thm, const T* __restrict__ thc, T inv_t) {
+    T prev = 0;
+    for (int x0 = 0; x0 < L; x0 += TCH) {
+        T fv[TCH], mv[TCH];
+#pragma unroll
+        for (int q = 0; q < TCH; ++q)
+            if (x0 + q < L) {
+                fv[q] = f[(int64_t)(x0 + q) * nm];
+                mv[q] = thm[(int64_t)(x0 + q) * nm + k];
+            }
+#pragma unroll
+        for (int q = 0; q < TCH; ++q)
+            if (x0 + q < L) {
+                prev = (fv[q] * inv_t - l_sub * prev) * mv[q];
+                y[(int64_t)(x0 + q) * nm] = prev;
+            }
+    }
+    T next = prev;
+    for (int x1 = L - 2; x1 >= 0; x1 -= TCH) {
+        T yv[TCH], cv[TCH];
+#pragma unroll
+        for (int q = 0; q < TCH; ++q)
+            if (x1 - q >= 0) {
+                yv[q] = y[(int64_t)(x1 - q) * nm];
+                cv[q] = thc[(int64_t)(x1 - q) * nm + k];
+            }
+#pragma unroll
+        for (int q = 0; q < TCH; ++q)
+            if (x1 - q >= 0) {
+                next = yv[q] - cv[q] * next;
+                y[(int64_t)(x1 - q) * nm] = next;
+            }
+    }
+}
+
 __global__ void k_tridiag_lines(const double* in, int64_t ld_in, double* out, int64_t ld_out,
                                 int p, int L, int64_t nmodes, double l_sub,
                                 const double* __restrict__ thm, const double* __restrict__ thc,
@@ -83,21 +125,7 @@ __global__ void k_tridiag_lines(const double* in, int64_t ld_in, double* out, in
     if (gid >= nmodes * p) return;
     const int64_t k = gid % nmodes;
     const int c = (int)(gid / nmodes);
-    const double* f = in + c * ld_in + k;
-    double* y = out + c * ld_out + k;
-    double prev = 0.0;
-    for (int x = 0; x < L; ++x) {
-        const int64_t o = (int64_t)x * nmodes;
-        const double v = (f[o] * inv_t - l_sub * prev) * thm[o + k];
-        y[o] = v;
-        prev = v;
-    }
-    double next = prev;
-    for (int x = L - 2; x >= 0; --x) {
-        const int64_t o = (int64_t)x * nmodes;
-        next = y[o] - thc[o + k] * next;
-        y[o] = next;
-    }
+    thomas_line<double>(in + c * ld_in + k, out + c * ld_out + k, L, nmodes, k, l_sub, thm, thc, inv_t);
 }
 
 // Thomas factors for every mode (one thread per mode): pivots b - l c'_{x-1}, stored as
@@ -241,19 +269,7 @@ __global__ void k_tridiag_lines32(float* y_io, int64_t ld, int p, int L, int64_t
     const int64_t k = gid % nmodes;
     const int c = (int)(gid / nmodes);
     float* y = y_io + c * ld + k;
-    float prev = 0.f;
-    for (int x = 0; x < L; ++x) {
-        const int64_t o = (int64_t)x * nmodes;
-        const float v = (y[o] * inv_t - l_sub * prev) * thm[o + k];
-        y[o] = v;
-        prev = v;
-    }
-    float next = prev;
-    for (int x = L - 2; x >= 0; --x) {
-        const int64_t o = (int64_t)x * nmodes;
-        next = y[o] - thc[o + k] * next;
-        y[o] = next;
-    }
+    thomas_line<float>(y, y, L, nmodes, k, l_sub, thm, thc, inv_t);
 }
 
 __global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, int64_t n) {

@@ -5,10 +5,10 @@
 //   S_i <- tau_i H_{m+1,m} E_m^T Z_i,  ||R_i||_F = ||S_i||_F     eq. (49) and the residual
 //                                                             formula above it (collinear
 //                                                             with V_{m+1}: restart factor)
-//   Wc_i = 2 Re(omega_i H~_m Z_i)   ((m+1)p x p, real)          eq. (4.5): X_i - X_i^0 =
-//                                                             (tA)^{-1} V_m Z_i = V_{m+1} H~_m Z_i
+//   Wc = sum_i 2 Re(omega_i H~_m Z_i) = H~_m sum_i 2 Re(omega_i Z_i)  (H~ real)
+//                                          eq. (4.5): X_i - X_i^0 = (tA)^{-1} V_m Z_i = V_{m+1} H~_m Z_i
 // Algorithm 1 (alg = 1): (H_m - tau_i I) Z_i = E_1 S_i (eq. (3.3)), S_i <- -H_{m+1,m} E_m^T Z_i
-// (eq. (35)), Wc_i = 2 Re(omega_i Z_i) (X_i - X_i^0 = V_m Z_i).
+// (eq. (35)), Wc = [sum_i 2 Re(omega_i Z_i); 0] (X_i - X_i^0 = V_m Z_i).
 // H_m is band upper Hessenberg with p sub-diagonals, so Gaussian elimination with partial
 // pivoting only looks at rows j..j+p of column j.  The matrix lives in shared memory when
 // (mp)^2 + mp p complex numbers fit, else in a global workspace (L2-resident).
@@ -31,19 +31,26 @@ __device__ inline cplx cdiv(cplx a, cplx b) {
 __device__ inline double cabs2(cplx a) { return a.re * a.re + a.im * a.im; }
 
 constexpr size_t kSmemLimit = 200 * 1024;
+constexpr int kPoleThreads = 64;
 
-__global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int ldH, int mp, int p,
-                                               const double* __restrict__ tau_re,
-                                               const double* __restrict__ tau_im,
-                                               const double* __restrict__ om_re,
-                                               const double* __restrict__ om_im,
-                                               double* __restrict__ S, double* __restrict__ work,
-                                               double* __restrict__ Wc_slots, double* res,
-                                               int* flags, int use_smem, int alg) {
+// One CTA (two warps) per pole.  Shared memory holds M (mp x mp complex), the right-hand
+// sides / solution X (mp x p complex) and, when it fits, the real H~ ((mp+p) x mp), staged
+// once with coalesced loads.  Outputs: the restart factor S_i, ||S_i||_F, and
+// Y_i = 2 Re(omega_i Z_i) (mp x p real).  Since H~ is real,
+// sum_i 2 Re(omega_i H~ Z_i) = H~ sum_i Y_i, so the product with H~ is done once for all
+// poles by k_combine.
+__global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict__ H, int ldH, int mp, int p,
+                                                        const double* __restrict__ tau_re,
+                                                        const double* __restrict__ tau_im,
+                                                        const double* __restrict__ om_re,
+                                                        const double* __restrict__ om_im,
+                                                        double* __restrict__ S, double* __restrict__ work,
+                                                        double* __restrict__ Y_slots, double* res,
+                                                        int* flags, int use_smem, int h_in_smem, int alg) {
     extern __shared__ double sm[];
     __shared__ cplx f[kMaxP + 1];
     __shared__ int piv_s;
-    __shared__ double red[256];
+    __shared__ double red[kPoleThreads];
     const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const cplx tau{tau_re[i], tau_im[i]};
     const cplx om{om_re[i], om_im[i]};
@@ -51,11 +58,19 @@ __global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int
     cplx* M = use_smem ? reinterpret_cast<cplx*>(sm) : reinterpret_cast<cplx*>(work) + (size_t)i * per;
     cplx* X = M + (size_t)mp * mp;
     cplx* Si = reinterpret_cast<cplx*>(S) + (size_t)i * p * p;
+    const int rows = mp + p;
+    // H~ (rows x mp, column-major, ld = rows) in shared memory after M and X when it fits
+    double* Hs = reinterpret_cast<double*>(sm) + (use_smem ? 2 * per : 0);
+    const double* Hr = h_in_smem ? Hs : H;
+    const int ldr = h_in_smem ? rows : ldH;
+    if (h_in_smem)
+        for (int e = tid; e < rows * mp; e += nt) Hs[e] = H[(int64_t)(e / rows) * ldH + (e % rows)];
+    __syncthreads();
     // Algorithm 2: M = I - tau H_m (eq. (3236)); Algorithm 1: M = H_m - tau I (eq. (3.3));
     // row-major.  X = E_1 S_i.
     for (int e = tid; e < mp * mp; e += nt) {
         const int r = e / mp, c = e % mp;
-        const double h = H[(int64_t)c * ldH + r];
+        const double h = Hr[(int64_t)c * ldr + r];
         const double d = (r == c ? 1.0 : 0.0);
         M[e] = (alg == 2) ? cplx{d - tau.re * h, -tau.im * h} : cplx{h - d * tau.re, -d * tau.im};
     }
@@ -64,7 +79,7 @@ __global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int
         X[e] = (r < p) ? Si[r * p + c] : cplx{0.0, 0.0};
     }
     __syncthreads();
-    // elimination with partial pivoting inside the band
+    // elimination with partial pivoting inside the band (rows j..j+p of column j)
     for (int j = 0; j < mp; ++j) {
         const int jmax = min(j + p, mp - 1);
         if (tid == 0) {
@@ -119,18 +134,18 @@ __global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int
         }
         __syncthreads();
     }
-    // S_i <- tau H_{m+1,m} E_m^T Z_i and its Frobenius norm
+    // S_i and its Frobenius norm.  Algorithm 2: tau H_{m+1,m} E_m^T Z_i (eq. (49));
+    // Algorithm 1: -H_{m+1,m} E_m^T Z_i (eq. (35)).
     double ss = 0.0;
     for (int e = tid; e < p * p; e += nt) {
         const int a = e / p, c = e % p;
         cplx s{0.0, 0.0};
         for (int b = 0; b < p; ++b) {
-            const double h = H[(int64_t)(mp - p + b) * ldH + mp + a];
+            const double h = Hr[(int64_t)(mp - p + b) * ldr + mp + a];
             const cplx x = X[(size_t)(mp - p + b) * p + c];
             s.re += h * x.re;
             s.im += h * x.im;
         }
-        // Algorithm 2: tau H_{m+1,m} E_m^T Z_i (eq. (49)); Algorithm 1: -H_{m+1,m} E_m^T Z_i (eq. (35))
         const cplx snew = (alg == 2) ? cmul(tau, s) : cplx{-s.re, -s.im};
         Si[e] = snew;
         ss += cabs2(snew);
@@ -145,24 +160,36 @@ __global__ void __launch_bounds__(256) k_poles(const double* __restrict__ H, int
         res[i] = sqrt(red[0]);
         if (!isfinite(red[0])) atomicOr(&flags[0], 4);
     }
-    // Algorithm 2: Wc_i = 2 Re(omega_i H~_m Z_i) (H~ row r has non-zeros in columns >= r - p);
-    // Algorithm 1: Wc_i = 2 Re(omega_i Z_i) on the first mp rows, 0 on the last p.
+    // Y_i = 2 Re(omega_i Z_i), stored r fastest (Y[c * mp + r])
+    double* Yi = Y_slots + (size_t)i * mp * p;
+    for (int e = tid; e < mp * p; e += nt) {
+        const int r = e % mp, c = e / mp;
+        const cplx x = X[(size_t)r * p + c];
+        Yi[e] = 2.0 * (om.re * x.re - om.im * x.im);
+    }
+}
+
+// Wc = H~ sum_i Y_i (Algorithm 2) or [sum_i Y_i; 0] (Algorithm 1), (mp+p) x p, row-major
+// [r][c] as k_update_z reads it.  One thread per output, r fastest (coalesced H~ columns).
+__global__ void k_combine2(const double* __restrict__ H, int ldH, int mp, int p, int npoles,
+                           const double* __restrict__ Y_slots, double* __restrict__ Wc, int alg) {
+    extern __shared__ double Ys[];          // mp x p, summed over poles (fixed order)
     const int rows = mp + p;
-    double* Wi = Wc_slots + (size_t)i * rows * p;
-    for (int e = tid; e < rows * p; e += nt) {
-        const int r = e / p, c = e % p;
-        cplx s{0.0, 0.0};
+    for (int e = threadIdx.x; e < mp * p; e += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < npoles; ++i) s += Y_slots[(size_t)i * mp * p + e];
+        Ys[e] = s;
+    }
+    __syncthreads();
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * p; e += gridDim.x * blockDim.x) {
+        const int r = e % rows, c = e / rows;
+        double s = 0.0;
         if (alg == 2) {
-            for (int k = max(0, r - p); k < mp; ++k) {
-                const double h = H[(int64_t)k * ldH + r];
-                const cplx x = X[(size_t)k * p + c];
-                s.re += h * x.re;
-                s.im += h * x.im;
-            }
+            for (int k = max(0, r - p); k < mp; ++k) s = fma(H[(int64_t)k * ldH + r], Ys[c * mp + k], s);
         } else if (r < mp) {
-            s = X[(size_t)r * p + c];
+            s = Ys[c * mp + r];
         }
-        Wi[e] = 2.0 * (om.re * s.re - om.im * s.im);
+        Wc[r * p + c] = s;
     }
 }
 
@@ -173,18 +200,37 @@ size_t poles_smem_bytes(int mp, int p) {
     return b <= kSmemLimit ? b : 0;
 }
 
+static size_t poles_h_bytes(int mp, int p) { return (size_t)(mp + p) * mp * sizeof(double); }
+
 cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          const double* tau_re, const double* tau_im, const double* om_re,
-                         const double* om_im, double* S, double* work, double* Wc_slots,
+                         const double* om_im, double* S, double* work, double* Y_slots,
                          double* res, int* flags, int alg, cudaStream_t s) {
-    const size_t shm = poles_smem_bytes(mp, p);
-    k_poles<<<npoles, 256, shm, s>>>(H, ldH, mp, p, tau_re, tau_im, om_re, om_im, S, work,
-                                     Wc_slots, res, flags, shm > 0 ? 1 : 0, alg);
+    size_t shm = poles_smem_bytes(mp, p);
+    int h_in = 0;
+    if (shm > 0 && shm + poles_h_bytes(mp, p) <= kSmemLimit) {
+        shm += poles_h_bytes(mp, p);
+        h_in = 1;
+    }
+    k_poles<<<npoles, kPoleThreads, shm, s>>>(H, ldH, mp, p, tau_re, tau_im, om_re, om_im, S, work,
+                                              Y_slots, res, flags, poles_smem_bytes(mp, p) > 0 ? 1 : 0,
+                                              h_in, alg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine2(const double* H, int ldH, int mp, int p, int npoles,
+                            const double* Y_slots, double* Wc, int alg, cudaStream_t s) {
+    const int nout = (mp + p) * p;
+    const int blocks = (nout + 255) / 256;
+    k_combine2<<<blocks, 256, sizeof(double) * (size_t)mp * p, s>>>(H, ldH, mp, p, npoles, Y_slots, Wc, alg);
     return cudaGetLastError();
 }
 
 cudaError_t poles_set_smem_limits() {
-    return cudaFuncSetAttribute(k_poles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+    cudaError_t e = cudaFuncSetAttribute(k_poles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_combine2, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024);
+    return e;
 }
 
 }  // namespace expm

@@ -36,21 +36,23 @@ def test_refined_fp32_inverse_matches_fp64(sides, diff, vel, t, p):
 
 
 @pytest.mark.parametrize("sides,diff,vel,t,p", CASES[:3])
-def test_mixed_fixed_cycles_parity(tab, sides, diff, vel, t, p):
+def test_mixed_converged_matches_fp64_and_closed_form(tab, sides, diff, vel, t, p):
+    """Converged to tol 1e-12, the mixed path agrees with the FP64 path and with r(tA)B.
+    (Unconverged iterates of the two are not comparable: FP32 projections perturb the basis
+    at the 1e-7 level, which moves an unconverged iterate by about its own residual.)"""
     need_gpu()
     from paper_1405_0707_gb300 import Plan
     n = int(np.prod(sides))
     B = inputs.rhs(n, p, 78)
-    m = 5
-    for alg in (1, 2):
-        Z64, i64 = Plan(sides, diff, vel, p_max=p, m=m, fixed_cycles=3, algorithm=alg).expm_block(t, to_dev(B))
-        Z32, i32 = Plan(sides, diff, vel, p_max=p, m=m, fixed_cycles=3, algorithm=alg,
+    ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+    for alg in (0,):          # AUTO: Algorithm 1 on the first case, Algorithm 2 on the others
+        Z64, i64 = Plan(sides, diff, vel, p_max=p, m=5, tol=1e-12, max_cycles=400,
+                        algorithm=alg).expm_block(t, to_dev(B))
+        Z32, i32 = Plan(sides, diff, vel, p_max=p, m=5, tol=1e-12, max_cycles=400, algorithm=alg,
                         precision="mixed").expm_block(t, to_dev(B))
-        Z64, Z32 = to_np(Z64), to_np(Z32)
-        # FP32 projections perturb the basis at the 1e-7 level but keep the Arnoldi relation
-        # exact, so the cycle-3 iterates agree to the size of their own residual (the
-        # bases span slightly different spaces), well inside 1e-8 of Z
-        assert rel(Z32, Z64) <= 1e-8, (alg, rel(Z32, Z64))
+        assert i64.converged and i32.converged, alg
+        assert rel(to_np(Z32), to_np(Z64)) <= 1e-9, (alg, rel(to_np(Z32), to_np(Z64)))
+        assert rel(to_np(Z32), ref) <= 1e-9
 
 
 @pytest.mark.parametrize("t", [1e-3, 1e-2, 1e-1])
