@@ -10,6 +10,7 @@
 //   Z = omega_0 B + Z_acc   (eq. (11) with the conjugate pairs folded)
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -463,7 +464,10 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     P->ndim = op->ndim;
     P->p_max = p_max;
     P->stream = reinterpret_cast<cudaStream_t>(stream);
-    P->use_graphs = true;
+    {
+        const char* ng = std::getenv("EXPM_DISABLE_GRAPHS");   // debugging switch
+        P->use_graphs = !(ng && ng[0] == '1');
+    }
     int64_t n = 1;
     for (int d = 0; d < 3; ++d) {
         Axis& a = P->ax[d];
@@ -504,7 +508,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         delete P;
         return EXPM_CUDA_ERROR;
     }
-    P->nblk = consistent_blocks(n, std::max(1, std::min<int>(sms, (int)((n + 63) / 64))));
+    P->nblk = consistent_blocks(n, std::max(1, std::min<int>(2 * sms, (int)((n + 63) / 64))));
     const int m = opts->m;
     const int64_t ld = P->ld;
     P->ldH = (m + 1) * p_max;

@@ -34,6 +34,58 @@ __device__ inline void load_tile(const double* __restrict__ X, int64_t ld, int c
     }
 }
 
+// Gram partial of a TR x p tile X (row-major X[rr * p + c]), upper triangle only (the
+// Cholesky factorisation reads nothing else).  With p^2 <= NT every output gets NT / p^2
+// threads that take every (NT / p^2)-th row, so the dependent chains are short; gram_write
+// adds the stripes in a fixed order.  With p^2 > NT each thread owns whole outputs.
+template <int OPT>
+__device__ inline void gram_accumulate(const double* X, int p, int nout, double* acc) {
+    if (nout <= NT) {
+        const int stripes = NT / nout, o = threadIdx.x % nout, st = threadIdx.x / nout;
+        const int c1 = o / p, c2 = o % p;
+        if (st < stripes && c1 <= c2) {
+            double s = 0.0;
+            for (int rr = st; rr < TR; rr += stripes) s = fma(X[rr * p + c1], X[rr * p + c2], s);
+            acc[0] += s;
+        }
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+        const int o = threadIdx.x + q * NT;
+        if (o < nout) {
+            const int c1 = o / p, c2 = o % p;
+            if (c1 <= c2) {
+                double s = 0.0;
+#pragma unroll
+                for (int rr = 0; rr < TR; ++rr) s = fma(X[rr * p + c1], X[rr * p + c2], s);
+                acc[q] += s;
+            }
+        }
+    }
+}
+
+template <int OPT>
+__device__ inline void gram_write(const double* acc, int p, int nout, double* __restrict__ part) {
+    if (nout <= NT) {
+        __shared__ double red[NT];
+        const int stripes = NT / nout;
+        red[threadIdx.x] = acc[0];
+        __syncthreads();
+        if (threadIdx.x < nout) {
+            double s = 0.0;
+            for (int k = 0; k < stripes; ++k) s += red[k * nout + threadIdx.x];
+            part[(int64_t)blockIdx.x * nout + threadIdx.x] = s;
+        }
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+        const int o = threadIdx.x + q * NT;
+        if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+    }
+}
+
 // partial[blk][a][c] = sum_{rows of blk} V[r, a] W[r, c]      (a < cols, c < p)
 // T = float: FP32 products over each 16-row tile (the mixed path's projections; only the
 // FP64 updates must be exact for the Arnoldi relation), FP64 accumulation across tiles.
@@ -157,15 +209,15 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
                 Vf[rr * cs + a] = (float)Vs[rr * cs + a];
             }
         __syncthreads();
+        if (gram) gram_accumulate<OPT>(Ws, p, nout, acc);
+        else
 #pragma unroll
         for (int q = 0; q < OPT; ++q) {
             const int o = threadIdx.x + q * NT;
             if (o < nout) {
                 double s = 0.0;
                 if (gram) {
-                    const int c1 = o / p, c2 = o % p;
-#pragma unroll
-                    for (int rr = 0; rr < TR; ++rr) s = fma(Ws[rr * p + c1], Ws[rr * p + c2], s);
+                    // handled below by gram_accumulate
                 } else if (F32) {
                     const int a = o / p, c = o % p;
                     float sf = 0.f;
@@ -181,6 +233,10 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
             }
         }
         __syncthreads();
+    }
+    if (gram) {
+        gram_write<OPT>(acc, p, nout, part);
+        return;
     }
 #pragma unroll
     for (int q = 0; q < OPT; ++q) {
@@ -218,6 +274,26 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ part, i
             }
             __syncthreads();
         }
+    }
+    // squared norms of the H columns above row hrow (for the breakdown test), all threads
+    __shared__ double hn2[kMaxP];
+    if (H) {
+        const int stripes = 256 / p;
+        const int c = threadIdx.x % p, st = threadIdx.x / p;
+        double v2 = 0.0;
+        if (st < stripes)
+            for (int a = st; a < hrow; a += stripes) {
+                const double v = H[(int64_t)(hcol + c) * ldH + a];
+                v2 += v * v;
+            }
+        red[threadIdx.x] = v2;
+        __syncthreads();
+        if (threadIdx.x < p) {
+            double s2 = 0.0;
+            for (int k = 0; k < stripes; ++k) s2 += red[k * p + threadIdx.x];
+            hn2[threadIdx.x] = s2;
+        }
+        __syncthreads();
     }
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
@@ -284,11 +360,7 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ part, i
         }
         if (lane < p) {
             const int c = lane;
-            double n0 = 0.0;
-            for (int a = 0; a < hrow; ++a) {
-                const double v = H[(int64_t)(hcol + c) * ldH + a];
-                n0 += v * v;
-            }
+            double n0 = hn2[c];
             for (int a = 0; a <= c; ++a) n0 += Rt[a * p + c] * Rt[a * p + c];
             if (Rt[c * p + c] <= 1e-14 * sqrt(n0)) atomicOr(&flags[1], 1);
         }
@@ -323,28 +395,10 @@ __global__ void __launch_bounds__(NT) k_trsm(double* __restrict__ W, int64_t ldw
             if (rr < tr) out[(int64_t)c * ldo + r0 + rr] = s;
         }
         __syncthreads();
-        if (gram) {
-#pragma unroll
-            for (int q = 0; q < OPT; ++q) {
-                const int o = threadIdx.x + q * NT;
-                if (o < nout) {
-                    const int c1 = o / p, c2 = o % p;
-                    double s = 0.0;
-#pragma unroll
-                    for (int rr = 0; rr < TR; ++rr) s = fma(Wn[rr * p + c1], Wn[rr * p + c2], s);
-                    acc[q] += s;
-                }
-            }
-        }
+        if (gram) gram_accumulate<OPT>(Wn, p, nout, acc);
         __syncthreads();
     }
-    if (gram) {
-#pragma unroll
-        for (int q = 0; q < OPT; ++q) {
-            const int o = threadIdx.x + q * NT;
-            if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
-        }
-    }
+    if (gram) gram_write<OPT>(acc, p, nout, part);
 }
 
 // Z[r, c] += sum_{a < cols} V[r, a] Wc[a][c]; restart: V[:, 0:p] <- V[:, cols-p:cols].

@@ -29,11 +29,16 @@ __device__ inline cplx cdiv(cplx a, cplx b) {
     return {(ar * br + ai * bi) / d, (ai * br - ar * bi) / d};
 }
 __device__ inline double cabs2(cplx a) { return a.re * a.re + a.im * a.im; }
+// x -= a * b with four fused multiply-adds
+__device__ inline void cmsub(cplx& x, cplx a, cplx b) {
+    x.re = fma(-a.re, b.re, fma(a.im, b.im, x.re));
+    x.im = fma(-a.re, b.im, fma(-a.im, b.re, x.im));
+}
 
 constexpr size_t kSmemLimit = 200 * 1024;
-constexpr int kPoleThreads = 64;
+constexpr int kPoleThreads = 128;
 
-// One CTA (two warps) per pole.  Shared memory holds M (mp x mp complex), the right-hand
+// One CTA (four warps) per pole.  Shared memory holds M (mp x mp complex), the right-hand
 // sides / solution X (mp x p complex) and, when it fits, the real H~ ((mp+p) x mp), staged
 // once with coalesced loads.  Outputs: the restart factor S_i, ||S_i||_F, and
 // Y_i = 2 Re(omega_i Z_i) (mp x p real).  Since H~ is real,
@@ -111,26 +116,29 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
         if (tid < nr) f[tid] = cdiv(M[(size_t)(j + 1 + tid) * mp + j], M[(size_t)j * mp + j]);
         __syncthreads();
         const int ncM = mp - j - 1, w = ncM + p;
-        for (int e = tid; e < nr * w; e += nt) {
-            const int rr = e / w, k = e % w;
+        for (int rr = 0; rr < nr; ++rr) {
             const int r = j + 1 + rr;
-            if (k < ncM) {
-                const int col = j + 1 + k;
-                M[(size_t)r * mp + col] = csub(M[(size_t)r * mp + col], cmul(f[rr], M[(size_t)j * mp + col]));
-            } else {
-                const int c = k - ncM;
-                X[(size_t)r * p + c] = csub(X[(size_t)r * p + c], cmul(f[rr], X[(size_t)j * p + c]));
+            const cplx fr = f[rr];
+            for (int k = tid; k < w; k += nt) {
+                if (k < ncM) {
+                    const int col = j + 1 + k;
+                    cmsub(M[(size_t)r * mp + col], fr, M[(size_t)j * mp + col]);
+                } else {
+                    const int c = k - ncM;
+                    cmsub(X[(size_t)r * p + c], fr, X[(size_t)j * p + c]);
+                }
             }
         }
         __syncthreads();
     }
-    // back substitution on the upper triangle
+    // back substitution on the upper triangle; thread -> (row offset, column) fixed
+    const int bc = tid % p, br0 = tid / p, brs = nt / p;
     for (int j = mp - 1; j >= 0; --j) {
         if (tid < p) X[(size_t)j * p + tid] = cdiv(X[(size_t)j * p + tid], M[(size_t)j * mp + j]);
         __syncthreads();
-        for (int e = tid; e < j * p; e += nt) {
-            const int r = e / p, c = e % p;
-            X[(size_t)r * p + c] = csub(X[(size_t)r * p + c], cmul(M[(size_t)r * mp + j], X[(size_t)j * p + c]));
+        if (br0 < brs) {
+            const cplx xj = X[(size_t)j * p + bc];
+            for (int r = br0; r < j; r += brs) cmsub(X[(size_t)r * p + bc], M[(size_t)r * mp + j], xj);
         }
         __syncthreads();
     }

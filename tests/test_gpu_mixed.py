@@ -9,9 +9,11 @@ from tests.gpu_util import cancellation_floor, need_gpu, rel, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
+# (at t = 1 the 11 x 9 x 7 operator has ||e^{tA}|| ~ e^-30: Z would sit at the rounding
+#  floor of the partial-fraction sum, so the 3-D case uses t = 0.3)
 CASES = [((37, 29), 0.1, (1.0, 1.0), 1e-1, 3),
          ((70, 66), 0.1, (1.0, -0.5), 1.0, 5),
-         ((11, 9, 7), 1.0, (3.0, -2.0, 1.0), 1.0, 2),
+         ((11, 9, 7), 1.0, (3.0, -2.0, 1.0), 0.3, 2),
          ((256, 256), 0.1, (1.0, 1.0), 1e-1, 8)]
 
 
