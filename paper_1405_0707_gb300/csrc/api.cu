@@ -454,7 +454,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         const size_t cols = (size_t)opts->m * p_max, cs = cols | 1;
         size_t shm = 8 * (cols * p_max + 16 * cs + 16 * (size_t)p_max);
         if (opts->precision == EXPM_PREC_MIXED) shm += 4 * (16 * cs + 16 * (size_t)p_max);
-        if (shm > 227 * 1024) return EXPM_INVALID_ARG;
+        if (shm > 225 * 1024) return EXPM_INVALID_ARG;   // 227 KB opt-in minus static memory
     }
     if (opts->algorithm < EXPM_ALG_AUTO || opts->algorithm > EXPM_ALG_PSBFOM) return EXPM_INVALID_ARG;
     expm_plan* P = new (std::nothrow) expm_plan_s();

@@ -590,12 +590,23 @@ cudaError_t launch_zero(double* X, int64_t ldx, int64_t n, int p, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Shared-memory opt-in for the launches whose dynamic size can pass 48 KB.
+// Shared-memory opt-in for the launches whose dynamic size can pass 48 KB: the device's
+// per-block opt-in maximum minus the kernel's own static shared memory.
+template <class K>
+static cudaError_t set_max_dynamic(K kernel, int optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t krylov_set_smem_limits() {
-    const int big = 227 * 1024;   // k_update_z needs up to 209 KB at m p = 512, p = 32
-    cudaError_t e = cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 #define EXPM_SET(K) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, big)
+    if (e == cudaSuccess) e = set_max_dynamic(K, optin)
     EXPM_SET((k_proj<1, double>)); EXPM_SET((k_proj<4, double>)); EXPM_SET((k_proj<16, double>));
     EXPM_SET((k_proj<64, double>)); EXPM_SET((k_proj<1, float>)); EXPM_SET((k_proj<4, float>));
     EXPM_SET((k_proj<16, float>)); EXPM_SET((k_proj<64, float>));

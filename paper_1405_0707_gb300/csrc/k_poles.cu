@@ -235,6 +235,8 @@ cudaError_t launch_combine2(const double* H, int ldH, int mp, int p, int npoles,
 }
 
 cudaError_t poles_set_smem_limits() {
+    // kSmemLimit (200 KB) of dynamic memory plus the kernel's few KB of static memory stays
+    // below the 227 KB per-block opt-in maximum
     cudaError_t e = cudaFuncSetAttribute(k_poles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_combine2, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024);
