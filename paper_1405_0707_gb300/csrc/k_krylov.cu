@@ -249,25 +249,26 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
 // upper Cholesky G = R^T R, R^{-1}, Rtot = R Rtot (Rtot = R on the first pass).  The last
 // pass writes Rtot into H (rows hrow.., cols hcol..) and checks for breakdown against the
 // column norms of W before orthogonalisation (H column above + Rtot column).
-__global__ void __launch_bounds__(256) k_chol(const double* __restrict__ part, int nblk, int p,
+constexpr int CHOL_T = 1024;
+__global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part, int nblk, int p,
                                               double shift_rel, double* R, double* Rinv,
                                               double* Rtot, int first, double* H, int ldH,
                                               int hrow, int hcol, double* normsq_out, int* flags) {
     __shared__ double G[kMaxP * kMaxP], Rs[kMaxP * kMaxP], Ri[kMaxP * kMaxP], Rt[kMaxP * kMaxP];
-    __shared__ double red[256];
+    __shared__ double red[CHOL_T];
     __shared__ int bad;
     const int pp = p * p;
-    // G = sum of the partial Gram matrices: every output split over 256 / pp stripes
+    // G = sum of the partial Gram matrices: every output split over CHOL_T / pp stripes
     {
-        const int stripes = pp >= 256 ? 1 : 256 / pp;
-        for (int base = 0; base < pp; base += 256 / stripes) {
-            const int ol = threadIdx.x % (256 / stripes), st = threadIdx.x / (256 / stripes);
+        const int stripes = pp >= CHOL_T ? 1 : CHOL_T / pp;
+        for (int base = 0; base < pp; base += CHOL_T / stripes) {
+            const int ol = threadIdx.x % (CHOL_T / stripes), st = threadIdx.x / (CHOL_T / stripes);
             const int o = base + ol;
             red[threadIdx.x] = (o < pp && st < stripes) ? stripe_sum(part, nblk, pp, o, st, stripes) : 0.0;
             __syncthreads();
             if (st == 0 && o < pp) {
                 double s = 0.0;
-                for (int k = 0; k < stripes; ++k) s += red[k * (256 / stripes) + ol];
+                for (int k = 0; k < stripes; ++k) s += red[k * (CHOL_T / stripes) + ol];
                 G[o] = s;
                 Rs[o] = 0.0;
                 Ri[o] = 0.0;
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ part, i
     // squared norms of the H columns above row hrow (for the breakdown test), all threads
     __shared__ double hn2[kMaxP];
     if (H) {
-        const int stripes = 256 / p;
+        const int stripes = CHOL_T / p;
         const int c = threadIdx.x % p, st = threadIdx.x / p;
         double v2 = 0.0;
         if (st < stripes)
@@ -399,6 +400,166 @@ __global__ void __launch_bounds__(NT) k_trsm(double* __restrict__ W, int64_t ldw
         __syncthreads();
     }
     if (gram) gram_write<OPT>(acc, p, nout, part);
+}
+
+// Row-per-thread variant for p <= 8 (the common block sizes): a row of W lives in
+// registers, W R^{-1} and the upper-triangular outer product w^T w are formed there, and
+// the Gram partial of the CTA is one warp-shuffle reduction at the end.  Loads and stores
+// are coalesced per column (consecutive threads, consecutive rows); no tile barriers.
+constexpr int RP = 8;
+constexpr int RG = RP * (RP + 1) / 2;
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(NT) k_trsm_rows(const double* __restrict__ W, int64_t ldw, int p,
+                                                  int64_t n, int64_t rpb, const double* __restrict__ Rinv,
+                                                  double* __restrict__ out, int64_t ldo,
+                                                  double* __restrict__ part, int gram) {
+    __shared__ double Ri[RP * RP];
+    __shared__ double red[NT / 32][RG];
+    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+        const int a = e / RP, c = e % RP;
+        Ri[e] = (a < p && c < p) ? Rinv[a * p + c] : 0.0;
+    }
+    __syncthreads();
+    double g[RG];
+#pragma unroll
+    for (int k = 0; k < RG; ++k) g[k] = 0.0;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        double w[RP], y[RP];
+#pragma unroll
+        for (int c = 0; c < RP; ++c) w[c] = (c < p) ? W[(int64_t)c * ldw + r] : 0.0;
+#pragma unroll
+        for (int c = 0; c < RP; ++c) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a <= c; ++a) s = fma(w[a], Ri[a * RP + c], s);
+            y[c] = s;
+            if (c < p) out[(int64_t)c * ldo + r] = s;
+        }
+        if (gram) {
+            int k = 0;
+#pragma unroll
+            for (int c1 = 0; c1 < RP; ++c1)
+#pragma unroll
+                for (int c2 = c1; c2 < RP; ++c2) {
+                    g[k] = fma(y[c1], y[c2], g[k]);
+                    ++k;
+                }
+        }
+    }
+    if (!gram) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < RG; ++k) {
+        const double v = warp_sum(g[k]);
+        if (lane == 0) red[wid][k] = v;
+    }
+    __syncthreads();
+    // partial in the p x p layout the Cholesky kernel reads (upper triangle; lower = 0)
+    for (int o = threadIdx.x; o < p * p; o += blockDim.x) {
+        const int c1 = o / p, c2 = o % p;
+        double s = 0.0;
+        if (c1 <= c2) {
+            const int k = c1 * RP - c1 * (c1 - 1) / 2 + (c2 - c1);
+            for (int w_ = 0; w_ < NT / 32; ++w_) s += red[w_][k];
+        }
+        part[(int64_t)blockIdx.x * p * p + o] = s;
+    }
+}
+
+// Row-per-thread, p <= 8: W <- W - V h (FP64, the Arnoldi relation stays exact) and the
+// upper-triangular Gram partial of the result.  h (cols x p) is broadcast from shared memory.
+__global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restrict__ V, int64_t ldv, int cols,
+                                                         double* __restrict__ W, int64_t ldw, int p,
+                                                         int64_t n, int64_t rpb,
+                                                         const double* __restrict__ h,
+                                                         double* __restrict__ part) {
+    extern __shared__ double hs[];           // cols x RP (zero-padded columns)
+    __shared__ double red[NT / 32][RG];
+    for (int e = threadIdx.x; e < cols * RP; e += blockDim.x) {
+        const int a = e / RP, c = e % RP;
+        hs[e] = (c < p) ? h[a * p + c] : 0.0;
+    }
+    __syncthreads();
+    double g[RG];
+#pragma unroll
+    for (int k = 0; k < RG; ++k) g[k] = 0.0;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        double w[RP];
+#pragma unroll
+        for (int c = 0; c < RP; ++c) w[c] = (c < p) ? W[(int64_t)c * ldw + r] : 0.0;
+        for (int a = 0; a < cols; ++a) {
+            const double v = V[(int64_t)a * ldv + r];
+#pragma unroll
+            for (int c = 0; c < RP; ++c) w[c] = fma(-v, hs[a * RP + c], w[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < RP; ++c)
+            if (c < p) W[(int64_t)c * ldw + r] = w[c];
+        int k = 0;
+#pragma unroll
+        for (int c1 = 0; c1 < RP; ++c1)
+#pragma unroll
+            for (int c2 = c1; c2 < RP; ++c2) {
+                g[k] = fma(w[c1], w[c2], g[k]);
+                ++k;
+            }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < RG; ++k) {
+        const double v = warp_sum(g[k]);
+        if (lane == 0) red[wid][k] = v;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < p * p; o += blockDim.x) {
+        const int c1 = o / p, c2 = o % p;
+        double s = 0.0;
+        if (c1 <= c2) {
+            const int k = c1 * RP - c1 * (c1 - 1) / 2 + (c2 - c1);
+            for (int w_ = 0; w_ < NT / 32; ++w_) s += red[w_][k];
+        }
+        part[(int64_t)blockIdx.x * p * p + o] = s;
+    }
+}
+
+// Row-per-thread, p <= 8: Z[r, :] += V[r, 0:cols] Wc; restart copy V[r, 0:p] <- V[r, cols-p:cols].
+__global__ void __launch_bounds__(NT) k_update_z_rows(double* __restrict__ V, int64_t ldv, int cols, int p,
+                                                      int64_t n, int64_t rpb,
+                                                      const double* __restrict__ Wc,
+                                                      double* __restrict__ Z, int64_t ldz,
+                                                      int restart_copy) {
+    extern __shared__ double ws[];           // cols x RP
+    for (int e = threadIdx.x; e < cols * RP; e += blockDim.x) {
+        const int a = e / RP, c = e % RP;
+        ws[e] = (c < p) ? Wc[a * p + c] : 0.0;
+    }
+    __syncthreads();
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        double z[RP];
+#pragma unroll
+        for (int c = 0; c < RP; ++c) z[c] = 0.0;
+        for (int a = 0; a < cols; ++a) {
+            const double v = V[(int64_t)a * ldv + r];
+#pragma unroll
+            for (int c = 0; c < RP; ++c) z[c] = fma(v, ws[a * RP + c], z[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < RP; ++c)
+            if (c < p) {
+                Z[(int64_t)c * ldz + r] += z[c];
+                // restart copy: this thread's row only, after all its reads of the row
+                if (restart_copy) V[(int64_t)c * ldv + r] = V[(int64_t)(cols - p + c) * ldv + r];
+            }
+    }
 }
 
 // Z[r, c] += sum_{a < cols} V[r, a] Wc[a][c]; restart: V[:, 0:p] <- V[:, cols-p:cols].
@@ -524,6 +685,10 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
     size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1) + TR * p);
     if (f32) shm += sizeof(float) * (TR * (cols | 1) + TR * p);
     const int nout = gram ? p * p : cols * p;
+    if (gram && p <= RP) {
+        k_update_gram_rows<<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part);
+        return cudaGetLastError();
+    }
     if (f32)
         EXPM_OPT_DISPATCH(nout, (k_update<O, true><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
     else
@@ -534,8 +699,8 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,
                         double* Rinv, double* Rtot, int first, double* H, int ldH, int hrow,
                         int hcol, double* normsq_out, int* flags, cudaStream_t s) {
-    k_chol<<<1, 256, 0, s>>>(part, nblk, p, shift_rel, R, Rinv, Rtot, first, H, ldH, hrow, hcol,
-                             normsq_out, flags);
+    k_chol<<<1, CHOL_T, 0, s>>>(part, nblk, p, shift_rel, R, Rinv, Rtot, first, H, ldH, hrow, hcol,
+                                normsq_out, flags);
     return cudaGetLastError();
 }
 
@@ -544,6 +709,10 @@ cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* 
                         cudaStream_t s) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
+    if (p <= RP) {
+        k_trsm_rows<<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram);
+        return cudaGetLastError();
+    }
     EXPM_OPT_DISPATCH(p * p, (k_trsm<O><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram)));
     return cudaGetLastError();
 }
@@ -553,6 +722,11 @@ cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
                             cudaStream_t s, int nblk) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
+    if (p <= RP) {
+        k_update_z_rows<<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz,
+                                                                         restart_copy);
+        return cudaGetLastError();
+    }
     const size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1));
     k_update_z<<<g, NT, shm, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy);
     return cudaGetLastError();
@@ -614,6 +788,8 @@ cudaError_t krylov_set_smem_limits() {
     EXPM_SET((k_update<64, false>)); EXPM_SET((k_update<1, true>)); EXPM_SET((k_update<4, true>));
     EXPM_SET((k_update<16, true>)); EXPM_SET((k_update<64, true>));
     EXPM_SET(k_update_z);
+    EXPM_SET(k_update_gram_rows);
+    EXPM_SET(k_update_z_rows);
 #undef EXPM_SET
     return e;
 }
