@@ -415,53 +415,40 @@ __device__ inline double warp_sum(double v) {
     return v;
 }
 
-__global__ void __launch_bounds__(NT) k_trsm_rows(const double* __restrict__ W, int64_t ldw, int p,
-                                                  int64_t n, int64_t rpb, const double* __restrict__ Rinv,
-                                                  double* __restrict__ out, int64_t ldo,
-                                                  double* __restrict__ part, int gram) {
-    __shared__ double Ri[RP * RP];
-    __shared__ double red[NT / 32][RG];
-    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
-        const int a = e / RP, c = e % RP;
-        Ri[e] = (a < p && c < p) ? Rinv[a * p + c] : 0.0;
-    }
-    __syncthreads();
-    double g[RG];
+// Gram partial of rows held one per lane: each warp stages its 32 rows in shared memory
+// (buf, 32 x RP), then lane l sums upper-triangle entries l and l + 32 over those rows.
+// FP64 work equals the useful products; no reduction tree.  Every lane of the warp must
+// call it (rows past the end are zero).
+__device__ inline void warp_gram_rows(const double* y, double* buf, double& acc0, double& acc1) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < RG; ++k) g[k] = 0.0;
-    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
-    for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
-        double w[RP], y[RP];
-#pragma unroll
-        for (int c = 0; c < RP; ++c) w[c] = (c < p) ? W[(int64_t)c * ldw + r] : 0.0;
-#pragma unroll
-        for (int c = 0; c < RP; ++c) {
+    for (int c = 0; c < RP; ++c) buf[lane * RP + c] = y[c];
+    __syncwarp();
+    // upper-triangle entry k -> (c1, c2)
+    for (int q = 0; q < 2; ++q) {
+        const int kk = lane + 32 * q;
+        if (kk < RG) {
+            int c1 = 0, rem = kk;
+            while (rem >= RP - c1) { rem -= RP - c1; ++c1; }
+            const int c2 = c1 + rem;
             double s = 0.0;
-#pragma unroll
-            for (int a = 0; a <= c; ++a) s = fma(w[a], Ri[a * RP + c], s);
-            y[c] = s;
-            if (c < p) out[(int64_t)c * ldo + r] = s;
-        }
-        if (gram) {
-            int k = 0;
-#pragma unroll
-            for (int c1 = 0; c1 < RP; ++c1)
-#pragma unroll
-                for (int c2 = c1; c2 < RP; ++c2) {
-                    g[k] = fma(y[c1], y[c2], g[k]);
-                    ++k;
-                }
+#pragma unroll 8
+            for (int rr = 0; rr < 32; ++rr) s = fma(buf[rr * RP + c1], buf[rr * RP + c2], s);
+            if (q == 0) acc0 += s;
+            else acc1 += s;
         }
     }
-    if (!gram) return;
+    __syncwarp();
+}
+
+// The CTA's Gram partial (p x p layout, upper triangle; lower = 0) from the per-lane
+// accumulators of warp_gram_rows.
+__device__ inline void cta_gram_write(double acc0, double acc1, int p, double (*red)[RG],
+                                      double* __restrict__ part) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < RG; ++k) {
-        const double v = warp_sum(g[k]);
-        if (lane == 0) red[wid][k] = v;
-    }
+    red[wid][lane] = acc0;
+    if (lane + 32 < RG) red[wid][lane + 32] = acc1;
     __syncthreads();
-    // partial in the p x p layout the Cholesky kernel reads (upper triangle; lower = 0)
     for (int o = threadIdx.x; o < p * p; o += blockDim.x) {
         const int c1 = o / p, c2 = o % p;
         double s = 0.0;
@@ -471,6 +458,40 @@ __global__ void __launch_bounds__(NT) k_trsm_rows(const double* __restrict__ W, 
         }
         part[(int64_t)blockIdx.x * p * p + o] = s;
     }
+}
+
+__global__ void __launch_bounds__(NT) k_trsm_rows(const double* __restrict__ W, int64_t ldw, int p,
+                                                  int64_t n, int64_t rpb, const double* __restrict__ Rinv,
+                                                  double* __restrict__ out, int64_t ldo,
+                                                  double* __restrict__ part, int gram) {
+    __shared__ double Ri[RP * RP];
+    __shared__ double red[NT / 32][RG];
+    __shared__ double buf[NT / 32][32 * RP];
+    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+        const int a = e / RP, c = e % RP;
+        Ri[e] = (a < p && c < p) ? Rinv[a * p + c] : 0.0;
+    }
+    __syncthreads();
+    double acc0 = 0.0, acc1 = 0.0;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    // whole warps step through the rows together (rows past the end contribute zeros)
+    for (int64_t r0 = rb + (threadIdx.x & ~31); r0 < re; r0 += blockDim.x) {
+        const int64_t r = r0 + (threadIdx.x & 31);
+        const bool ok = r < re;
+        double w[RP], y[RP];
+#pragma unroll
+        for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
+#pragma unroll
+        for (int c = 0; c < RP; ++c) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a <= c; ++a) s = fma(w[a], Ri[a * RP + c], s);
+            y[c] = s;
+            if (ok && c < p) out[(int64_t)c * ldo + r] = s;
+        }
+        if (gram) warp_gram_rows(y, buf[threadIdx.x >> 5], acc0, acc1);
+    }
+    if (gram) cta_gram_write(acc0, acc1, p, red, part);
 }
 
 // Row-per-thread, p <= 8: W <- W - V h (FP64, the Arnoldi relation stays exact) and the
@@ -487,47 +508,27 @@ __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restric
         hs[e] = (c < p) ? h[a * p + c] : 0.0;
     }
     __syncthreads();
-    double g[RG];
-#pragma unroll
-    for (int k = 0; k < RG; ++k) g[k] = 0.0;
+    __shared__ double buf[NT / 32][32 * RP];
+    double acc0 = 0.0, acc1 = 0.0;
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
-    for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
+    for (int64_t r0 = rb + (threadIdx.x & ~31); r0 < re; r0 += blockDim.x) {
+        const int64_t r = r0 + (threadIdx.x & 31);
+        const bool ok = r < re;
         double w[RP];
 #pragma unroll
-        for (int c = 0; c < RP; ++c) w[c] = (c < p) ? W[(int64_t)c * ldw + r] : 0.0;
-        for (int a = 0; a < cols; ++a) {
-            const double v = V[(int64_t)a * ldv + r];
+        for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
+        if (ok)
+            for (int a = 0; a < cols; ++a) {
+                const double v = V[(int64_t)a * ldv + r];
 #pragma unroll
-            for (int c = 0; c < RP; ++c) w[c] = fma(-v, hs[a * RP + c], w[c]);
-        }
+                for (int c = 0; c < RP; ++c) w[c] = fma(-v, hs[a * RP + c], w[c]);
+            }
 #pragma unroll
         for (int c = 0; c < RP; ++c)
-            if (c < p) W[(int64_t)c * ldw + r] = w[c];
-        int k = 0;
-#pragma unroll
-        for (int c1 = 0; c1 < RP; ++c1)
-#pragma unroll
-            for (int c2 = c1; c2 < RP; ++c2) {
-                g[k] = fma(w[c1], w[c2], g[k]);
-                ++k;
-            }
+            if (ok && c < p) W[(int64_t)c * ldw + r] = w[c];
+        warp_gram_rows(w, buf[threadIdx.x >> 5], acc0, acc1);
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < RG; ++k) {
-        const double v = warp_sum(g[k]);
-        if (lane == 0) red[wid][k] = v;
-    }
-    __syncthreads();
-    for (int o = threadIdx.x; o < p * p; o += blockDim.x) {
-        const int c1 = o / p, c2 = o % p;
-        double s = 0.0;
-        if (c1 <= c2) {
-            const int k = c1 * RP - c1 * (c1 - 1) / 2 + (c2 - c1);
-            for (int w_ = 0; w_ < NT / 32; ++w_) s += red[w_][k];
-        }
-        part[(int64_t)blockIdx.x * p * p + o] = s;
-    }
+    cta_gram_write(acc0, acc1, p, red, part);
 }
 
 // Row-per-thread, p <= 8: Z[r, :] += V[r, 0:cols] Wc; restart copy V[r, 0:p] <- V[r, cols-p:cols].

@@ -36,9 +36,9 @@ __device__ inline void cmsub(cplx& x, cplx a, cplx b) {
 }
 
 constexpr size_t kSmemLimit = 200 * 1024;
-constexpr int kPoleThreads = 128;
+constexpr int kPoleThreads = 32;    // one warp per pole: warp-synchronous, no block barriers
 
-// One CTA (four warps) per pole.  Shared memory holds M (mp x mp complex), the right-hand
+// One CTA (one warp) per pole.  Shared memory holds M (mp x mp complex), the right-hand
 // sides / solution X (mp x p complex) and, when it fits, the real H~ ((mp+p) x mp), staged
 // once with coalesced loads.  Outputs: the restart factor S_i, ||S_i||_F, and
 // Y_i = 2 Re(omega_i Z_i) (mp x p real).  Since H~ is real,
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
     const int ldr = h_in_smem ? rows : ldH;
     if (h_in_smem)
         for (int e = tid; e < rows * mp; e += nt) Hs[e] = H[(int64_t)(e / rows) * ldH + (e % rows)];
-    __syncthreads();
+    __syncwarp();
     // Algorithm 2: M = I - tau H_m (eq. (3236)); Algorithm 1: M = H_m - tau I (eq. (3.3));
     // row-major.  X = E_1 S_i.
     for (int e = tid; e < mp * mp; e += nt) {
@@ -83,21 +83,30 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
         const int r = e / p, c = e % p;
         X[e] = (r < p) ? Si[r * p + c] : cplx{0.0, 0.0};
     }
-    __syncthreads();
+    __syncwarp();
     // elimination with partial pivoting inside the band (rows j..j+p of column j)
     for (int j = 0; j < mp; ++j) {
         const int jmax = min(j + p, mp - 1);
-        if (tid == 0) {
+        // pivot: warp arg-max of |M[r][j]|^2 over r = j..jmax (ties -> smallest r)
+        {
+            double best = -1.0;
             int piv = j;
-            double best = cabs2(M[(size_t)j * mp + j]);
-            for (int r = j + 1; r <= jmax; ++r) {
+            for (int r = j + tid; r <= jmax; r += 32) {
                 const double v = cabs2(M[(size_t)r * mp + j]);
                 if (v > best) { best = v; piv = r; }
             }
-            if (!(best > 0.0)) atomicOr(&flags[0], 2);
-            piv_s = piv;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int op = __shfl_xor_sync(0xffffffffu, piv, o);
+                if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+            }
+            if (tid == 0) {
+                if (!(best > 0.0)) atomicOr(&flags[0], 2);
+                piv_s = piv;
+            }
         }
-        __syncthreads();
+        __syncwarp();
         const int piv = piv_s;
         if (piv != j) {
             for (int k = j + tid; k < mp; k += nt) {
@@ -110,11 +119,11 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
                 X[(size_t)j * p + c] = X[(size_t)piv * p + c];
                 X[(size_t)piv * p + c] = a;
             }
-            __syncthreads();
+            __syncwarp();
         }
         const int nr = jmax - j;
         if (tid < nr) f[tid] = cdiv(M[(size_t)(j + 1 + tid) * mp + j], M[(size_t)j * mp + j]);
-        __syncthreads();
+        __syncwarp();
         const int ncM = mp - j - 1, w = ncM + p;
         for (int rr = 0; rr < nr; ++rr) {
             const int r = j + 1 + rr;
@@ -129,18 +138,18 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
                 }
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
     // back substitution on the upper triangle; thread -> (row offset, column) fixed
     const int bc = tid % p, br0 = tid / p, brs = nt / p;
     for (int j = mp - 1; j >= 0; --j) {
         if (tid < p) X[(size_t)j * p + tid] = cdiv(X[(size_t)j * p + tid], M[(size_t)j * mp + j]);
-        __syncthreads();
+        __syncwarp();
         if (br0 < brs) {
             const cplx xj = X[(size_t)j * p + bc];
             for (int r = br0; r < j; r += brs) cmsub(X[(size_t)r * p + bc], M[(size_t)r * mp + j], xj);
         }
-        __syncthreads();
+        __syncwarp();
     }
     // S_i and its Frobenius norm.  Algorithm 2: tau H_{m+1,m} E_m^T Z_i (eq. (49));
     // Algorithm 1: -H_{m+1,m} E_m^T Z_i (eq. (35)).
@@ -159,10 +168,10 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
         ss += cabs2(snew);
     }
     red[tid] = ss;
-    __syncthreads();
+    __syncwarp();
     for (int st = nt / 2; st > 0; st >>= 1) {
         if (tid < st) red[tid] += red[tid + st];
-        __syncthreads();
+        __syncwarp();
     }
     if (tid == 0) {
         res[i] = sqrt(red[0]);
