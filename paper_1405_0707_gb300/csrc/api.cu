@@ -83,16 +83,20 @@ expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, 
     const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * std::ldexp(1.0, -53);
     int* flags = flags_of(P->stat);
     if (!gram_done) LAUNCH(EXPM_STAGE_QR, launch_proj_partial(P->W, ld, p, P->W, ld, p, n, P->part, P->nblk, s));
+    double* Hq = withH ? P->H : nullptr;
+    const int* extra = flags + 2;
+    // pass 1: unshifted Cholesky, shifted when W is ill-conditioned (sets the third-pass flag)
     LAUNCH(EXPM_STAGE_QR, launch_chol(P->part, P->nblk, p, shift, sm(P, kOffR), sm(P, kOffRi),
-                                      sm(P, kOffRt), 1, nullptr, 0, 0, 0, normsq, flags, s));
-    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, s));
+                                      sm(P, kOffRt), 0, Hq, P->ldH, hrow, hcol, normsq, flags, s));
+    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, extra, 0, s));
+    // pass 2: the last one for a well-conditioned block (writes the final block directly)
     LAUNCH(EXPM_STAGE_QR, launch_chol(P->part, P->nblk, p, 0.0, sm(P, kOffR), sm(P, kOffRi),
-                                      sm(P, kOffRt), 0, nullptr, 0, 0, 0, nullptr, flags, s));
-    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), P->W, ld, P->part, P->nblk, 1, s));
+                                      sm(P, kOffRt), 1, Hq, P->ldH, hrow, hcol, nullptr, flags, s));
+    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), out, ldo, P->part, P->nblk, 1, extra, 1, s));
+    // pass 3: only when pass 1 needed the shift (no-op otherwise)
     LAUNCH(EXPM_STAGE_QR, launch_chol(P->part, P->nblk, p, 0.0, sm(P, kOffR), sm(P, kOffRi),
-                                      sm(P, kOffRt), 0, withH ? P->H : nullptr, P->ldH, hrow, hcol,
-                                      nullptr, flags, s));
-    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), out, ldo, nullptr, P->nblk, 0, s));
+                                      sm(P, kOffRt), 2, Hq, P->ldH, hrow, hcol, nullptr, flags, s));
+    LAUNCH(EXPM_STAGE_QR, launch_trsm(P->W, ld, p, n, sm(P, kOffRi), out, ldo, nullptr, P->nblk, 0, extra, 2, s));
     return EXPM_OK;
 }
 

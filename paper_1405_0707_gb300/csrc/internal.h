@@ -147,12 +147,14 @@ cudaError_t launch_reduce_h(const double* part, int nblk, int cols, int p, doubl
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
                                int p, int64_t n, const double* h, double* part, int nblk,
                                int gram, cudaStream_t s, int f32 = 0);
+// Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
+// third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,
-                        double* Rinv, double* Rtot, int first, double* H, int ldH, int hrow,
+                        double* Rinv, double* Rtot, int mode, double* H, int ldH, int hrow,
                         int hcol, double* normsq_out, int* flags, cudaStream_t s);
 cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* Rinv,
                         double* out, int64_t ldo, double* part, int nblk, int gram,
-                        cudaStream_t s);
+                        const int* extra, int tmode, cudaStream_t s);
 // projected solves / update
 cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          const double* tau_re, const double* tau_im, const double* om_re,

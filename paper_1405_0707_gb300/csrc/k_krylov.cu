@@ -34,6 +34,23 @@ __device__ inline void load_tile(const double* __restrict__ X, int64_t ld, int c
     }
 }
 
+// Destination, Gram and skip of a triangular-solve pass (see k_chol's pass modes):
+// tmode 0: write `out` (gram as asked); tmode 1: a third pass follows iff extra -> in place
+// with Gram, else the final block `out`; tmode 2: only if extra, into `out`.
+struct TrsmPass {
+    double* dest;
+    int64_t ldd;
+    int gram;
+    bool skip;
+};
+__device__ inline TrsmPass trsm_pass(double* W, int64_t ldw, double* out, int64_t ldo, int gram,
+                                     const int* extra, int tmode) {
+    if (tmode == 0) return {out, ldo, gram, false};
+    const int ex = *extra;
+    if (tmode == 1) return ex ? TrsmPass{W, ldw, 1, false} : TrsmPass{out, ldo, 0, false};
+    return {out, ldo, 0, ex == 0};
+}
+
 // Gram partial of a TR x p tile X (row-major X[rr * p + c]), upper triangle only (the
 // Cholesky factorisation reads nothing else).  With p^2 <= NT every output gets NT / p^2
 // threads that take every (NT / p^2)-th row, so the dependent chains are short; gram_write
@@ -245,20 +262,30 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
     }
 }
 
-// One warp: G = sum of the p x p partials (+ shift_rel * trace on the first pass),
-// upper Cholesky G = R^T R, R^{-1}, Rtot = R Rtot (Rtot = R on the first pass).  The last
-// pass writes Rtot into H (rows hrow.., cols hcol..) and checks for breakdown against the
-// column norms of W before orthogonalisation (H column above + Rtot column).
+// Cholesky-QR factor step, one CTA.  G = sum of the p x p partials (all CHOL_T threads),
+// then one warp factorises.  Pass modes (the QR of a block runs 3 passes, the third only
+// when needed; the decision is made on the device so a captured graph stays valid):
+//   mode 0: unshifted Cholesky of G; if a pivot is not positive or the smallest pivot is
+//           below 1e-10 of the largest diagonal entry (kappa(W) above ~1e5) it is redone
+//           with the shift shift_rel * trace(G) and extra[0] = 1 requests a third pass,
+//           else extra[0] = 0.  Rtot = R.
+//   mode 1: Rtot = R Rtot; the last pass when extra[0] == 0.
+//   mode 2: returns at once when extra[0] == 0; else Rtot = R Rtot, the last pass.
+// The last pass writes Rtot into H (rows hrow.., cols hcol..) when H is given and checks
+// for breakdown against the column norms of W before orthogonalisation.
 constexpr int CHOL_T = 1024;
 __global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part, int nblk, int p,
-                                              double shift_rel, double* R, double* Rinv,
-                                              double* Rtot, int first, double* H, int ldH,
-                                              int hrow, int hcol, double* normsq_out, int* flags) {
-    __shared__ double G[kMaxP * kMaxP], Rs[kMaxP * kMaxP], Ri[kMaxP * kMaxP], Rt[kMaxP * kMaxP];
+                                                 double shift_rel, double* R, double* Rinv,
+                                                 double* Rtot, int mode, double* H, int ldH,
+                                                 int hrow, int hcol, double* normsq_out, int* flags) {
+    int* extra = flags + 2;
+    if (mode == 2 && *extra == 0) return;
+    __shared__ double G[kMaxP * kMaxP], G0[kMaxP * kMaxP], Rs[kMaxP * kMaxP], Ri[kMaxP * kMaxP],
+        Rt[kMaxP * kMaxP];
     __shared__ double red[CHOL_T];
-    __shared__ int bad;
+    __shared__ double rdiag[kMaxP];
+    __shared__ int bad, ill;
     const int pp = p * p;
-    // G = sum of the partial Gram matrices: every output split over CHOL_T / pp stripes
     {
         const int stripes = pp >= CHOL_T ? 1 : CHOL_T / pp;
         for (int base = 0; base < pp; base += CHOL_T / stripes) {
@@ -269,16 +296,14 @@ __global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part
             if (st == 0 && o < pp) {
                 double s = 0.0;
                 for (int k = 0; k < stripes; ++k) s += red[k * (CHOL_T / stripes) + ol];
-                G[o] = s;
-                Rs[o] = 0.0;
-                Ri[o] = 0.0;
+                G0[o] = s;
             }
             __syncthreads();
         }
     }
-    // squared norms of the H columns above row hrow (for the breakdown test), all threads
+    const bool last = (mode == 1 && *extra == 0) || mode == 2;
     __shared__ double hn2[kMaxP];
-    if (H) {
+    if (H && last) {
         const int stripes = CHOL_T / p;
         const int c = threadIdx.x % p, st = threadIdx.x / p;
         double v2 = 0.0;
@@ -298,38 +323,55 @@ __global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part
     }
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
-    if (lane == 0) bad = 0;
-    __syncwarp();
-    double tr = 0.0;
-    for (int c = 0; c < p; ++c) tr += G[c * p + c];
-    if (normsq_out && lane == 0) *normsq_out = tr;
-    if (first && lane < p) G[lane * p + lane] += shift_rel * tr;
-    __syncwarp();
-    // right-looking upper Cholesky on G (row-major, upper part used)
-    for (int j = 0; j < p; ++j) {
-        if (lane == 0) {
-            double d = G[j * p + j];
-            if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
-            Rs[j * p + j] = sqrt(d);
+    if (lane == 0) { bad = 0; ill = 0; }
+    double tr = 0.0, dmax = 0.0;
+    for (int c = 0; c < p; ++c) {
+        tr += G0[c * p + c];
+        dmax = fmax(dmax, G0[c * p + c]);
+    }
+    if (normsq_out && lane == 0 && mode == 0) *normsq_out = tr;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const double shift = (attempt == 1) ? shift_rel * tr : 0.0;
+        for (int o = lane; o < pp; o += 32) {
+            G[o] = G0[o] + ((o / p == o % p) ? shift : 0.0);
+            Rs[o] = 0.0;
+            Ri[o] = 0.0;
         }
         __syncwarp();
-        const double inv = 1.0 / Rs[j * p + j];
-        if (lane > j && lane < p) Rs[j * p + lane] = G[j * p + lane] * inv;
-        __syncwarp();
-        if (lane > j && lane < p) {
-            const double rb = Rs[j * p + lane];
-            for (int a = j + 1; a <= lane; ++a) G[a * p + lane] -= Rs[j * p + a] * rb;
+        // right-looking upper Cholesky G = R^T R (upper part), one reciprocal per pivot
+        for (int j = 0; j < p; ++j) {
+            if (lane == 0) {
+                double d = G[j * p + j];
+                if (!(d > 0.0) || !isfinite(d) || (mode == 0 && attempt == 0 && d < 1e-10 * dmax)) ill = 1;
+                if (!(d > 0.0) || !isfinite(d)) d = 1.0;
+                const double rj = sqrt(d);
+                Rs[j * p + j] = rj;
+                rdiag[j] = 1.0 / rj;
+            }
+            __syncwarp();
+            const double inv = rdiag[j];
+            if (lane > j && lane < p) Rs[j * p + lane] = G[j * p + lane] * inv;
+            __syncwarp();
+            if (lane > j && lane < p) {
+                const double rb = Rs[j * p + lane];
+                for (int a = j + 1; a <= lane; ++a) G[a * p + lane] -= Rs[j * p + a] * rb;
+            }
+            __syncwarp();
         }
+        if (mode != 0 || attempt == 1 || !ill) break;   // mode 0 retries with the shift
         __syncwarp();
     }
-    // inverse of the upper triangular R, column `lane`
+    if (mode == 0 && lane == 0) *extra = ill;
+    if (mode != 0 && lane == 0 && ill) bad = 1;       // a later pass must factor cleanly
+    __syncwarp();
+    // inverse of the upper triangular R, column `lane` (reciprocal pivots, no division)
     if (lane < p) {
         const int c = lane;
-        Ri[c * p + c] = 1.0 / Rs[c * p + c];
+        Ri[c * p + c] = rdiag[c];
         for (int r = c - 1; r >= 0; --r) {
             double s = 0.0;
-            for (int k = r + 1; k <= c; ++k) s += Rs[r * p + k] * Ri[k * p + c];
-            Ri[r * p + c] = -s / Rs[r * p + r];
+            for (int k = r + 1; k <= c; ++k) s = fma(Rs[r * p + k], Ri[k * p + c], s);
+            Ri[r * p + c] = -s * rdiag[r];
         }
     }
     __syncwarp();
@@ -338,10 +380,10 @@ __global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part
         const int c = lane;
         for (int r = 0; r < p; ++r) {
             double s;
-            if (first) s = Rs[r * p + c];
+            if (mode == 0) s = Rs[r * p + c];
             else {
                 s = 0.0;
-                for (int k = r; k <= c; ++k) s += Rs[r * p + k] * Rtot[k * p + c];
+                for (int k = r; k <= c; ++k) s = fma(Rs[r * p + k], Rtot[k * p + c], s);
             }
             Rt[r * p + c] = (r <= c) ? s : 0.0;
         }
@@ -354,7 +396,7 @@ __global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part
         if (!isfinite(Rt[o])) bad = 1;
     }
     __syncwarp();
-    if (H) {
+    if (H && last) {
         for (int o = lane; o < pp; o += 32) {
             const int a = o / p, c = o % p;
             H[(int64_t)(hcol + c) * ldH + hrow + a] = Rt[o];
@@ -372,10 +414,16 @@ __global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part
 
 // W_out = W R^{-1} (row by row); gram: also partial of W_out^T W_out.
 template <int OPT>
-__global__ void __launch_bounds__(NT) k_trsm(double* __restrict__ W, int64_t ldw, int p, int64_t n,
+__global__ void __launch_bounds__(NT) k_trsm(double* W, int64_t ldw, int p, int64_t n,
                                              int64_t rpb, const double* __restrict__ Rinv,
-                                             double* __restrict__ out, int64_t ldo,
-                                             double* __restrict__ part, int gram) {
+                                             double* out_, int64_t ldo_,
+                                             double* __restrict__ part, int gram_,
+                                             const int* extra, int tmode) {
+    const TrsmPass ps = trsm_pass(W, ldw, out_, ldo_, gram_, extra, tmode);
+    if (ps.skip) return;
+    double* out = ps.dest;
+    const int64_t ldo = ps.ldd;
+    const int gram = ps.gram;
     __shared__ double Ri[kMaxP * kMaxP];
     __shared__ double Ws[TR * kMaxP], Wn[TR * kMaxP];
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ri[e] = Rinv[e];
@@ -460,10 +508,16 @@ __device__ inline void cta_gram_write(double acc0, double acc1, int p, double (*
     }
 }
 
-__global__ void __launch_bounds__(NT) k_trsm_rows(const double* __restrict__ W, int64_t ldw, int p,
+__global__ void __launch_bounds__(NT) k_trsm_rows(double* W, int64_t ldw, int p,
                                                   int64_t n, int64_t rpb, const double* __restrict__ Rinv,
-                                                  double* __restrict__ out, int64_t ldo,
-                                                  double* __restrict__ part, int gram) {
+                                                  double* out_, int64_t ldo_,
+                                                  double* __restrict__ part, int gram_,
+                                                  const int* extra, int tmode) {
+    const TrsmPass ps = trsm_pass(W, ldw, out_, ldo_, gram_, extra, tmode);
+    if (ps.skip) return;
+    double* out = ps.dest;
+    const int64_t ldo = ps.ldd;
+    const int gram = ps.gram;
     __shared__ double Ri[RP * RP];
     __shared__ double red[NT / 32][RG];
     __shared__ double buf[NT / 32][32 * RP];
@@ -698,23 +752,24 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
 }
 
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,
-                        double* Rinv, double* Rtot, int first, double* H, int ldH, int hrow,
+                        double* Rinv, double* Rtot, int mode, double* H, int ldH, int hrow,
                         int hcol, double* normsq_out, int* flags, cudaStream_t s) {
-    k_chol<<<1, CHOL_T, 0, s>>>(part, nblk, p, shift_rel, R, Rinv, Rtot, first, H, ldH, hrow, hcol,
+    k_chol<<<1, CHOL_T, 0, s>>>(part, nblk, p, shift_rel, R, Rinv, Rtot, mode, H, ldH, hrow, hcol,
                                 normsq_out, flags);
     return cudaGetLastError();
 }
 
 cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* Rinv,
                         double* out, int64_t ldo, double* part, int nblk, int gram,
-                        cudaStream_t s) {
+                        const int* extra, int tmode, cudaStream_t s) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
     if (p <= RP) {
-        k_trsm_rows<<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram);
+        k_trsm_rows<<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram, extra, tmode);
         return cudaGetLastError();
     }
-    EXPM_OPT_DISPATCH(p * p, (k_trsm<O><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram)));
+    EXPM_OPT_DISPATCH(p * p, (k_trsm<O><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram,
+                                                       extra, tmode)));
     return cudaGetLastError();
 }
 

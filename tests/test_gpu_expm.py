@@ -141,3 +141,21 @@ def test_auto_selection_follows_norm_ratio(tab):
         assert info.algorithm == (2 if bound >= 50 * taumax else 1)
         ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
         assert info.converged == 1 and rel(to_np(Zg), ref) < 1e-9, (t, rel(to_np(Zg), ref))
+
+
+def test_nearly_dependent_rhs_takes_the_shifted_qr_pass(tab):
+    """kappa(B) ~ 1e7: the first Cholesky-QR pass is ill-conditioned, the shifted pass and
+    the third pass run; the result must still match the closed form."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    sides, diff, vel, t = (41, 35), 0.1, (1.0, 1.0), 1.0
+    n = 41 * 35
+    rng = np.random.default_rng(12)
+    b = rng.standard_normal((n, 3))
+    B = np.column_stack([b[:, 0], b[:, 1], b[:, 0] + 1e-7 * b[:, 2]])
+    assert np.linalg.cond(B) > 1e6
+    plan = Plan(sides, diff, vel, p_max=3, m=6, tol=1e-12, max_cycles=200)
+    Zg, info = plan.expm_block(t, to_dev(B))
+    ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+    assert info.converged == 1
+    assert rel(to_np(Zg), ref) < 1e-9
