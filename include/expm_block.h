@@ -96,6 +96,8 @@ typedef struct {
     int32_t precision;     /* expm_precision                                         */
     int32_t fixed_cycles;  /* > 0: run exactly this many cycles, ignoring tol        */
     int32_t algorithm;     /* expm_algorithm                                         */
+    int32_t certify;       /* 1: also accumulate every pole's X_i and report the true
+                              FP64 residuals ||B - (tA - tau_i I) X_i||_F (eq. (3))   */
 } expm_opts;
 
 #define EXPM_MAX_POLES 16
@@ -111,6 +113,7 @@ typedef struct {
     double  normB;               /* ||B||_F                                          */
     int32_t algorithm;           /* 1 or 2: the algorithm that ran                   */
     double  normA_bound;         /* Gershgorin bound of ||tA|| used by AUTO          */
+    double  true_resid[EXPM_MAX_POLES]; /* certify: ||B - (tA - tau_i I) X_i||_F in FP64 */
 } expm_info;
 
 typedef struct expm_plan_s expm_plan;

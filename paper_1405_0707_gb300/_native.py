@@ -41,14 +41,16 @@ class expm_op_desc(C.Structure):
 
 class expm_opts(C.Structure):
     _fields_ = [("m", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double),
-                ("precision", C.c_int32), ("fixed_cycles", C.c_int32), ("algorithm", C.c_int32)]
+                ("precision", C.c_int32), ("fixed_cycles", C.c_int32), ("algorithm", C.c_int32),
+                ("certify", C.c_int32)]
 
 
 class expm_info(C.Structure):
     _fields_ = [("cycles", C.c_int32), ("block_steps", C.c_int32), ("matvecs", C.c_int64),
                 ("converged", C.c_int32), ("breakdown", C.c_int32), ("npoles", C.c_int32),
                 ("resid", C.c_double * EXPM_MAX_POLES), ("normB", C.c_double),
-                ("algorithm", C.c_int32), ("normA_bound", C.c_double)]
+                ("algorithm", C.c_int32), ("normA_bound", C.c_double),
+                ("true_resid", C.c_double * EXPM_MAX_POLES)]
 
 
 _lib = None

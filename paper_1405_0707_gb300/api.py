@@ -37,7 +37,7 @@ class Plan:
     """A plan for tA = t (diff Laplacian_h - vel . grad_h) on a 1/2/3-D grid (x fastest)."""
 
     def __init__(self, sides, diff, vel, p_max, m=10, tol=1e-10, max_cycles=200,
-                 fixed_cycles=0, stream=None, algorithm=0, precision="fp64"):
+                 fixed_cycles=0, stream=None, algorithm=0, precision="fp64", certify=False):
         import torch
         sides = tuple(int(s) for s in sides)
         vel = tuple(float(v) for v in vel)
@@ -55,6 +55,7 @@ class Plan:
         opts.precision = {"fp64": N.EXPM_PREC_FP64, "mixed": N.EXPM_PREC_MIXED}[precision]
         opts.fixed_cycles = int(fixed_cycles)
         opts.algorithm = int(algorithm)        # 0 auto, 1 SBFOM (Algorithm 1), 2 PSBFOM (Algorithm 2)
+        opts.certify = 1 if certify else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
         self.n = 1

@@ -250,8 +250,15 @@ expm_status issue_cycle(expm_plan* P, double t, int p, int alg) {
     double* tau_re = sm(P, kOffTau);
     LAUNCH(EXPM_STAGE_POLES, launch_poles(P->H, P->ldH, mp, p, P->npoles, tau_re, tau_re + EXPM_MAX_POLES,
                                           tau_re + 2 * EXPM_MAX_POLES, tau_re + 3 * EXPM_MAX_POLES,
-                                          P->S, P->poles, P->Wc_slots, P->stat, flags_of(P->stat), alg, s));
+                                          P->S, P->poles, P->Wc_slots, P->stat, flags_of(P->stat), alg, s,
+                                          P->opts.certify ? P->Zcert : nullptr));
     LAUNCH(EXPM_STAGE_POLES, launch_combine2(P->H, P->ldH, mp, p, P->npoles, P->Wc_slots, sm(P, kOffWc), alg, s));
+    if (P->opts.certify) {
+        // every pole's X_i (real and imaginary columns) += V_{m+1} C, before the restart copy
+        LAUNCH(EXPM_STAGE_OTHER, launch_certify_coeffs(P->H, P->ldH, mp, p, P->npoles, P->Zcert, P->Ccert, alg, s));
+        LAUNCH(EXPM_STAGE_OTHER, launch_update_z(P->V, ld, mp + p, 2 * P->npoles * p, n, P->Ccert, P->Xcert, ld, 0,
+                                                 s, P->nblk));
+    }
     LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk));
     CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
     return EXPM_OK;
@@ -309,6 +316,7 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
     CK(cudaMemsetAsync(P->stat, 0, sizeof(double) * kStatDoubles, s));
     CK(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)P->ldH * m * P->p_max, s));
     LAUNCH(EXPM_STAGE_OTHER, launch_zero(P->Zacc, ld, n, p, s));
+    if (P->opts.certify) LAUNCH(EXPM_STAGE_OTHER, launch_zero(P->Xcert, ld, n, 2 * P->npoles * p, s));
     // Steps 1-2: R_i^0 = B = V_1 R for every pole
     LAUNCH(EXPM_STAGE_OTHER, launch_copy(dB, ldb, P->W, ld, n, p, s));
     expm_status st = qr_block(P, p, P->V, ld, false, 0, 0, P->stat + 16, false);
@@ -346,6 +354,22 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
     }
     // Z = omega_0 B + Z_acc
     LAUNCH(EXPM_STAGE_OTHER, launch_axpby(P->omega0, dB, ldb, 1.0, P->Zacc, ld, dZ, ldz, n, p, s));
+    double true_res[EXPM_MAX_POLES] = {0};
+    if (P->opts.certify) {
+        // the true FP64 residuals ||B - (tA - tau_i I) X_i||_F of every pole (eq. (3))
+        double* tau = sm(P, kOffTau);
+        LAUNCH(EXPM_STAGE_OTHER, launch_true_resid(P->Xcert, ld, dB, ldb, p, P->npoles, P->ndim, P->ax[0].N,
+                                                   P->ax[1].N, P->ax[2].N, P->ax, t, tau, tau + EXPM_MAX_POLES,
+                                                   P->rcert, s));
+        const int nb = true_resid_blocks(n);
+        CK(cudaMemcpyAsync(P->hcert, P->rcert, sizeof(double) * (size_t)P->npoles * nb, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < P->npoles; ++i) {
+            double s2 = 0.0;
+            for (int b = 0; b < nb; ++b) s2 += P->hcert[(size_t)i * nb + b];
+            true_res[i] = std::sqrt(s2);
+        }
+    }
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->cycles = cycles;
@@ -357,6 +381,7 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
         info->normB = normB;
         info->algorithm = alg;
         info->normA_bound = norm_bound(P, t);
+        for (int i = 0; i < P->npoles; ++i) info->true_resid[i] = true_res[i];
     }
     if (result != EXPM_OK) return result;
     if (P->opts.fixed_cycles > 0) return EXPM_OK;
@@ -388,6 +413,11 @@ void free_plan(expm_plan* P) {
     cudaFree(P->Zacc);
     cudaFree(P->Bst);
     cudaFree(P->Zst);
+    cudaFree(P->Xcert);
+    cudaFree(P->Zcert);
+    cudaFree(P->Ccert);
+    cudaFree(P->rcert);
+    delete[] P->hcert;
     cudaFree(P->H);
     cudaFree(P->part);
     cudaFree(P->small);
@@ -531,6 +561,14 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     ok = ok && dalloc(&P->S, (size_t)P->npoles * p_max * p_max * 2);
     ok = ok && dalloc(&P->Wc_slots, (size_t)P->npoles * (mpm + p_max) * p_max);
     ok = ok && dalloc(&P->stat, kStatDoubles);
+    if (opts->certify) {
+        const size_t w = 2 * (size_t)P->npoles * p_max, rows = (size_t)mpm + p_max;
+        if (8 * (rows * w + 16 * (rows | 1)) > 225 * 1024) { free_plan(P); return EXPM_INVALID_ARG; }
+        ok = ok && dalloc(&P->Xcert, (size_t)ld * w) && dalloc(&P->Zcert, (size_t)P->npoles * mpm * p_max * 2) &&
+             dalloc(&P->Ccert, rows * w) && dalloc(&P->rcert, (size_t)P->npoles * true_resid_blocks(n));
+        P->hcert = new (std::nothrow) double[(size_t)P->npoles * true_resid_blocks(n)];
+        ok = ok && P->hcert != nullptr;
+    }
     if (poles_smem_bytes(mpm, p_max) == 0)   // elimination does not fit in shared memory
         ok = ok && dalloc(&P->poles, (size_t)P->npoles * ((size_t)mpm * mpm + (size_t)mpm * p_max) * 2);
     ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hpin), sizeof(double) * kStatDoubles) == cudaSuccess;

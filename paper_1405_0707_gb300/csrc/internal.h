@@ -103,6 +103,12 @@ struct expm_plan_s {
     double* stat = nullptr;    // device status block: res[16], normsq, flags (ints)
     double* hpin = nullptr;    // pinned host mirror of stat
     double* Zst = nullptr;     // ld x p_max staging for the host entry point
+    // certify mode: per-pole solutions (real/imag columns), Z_i, coefficient matrix, partials
+    double* Xcert = nullptr;   // ld x 2 npoles p_max
+    double* Zcert = nullptr;   // npoles x m p_max x p_max complex
+    double* Ccert = nullptr;   // ((m+1) p_max) x 2 npoles p_max
+    double* rcert = nullptr;   // npoles x true_resid_blocks(n)
+    double* hcert = nullptr;   // host copy of rcert
     // profiling: launch counts always, event timing when enabled
     bool prof = false;
     int64_t launches = 0;
@@ -159,7 +165,13 @@ cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* 
 cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          const double* tau_re, const double* tau_im, const double* om_re,
                          const double* om_im, double* S, double* work, double* Wc_slots,
-                         double* res, int* flags, int alg, cudaStream_t s);
+                         double* res, int* flags, int alg, cudaStream_t s, double* Zout = nullptr);
+cudaError_t launch_certify_coeffs(const double* H, int ldH, int mp, int p, int npoles, const double* Zs,
+                                  double* C, int alg, cudaStream_t s);
+int true_resid_blocks(int64_t n);
+cudaError_t launch_true_resid(const double* X, int64_t ldx, const double* B, int64_t ldb, int p, int npoles,
+                              int ndim, int nx, int ny, int nz, const Axis* ax, double t, const double* tau_re,
+                              const double* tau_im, double* part, cudaStream_t s);
 cudaError_t launch_combine(const double* Wc_slots, int npoles, int rows, int p, double* Wc,
                            cudaStream_t s);
 cudaError_t launch_combine2(const double* H, int ldH, int mp, int p, int npoles,

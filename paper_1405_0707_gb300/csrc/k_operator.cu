@@ -272,6 +272,59 @@ __global__ void k_tridiag_lines32(float* y_io, int64_t ld, int p, int L, int64_t
     thomas_line<float>(y, y, L, nmodes, k, l_sub, thm, thc, inv_t);
 }
 
+// Certify mode: partial sums of ||B - (tA - tau_i I) X_i||_F^2 per pole, X_i = Xr + i Xi stored
+// as columns [i 2p + c] (real) and [i 2p + p + c] (imaginary) of X.  One partial per CTA and
+// pole; the host adds them.
+__global__ void k_true_resid(const double* __restrict__ X, int64_t ldx, const double* __restrict__ B,
+                             int64_t ldb, int p, int npoles, int ndim, int nx, int ny, int nz, Axis ax0,
+                             Axis ax1, Axis ax2, double t, const double* __restrict__ tau_re,
+                             const double* __restrict__ tau_im, double* __restrict__ part) {
+    __shared__ double red[256];
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pole = blockIdx.y;
+    double acc = 0.0;
+    if (i < n) {
+        const int ix = (int)(i % nx);
+        const int iy = (int)((i / nx) % ny);
+        const int iz = (int)(i / ((int64_t)nx * ny));
+        const double dc = ax0.c + (ndim > 1 ? ax1.c : 0.0) + (ndim > 2 ? ax2.c : 0.0);
+        const double tr = tau_re[pole], ti = tau_im[pole];
+        for (int c = 0; c < p; ++c) {
+            double ax[2];
+            for (int part_ = 0; part_ < 2; ++part_) {
+                const double* v = X + (int64_t)(2 * pole * p + part_ * p + c) * ldx;
+                double s = dc * v[i];
+                if (ix > 0) s += ax0.l * v[i - 1];
+                if (ix < nx - 1) s += ax0.u * v[i + 1];
+                if (ndim > 1) {
+                    if (iy > 0) s += ax1.l * v[i - nx];
+                    if (iy < ny - 1) s += ax1.u * v[i + nx];
+                }
+                if (ndim > 2) {
+                    const int64_t st = (int64_t)nx * ny;
+                    if (iz > 0) s += ax2.l * v[i - st];
+                    if (iz < nz - 1) s += ax2.u * v[i + st];
+                }
+                ax[part_] = t * s;
+            }
+            const double xr = X[(int64_t)(2 * pole * p + c) * ldx + i];
+            const double xi = X[(int64_t)(2 * pole * p + p + c) * ldx + i];
+            // (tA - tau)(xr + i xi) = (A xr - tr xr + ti xi) + i (A xi - tr xi - ti xr)
+            const double rre = B[(int64_t)c * ldb + i] - (ax[0] - tr * xr + ti * xi);
+            const double rim = -(ax[1] - tr * xi - ti * xr);
+            acc += rre * rre + rim * rim;
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)pole * gridDim.x + blockIdx.x] = red[0];
+}
+
 __global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
@@ -347,6 +400,18 @@ cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t n
     const int thr = 128;
     k_tridiag_lines32<<<(unsigned)((tot + thr - 1) / thr), thr, 0, s>>>(y, ld, p, L, nmodes, l_sub,
                                                                        th_m, th_c, inv_t);
+    return cudaGetLastError();
+}
+
+int true_resid_blocks(int64_t n) { return (int)((n + 255) / 256); }
+
+cudaError_t launch_true_resid(const double* X, int64_t ldx, const double* B, int64_t ldb, int p, int npoles,
+                              int ndim, int nx, int ny, int nz, const Axis* ax, double t, const double* tau_re,
+                              const double* tau_im, double* part, cudaStream_t s) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    dim3 grid((unsigned)true_resid_blocks(n), npoles);
+    k_true_resid<<<grid, 256, 0, s>>>(X, ldx, B, ldb, p, npoles, ndim, nx, ny, nz, ax[0], ax[1], ax[2], t,
+                                      tau_re, tau_im, part);
     return cudaGetLastError();
 }
 

@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
                                                         const double* __restrict__ om_im,
                                                         double* __restrict__ S, double* __restrict__ work,
                                                         double* __restrict__ Y_slots, double* res,
-                                                        int* flags, int use_smem, int h_in_smem, int alg) {
+                                                        int* flags, int use_smem, int h_in_smem, int alg,
+                                                        double* __restrict__ Zout) {
     extern __shared__ double sm[];
     __shared__ cplx f[kMaxP + 1];
     __shared__ int piv_s;
@@ -177,6 +178,10 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
         res[i] = sqrt(red[0]);
         if (!isfinite(red[0])) atomicOr(&flags[0], 4);
     }
+    if (Zout) {   // certify mode: Z_i itself (complex, row-major [r][c])
+        cplx* Zi = reinterpret_cast<cplx*>(Zout) + (size_t)i * mp * p;
+        for (int e = tid; e < mp * p; e += nt) Zi[e] = X[e];
+    }
     // Y_i = 2 Re(omega_i Z_i), stored r fastest (Y[c * mp + r])
     double* Yi = Y_slots + (size_t)i * mp * p;
     for (int e = tid; e < mp * p; e += nt) {
@@ -210,7 +215,39 @@ __global__ void k_combine2(const double* __restrict__ H, int ldH, int mp, int p,
     }
 }
 
+// Certify mode: C[a][i 2p + c] = Re(F_i)[a][c], C[a][i 2p + p + c] = Im(F_i)[a][c] with
+// F_i = H~_m Z_i (Algorithm 2: X_i - X_i^0 = V_{m+1} H~_m Z_i) or F_i = [Z_i; 0] (Algorithm 1),
+// so X += V_{m+1} C updates every pole's real and imaginary parts in one tall-skinny product.
+__global__ void k_certify_coeffs(const double* __restrict__ H, int ldH, int mp, int p, int npoles,
+                                 const double* __restrict__ Zs, double* __restrict__ C, int alg) {
+    const int rows = mp + p, w = 2 * npoles * p;
+    const cplx* Z = reinterpret_cast<const cplx*>(Zs);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * npoles * p; e += gridDim.x * blockDim.x) {
+        const int a = e % rows, ic = e / rows, i = ic / p, c = ic % p;
+        const cplx* Zi = Z + (size_t)i * mp * p;
+        cplx s{0.0, 0.0};
+        if (alg == 2) {
+            for (int k = max(0, a - p); k < mp; ++k) {
+                const double h = H[(int64_t)k * ldH + a];
+                s.re = fma(h, Zi[(size_t)k * p + c].re, s.re);
+                s.im = fma(h, Zi[(size_t)k * p + c].im, s.im);
+            }
+        } else if (a < mp) {
+            s = Zi[(size_t)a * p + c];
+        }
+        C[(size_t)a * w + 2 * i * p + c] = s.re;
+        C[(size_t)a * w + 2 * i * p + p + c] = s.im;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_certify_coeffs(const double* H, int ldH, int mp, int p, int npoles, const double* Zs,
+                                  double* C, int alg, cudaStream_t s) {
+    const int tot = (mp + p) * npoles * p;
+    k_certify_coeffs<<<(tot + 255) / 256, 256, 0, s>>>(H, ldH, mp, p, npoles, Zs, C, alg);
+    return cudaGetLastError();
+}
 
 size_t poles_smem_bytes(int mp, int p) {
     const size_t b = ((size_t)mp * mp + (size_t)mp * p) * sizeof(cplx);
@@ -222,7 +259,7 @@ static size_t poles_h_bytes(int mp, int p) { return (size_t)(mp + p) * mp * size
 cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          const double* tau_re, const double* tau_im, const double* om_re,
                          const double* om_im, double* S, double* work, double* Y_slots,
-                         double* res, int* flags, int alg, cudaStream_t s) {
+                         double* res, int* flags, int alg, cudaStream_t s, double* Zout) {
     size_t shm = poles_smem_bytes(mp, p);
     int h_in = 0;
     if (shm > 0 && shm + poles_h_bytes(mp, p) <= kSmemLimit) {
@@ -231,7 +268,7 @@ cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
     }
     k_poles<<<npoles, kPoleThreads, shm, s>>>(H, ldH, mp, p, tau_re, tau_im, om_re, om_im, S, work,
                                               Y_slots, res, flags, poles_smem_bytes(mp, p) > 0 ? 1 : 0,
-                                              h_in, alg);
+                                              h_in, alg, Zout);
     return cudaGetLastError();
 }
 

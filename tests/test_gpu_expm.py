@@ -159,3 +159,25 @@ def test_nearly_dependent_rhs_takes_the_shifted_qr_pass(tab):
     ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
     assert info.converged == 1
     assert rel(to_np(Zg), ref) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("sides,diff,vel,t,p,alg", [((37, 29), 0.1, (1.0, 1.0), 0.1, 3, 1),
+                                                    ((40, 33), 0.1, (1.0, 1.0), 1.0, 2, 2),
+                                                    ((11, 9, 7), 1.0, (3.0, -2.0, 1.0), 0.3, 2, 2)])
+def test_certify_true_residual_matches_eq49(tab, precision, sides, diff, vel, t, p, alg):
+    """Certify mode recomputes ||B - (tA - tau_i I) X_i||_F in FP64 from the accumulated X_i
+    (eq. (3)); it must equal the collinear-residual estimate of eq. (49) / eq. (365) that
+    drives the stop test, for both precisions, and must not change Z."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n = int(np.prod(sides))
+    B = inputs.rhs(n, p, 91)
+    kw = dict(p_max=p, m=5, fixed_cycles=3, algorithm=alg, precision=precision)
+    Zc, ic = Plan(sides, diff, vel, certify=True, **kw).expm_block(t, to_dev(B))
+    Zp, ip = Plan(sides, diff, vel, **kw).expm_block(t, to_dev(B))
+    assert rel(to_np(Zc), to_np(Zp)) < 1e-14
+    nb = np.linalg.norm(B)
+    for i in range(7):
+        est, true = ic.resid[i], ic.true_resid[i]
+        assert abs(true - est) <= 1e-6 * est + 1e-11 * nb, (i, est, true)
