@@ -58,6 +58,7 @@ class Plan:
         opts.certify = 1 if certify else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
+        self.tol, self.max_cycles, self.algorithm, self.precision = tol, max_cycles, algorithm, precision
         self.n = 1
         for s in sides:
             self.n *= s

@@ -23,7 +23,19 @@ WORKLOADS = {
                        seed=SEED_BASE + 1),
     "cd2d-256": dict(sides=(256, 256), diff=0.1, vel=(1.0, 1.0), t=(1e-3, 1e-2, 1e-1), p=8, m=10,
                      tol=1e-10, seed=SEED_BASE + 2),
+    # differentiation: L = ||r(tA) B - Y||_F^2, Y = r(t0 A) B0 (t0, B0 seeded perturbations)
+    "cd2d-512-grad": dict(sides=(512, 512), diff=0.1, vel=(1.0, 1.0), t=(1e-2,), p=32, m=10,
+                          tol=1e-10, seed=SEED_BASE + 5),
 }
+
+
+def grad_target(n, p, seed, t):
+    """(t0, B0) of the differentiation workload: t0 = t (1 + 0.05 N(0,1)) (kept > 0),
+    B0 = B + 0.1 N(0,1); B itself is rhs(n, p, seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    t0 = max(1e-6, t * (1.0 + 0.05 * rng.standard_normal()))
+    B0 = rhs(n, p, seed) + 0.1 * np.asfortranarray(rng.standard_normal((p, n)).T)
+    return t0, B0
 
 
 def rhs(n, p, seed):
