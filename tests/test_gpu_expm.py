@@ -181,3 +181,19 @@ def test_certify_true_residual_matches_eq49(tab, precision, sides, diff, vel, t,
     for i in range(7):
         est, true = ic.resid[i], ic.true_resid[i]
         assert abs(true - est) <= 1e-6 * est + 1e-11 * nb, (i, est, true)
+
+
+def test_example_5_1a_replay_on_gpu(tab):
+    """The paper's Example 5.1a operator (-2500 gallery('poisson', 99), p = 3, m = 30,
+    tol = 1e-8) on the GPU: Algorithm 2 converges within Table 5.1's Mat-Vec count (123) and
+    error (5.76e-10 against expm); Algorithm 1 needs several times more Mat-Vecs."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    sides, diff, vel, t = (99, 99), 0.25, (0.0, 0.0), 1.0
+    B = np.random.default_rng(2014).standard_normal((9801, 3))
+    ex = ops.exact_expm_B(sides, diff, vel, t, B)
+    Z2, i2 = Plan(sides, diff, vel, p_max=3, m=30, tol=1e-8, algorithm=2).expm_block(t, to_dev(B))
+    Z1, i1 = Plan(sides, diff, vel, p_max=3, m=30, tol=1e-8, max_cycles=2000, algorithm=1).expm_block(t, to_dev(B))
+    assert i2.converged and i1.converged
+    assert i2.matvecs <= 123 and rel(to_np(Z2), ex) <= 5.76e-10
+    assert i1.matvecs >= 6 * i2.matvecs and rel(to_np(Z1), ex) <= 4.5e-8
