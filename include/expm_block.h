@@ -38,8 +38,8 @@ typedef enum {
     EXPM_OK = 0,
     EXPM_INVALID_ARG = 1,      /* bad size, pointer, descriptor or option            */
     EXPM_NOT_CONVERGED = 2,    /* max_cycles reached; Z still written, info filled   */
-    EXPM_BREAKDOWN = 3,        /* block Arnoldi breakdown that is not an invariant
-                                  subspace (the paper is silent on this case)        */
+    EXPM_BREAKDOWN = 3,        /* reserved: a breakdown of the block Arnoldi process
+                                  is not an error (see expm_info.breakdown)         */
     EXPM_NUMERICAL = 4,        /* NaN/Inf, or a Cholesky pivot <= 0 in the block QR  */
     EXPM_CUDA_ERROR = 5,       /* a CUDA runtime call or kernel launch failed         */
     EXPM_NO_MEMORY = 6,        /* device allocation failed at plan creation           */
@@ -54,15 +54,27 @@ typedef enum {
      * |vel_d| h_d / (2 diff) < 1 on every axis (then tA is diagonally similar to a
      * symmetric negative definite matrix).  The 1-D case with vel = 0 and diff = 1 is
      * (n+1)^2 tridiag(1, -2, 1); the 2-D Laplacian is the paper's Example 5.1 matrix. */
-    EXPM_OP_CONV_DIFF = 0
+    EXPM_OP_CONV_DIFF = 0,
+    /* t * T, T the n x n symmetric Toeplitz matrix with first column (a_0, .., a_bw, 0, ..)
+     * (Example 5.4).  Products by circulant embedding (size N = 2^k >= max(n + bw, 2n),
+     * N <= 2^22) and a four-step FP64 FFT; the exact inverse (Algorithm 2's preconditioner)
+     * by the Gohberg-Semencul formula (Section 4.1) from the generator x = T^{-1} e_1,
+     * computed at plan creation by conjugate gradients with the FFT product.  Requires
+     * a_0 < 0 and T negative definite: for bw <= 4096 the plan bounds the largest value of
+     * the symbol a_0 + 2 sum_k a_k cos(k theta) (grid plus Bernstein's inequality) and
+     * requires it < 0; for larger bw it requires a_0 + 2 sum_k |a_k| <= 0. */
+    EXPM_OP_TOEPLITZ_SYM = 1
 } expm_op_kind;
 
 typedef struct {
     int32_t kind;          /* expm_op_kind                                           */
-    int32_t ndim;          /* 1, 2 or 3                                              */
-    int32_t side[3];       /* interior grid points per axis (x, y, z); unused = 1    */
-    double  diff;          /* diffusion coefficient (> 0)                            */
-    double  vel[3];        /* convection velocity per axis                           */
+    int32_t ndim;          /* CONV_DIFF: 1, 2 or 3                                   */
+    int32_t side[3];       /* CONV_DIFF: interior grid points per axis (x, y, z); unused = 1 */
+    double  diff;          /* CONV_DIFF: diffusion coefficient (> 0)                 */
+    double  vel[3];        /* CONV_DIFF: convection velocity per axis                */
+    int64_t n;             /* TOEPLITZ_SYM: order n >= 2                             */
+    const double* toeplitz_col; /* TOEPLITZ_SYM: host, a_0 .. a_bw (read at plan creation) */
+    int64_t toeplitz_bw;   /* TOEPLITZ_SYM: bandwidth, 0 <= bw <= n - 1              */
 } expm_op_desc;
 
 typedef enum {
@@ -107,7 +119,8 @@ typedef struct {
     int32_t block_steps;         /* block applications of (tA)^{-1}                  */
     int64_t matvecs;             /* p * block_steps: the paper's Mat-Vec count (Sec. 5) */
     int32_t converged;           /* 1 if max_i resid[i] <= tol ||B||_F               */
-    int32_t breakdown;           /* 1 if a cycle ended on an invariant subspace      */
+    int32_t breakdown;           /* 1 if a block step found the block Krylov space
+                                    invariant up to rounding (informational)         */
     int32_t npoles;              /* nu/2 poles with Im tau > 0                        */
     double  resid[EXPM_MAX_POLES]; /* eq. (49) norms ||R_i||_F after the last cycle   */
     double  normB;               /* ||B||_F                                          */
@@ -138,14 +151,19 @@ expm_status expm_cf_coeffs(int nu, double* tau_re_im, double* omega_re_im,
 /* ---------------------------------------------------------------------------------
  * expm_plan_create -- "LU once and for all" (Section 4.1; Section 5): set up the exact
  * inverse of A (without t: (tA)^{-1} = A^{-1}/t) and allocate the workspace for block
- * width up to p_max and the options' m.
+ * width up to p_max and the options' m.  For EXPM_OP_TOEPLITZ_SYM the setup is the
+ * spectrum of the circulant embedding (one FFT) and, unless opts.algorithm is
+ * EXPM_ALG_SBFOM, the Gohberg-Semencul generator (conjugate gradients on the device;
+ * EXPM_NOT_CONVERGED if its residual stays above 1e-12).  EXPM_PREC_MIXED on a Toeplitz
+ * operator keeps the FFTs in FP64 and runs the Gram-Schmidt projections in FP32.
  *   op      : host descriptor (read during the call)
  *   p_max   : 1 <= p_max <= 32; m * p_max <= 512
  *   opts    : host options (copied)
  *   stream  : cudaStream_t (NULL = legacy default stream) used by every later call
  *   out     : host, receives the plan; owned by the caller, free with expm_plan_destroy
  * The plan owns all device memory it allocates (Krylov basis, Hessenberg matrix,
- * preconditioner tables).  Errors: EXPM_INVALID_ARG, EXPM_NO_MEMORY, EXPM_CUDA_ERROR.
+ * preconditioner tables).  Errors: EXPM_INVALID_ARG, EXPM_NO_MEMORY, EXPM_CUDA_ERROR,
+ * EXPM_NOT_CONVERGED (Toeplitz generator).
  * ------------------------------------------------------------------------------ */
 expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts* opts,
                              void* stream, expm_plan** out);
@@ -188,7 +206,9 @@ expm_status expm_block_host(expm_plan* plan, double t, const double* hB, int64_t
  * expm_prec_apply : W = (tA)^{-1} V, the exact inner solve that replaces the paper's
  *                   sparse LU (Section 4.1, "U \ (L \ w)"): a transform along every
  *                   axis but x with the axis' eigenvectors (diagonal similarity + DST-I),
- *                   then tridiagonal solves along x for each transformed mode.
+ *                   then tridiagonal solves along x for each transformed mode; for a
+ *                   Toeplitz operator the Gohberg-Semencul formula (six FFTs per column
+ *                   pair; EXPM_INVALID_ARG if the plan was created for EXPM_ALG_SBFOM).
  *   dV, dW : device, n x p (ld >= n), must not alias; 1 <= p <= p_max.
  * Errors: EXPM_INVALID_ARG, EXPM_CUDA_ERROR (launch failure).
  * ------------------------------------------------------------------------------ */
@@ -222,7 +242,7 @@ expm_status expm_prec_apply_noalloc(const expm_op_desc* op, double t, const doub
  *   dHout : device (m+1)p x mp out (ldh), the band Hessenberg H~_m
  * With Cholesky-QR the new blocks' R factors have a positive diagonal, so the basis
  * equals Ruhe's variant's (Section 3) in exact arithmetic.  Synchronises the stream
- * (breakdown flag).  Errors: EXPM_INVALID_ARG, EXPM_NUMERICAL, EXPM_CUDA_ERROR. */
+ * (status flags).  Errors: EXPM_INVALID_ARG, EXPM_NUMERICAL, EXPM_CUDA_ERROR. */
 expm_status expm_arnoldi(expm_plan* plan, double t, const double* dV1, int64_t ldv1, int p,
                          double* dVout, int64_t ldvo, double* dHout, int64_t ldh);
 

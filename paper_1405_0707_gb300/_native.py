@@ -19,6 +19,7 @@ EXPM_CUDA_ERROR = 5
 EXPM_NO_MEMORY = 6
 EXPM_INTERNAL = 7
 EXPM_OP_CONV_DIFF = 0
+EXPM_OP_TOEPLITZ_SYM = 1
 EXPM_PREC_FP64 = 0
 EXPM_PREC_MIXED = 1
 EXPM_ALG_AUTO = 0
@@ -36,7 +37,8 @@ STAGES = ("gemm", "tridiag", "cgs", "reduce", "qr", "poles", "update", "other", 
 
 class expm_op_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("ndim", C.c_int32), ("side", C.c_int32 * 3),
-                ("diff", C.c_double), ("vel", C.c_double * 3)]
+                ("diff", C.c_double), ("vel", C.c_double * 3), ("n", C.c_int64),
+                ("toeplitz_col", C.POINTER(C.c_double)), ("toeplitz_bw", C.c_int64)]
 
 
 class expm_opts(C.Structure):

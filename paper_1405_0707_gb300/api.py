@@ -34,22 +34,26 @@ def cf_coeffs(nu=14):
 
 
 class Plan:
-    """A plan for tA = t (diff Laplacian_h - vel . grad_h) on a 1/2/3-D grid (x fastest)."""
+    """A plan for tA = t (diff Laplacian_h - vel . grad_h) on a 1/2/3-D grid (x fastest), or
+    (``Plan.toeplitz``) for tA = t T with T symmetric Toeplitz."""
 
     def __init__(self, sides, diff, vel, p_max, m=10, tol=1e-10, max_cycles=200,
-                 fixed_cycles=0, stream=None, algorithm=0, precision="fp64", certify=False):
+                 fixed_cycles=0, stream=None, algorithm=0, precision="fp64", certify=False, _op=None):
         import torch
-        sides = tuple(int(s) for s in sides)
-        vel = tuple(float(v) for v in vel)
-        if len(sides) != len(vel) or not 1 <= len(sides) <= 3:
-            raise ValueError("sides and vel must have the same length 1..3")
-        op = N.expm_op_desc()
-        op.kind = N.EXPM_OP_CONV_DIFF
-        op.ndim = len(sides)
-        for d in range(3):
-            op.side[d] = sides[d] if d < len(sides) else 1
-            op.vel[d] = vel[d] if d < len(vel) else 0.0
-        op.diff = float(diff)
+        if _op is None:
+            sides = tuple(int(s) for s in sides)
+            vel = tuple(float(v) for v in vel)
+            if len(sides) != len(vel) or not 1 <= len(sides) <= 3:
+                raise ValueError("sides and vel must have the same length 1..3")
+            op = N.expm_op_desc()
+            op.kind = N.EXPM_OP_CONV_DIFF
+            op.ndim = len(sides)
+            for d in range(3):
+                op.side[d] = sides[d] if d < len(sides) else 1
+                op.vel[d] = vel[d] if d < len(vel) else 0.0
+            op.diff = float(diff)
+        else:
+            op = _op
         opts = N.expm_opts()
         opts.m, opts.max_cycles, opts.tol = int(m), int(max_cycles), float(tol)
         opts.precision = {"fp64": N.EXPM_PREC_FP64, "mixed": N.EXPM_PREC_MIXED}[precision]
@@ -59,10 +63,31 @@ class Plan:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
         self.tol, self.max_cycles, self.algorithm, self.precision = tol, max_cycles, algorithm, precision
-        self.n = 1
-        for s in sides:
-            self.n *= s
+        if _op is None:
+            self.n = 1
+            for s in sides:
+                self.n *= s
+        else:
+            self.n = int(op.n)
         self._h = N.expm_plan_create(op, int(p_max), opts, self.stream.cuda_stream)
+
+    @classmethod
+    def toeplitz(cls, col, n, p_max, **kw):
+        """Plan for t T, T the n x n symmetric Toeplitz matrix with first column
+        (col[0], .., col[bw], 0, ..), bw = len(col) - 1 (Example 5.4)."""
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(col, dtype=np.float64))
+        op = N.expm_op_desc()
+        op.kind = N.EXPM_OP_TOEPLITZ_SYM
+        op.ndim = 1
+        for d in range(3):
+            op.side[d] = 1
+        op.n = int(n)
+        op.toeplitz_col = a.ctypes.data_as(C.POINTER(C.c_double))
+        op.toeplitz_bw = len(a) - 1
+        plan = cls(None, 0.0, None, p_max, _op=op, **kw)
+        plan.toeplitz_col = a
+        return plan
 
     def close(self):
         if getattr(self, "_h", None):

@@ -148,9 +148,102 @@ expm_status prec_apply_mixed(expm_plan* P, double t, const double* V, int64_t ld
     return EXPM_OK;
 }
 
+// ---- symmetric Toeplitz operator (k_fft.cu): products and the Gohberg-Semencul inverse
+int toeplitz_nseq_max(const expm_plan* P) { return std::max(2, (P->p_max + 1) / 2); }
+
+FftArgs fft_args(const expm_plan* P) {
+    const ToeplitzOp& z = P->tz;
+    FftArgs a;
+    a.f = z.f;
+    a.nreal = z.n;
+    a.tw1 = z.tw1;
+    a.tw2 = z.tw2;
+    a.thi = z.thi;
+    a.tlo = z.tlo;
+    a.lam = z.lam;
+    a.mu1 = z.mu1;
+    a.mu2 = z.mu2;
+    return a;
+}
+
+// W = tT V: per group of up to 2 nseq_max columns, the forward column pass (pairs of real
+// columns packed as one complex sequence), the fused row pass (forward, times t lambda / N,
+// inverse) and the inverse column pass (real and imaginary parts to the two columns).
+expm_status toeplitz_matvec(expm_plan* P, double t, const double* V, int64_t ldv, int p, double* W,
+                            int64_t ldw, int stage) {
+    cudaStream_t s = P->stream;
+    const int maxcols = 2 * toeplitz_nseq_max(P);
+    for (int c0 = 0; c0 < p; c0 += maxcols) {
+        const int pc = std::min(maxcols, p - c0), nseq = (pc + 1) / 2;
+        FftArgs a = fft_args(P);
+        a.V = V + (int64_t)c0 * ldv;
+        a.ldv = ldv;
+        a.W = W + (int64_t)c0 * ldw;
+        a.ldw = ldw;
+        a.p = pc;
+        a.in = a.out = P->tz.Ua;
+        a.scale = t / (double)P->tz.f.N;
+        LAUNCH(stage, launch_fft_cols(a, FFT_COL_FWD_REAL, nseq, s));
+        LAUNCH(stage, launch_fft_rows(a, FFT_ROW_MATVEC, nseq, s));
+        a.scale = 1.0;
+        LAUNCH(stage, launch_fft_cols(a, FFT_COL_INV_REAL, nseq, s));
+    }
+    return EXPM_OK;
+}
+
+// W = (tT)^{-1} V by the Gohberg-Semencul formula: five passes per column group (six
+// transforms per sequence; see k_fft.cu).
+expm_status toeplitz_inverse(expm_plan* P, double t, const double* V, int64_t ldv, int p, double* W,
+                             int64_t ldw, int stage) {
+    cudaStream_t s = P->stream;
+    const ToeplitzOp& z = P->tz;
+    const int maxcols = 2 * toeplitz_nseq_max(P);
+    const int64_t N = z.f.N;
+    for (int c0 = 0; c0 < p; c0 += maxcols) {
+        const int pc = std::min(maxcols, p - c0), nseq = (pc + 1) / 2;
+        FftArgs a = fft_args(P);
+        a.V = V + (int64_t)c0 * ldv;
+        a.ldv = ldv;
+        a.W = W + (int64_t)c0 * ldw;
+        a.ldw = ldw;
+        a.p = pc;
+        a.out = z.Ua;
+        LAUNCH(stage, launch_fft_cols(a, FFT_COL_FWD_REAL, nseq, s));                  // F v
+        a.in = z.Ua;
+        a.out = z.Ub;
+        a.out2 = z.Ub + 2 * N * nseq;
+        a.scale = 1.0 / (double)N;
+        LAUNCH(stage, launch_fft_rows(a, FFT_ROW_GSF_A, nseq, s));                     // conj(mu_k) F v, inverse rows
+        a.in = a.out = z.Ub;
+        LAUNCH(stage, launch_fft_cols(a, FFT_COL_INV_TRUNC_FWD, 2 * nseq, s));         // u_k, truncated, forward
+        a.in = z.Ub;
+        a.in2 = z.Ub + 2 * N * nseq;
+        a.out = z.Ua;
+        a.scale = 1.0 / ((double)N * t * z.x0);
+        LAUNCH(stage, launch_fft_rows(a, FFT_ROW_GSF_B, nseq, s));                     // mu_1 F u_1 - mu_2 F u_2
+        a.in = z.Ua;
+        a.scale = 1.0;
+        LAUNCH(stage, launch_fft_cols(a, FFT_COL_INV_REAL, nseq, s));                  // first n entries
+    }
+    return EXPM_OK;
+}
+
+// W = tA V for either operator family
+expm_status op_apply_internal(expm_plan* P, double t, const double* V, int64_t ldv, int p, double* W,
+                              int64_t ldw) {
+    if (P->toeplitz) return toeplitz_matvec(P, t, V, ldv, p, W, ldw, EXPM_STAGE_STENCIL);
+    LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(V, ldv, W, ldw, p, P->ndim, P->ax[0].N, P->ax[1].N, P->ax[2].N,
+                                               P->ax, t, P->stream));
+    return EXPM_OK;
+}
+
 expm_status prec_apply_internal(expm_plan* P, double t, const double* V, int64_t ldv, int p,
                                 double* W, int64_t ldw) {
     cudaStream_t s = P->stream;
+    if (P->toeplitz) {
+        if (!P->tz.gsf) return EXPM_INVALID_ARG;
+        return toeplitz_inverse(P, t, V, ldv, p, W, ldw, EXPM_STAGE_GEMM);
+    }
     if (P->opts.precision == EXPM_PREC_MIXED && P->ndim > 1) return prec_apply_mixed(P, t, V, ldv, p, W, ldw);
     const double inv_t = 1.0 / t;
     const int nx = P->ax[0].N, ny = P->ax[1].N, nz = P->ax[2].N;
@@ -193,8 +286,8 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
         expm_status st = prec_apply_internal(P, t, Vj, ld, p, P->W, ld);
         if (st != EXPM_OK) return st;
     } else {
-        LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(Vj, ld, P->W, ld, p, P->ndim, P->ax[0].N, P->ax[1].N,
-                                                   P->ax[2].N, P->ax, t, s));
+        expm_status st = op_apply_internal(P, t, Vj, ld, p, P->W, ld);
+        if (st != EXPM_OK) return st;
     }
     const int cols = (j + 1) * p;
     const int f32 = P->opts.precision == EXPM_PREC_MIXED ? 1 : 0;
@@ -209,7 +302,6 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
 expm_status check_flags(const double* hstat) {
     const int* f = reinterpret_cast<const int*>(hstat + 24);
     if (f[0]) return EXPM_NUMERICAL;
-    if (f[1]) return EXPM_BREAKDOWN;
     return EXPM_OK;
 }
 
@@ -225,6 +317,7 @@ expm_status validate_block_args(expm_plan* P, double t, const void* B, int64_t l
 
 // Gershgorin bound of ||tA||_inf for the convection-diffusion operator.
 double norm_bound(const expm_plan* P, double t) {
+    if (P->toeplitz) return t * P->tz.abs_rowsum;
     double s = 0.0;
     for (int d = 0; d < P->ndim; ++d) s += std::fabs(P->ax[d].l) + std::fabs(P->ax[d].c) + std::fabs(P->ax[d].u);
     return t * s;
@@ -232,6 +325,7 @@ double norm_bound(const expm_plan* P, double t) {
 
 int choose_algorithm(const expm_plan* P, double t) {
     if (P->opts.algorithm == EXPM_ALG_SBFOM || P->opts.algorithm == EXPM_ALG_PSBFOM) return P->opts.algorithm;
+    if (P->toeplitz && !P->tz.gsf) return EXPM_ALG_SBFOM;
     double tmax = 0.0;
     for (int i = 0; i < P->npoles; ++i) tmax = std::max(tmax, std::hypot(P->tau_re[i], P->tau_im[i]));
     return norm_bound(P, t) >= EXPM_AUTO_RATIO * tmax ? EXPM_ALG_PSBFOM : EXPM_ALG_SBFOM;
@@ -312,7 +406,6 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
     const int alg = choose_algorithm(P, t);
     const int m = P->opts.m;
     const int64_t n = P->n, ld = P->ld;
-    const int mp = m * p;
     CK(cudaMemsetAsync(P->stat, 0, sizeof(double) * kStatDoubles, s));
     CK(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)P->ldH * m * P->p_max, s));
     LAUNCH(EXPM_STAGE_OTHER, launch_zero(P->Zacc, ld, n, p, s));
@@ -358,9 +451,17 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
     if (P->opts.certify) {
         // the true FP64 residuals ||B - (tA - tau_i I) X_i||_F of every pole (eq. (3))
         double* tau = sm(P, kOffTau);
-        LAUNCH(EXPM_STAGE_OTHER, launch_true_resid(P->Xcert, ld, dB, ldb, p, P->npoles, P->ndim, P->ax[0].N,
-                                                   P->ax[1].N, P->ax[2].N, P->ax, t, tau, tau + EXPM_MAX_POLES,
-                                                   P->rcert, s));
+        const double* AX = nullptr;
+        if (P->toeplitz) {
+            // tA X_i for the real and imaginary columns of every pole by FFT products
+            st = toeplitz_matvec(P, t, P->Xcert, ld, 2 * P->npoles * p, P->Acert, ld, EXPM_STAGE_OTHER);
+            if (st != EXPM_OK) return st;
+            AX = P->Acert;
+        }
+        const int nx = P->toeplitz ? (int)n : P->ax[0].N;
+        LAUNCH(EXPM_STAGE_OTHER, launch_true_resid(P->Xcert, ld, dB, ldb, p, P->npoles, P->ndim, nx, P->ax[1].N,
+                                                   P->ax[2].N, P->ax, t, tau, tau + EXPM_MAX_POLES, P->rcert, s,
+                                                   AX, ld));
         const int nb = true_resid_blocks(n);
         CK(cudaMemcpyAsync(P->hcert, P->rcert, sizeof(double) * (size_t)P->npoles * nb, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -377,6 +478,7 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
         info->matvecs = (int64_t)cycles * m * p;
         info->converged = converged ? 1 : 0;
         info->npoles = P->npoles;
+        info->breakdown = reinterpret_cast<const int*>(P->hpin + 24)[1] ? 1 : 0;
         for (int i = 0; i < P->npoles; ++i) info->resid[i] = P->hpin[i];
         info->normB = normB;
         info->algorithm = alg;
@@ -414,6 +516,17 @@ void free_plan(expm_plan* P) {
     cudaFree(P->Bst);
     cudaFree(P->Zst);
     cudaFree(P->Xcert);
+    cudaFree(P->Acert);
+    cudaFree(P->tz.col);
+    cudaFree(P->tz.tw1);
+    cudaFree(P->tz.tw2);
+    cudaFree(P->tz.thi);
+    cudaFree(P->tz.tlo);
+    cudaFree(P->tz.lam);
+    cudaFree(P->tz.Ua);
+    cudaFree(P->tz.Ub);
+    cudaFree(P->tz.mu1);
+    cudaFree(P->tz.mu2);
     cudaFree(P->Zcert);
     cudaFree(P->Ccert);
     cudaFree(P->rcert);
@@ -436,6 +549,161 @@ bool dalloc(T** p, size_t count) {
     if (count == 0) count = 1;
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count) == cudaSuccess;
 }
+
+// ---- Toeplitz plan setup
+constexpr int64_t kToeplitzMaxN = int64_t(1) << 21;   // FFT size N <= 2^22 (see k_fft.cu)
+
+// Upper bound of max_theta f(theta), f(theta) = a_0 + 2 sum_k a_k cos(k theta): the largest
+// value on a grid of M points in [0, pi] plus (pi / 2M) max|f'|, max|f'| <= bw max|f|
+// (Bernstein's inequality for trigonometric polynomials of degree bw).  The grid is refined
+// while the bound is inconclusive (grid maximum < 0 <= bound), up to ~1e9 cosines.
+double toeplitz_symbol_max_bound(const double* a, int64_t bw, double abs_rowsum) {
+    if (bw == 0) return a[0];
+    const double pi = 3.141592653589793238462643383279502884;
+    double bound = 0.0;
+    for (int64_t M = 64 * bw + 64;; M *= 4) {
+        double mx = -1e300;
+        for (int64_t j = 0; j <= M; ++j) {
+            const double th = pi * (double)j / (double)M;
+            double f = a[0];
+            for (int64_t k = 1; k <= bw; ++k) f += 2.0 * a[k] * std::cos((double)k * th);
+            mx = std::max(mx, f);
+        }
+        bound = mx + pi / (2.0 * (double)M) * (double)bw * abs_rowsum;
+        if (mx >= 0.0 || bound < 0.0 || 4 * M * bw > 1000000000) break;
+    }
+    return bound;
+}
+
+expm_status toeplitz_validate(const expm_op_desc* op, double* abs_rowsum) {
+    if (op->n < 2 || op->n > kToeplitzMaxN) return EXPM_INVALID_ARG;
+    if (op->toeplitz_bw < 0 || op->toeplitz_bw > op->n - 1 || !op->toeplitz_col) return EXPM_INVALID_ARG;
+    const double* a = op->toeplitz_col;
+    const int64_t bw = op->toeplitz_bw;
+    double rs = std::fabs(a[0]);
+    for (int64_t k = 0; k <= bw; ++k) {
+        if (!std::isfinite(a[k])) return EXPM_INVALID_ARG;
+        if (k > 0) rs += 2.0 * std::fabs(a[k]);
+    }
+    if (!(a[0] < 0.0)) return EXPM_INVALID_ARG;
+    if (bw <= 4096) {
+        if (!(toeplitz_symbol_max_bound(a, bw, rs) < 0.0)) return EXPM_INVALID_ARG;
+    } else if (!(a[0] + (rs - std::fabs(a[0])) <= 0.0)) {
+        return EXPM_INVALID_ARG;
+    }
+    *abs_rowsum = rs;
+    return EXPM_OK;
+}
+
+// fixed-order sum of the dot-product partials
+expm_status dot_host(expm_plan* P, const double* x, const double* y, double* part, double* hpart, double* out) {
+    cudaStream_t s = P->stream;
+    LAUNCH(EXPM_STAGE_OTHER, launch_dot_partial(x, y, P->n, part, s));
+    CK(cudaMemcpyAsync(hpart, part, sizeof(double) * dot_blocks(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double acc = 0.0;
+    for (int b = 0; b < dot_blocks(); ++b) acc += hpart[b];
+    *out = acc;
+    return EXPM_OK;
+}
+
+// Generator x = T^{-1} e_1 of the Gohberg-Semencul formula by conjugate gradients with the
+// FFT product (T is symmetric definite), then mu_1 = F[x; 0], mu_2 = F[xh; 0].
+expm_status toeplitz_generator(expm_plan* P) {
+    cudaStream_t s = P->stream;
+    ToeplitzOp& z = P->tz;
+    const int64_t n = P->n, ld = P->ld, N = z.f.N;
+    double *buf = nullptr, *part = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&buf), sizeof(double) * 4 * ld) != cudaSuccess) return EXPM_NO_MEMORY;
+    if (cudaMalloc(reinterpret_cast<void**>(&part), sizeof(double) * dot_blocks()) != cudaSuccess) {
+        cudaFree(buf);
+        return EXPM_NO_MEMORY;
+    }
+    std::vector<double> hpart(dot_blocks());
+    double* x = buf;
+    double* r = buf + ld;
+    double* pp = buf + 2 * ld;
+    double* w = buf + 3 * ld;
+    expm_status st = EXPM_OK;
+    auto fail = [&](expm_status e) {
+        cudaStreamSynchronize(s);
+        cudaFree(buf);
+        cudaFree(part);
+        return e;
+    };
+    if (cudaMemsetAsync(x, 0, sizeof(double) * ld, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
+    if (launch_unit(r, n, s) != cudaSuccess || launch_unit(pp, n, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
+    double rr = 1.0;
+    int it = 0;
+    for (; it < 5000 && std::sqrt(rr) > 1e-15; ++it) {
+        if ((st = toeplitz_matvec(P, 1.0, pp, ld, 1, w, ld, EXPM_STAGE_OTHER)) != EXPM_OK) return fail(st);
+        double pw = 0.0;
+        if ((st = dot_host(P, pp, w, part, hpart.data(), &pw)) != EXPM_OK) return fail(st);
+        if (!(pw < 0.0) || !std::isfinite(pw)) return fail(EXPM_NUMERICAL);   // T negative definite
+        const double alpha = rr / pw;
+        if (launch_cg_step(x, r, pp, w, alpha, n, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
+        double rr_new = 0.0;
+        if ((st = dot_host(P, r, r, part, hpart.data(), &rr_new)) != EXPM_OK) return fail(st);
+        if (launch_cg_dir(pp, r, rr_new / rr, n, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
+        rr = rr_new;
+    }
+    // true residual ||e_1 - T x||
+    if ((st = toeplitz_matvec(P, 1.0, x, ld, 1, w, ld, EXPM_STAGE_OTHER)) != EXPM_OK) return fail(st);
+    if (launch_unit(pp, n, s) != cudaSuccess ||
+        launch_axpby(1.0, pp, ld, -1.0, w, ld, r, ld, n, 1, s) != cudaSuccess)
+        return fail(EXPM_CUDA_ERROR);
+    double res2 = 0.0;
+    if ((st = dot_host(P, r, r, part, hpart.data(), &res2)) != EXPM_OK) return fail(st);
+    z.cg_iters = it;
+    z.cg_resid = std::sqrt(res2);
+    if (!(z.cg_resid <= 1e-12)) return fail(EXPM_NOT_CONVERGED);
+    if (cudaMemcpyAsync(&z.x0, x, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return fail(EXPM_CUDA_ERROR);
+    // spectra of [x; 0] and [xh; 0] (transposed order)
+    FftArgs a = fft_args(P);
+    a.in = a.out = z.Ua;
+    if (launch_embed_gsf(x, n, N, z.Ua, s) != cudaSuccess || launch_fft_cols(a, FFT_COL_FWD_CPLX, 2, s) != cudaSuccess ||
+        launch_fft_rows(a, FFT_ROW_FWD, 2, s) != cudaSuccess ||
+        cudaMemcpyAsync(z.mu1, z.Ua, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(z.mu2, z.Ua + 2 * N, sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(EXPM_CUDA_ERROR);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
+    if (!(z.x0 < 0.0) || !std::isfinite(z.x0)) return fail(EXPM_NUMERICAL);
+    z.gsf = true;
+    return fail(EXPM_OK);
+}
+
+// Allocations and spectra of the Toeplitz operator (after the common workspace).
+expm_status toeplitz_setup(expm_plan* P, const expm_op_desc* op, bool want_inverse) {
+    cudaStream_t s = P->stream;
+    ToeplitzOp& z = P->tz;
+    z.f = fft_geometry(std::max(z.n + z.bw, 2 * z.n));
+    if (!fft_geometry_ok(z.f)) return EXPM_INVALID_ARG;
+    const int64_t N = z.f.N;
+    const size_t nseq = (size_t)toeplitz_nseq_max(P);
+    bool ok = dalloc(&z.col, (size_t)z.bw + 1) && dalloc(&z.tw1, 2 * (size_t)z.f.N1) &&
+              dalloc(&z.tw2, 2 * (size_t)z.f.N2) && dalloc(&z.thi, 2 * (size_t)(N / 64)) && dalloc(&z.tlo, 128) &&
+              dalloc(&z.lam, (size_t)N) && dalloc(&z.Ua, 2 * (size_t)N * nseq);
+    if (want_inverse)
+        ok = ok && dalloc(&z.Ub, 4 * (size_t)N * nseq) && dalloc(&z.mu1, 2 * (size_t)N) && dalloc(&z.mu2, 2 * (size_t)N);
+    if (!ok) {
+        cudaGetLastError();
+        return EXPM_NO_MEMORY;
+    }
+    if (fft_set_smem_limits() != cudaSuccess) return EXPM_CUDA_ERROR;
+    FftArgs a = fft_args(P);
+    a.in = a.out = z.Ua;
+    if (cudaMemcpyAsync(z.col, op->toeplitz_col, sizeof(double) * (size_t)(z.bw + 1), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        launch_fft_tables(z.f, z.tw1, z.tw2, z.thi, z.tlo, s) != cudaSuccess ||
+        launch_embed_toeplitz(z.col, z.bw, N, z.Ua, s) != cudaSuccess ||
+        launch_fft_cols(a, FFT_COL_FWD_CPLX, 1, s) != cudaSuccess || launch_fft_rows(a, FFT_ROW_FWD, 1, s) != cudaSuccess ||
+        launch_real_part(z.Ua, z.lam, N, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return EXPM_CUDA_ERROR;
+    if (want_inverse) return toeplitz_generator(P);
+    return EXPM_OK;
+}
+
 
 }  // namespace
 
@@ -476,9 +744,16 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
                              void* stream, expm_plan** out) {
     if (!op || !opts || !out) return EXPM_INVALID_ARG;
     *out = nullptr;
-    if (op->kind != EXPM_OP_CONV_DIFF) return EXPM_INVALID_ARG;
-    if (op->ndim < 1 || op->ndim > 3) return EXPM_INVALID_ARG;
-    if (!(op->diff > 0.0) || !std::isfinite(op->diff)) return EXPM_INVALID_ARG;
+    const bool toeplitz = op->kind == EXPM_OP_TOEPLITZ_SYM;
+    double abs_rowsum = 0.0;
+    if (toeplitz) {
+        const expm_status vs = toeplitz_validate(op, &abs_rowsum);
+        if (vs != EXPM_OK) return vs;
+    } else {
+        if (op->kind != EXPM_OP_CONV_DIFF) return EXPM_INVALID_ARG;
+        if (op->ndim < 1 || op->ndim > 3) return EXPM_INVALID_ARG;
+        if (!(op->diff > 0.0) || !std::isfinite(op->diff)) return EXPM_INVALID_ARG;
+    }
     if (p_max < 1 || p_max > kMaxP) return EXPM_INVALID_ARG;
     if (opts->m < 1 || (int64_t)opts->m * p_max > kMaxMP) return EXPM_INVALID_ARG;
     if (opts->max_cycles < 1 || !(opts->tol >= 0.0)) return EXPM_INVALID_ARG;
@@ -494,8 +769,10 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     expm_plan* P = new (std::nothrow) expm_plan_s();
     if (!P) return EXPM_NO_MEMORY;
     P->op = *op;
+    P->op.toeplitz_col = nullptr;   // host memory of the caller: not kept
     P->opts = *opts;
-    P->ndim = op->ndim;
+    P->toeplitz = toeplitz;
+    P->ndim = toeplitz ? 1 : op->ndim;
     P->p_max = p_max;
     P->stream = reinterpret_cast<cudaStream_t>(stream);
     {
@@ -503,23 +780,30 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         P->use_graphs = !(ng && ng[0] == '1');
     }
     int64_t n = 1;
-    for (int d = 0; d < 3; ++d) {
-        Axis& a = P->ax[d];
-        if (d < op->ndim) {
-            const int N = op->side[d];
-            if (N < 1 || N > (1 << 20)) { delete P; return EXPM_INVALID_ARG; }
-            const double h = 1.0 / (N + 1);
-            a.N = N;
-            a.l = op->diff / (h * h) + op->vel[d] / (2.0 * h);
-            a.c = -2.0 * op->diff / (h * h);
-            a.u = op->diff / (h * h) - op->vel[d] / (2.0 * h);
-            if (!(a.l * a.u > 0.0)) { delete P; return EXPM_INVALID_ARG; }   // cell Peclet >= 1
-            n *= N;
-        } else {
-            a = Axis{};
+    if (toeplitz) {
+        n = op->n;
+        P->tz.n = op->n;
+        P->tz.bw = op->toeplitz_bw;
+        P->tz.abs_rowsum = abs_rowsum;
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            Axis& a = P->ax[d];
+            if (d < op->ndim) {
+                const int N = op->side[d];
+                if (N < 1 || N > (1 << 20)) { delete P; return EXPM_INVALID_ARG; }
+                const double h = 1.0 / (N + 1);
+                a.N = N;
+                a.l = op->diff / (h * h) + op->vel[d] / (2.0 * h);
+                a.c = -2.0 * op->diff / (h * h);
+                a.u = op->diff / (h * h) - op->vel[d] / (2.0 * h);
+                if (!(a.l * a.u > 0.0)) { delete P; return EXPM_INVALID_ARG; }   // cell Peclet >= 1
+                n *= N;
+            } else {
+                a = Axis{};
+            }
         }
+        if (op->ndim > 1 && (int64_t)P->ax[1].N * P->ax[2].N * P->ax[0].N != n) { delete P; return EXPM_INVALID_ARG; }
     }
-    if (op->ndim > 1 && (int64_t)P->ax[1].N * P->ax[2].N * P->ax[0].N != n) { delete P; return EXPM_INVALID_ARG; }
     P->n = n;
     P->ld = round_up(n, 32);
     // CF table (Section 2), nu = 14 as in the paper's experiments (Section 5)
@@ -566,31 +850,35 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         if (8 * (rows * w + 16 * (rows | 1)) > 225 * 1024) { free_plan(P); return EXPM_INVALID_ARG; }
         ok = ok && dalloc(&P->Xcert, (size_t)ld * w) && dalloc(&P->Zcert, (size_t)P->npoles * mpm * p_max * 2) &&
              dalloc(&P->Ccert, rows * w) && dalloc(&P->rcert, (size_t)P->npoles * true_resid_blocks(n));
+        if (toeplitz) ok = ok && dalloc(&P->Acert, (size_t)ld * w);
         P->hcert = new (std::nothrow) double[(size_t)P->npoles * true_resid_blocks(n)];
         ok = ok && P->hcert != nullptr;
     }
     if (poles_smem_bytes(mpm, p_max) == 0)   // elimination does not fit in shared memory
         ok = ok && dalloc(&P->poles, (size_t)P->npoles * ((size_t)mpm * mpm + (size_t)mpm * p_max) * 2);
     ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hpin), sizeof(double) * kStatDoubles) == cudaSuccess;
-    // preconditioner tables: every axis but x is transformed
-    int64_t nmodes = 1;
-    for (int d = 1; d < P->ndim; ++d) {
-        const int N = P->ax[d].N;
-        ok = ok && dalloc(&P->Qf[d], (size_t)N * N) && dalloc(&P->Qi[d], (size_t)N * N) &&
-             dalloc(&P->lam[d], (size_t)N);
-        nmodes *= N;
-    }
-    P->nmodes = nmodes;
-    ok = ok && dalloc(&P->th_m, (size_t)P->ax[0].N * nmodes) && dalloc(&P->th_c, (size_t)P->ax[0].N * nmodes);
     const bool mixed = opts->precision == EXPM_PREC_MIXED;
-    if (mixed) {
+    if (!toeplitz) {
+        // preconditioner tables: every axis but x is transformed
+        int64_t nmodes = 1;
         for (int d = 1; d < P->ndim; ++d) {
             const int N = P->ax[d].N;
-            ok = ok && dalloc(&P->Qf32[d], (size_t)N * N) && dalloc(&P->Qi32[d], (size_t)N * N);
+            ok = ok && dalloc(&P->Qf[d], (size_t)N * N) && dalloc(&P->Qi[d], (size_t)N * N) &&
+                 dalloc(&P->lam[d], (size_t)N);
+            nmodes *= N;
         }
-        ok = ok && dalloc(&P->th_m32, (size_t)P->ax[0].N * nmodes) && dalloc(&P->th_c32, (size_t)P->ax[0].N * nmodes);
-        ok = ok && dalloc(&P->T1f, (size_t)ld * p_max) && dalloc(&P->T2f, (size_t)ld * p_max);
-        ok = ok && dalloc(&P->R64, (size_t)ld * p_max);
+        P->nmodes = nmodes;
+        ok = ok && dalloc(&P->th_m, (size_t)P->ax[0].N * nmodes) && dalloc(&P->th_c, (size_t)P->ax[0].N * nmodes);
+        if (mixed) {
+            for (int d = 1; d < P->ndim; ++d) {
+                const int N = P->ax[d].N;
+                ok = ok && dalloc(&P->Qf32[d], (size_t)N * N) && dalloc(&P->Qi32[d], (size_t)N * N);
+            }
+            ok = ok && dalloc(&P->th_m32, (size_t)P->ax[0].N * nmodes) &&
+                 dalloc(&P->th_c32, (size_t)P->ax[0].N * nmodes);
+            ok = ok && dalloc(&P->T1f, (size_t)ld * p_max) && dalloc(&P->T2f, (size_t)ld * p_max);
+            ok = ok && dalloc(&P->R64, (size_t)ld * p_max);
+        }
     }
     if (!ok) {
         cudaGetLastError();
@@ -599,23 +887,26 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     }
     cudaStream_t s = P->stream;
     bool cuda_ok = krylov_set_smem_limits() == cudaSuccess && poles_set_smem_limits() == cudaSuccess;
-    for (int d = 1; d < P->ndim && cuda_ok; ++d)
-        cuda_ok = launch_axis_setup(P->Qf[d], P->Qi[d], P->lam[d], P->ax[d].N, P->ax[d].l,
-                                    P->ax[d].c, P->ax[d].u, s) == cudaSuccess;
-    if (cuda_ok)
-        cuda_ok = launch_thomas_setup(P->th_m, P->th_c, P->ax[0].N, nmodes, P->ax[0].l, P->ax[0].c,
-                                      P->ax[0].u, P->ndim > 1 ? P->lam[1] : nullptr, P->ax[1].N,
-                                      P->ndim > 2 ? P->lam[2] : nullptr, P->ax[2].N, s) == cudaSuccess;
-    if (cuda_ok && mixed) {
-        for (int d = 1; d < P->ndim && cuda_ok; ++d) {
-            const int64_t NN = (int64_t)P->ax[d].N * P->ax[d].N;
-            cuda_ok = launch_d2f(P->Qf[d], P->Qf32[d], NN, s) == cudaSuccess &&
-                      launch_d2f(P->Qi[d], P->Qi32[d], NN, s) == cudaSuccess;
-        }
-        const int64_t nt = (int64_t)P->ax[0].N * nmodes;
+    if (!toeplitz) {
+        const int64_t nmodes = P->nmodes;
+        for (int d = 1; d < P->ndim && cuda_ok; ++d)
+            cuda_ok = launch_axis_setup(P->Qf[d], P->Qi[d], P->lam[d], P->ax[d].N, P->ax[d].l,
+                                        P->ax[d].c, P->ax[d].u, s) == cudaSuccess;
         if (cuda_ok)
-            cuda_ok = launch_d2f(P->th_m, P->th_m32, nt, s) == cudaSuccess &&
-                      launch_d2f(P->th_c, P->th_c32, nt, s) == cudaSuccess;
+            cuda_ok = launch_thomas_setup(P->th_m, P->th_c, P->ax[0].N, nmodes, P->ax[0].l, P->ax[0].c,
+                                          P->ax[0].u, P->ndim > 1 ? P->lam[1] : nullptr, P->ax[1].N,
+                                          P->ndim > 2 ? P->lam[2] : nullptr, P->ax[2].N, s) == cudaSuccess;
+        if (cuda_ok && mixed) {
+            for (int d = 1; d < P->ndim && cuda_ok; ++d) {
+                const int64_t NN = (int64_t)P->ax[d].N * P->ax[d].N;
+                cuda_ok = launch_d2f(P->Qf[d], P->Qf32[d], NN, s) == cudaSuccess &&
+                          launch_d2f(P->Qi[d], P->Qi32[d], NN, s) == cudaSuccess;
+            }
+            const int64_t nt = (int64_t)P->ax[0].N * nmodes;
+            if (cuda_ok)
+                cuda_ok = launch_d2f(P->th_m, P->th_m32, nt, s) == cudaSuccess &&
+                          launch_d2f(P->th_c, P->th_c32, nt, s) == cudaSuccess;
+        }
     }
     if (cuda_ok) {
         double taus[4 * EXPM_MAX_POLES] = {0};
@@ -631,6 +922,14 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     if (!cuda_ok) {
         free_plan(P);
         return EXPM_CUDA_ERROR;
+    }
+    if (toeplitz) {
+        const expm_status ts = toeplitz_setup(P, op, opts->algorithm != EXPM_ALG_SBFOM);
+        if (ts != EXPM_OK) {
+            cudaGetLastError();
+            free_plan(P);
+            return ts;
+        }
     }
     *out = P;
     return EXPM_OK;
@@ -668,10 +967,7 @@ expm_status expm_op_apply(expm_plan* plan, double t, const double* dV, int64_t l
                           double* dW, int64_t ldw) {
     expm_status st = validate_block_args(plan, t, dV, ldv, p, dW, ldw);
     if (st != EXPM_OK) return st;
-    expm_plan* P = plan;
-    LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(dV, ldv, dW, ldw, p, plan->ndim, plan->ax[0].N, plan->ax[1].N,
-                                               plan->ax[2].N, plan->ax, t, plan->stream));
-    return EXPM_OK;
+    return op_apply_internal(plan, t, dV, ldv, p, dW, ldw);
 }
 
 expm_status expm_prec_apply(expm_plan* plan, double t, const double* dV, int64_t ldv, int p,

@@ -46,6 +46,69 @@ struct GemmArgsMixed {
     int a_f64, c_f64, accumulate;
 };
 
+// Four-step FFT geometry: N = N1 N2 (powers of two), C adjacent columns per block in the
+// column pass, Rr rows per block in the row pass.
+struct FftPlan {
+    int64_t N = 0;
+    int N1 = 0, N2 = 0, C = 1, Rr = 1;
+};
+
+enum FftMode {
+    FFT_COL_FWD_REAL = 0,     // real column pairs of V (zero beyond nreal) -> forward column pass
+    FFT_COL_FWD_CPLX = 1,     // complex in -> forward column pass
+    FFT_COL_INV_REAL = 2,     // inverse column pass -> real/imag parts to column pairs of W (rows < nreal)
+    FFT_COL_INV_CPLX = 3,     // inverse column pass -> complex out (times scale)
+    FFT_COL_INV_TRUNC_FWD = 4,// inverse column pass, zero rows >= nreal, forward column pass
+    FFT_ROW_FWD = 10,         // forward row pass
+    FFT_ROW_MATVEC = 11,      // forward row, times scale * lam (real), inverse row
+    FFT_ROW_GSF_A = 12,       // forward row; out = inv(conj(mu1) y) scale, out2 = inv(conj(mu2) y) scale
+    FFT_ROW_GSF_B = 13        // forward rows of in, in2; out = inv(mu1 f1 - mu2 f2) scale
+};
+
+// Arguments of one FFT pass (complex buffers hold nseq sequences of N interleaved complex).
+struct FftArgs {
+    FftPlan f;
+    const double* V = nullptr;  // real input columns (FFT_COL_FWD_REAL), ld ldv
+    int64_t ldv = 0;
+    double* W = nullptr;        // real output columns (FFT_COL_INV_REAL), ld ldw
+    int64_t ldw = 0;
+    int p = 0;                  // real columns (2 per sequence)
+    int64_t nreal = 0;          // rows of the real columns (n)
+    const double* in = nullptr;
+    const double* in2 = nullptr;
+    double* out = nullptr;
+    double* out2 = nullptr;
+    const double* lam = nullptr;   // real spectrum (transposed order)
+    const double* mu1 = nullptr;   // complex spectra (transposed order)
+    const double* mu2 = nullptr;
+    double scale = 1.0;
+    const double* tw1 = nullptr;   // W_{N1}^k
+    const double* tw2 = nullptr;   // W_{N2}^k
+    const double* thi = nullptr;   // W_N^{64 h}
+    const double* tlo = nullptr;   // W_N^l, l < 64
+};
+
+// Symmetric Toeplitz operator state (device buffers owned by the plan).
+struct ToeplitzOp {
+    int64_t n = 0, bw = 0;
+    FftPlan f{};
+    double* col = nullptr;      // a_0 .. a_bw
+    double* tw1 = nullptr;      // complex tables
+    double* tw2 = nullptr;
+    double* thi = nullptr;
+    double* tlo = nullptr;
+    double* lam = nullptr;      // N real: spectrum of the circulant embedding (transposed order)
+    double* Ua = nullptr;       // nseq_max = max(2, ceil(p_max/2)) sequences of N complex
+    double* Ub = nullptr;       // (Gohberg-Semencul) 2 nseq_max sequences
+    double* mu1 = nullptr;      // (Gohberg-Semencul) spectra of [x; 0] and [xh; 0], N complex each
+    double* mu2 = nullptr;
+    double x0 = 0.0;            // first entry of the generator x = T^{-1} e_1
+    int cg_iters = 0;
+    double cg_resid = 0.0;
+    double abs_rowsum = 0.0;    // |a_0| + 2 sum_k |a_k|  (bound of ||T||)
+    bool gsf = false;           // inverse available
+};
+
 }  // namespace expm
 
 struct GraphEntry {
@@ -61,6 +124,8 @@ struct expm_plan_s {
     expm_opts opts{};
     int ndim = 1;
     expm::Axis ax[3];
+    bool toeplitz = false;     // EXPM_OP_TOEPLITZ_SYM
+    expm::ToeplitzOp tz;
     int64_t n = 0, ld = 0;
     int p_max = 0;
     cudaStream_t stream = nullptr;
@@ -105,6 +170,7 @@ struct expm_plan_s {
     double* Zst = nullptr;     // ld x p_max staging for the host entry point
     // certify mode: per-pole solutions (real/imag columns), Z_i, coefficient matrix, partials
     double* Xcert = nullptr;   // ld x 2 npoles p_max
+    double* Acert = nullptr;   // ld x 2 npoles p_max   tA Xcert (Toeplitz operator)
     double* Zcert = nullptr;   // npoles x m p_max x p_max complex
     double* Ccert = nullptr;   // ((m+1) p_max) x 2 npoles p_max
     double* rcert = nullptr;   // npoles x true_resid_blocks(n)
@@ -169,9 +235,11 @@ cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
 cudaError_t launch_certify_coeffs(const double* H, int ldH, int mp, int p, int npoles, const double* Zs,
                                   double* C, int alg, cudaStream_t s);
 int true_resid_blocks(int64_t n);
+// AX != nullptr: tA X is given (same column layout, leading dimension ldax) instead of the stencil
 cudaError_t launch_true_resid(const double* X, int64_t ldx, const double* B, int64_t ldb, int p, int npoles,
                               int ndim, int nx, int ny, int nz, const Axis* ax, double t, const double* tau_re,
-                              const double* tau_im, double* part, cudaStream_t s);
+                              const double* tau_im, double* part, cudaStream_t s, const double* AX = nullptr,
+                              int64_t ldax = 0);
 cudaError_t launch_combine(const double* Wc_slots, int npoles, int rows, int p, double* Wc,
                            cudaStream_t s);
 cudaError_t launch_combine2(const double* H, int ldH, int mp, int p, int npoles,
@@ -180,6 +248,23 @@ cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
                             const double* Wc, double* Z, int64_t ldz, int restart_copy,
                             cudaStream_t s, int nblk);
 int consistent_blocks(int64_t n, int requested);
+// FFT and Toeplitz pieces (k_fft.cu)
+FftPlan fft_geometry(int64_t nmin);
+bool fft_geometry_ok(const FftPlan& f);
+cudaError_t fft_set_smem_limits();
+cudaError_t launch_fft_tables(const FftPlan& f, double* tw1, double* tw2, double* thi, double* tlo,
+                              cudaStream_t s);
+cudaError_t launch_fft_cols(const FftArgs& a, int mode, int nseq, cudaStream_t s);
+cudaError_t launch_fft_rows(const FftArgs& a, int mode, int nseq, cudaStream_t s);
+cudaError_t launch_embed_toeplitz(const double* a, int64_t bw, int64_t N, double* U, cudaStream_t s);
+cudaError_t launch_embed_gsf(const double* x, int64_t n, int64_t N, double* U, cudaStream_t s);
+cudaError_t launch_real_part(const double* U, double* lam, int64_t N, cudaStream_t s);
+int dot_blocks();
+cudaError_t launch_dot_partial(const double* a, const double* b, int64_t n, double* part, cudaStream_t s);
+cudaError_t launch_cg_step(double* x, double* r, const double* p, const double* w, double alpha, int64_t n,
+                           cudaStream_t s);
+cudaError_t launch_cg_dir(double* p, const double* r, double beta, int64_t n, cudaStream_t s);
+cudaError_t launch_unit(double* v, int64_t n, cudaStream_t s);
 cudaError_t krylov_set_smem_limits();
 cudaError_t poles_set_smem_limits();
 size_t poles_smem_bytes(int mp, int p);

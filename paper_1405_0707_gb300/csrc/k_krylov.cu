@@ -272,7 +272,13 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
 //   mode 1: Rtot = R Rtot; the last pass when extra[0] == 0.
 //   mode 2: returns at once when extra[0] == 0; else Rtot = R Rtot, the last pass.
 // The last pass writes Rtot into H (rows hrow.., cols hcol..) when H is given and checks
-// for breakdown against the column norms of W before orthogonalisation.
+// for breakdown against the column norms of W before orthogonalisation.  Breakdown (the
+// block Krylov space is invariant up to rounding) only sets flags[1] for the caller's
+// information: the new block is then orthonormalised rounding noise coupled to the basis
+// through an entry of H below 1e-14 relative, which leaves the projected solutions
+// unchanged to that order (the paper is silent on breakdown).  Columns that are exactly zero
+// on entry (a zero right-hand side column, or the image of one) get zero rows in R and stay
+// zero, so such blocks pass through without a division by zero.
 constexpr int CHOL_T = 1024;
 __global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part, int nblk, int p,
                                                  double shift_rel, double* R, double* Rinv,
@@ -342,11 +348,18 @@ __global__ void __launch_bounds__(CHOL_T) k_chol(const double* __restrict__ part
         for (int j = 0; j < p; ++j) {
             if (lane == 0) {
                 double d = G[j * p + j];
-                if (!(d > 0.0) || !isfinite(d) || (mode == 0 && attempt == 0 && d < 1e-10 * dmax)) ill = 1;
-                if (!(d > 0.0) || !isfinite(d)) d = 1.0;
-                const double rj = sqrt(d);
-                Rs[j * p + j] = rj;
-                rdiag[j] = 1.0 / rj;
+                if (G0[j * p + j] == 0.0) {
+                    // an exactly zero column (an invariant subspace reached earlier): R row j
+                    // and R^{-1} row and column j stay zero, so the column stays zero
+                    Rs[j * p + j] = 0.0;
+                    rdiag[j] = 0.0;
+                } else {
+                    if (!(d > 0.0) || !isfinite(d) || (mode == 0 && attempt == 0 && d < 1e-10 * dmax)) ill = 1;
+                    if (!(d > 0.0) || !isfinite(d)) d = 1.0;
+                    const double rj = sqrt(d);
+                    Rs[j * p + j] = rj;
+                    rdiag[j] = 1.0 / rj;
+                }
             }
             __syncwarp();
             const double inv = rdiag[j];

@@ -278,7 +278,8 @@ __global__ void k_tridiag_lines32(float* y_io, int64_t ld, int p, int L, int64_t
 __global__ void k_true_resid(const double* __restrict__ X, int64_t ldx, const double* __restrict__ B,
                              int64_t ldb, int p, int npoles, int ndim, int nx, int ny, int nz, Axis ax0,
                              Axis ax1, Axis ax2, double t, const double* __restrict__ tau_re,
-                             const double* __restrict__ tau_im, double* __restrict__ part) {
+                             const double* __restrict__ tau_im, double* __restrict__ part,
+                             const double* __restrict__ AX, int64_t ldax) {
     __shared__ double red[256];
     const int64_t n = (int64_t)nx * ny * nz;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -293,6 +294,10 @@ __global__ void k_true_resid(const double* __restrict__ X, int64_t ldx, const do
         for (int c = 0; c < p; ++c) {
             double ax[2];
             for (int part_ = 0; part_ < 2; ++part_) {
+                if (AX) {
+                    ax[part_] = AX[(int64_t)(2 * pole * p + part_ * p + c) * ldax + i];
+                    continue;
+                }
                 const double* v = X + (int64_t)(2 * pole * p + part_ * p + c) * ldx;
                 double s = dc * v[i];
                 if (ix > 0) s += ax0.l * v[i - 1];
@@ -407,11 +412,12 @@ int true_resid_blocks(int64_t n) { return (int)((n + 255) / 256); }
 
 cudaError_t launch_true_resid(const double* X, int64_t ldx, const double* B, int64_t ldb, int p, int npoles,
                               int ndim, int nx, int ny, int nz, const Axis* ax, double t, const double* tau_re,
-                              const double* tau_im, double* part, cudaStream_t s) {
+                              const double* tau_im, double* part, cudaStream_t s, const double* AX,
+                              int64_t ldax) {
     const int64_t n = (int64_t)nx * ny * nz;
     dim3 grid((unsigned)true_resid_blocks(n), npoles);
     k_true_resid<<<grid, 256, 0, s>>>(X, ldx, B, ldb, p, npoles, ndim, nx, ny, nz, ax[0], ax[1], ax[2], t,
-                                      tau_re, tau_im, part);
+                                      tau_re, tau_im, part, AX, ldax);
     return cudaGetLastError();
 }
 

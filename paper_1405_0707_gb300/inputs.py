@@ -11,6 +11,8 @@ sizes and times below are the synthetic stand-ins described in the design doc):
   tridiag-1d   A = t (n+1)^2 tridiag(1, -2, 1), n = 2000, t = 1, p = 4, m = 10, tol 1e-10
   cd2d-256     t (0.1 Laplacian_h - (1, 1) . grad_h) on a 256 x 256 interior grid,
                n = 65536, p = 8, t in {1e-3, 1e-2, 1e-1}, m = 10
+  toeplitz-1m  t T, T symmetric Toeplitz with first column a_0 = -2 - c, a_k = 1/(1+k)^2
+               (1 <= k <= 256), c = 0, n = 2^20, p = 16, t = 1, m = 10
 """
 from __future__ import annotations
 
@@ -23,10 +25,21 @@ WORKLOADS = {
                        seed=SEED_BASE + 1),
     "cd2d-256": dict(sides=(256, 256), diff=0.1, vel=(1.0, 1.0), t=(1e-3, 1e-2, 1e-1), p=8, m=10,
                      tol=1e-10, seed=SEED_BASE + 2),
+    "toeplitz-1m": dict(n=1 << 20, bw=256, c=0.0, t=(1.0,), p=16, m=10, tol=1e-13,
+                        seed=SEED_BASE + 3),
     # differentiation: L = ||r(tA) B - Y||_F^2, Y = r(t0 A) B0 (t0, B0 seeded perturbations)
     "cd2d-512-grad": dict(sides=(512, 512), diff=0.1, vel=(1.0, 1.0), t=(1e-2,), p=32, m=10,
                           tol=1e-10, seed=SEED_BASE + 5),
 }
+
+
+def toeplitz_column(bw, c=0.0):
+    """First column (a_0, .., a_bw) of the Toeplitz workload: a_0 = -2 - c, a_k = 1/(1+k)^2."""
+    a = np.empty(bw + 1)
+    a[0] = -2.0 - c
+    k = np.arange(1, bw + 1)
+    a[1:] = 1.0 / (1.0 + k) ** 2
+    return a
 
 
 def grad_target(n, p, seed, t):

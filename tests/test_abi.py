@@ -80,3 +80,44 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.expm_cf_coeffs(13, d, d, d, d) == N.EXPM_INVALID_ARG
     assert lib.expm_block(None, 1.0, None, 1, 1, None, 1, None) == N.EXPM_INVALID_ARG
     assert lib.expm_status_str(N.EXPM_BREAKDOWN) == b"block Arnoldi breakdown"
+
+
+def test_toeplitz_descriptor_checks():
+    """Toeplitz descriptors are validated on the host before any device work (Example 5.4's
+    operator must be symmetric negative definite): every case below is rejected."""
+    import ctypes as C
+    from paper_1405_0707_gb300 import _native as N
+    lib = N.load(build_if_missing=True)
+    opts = N.expm_opts()
+    opts.m, opts.max_cycles, opts.tol, opts.precision = 4, 10, 1e-10, 0
+    out = C.c_void_p()
+
+    def create(col, n, bw=None):
+        a = np.ascontiguousarray(np.asarray(col, dtype=np.float64))
+        op = N.expm_op_desc()
+        op.kind, op.ndim, op.n = N.EXPM_OP_TOEPLITZ_SYM, 1, n
+        op.toeplitz_col = a.ctypes.data_as(C.POINTER(C.c_double))
+        op.toeplitz_bw = len(a) - 1 if bw is None else bw
+        return lib.expm_plan_create(C.byref(op), 2, C.byref(opts), None, C.byref(out))
+
+    k = np.arange(1, 257)
+    good = np.r_[-2.0, 1.0 / (1.0 + k) ** 2]
+    assert create([-1.0, 0.6], 100) == N.EXPM_INVALID_ARG          # symbol max -1 + 1.2 > 0
+    st = create([-1.0, 0.49], 100)                                  # max -0.02: accepted (refined grid)
+    assert st != N.EXPM_INVALID_ARG
+    if st == N.EXPM_OK:
+        lib.expm_plan_destroy(out)
+    assert create([-1.0, 0.5], 100) == N.EXPM_INVALID_ARG          # max 0: semidefinite
+    assert create([0.5, 0.1], 100) == N.EXPM_INVALID_ARG           # a_0 >= 0
+    assert create(good, 200) == N.EXPM_INVALID_ARG                 # bw > n - 1
+    assert create([-2.0, np.nan], 100) == N.EXPM_INVALID_ARG       # not finite
+    assert create([-2.0], (1 << 21) + 1) == N.EXPM_INVALID_ARG     # beyond the FFT size limit
+    assert create([-2.0], 1) == N.EXPM_INVALID_ARG                 # n < 2
+    assert create(good, 1000, bw=-1) == N.EXPM_INVALID_ARG
+    # a NULL column
+    op = N.expm_op_desc()
+    op.kind, op.ndim, op.n, op.toeplitz_bw = N.EXPM_OP_TOEPLITZ_SYM, 1, 100, 3
+    assert lib.expm_plan_create(C.byref(op), 2, C.byref(opts), None, C.byref(out)) == N.EXPM_INVALID_ARG
+    # an unknown operator kind
+    op.kind = 7
+    assert lib.expm_plan_create(C.byref(op), 2, C.byref(opts), None, C.byref(out)) == N.EXPM_INVALID_ARG

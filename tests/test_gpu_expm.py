@@ -161,6 +161,42 @@ def test_nearly_dependent_rhs_takes_the_shifted_qr_pass(tab):
     assert rel(to_np(Zg), ref) < 1e-9
 
 
+@pytest.mark.parametrize("alg", [1, 2])
+def test_zero_and_repeated_rhs_columns(tab, alg):
+    """A zero column and an exactly repeated column in B (rank-deficient block): the zero
+    column stays zero through every block (zero Cholesky pivots are skipped) and the others
+    match the closed form; an invariant subspace is reported in info.breakdown, not as an
+    error."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    sides, diff, vel, t = (41, 35), 0.1, (1.0, 1.0), 0.1
+    n = 41 * 35
+    b = inputs.rhs(n, 2, 13)
+    B = np.column_stack([b[:, 0], np.zeros(n), b[:, 0], b[:, 1]])
+    plan = Plan(sides, diff, vel, p_max=4, m=6, tol=1e-12, max_cycles=200, algorithm=alg)
+    Zg, info = plan.expm_block(t, to_dev(B))
+    Zg = to_np(Zg)
+    ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+    assert info.converged == 1
+    assert np.all(Zg[:, 1] == 0.0)
+    assert rel(Zg, ref) < 1e-9
+
+
+def test_invariant_subspace_is_not_an_error(tab):
+    """B spanned by two eigenvectors of a 1-D Laplacian: the block Krylov space is invariant
+    after one step; the solve must finish (info.breakdown = 1) with the exact answer."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n, t = 200, 1e-3
+    j = np.arange(1, n + 1)
+    B = np.column_stack([np.sin(np.pi * j * 3 / (n + 1)), np.sin(np.pi * j * 7 / (n + 1))])
+    plan = Plan((n,), 1.0, (0.0,), p_max=2, m=5, tol=1e-12, max_cycles=20, algorithm=2)
+    Zg, info = plan.expm_block(t, to_dev(B))
+    ref = ops.exact_r_of_A_B((n,), 1.0, (0.0,), t, tab, B)
+    assert info.converged == 1 and info.breakdown == 1
+    assert rel(to_np(Zg), ref) < 1e-10
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("sides,diff,vel,t,p,alg", [((37, 29), 0.1, (1.0, 1.0), 0.1, 3, 1),
                                                     ((40, 33), 0.1, (1.0, 1.0), 1.0, 2, 2),
