@@ -1,7 +1,7 @@
 """Throughput of Z = r(tA) B (preconditioned shifted block FOM, Algorithm 2) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload cd2d-256|tridiag-1d]
+                    [--workload cd2d-256|tridiag-1d|toeplitz-1m]
 
 One step = one pass of the whole hot path over one batch: for the default workload
 (cd2d-256: 2-D convection-diffusion, 256 x 256 interior grid, n = 65536, p = 8 columns
@@ -10,6 +10,9 @@ i.e. 24 right-hand-side columns.  The metric is RHS columns per second (higher i
 better).  Inputs are resident in HBM when the timed region starts; before every timed
 step a 512 MB buffer is written to flush the 129 MB L2 (the working set, about 60 MB,
 would otherwise stay L2-resident across steps), outside the event-timed interval.
+
+--workload toeplitz-1m times the symmetric Toeplitz workload (n = 2^20, bandwidth 256,
+p = 16, t = 1; products by circulant embedding and the four-step FP64 FFT).
 
 Multi-GPU: the path does not shard (the block Krylov space couples the p columns), so
 N > 1 runs N independent replicas, one per rank, each on its own seeded batch ("weak"
@@ -42,7 +45,9 @@ KERNEL_OF = {"gemm": "k_gemm (DST-I transforms of the exact inverse, FP64)",
              "stencil": "k_cd_apply (stencil W = tA V, FP64)",
              "update": "k_update_z (Z += V_{m+1} Wc, FP64)",
              "tridiag": "k_tridiag_lines (Thomas line solves, FP64)",
-             "qr": "k_chol/k_trsm (Cholesky QR, FP64)"}
+             "qr": "k_chol/k_trsm (Cholesky QR, FP64)",
+             "fft": "k_fft_cols/k_fft_rows (four-step FFT Toeplitz product, FP64)",
+             "gsf": "k_fft_cols/k_fft_rows (Gohberg-Semencul inverse, FP64)"}
 
 
 def _hbm_peak():
@@ -55,17 +60,38 @@ def _hbm_peak():
 HBM_PEAK_GBS = _hbm_peak()
 
 
-def algorithmic_work(sides, p, m, cycles, algs):
-    """(flops, bytes) per step of every kernel class, from the algorithm's own counts:
-    minimum traffic (each operand read once per pass, results written once)."""
+def workload_n(w):
+    if "n" in w:
+        return int(w["n"])
     n = 1
-    for s_ in sides:
+    for s_ in w["sides"]:
         n *= s_
+    return n
+
+
+def fft_size(w):
+    """FFT length of the Toeplitz embedding: the power of two >= max(n + bw, 2n), >= 64."""
+    n, bw = int(w["n"]), int(w["bw"])
+    N = 64
+    while N < max(n + bw, 2 * n):
+        N *= 2
+    return N
+
+
+def algorithmic_work(w, p, m, cycles, algs):
+    """(flops, bytes) per step of every kernel class, from the algorithm's own counts:
+    minimum traffic (each operand read once per pass, results written once).  FFTs count
+    5 N log2 N flops per complex transform of length N and two passes over the data per
+    transform (four-step), 16 bytes per complex element read and written per pass."""
+    import math
+    n = workload_n(w)
+    toe = "n" in w
+    sides = w.get("sides", (n,))
     nx = sides[0]
     trans = 1
     for s_ in sides[1:]:
         trans *= s_
-    out = {k: [0.0, 0.0] for k in ("gemm", "cgs", "stencil", "update", "tridiag", "qr")}
+    out = {k: [0.0, 0.0] for k in ("gemm", "cgs", "stencil", "update", "tridiag", "qr", "fft", "gsf")}
     for t, c in cycles.items():
         alg = algs[t]
         steps = c * m
@@ -76,7 +102,14 @@ def algorithmic_work(sides, p, m, cycles, algs):
         out["qr"][1] += steps * 8.0 * 6.0 * n * p
         out["update"][0] += c * 2.0 * n * (m + 1) * p * p
         out["update"][1] += c * 8.0 * (n * (m + 1) * p + 2.0 * n * p)
-        if alg == 2:
+        if toe:
+            N = fft_size(w)
+            nseq = (p + 1) // 2
+            per_tf = 5.0 * N * math.log2(N)
+            key, ntf = ("gsf", 6) if alg == 2 else ("fft", 2)
+            out[key][0] += steps * nseq * (ntf * per_tf + 6.0 * N)
+            out[key][1] += steps * nseq * ntf * 2 * 2 * 16.0 * N
+        elif alg == 2:
             # per apply: forward + inverse transform along every axis but x (2-D case)
             out["gemm"][0] += steps * 2 * 2.0 * nx * trans * (sum(sides[1:]) if len(sides) > 1 else 0) * p
             out["gemm"][1] += steps * 2 * 8.0 * 2.0 * n * p
@@ -170,6 +203,15 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- our arm
+def make_plan(w, precision, stream=None, **kw):
+    from paper_1405_0707_gb300 import Plan, inputs
+    args = dict(p_max=w["p"], m=w["m"], tol=w["tol"], max_cycles=400, stream=stream, precision=precision)
+    args.update(kw)
+    if "n" in w:
+        return Plan.toeplitz(inputs.toeplitz_column(w["bw"], w["c"]), w["n"], **args)
+    return Plan(w["sides"], w["diff"], w["vel"], **args)
+
+
 def traffic_record(kernel):
     """ncu DRAM bytes per launch recorded in profiles/ncu_traffic.json, or None when the
     kernel's source changed since the capture (sha256 of the source file)."""
@@ -200,13 +242,13 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
     w = inputs.WORKLOADS[args.workload]
-    sides, p, m = w["sides"], w["p"], w["m"]
-    n = int(np.prod(sides))
+    p, m = w["p"], w["m"]
+    n = workload_n(w)
+    sides = w.get("sides", (n,))
     times = w["t"]
     N.load()
     stream = torch.cuda.Stream(device=dev)
-    plans = {prec: Plan(sides, w["diff"], w["vel"], p_max=p, m=m, tol=w["tol"], max_cycles=400,
-                        stream=stream, precision=prec) for prec in ("mixed", "fp64")}
+    plans = {prec: make_plan(w, prec, stream) for prec in ("mixed", "fp64")}
     Bh = inputs.rhs(n, p, w["seed"] + 1000 * rank)
     with torch.cuda.stream(stream):
         B = inputs.to_device_colmajor(Bh, device=dev)
@@ -289,7 +331,12 @@ def run_ours(args):
     cycles, algs = res[head]["cycles"], res[head]["algs"]
     # rooflines: analytic algorithmic flops / bytes of every kernel class over the profiled
     # pass, divided by its event-timed duration
-    alg_work = algorithmic_work(sides, p, m, dict(zip(times, cycles)), dict(zip(times, algs)))
+    alg_work = algorithmic_work(w, p, m, dict(zip(times, cycles)), dict(zip(times, algs)))
+    if "n" in w:
+        # the Toeplitz products and inverses are timed in the stencil / gemm stages
+        prof = dict(prof)
+        prof["fft"] = prof.pop("stencil", (0.0, 0))
+        prof["gsf"] = prof.pop("gemm", (0.0, 0))
     roofs = {}
     for k, (fl, by) in alg_work.items():
         ms_k, n_k = prof.get(k, (0.0, 0))
@@ -330,6 +377,9 @@ def run_ours(args):
         "dtype": "f32+f64" if head == "mixed" else "f64",
         "data": "synthetic (seeded N(0,1) right-hand sides; operator from its definition)",
         "config": {"workload": args.workload, "n": n, "grid": list(sides), "p": p, "m": m,
+                   "operator": ("symmetric Toeplitz, bandwidth %d, FFT length %d" % (w["bw"], fft_size(w))
+                                if "n" in w else "2-D convection-diffusion stencil" if len(sides) == 2
+                                else "%d-D convection-diffusion stencil" % len(sides)),
                    "t": list(times), "tol": w["tol"], "nu": 14, "precision": head,
                    "rel_err_vs_fp64_gpu": rel_err,
                    "columns_per_step": len(times) * p, "cycles_per_t": cycles,
@@ -369,12 +419,43 @@ def run_ours(args):
 def auto_algorithm(workload, t):
     """The library's AUTO rule, restated on the host: Algorithm 2 iff the Gershgorin bound
     of ||tA|| is >= 50 max|tau| (eq. (43)).  The pole modulus comes from the stored table."""
+    import numpy as np
+
     from oracle import cf
     from paper_1405_0707_gb300 import inputs
     w = inputs.WORKLOADS[workload]
-    bound = t * sum(4.0 * w["diff"] * (s + 1) ** 2 for s in w["sides"])
+    if "n" in w:
+        bound = t * np.abs(inputs.toeplitz_column(w["bw"], w["c"])).sum() * 2
+    else:
+        bound = t * sum(4.0 * w["diff"] * (s + 1) ** 2 for s in w["sides"])
     taumax = max(abs(z) for z in cf.load_table()["tau"])
     return 2 if bound >= 50.0 * taumax else 1
+
+
+TOEPLITZ_SAMPLE_ROWS = 1 << 17
+
+
+def oracle_toeplitz_cycle(workload, t, alg):
+    """One restart cycle of the oracle (Algorithm 1 with scipy's FFT product, or Algorithm 2
+    with the Gohberg-Semencul inverse) on the Toeplitz workload's column and bandwidth with
+    n = 2^17 rows (1/8 of the full order): (seconds, rows)."""
+    import numpy as np
+
+    from oracle import cf, psbfom, toeplitz as TZ
+    from paper_1405_0707_gb300 import inputs
+    w = inputs.WORKLOADS[workload]
+    n = min(TOEPLITZ_SAMPLE_ROWS, int(w["n"]))
+    a = inputs.toeplitz_column(w["bw"], w["c"])
+    col = np.zeros(n)
+    col[:len(a)] = a
+    B = inputs.rhs(n, w["p"], w["seed"])
+    t0 = time.perf_counter()
+    if alg == 2:
+        x = TZ.gsf_generator(col)
+        psbfom.psbfom(lambda V: TZ.gsf_apply(x, V, t), B, cf.load_table(), m=w["m"], fixed_cycles=1)
+    else:
+        psbfom.sbfom(lambda V: TZ.matvec(col, V, t), B, cf.load_table(), m=w["m"], fixed_cycles=1)
+    return time.perf_counter() - t0, n
 
 
 def oracle_sample(workload, t, alg):
@@ -405,6 +486,18 @@ def cpu_baseline(workload, algs, gpu_cycles, budget_s=32.0, sec_per_cycle=2.8):
     ~budget_s (at least one)."""
     from paper_1405_0707_gb300 import inputs
     w = inputs.WORKLOADS[workload]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    if "n" in w:
+        t = w["t"][0]
+        alg = algs.get(t, auto_algorithm(workload, t))
+        dt, rows = oracle_toeplitz_cycle(workload, t, alg)
+        cyc = gpu_cycles.get(t, 1)
+        sec = dt * (w["n"] / rows) * cyc
+        return {"value": round(w["p"] / sec, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"one restart cycle of the oracle (Algorithm {alg}, m = {w['m']}, p = {w['p']}) "
+                          f"on n = {rows} rows of the same Toeplitz column ({dt:.1f} s), scaled by "
+                          f"n / {rows} = {w['n'] // rows} (its cost per cycle grows at least linearly "
+                          f"in n) and by the {cyc} cycles the GPU path needed"}
     tot, cols, done, est = 0.0, 0, [], 0.0
     for t in sorted(w["t"], key=lambda x: gpu_cycles.get(x, 0)):
         e = sec_per_cycle * gpu_cycles.get(t, 1) + 2.0
@@ -415,7 +508,6 @@ def cpu_baseline(workload, algs, gpu_cycles, budget_s=32.0, sec_per_cycle=2.8):
         tot += dt
         cols += p
         done.append({"t": t, "algorithm": algs.get(t), "s": round(dt, 2), "cycles": info["cycles"]})
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": round(cols / tot, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"complete oracle solves for t in {[d['t'] for d in done]} of "
                       f"{list(w['t'])} (p = {w['p']} each; numpy/scipy with their default "
@@ -430,6 +522,9 @@ def run_reference(args):
     w = inputs.WORKLOADS[args.workload]
     t = min(w["t"])          # the cheapest solve of the workload keeps each step bounded
     alg = auto_algorithm(args.workload, t)
+    if "n" in w:
+        run_reference_toeplitz(args, w, t, alg)
+        return
     for _ in range(args.warmup):
         oracle_sample(args.workload, t, alg)
     tot, cols = 0.0, 0
@@ -453,17 +548,46 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_toeplitz(args, w, t, alg):
+    """Reference arm on the Toeplitz workload: each step one oracle restart cycle on 2^17 rows,
+    scaled to the full order; the cycle count of a full solve is the oracle's own (2 for
+    Algorithm 1 at tol 1e-13 on this operator, measured at n = 3000 and unchanged in n since
+    the spectrum lies in the symbol's range)."""
+    cycles = 2 if alg == 1 else 3
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        oracle_toeplitz_cycle(args.workload, t, alg)
+    tot = 0.0
+    rows = None
+    for _ in range(args.steps):
+        dt, rows = oracle_toeplitz_cycle(args.workload, t, alg)
+        tot += dt * (w["n"] / rows) * cycles
+    value = args.steps * w["p"] / tot
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"per step one oracle restart cycle (Algorithm {alg}, p = {w['p']}) on n = {rows} rows of "
+              f"the Toeplitz column, scaled by n / {rows} and by {cycles} cycles per solve")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": warm,
+            "ms_per_step": round(1e3 * tot / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "t": [t], "p": w["p"], "n": w["n"]},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_component(args):
     """Time one library entry point on the workload's shapes (for ncu captures)."""
     import numpy as np
     import torch
 
-    from paper_1405_0707_gb300 import Plan, inputs
+    from paper_1405_0707_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
-    n, p = int(np.prod(w["sides"])), w["p"]
+    n, p = workload_n(w), w["p"]
     t = args.t if args.t is not None else max(w["t"])
-    plan = Plan(w["sides"], w["diff"], w["vel"], p_max=p, m=w["m"], tol=w["tol"],
-                precision=args.precision)
+    plan = make_plan(w, args.precision, algorithm=2 if args.component == "prec" else 0)
     B = inputs.to_device_colmajor(inputs.rhs(n, p, w["seed"]))
     Wd = torch.empty((p, n), dtype=torch.float64, device="cuda").T
     fn = {"prec": lambda: plan.prec_apply(t, B, Wd), "stencil": lambda: plan.op_apply(t, B, Wd),

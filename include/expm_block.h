@@ -198,6 +198,47 @@ expm_status expm_block_host(expm_plan* plan, double t, const double* hB, int64_t
                             int p, double* hZ, int64_t ldz, expm_info* info);
 
 /* ---------------------------------------------------------------------------------
+ * expm_block_batched -- count independent calls of expm_block in one call: instance i
+ * computes dZ[i] = r(t[i] A_i) dB[i] with plans[i] (n_i x p[i], leading dimensions ldb[i],
+ * ldz[i]).  Instances of different order, width, time and operator family may be mixed.
+ * Each plan's restart cycles run on that plan's stream (as captured CUDA graphs when the
+ * stream is not the legacy default stream); the host keeps every instance's next cycle
+ * queued as soon as its stop test has been read, so instances on distinct streams overlap
+ * on the GPU.  The paper solves one problem at a time; this is a serving variant.
+ *   plans : host array of count distinct plans (one call per plan: the plan's workspace)
+ *   t, ldb, p, ldz : host arrays of count entries; dB, dZ: host arrays of device pointers
+ *   info  : host array of count expm_info (may be NULL)
+ * Returns the first hard error of any instance, else EXPM_NOT_CONVERGED if any instance
+ * stopped unconverged (its Z is still written), else EXPM_OK.  Synchronises every plan's
+ * stream.  Errors: EXPM_INVALID_ARG (bad argument of any instance, a repeated plan) and
+ * those of expm_block.
+ * ------------------------------------------------------------------------------ */
+expm_status expm_block_batched(expm_plan* const* plans, int count, const double* t,
+                               const double* const* dB, const int64_t* ldb, const int* p,
+                               double* const* dZ, const int64_t* ldz, expm_info* info);
+
+/* ---------------------------------------------------------------------------------
+ * expm_block_adjoint -- the adjoint of Z = r(tA) B for a loss L with G = dL/dZ:
+ *   dGB = dL/dB = r(tA)^T G = r(tA^T) G  (r has real coefficients), computed by the same
+ *         method on A^T: for EXPM_OP_CONV_DIFF the stencil with the velocity negated
+ *         (central differences), held in a companion plan created on the first call with
+ *         the plan's options (it allocates); a Toeplitz operator is its own transpose;
+ *   hGt = dL/dt = <G, A Z>  (d/dt e^{tA} B = A e^{tA} B; the derivative of the exponential
+ *         that r approximates), from the forward result Z.
+ * Nothing of the forward Krylov bases is kept: the backward solve recomputes its own.
+ *   dG  : device n x p (ldg), not modified;  1 <= p <= p_max
+ *   dZ  : device n x p (ldz), the forward result (needed only when hGt != NULL)
+ *   dGB : device n x p out (ldgb), or NULL to skip dL/dB; must not alias dG or dZ
+ *   hGt : host, 1 double out, or NULL to skip dL/dt
+ *   info: host out (may be NULL): the A^T solve's info
+ * Synchronises the plan's stream.  Errors: those of expm_block, EXPM_INVALID_ARG when both
+ * outputs are NULL.
+ * ------------------------------------------------------------------------------ */
+expm_status expm_block_adjoint(expm_plan* plan, double t, const double* dG, int64_t ldg, int p,
+                               const double* dZ, int64_t ldz, double* dGB, int64_t ldgb,
+                               double* hGt, expm_info* info);
+
+/* ---------------------------------------------------------------------------------
  * Component entry points (the hot path's kernels, exposed for parity tests and
  * measurement).  All are stream-ordered on the plan's stream and do not synchronise.
  *

@@ -31,7 +31,7 @@ EXPM_MAX_POLES = 16
 EXPORTS = ("expm_cf_coeffs", "expm_plan_create", "expm_plan_destroy", "expm_block",
            "expm_block_host", "expm_op_apply", "expm_prec_apply", "expm_arnoldi",
            "expm_plan_profile", "expm_plan_get_profile", "expm_status_str",
-           "expm_prec_apply_noalloc")
+           "expm_prec_apply_noalloc", "expm_block_batched", "expm_block_adjoint")
 STAGES = ("gemm", "tridiag", "cgs", "reduce", "qr", "poles", "update", "other", "stencil")
 
 
@@ -93,6 +93,12 @@ def load(build_if_missing: bool = False):
         f = getattr(lib, name)
         f.restype = C.c_int
         f.argtypes = [p, d, p, i64, i32, p, i64]
+    lib.expm_block_batched.restype = C.c_int
+    lib.expm_block_batched.argtypes = [C.POINTER(p), C.c_int, C.POINTER(d), C.POINTER(p),
+                                       C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(p), C.POINTER(i64),
+                                       C.POINTER(expm_info)]
+    lib.expm_block_adjoint.restype = C.c_int
+    lib.expm_block_adjoint.argtypes = [p, d, p, i64, i32, p, i64, p, i64, C.POINTER(d), C.POINTER(expm_info)]
     lib.expm_arnoldi.restype = C.c_int
     lib.expm_arnoldi.argtypes = [p, d, p, i64, i32, p, i64, p, i64]
     lib.expm_prec_apply_noalloc.restype = C.c_int
@@ -159,6 +165,29 @@ def expm_block_host(plan, t, hB, ldb, p, hZ, ldz, allow_not_converged=True):
     code = check(load().expm_block_host(plan, t, C.c_void_p(hB), ldb, p, C.c_void_p(hZ), ldz,
                                         C.byref(info)), "expm_block_host", allow)
     return code, info
+
+
+def expm_block_batched(plans, ts, dBs, ldbs, ps, dZs, ldzs, allow_not_converged=True):
+    """Independent solves in one call (see include/expm_block.h); returns (code, [info])."""
+    k = len(plans)
+    infos = (expm_info * k)()
+    arr = lambda T, xs: (T * k)(*xs)
+    allow = (EXPM_OK, EXPM_NOT_CONVERGED) if allow_not_converged else (EXPM_OK,)
+    code = check(load().expm_block_batched(
+        arr(C.c_void_p, [pl.value if isinstance(pl, C.c_void_p) else pl for pl in plans]), k,
+        arr(C.c_double, ts), arr(C.c_void_p, dBs), arr(C.c_int64, ldbs), arr(C.c_int, ps),
+        arr(C.c_void_p, dZs), arr(C.c_int64, ldzs), infos), "expm_block_batched", allow)
+    return code, list(infos)
+
+
+def expm_block_adjoint(plan, t, dG, ldg, p, dZ, ldz, dGB, ldgb, want_dt=True):
+    """(dL/dt or None, info); dL/dB written to dGB when dGB is not 0."""
+    info = expm_info()
+    gt = C.c_double()
+    check(load().expm_block_adjoint(plan, t, C.c_void_p(dG), ldg, p, C.c_void_p(dZ), ldz,
+                                    C.c_void_p(dGB), ldgb, C.byref(gt) if want_dt else None,
+                                    C.byref(info)), "expm_block_adjoint", (EXPM_OK, EXPM_NOT_CONVERGED))
+    return (gt.value if want_dt else None), info
 
 
 def expm_op_apply(plan, t, dV, ldv, p, dW, ldw):

@@ -127,6 +127,22 @@ class Plan:
         code, info = N.expm_block_host(self._h, float(t), hB.data_ptr(), ldb, p, hZ.data_ptr(), ldz)
         return hZ, info
 
+    def expm_block_adjoint(self, t, G, Z=None, want_dB=True, want_dt=True):
+        """Adjoint of Z = r(tA) B for G = dL/dZ: (dL/dB = r(tA^T) G or None, dL/dt = <G, A Z> or
+        None, info).  Z (the forward result) is needed for dL/dt."""
+        n, p = self.n, G.shape[1]
+        ldg = _check_colmajor(G, n, p, "G")
+        dGB = colmajor(n, p, device=G.device) if want_dB else None
+        if want_dt and Z is None:
+            raise ValueError("dL/dt needs the forward result Z")
+        ldz = _check_colmajor(Z, n, p, "Z") if Z is not None else n
+        gt, info = N.expm_block_adjoint(self._h, float(t), G.data_ptr(), ldg, p,
+                                        Z.data_ptr() if Z is not None else 0, ldz,
+                                        dGB.data_ptr() if dGB is not None else 0,
+                                        _check_colmajor(dGB, n, p, "dGB") if dGB is not None else n,
+                                        want_dt)
+        return dGB, gt, info
+
     def op_apply(self, t, V, W=None):
         n, p = self.n, V.shape[1]
         ldv = _check_colmajor(V, n, p, "V")
@@ -152,3 +168,16 @@ class Plan:
         N.expm_arnoldi(self._h, float(t), V1.data_ptr(), ldv, p, V.data_ptr(), V.stride(1),
                        H.data_ptr(), H.stride(1))
         return V, H
+
+
+def expm_block_batched(plans, ts, Bs, Zs=None):
+    """Independent solves Z_i = r(t_i A_i) B_i in one library call (each plan once; plans on
+    distinct streams overlap on the GPU).  Returns (list of Z, list of info)."""
+    if Zs is None:
+        Zs = [colmajor(pl.n, B.shape[1], device=B.device) for pl, B in zip(plans, Bs)]
+    ldbs = [_check_colmajor(B, pl.n, B.shape[1], "B") for pl, B in zip(plans, Bs)]
+    ldzs = [_check_colmajor(Z, pl.n, B.shape[1], "Z") for pl, B, Z in zip(plans, Bs, Zs)]
+    code, infos = N.expm_block_batched([pl._h for pl in plans], [float(t) for t in ts],
+                                       [B.data_ptr() for B in Bs], ldbs, [B.shape[1] for B in Bs],
+                                       [Z.data_ptr() for Z in Zs], ldzs)
+    return Zs, infos

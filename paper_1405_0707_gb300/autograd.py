@@ -9,8 +9,9 @@ For a loss L(Z) with G = dL/dZ:
   dL/dt = <G, A Z>                    d/dt e^{tA} B = A e^{tA} B; this is the derivative of
                                       the exponential that r approximates (it differs from
                                       the derivative of r(tA) B by the CF error of r').
-The backward pass is a fresh solve: nothing of the forward Krylov bases is stored (only Z,
-for dL/dt), so memory is that of one forward call.
+The backward pass is one call of the library's expm_block_adjoint: a fresh solve with A^T
+(nothing of the forward Krylov bases is stored, only Z for dL/dt, so memory is that of one
+forward call plus the companion plan of A^T) and the inner product on the device.
 """
 from __future__ import annotations
 
@@ -27,41 +28,31 @@ def _as_colmajor(X):
     return Y
 
 
-def transpose_plan(plan: Plan, **kw) -> Plan:
-    """A plan for A^T (same grid and diffusion, velocity negated), same options."""
-    opts = dict(p_max=plan.p_max, m=plan.m, tol=plan.tol, max_cycles=plan.max_cycles,
-                algorithm=plan.algorithm, precision=plan.precision)
-    opts.update(kw)
-    return Plan(plan.sides, plan.diff, tuple(-v for v in plan.vel), stream=plan.stream, **opts)
-
-
 class _ExpmBlock(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, t, B, plan, plan_T):
+    def forward(ctx, t, B, plan):
         tt = float(t)
         Z, info = plan.expm_block(tt, _as_colmajor(B.detach()))
         ctx.save_for_backward(Z)
-        ctx.plan, ctx.plan_T, ctx.t = plan, plan_T, tt
+        ctx.plan, ctx.t = plan, tt
         return Z
 
     @staticmethod
     def backward(ctx, G):
         (Z,) = ctx.saved_tensors
         G = _as_colmajor(G.detach())
-        dB = dt = None
-        if ctx.needs_input_grad[1]:
-            dB, _ = ctx.plan_T.expm_block(ctx.t, G)
-        if ctx.needs_input_grad[0]:
-            AZ = ctx.plan.op_apply(1.0, Z)                # A Z (t folded out)
-            dt = (G * AZ).sum().reshape(())
-        return dt, dB, None, None
+        want_dB, want_dt = bool(ctx.needs_input_grad[1]), bool(ctx.needs_input_grad[0])
+        if not (want_dB or want_dt):
+            return None, None, None
+        dB, gt, _ = ctx.plan.expm_block_adjoint(ctx.t, G, Z, want_dB=want_dB, want_dt=want_dt)
+        dt = torch.tensor(gt, dtype=torch.float64, device=G.device) if want_dt else None
+        return dt, dB, None
 
 
-def expm_block(t, B, plan: Plan, plan_T: Plan | None = None):
+def expm_block(t, B, plan: Plan):
     """Differentiable Z = r(tA) B.  t: 0-d float64 tensor (may require grad), B: (n, p)
-    float64 CUDA tensor (may require grad).  plan_T defaults to transpose_plan(plan)."""
-    if plan_T is None:
-        plan_T = transpose_plan(plan)
+    float64 CUDA tensor (may require grad).  The backward pass is one library call
+    (expm_block_adjoint): dL/dB by the method on A^T, dL/dt = <G, A Z> on the device."""
     if not torch.is_tensor(t):
         t = torch.tensor(float(t), dtype=torch.float64, device=B.device)
-    return _ExpmBlock.apply(t, B, plan, plan_T)
+    return _ExpmBlock.apply(t, B, plan)

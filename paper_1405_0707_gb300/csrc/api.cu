@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "internal.h"
 
@@ -400,53 +401,83 @@ GraphEntry* graph_for(expm_plan* P, double t, int p, int alg) {
     return &P->graphs.back();
 }
 
-expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int p, double* dZ,
-                      int64_t ldz, expm_info* info) {
+// State of one expm_block call between restart cycles.  run_block drives one call to the
+// end; expm_block_batched interleaves several calls on their plans' streams.
+struct RunState {
+    double t = 0.0;
+    const double* dB = nullptr;
+    int64_t ldb = 0;
+    int p = 0;
+    double* dZ = nullptr;
+    int64_t ldz = 0;
+    int alg = 0;
+    int cycles = 0;
+    bool converged = false;
+    bool done = false;
+    double normB = 0.0;
+    expm_status result = EXPM_OK;
+    GraphEntry* ge = nullptr;
+};
+
+// Steps 1-2 of the algorithm: R_i^0 = B = V_1 R for every pole; the cycle graph.
+expm_status run_begin(expm_plan* P, RunState& r) {
     cudaStream_t s = P->stream;
-    const int alg = choose_algorithm(P, t);
-    const int m = P->opts.m;
+    r.alg = choose_algorithm(P, r.t);
+    const int m = P->opts.m, p = r.p;
     const int64_t n = P->n, ld = P->ld;
     CK(cudaMemsetAsync(P->stat, 0, sizeof(double) * kStatDoubles, s));
     CK(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)P->ldH * m * P->p_max, s));
     LAUNCH(EXPM_STAGE_OTHER, launch_zero(P->Zacc, ld, n, p, s));
     if (P->opts.certify) LAUNCH(EXPM_STAGE_OTHER, launch_zero(P->Xcert, ld, n, 2 * P->npoles * p, s));
-    // Steps 1-2: R_i^0 = B = V_1 R for every pole
-    LAUNCH(EXPM_STAGE_OTHER, launch_copy(dB, ldb, P->W, ld, n, p, s));
+    LAUNCH(EXPM_STAGE_OTHER, launch_copy(r.dB, r.ldb, P->W, ld, n, p, s));
     expm_status st = qr_block(P, p, P->V, ld, false, 0, 0, P->stat + 16, false);
     if (st != EXPM_OK) return st;
     LAUNCH(EXPM_STAGE_OTHER, launch_init_S(sm(P, kOffRt), p, P->npoles, P->S, s));
-    double* tau_re = sm(P, kOffTau);
-    int cycles = 0;
-    bool converged = false;
-    double normB = 0.0;
-    expm_status result = EXPM_OK;
     // graph of one restart cycle, cached per (algorithm, p, t)
-    GraphEntry* ge = nullptr;
-    if (P->use_graphs && !P->prof && P->stream != nullptr) ge = graph_for(P, t, p, alg);
-    while (true) {
-        ++cycles;
-        if (ge) {
-            CK(cudaGraphLaunch(ge->exec, s));
-            P->launches += ge->launches;
-            for (int k = 0; k < EXPM_NSTAGES; ++k) P->stage_launches[k] += ge->stage_launches[k];
-        } else {
-            st = issue_cycle(P, t, p, alg);
-            if (st != EXPM_OK) return st;
-        }
-        CK(cudaStreamSynchronize(s));
-        prof_flush(P);
-        st = check_flags(P->hpin);
-        if (st != EXPM_OK) { result = st; break; }
-        normB = std::sqrt(P->hpin[16]);
-        double mx = 0.0;
-        for (int i = 0; i < P->npoles; ++i) mx = std::max(mx, P->hpin[i]);
-        converged = mx <= P->opts.tol * normB;
-        const bool done = (P->opts.fixed_cycles > 0) ? cycles >= P->opts.fixed_cycles
-                                                     : (converged || cycles >= P->opts.max_cycles);
-        if (done) break;
+    r.ge = nullptr;
+    if (P->use_graphs && !P->prof && P->stream != nullptr) r.ge = graph_for(P, r.t, p, r.alg);
+    return EXPM_OK;
+}
+
+// Issue one restart cycle (graph or direct launches) and mark its end with the plan's event.
+expm_status run_issue(expm_plan* P, RunState& r) {
+    cudaStream_t s = P->stream;
+    ++r.cycles;
+    if (r.ge) {
+        CK(cudaGraphLaunch(r.ge->exec, s));
+        P->launches += r.ge->launches;
+        for (int k = 0; k < EXPM_NSTAGES; ++k) P->stage_launches[k] += r.ge->stage_launches[k];
+    } else {
+        expm_status st = issue_cycle(P, r.t, r.p, r.alg);
+        if (st != EXPM_OK) return st;
     }
-    // Z = omega_0 B + Z_acc
-    LAUNCH(EXPM_STAGE_OTHER, launch_axpby(P->omega0, dB, ldb, 1.0, P->Zacc, ld, dZ, ldz, n, p, s));
+    CK(cudaEventRecord(P->cycle_ev, s));
+    return EXPM_OK;
+}
+
+// After a cycle's work has completed: flags, eq. (49) norms, the stop test.
+void run_check(expm_plan* P, RunState& r) {
+    prof_flush(P);
+    const expm_status st = check_flags(P->hpin);
+    if (st != EXPM_OK) {
+        r.result = st;
+        r.done = true;
+        return;
+    }
+    r.normB = std::sqrt(P->hpin[16]);
+    double mx = 0.0;
+    for (int i = 0; i < P->npoles; ++i) mx = std::max(mx, P->hpin[i]);
+    r.converged = mx <= P->opts.tol * r.normB;
+    r.done = (P->opts.fixed_cycles > 0) ? r.cycles >= P->opts.fixed_cycles
+                                        : (r.converged || r.cycles >= P->opts.max_cycles);
+}
+
+// Z = omega_0 B + Z_acc (eq. (11) with the conjugate pairs folded), certify, info.
+expm_status run_finish(expm_plan* P, RunState& r, expm_info* info) {
+    cudaStream_t s = P->stream;
+    const int p = r.p, m = P->opts.m;
+    const int64_t n = P->n, ld = P->ld;
+    LAUNCH(EXPM_STAGE_OTHER, launch_axpby(P->omega0, r.dB, r.ldb, 1.0, P->Zacc, ld, r.dZ, r.ldz, n, p, s));
     double true_res[EXPM_MAX_POLES] = {0};
     if (P->opts.certify) {
         // the true FP64 residuals ||B - (tA - tau_i I) X_i||_F of every pole (eq. (3))
@@ -454,13 +485,13 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
         const double* AX = nullptr;
         if (P->toeplitz) {
             // tA X_i for the real and imaginary columns of every pole by FFT products
-            st = toeplitz_matvec(P, t, P->Xcert, ld, 2 * P->npoles * p, P->Acert, ld, EXPM_STAGE_OTHER);
+            expm_status st = toeplitz_matvec(P, r.t, P->Xcert, ld, 2 * P->npoles * p, P->Acert, ld, EXPM_STAGE_OTHER);
             if (st != EXPM_OK) return st;
             AX = P->Acert;
         }
         const int nx = P->toeplitz ? (int)n : P->ax[0].N;
-        LAUNCH(EXPM_STAGE_OTHER, launch_true_resid(P->Xcert, ld, dB, ldb, p, P->npoles, P->ndim, nx, P->ax[1].N,
-                                                   P->ax[2].N, P->ax, t, tau, tau + EXPM_MAX_POLES, P->rcert, s,
+        LAUNCH(EXPM_STAGE_OTHER, launch_true_resid(P->Xcert, ld, r.dB, r.ldb, p, P->npoles, P->ndim, nx, P->ax[1].N,
+                                                   P->ax[2].N, P->ax, r.t, tau, tau + EXPM_MAX_POLES, P->rcert, s,
                                                    AX, ld));
         const int nb = true_resid_blocks(n);
         CK(cudaMemcpyAsync(P->hcert, P->rcert, sizeof(double) * (size_t)P->npoles * nb, cudaMemcpyDeviceToHost, s));
@@ -473,21 +504,40 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
     }
     if (info) {
         std::memset(info, 0, sizeof(*info));
-        info->cycles = cycles;
-        info->block_steps = cycles * m;
-        info->matvecs = (int64_t)cycles * m * p;
-        info->converged = converged ? 1 : 0;
+        info->cycles = r.cycles;
+        info->block_steps = r.cycles * m;
+        info->matvecs = (int64_t)r.cycles * m * p;
+        info->converged = r.converged ? 1 : 0;
         info->npoles = P->npoles;
         info->breakdown = reinterpret_cast<const int*>(P->hpin + 24)[1] ? 1 : 0;
         for (int i = 0; i < P->npoles; ++i) info->resid[i] = P->hpin[i];
-        info->normB = normB;
-        info->algorithm = alg;
-        info->normA_bound = norm_bound(P, t);
+        info->normB = r.normB;
+        info->algorithm = r.alg;
+        info->normA_bound = norm_bound(P, r.t);
         for (int i = 0; i < P->npoles; ++i) info->true_resid[i] = true_res[i];
     }
-    if (result != EXPM_OK) return result;
+    if (r.result != EXPM_OK) return r.result;
     if (P->opts.fixed_cycles > 0) return EXPM_OK;
-    return converged ? EXPM_OK : EXPM_NOT_CONVERGED;
+    return r.converged ? EXPM_OK : EXPM_NOT_CONVERGED;
+}
+
+expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int p, double* dZ,
+                      int64_t ldz, expm_info* info) {
+    RunState r;
+    r.t = t;
+    r.dB = dB;
+    r.ldb = ldb;
+    r.p = p;
+    r.dZ = dZ;
+    r.ldz = ldz;
+    expm_status st = run_begin(P, r);
+    if (st != EXPM_OK) return st;
+    while (!r.done) {
+        if ((st = run_issue(P, r)) != EXPM_OK) return st;
+        CK(cudaStreamSynchronize(P->stream));
+        run_check(P, r);
+    }
+    return run_finish(P, r, info);
 }
 
 void free_plan(expm_plan* P) {
@@ -538,7 +588,11 @@ void free_plan(expm_plan* P) {
     cudaFree(P->S);
     cudaFree(P->Wc_slots);
     cudaFree(P->stat);
+    cudaFree(P->dotpart);
     if (P->hpin) cudaFreeHost(P->hpin);
+    if (P->hdot) cudaFreeHost(P->hdot);
+    if (P->cycle_ev) cudaEventDestroy(P->cycle_ev);
+    if (P->adj) free_plan(P->adj);
     for (auto& e : P->ev) cudaEventDestroy(e);
     for (auto& g : P->graphs) cudaGraphExecDestroy(g.exec);
     delete P;
@@ -857,6 +911,9 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     if (poles_smem_bytes(mpm, p_max) == 0)   // elimination does not fit in shared memory
         ok = ok && dalloc(&P->poles, (size_t)P->npoles * ((size_t)mpm * mpm + (size_t)mpm * p_max) * 2);
     ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hpin), sizeof(double) * kStatDoubles) == cudaSuccess;
+    ok = ok && dalloc(&P->dotpart, (size_t)dot_blocks() * p_max) &&
+         cudaMallocHost(reinterpret_cast<void**>(&P->hdot), sizeof(double) * dot_blocks() * p_max) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&P->cycle_ev, cudaEventDisableTiming) == cudaSuccess;
     const bool mixed = opts->precision == EXPM_PREC_MIXED;
     if (!toeplitz) {
         // preconditioner tables: every axis but x is transformed
@@ -961,6 +1018,126 @@ expm_status expm_block_host(expm_plan* plan, double t, const double* hB, int64_t
                          cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return st;
+}
+
+expm_status expm_block_batched(expm_plan* const* plans, int count, const double* t, const double* const* dB,
+                               const int64_t* ldb, const int* p, double* const* dZ, const int64_t* ldz,
+                               expm_info* info) {
+    if (count < 1 || !plans || !t || !dB || !ldb || !p || !dZ || !ldz) return EXPM_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        const expm_status st = validate_block_args(plans[i], t[i], dB[i], ldb[i], p[i], dZ[i], ldz[i]);
+        if (st != EXPM_OK) return st;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return EXPM_INVALID_ARG;   // one call per plan (its workspace)
+    }
+    std::vector<RunState> rs(count);
+    std::vector<char> active(count, 0);
+    std::vector<expm_status> status(count, EXPM_OK);
+    int left = 0;
+    for (int i = 0; i < count; ++i) {
+        RunState& r = rs[i];
+        r.t = t[i];
+        r.dB = dB[i];
+        r.ldb = ldb[i];
+        r.p = p[i];
+        r.dZ = dZ[i];
+        r.ldz = ldz[i];
+        expm_status st = run_begin(plans[i], r);
+        if (st == EXPM_OK) st = run_issue(plans[i], r);
+        if (st != EXPM_OK) {
+            status[i] = st;
+            continue;
+        }
+        active[i] = 1;
+        ++left;
+    }
+    // every plan's cycles run on its own stream; poll the cycle events and keep each
+    // instance's next cycle queued as soon as its stop test has been read
+    while (left > 0) {
+        bool progress = false;
+        for (int i = 0; i < count; ++i) {
+            if (!active[i]) continue;
+            expm_plan* P = plans[i];
+            const cudaError_t q = cudaEventQuery(P->cycle_ev);
+            if (q == cudaErrorNotReady) continue;
+            progress = true;
+            expm_status st = EXPM_OK;
+            if (q != cudaSuccess) {
+                st = EXPM_CUDA_ERROR;
+            } else {
+                run_check(P, rs[i]);
+                if (!rs[i].done) {
+                    st = run_issue(P, rs[i]);
+                    if (st == EXPM_OK) continue;
+                } else {
+                    st = run_finish(P, rs[i], info ? &info[i] : nullptr);
+                }
+            }
+            status[i] = st;
+            active[i] = 0;
+            --left;
+        }
+        if (!progress) std::this_thread::yield();
+    }
+    for (int i = 0; i < count; ++i)
+        if (cudaStreamSynchronize(plans[i]->stream) != cudaSuccess && status[i] == EXPM_OK) status[i] = EXPM_CUDA_ERROR;
+    // first hard error, else NOT_CONVERGED if any instance stopped unconverged
+    expm_status worst = EXPM_OK;
+    for (int i = 0; i < count; ++i) {
+        if (status[i] != EXPM_OK && status[i] != EXPM_NOT_CONVERGED) return status[i];
+        if (status[i] == EXPM_NOT_CONVERGED) worst = EXPM_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+expm_status expm_block_adjoint(expm_plan* plan, double t, const double* dG, int64_t ldg, int p,
+                               const double* dZ, int64_t ldz, double* dGB, int64_t ldgb, double* hGt,
+                               expm_info* info) {
+    if (!plan || !dG || (!dGB && !hGt) || (hGt && !dZ)) return EXPM_INVALID_ARG;
+    expm_status st = validate_block_args(plan, t, dG, ldg, p, dGB ? (const void*)dGB : (const void*)dZ,
+                                         dGB ? ldgb : ldz);
+    if (st != EXPM_OK) return st;
+    if (hGt && (ldz < plan->n || dZ == dGB)) return EXPM_INVALID_ARG;
+    expm_plan* P = plan;
+    cudaStream_t s = P->stream;
+    const int64_t n = P->n, ld = P->ld;
+    if (hGt) {
+        // dL/dt = <G, A Z> (t folded out): A Z into T1, then per-column dot products with
+        // fixed-order partial sums
+        if ((st = op_apply_internal(P, 1.0, dZ, ldz, p, P->T1, ld)) != EXPM_OK) return st;
+        const int nb = dot_blocks();
+        for (int c = 0; c < p; ++c)
+            LAUNCH(EXPM_STAGE_OTHER, launch_dot_partial(dG + (int64_t)c * ldg, P->T1 + (int64_t)c * ld, n,
+                                                        P->dotpart + (int64_t)c * nb, s));
+        CK(cudaMemcpyAsync(P->hdot, P->dotpart, sizeof(double) * (size_t)nb * p, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double acc = 0.0;
+        for (int c = 0; c < p; ++c) {
+            double sc = 0.0;
+            for (int b = 0; b < nb; ++b) sc += P->hdot[(size_t)c * nb + b];
+            acc += sc;
+        }
+        *hGt = acc;
+    }
+    if (!dGB) {
+        if (info) std::memset(info, 0, sizeof(*info));
+        return EXPM_OK;
+    }
+    // dL/dB = r(tA)^T G = r(tA^T) G by the same method on A^T
+    expm_plan* PT = P;
+    if (!P->toeplitz) {
+        if (!P->adj) {
+            expm_op_desc opT = P->op;
+            for (int d = 0; d < 3; ++d) opT.vel[d] = -opT.vel[d];
+            st = expm_plan_create(&opT, P->p_max, &P->opts, P->stream, &P->adj);
+            if (st != EXPM_OK) {
+                P->adj = nullptr;
+                return st;
+            }
+        }
+        PT = P->adj;
+    }
+    return run_block(PT, t, dG, ldg, p, dGB, ldgb, info);
 }
 
 expm_status expm_op_apply(expm_plan* plan, double t, const double* dV, int64_t ldv, int p,

@@ -167,6 +167,10 @@ struct expm_plan_s {
     double* Wc_slots = nullptr;// per-pole (m+1)p x p update coefficients
     double* stat = nullptr;    // device status block: res[16], normsq, flags (ints)
     double* hpin = nullptr;    // pinned host mirror of stat
+    cudaEvent_t cycle_ev = nullptr;   // recorded after every restart cycle
+    double* dotpart = nullptr; // dot_blocks() x p_max partial sums (adjoint's <G, A Z>)
+    double* hdot = nullptr;    // pinned host mirror of dotpart
+    expm_plan_s* adj = nullptr;// plan of A^T for the adjoint (created on first use)
     double* Zst = nullptr;     // ld x p_max staging for the host entry point
     // certify mode: per-pole solutions (real/imag columns), Z_i, coefficient matrix, partials
     double* Xcert = nullptr;   // ld x 2 npoles p_max

@@ -23,26 +23,25 @@ def tab():
 def _loss_setup(sides, diff, vel, t, p, seed, precision, m=8, tol=1e-13):
     torch = need_gpu()
     from paper_1405_0707_gb300 import Plan
-    from paper_1405_0707_gb300.autograd import expm_block, transpose_plan
+    from paper_1405_0707_gb300.autograd import expm_block
     n = int(np.prod(sides))
     B = inputs.rhs(n, p, seed)
     t0, B0 = inputs.grad_target(n, p, seed, t)
     plan = Plan(sides, diff, vel, p_max=p, m=m, tol=tol, max_cycles=400, precision=precision)
-    plan_T = transpose_plan(plan)
     Y, _ = plan.expm_block(t0, to_dev(B0))
     Y = Y.clone()
 
     def loss(tv, Bt):
-        Z = expm_block(tv, Bt, plan, plan_T)
+        Z = expm_block(tv, Bt, plan)
         return ((Z - Y) ** 2).sum(), Z
-    return torch, plan, plan_T, B, Y, loss
+    return torch, plan, B, Y, loss
 
 
 @pytest.mark.parametrize("sides,diff,vel,t,p,precision", [((37, 29), 0.1, (1.0, 1.0), 0.1, 3, "fp64"),
                                                           ((40, 33), 0.1, (1.0, -0.5), 1.0, 2, "mixed"),
                                                           ((11, 9, 7), 1.0, (3.0, -2.0, 1.0), 0.3, 2, "fp64")])
 def test_adjoint_matches_closed_form_and_finite_differences(tab, sides, diff, vel, t, p, precision):
-    torch, plan, plan_T, B, Y, loss = _loss_setup(sides, diff, vel, t, p, 17, precision)
+    torch, plan, B, Y, loss = _loss_setup(sides, diff, vel, t, p, 17, precision)
     tv = torch.tensor(t, dtype=torch.float64, device="cuda", requires_grad=True)
     Bt = to_dev(B).clone().requires_grad_(True)
     L, Z = loss(tv, Bt)
@@ -75,8 +74,8 @@ def test_differentiation_workload_512(tab):
     t = 1e-2, mixed precision (FP32 transforms refined to FP64, FP64 projected solves)."""
     w = inputs.WORKLOADS["cd2d-512-grad"]
     t = w["t"][0]
-    torch, plan, plan_T, B, Y, loss = _loss_setup(w["sides"], w["diff"], w["vel"], t, w["p"],
-                                                  w["seed"], "mixed", m=w["m"], tol=w["tol"])
+    torch, plan, B, Y, loss = _loss_setup(w["sides"], w["diff"], w["vel"], t, w["p"],
+                                          w["seed"], "mixed", m=w["m"], tol=w["tol"])
     tv = torch.tensor(t, dtype=torch.float64, device="cuda", requires_grad=True)
     Bt = to_dev(B).clone().requires_grad_(True)
     L, Z = loss(tv, Bt)
@@ -92,3 +91,48 @@ def test_differentiation_workload_512(tab):
         Lm, _ = loss(torch.tensor(t - ht, dtype=torch.float64, device="cuda"), to_dev(B))
     fdt = (float(Lp) - float(Lm)) / (2 * ht)
     assert abs(fdt - float(tv.grad)) <= 1e-5 * abs(fdt), (fdt, float(tv.grad))
+
+
+def test_adjoint_entry_point_parts(tab):
+    """expm_block_adjoint directly: dL/dt alone equals <G, A Z> computed on the host from the
+    oracle's operator; dL/dB alone equals the closed form on A^T; both outputs together
+    agree with the separate calls."""
+    torch = need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    sides, diff, vel, t, p = (33, 27), 0.1, (1.0, -1.0), 0.05, 3
+    n = int(np.prod(sides))
+    plan = Plan(sides, diff, vel, p_max=p, m=8, tol=1e-13)
+    B = inputs.rhs(n, p, 51)
+    G = inputs.rhs(n, p, 52)
+    Z, _ = plan.expm_block(t, to_dev(B))
+    Gd = to_dev(G)
+    _, gt, _ = plan.expm_block_adjoint(t, Gd, Z, want_dB=False)
+    A = ops.cd_matrix(sides, diff, vel, 1.0)
+    ref_t = float(np.sum(G * (A @ to_np(Z))))
+    assert abs(gt - ref_t) <= 1e-12 * abs(ref_t) + 1e-12
+    dB, none, _ = plan.expm_block_adjoint(t, Gd, None, want_dt=False)
+    assert none is None
+    ref_B = ops.exact_r_of_A_B(sides, diff, tuple(-v for v in vel), t, tab, G)
+    assert rel(to_np(dB), ref_B) <= 1e-10
+    dB2, gt2, _ = plan.expm_block_adjoint(t, Gd, Z)
+    assert np.array_equal(to_np(dB2), to_np(dB)) and gt2 == gt
+
+
+def test_adjoint_toeplitz_is_self_adjoint(tab):
+    """A symmetric Toeplitz operator is its own transpose: dL/dB = r(tT) G, checked against
+    the forward call on G, and dL/dt against <G, T Z> from the oracle's product."""
+    need_gpu()
+    from oracle import toeplitz as TZ
+    from paper_1405_0707_gb300 import Plan
+    n, p, t = 3000, 2, 1.0
+    a = inputs.toeplitz_column(256)
+    plan = Plan.toeplitz(a, n, p_max=p, tol=1e-13)
+    B, G = inputs.rhs(n, p, 53), inputs.rhs(n, p, 54)
+    Z, _ = plan.expm_block(t, to_dev(B))
+    dB, gt, _ = plan.expm_block_adjoint(t, to_dev(G), Z)
+    ZG, _ = plan.expm_block(t, to_dev(G))
+    assert np.array_equal(to_np(dB), to_np(ZG))
+    col = np.zeros(n)
+    col[:len(a)] = a
+    ref_t = float(np.sum(G * TZ.matvec(col, to_np(Z), 1.0)))
+    assert abs(gt - ref_t) <= 1e-12 * abs(ref_t)
