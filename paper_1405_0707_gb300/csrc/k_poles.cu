@@ -10,8 +10,9 @@
 // Algorithm 1 (alg = 1): (H_m - tau_i I) Z_i = E_1 S_i (eq. (3.3)), S_i <- -H_{m+1,m} E_m^T Z_i
 // (eq. (35)), Wc = [sum_i 2 Re(omega_i Z_i); 0] (X_i - X_i^0 = V_m Z_i).
 // H_m is band upper Hessenberg with p sub-diagonals, so Gaussian elimination with partial
-// pivoting only looks at rows j..j+p of column j.  The matrix lives in shared memory when
-// (mp)^2 + mp p complex numbers fit, else in a global workspace (L2-resident).
+// pivoting only looks at rows j..j+p of column j (blocked by p x p blocks, see k_poles).  The
+// matrix lives in shared memory when (mp)^2 + mp p complex numbers fit, else in a global
+// workspace (L2-resident).
 #include "internal.h"
 
 namespace expm {
@@ -36,14 +37,31 @@ __device__ inline void cmsub(cplx& x, cplx a, cplx b) {
 }
 
 constexpr size_t kSmemLimit = 200 * 1024;
-constexpr int kPoleThreads = 32;    // one warp per pole: warp-synchronous, no block barriers
+constexpr int kPoleThreads = 128;   // four warps per pole
 
-// One CTA (one warp) per pole.  Shared memory holds M (mp x mp complex), the right-hand
-// sides / solution X (mp x p complex) and, when it fits, the real H~ ((mp+p) x mp), staged
-// once with coalesced loads.  Outputs: the restart factor S_i, ||S_i||_F, and
-// Y_i = 2 Re(omega_i Z_i) (mp x p real).  Since H~ is real,
-// sum_i 2 Re(omega_i H~ Z_i) = H~ sum_i Y_i, so the product with H~ is done once for all
-// poles by k_combine.
+// 1 / d with one scaling division and one reciprocal
+__device__ inline cplx crecip(cplx d) {
+    const double s = fabs(d.re) + fabs(d.im);
+    const double is = 1.0 / s;
+    const double dr = d.re * is, di = d.im * is;
+    const double k = is / (dr * dr + di * di);
+    return {dr * k, -di * k};
+}
+
+// One CTA (four warps) per pole.  Shared memory holds M (mp x mp complex, row-major), the
+// right-hand sides / solution X (mp x p complex) and, when it fits, the real H~ ((mp+p) x mp),
+// staged once with coalesced loads.  Outputs: the restart factor S_i, ||S_i||_F and
+// Y_i = 2 Re(omega_i Z_i) (mp x p real).  Since H~ is real, sum_i 2 Re(omega_i H~ Z_i) =
+// H~ sum_i Y_i, so the product with H~ is done once for all poles by k_combine2.
+//
+// M is block upper Hessenberg with p x p blocks (H_m is band Hessenberg with p sub-diagonals),
+// so Gaussian elimination with partial pivoting is blocked by block columns J:
+//   panel   (warp 0): LU with partial pivoting of the 2p x p block [M_JJ; M_J+1,J] (pivots
+//           are searched only in those rows, as the band allows); full rows are swapped, the
+//           multipliers stored in place, the pivots' reciprocals kept;
+//   update  (all threads, one column each): U_J,c = L_JJ^{-1} M_J,c and
+//           M_J+1,c -= L_J+1,J U_J,c for every later column c of M and every column of X;
+// then blocked back substitution: X_J = U_JJ^{-1} X_J, X_0..J-1 -= U_0..J-1,J X_J.
 __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict__ H, int ldH, int mp, int p,
                                                         const double* __restrict__ tau_re,
                                                         const double* __restrict__ tau_im,
@@ -54,10 +72,10 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
                                                         int* flags, int use_smem, int h_in_smem, int alg,
                                                         double* __restrict__ Zout) {
     extern __shared__ double sm[];
-    __shared__ cplx f[kMaxP + 1];
-    __shared__ int piv_s;
+    __shared__ cplx rdiag[kMaxMP];
     __shared__ double red[kPoleThreads];
     const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const cplx tau{tau_re[i], tau_im[i]};
     const cplx om{om_re[i], om_im[i]};
     const size_t per = (size_t)mp * mp + (size_t)mp * p;
@@ -70,87 +88,112 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
     const double* Hr = h_in_smem ? Hs : H;
     const int ldr = h_in_smem ? rows : ldH;
     if (h_in_smem)
-        for (int e = tid; e < rows * mp; e += nt) Hs[e] = H[(int64_t)(e / rows) * ldH + (e % rows)];
-    __syncwarp();
-    // Algorithm 2: M = I - tau H_m (eq. (3236)); Algorithm 1: M = H_m - tau I (eq. (3.3));
-    // row-major.  X = E_1 S_i.
-    for (int e = tid; e < mp * mp; e += nt) {
-        const int r = e / mp, c = e % mp;
-        const double h = Hr[(int64_t)c * ldr + r];
-        const double d = (r == c ? 1.0 : 0.0);
-        M[e] = (alg == 2) ? cplx{d - tau.re * h, -tau.im * h} : cplx{h - d * tau.re, -d * tau.im};
-    }
+        for (int c = 0; c < mp; ++c)
+            for (int r = tid; r < rows; r += nt) Hs[(int64_t)c * rows + r] = H[(int64_t)c * ldH + r];
+    __syncthreads();
+    // Algorithm 2: M = I - tau H_m (eq. (3236)); Algorithm 1: M = H_m - tau I (eq. (3.3)).
+    // X = E_1 S_i.
+    for (int r = 0; r < mp; ++r)
+        for (int c = tid; c < mp; c += nt) {
+            const double h = Hr[(int64_t)c * ldr + r];
+            const double d = (r == c ? 1.0 : 0.0);
+            M[(size_t)r * mp + c] = (alg == 2) ? cplx{d - tau.re * h, -tau.im * h} : cplx{h - d * tau.re, -d * tau.im};
+        }
     for (int e = tid; e < mp * p; e += nt) {
         const int r = e / p, c = e % p;
         X[e] = (r < p) ? Si[r * p + c] : cplx{0.0, 0.0};
     }
-    __syncwarp();
-    // elimination with partial pivoting inside the band (rows j..j+p of column j)
-    for (int j = 0; j < mp; ++j) {
-        const int jmax = min(j + p, mp - 1);
-        // pivot: warp arg-max of |M[r][j]|^2 over r = j..jmax (ties -> smallest r)
-        {
-            double best = -1.0;
-            int piv = j;
-            for (int r = j + tid; r <= jmax; r += 32) {
-                const double v = cabs2(M[(size_t)r * mp + j]);
-                if (v > best) { best = v; piv = r; }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int op = __shfl_xor_sync(0xffffffffu, piv, o);
-                if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
-            }
-            if (tid == 0) {
-                if (!(best > 0.0)) atomicOr(&flags[0], 2);
-                piv_s = piv;
-            }
-        }
-        __syncwarp();
-        const int piv = piv_s;
-        if (piv != j) {
-            for (int k = j + tid; k < mp; k += nt) {
-                const cplx a = M[(size_t)j * mp + k];
-                M[(size_t)j * mp + k] = M[(size_t)piv * mp + k];
-                M[(size_t)piv * mp + k] = a;
-            }
-            for (int c = tid; c < p; c += nt) {
-                const cplx a = X[(size_t)j * p + c];
-                X[(size_t)j * p + c] = X[(size_t)piv * p + c];
-                X[(size_t)piv * p + c] = a;
-            }
-            __syncwarp();
-        }
-        const int nr = jmax - j;
-        if (tid < nr) f[tid] = cdiv(M[(size_t)(j + 1 + tid) * mp + j], M[(size_t)j * mp + j]);
-        __syncwarp();
-        const int ncM = mp - j - 1, w = ncM + p;
-        for (int rr = 0; rr < nr; ++rr) {
-            const int r = j + 1 + rr;
-            const cplx fr = f[rr];
-            for (int k = tid; k < w; k += nt) {
-                if (k < ncM) {
-                    const int col = j + 1 + k;
-                    cmsub(M[(size_t)r * mp + col], fr, M[(size_t)j * mp + col]);
-                } else {
-                    const int c = k - ncM;
-                    cmsub(X[(size_t)r * p + c], fr, X[(size_t)j * p + c]);
+    __syncthreads();
+    const int nbc = mp / p;
+    for (int J = 0; J < nbc; ++J) {
+        const int r0 = J * p;
+        const int rend = (J + 1 < nbc) ? r0 + 2 * p : r0 + p;   // panel rows r0 .. rend-1
+        if (warp == 0) {
+            for (int jj = 0; jj < p; ++jj) {
+                const int c = r0 + jj;
+                // pivot: arg-max of |M[r][c]|^2 over the panel rows r >= c (ties -> smallest r)
+                double best = -1.0;
+                int piv = c;
+                for (int r = c + lane; r < rend; r += 32) {
+                    const double v = cabs2(M[(size_t)r * mp + c]);
+                    if (v > best) { best = v; piv = r; }
                 }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int op = __shfl_xor_sync(0xffffffffu, piv, o);
+                    if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+                }
+                if (lane == 0 && !(best > 0.0)) atomicOr(&flags[0], 2);
+                if (piv != c) {   // swap the full rows (M from column r0 on, and X)
+                    for (int k = r0 + lane; k < mp; k += 32) {
+                        const cplx a = M[(size_t)c * mp + k];
+                        M[(size_t)c * mp + k] = M[(size_t)piv * mp + k];
+                        M[(size_t)piv * mp + k] = a;
+                    }
+                    for (int k = lane; k < p; k += 32) {
+                        const cplx a = X[(size_t)c * p + k];
+                        X[(size_t)c * p + k] = X[(size_t)piv * p + k];
+                        X[(size_t)piv * p + k] = a;
+                    }
+                    __syncwarp();
+                }
+                const cplx inv = crecip(M[(size_t)c * mp + c]);
+                if (lane == 0) rdiag[c] = inv;
+                // multipliers of the panel rows below, and the rest of the panel's columns
+                for (int r = c + 1 + lane; r < rend; r += 32) {
+                    const cplx l = cmul(M[(size_t)r * mp + c], inv);
+                    M[(size_t)r * mp + c] = l;
+                    for (int k = c + 1; k < r0 + p; ++k) cmsub(M[(size_t)r * mp + k], l, M[(size_t)c * mp + k]);
+                }
+                __syncwarp();
             }
         }
-        __syncwarp();
-    }
-    // back substitution on the upper triangle; thread -> (row offset, column) fixed
-    const int bc = tid % p, br0 = tid / p, brs = nt / p;
-    for (int j = mp - 1; j >= 0; --j) {
-        if (tid < p) X[(size_t)j * p + tid] = cdiv(X[(size_t)j * p + tid], M[(size_t)j * mp + j]);
-        __syncwarp();
-        if (br0 < brs) {
-            const cplx xj = X[(size_t)j * p + bc];
-            for (int r = br0; r < j; r += brs) cmsub(X[(size_t)r * p + bc], M[(size_t)r * mp + j], xj);
+        __syncthreads();
+        // trailing update, one column per thread: columns of M right of the panel, then X
+        const int ncm = mp - r0 - p, ncol = ncm + p;
+        for (int base = 0; base < ncol; base += nt) {
+            // eight consecutive columns per lane group, interleaved over the warps
+            const int q = base + 32 * (lane >> 3) + 8 * warp + (lane & 7);
+            if (q >= ncol) continue;
+            cplx* col;
+            size_t ld;
+            if (q < ncm) { col = M + r0 + p + q; ld = mp; }
+            else { col = X + (q - ncm); ld = p; }
+            for (int a = 1; a < p; ++a) {          // U_J,c = L_JJ^{-1} M_J,c (unit lower)
+                cplx s = col[(size_t)(r0 + a) * ld];
+                for (int k = 0; k < a; ++k) cmsub(s, M[(size_t)(r0 + a) * mp + r0 + k], col[(size_t)(r0 + k) * ld]);
+                col[(size_t)(r0 + a) * ld] = s;
+            }
+            if (rend > r0 + p)
+                for (int a = 0; a < p; ++a) {      // M_J+1,c -= L_J+1,J U_J,c
+                    const int r = r0 + p + a;
+                    cplx s = col[(size_t)r * ld];
+                    for (int k = 0; k < p; ++k) cmsub(s, M[(size_t)r * mp + r0 + k], col[(size_t)(r0 + k) * ld]);
+                    col[(size_t)r * ld] = s;
+                }
         }
-        __syncwarp();
+        __syncthreads();
+    }
+    // blocked back substitution on the upper triangle
+    for (int J = nbc - 1; J >= 0; --J) {
+        const int r0 = J * p;
+        if (tid < p) {                              // X_J = U_JJ^{-1} X_J, one column per thread
+            const int c = tid;
+            for (int a = p - 1; a >= 0; --a) {
+                cplx s = X[(size_t)(r0 + a) * p + c];
+                for (int k = a + 1; k < p; ++k) cmsub(s, M[(size_t)(r0 + a) * mp + r0 + k], X[(size_t)(r0 + k) * p + c]);
+                X[(size_t)(r0 + a) * p + c] = cmul(s, rdiag[r0 + a]);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < r0 * p; e += nt) {   // X_0..J-1 -= U_0..J-1,J X_J
+            const int r = e / p, c = e % p;
+            cplx s = X[(size_t)r * p + c];
+            for (int k = 0; k < p; ++k) cmsub(s, M[(size_t)r * mp + r0 + k], X[(size_t)(r0 + k) * p + c]);
+            X[(size_t)r * p + c] = s;
+        }
+        __syncthreads();
     }
     // S_i and its Frobenius norm.  Algorithm 2: tau H_{m+1,m} E_m^T Z_i (eq. (49));
     // Algorithm 1: -H_{m+1,m} E_m^T Z_i (eq. (35)).
@@ -169,10 +212,10 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
         ss += cabs2(snew);
     }
     red[tid] = ss;
-    __syncwarp();
+    __syncthreads();
     for (int st = nt / 2; st > 0; st >>= 1) {
         if (tid < st) red[tid] += red[tid + st];
-        __syncwarp();
+        __syncthreads();
     }
     if (tid == 0) {
         res[i] = sqrt(red[0]);
