@@ -296,7 +296,8 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
     LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s, f32));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
-    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 1, s));
+    // second pass: in the mixed path the update is an O(eps_32) correction, formed in FP32
+    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 1, s, 0, f32));
     return qr_block(P, p, P->V + (int64_t)(j + 1) * p * ld, ld, true, (j + 1) * p, j * p, nullptr, true);
 }
 
@@ -816,7 +817,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     {
         const size_t cols = (size_t)opts->m * p_max, cs = cols | 1;
         size_t shm = 8 * (cols * p_max + 16 * cs + 16 * (size_t)p_max);
-        if (opts->precision == EXPM_PREC_MIXED) shm += 4 * (16 * cs + 16 * (size_t)p_max);
+        if (opts->precision == EXPM_PREC_MIXED) shm += 4 * (16 * cs + 16 * (size_t)p_max + cols * p_max);
         if (shm > 225 * 1024) return EXPM_INVALID_ARG;   // 227 KB opt-in minus static memory
     }
     if (opts->algorithm < EXPM_ALG_AUTO || opts->algorithm > EXPM_ALG_PSBFOM) return EXPM_INVALID_ARG;

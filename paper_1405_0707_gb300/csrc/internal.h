@@ -222,7 +222,7 @@ cudaError_t launch_reduce_h(const double* part, int nblk, int cols, int p, doubl
                             cudaStream_t s);
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
                                int p, int64_t n, const double* h, double* part, int nblk,
-                               int gram, cudaStream_t s, int f32 = 0);
+                               int gram, cudaStream_t s, int f32 = 0, int upd32 = 0);
 // Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
 // third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,

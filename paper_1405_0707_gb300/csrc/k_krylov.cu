@@ -188,7 +188,9 @@ k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p, double* _
 
 // W <- W - V h (FP64: keeps the Arnoldi relation exact); then partial of V^T W (gram = 0)
 // or W^T W (gram = 1).  F32: the projection's products in FP32 on FP32 copies of the tiles.
-template <int OPT, bool F32>
+// UPD32 (mixed path, second CGS pass, gram = 1): the correction V h in FP32 on FP32 copies,
+// subtracted from the FP64 W (see k_update_gram_rows).
+template <int OPT, bool F32, bool UPD32 = false>
 __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int64_t ldv, int cols,
                                                double* __restrict__ W, int64_t ldw, int p,
                                                int64_t n, int64_t rpb,
@@ -201,7 +203,11 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
     double* Ws = Vs + TR * cs;            // TR x p
     float* Vf = reinterpret_cast<float*>(Ws + TR * p);   // F32 copies (TR x cs, TR x p)
     float* Wf = Vf + TR * cs;
-    for (int e = threadIdx.x; e < cols * p; e += blockDim.x) hs[e] = h[e];
+    float* hf = Wf + TR * p;              // UPD32: FP32 copy of h (cols x p)
+    for (int e = threadIdx.x; e < cols * p; e += blockDim.x) {
+        hs[e] = h[e];
+        if (UPD32) hf[e] = (float)h[e];
+    }
     const int nout = gram ? p * p : cols * p;
     double acc[OPT];
 #pragma unroll
@@ -209,13 +215,20 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
     for (int64_t r0 = rb; r0 < re; r0 += TR) {
         const int tr = (int)min((int64_t)TR, re - r0);
-        load_tile(V, ldv, cols, r0, tr, Vs, cs);
+        if (UPD32) load_tile(V, ldv, cols, r0, tr, Vf, cs);
+        else load_tile(V, ldv, cols, r0, tr, Vs, cs);
         load_tile(W, ldw, p, r0, tr, Ws, p);
         __syncthreads();
         for (int e = threadIdx.x; e < TR * p; e += blockDim.x) {
             const int rr = e % TR, c = e / TR;
             double w = Ws[rr * p + c];
-            for (int a = 0; a < cols; ++a) w = fma(-Vs[rr * cs + a], hs[a * p + c], w);
+            if (UPD32) {
+                float corr = 0.f;
+                for (int a = 0; a < cols; ++a) corr = fmaf(Vf[rr * cs + a], hf[a * p + c], corr);
+                w -= (double)corr;
+            } else {
+                for (int a = 0; a < cols; ++a) w = fma(-Vs[rr * cs + a], hs[a * p + c], w);
+            }
             Ws[rr * p + c] = w;
             if (F32) Wf[rr * p + c] = (float)w;
             if (rr < tr) W[(int64_t)c * ldw + r0 + rr] = w;
@@ -561,18 +574,26 @@ __global__ void __launch_bounds__(NT) k_trsm_rows(double* W, int64_t ldw, int p,
     if (gram) cta_gram_write(acc0, acc1, p, red, part);
 }
 
-// Row-per-thread, p <= 8: W <- W - V h (FP64, the Arnoldi relation stays exact) and the
-// upper-triangular Gram partial of the result.  h (cols x p) is broadcast from shared memory.
+// Row-per-thread, p <= 8: W <- W - V h and the upper-triangular Gram partial of the result.
+// h (cols x p) is broadcast from shared memory.  UPD32 = false: the update in FP64 (the
+// Arnoldi relation stays exact to FP64 rounding).  UPD32 = true (mixed path, second CGS
+// pass only): h is then the O(eps_32) remainder left by the FP32 projection of the first
+// pass, so the correction V h is formed in FP32 and subtracted from the FP64 W; its error,
+// eps_32 |V h| ~ eps_32^2 |W|, stays far below the accuracy the mixed path delivers.
+template <bool UPD32>
 __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restrict__ V, int64_t ldv, int cols,
                                                          double* __restrict__ W, int64_t ldw, int p,
                                                          int64_t n, int64_t rpb,
                                                          const double* __restrict__ h,
                                                          double* __restrict__ part) {
-    extern __shared__ double hs[];           // cols x RP (zero-padded columns)
+    extern __shared__ double hs[];           // cols x RP (zero-padded columns), FP64 or FP32
+    float* hsf = reinterpret_cast<float*>(hs);
     __shared__ double red[NT / 32][RG];
     for (int e = threadIdx.x; e < cols * RP; e += blockDim.x) {
         const int a = e / RP, c = e % RP;
-        hs[e] = (c < p) ? h[a * p + c] : 0.0;
+        const double v = (c < p) ? h[a * p + c] : 0.0;
+        if (UPD32) hsf[e] = (float)v;
+        else hs[e] = v;
     }
     __syncthreads();
     __shared__ double buf[NT / 32][32 * RP];
@@ -584,12 +605,24 @@ __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restric
         double w[RP];
 #pragma unroll
         for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
-        if (ok)
+        if (ok && UPD32) {
+            float corr[RP];
+#pragma unroll
+            for (int c = 0; c < RP; ++c) corr[c] = 0.f;
+            for (int a = 0; a < cols; ++a) {
+                const float v = (float)V[(int64_t)a * ldv + r];
+#pragma unroll
+                for (int c = 0; c < RP; ++c) corr[c] = fmaf(v, hsf[a * RP + c], corr[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < RP; ++c) w[c] -= (double)corr[c];
+        } else if (ok) {
             for (int a = 0; a < cols; ++a) {
                 const double v = V[(int64_t)a * ldv + r];
 #pragma unroll
                 for (int c = 0; c < RP; ++c) w[c] = fma(-v, hs[a * RP + c], w[c]);
             }
+        }
 #pragma unroll
         for (int c = 0; c < RP; ++c)
             if (ok && c < p) W[(int64_t)c * ldw + r] = w[c];
@@ -747,17 +780,26 @@ cudaError_t launch_reduce_h(const double* part, int nblk_req, int cols, int p, d
 
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
                                int p, int64_t n, const double* h, double* part, int nblk,
-                               int gram, cudaStream_t s, int f32) {
+                               int gram, cudaStream_t s, int f32, int upd32) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
     size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1) + TR * p);
-    if (f32) shm += sizeof(float) * (TR * (cols | 1) + TR * p);
+    if (f32 || upd32) shm += sizeof(float) * (TR * (cols | 1) + TR * p);
+    if (upd32) shm += sizeof(float) * (size_t)cols * p;
     const int nout = gram ? p * p : cols * p;
     if (gram && p <= RP) {
-        k_update_gram_rows<<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part);
+        if (upd32)
+            k_update_gram_rows<true><<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, W, ldw, p, n,
+                                                                                       rpb, h, part);
+        else
+            k_update_gram_rows<false><<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, W, ldw, p, n,
+                                                                                        rpb, h, part);
         return cudaGetLastError();
     }
-    if (f32)
+    if (upd32 && gram)
+        EXPM_OPT_DISPATCH(nout, (k_update<O, false, true><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part,
+                                                                             gram)));
+    else if (f32)
         EXPM_OPT_DISPATCH(nout, (k_update<O, true><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
     else
         EXPM_OPT_DISPATCH(nout, (k_update<O, false><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
@@ -856,8 +898,11 @@ cudaError_t krylov_set_smem_limits() {
     EXPM_SET((k_update<1, false>)); EXPM_SET((k_update<4, false>)); EXPM_SET((k_update<16, false>));
     EXPM_SET((k_update<64, false>)); EXPM_SET((k_update<1, true>)); EXPM_SET((k_update<4, true>));
     EXPM_SET((k_update<16, true>)); EXPM_SET((k_update<64, true>));
+    EXPM_SET((k_update<1, false, true>)); EXPM_SET((k_update<4, false, true>));
+    EXPM_SET((k_update<16, false, true>)); EXPM_SET((k_update<64, false, true>));
     EXPM_SET(k_update_z);
-    EXPM_SET(k_update_gram_rows);
+    EXPM_SET(k_update_gram_rows<false>);
+    EXPM_SET(k_update_gram_rows<true>);
     EXPM_SET(k_update_z_rows);
 #undef EXPM_SET
     return e;
