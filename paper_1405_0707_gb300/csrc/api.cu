@@ -36,7 +36,10 @@ constexpr size_t kOffRi = kOffR + kMaxP * kMaxP;                   // R^{-1}
 constexpr size_t kOffRt = kOffRi + kMaxP * kMaxP;                  // product of R factors
 constexpr size_t kOffWc = kOffRt + kMaxP * kMaxP;                  // (kMaxMP + kMaxP) x kMaxP
 constexpr size_t kOffTau = kOffWc + (size_t)(kMaxMP + kMaxP) * kMaxP;   // 4 x 16
-constexpr size_t kSmallDoubles = kOffTau + 4 * EXPM_MAX_POLES;
+constexpr size_t kOffG = kOffTau + 4 * EXPM_MAX_POLES;               // reduced Gram matrix
+constexpr size_t kOffRt2 = kOffG + kMaxP * kMaxP;                    // Rtot after pass 2
+constexpr size_t kOffRt3 = kOffRt2 + kMaxP * kMaxP;                  // Rtot after pass 3
+constexpr size_t kSmallDoubles = kOffRt3 + kMaxP * kMaxP;
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int* flags_of(double* stat) { return reinterpret_cast<int*>(stat + 24); }
@@ -77,12 +80,38 @@ void prof_flush(expm_plan* P) {
         prof_end(P, (stage), e_, 1);                 \
     } while (0)
 
+// The mixed path with p <= 8 runs the Cholesky QR with FP32 factorisations fused into the
+// triangular solves (k_qr_mixed_rows); everything else uses k_chol + k_trsm.
+inline bool fused_qr(const expm_plan* P, int p) {
+    return p <= kRowsMaxP && P->opts.precision == EXPM_PREC_MIXED;
+}
+
 expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, int hrow, int hcol,
                      double* normsq, bool gram_done) {
     cudaStream_t s = P->stream;
     const int64_t n = P->n, ld = P->ld;
     const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * std::ldexp(1.0, -53);
     int* flags = flags_of(P->stat);
+    if (fused_qr(P, p)) {
+        // mixed path: three passes with FP32 factorisations fused into the triangular solves;
+        // the Gram matrix arrives reduced in G (from the last Gram-Schmidt pass, or here)
+        double* G = sm(P, kOffG);
+        double* Hq = withH ? P->H : nullptr;
+        if (!gram_done) {
+            LAUNCH(EXPM_STAGE_QR, launch_proj_partial(P->W, ld, p, P->W, ld, p, n, P->part, P->nblk, s));
+            LAUNCH(EXPM_STAGE_QR, launch_reduce_h(P->part, P->nblk, p, p, G, nullptr, 0, 0, 0, 0, s));
+        }
+        LAUNCH(EXPM_STAGE_QR, launch_qr_mixed_rows(P->W, ld, p, n, P->nblk, G, P->part, P->ctr, 0, sm(P, kOffR),
+                                                   sm(P, kOffRi), nullptr, sm(P, kOffRt), Hq, P->ldH, hrow, hcol,
+                                                   normsq, flags, P->W, ld, s));
+        LAUNCH(EXPM_STAGE_QR, launch_qr_mixed_rows(P->W, ld, p, n, P->nblk, G, P->part, P->ctr, 1, sm(P, kOffR),
+                                                   sm(P, kOffRi), sm(P, kOffRt), sm(P, kOffRt2), Hq, P->ldH, hrow,
+                                                   hcol, nullptr, flags, out, ldo, s));
+        LAUNCH(EXPM_STAGE_QR, launch_qr_mixed_rows(P->W, ld, p, n, P->nblk, G, P->part, P->ctr, 2, sm(P, kOffR),
+                                                   sm(P, kOffRi), sm(P, kOffRt2), sm(P, kOffRt3), Hq, P->ldH, hrow,
+                                                   hcol, nullptr, flags, out, ldo, s));
+        return EXPM_OK;
+    }
     if (!gram_done) LAUNCH(EXPM_STAGE_QR, launch_proj_partial(P->W, ld, p, P->W, ld, p, n, P->part, P->nblk, s));
     double* Hq = withH ? P->H : nullptr;
     const int* extra = flags + 2;
@@ -296,8 +325,11 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
     LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s, f32));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
-    // second pass: in the mixed path the update is an O(eps_32) correction, formed in FP32
-    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 1, s, 0, f32));
+    // second pass: in the mixed path the update is an O(eps_32) correction, formed in FP32;
+    // with the fused QR its last CTA also reduces the Gram partials
+    const bool fused = fused_qr(P, p);
+    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 1, s, 0, f32,
+                                              fused ? sm(P, kOffG) : nullptr, fused ? P->ctr : nullptr));
     return qr_block(P, p, P->V + (int64_t)(j + 1) * p * ld, ld, true, (j + 1) * p, j * p, nullptr, true);
 }
 
@@ -427,13 +459,18 @@ expm_status run_begin(expm_plan* P, RunState& r) {
     const int m = P->opts.m, p = r.p;
     const int64_t n = P->n, ld = P->ld;
     CK(cudaMemsetAsync(P->stat, 0, sizeof(double) * kStatDoubles, s));
+    CK(cudaMemsetAsync(P->ctr, 0, sizeof(unsigned) * 4, s));
     CK(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)P->ldH * m * P->p_max, s));
     LAUNCH(EXPM_STAGE_OTHER, launch_zero(P->Zacc, ld, n, p, s));
     if (P->opts.certify) LAUNCH(EXPM_STAGE_OTHER, launch_zero(P->Xcert, ld, n, 2 * P->npoles * p, s));
     LAUNCH(EXPM_STAGE_OTHER, launch_copy(r.dB, r.ldb, P->W, ld, n, p, s));
     expm_status st = qr_block(P, p, P->V, ld, false, 0, 0, P->stat + 16, false);
     if (st != EXPM_OK) return st;
-    LAUNCH(EXPM_STAGE_OTHER, launch_init_S(sm(P, kOffRt), p, P->npoles, P->S, s));
+    if (fused_qr(P, p))   // the fused QR leaves R in Rt2, or in Rt3 when its third pass ran
+        LAUNCH(EXPM_STAGE_OTHER, launch_init_S(sm(P, kOffRt2), p, P->npoles, P->S, s, sm(P, kOffRt3),
+                                               flags_of(P->stat) + 2));
+    else
+        LAUNCH(EXPM_STAGE_OTHER, launch_init_S(sm(P, kOffRt), p, P->npoles, P->S, s));
     // graph of one restart cycle, cached per (algorithm, p, t)
     r.ge = nullptr;
     if (P->use_graphs && !P->prof && P->stream != nullptr) r.ge = graph_for(P, r.t, p, r.alg);
@@ -589,6 +626,7 @@ void free_plan(expm_plan* P) {
     cudaFree(P->S);
     cudaFree(P->Wc_slots);
     cudaFree(P->stat);
+    cudaFree(P->ctr);
     cudaFree(P->dotpart);
     if (P->hpin) cudaFreeHost(P->hpin);
     if (P->hdot) cudaFreeHost(P->hdot);
@@ -900,6 +938,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     ok = ok && dalloc(&P->S, (size_t)P->npoles * p_max * p_max * 2);
     ok = ok && dalloc(&P->Wc_slots, (size_t)P->npoles * (mpm + p_max) * p_max);
     ok = ok && dalloc(&P->stat, kStatDoubles);
+    ok = ok && dalloc(&P->ctr, 4) && cudaMemset(P->ctr, 0, sizeof(unsigned) * 4) == cudaSuccess;
     if (opts->certify) {
         const size_t w = 2 * (size_t)P->npoles * p_max, rows = (size_t)mpm + p_max;
         if (8 * (rows * w + 16 * (rows | 1)) > 225 * 1024) { free_plan(P); return EXPM_INVALID_ARG; }
@@ -1165,6 +1204,7 @@ expm_status expm_arnoldi(expm_plan* plan, double t, const double* dV1, int64_t l
     cudaStream_t s = plan->stream;
     const int64_t n = plan->n, ld = plan->ld;
     CK(cudaMemsetAsync(plan->stat, 0, sizeof(double) * kStatDoubles, s));
+    CK(cudaMemsetAsync(plan->ctr, 0, sizeof(unsigned) * 4, s));
     CK(cudaMemsetAsync(plan->H, 0, sizeof(double) * (size_t)plan->ldH * m * plan->p_max, s));
     expm_plan* P = plan;
     LAUNCH(EXPM_STAGE_OTHER, launch_copy(dV1, ldv1, plan->V, ld, n, p, s));

@@ -166,6 +166,7 @@ struct expm_plan_s {
     double* S = nullptr;       // per-pole restart factors, npoles x p x p complex
     double* Wc_slots = nullptr;// per-pole (m+1)p x p update coefficients
     double* stat = nullptr;    // device status block: res[16], normsq, flags (ints)
+    unsigned* ctr = nullptr;   // last-CTA ticket counter of the fused reductions
     double* hpin = nullptr;    // pinned host mirror of stat
     cudaEvent_t cycle_ev = nullptr;   // recorded after every restart cycle
     double* dotpart = nullptr; // dot_blocks() x p_max partial sums (adjoint's <G, A Z>)
@@ -222,7 +223,15 @@ cudaError_t launch_reduce_h(const double* part, int nblk, int cols, int p, doubl
                             cudaStream_t s);
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
                                int p, int64_t n, const double* h, double* part, int nblk,
-                               int gram, cudaStream_t s, int f32 = 0, int upd32 = 0);
+                               int gram, cudaStream_t s, int f32 = 0, int upd32 = 0, double* G = nullptr,
+                               unsigned* ctr = nullptr);
+// Mixed path, p <= 8: Cholesky-QR pass with an FP32 factorisation (mode 0: of G; modes 1
+// and 2: of the deviation G - I), corrections in FP32, W and the R product in FP64.
+cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int nblk, double* G, double* part,
+                                 unsigned* ctr, int mode, double* R, double* Rinv, const double* Rtot_in,
+                                 double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
+                                 int* flags, double* out, int64_t ldo, cudaStream_t s);
+constexpr int kRowsMaxP = 8;   // widths handled by the row-per-thread kernels
 // Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
 // third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,
@@ -272,7 +281,8 @@ cudaError_t launch_unit(double* v, int64_t n, cudaStream_t s);
 cudaError_t krylov_set_smem_limits();
 cudaError_t poles_set_smem_limits();
 size_t poles_smem_bytes(int mp, int p);
-cudaError_t launch_init_S(const double* R, int p, int npoles, double* S, cudaStream_t s);
+cudaError_t launch_init_S(const double* R, int p, int npoles, double* S, cudaStream_t s,
+                          const double* R_alt = nullptr, const int* use_alt = nullptr);
 cudaError_t launch_axpby(double a, const double* X, int64_t ldx, double b, const double* Y,
                          int64_t ldy, double* out, int64_t ldo, int64_t n, int p,
                          cudaStream_t s);

@@ -534,6 +534,338 @@ __device__ inline void cta_gram_write(double acc0, double acc1, int p, double (*
     }
 }
 
+// Last-CTA reduction: every CTA has written its partial; the CTA that takes the last ticket
+// (atomic counter) sums the nblk partials of each output in a fixed order (independent of
+// which CTA is last) and resets the counter for the next kernel.  No CTA waits on another.
+__device__ inline bool take_last_ticket(unsigned* ctr) {
+    __shared__ unsigned ticket;
+    __threadfence();                       // this CTA's partial is visible device-wide
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(ctr, 1u);
+    __syncthreads();
+    return ticket == gridDim.x - 1;
+}
+
+// out[o] = sum_b part[b][o] for o < nout (nout <= RP * RP), by the last CTA: RED_S stripes
+// per output, each stripe's loads issued back to back, stripes added in a fixed order.
+__device__ inline void last_cta_sum(const double* part, int nblk, int nout, double* __restrict__ out,
+                                    unsigned* ctr) {
+    __shared__ double red[NT];
+    __threadfence();
+    const int stripes = NT / nout;         // nout <= 64 -> at least 4 stripes
+    const int o = threadIdx.x % nout, st = threadIdx.x / nout;
+    double acc = 0.0;
+    if (st < stripes) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int b = st;
+        for (; b + 3 * stripes < nblk; b += 4 * stripes) {
+            a0 += __ldcg(part + (int64_t)b * nout + o);
+            a1 += __ldcg(part + (int64_t)(b + stripes) * nout + o);
+            a2 += __ldcg(part + (int64_t)(b + 2 * stripes) * nout + o);
+            a3 += __ldcg(part + (int64_t)(b + 3 * stripes) * nout + o);
+        }
+        for (; b < nblk; b += stripes) a0 += __ldcg(part + (int64_t)b * nout + o);
+        acc = (a0 + a1) + (a2 + a3);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < nout) {
+        double s = 0.0;
+        for (int k = 0; k < stripes; ++k) s += red[k * nout + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) *ctr = 0u;
+}
+
+// ---- Mixed-path Cholesky QR for p <= 8 (every CTA factors the reduced Gram matrix G
+// itself, in FP32; CTA 0 alone writes R, Rtot, H and the flags).
+//   KIND 1 (pass 1, mode 0): G (summed in FP64) is scaled by a power of two near its largest
+//     diagonal entry (exact) and factored in FP32; pivots below 1e-6 of the largest (kappa(W)
+//     above ~1e3) redo it with the shift 11 p (p+1) 2^-24 trace and request a third pass
+//     (flags[2]).  R is that factor scaled back (exact), and W <- W R^{-1} is a forward
+//     substitution with R in FP64, so W = W_new R holds to FP64 rounding whatever the FP32
+//     factor's own accuracy.  Gram partials in FP64, reduced by the last CTA into G.
+//   KIND 2 (passes 2 and 3, modes 1 and 2): now G = I + E with E small, so R = I + U is
+//     found from the deviation alone, in FP32: U_jl = (E_jl - sum_{k<j} U_kj U_kl)/(1 + U_jj),
+//     U_jj = x / (1 + sqrt(1 + x)) with x = E_jj - sum_{k<j} U_kj^2; R^{-1} = I + Y with
+//     (I + U) Y = -U.  Each entry has FP32 relative accuracy on a quantity of size |E|, so
+//     absolute errors are ~eps_32 |E|.  Rtot <- Rtot + U Rtot (FP32 correction of the FP64
+//     product) and W <- W + W Y (FP32 correction of the FP64 W).
+// Columns that are exactly zero stay zero (zero rows in R), as in k_chol.
+struct CholF {
+    float G[RP * RP], U[RP * RP], Y[RP * RP];
+    float rd[RP];
+    float umax;       // KIND 2: max |U|
+    int ill, bad;
+};
+
+// pass 1: FP32 Cholesky of G 2^-k (upper triangle) -> U; warp 0
+__device__ inline void chol32_full(CholF& cf, const double* G0, int p, int k, double tr_s) {
+    const int lane = threadIdx.x;
+    const int pp = p * p;
+    if (lane == 0) { cf.ill = 0; cf.bad = 0; }
+    __syncwarp();
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const double shift = attempt ? 11.0 * p * (p + 1) * 0x1p-24 * tr_s : 0.0;
+        for (int o = lane; o < pp; o += 32) {
+            cf.G[o] = (float)(ldexp(G0[o], -k) + ((o / p == o % p) ? shift : 0.0));
+            cf.U[o] = 0.f;
+        }
+        __syncwarp();
+        float dmax = 0.f;
+        for (int c = 0; c < p; ++c) dmax = fmaxf(dmax, cf.G[c * p + c]);
+        for (int j = 0; j < p; ++j) {
+            if (lane == 0) {
+                float d = cf.G[j * p + j];
+                if (G0[j * p + j] == 0.0) {
+                    cf.U[j * p + j] = 0.f;
+                    cf.rd[j] = 0.f;
+                } else {
+                    if (!(d > 0.f) || !isfinite(d) || (attempt == 0 && d < 1e-6f * dmax)) cf.ill = 1;
+                    if (!(d > 0.f) || !isfinite(d)) d = 1.f;
+                    const float rj = sqrtf(d);
+                    cf.U[j * p + j] = rj;
+                    cf.rd[j] = 1.f / rj;
+                }
+            }
+            __syncwarp();
+            const float inv = cf.rd[j];
+            if (lane > j && lane < p) cf.U[j * p + lane] = cf.G[j * p + lane] * inv;
+            __syncwarp();
+            if (lane > j && lane < p) {
+                const float rb = cf.U[j * p + lane];
+                for (int a = j + 1; a <= lane; ++a) cf.G[a * p + lane] -= cf.U[j * p + a] * rb;
+            }
+            __syncwarp();
+        }
+        if (attempt == 1 || !cf.ill) break;
+        __syncwarp();
+    }
+}
+
+// passes 2/3: deviation Cholesky of G = I + E -> U (R = I + U), Y (R^{-1} = I + Y); warp 0
+__device__ inline void chol32_dev(CholF& cf, const double* G0, int p) {
+    const int lane = threadIdx.x;
+    const int pp = p * p;
+    if (lane == 0) { cf.ill = 0; cf.bad = 0; }
+    for (int o = lane; o < pp; o += 32) {
+        const bool dg = o / p == o % p;
+        cf.G[o] = (float)(G0[o] - (dg ? 1.0 : 0.0));   // E (upper triangle)
+        cf.U[o] = 0.f;
+        cf.Y[o] = 0.f;
+    }
+    __syncwarp();
+    for (int j = 0; j < p; ++j) {
+        if (lane == 0) {
+            if (G0[j * p + j] == 0.0) {
+                cf.U[j * p + j] = -1.f;                  // R_jj = 0: a zero column stays zero
+                cf.rd[j] = 0.f;
+            } else {
+                float x = cf.G[j * p + j];
+                for (int k = 0; k < j; ++k) x -= cf.U[k * p + j] * cf.U[k * p + j];
+                if (!(x > -0.75f) || !isfinite(x)) cf.bad = 1;   // not close to orthonormal
+                if (!(x > -0.75f) || !isfinite(x)) x = 0.f;
+                const float ujj = x / (1.f + sqrtf(1.f + x));
+                cf.U[j * p + j] = ujj;
+                cf.rd[j] = 1.f / (1.f + ujj);
+            }
+        }
+        __syncwarp();
+        if (lane > j && lane < p) {
+            float s = cf.G[j * p + lane];
+            for (int k = 0; k < j; ++k) s -= cf.U[k * p + j] * cf.U[k * p + lane];
+            cf.U[j * p + lane] = s * cf.rd[j];
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        float um = 0.f;
+        for (int o = 0; o < pp; ++o) um = fmaxf(um, fabsf(cf.U[o]));
+        cf.umax = um;
+    }
+    // (I + U) Y = -U, column `lane` by back substitution
+    if (lane < p) {
+        const int c = lane;
+        for (int r = c; r >= 0; --r) {
+            float s = -cf.U[r * p + c];
+            for (int k = r + 1; k <= c; ++k) s -= cf.U[r * p + k] * cf.Y[k * p + c];
+            cf.Y[r * p + c] = (r == c && cf.rd[r] == 0.f) ? -1.f : s * cf.rd[r];
+        }
+    }
+    __syncwarp();
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NT) k_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int64_t rpb,
+                                                      double* G, double* __restrict__ part, unsigned* ctr,
+                                                      int mode, double* R, double* Rinv, const double* Rtot_in,
+                                                      double* Rtot_out, double* H, int ldH, int hrow, int hcol,
+                                                      double* normsq_out, int* flags, double* out_, int64_t ldo_) {
+    int* extra = flags + 2;
+    if (mode == 2 && *extra == 0) return;
+    __shared__ CholF cf;
+    __shared__ double G0[RP * RP];
+    __shared__ double hn2[RP];
+    __shared__ double Rd[RP * RP];          // KIND 1: R (padded to RP x RP); KIND 2 unused
+    __shared__ double rcp[RP];              // KIND 1: 1 / R_cc (0 for a zero column)
+    __shared__ float Yf[RP * RP];           // KIND 2: Y padded to RP x RP
+    __shared__ double red[NT / 32][RG];
+    __shared__ double buf[NT / 32][32 * RP];
+    const int pp = p * p;
+    for (int o = threadIdx.x; o < pp; o += blockDim.x) G0[o] = G[o];
+    const bool last = (mode == 1 && *extra == 0) || mode == 2;
+    const bool lead = blockIdx.x == 0;
+    if (H && last && lead) {
+        const int stripes = NT / p;
+        const int c = threadIdx.x % p, st = threadIdx.x / p;
+        double v2 = 0.0;
+        if (st < stripes)
+            for (int a = st; a < hrow; a += stripes) {
+                const double v = H[(int64_t)(hcol + c) * ldH + a];
+                v2 += v * v;
+            }
+        buf[0][threadIdx.x] = v2;
+    }
+    __syncthreads();
+    if (H && last && lead && threadIdx.x < p) {
+        const int stripes = NT / p;
+        double s2 = 0.0;
+        for (int k = 0; k < stripes; ++k) s2 += buf[0][k * p + threadIdx.x];
+        hn2[threadIdx.x] = s2;
+    }
+    __syncthreads();
+    int kexp = 0;                           // KIND 1: G is factored as G 2^-kexp (kexp even)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double tr = 0.0, dmax = 0.0;
+        if (KIND == 1) {
+            for (int c = 0; c < p; ++c) {
+                tr += G0[c * p + c];
+                dmax = fmax(dmax, G0[c * p + c]);
+            }
+            if (dmax > 0.0 && isfinite(dmax)) {
+                frexp(dmax, &kexp);
+                kexp &= ~1;
+            }
+            chol32_full(cf, G0, p, kexp, ldexp(tr, -kexp));
+        } else {
+            chol32_dev(cf, G0, p);
+        }
+        if (lead) {
+            if (KIND == 1 && normsq_out && lane == 0) *normsq_out = tr;
+            if (KIND == 1 && lane == 0) *extra = cf.ill;
+            if (lane < p) {
+                const int c = lane;
+                for (int r = 0; r < p; ++r) {
+                    const int o = r * p + c;
+                    double rt;
+                    if (KIND == 1) {
+                        rt = (r <= c) ? ldexp((double)cf.U[o], kexp / 2) : 0.0;
+                        R[o] = rt;
+                    } else {
+                        // Rtot_out = Rtot_in + U Rtot_in (FP32 correction of the FP64 product)
+                        float corr = 0.f;
+                        for (int k = r; k <= c; ++k) corr = fmaf(cf.U[r * p + k], (float)Rtot_in[k * p + c], corr);
+                        rt = (r <= c) ? Rtot_in[o] + (double)corr : 0.0;
+                        R[o] = (r <= c) ? (double)cf.U[o] + (r == c ? 1.0 : 0.0) : 0.0;
+                        Rinv[o] = (r <= c) ? (double)cf.Y[o] + (r == c ? 1.0 : 0.0) : 0.0;
+                    }
+                    Rtot_out[o] = rt;
+                    if (!isfinite(rt)) cf.bad = 1;
+                    if (H && last) H[(int64_t)(hcol + c) * ldH + hrow + r] = rt;
+                }
+            }
+            __syncwarp();
+            if (H && last && lane < p) {
+                const int c = lane;
+                double n0 = hn2[c], dg = 0.0;
+                for (int a = 0; a <= c; ++a) {
+                    const double v = Rtot_out[a * p + c];
+                    n0 += v * v;
+                    if (a == c) dg = v;
+                }
+                if (dg <= 1e-14 * sqrt(n0)) atomicOr(&flags[1], 1);
+            }
+            __syncwarp();
+            if (lane == 0 && cf.bad) atomicOr(&flags[0], 1);
+        }
+    }
+    __syncthreads();
+    if (KIND == 1) {
+        // kexp as computed by warp 0 (every thread recomputes it from the same G0)
+        double dmax = 0.0;
+        for (int c = 0; c < p; ++c) dmax = fmax(dmax, G0[c * p + c]);
+        kexp = 0;
+        if (dmax > 0.0 && isfinite(dmax)) {
+            frexp(dmax, &kexp);
+            kexp &= ~1;
+        }
+    }
+    // KIND 2 with max|U| above 1e-4 (a pass after the shifted one): the FP32 inverse I + Y
+    // would leave an eps_32 |U| mismatch with the recorded R, so the solve is a forward
+    // substitution with R = I + U in FP64, as in pass 1
+    const bool subst = KIND == 1 || cf.umax > 1e-4f;
+    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+        const int a = e / RP, c = e % RP;
+        const bool in = a < p && c < p && a <= c;
+        if (KIND == 1) Rd[e] = in ? ldexp((double)cf.U[a * p + c], kexp / 2) : 0.0;
+        else {
+            Yf[e] = in ? cf.Y[a * p + c] : 0.f;
+            Rd[e] = in ? (double)cf.U[a * p + c] + (a == c ? 1.0 : 0.0) : 0.0;
+        }
+    }
+    __syncthreads();
+    if (subst && threadIdx.x < RP) {
+        const double d = Rd[threadIdx.x * RP + threadIdx.x];
+        rcp[threadIdx.x] = (d != 0.0) ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    double* out;
+    int64_t ldo;
+    int gram;
+    if (mode == 0) { out = W; ldo = ldw; gram = 1; }
+    else if (mode == 1 && *extra) { out = W; ldo = ldw; gram = 1; }
+    else { out = out_; ldo = ldo_; gram = 0; }
+    double acc0 = 0.0, acc1 = 0.0;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r0 = rb + (threadIdx.x & ~31); r0 < re; r0 += blockDim.x) {
+        const int64_t r = r0 + (threadIdx.x & 31);
+        const bool ok = r < re;
+        double w[RP], y[RP];
+#pragma unroll
+        for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
+        if (subst) {
+            // forward substitution y R = w (R upper triangular)
+#pragma unroll
+            for (int c = 0; c < RP; ++c) {
+                double s = w[c];
+#pragma unroll
+                for (int a = 0; a < c; ++a) s = fma(-y[a], Rd[a * RP + c], s);
+                y[c] = s * rcp[c];
+            }
+        } else {
+            float wf[RP];
+#pragma unroll
+            for (int c = 0; c < RP; ++c) wf[c] = (float)w[c];
+#pragma unroll
+            for (int c = 0; c < RP; ++c) {
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a <= c; ++a) s = fmaf(wf[a], Yf[a * RP + c], s);
+                y[c] = w[c] + (double)s;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < RP; ++c)
+            if (ok && c < p) out[(int64_t)c * ldo + r] = y[c];
+        if (gram) warp_gram_rows(y, buf[threadIdx.x >> 5], acc0, acc1);
+    }
+    if (gram) {
+        cta_gram_write(acc0, acc1, p, red, part);
+        if (take_last_ticket(ctr)) last_cta_sum(part, gridDim.x, pp, G, ctr);
+    }
+}
+
 __global__ void __launch_bounds__(NT) k_trsm_rows(double* W, int64_t ldw, int p,
                                                   int64_t n, int64_t rpb, const double* __restrict__ Rinv,
                                                   double* out_, int64_t ldo_,
@@ -585,7 +917,8 @@ __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restric
                                                          double* __restrict__ W, int64_t ldw, int p,
                                                          int64_t n, int64_t rpb,
                                                          const double* __restrict__ h,
-                                                         double* __restrict__ part) {
+                                                         double* __restrict__ part, double* G,
+                                                         unsigned* ctr) {
     extern __shared__ double hs[];           // cols x RP (zero-padded columns), FP64 or FP32
     float* hsf = reinterpret_cast<float*>(hs);
     __shared__ double red[NT / 32][RG];
@@ -629,6 +962,7 @@ __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restric
         warp_gram_rows(w, buf[threadIdx.x >> 5], acc0, acc1);
     }
     cta_gram_write(acc0, acc1, p, red, part);
+    if (G && take_last_ticket(ctr)) last_cta_sum(part, gridDim.x, p * p, G, ctr);
 }
 
 // Row-per-thread, p <= 8: Z[r, :] += V[r, 0:cols] Wc; restart copy V[r, 0:p] <- V[r, cols-p:cols].
@@ -701,10 +1035,13 @@ __global__ void k_combine(const double* __restrict__ slots, int npoles, int nout
     Wc[o] = s;
 }
 
-__global__ void k_init_S(const double* __restrict__ R, int p, int npoles, double* __restrict__ S) {
+// S_i = R for every pole (R_alt instead when *use_alt != 0: the QR's third pass ran)
+__global__ void k_init_S(const double* __restrict__ R, int p, int npoles, double* __restrict__ S,
+                         const double* __restrict__ R_alt, const int* use_alt) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= npoles * p * p) return;
-    S[2 * e] = R[e % (p * p)];
+    const double* src = (R_alt && *use_alt) ? R_alt : R;
+    S[2 * e] = src[e % (p * p)];
     S[2 * e + 1] = 0.0;
 }
 
@@ -778,9 +1115,25 @@ cudaError_t launch_reduce_h(const double* part, int nblk_req, int cols, int p, d
     return cudaGetLastError();
 }
 
+cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int nblk, double* G, double* part,
+                                 unsigned* ctr, int mode, double* R, double* Rinv, const double* Rtot_in,
+                                 double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
+                                 int* flags, double* out, int64_t ldo, cudaStream_t s) {
+    if (p > RP) return cudaErrorInvalidValue;
+    const int64_t rpb = rows_per_block(n, nblk);
+    const int g = blocks_for(n, nblk);
+    if (mode == 0)
+        k_qr_mixed_rows<1><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H,
+                                            ldH, hrow, hcol, normsq_out, flags, out, ldo);
+    else
+        k_qr_mixed_rows<2><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H,
+                                            ldH, hrow, hcol, normsq_out, flags, out, ldo);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
                                int p, int64_t n, const double* h, double* part, int nblk,
-                               int gram, cudaStream_t s, int f32, int upd32) {
+                               int gram, cudaStream_t s, int f32, int upd32, double* G, unsigned* ctr) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
     size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1) + TR * p);
@@ -790,10 +1143,10 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
     if (gram && p <= RP) {
         if (upd32)
             k_update_gram_rows<true><<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, W, ldw, p, n,
-                                                                                       rpb, h, part);
+                                                                                       rpb, h, part, G, ctr);
         else
             k_update_gram_rows<false><<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, W, ldw, p, n,
-                                                                                        rpb, h, part);
+                                                                                        rpb, h, part, G, ctr);
         return cudaGetLastError();
     }
     if (upd32 && gram)
@@ -850,9 +1203,10 @@ cudaError_t launch_combine(const double* Wc_slots, int npoles, int rows, int p, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_S(const double* R, int p, int npoles, double* S, cudaStream_t s) {
+cudaError_t launch_init_S(const double* R, int p, int npoles, double* S, cudaStream_t s, const double* R_alt,
+                          const int* use_alt) {
     const int tot = npoles * p * p;
-    k_init_S<<<(tot + 127) / 128, 128, 0, s>>>(R, p, npoles, S);
+    k_init_S<<<(tot + 127) / 128, 128, 0, s>>>(R, p, npoles, S, R_alt, use_alt);
     return cudaGetLastError();
 }
 
