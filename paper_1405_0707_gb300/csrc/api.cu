@@ -323,7 +323,9 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     const int f32 = P->opts.precision == EXPM_PREC_MIXED ? 1 : 0;
     LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, P->nblk, s, f32));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
-    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s, f32));
+    // first pass update: FP64, or double-float on the FP32 pipe in the mixed path (f32 = 2)
+    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s,
+                                              f32 ? 2 : 0));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
     // second pass: in the mixed path the update is an O(eps_32) correction, formed in FP32;
     // with the fused QR its last CTA also reduces the Gram partials

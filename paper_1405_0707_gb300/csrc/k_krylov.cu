@@ -275,6 +275,135 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
     }
 }
 
+// ---- double-float (FP32 pair) arithmetic for the mixed path's first CGS update
+// v = hi + lo with hi = v truncated to 24 significant bits (exact as a float) and lo the
+// remainder rounded to a float (relative error 2^-48 of v), built from the bit pattern with
+// integer and FP32 operations only.  Values below 2^-74 in magnitude keep hi = (float)v.
+__device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 949 || e > 1150) {          // outside the range where the split is exact
+        hi = (float)v;
+        lo = 0.f;
+        return;
+    }
+    hi = (float)__longlong_as_double(b & ~((1LL << 29) - 1));
+    const float mag = (float)(int)(b & ((1LL << 29) - 1)) * __int_as_float((e - 1075 + 127) << 23);
+    lo = (b < 0) ? -mag : mag;
+}
+
+// s + x into the pair (s, c): TwoSum for the large parts, the rounding error into c
+__device__ __forceinline__ void df_add(float& s, float& c, float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (x - bp);
+    s = t;
+    c += err;
+}
+
+// W <- W - V h with V h formed in double-float arithmetic on the FP32 pipe (mixed path, first
+// CGS pass), then the FP32 partials of V^T W for the second pass.  Each product
+// v h = vh hh + (err(vh hh) + vh hl + vl hh) with the FP32 product error recovered by an FMA;
+// the large parts are accumulated with TwoSum, the small ones in FP32, and W is updated in
+// FP64 by the pair's value.  Relative error ~ cols 2^-48 of |V h|, which keeps the Arnoldi
+// relation exact far below the accuracy the mixed path delivers.  The work items (row, column)
+// of a tile are split over S = NT / (TR p) threads each when that is more than one; their
+// partial pairs are combined in a fixed order.
+template <int OPT>
+__global__ void __launch_bounds__(NT) k_update_df(const double* __restrict__ V, int64_t ldv, int cols,
+                                                  double* __restrict__ W, int64_t ldw, int p, int64_t n,
+                                                  int64_t rpb, const double* __restrict__ h,
+                                                  double* __restrict__ part) {
+    extern __shared__ double sm[];
+    const int cs = cols | 1;
+    float* hh = reinterpret_cast<float*>(sm);       // cols x p
+    float* hl = hh + cols * p;
+    float* Vh = hl + cols * p;                      // TR x cs
+    float* Vl = Vh + TR * cs;
+    float* Wf = Vl + TR * cs;                       // TR x p
+    float* cmb = Wf + TR * p;                       // 2 NT
+    for (int e = threadIdx.x; e < cols * p; e += blockDim.x) split_df(h[e], hh[e], hl[e]);
+    const int nitems = TR * p;
+    const int S = nitems >= NT ? 1 : NT / nitems;
+    const int nout = cols * p;
+    double acc[OPT];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) acc[q] = 0.0;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r0 = rb; r0 < re; r0 += TR) {
+        const int tr = (int)min((int64_t)TR, re - r0);
+        for (int e = threadIdx.x; e < TR * cols; e += blockDim.x) {
+            const int rr = e % TR, a = e / TR;
+            float vh = 0.f, vl = 0.f;
+            if (rr < tr) split_df(V[(int64_t)a * ldv + r0 + rr], vh, vl);
+            Vh[rr * cs + a] = vh;
+            Vl[rr * cs + a] = vl;
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < S * nitems; it += blockDim.x) {
+            const int item = it % nitems, seg = it / nitems;
+            const int rr = item % TR, c = item / TR;
+            float sh = 0.f, sc = 0.f;
+            for (int a = seg; a < cols; a += S) {
+                const float vh = Vh[rr * cs + a], vl = Vl[rr * cs + a];
+                const float h1 = hh[a * p + c], h2 = hl[a * p + c];
+                const float pr = vh * h1;
+                float t = fmaf(vh, h1, -pr);
+                t = fmaf(vl, h1, t);
+                t = fmaf(vh, h2, t);
+                df_add(sh, sc, pr);
+                sc += t;
+            }
+            if (S > 1) {
+                cmb[2 * it] = sh;
+                cmb[2 * it + 1] = sc;
+            } else {
+                double w = 0.0;
+                if (rr < tr) {
+                    w = W[(int64_t)c * ldw + r0 + rr] - ((double)sh + (double)sc);
+                    W[(int64_t)c * ldw + r0 + rr] = w;
+                }
+                Wf[rr * p + c] = (float)w;
+            }
+        }
+        if (S > 1) {
+            __syncthreads();
+            for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
+                const int rr = item % TR, c = item / TR;
+                float sh = cmb[2 * item], sc = cmb[2 * item + 1];
+                for (int sg = 1; sg < S; ++sg) {
+                    df_add(sh, sc, cmb[2 * (sg * nitems + item)]);
+                    sc += cmb[2 * (sg * nitems + item) + 1];
+                }
+                double w = 0.0;
+                if (rr < tr) {
+                    w = W[(int64_t)c * ldw + r0 + rr] - ((double)sh + (double)sc);
+                    W[(int64_t)c * ldw + r0 + rr] = w;
+                }
+                Wf[rr * p + c] = (float)w;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) {
+            const int o = threadIdx.x + q * NT;
+            if (o < nout) {
+                const int a = o / p, c = o % p;
+                float sf = 0.f;
+#pragma unroll
+                for (int rr = 0; rr < TR; ++rr) sf = fmaf(Vh[rr * cs + a], Wf[rr * p + c], sf);
+                acc[q] += (double)sf;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+        const int o = threadIdx.x + q * NT;
+        if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+    }
+}
+
 // Cholesky-QR factor step, one CTA.  G = sum of the p x p partials (all CHOL_T threads),
 // then one warp factorises.  Pass modes (the QR of a block runs 3 passes, the third only
 // when needed; the decision is made on the device so a captured graph stays valid):
@@ -1152,7 +1281,10 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
     if (upd32 && gram)
         EXPM_OPT_DISPATCH(nout, (k_update<O, false, true><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part,
                                                                              gram)));
-    else if (f32)
+    else if (f32 && !gram && f32 == 2) {
+        const size_t shm_df = sizeof(float) * (2 * (size_t)cols * p + 2 * TR * (cols | 1) + TR * p + 2 * NT);
+        EXPM_OPT_DISPATCH(nout, (k_update_df<O><<<g, NT, shm_df, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part)));
+    } else if (f32)
         EXPM_OPT_DISPATCH(nout, (k_update<O, true><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
     else
         EXPM_OPT_DISPATCH(nout, (k_update<O, false><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, gram)));
@@ -1254,6 +1386,7 @@ cudaError_t krylov_set_smem_limits() {
     EXPM_SET((k_update<16, true>)); EXPM_SET((k_update<64, true>));
     EXPM_SET((k_update<1, false, true>)); EXPM_SET((k_update<4, false, true>));
     EXPM_SET((k_update<16, false, true>)); EXPM_SET((k_update<64, false, true>));
+    EXPM_SET(k_update_df<1>); EXPM_SET(k_update_df<4>); EXPM_SET(k_update_df<16>); EXPM_SET(k_update_df<64>);
     EXPM_SET(k_update_z);
     EXPM_SET(k_update_gram_rows<false>);
     EXPM_SET(k_update_gram_rows<true>);
