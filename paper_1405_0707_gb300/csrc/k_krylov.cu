@@ -106,33 +106,48 @@ __device__ inline void gram_write(const double* acc, int p, int nout, double* __
 // partial[blk][a][c] = sum_{rows of blk} V[r, a] W[r, c]      (a < cols, c < p)
 // T = float: FP32 products over each 16-row tile (the mixed path's projections; only the
 // FP64 updates must be exact for the Arnoldi relation), FP64 accumulation across tiles.
+// Tiles of trp rows (64 when the tiles fit in 100 KB of shared memory, else 32 or 16): more
+// loads in flight per barrier round than the 16-row tiles of the update kernels (the
+// projection's own arithmetic is small).
+template <typename T>
+__device__ inline void load_tile_p(const double* __restrict__ X, int64_t ld, int cols, int64_t r0,
+                                   int tr, T* S, int cs, int trp) {
+    for (int e = threadIdx.x; e < trp * cols; e += blockDim.x) {
+        const int rr = e % trp, a = e / trp;
+        S[rr * cs + a] = (rr < tr) ? (T)X[(int64_t)a * ld + r0 + rr] : (T)0;
+    }
+}
+
 template <int OPT, typename T>
 __global__ void __launch_bounds__(NT) k_proj(const double* __restrict__ V, int64_t ldv, int cols,
                                              const double* __restrict__ W, int64_t ldw, int p,
-                                             int64_t n, int64_t rpb, double* __restrict__ part) {
+                                             int64_t n, int64_t rpb, double* __restrict__ part, int TRP) {
     extern __shared__ double sm[];
     const int cs = cols | 1;
     T* Vs = reinterpret_cast<T*>(sm);
-    T* Ws = Vs + TR * cs;
+    T* Ws = Vs + TRP * cs;
     const int nout = cols * p;
     double acc[OPT];
 #pragma unroll
     for (int q = 0; q < OPT; ++q) acc[q] = 0.0;
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
-    for (int64_t r0 = rb; r0 < re; r0 += TR) {
-        const int tr = (int)min((int64_t)TR, re - r0);
-        load_tile(V, ldv, cols, r0, tr, Vs, cs);
-        load_tile(W, ldw, p, r0, tr, Ws, p);
+    for (int64_t r0 = rb; r0 < re; r0 += TRP) {
+        const int tr = (int)min((int64_t)TRP, re - r0);
+        load_tile_p(V, ldv, cols, r0, tr, Vs, cs, TRP);
+        load_tile_p(W, ldw, p, r0, tr, Ws, p, TRP);
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < OPT; ++q) {
             const int o = threadIdx.x + q * NT;
             if (o < nout) {
                 const int a = o / p, c = o % p;
-                T s = 0;
-#pragma unroll
-                for (int rr = 0; rr < TR; ++rr) s = fma(Vs[rr * cs + a], Ws[rr * p + c], s);
-                acc[q] += (double)s;
+                T s0 = 0, s1 = 0;
+#pragma unroll 8
+                for (int rr = 0; rr < TRP; rr += 2) {
+                    s0 = fma(Vs[rr * cs + a], Ws[rr * p + c], s0);
+                    s1 = fma(Vs[(rr + 1) * cs + a], Ws[(rr + 1) * p + c], s1);
+                }
+                acc[q] += (double)s0 + (double)s1;
             }
         }
         __syncthreads();
@@ -1227,11 +1242,15 @@ cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const do
                                 cudaStream_t s, int f32) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
-    const size_t shm = sizeof(double) * (TR * (cols | 1) + TR * p);
+    const size_t esz = f32 ? sizeof(float) : sizeof(double);
+    int trp = 64;
+    while (trp > TR && esz * trp * ((cols | 1) + p) > 100 * 1024) trp /= 2;
+    const size_t shm = esz * trp * ((cols | 1) + p);
     if (f32)
-        EXPM_OPT_DISPATCH(cols * p, (k_proj<O, float><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, part)));
+        EXPM_OPT_DISPATCH(cols * p, (k_proj<O, float><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, part, trp)));
     else
-        EXPM_OPT_DISPATCH(cols * p, (k_proj<O, double><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, part)));
+        EXPM_OPT_DISPATCH(cols * p, (k_proj<O, double><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, part,
+                                                                         trp)));
     return cudaGetLastError();
 }
 
