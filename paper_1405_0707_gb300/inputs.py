@@ -13,6 +13,10 @@ sizes and times below are the synthetic stand-ins described in the design doc):
                n = 65536, p = 8, t in {1e-3, 1e-2, 1e-1}, m = 10
   toeplitz-1m  t T, T symmetric Toeplitz with first column a_0 = -2 - c, a_k = 1/(1+k)^2
                (1 <= k <= 256), c = 0, n = 2^20, p = 16, t = 1, m = 10
+  batched3d-64 64 independent instances t (Laplacian_h - v . grad_h) on N_x x N_y x N_z grids,
+               N_d uniform in {32..96} per axis, v ~ 5 N(0, I_3) (redrawn if a cell Peclet
+               number |v_d| h_d / 2 reaches 1), t = 10^U(-3, 0), p uniform in {1..16}, m = 10,
+               mixed precision (batched3d_instances)
 """
 from __future__ import annotations
 
@@ -27,10 +31,27 @@ WORKLOADS = {
                      tol=1e-10, seed=SEED_BASE + 2),
     "toeplitz-1m": dict(n=1 << 20, bw=256, c=0.0, t=(1.0,), p=16, m=10, tol=1e-13,
                         seed=SEED_BASE + 3),
+    "batched3d-64": dict(count=64, m=10, tol=1e-10, seed=SEED_BASE + 4),
     # differentiation: L = ||r(tA) B - Y||_F^2, Y = r(t0 A) B0 (t0, B0 seeded perturbations)
     "cd2d-512-grad": dict(sides=(512, 512), diff=0.1, vel=(1.0, 1.0), t=(1e-2,), p=32, m=10,
                           tol=1e-10, seed=SEED_BASE + 5),
 }
+
+
+def batched3d_instances(count=64, seed=SEED_BASE + 4):
+    """The seeded instance list of the batched workload: dicts with sides, diff (1), vel, t, p
+    and the seed of the instance's right-hand side."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    while len(out) < count:
+        sides = tuple(int(x) for x in rng.integers(32, 97, size=3))
+        vel = tuple(float(x) for x in 5.0 * rng.standard_normal(3))
+        t = float(10.0 ** rng.uniform(-3.0, 0.0))
+        p = int(rng.integers(1, 17))
+        if any(abs(v) / (2.0 * (N + 1)) >= 1.0 for v, N in zip(vel, sides)):
+            continue
+        out.append(dict(sides=sides, diff=1.0, vel=vel, t=t, p=p, seed=seed + 1000 + len(out)))
+    return out
 
 
 def toeplitz_column(bw, c=0.0):
