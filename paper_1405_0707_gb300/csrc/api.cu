@@ -921,7 +921,13 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         delete P;
         return EXPM_CUDA_ERROR;
     }
-    P->nblk = consistent_blocks(n, std::max(1, std::min<int>(2 * sms, (int)((n + 63) / 64))));
+    {
+        // CTAs of the row-parallel passes: blocks_per_sm x SMs, at least 64 rows each
+        int per_sm = 2;
+        const char* bs = std::getenv("EXPM_BLOCKS_PER_SM");   // tuning knob (1..8)
+        if (bs && bs[0] >= '1' && bs[0] <= '8' && bs[1] == 0) per_sm = bs[0] - '0';
+        P->nblk = consistent_blocks(n, std::max(1, std::min<int>(per_sm * sms, (int)((n + 63) / 64))));
+    }
     const int m = opts->m;
     const int64_t ld = P->ld;
     P->ldH = (m + 1) * p_max;

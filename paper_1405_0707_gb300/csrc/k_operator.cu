@@ -202,10 +202,15 @@ __global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __
 // FP32 arithmetic for the DST-I transforms of the exact inverse; the result is refined
 // in FP64 by the caller (residual with the FP64 stencil, Theorem 4.3 bounds what an
 // inexact inverse costs).  TA / TC: element types of A and C; acc: C += A B.
+constexpr int BK32 = 32;   // k-depth of one FP32 tile
+
+// FP32 tiles of 64 x 64 outputs, 4 x 4 per thread; the next k-tile's global loads are
+// issued into registers before the current tile's FMAs (software pipelining), so each
+// barrier round overlaps its loads with arithmetic.
 template <bool CM, typename TA, typename TC>
 __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
-    __shared__ float As[BK][BM + 1];
-    __shared__ float Bs[BK][BN];
+    __shared__ float As[BK32][BM + 1];
+    __shared__ float Bs[BK32][BN];
     const int b1 = blockIdx.z % g.nb1, b2 = blockIdx.z / g.nb1;
     const TA* A = reinterpret_cast<const TA*>(g.A) + b1 * g.a_b1 + b2 * g.a_b2;
     TC* C = reinterpret_cast<TC*>(g.C) + b1 * g.c_b1 + b2 * g.c_b2;
@@ -217,26 +222,41 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < g.K; k0 += BK) {
+    constexpr int NQ = BK32 * BM / 256;   // elements of each tile per thread (8)
+    float ra[NQ], rb[NQ];
+    auto fetch = [&](int k0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int e = tid + q * 256;
             int mm, kk;
             if (a_mfast) { mm = e % BM; kk = e / BM; }
-            else { kk = e % BK; mm = e / BK; }
+            else { kk = e % BK32; mm = e / BK32; }
             const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < g.M && gk < g.K) ? (float)A[(int64_t)gm * g.a_rs + (int64_t)gk * g.a_cs] : 0.f;
+            ra[q] = (gm < g.M && gk < g.K) ? (float)A[(int64_t)gm * g.a_rs + (int64_t)gk * g.a_cs] : 0.f;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int e = tid + q * 256;
             const int nn = e % BN, kk = e / BN;
             const int gn = n0 + nn, gk = k0 + kk;
-            Bs[kk][nn] = (gn < g.N && gk < g.K) ? g.B[(int64_t)gk * g.ldb + gn] : 0.f;
+            rb[q] = (gn < g.N && gk < g.K) ? g.B[(int64_t)gk * g.ldb + gn] : 0.f;
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < g.K; k0 += BK32) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int e = tid + q * 256;
+            int mm, kk;
+            if (a_mfast) { mm = e % BM; kk = e / BM; }
+            else { kk = e % BK32; mm = e / BK32; }
+            As[kk][mm] = ra[q];
+            Bs[e / BN][e % BN] = rb[q];
         }
         __syncthreads();
+        if (k0 + BK32 < g.K) fetch(k0 + BK32);
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
+        for (int kk = 0; kk < BK32; ++kk) {
             float a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[kk][(CM ? tx : ty) + 16 * i];
