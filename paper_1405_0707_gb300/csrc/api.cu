@@ -957,7 +957,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         ok = ok && P->hcert != nullptr;
     }
     if (poles_smem_bytes(mpm, p_max) == 0)   // elimination does not fit in shared memory
-        ok = ok && dalloc(&P->poles, (size_t)P->npoles * ((size_t)mpm * mpm + (size_t)mpm * p_max) * 2);
+        ok = ok && dalloc(&P->poles, (size_t)P->npoles * ((size_t)mpm * mpm + 2 * (size_t)mpm * p_max) * 2);
     ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hpin), sizeof(double) * kStatDoubles) == cudaSuccess;
     ok = ok && dalloc(&P->dotpart, (size_t)dot_blocks() * p_max) &&
          cudaMallocHost(reinterpret_cast<void**>(&P->hdot), sizeof(double) * dot_blocks() * p_max) == cudaSuccess;

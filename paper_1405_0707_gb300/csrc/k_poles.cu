@@ -49,19 +49,23 @@ __device__ inline cplx crecip(cplx d) {
 }
 
 // One CTA (four warps) per pole.  Shared memory holds M (mp x mp complex, row-major), the
-// right-hand sides / solution X (mp x p complex) and, when it fits, the real H~ ((mp+p) x mp),
-// staged once with coalesced loads.  Outputs: the restart factor S_i, ||S_i||_F and
-// Y_i = 2 Re(omega_i Z_i) (mp x p real).  Since H~ is real, sum_i 2 Re(omega_i H~ Z_i) =
-// H~ sum_i Y_i, so the product with H~ is done once for all poles by k_combine2.
+// right-hand sides / solution X (mp x p complex), the inverses of U's diagonal blocks
+// (mp x p complex) and, when it fits, the real H~ ((mp+p) x mp), staged once with coalesced
+// loads.  Outputs: the restart factor S_i, ||S_i||_F and Y_i = 2 Re(omega_i Z_i) (mp x p
+// real).  Since H~ is real, sum_i 2 Re(omega_i H~ Z_i) = H~ sum_i Y_i, so the product with H~
+// is done once for all poles by k_combine2.
 //
 // M is block upper Hessenberg with p x p blocks (H_m is band Hessenberg with p sub-diagonals),
 // so Gaussian elimination with partial pivoting is blocked by block columns J:
-//   panel   (warp 0): LU with partial pivoting of the 2p x p block [M_JJ; M_J+1,J] (pivots
-//           are searched only in those rows, as the band allows); full rows are swapped, the
-//           multipliers stored in place, the pivots' reciprocals kept;
-//   update  (all threads, one column each): U_J,c = L_JJ^{-1} M_J,c and
-//           M_J+1,c -= L_J+1,J U_J,c for every later column c of M and every column of X;
-// then blocked back substitution: X_J = U_JJ^{-1} X_J, X_0..J-1 -= U_0..J-1,J X_J.
+//   panel   (2p x p block [M_JJ; M_J+1,J], column by column, all threads): pivot searched
+//           among the panel rows only (the band) on FP32 magnitudes, full rows swapped, one
+//           reciprocal per pivot, multipliers stored in place, the panel's own columns updated;
+//   update  U_J,c = L_JJ^{-1} M_J,c (one column per thread), then M_J+1,c -= L_J+1,J U_J,c
+//           (one (row, column) pair per thread) for every later column c of M and of X;
+// then the inverses of the diagonal blocks U_JJ (one block column per thread, all blocks at
+// once) and the blocked back substitution X_J = U_JJ^{-1} X_J, X_0..J-1 -= U_0..J-1,J X_J as
+// parallel products.  FP64 throughout; the FP64 pipe of one SM is the bound, so the layout
+// keeps every lane of every warp busy wherever the work allows.
 __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict__ H, int ldH, int mp, int p,
                                                         const double* __restrict__ tau_re,
                                                         const double* __restrict__ tau_im,
@@ -74,16 +78,18 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
     extern __shared__ double sm[];
     __shared__ cplx rdiag[kMaxMP];
     __shared__ double red[kPoleThreads];
+    __shared__ int piv_s;
     const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
     const cplx tau{tau_re[i], tau_im[i]};
     const cplx om{om_re[i], om_im[i]};
-    const size_t per = (size_t)mp * mp + (size_t)mp * p;
+    const size_t per = (size_t)mp * mp + 2 * (size_t)mp * p;
     cplx* M = use_smem ? reinterpret_cast<cplx*>(sm) : reinterpret_cast<cplx*>(work) + (size_t)i * per;
     cplx* X = M + (size_t)mp * mp;
+    cplx* Ui = X + (size_t)mp * p;          // Ui[J p + a][b] = (U_JJ^{-1})[a][b]
     cplx* Si = reinterpret_cast<cplx*>(S) + (size_t)i * p * p;
     const int rows = mp + p;
-    // H~ (rows x mp, column-major, ld = rows) in shared memory after M and X when it fits
+    // H~ (rows x mp, column-major, ld = rows) in shared memory after M, X and Ui when it fits
     double* Hs = reinterpret_cast<double*>(sm) + (use_smem ? 2 * per : 0);
     const double* Hr = h_in_smem ? Hs : H;
     const int ldr = h_in_smem ? rows : ldH;
@@ -108,84 +114,117 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
     for (int J = 0; J < nbc; ++J) {
         const int r0 = J * p;
         const int rend = (J + 1 < nbc) ? r0 + 2 * p : r0 + p;   // panel rows r0 .. rend-1
-        if (warp == 0) {
-            for (int jj = 0; jj < p; ++jj) {
-                const int c = r0 + jj;
-                // pivot: arg-max of |M[r][c]|^2 over the panel rows r >= c (ties -> smallest r)
-                double best = -1.0;
+        for (int jj = 0; jj < p; ++jj) {
+            const int c = r0 + jj;
+            if (warp == 0) {
+                // pivot: arg-max of |M[r][c]|^2 in FP32 over the panel rows r >= c
+                float best = -1.f;
                 int piv = c;
                 for (int r = c + lane; r < rend; r += 32) {
-                    const double v = cabs2(M[(size_t)r * mp + c]);
-                    if (v > best) { best = v; piv = r; }
+                    const cplx v = M[(size_t)r * mp + c];
+                    const float fr = (float)v.re, fi = (float)v.im;
+                    const float m = fmaf(fr, fr, fi * fi);
+                    if (m > best) { best = m; piv = r; }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
                     const int op = __shfl_xor_sync(0xffffffffu, piv, o);
                     if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
                 }
-                if (lane == 0 && !(best > 0.0)) atomicOr(&flags[0], 2);
-                if (piv != c) {   // swap the full rows (M from column r0 on, and X)
-                    for (int k = r0 + lane; k < mp; k += 32) {
-                        const cplx a = M[(size_t)c * mp + k];
-                        M[(size_t)c * mp + k] = M[(size_t)piv * mp + k];
-                        M[(size_t)piv * mp + k] = a;
-                    }
-                    for (int k = lane; k < p; k += 32) {
-                        const cplx a = X[(size_t)c * p + k];
-                        X[(size_t)c * p + k] = X[(size_t)piv * p + k];
-                        X[(size_t)piv * p + k] = a;
-                    }
-                    __syncwarp();
-                }
-                const cplx inv = crecip(M[(size_t)c * mp + c]);
-                if (lane == 0) rdiag[c] = inv;
-                // multipliers of the panel rows below, and the rest of the panel's columns
-                for (int r = c + 1 + lane; r < rend; r += 32) {
-                    const cplx l = cmul(M[(size_t)r * mp + c], inv);
-                    M[(size_t)r * mp + c] = l;
-                    for (int k = c + 1; k < r0 + p; ++k) cmsub(M[(size_t)r * mp + k], l, M[(size_t)c * mp + k]);
-                }
-                __syncwarp();
+                if (lane == 0) piv_s = piv;
             }
+            __syncthreads();
+            const int piv = piv_s;
+            if (piv != c) {   // swap the full rows (M from column r0 on, and X)
+                for (int k = r0 + tid; k < mp; k += nt) {
+                    const cplx a = M[(size_t)c * mp + k];
+                    M[(size_t)c * mp + k] = M[(size_t)piv * mp + k];
+                    M[(size_t)piv * mp + k] = a;
+                }
+                for (int k = tid; k < p; k += nt) {
+                    const cplx a = X[(size_t)c * p + k];
+                    X[(size_t)c * p + k] = X[(size_t)piv * p + k];
+                    X[(size_t)piv * p + k] = a;
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                const cplx d = M[(size_t)c * mp + c];
+                const double n2 = d.re * d.re + d.im * d.im;
+                if (!(n2 > 0.0)) atomicOr(&flags[0], 2);
+                const double x = 1.0 / n2;
+                rdiag[c] = cplx{d.re * x, -d.im * x};
+            }
+            __syncthreads();
+            const cplx inv = rdiag[c];
+            const int nr = rend - c - 1, wc = r0 + p - c - 1;
+            for (int r = c + 1 + tid; r < rend; r += nt) M[(size_t)r * mp + c] = cmul(M[(size_t)r * mp + c], inv);
+            __syncthreads();
+            for (int e = tid; e < nr * wc; e += nt) {
+                const int r = c + 1 + e / wc, k = c + 1 + e % wc;
+                cmsub(M[(size_t)r * mp + k], M[(size_t)r * mp + c], M[(size_t)c * mp + k]);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        // trailing update, one column per thread: columns of M right of the panel, then X
+        // trailing update: columns of M right of the panel, then the columns of X
         const int ncm = mp - r0 - p, ncol = ncm + p;
-        for (int base = 0; base < ncol; base += nt) {
-            // eight consecutive columns per lane group, interleaved over the warps
-            const int q = base + 32 * (lane >> 3) + 8 * warp + (lane & 7);
-            if (q >= ncol) continue;
+        for (int q = tid; q < ncol; q += nt) {      // U_J,c = L_JJ^{-1} M_J,c (unit lower)
             cplx* col;
             size_t ld;
             if (q < ncm) { col = M + r0 + p + q; ld = mp; }
             else { col = X + (q - ncm); ld = p; }
-            for (int a = 1; a < p; ++a) {          // U_J,c = L_JJ^{-1} M_J,c (unit lower)
+            for (int a = 1; a < p; ++a) {
                 cplx s = col[(size_t)(r0 + a) * ld];
                 for (int k = 0; k < a; ++k) cmsub(s, M[(size_t)(r0 + a) * mp + r0 + k], col[(size_t)(r0 + k) * ld]);
                 col[(size_t)(r0 + a) * ld] = s;
             }
-            if (rend > r0 + p)
-                for (int a = 0; a < p; ++a) {      // M_J+1,c -= L_J+1,J U_J,c
-                    const int r = r0 + p + a;
-                    cplx s = col[(size_t)r * ld];
-                    for (int k = 0; k < p; ++k) cmsub(s, M[(size_t)r * mp + r0 + k], col[(size_t)(r0 + k) * ld]);
-                    col[(size_t)r * ld] = s;
-                }
         }
         __syncthreads();
+        if (rend > r0 + p)
+            for (int e = tid; e < p * ncol; e += nt) {   // M_J+1,c -= L_J+1,J U_J,c
+                const int a = e / ncol, q = e % ncol;
+                cplx* col;
+                size_t ld;
+                if (q < ncm) { col = M + r0 + p + q; ld = mp; }
+                else { col = X + (q - ncm); ld = p; }
+                const int r = r0 + p + a;
+                cplx s = col[(size_t)r * ld];
+                for (int k = 0; k < p; ++k) cmsub(s, M[(size_t)r * mp + r0 + k], col[(size_t)(r0 + k) * ld]);
+                col[(size_t)r * ld] = s;
+            }
+        __syncthreads();
     }
-    // blocked back substitution on the upper triangle
+    // inverses of the diagonal blocks U_JJ (upper triangular), one block column per thread
+    for (int e = tid; e < nbc * p; e += nt) {
+        const int J = e / p, b = e % p, r0 = J * p;
+        for (int a = p - 1; a >= 0; --a) {
+            cplx s{a == b ? 1.0 : 0.0, 0.0};
+            for (int k = a + 1; k <= b; ++k) cmsub(s, M[(size_t)(r0 + a) * mp + r0 + k], Ui[(size_t)(r0 + k) * p + b]);
+            Ui[(size_t)(r0 + a) * p + b] = (a > b) ? cplx{0.0, 0.0} : cmul(s, rdiag[r0 + a]);
+        }
+    }
+    __syncthreads();
+    // blocked back substitution
     for (int J = nbc - 1; J >= 0; --J) {
         const int r0 = J * p;
-        if (tid < p) {                              // X_J = U_JJ^{-1} X_J, one column per thread
-            const int c = tid;
-            for (int a = p - 1; a >= 0; --a) {
-                cplx s = X[(size_t)(r0 + a) * p + c];
-                for (int k = a + 1; k < p; ++k) cmsub(s, M[(size_t)(r0 + a) * mp + r0 + k], X[(size_t)(r0 + k) * p + c]);
-                X[(size_t)(r0 + a) * p + c] = cmul(s, rdiag[r0 + a]);
+        // X_J = U_JJ^{-1} X_J: outputs (a, c); the old X_J is read before any is written
+        constexpr int kXo = (kMaxP * kMaxP + kPoleThreads - 1) / kPoleThreads;
+        cplx xo[kXo];
+        int cnt = 0;
+        for (int e = tid; e < p * p; e += nt, ++cnt) {
+            const int a = e / p, c = e % p;
+            cplx s{0.0, 0.0};
+            for (int k = a; k < p; ++k) {
+                const cplx u = Ui[(size_t)(r0 + a) * p + k], x = X[(size_t)(r0 + k) * p + c];
+                s.re = fma(u.re, x.re, fma(-u.im, x.im, s.re));
+                s.im = fma(u.re, x.im, fma(u.im, x.re, s.im));
             }
+            xo[cnt] = s;
         }
+        __syncthreads();
+        cnt = 0;
+        for (int e = tid; e < p * p; e += nt, ++cnt) X[(size_t)(r0 + e / p) * p + e % p] = xo[cnt];
         __syncthreads();
         for (int e = tid; e < r0 * p; e += nt) {   // X_0..J-1 -= U_0..J-1,J X_J
             const int r = e / p, c = e % p;
@@ -293,7 +332,7 @@ cudaError_t launch_certify_coeffs(const double* H, int ldH, int mp, int p, int n
 }
 
 size_t poles_smem_bytes(int mp, int p) {
-    const size_t b = ((size_t)mp * mp + (size_t)mp * p) * sizeof(cplx);
+    const size_t b = ((size_t)mp * mp + 2 * (size_t)mp * p) * sizeof(cplx);
     return b <= kSmemLimit ? b : 0;
 }
 
