@@ -176,23 +176,30 @@ __device__ inline double stripe_sum(const double* __restrict__ part, int nblk, i
     return (a0 + a1) + (a2 + a3);
 }
 
-constexpr int RED_OUT = 32;       // outputs per reduction CTA
-constexpr int RED_STRIPES = 8;    // threads per output
+constexpr int RED_OUT = 8;        // outputs per reduction CTA
+constexpr int RED_STRIPES = 32;   // threads per output
 
-// h[o] = sum_b part[b][o]; H[row0 + a, col0 + c] (+)= h[a][c].  CTA = 32 outputs x 8 stripes.
+// h[o] = sum_b part[b][o]; H[row0 + a, col0 + c] (+)= h[a][c].  CTA = 8 outputs x 32 stripes;
+// the stripes are added in two fixed-order levels (4 groups of 8, then the 4 groups).
 __global__ void __launch_bounds__(RED_OUT * RED_STRIPES)
 k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p, double* __restrict__ h,
            double* H, int ldH, int row0, int col0, int accumulate) {
     __shared__ double red[RED_STRIPES][RED_OUT];
+    __shared__ double red2[4][RED_OUT];
     const int nout = cols * p;
     const int ol = threadIdx.x % RED_OUT, st = threadIdx.x / RED_OUT;
     const int o = blockIdx.x * RED_OUT + ol;
     red[st][ol] = (o < nout) ? stripe_sum(part, nblk, nout, o, st, RED_STRIPES) : 0.0;
     __syncthreads();
-    if (st != 0 || o >= nout) return;
-    double s = 0.0;
+    if (st < 4) {
+        double g = 0.0;
 #pragma unroll
-    for (int k = 0; k < RED_STRIPES; ++k) s += red[k][ol];
+        for (int k = 0; k < 8; ++k) g += red[st * 8 + k][ol];
+        red2[st][ol] = g;
+    }
+    __syncthreads();
+    if (st != 0 || o >= nout) return;
+    const double s = (red2[0][ol] + red2[1][ol]) + (red2[2][ol] + red2[3][ol]);
     h[o] = s;
     if (H) {
         const int a = o / p, c = o % p;
@@ -659,6 +666,29 @@ __device__ inline void warp_gram_rows(const double* y, double* buf, double& acc0
     __syncwarp();
 }
 
+// FP32 variant (the mixed path's Gram for the first Cholesky-QR pass, whose factorisation
+// is FP32 anyway): rows staged as floats, products and per-lane sums in FP32.
+__device__ inline void warp_gram_rows32(const double* y, float* buf, float& acc0, float& acc1) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < RP; ++c) buf[lane * RP + c] = (float)y[c];
+    __syncwarp();
+    for (int q = 0; q < 2; ++q) {
+        const int kk = lane + 32 * q;
+        if (kk < RG) {
+            int c1 = 0, rem = kk;
+            while (rem >= RP - c1) { rem -= RP - c1; ++c1; }
+            const int c2 = c1 + rem;
+            float s = 0.f;
+#pragma unroll 8
+            for (int rr = 0; rr < 32; ++rr) s = fmaf(buf[rr * RP + c1], buf[rr * RP + c2], s);
+            if (q == 0) acc0 += s;
+            else acc1 += s;
+        }
+    }
+    __syncwarp();
+}
+
 // The CTA's Gram partial (p x p layout, upper triangle; lower = 0) from the per-lane
 // accumulators of warp_gram_rows.
 __device__ inline void cta_gram_write(double acc0, double acc1, int p, double (*red)[RG],
@@ -690,8 +720,10 @@ __device__ inline bool take_last_ticket(unsigned* ctr) {
     return ticket == gridDim.x - 1;
 }
 
-// out[o] = sum_b part[b][o] for o < nout (nout <= RP * RP), by the last CTA: RED_S stripes
+// out[o] = sum_b part[b][o] for o < nout (nout <= RP * RP), by the last CTA: NT / nout stripes
 // per output, each stripe's loads issued back to back, stripes added in a fixed order.
+// ACC = float: FP32 sums (for a Gram matrix that only feeds an FP32 factorisation).
+template <typename ACC = double>
 __device__ inline void last_cta_sum(const double* part, int nblk, int nout, double* __restrict__ out,
                                     unsigned* ctr) {
     __shared__ double red[NT];
@@ -700,16 +732,16 @@ __device__ inline void last_cta_sum(const double* part, int nblk, int nout, doub
     const int o = threadIdx.x % nout, st = threadIdx.x / nout;
     double acc = 0.0;
     if (st < stripes) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        ACC a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         int b = st;
         for (; b + 3 * stripes < nblk; b += 4 * stripes) {
-            a0 += __ldcg(part + (int64_t)b * nout + o);
-            a1 += __ldcg(part + (int64_t)(b + stripes) * nout + o);
-            a2 += __ldcg(part + (int64_t)(b + 2 * stripes) * nout + o);
-            a3 += __ldcg(part + (int64_t)(b + 3 * stripes) * nout + o);
+            a0 += (ACC)__ldcg(part + (int64_t)b * nout + o);
+            a1 += (ACC)__ldcg(part + (int64_t)(b + stripes) * nout + o);
+            a2 += (ACC)__ldcg(part + (int64_t)(b + 2 * stripes) * nout + o);
+            a3 += (ACC)__ldcg(part + (int64_t)(b + 3 * stripes) * nout + o);
         }
-        for (; b < nblk; b += stripes) a0 += __ldcg(part + (int64_t)b * nout + o);
-        acc = (a0 + a1) + (a2 + a3);
+        for (; b < nblk; b += stripes) a0 += (ACC)__ldcg(part + (int64_t)b * nout + o);
+        acc = (double)((a0 + a1) + (a2 + a3));
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -1006,7 +1038,7 @@ __global__ void __launch_bounds__(NT) k_qr_mixed_rows(double* W, int64_t ldw, in
     }
     if (gram) {
         cta_gram_write(acc0, acc1, p, red, part);
-        if (take_last_ticket(ctr)) last_cta_sum(part, gridDim.x, pp, G, ctr);
+        if (take_last_ticket(ctr)) last_cta_sum<double>(part, gridDim.x, pp, G, ctr);
     }
 }
 
@@ -1075,6 +1107,7 @@ __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restric
     __syncthreads();
     __shared__ double buf[NT / 32][32 * RP];
     double acc0 = 0.0, acc1 = 0.0;
+    float facc0 = 0.f, facc1 = 0.f;
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
     for (int64_t r0 = rb + (threadIdx.x & ~31); r0 < re; r0 += blockDim.x) {
         const int64_t r = r0 + (threadIdx.x & 31);
@@ -1086,6 +1119,7 @@ __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restric
             float corr[RP];
 #pragma unroll
             for (int c = 0; c < RP; ++c) corr[c] = 0.f;
+#pragma unroll 8
             for (int a = 0; a < cols; ++a) {
                 const float v = (float)V[(int64_t)a * ldv + r];
 #pragma unroll
@@ -1094,6 +1128,7 @@ __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restric
 #pragma unroll
             for (int c = 0; c < RP; ++c) w[c] -= (double)corr[c];
         } else if (ok) {
+#pragma unroll 8
             for (int a = 0; a < cols; ++a) {
                 const double v = V[(int64_t)a * ldv + r];
 #pragma unroll
@@ -1103,10 +1138,18 @@ __global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restric
 #pragma unroll
         for (int c = 0; c < RP; ++c)
             if (ok && c < p) W[(int64_t)c * ldw + r] = w[c];
-        warp_gram_rows(w, buf[threadIdx.x >> 5], acc0, acc1);
+        if (UPD32) warp_gram_rows32(w, reinterpret_cast<float*>(buf[threadIdx.x >> 5]), facc0, facc1);
+        else warp_gram_rows(w, buf[threadIdx.x >> 5], acc0, acc1);
+    }
+    if (UPD32) {
+        acc0 = facc0;
+        acc1 = facc1;
     }
     cta_gram_write(acc0, acc1, p, red, part);
-    if (G && take_last_ticket(ctr)) last_cta_sum(part, gridDim.x, p * p, G, ctr);
+    if (G && take_last_ticket(ctr)) {
+        if (UPD32) last_cta_sum<float>(part, gridDim.x, p * p, G, ctr);
+        else last_cta_sum<double>(part, gridDim.x, p * p, G, ctr);
+    }
 }
 
 // Row-per-thread, p <= 8: Z[r, :] += V[r, 0:cols] Wc; restart copy V[r, 0:p] <- V[r, cols-p:cols].
