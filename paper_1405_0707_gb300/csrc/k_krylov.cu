@@ -51,6 +51,32 @@ __device__ inline TrsmPass trsm_pass(double* W, int64_t ldw, double* out, int64_
     return {out, ldo, 0, ex == 0};
 }
 
+// ---- double-float (FP32 pair) arithmetic for the mixed path's first CGS update
+// v = hi + lo with hi = v truncated to 24 significant bits (exact as a float) and lo the
+// remainder rounded to a float (relative error 2^-48 of v), built from the bit pattern with
+// integer and FP32 operations only.  Values below 2^-74 in magnitude keep hi = (float)v.
+__device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 949 || e > 1150) {          // outside the range where the split is exact
+        hi = (float)v;
+        lo = 0.f;
+        return;
+    }
+    hi = (float)__longlong_as_double(b & ~((1LL << 29) - 1));
+    const float mag = (float)(int)(b & ((1LL << 29) - 1)) * __int_as_float((e - 1075 + 127) << 23);
+    lo = (b < 0) ? -mag : mag;
+}
+
+// s + x into the pair (s, c): TwoSum for the large parts, the rounding error into c
+__device__ __forceinline__ void df_add(float& s, float& c, float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (x - bp);
+    s = t;
+    c += err;
+}
+
 // Gram partial of a TR x p tile X (row-major X[rr * p + c]), upper triangle only (the
 // Cholesky factorisation reads nothing else).  With p^2 <= NT every output gets NT / p^2
 // threads that take every (NT / p^2)-th row, so the dependent chains are short; gram_write
@@ -295,32 +321,6 @@ __global__ void __launch_bounds__(NT) k_update(const double* __restrict__ V, int
         const int o = threadIdx.x + q * NT;
         if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
     }
-}
-
-// ---- double-float (FP32 pair) arithmetic for the mixed path's first CGS update
-// v = hi + lo with hi = v truncated to 24 significant bits (exact as a float) and lo the
-// remainder rounded to a float (relative error 2^-48 of v), built from the bit pattern with
-// integer and FP32 operations only.  Values below 2^-74 in magnitude keep hi = (float)v.
-__device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
-    const long long b = __double_as_longlong(v);
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (e < 949 || e > 1150) {          // outside the range where the split is exact
-        hi = (float)v;
-        lo = 0.f;
-        return;
-    }
-    hi = (float)__longlong_as_double(b & ~((1LL << 29) - 1));
-    const float mag = (float)(int)(b & ((1LL << 29) - 1)) * __int_as_float((e - 1075 + 127) << 23);
-    lo = (b < 0) ? -mag : mag;
-}
-
-// s + x into the pair (s, c): TwoSum for the large parts, the rounding error into c
-__device__ __forceinline__ void df_add(float& s, float& c, float x) {
-    const float t = s + x;
-    const float bp = t - s;
-    const float err = (s - (t - bp)) + (x - bp);
-    s = t;
-    c += err;
 }
 
 // W <- W - V h with V h formed in double-float arithmetic on the FP32 pipe (mixed path, first
@@ -689,6 +689,43 @@ __device__ inline void warp_gram_rows32(const double* y, float* buf, float& acc0
     __syncwarp();
 }
 
+// Double-float variant (the mixed path's Gram matrix after the first Cholesky-QR pass, which
+// the deviation pass needs to ~1e-14): rows staged as (hi, lo) float pairs; each product
+// hi1 hi2 + (err(hi1 hi2) + hi1 lo2 + lo1 hi2) accumulated with TwoSum into a per-lane pair.
+__device__ inline void warp_gram_rows_df(const float* yh, const float* yl, float* buf, float* ah, float* al) {
+    const int lane = threadIdx.x & 31;
+    float* bh = buf;                 // 32 x RP
+    float* bl = buf + 32 * RP;       // 32 x RP
+#pragma unroll
+    for (int c = 0; c < RP; ++c) {
+        bh[lane * RP + c] = yh[c];
+        bl[lane * RP + c] = yl[c];
+    }
+    __syncwarp();
+    for (int q = 0; q < 2; ++q) {
+        const int kk = lane + 32 * q;
+        if (kk < RG) {
+            int c1 = 0, rem = kk;
+            while (rem >= RP - c1) { rem -= RP - c1; ++c1; }
+            const int c2 = c1 + rem;
+            float sh = ah[q], sl = al[q];
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const float h1 = bh[rr * RP + c1], h2 = bh[rr * RP + c2];
+                const float pr = h1 * h2;
+                float t = fmaf(h1, h2, -pr);
+                t = fmaf(h1, bl[rr * RP + c2], t);
+                t = fmaf(bl[rr * RP + c1], h2, t);
+                df_add(sh, sl, pr);
+                sl += t;
+            }
+            ah[q] = sh;
+            al[q] = sl;
+        }
+    }
+    __syncwarp();
+}
+
 // The CTA's Gram partial (p x p layout, upper triangle; lower = 0) from the per-lane
 // accumulators of warp_gram_rows.
 __device__ inline void cta_gram_write(double acc0, double acc1, int p, double (*red)[RG],
@@ -718,6 +755,36 @@ __device__ inline bool take_last_ticket(unsigned* ctr) {
     if (threadIdx.x == 0) ticket = atomicAdd(ctr, 1u);
     __syncthreads();
     return ticket == gridDim.x - 1;
+}
+
+// out[o] = sum_b part[b][o] in double-float arithmetic (each partial split into a float pair,
+// TwoSum accumulation): the FP32 pipe instead of the FP64 one for the last CTA's tail.
+__device__ inline void last_cta_sum_df(const double* part, int nblk, int nout, double* __restrict__ out,
+                                       unsigned* ctr) {
+    __shared__ float redh[NT], redl[NT];
+    __threadfence();
+    const int stripes = NT / nout;
+    const int o = threadIdx.x % nout, st = threadIdx.x / nout;
+    float sh = 0.f, sl = 0.f;
+    if (st < stripes)
+        for (int b = st; b < nblk; b += stripes) {
+            float h, l;
+            split_df(__ldcg(part + (int64_t)b * nout + o), h, l);
+            df_add(sh, sl, h);
+            sl += l;
+        }
+    redh[threadIdx.x] = sh;
+    redl[threadIdx.x] = sl;
+    __syncthreads();
+    if (threadIdx.x < nout) {
+        float th = 0.f, tl = 0.f;
+        for (int k = 0; k < stripes; ++k) {
+            df_add(th, tl, redh[k * nout + threadIdx.x]);
+            tl += redl[k * nout + threadIdx.x];
+        }
+        out[threadIdx.x] = (double)th + (double)tl;
+    }
+    if (threadIdx.x == 0) *ctr = 0u;
 }
 
 // out[o] = sum_b part[b][o] for o < nout (nout <= RP * RP), by the last CTA: NT / nout stripes
@@ -884,6 +951,8 @@ __global__ void __launch_bounds__(NT) k_qr_mixed_rows(double* W, int64_t ldw, in
     __shared__ double hn2[RP];
     __shared__ double Rd[RP * RP];          // KIND 1: R (padded to RP x RP); KIND 2 unused
     __shared__ double rcp[RP];              // KIND 1: 1 / R_cc (0 for a zero column)
+    __shared__ float Rh[RP * RP], Rl[RP * RP];   // KIND 1: R as float pairs
+    __shared__ float rch[RP], rcl[RP];           // KIND 1: 1 / R_cc as float pairs
     __shared__ float Yf[RP * RP];           // KIND 2: Y padded to RP x RP
     __shared__ double red[NT / 32][RG];
     __shared__ double buf[NT / 32][32 * RP];
@@ -994,7 +1063,10 @@ __global__ void __launch_bounds__(NT) k_qr_mixed_rows(double* W, int64_t ldw, in
     if (subst && threadIdx.x < RP) {
         const double d = Rd[threadIdx.x * RP + threadIdx.x];
         rcp[threadIdx.x] = (d != 0.0) ? 1.0 / d : 0.0;
+        if (KIND == 1) split_df(rcp[threadIdx.x], rch[threadIdx.x], rcl[threadIdx.x]);
     }
+    if (KIND == 1)
+        for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) split_df(Rd[e], Rh[e], Rl[e]);
     __syncthreads();
     double* out;
     int64_t ldo;
@@ -1003,6 +1075,7 @@ __global__ void __launch_bounds__(NT) k_qr_mixed_rows(double* W, int64_t ldw, in
     else if (mode == 1 && *extra) { out = W; ldo = ldw; gram = 1; }
     else { out = out_; ldo = ldo_; gram = 0; }
     double acc0 = 0.0, acc1 = 0.0;
+    float gah[2] = {0.f, 0.f}, gal[2] = {0.f, 0.f};
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
     for (int64_t r0 = rb + (threadIdx.x & ~31); r0 < re; r0 += blockDim.x) {
         const int64_t r = r0 + (threadIdx.x & 31);
@@ -1010,7 +1083,35 @@ __global__ void __launch_bounds__(NT) k_qr_mixed_rows(double* W, int64_t ldw, in
         double w[RP], y[RP];
 #pragma unroll
         for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
-        if (subst) {
+        float yh[RP], yl[RP];
+        if (KIND == 1) {
+            // forward substitution y R = w in double-float: R's entries are exact floats
+            // (pairs Rh + Rl for safety), 1 / R_cc as a pair, y kept as pairs
+#pragma unroll
+            for (int c = 0; c < RP; ++c) {
+                float sh, sl;
+                split_df(w[c], sh, sl);
+#pragma unroll
+                for (int a = 0; a < c; ++a) {
+                    const float r1 = Rh[a * RP + c], r2 = Rl[a * RP + c];
+                    const float pr = yh[a] * r1;
+                    float t = fmaf(yh[a], r1, -pr);
+                    t = fmaf(yh[a], r2, t);
+                    t = fmaf(yl[a], r1, t);
+                    df_add(sh, sl, -pr);
+                    sl -= t;
+                }
+                const float q1 = rch[c], q2 = rcl[c];
+                const float pr = sh * q1;
+                float t = fmaf(sh, q1, -pr);
+                t = fmaf(sh, q2, t);
+                t = fmaf(sl, q1, t);
+                const float s2 = pr + t;
+                yl[c] = t - (s2 - pr);
+                yh[c] = s2;
+                y[c] = (double)yh[c] + (double)yl[c];
+            }
+        } else if (subst) {
             // forward substitution y R = w (R upper triangular)
 #pragma unroll
             for (int c = 0; c < RP; ++c) {
@@ -1034,11 +1135,24 @@ __global__ void __launch_bounds__(NT) k_qr_mixed_rows(double* W, int64_t ldw, in
 #pragma unroll
         for (int c = 0; c < RP; ++c)
             if (ok && c < p) out[(int64_t)c * ldo + r] = y[c];
-        if (gram) warp_gram_rows(y, buf[threadIdx.x >> 5], acc0, acc1);
+        if (gram) {
+            if (KIND == 1) {
+#pragma unroll
+                for (int c = 0; c < RP; ++c)
+                    if (!ok || c >= p) { yh[c] = 0.f; yl[c] = 0.f; }
+                warp_gram_rows_df(yh, yl, reinterpret_cast<float*>(buf[threadIdx.x >> 5]), gah, gal);
+            } else {
+                warp_gram_rows(y, buf[threadIdx.x >> 5], acc0, acc1);
+            }
+        }
     }
     if (gram) {
+        if (KIND == 1) {
+            acc0 = (double)gah[0] + (double)gal[0];
+            acc1 = (double)gah[1] + (double)gal[1];
+        }
         cta_gram_write(acc0, acc1, p, red, part);
-        if (take_last_ticket(ctr)) last_cta_sum<double>(part, gridDim.x, pp, G, ctr);
+        if (take_last_ticket(ctr)) last_cta_sum_df(part, gridDim.x, pp, G, ctr);
     }
 }
 
