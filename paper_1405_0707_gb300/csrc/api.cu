@@ -321,12 +321,13 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     }
     const int cols = (j + 1) * p;
     const int f32 = P->opts.precision == EXPM_PREC_MIXED ? 1 : 0;
-    LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, P->nblk, s, f32));
-    LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
+    const int nbc = P->nblk_cgs;
+    LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, nbc, s, f32));
+    LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
     // first pass update: FP64, or double-float on the FP32 pipe in the mixed path (f32 = 2)
-    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, P->nblk, 0, s,
+    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 0, s,
                                               f32 ? 2 : 0));
-    LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, P->nblk, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
+    LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
     // second pass: in the mixed path the update is an O(eps_32) correction, formed in FP32;
     // with the fused QR its last CTA also reduces the Gram partials
     const bool fused = fused_qr(P, p);
@@ -927,6 +928,11 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         const char* bs = std::getenv("EXPM_BLOCKS_PER_SM");   // tuning knob (1..8)
         if (bs && bs[0] >= '1' && bs[0] <= '8' && bs[1] == 0) per_sm = bs[0] - '0';
         P->nblk = consistent_blocks(n, std::max(1, std::min<int>(per_sm * sms, (int)((n + 63) / 64))));
+        // the first CGS pass (projection, update) may use more CTAs than the other row passes
+        int per_sm_cgs = 2 * per_sm;   // measured best for the 256 x 256 workload
+        const char* bc = std::getenv("EXPM_CGS_BLOCKS_PER_SM");   // tuning knob (1..8)
+        if (bc && bc[0] >= '1' && bc[0] <= '8' && bc[1] == 0) per_sm_cgs = bc[0] - '0';
+        P->nblk_cgs = consistent_blocks(n, std::max(1, std::min<int>(per_sm_cgs * sms, (int)((n + 63) / 64))));
     }
     const int m = opts->m;
     const int64_t ld = P->ld;
@@ -941,7 +947,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     ok = ok && dalloc(&P->Bst, (size_t)ld * p_max);
     ok = ok && dalloc(&P->Zst, (size_t)ld * p_max);
     ok = ok && dalloc(&P->H, (size_t)P->ldH * mpm);
-    ok = ok && dalloc(&P->part, (size_t)P->nblk * std::max(mpm * p_max, p_max * p_max));
+    ok = ok && dalloc(&P->part, (size_t)std::max(P->nblk, P->nblk_cgs) * std::max(mpm * p_max, p_max * p_max));
     ok = ok && dalloc(&P->small, kSmallDoubles);
     ok = ok && dalloc(&P->S, (size_t)P->npoles * p_max * p_max * 2);
     ok = ok && dalloc(&P->Wc_slots, (size_t)P->npoles * (mpm + p_max) * p_max);

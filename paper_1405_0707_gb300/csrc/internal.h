@@ -161,6 +161,7 @@ struct expm_plan_s {
     int ldH = 0;
     double* part = nullptr;    // nblk x (m+1) p_max x p_max partial sums
     int nblk = 0;
+    int nblk_cgs = 0;          // CTAs of the first CGS pass (projection, update)
     double* small = nullptr;   // small scratch (see api.cu for the map)
     double* poles = nullptr;   // per-pole elimination workspace (global fallback)
     double* S = nullptr;       // per-pole restart factors, npoles x p x p complex

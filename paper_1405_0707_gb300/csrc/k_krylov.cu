@@ -23,14 +23,29 @@ constexpr int NT = 256;     // threads per CTA for the row passes
 
 __device__ inline int64_t rows_begin(int64_t rpb) { return (int64_t)blockIdx.x * rpb; }
 
+// Loads are issued in batches of LB per thread into registers before any is converted or
+// stored, so LB independent global loads are in flight per thread.
+constexpr int LB = 8;
+
 // Load a TR x cols tile of column-major X (rows r0.., ld) into S[rr * cs + a], zero-filled,
 // converted to the tile's element type.
 template <typename T>
 __device__ inline void load_tile(const double* __restrict__ X, int64_t ld, int cols, int64_t r0,
                                  int tr, T* S, int cs) {
-    for (int e = threadIdx.x; e < TR * cols; e += blockDim.x) {
-        const int rr = e % TR, a = e / TR;
-        S[rr * cs + a] = (rr < tr) ? (T)X[(int64_t)a * ld + r0 + rr] : (T)0;
+    const int total = TR * cols;
+    for (int e0 = threadIdx.x; e0 < total; e0 += LB * blockDim.x) {
+        double v[LB];
+#pragma unroll
+        for (int k = 0; k < LB; ++k) {
+            const int e = e0 + k * blockDim.x;
+            const int rr = e % TR, a = e / TR;
+            v[k] = (e < total && rr < tr) ? X[(int64_t)a * ld + r0 + rr] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < LB; ++k) {
+            const int e = e0 + k * blockDim.x;
+            if (e < total) S[(e % TR) * cs + e / TR] = (T)v[k];
+        }
     }
 }
 
@@ -138,9 +153,20 @@ __device__ inline void gram_write(const double* acc, int p, int nout, double* __
 template <typename T>
 __device__ inline void load_tile_p(const double* __restrict__ X, int64_t ld, int cols, int64_t r0,
                                    int tr, T* S, int cs, int trp) {
-    for (int e = threadIdx.x; e < trp * cols; e += blockDim.x) {
-        const int rr = e % trp, a = e / trp;
-        S[rr * cs + a] = (rr < tr) ? (T)X[(int64_t)a * ld + r0 + rr] : (T)0;
+    const int total = trp * cols;
+    for (int e0 = threadIdx.x; e0 < total; e0 += LB * blockDim.x) {
+        double v[LB];
+#pragma unroll
+        for (int k = 0; k < LB; ++k) {
+            const int e = e0 + k * blockDim.x;
+            const int rr = e % trp, a = e / trp;
+            v[k] = (e < total && rr < tr) ? X[(int64_t)a * ld + r0 + rr] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < LB; ++k) {
+            const int e = e0 + k * blockDim.x;
+            if (e < total) S[(e % trp) * cs + e / trp] = (T)v[k];
+        }
     }
 }
 
@@ -354,12 +380,24 @@ __global__ void __launch_bounds__(NT) k_update_df(const double* __restrict__ V, 
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
     for (int64_t r0 = rb; r0 < re; r0 += TR) {
         const int tr = (int)min((int64_t)TR, re - r0);
-        for (int e = threadIdx.x; e < TR * cols; e += blockDim.x) {
-            const int rr = e % TR, a = e / TR;
-            float vh = 0.f, vl = 0.f;
-            if (rr < tr) split_df(V[(int64_t)a * ldv + r0 + rr], vh, vl);
-            Vh[rr * cs + a] = vh;
-            Vl[rr * cs + a] = vl;
+        for (int e0 = threadIdx.x; e0 < TR * cols; e0 += LB * blockDim.x) {
+            double v[LB];
+#pragma unroll
+            for (int k = 0; k < LB; ++k) {
+                const int e = e0 + k * blockDim.x;
+                const int rr = e % TR, a = e / TR;
+                v[k] = (e < TR * cols && rr < tr) ? V[(int64_t)a * ldv + r0 + rr] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < LB; ++k) {
+                const int e = e0 + k * blockDim.x;
+                if (e < TR * cols) {
+                    float vh, vl;
+                    split_df(v[k], vh, vl);
+                    Vh[(e % TR) * cs + e / TR] = vh;
+                    Vl[(e % TR) * cs + e / TR] = vl;
+                }
+            }
         }
         __syncthreads();
         for (int it = threadIdx.x; it < S * nitems; it += blockDim.x) {

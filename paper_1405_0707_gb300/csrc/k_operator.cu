@@ -73,59 +73,129 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g) {
         }
 }
 
-// One thread per (mode, column): forward elimination and back substitution along x with
-// the precomputed Thomas factors of tridiag(l, c + lambda_mode, u).  The recurrence is
-// sequential in x, so loads are issued TCH steps ahead (chunked register prefetch) to keep
-// the dependent chain from waiting on one global load per step.  in may equal out (each
-// chunk is read before it is written).
-constexpr int TCH = 16;
+// Line solves along x with the precomputed Thomas factors of tridiag(l, c + lambda_mode, u):
+// forward  y_x = (f_x / t - l y_{x-1}) m_x,  backward  z_x = y_x - c'_x z_{x+1} (z_L = 0).
+// Both are first-order linear recurrences, i.e. compositions of affine maps v -> a v + b, so
+// each line is split into TSEG segments handled by TSEG lanes of one warp: every lane composes
+// its segment's map, the segments' entry values are passed lane to lane with shuffles, and
+// every lane then reruns its segment from the right entry value.  Lanes of a warp hold
+// 32 / TSEG consecutive modes of the same segment position, so each warp-wide load touches
+// TSEG fully used 32-byte sectors (the layout is mode-fastest).  in may equal out: every
+// element is read and written by the one lane that owns its segment.
+constexpr int TSEG = 8;
+constexpr int TUNR = 8;    // loads issued ahead inside a segment
 
 template <typename T>
-__device__ inline void thomas_line(const T* f, T* y, int L, int64_t nm, int64_t k, T l_sub,
-                                   const T* __restrict__ thm, const T* __restrict__ thc, T inv_t) {
-    T prev = 0;
-    for (int x0 = 0; x0 < L; x0 += TCH) {
-        T fv[TCH], mv[TCH];
+__device__ inline void tridiag_seg(const T* f, T* y, int L, int64_t nm, int64_t k, T l_sub,
+                                   const T* __restrict__ thm, const T* __restrict__ thc, T inv_t, int seg,
+                                   bool active) {
+    const int seglen = (L + TSEG - 1) / TSEG;
+    const int x0 = min(L, seg * seglen), x1 = min(L, x0 + seglen);
+    const unsigned full = 0xffffffffu;
+    // forward: compose y_out = A y_in + B over the segment
+    T A = 1, B = 0;
+    if (active)
+        for (int xb = x0; xb < x1; xb += TUNR) {
+            T fv[TUNR], mv[TUNR];
 #pragma unroll
-        for (int q = 0; q < TCH; ++q)
-            if (x0 + q < L) {
-                fv[q] = f[(int64_t)(x0 + q) * nm];
-                mv[q] = thm[(int64_t)(x0 + q) * nm + k];
-            }
+            for (int q = 0; q < TUNR; ++q)
+                if (xb + q < x1) {
+                    fv[q] = f[(int64_t)(xb + q) * nm];
+                    mv[q] = thm[(int64_t)(xb + q) * nm + k];
+                }
 #pragma unroll
-        for (int q = 0; q < TCH; ++q)
-            if (x0 + q < L) {
-                prev = (fv[q] * inv_t - l_sub * prev) * mv[q];
-                y[(int64_t)(x0 + q) * nm] = prev;
-            }
+            for (int q = 0; q < TUNR; ++q)
+                if (xb + q < x1) {
+                    const T a = -l_sub * mv[q];
+                    B = a * B + fv[q] * inv_t * mv[q];
+                    A = a * A;
+                }
+        }
+    T yin = 0;
+    for (int sgi = 1; sgi < TSEG; ++sgi) {
+        const T v = __shfl_up_sync(full, A * yin + B, 1);
+        if (seg == sgi) yin = v;
     }
-    T next = prev;
-    for (int x1 = L - 2; x1 >= 0; x1 -= TCH) {
-        T yv[TCH], cv[TCH];
+    if (active) {
+        T prev = yin;
+        for (int xb = x0; xb < x1; xb += TUNR) {
+            T fv[TUNR], mv[TUNR];
 #pragma unroll
-        for (int q = 0; q < TCH; ++q)
-            if (x1 - q >= 0) {
-                yv[q] = y[(int64_t)(x1 - q) * nm];
-                cv[q] = thc[(int64_t)(x1 - q) * nm + k];
-            }
+            for (int q = 0; q < TUNR; ++q)
+                if (xb + q < x1) {
+                    fv[q] = f[(int64_t)(xb + q) * nm];
+                    mv[q] = thm[(int64_t)(xb + q) * nm + k];
+                }
 #pragma unroll
-        for (int q = 0; q < TCH; ++q)
-            if (x1 - q >= 0) {
-                next = yv[q] - cv[q] * next;
-                y[(int64_t)(x1 - q) * nm] = next;
-            }
+            for (int q = 0; q < TUNR; ++q)
+                if (xb + q < x1) {
+                    prev = (fv[q] * inv_t - l_sub * prev) * mv[q];
+                    y[(int64_t)(xb + q) * nm] = prev;
+                }
+        }
     }
+    // backward: z_out(x0) = A z_in(x1) + B over the segment, from x1 - 1 down to x0
+    A = 1;
+    B = 0;
+    if (active)
+        for (int xb = x1 - 1; xb >= x0; xb -= TUNR) {
+            T yv[TUNR], cv[TUNR];
+#pragma unroll
+            for (int q = 0; q < TUNR; ++q)
+                if (xb - q >= x0) {
+                    yv[q] = y[(int64_t)(xb - q) * nm];
+                    cv[q] = (xb - q < L - 1) ? thc[(int64_t)(xb - q) * nm + k] : T(0);
+                }
+#pragma unroll
+            for (int q = 0; q < TUNR; ++q)
+                if (xb - q >= x0) {
+                    B = yv[q] - cv[q] * B;
+                    A = -cv[q] * A;
+                }
+        }
+    T zin = 0;
+    for (int sgi = TSEG - 2; sgi >= 0; --sgi) {
+        const T v = __shfl_down_sync(full, A * zin + B, 1);
+        if (seg == sgi) zin = v;
+    }
+    if (active) {
+        T next = zin;
+        for (int xb = x1 - 1; xb >= x0; xb -= TUNR) {
+            T yv[TUNR], cv[TUNR];
+#pragma unroll
+            for (int q = 0; q < TUNR; ++q)
+                if (xb - q >= x0) {
+                    yv[q] = y[(int64_t)(xb - q) * nm];
+                    cv[q] = (xb - q < L - 1) ? thc[(int64_t)(xb - q) * nm + k] : T(0);
+                }
+#pragma unroll
+            for (int q = 0; q < TUNR; ++q)
+                if (xb - q >= x0) {
+                    next = yv[q] - cv[q] * next;
+                    y[(int64_t)(xb - q) * nm] = next;
+                }
+        }
+    }
+}
+
+// line index of a lane: warp-major groups of 32 / TSEG lines, TSEG segment lanes per line
+__device__ inline int64_t seg_line(int& seg) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    seg = lane % TSEG;
+    return ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * (32 / TSEG) + lane / TSEG;
 }
 
 __global__ void k_tridiag_lines(const double* in, int64_t ld_in, double* out, int64_t ld_out,
                                 int p, int L, int64_t nmodes, double l_sub,
                                 const double* __restrict__ thm, const double* __restrict__ thc,
                                 double inv_t) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= nmodes * p) return;
-    const int64_t k = gid % nmodes;
-    const int c = (int)(gid / nmodes);
-    thomas_line<double>(in + c * ld_in + k, out + c * ld_out + k, L, nmodes, k, l_sub, thm, thc, inv_t);
+    int seg;
+    const int64_t line = seg_line(seg);
+    const bool active = line < nmodes * p;
+    const int64_t k = active ? line % nmodes : 0;
+    const int c = active ? (int)(line / nmodes) : 0;
+    tridiag_seg<double>(in + c * ld_in + k, out + c * ld_out + k, L, nmodes, k, l_sub, thm, thc, inv_t, seg,
+                        active);
 }
 
 // Thomas factors for every mode (one thread per mode): pivots b - l c'_{x-1}, stored as
@@ -284,12 +354,13 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
 __global__ void k_tridiag_lines32(float* y_io, int64_t ld, int p, int L, int64_t nmodes,
                                   float l_sub, const float* __restrict__ thm,
                                   const float* __restrict__ thc, float inv_t) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= nmodes * p) return;
-    const int64_t k = gid % nmodes;
-    const int c = (int)(gid / nmodes);
+    int seg;
+    const int64_t line = seg_line(seg);
+    const bool active = line < nmodes * p;
+    const int64_t k = active ? line % nmodes : 0;
+    const int c = active ? (int)(line / nmodes) : 0;
     float* y = y_io + c * ld + k;
-    thomas_line<float>(y, y, L, nmodes, k, l_sub, thm, thc, inv_t);
+    tridiag_seg<float>(y, y, L, nmodes, k, l_sub, thm, thc, inv_t, seg, active);
 }
 
 // Certify mode: partial sums of ||B - (tA - tau_i I) X_i||_F^2 per pole, X_i = Xr + i Xi stored
@@ -367,10 +438,9 @@ cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
 cudaError_t launch_tridiag_lines(const double* in, int64_t ld_in, double* out, int64_t ld_out,
                                  int p, int L, int64_t nmodes, double l_sub, const double* th_m,
                                  const double* th_c, double inv_t, cudaStream_t s) {
-    const int64_t tot = nmodes * p;
-    const int thr = 128;
-    k_tridiag_lines<<<(unsigned)((tot + thr - 1) / thr), thr, 0, s>>>(in, ld_in, out, ld_out, p, L,
-                                                                     nmodes, l_sub, th_m, th_c, inv_t);
+    const int64_t lines = nmodes * p, per_block = 128 / TSEG;
+    k_tridiag_lines<<<(unsigned)((lines + per_block - 1) / per_block), 128, 0, s>>>(in, ld_in, out, ld_out, p, L,
+                                                                                 nmodes, l_sub, th_m, th_c, inv_t);
     return cudaGetLastError();
 }
 
@@ -421,10 +491,9 @@ cudaError_t launch_gemm32(const GemmArgsMixed& g, cudaStream_t s) {
 cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t nmodes, float l_sub,
                                    const float* th_m, const float* th_c, float inv_t,
                                    cudaStream_t s) {
-    const int64_t tot = nmodes * p;
-    const int thr = 128;
-    k_tridiag_lines32<<<(unsigned)((tot + thr - 1) / thr), thr, 0, s>>>(y, ld, p, L, nmodes, l_sub,
-                                                                       th_m, th_c, inv_t);
+    const int64_t lines = nmodes * p, per_block = 128 / TSEG;
+    k_tridiag_lines32<<<(unsigned)((lines + per_block - 1) / per_block), 128, 0, s>>>(y, ld, p, L, nmodes, l_sub,
+                                                                                   th_m, th_c, inv_t);
     return cudaGetLastError();
 }
 
