@@ -279,8 +279,9 @@ constexpr int BK32 = 32;   // k-depth of one FP32 tile
 // barrier round overlaps its loads with arithmetic.
 template <bool CM, typename TA, typename TC>
 __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
-    __shared__ float As[BK32][BM + 1];
-    __shared__ float Bs[BK32][BN];
+    // rows padded to BM + 4 floats: 16-byte aligned rows for the float4 operand loads
+    __shared__ __align__(16) float As[BK32][BM + 4];
+    __shared__ __align__(16) float Bs[BK32][BN];
     const int b1 = blockIdx.z % g.nb1, b2 = blockIdx.z / g.nb1;
     const TA* A = reinterpret_cast<const TA*>(g.A) + b1 * g.a_b1 + b2 * g.a_b2;
     TC* C = reinterpret_cast<TC*>(g.C) + b1 * g.c_b1 + b2 * g.c_b2;
@@ -325,13 +326,14 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
         }
         __syncthreads();
         if (k0 + BK32 < g.K) fetch(k0 + BK32);
+        // each thread owns 4 consecutive rows m and 4 consecutive columns n: one float4 load
+        // per operand per k (the fastest-varying thread index walks C's contiguous dimension)
+        const int mi = 4 * (CM ? tx : ty), nj = 4 * (CM ? ty : tx);
 #pragma unroll
         for (int kk = 0; kk < BK32; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][(CM ? tx : ty) + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][(CM ? ty : tx) + 16 * j];
+            const float4 av = *reinterpret_cast<const float4*>(&As[kk][mi]);
+            const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][nj]);
+            const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -339,11 +341,12 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
         }
         __syncthreads();
     }
+    const int mi = 4 * (CM ? tx : ty), nj = 4 * (CM ? ty : tx);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int m = m0 + (CM ? tx : ty) + 16 * i, nn = n0 + (CM ? ty : tx) + 16 * j;
+            const int m = m0 + mi + i, nn = n0 + nj + j;
             if (m < g.M && nn < g.N) {
                 TC* dst = C + (int64_t)m * g.c_rs + (int64_t)nn * g.c_cs;
                 *dst = g.accumulate ? (TC)(*dst + (TC)acc[i][j]) : (TC)acc[i][j];
