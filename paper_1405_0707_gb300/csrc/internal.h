@@ -232,7 +232,7 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
                                  unsigned* ctr, int mode, double* R, double* Rinv, const double* Rtot_in,
                                  double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
                                  int* flags, double* out, int64_t ldo, cudaStream_t s);
-constexpr int kRowsMaxP = 8;   // widths handled by the row-per-thread kernels
+constexpr int kRowsMaxP = 16;  // widths handled by the row-per-thread kernels
 // Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
 // third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,

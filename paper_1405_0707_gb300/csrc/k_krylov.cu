@@ -665,676 +665,22 @@ __global__ void __launch_bounds__(NT) k_trsm(double* W, int64_t ldw, int p, int6
     if (gram) gram_write<OPT>(acc, p, nout, part);
 }
 
-// Row-per-thread variant for p <= 8 (the common block sizes): a row of W lives in
-// registers, W R^{-1} and the upper-triangular outer product w^T w are formed there, and
-// the Gram partial of the CTA is one warp-shuffle reduction at the end.  Loads and stores
-// are coalesced per column (consecutive threads, consecutive rows); no tile barriers.
+// The row-per-thread kernels, compiled for up to 8 and up to 16 columns per row (16-column
+// rows get 128-thread CTAs: twice the registers per thread).
+namespace rows8 {
 constexpr int RP = 8;
 constexpr int RG = RP * (RP + 1) / 2;
-
-__device__ inline double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Gram partial of rows held one per lane: each warp stages its 32 rows in shared memory
-// (buf, 32 x RP), then lane l sums upper-triangle entries l and l + 32 over those rows.
-// FP64 work equals the useful products; no reduction tree.  Every lane of the warp must
-// call it (rows past the end are zero).
-__device__ inline void warp_gram_rows(const double* y, double* buf, double& acc0, double& acc1) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < RP; ++c) buf[lane * RP + c] = y[c];
-    __syncwarp();
-    // upper-triangle entry k -> (c1, c2)
-    for (int q = 0; q < 2; ++q) {
-        const int kk = lane + 32 * q;
-        if (kk < RG) {
-            int c1 = 0, rem = kk;
-            while (rem >= RP - c1) { rem -= RP - c1; ++c1; }
-            const int c2 = c1 + rem;
-            double s = 0.0;
-#pragma unroll 8
-            for (int rr = 0; rr < 32; ++rr) s = fma(buf[rr * RP + c1], buf[rr * RP + c2], s);
-            if (q == 0) acc0 += s;
-            else acc1 += s;
-        }
-    }
-    __syncwarp();
-}
-
-// FP32 variant (the mixed path's Gram for the first Cholesky-QR pass, whose factorisation
-// is FP32 anyway): rows staged as floats, products and per-lane sums in FP32.
-__device__ inline void warp_gram_rows32(const double* y, float* buf, float& acc0, float& acc1) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < RP; ++c) buf[lane * RP + c] = (float)y[c];
-    __syncwarp();
-    for (int q = 0; q < 2; ++q) {
-        const int kk = lane + 32 * q;
-        if (kk < RG) {
-            int c1 = 0, rem = kk;
-            while (rem >= RP - c1) { rem -= RP - c1; ++c1; }
-            const int c2 = c1 + rem;
-            float s = 0.f;
-#pragma unroll 8
-            for (int rr = 0; rr < 32; ++rr) s = fmaf(buf[rr * RP + c1], buf[rr * RP + c2], s);
-            if (q == 0) acc0 += s;
-            else acc1 += s;
-        }
-    }
-    __syncwarp();
-}
-
-// Double-float variant (the mixed path's Gram matrix after the first Cholesky-QR pass, which
-// the deviation pass needs to ~1e-14): rows staged as (hi, lo) float pairs; each product
-// hi1 hi2 + (err(hi1 hi2) + hi1 lo2 + lo1 hi2) accumulated with TwoSum into a per-lane pair.
-__device__ inline void warp_gram_rows_df(const float* yh, const float* yl, float* buf, float* ah, float* al) {
-    const int lane = threadIdx.x & 31;
-    float* bh = buf;                 // 32 x RP
-    float* bl = buf + 32 * RP;       // 32 x RP
-#pragma unroll
-    for (int c = 0; c < RP; ++c) {
-        bh[lane * RP + c] = yh[c];
-        bl[lane * RP + c] = yl[c];
-    }
-    __syncwarp();
-    for (int q = 0; q < 2; ++q) {
-        const int kk = lane + 32 * q;
-        if (kk < RG) {
-            int c1 = 0, rem = kk;
-            while (rem >= RP - c1) { rem -= RP - c1; ++c1; }
-            const int c2 = c1 + rem;
-            float sh = ah[q], sl = al[q];
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-                const float h1 = bh[rr * RP + c1], h2 = bh[rr * RP + c2];
-                const float pr = h1 * h2;
-                float t = fmaf(h1, h2, -pr);
-                t = fmaf(h1, bl[rr * RP + c2], t);
-                t = fmaf(bl[rr * RP + c1], h2, t);
-                df_add(sh, sl, pr);
-                sl += t;
-            }
-            ah[q] = sh;
-            al[q] = sl;
-        }
-    }
-    __syncwarp();
-}
-
-// The CTA's Gram partial (p x p layout, upper triangle; lower = 0) from the per-lane
-// accumulators of warp_gram_rows.
-__device__ inline void cta_gram_write(double acc0, double acc1, int p, double (*red)[RG],
-                                      double* __restrict__ part) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    red[wid][lane] = acc0;
-    if (lane + 32 < RG) red[wid][lane + 32] = acc1;
-    __syncthreads();
-    for (int o = threadIdx.x; o < p * p; o += blockDim.x) {
-        const int c1 = o / p, c2 = o % p;
-        double s = 0.0;
-        if (c1 <= c2) {
-            const int k = c1 * RP - c1 * (c1 - 1) / 2 + (c2 - c1);
-            for (int w_ = 0; w_ < NT / 32; ++w_) s += red[w_][k];
-        }
-        part[(int64_t)blockIdx.x * p * p + o] = s;
-    }
-}
-
-// Last-CTA reduction: every CTA has written its partial; the CTA that takes the last ticket
-// (atomic counter) sums the nblk partials of each output in a fixed order (independent of
-// which CTA is last) and resets the counter for the next kernel.  No CTA waits on another.
-__device__ inline bool take_last_ticket(unsigned* ctr) {
-    __shared__ unsigned ticket;
-    __threadfence();                       // this CTA's partial is visible device-wide
-    __syncthreads();
-    if (threadIdx.x == 0) ticket = atomicAdd(ctr, 1u);
-    __syncthreads();
-    return ticket == gridDim.x - 1;
-}
-
-// out[o] = sum_b part[b][o] in double-float arithmetic (each partial split into a float pair,
-// TwoSum accumulation): the FP32 pipe instead of the FP64 one for the last CTA's tail.
-__device__ inline void last_cta_sum_df(const double* part, int nblk, int nout, double* __restrict__ out,
-                                       unsigned* ctr) {
-    __shared__ float redh[NT], redl[NT];
-    __threadfence();
-    const int stripes = NT / nout;
-    const int o = threadIdx.x % nout, st = threadIdx.x / nout;
-    float sh = 0.f, sl = 0.f;
-    if (st < stripes)
-        for (int b = st; b < nblk; b += stripes) {
-            float h, l;
-            split_df(__ldcg(part + (int64_t)b * nout + o), h, l);
-            df_add(sh, sl, h);
-            sl += l;
-        }
-    redh[threadIdx.x] = sh;
-    redl[threadIdx.x] = sl;
-    __syncthreads();
-    if (threadIdx.x < nout) {
-        float th = 0.f, tl = 0.f;
-        for (int k = 0; k < stripes; ++k) {
-            df_add(th, tl, redh[k * nout + threadIdx.x]);
-            tl += redl[k * nout + threadIdx.x];
-        }
-        out[threadIdx.x] = (double)th + (double)tl;
-    }
-    if (threadIdx.x == 0) *ctr = 0u;
-}
-
-// out[o] = sum_b part[b][o] for o < nout (nout <= RP * RP), by the last CTA: NT / nout stripes
-// per output, each stripe's loads issued back to back, stripes added in a fixed order.
-// ACC = float: FP32 sums (for a Gram matrix that only feeds an FP32 factorisation).
-template <typename ACC = double>
-__device__ inline void last_cta_sum(const double* part, int nblk, int nout, double* __restrict__ out,
-                                    unsigned* ctr) {
-    __shared__ double red[NT];
-    __threadfence();
-    const int stripes = NT / nout;         // nout <= 64 -> at least 4 stripes
-    const int o = threadIdx.x % nout, st = threadIdx.x / nout;
-    double acc = 0.0;
-    if (st < stripes) {
-        ACC a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        int b = st;
-        for (; b + 3 * stripes < nblk; b += 4 * stripes) {
-            a0 += (ACC)__ldcg(part + (int64_t)b * nout + o);
-            a1 += (ACC)__ldcg(part + (int64_t)(b + stripes) * nout + o);
-            a2 += (ACC)__ldcg(part + (int64_t)(b + 2 * stripes) * nout + o);
-            a3 += (ACC)__ldcg(part + (int64_t)(b + 3 * stripes) * nout + o);
-        }
-        for (; b < nblk; b += stripes) a0 += (ACC)__ldcg(part + (int64_t)b * nout + o);
-        acc = (double)((a0 + a1) + (a2 + a3));
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < nout) {
-        double s = 0.0;
-        for (int k = 0; k < stripes; ++k) s += red[k * nout + threadIdx.x];
-        out[threadIdx.x] = s;
-    }
-    if (threadIdx.x == 0) *ctr = 0u;
-}
-
-// ---- Mixed-path Cholesky QR for p <= 8 (every CTA factors the reduced Gram matrix G
-// itself, in FP32; CTA 0 alone writes R, Rtot, H and the flags).
-//   KIND 1 (pass 1, mode 0): G (summed in FP64) is scaled by a power of two near its largest
-//     diagonal entry (exact) and factored in FP32; pivots below 1e-6 of the largest (kappa(W)
-//     above ~1e3) redo it with the shift 11 p (p+1) 2^-24 trace and request a third pass
-//     (flags[2]).  R is that factor scaled back (exact), and W <- W R^{-1} is a forward
-//     substitution with R in FP64, so W = W_new R holds to FP64 rounding whatever the FP32
-//     factor's own accuracy.  Gram partials in FP64, reduced by the last CTA into G.
-//   KIND 2 (passes 2 and 3, modes 1 and 2): now G = I + E with E small, so R = I + U is
-//     found from the deviation alone, in FP32: U_jl = (E_jl - sum_{k<j} U_kj U_kl)/(1 + U_jj),
-//     U_jj = x / (1 + sqrt(1 + x)) with x = E_jj - sum_{k<j} U_kj^2; R^{-1} = I + Y with
-//     (I + U) Y = -U.  Each entry has FP32 relative accuracy on a quantity of size |E|, so
-//     absolute errors are ~eps_32 |E|.  Rtot <- Rtot + U Rtot (FP32 correction of the FP64
-//     product) and W <- W + W Y (FP32 correction of the FP64 W).
-// Columns that are exactly zero stay zero (zero rows in R), as in k_chol.
-struct CholF {
-    float G[RP * RP], U[RP * RP], Y[RP * RP];
-    float rd[RP];
-    float umax;       // KIND 2: max |U|
-    int ill, bad;
-};
-
-// pass 1: FP32 Cholesky of G 2^-k (upper triangle) -> U; warp 0
-__device__ inline void chol32_full(CholF& cf, const double* G0, int p, int k, double tr_s) {
-    const int lane = threadIdx.x;
-    const int pp = p * p;
-    if (lane == 0) { cf.ill = 0; cf.bad = 0; }
-    __syncwarp();
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        const double shift = attempt ? 11.0 * p * (p + 1) * 0x1p-24 * tr_s : 0.0;
-        for (int o = lane; o < pp; o += 32) {
-            cf.G[o] = (float)(ldexp(G0[o], -k) + ((o / p == o % p) ? shift : 0.0));
-            cf.U[o] = 0.f;
-        }
-        __syncwarp();
-        float dmax = 0.f;
-        for (int c = 0; c < p; ++c) dmax = fmaxf(dmax, cf.G[c * p + c]);
-        for (int j = 0; j < p; ++j) {
-            if (lane == 0) {
-                float d = cf.G[j * p + j];
-                if (G0[j * p + j] == 0.0) {
-                    cf.U[j * p + j] = 0.f;
-                    cf.rd[j] = 0.f;
-                } else {
-                    if (!(d > 0.f) || !isfinite(d) || (attempt == 0 && d < 1e-6f * dmax)) cf.ill = 1;
-                    if (!(d > 0.f) || !isfinite(d)) d = 1.f;
-                    const float rj = sqrtf(d);
-                    cf.U[j * p + j] = rj;
-                    cf.rd[j] = 1.f / rj;
-                }
-            }
-            __syncwarp();
-            const float inv = cf.rd[j];
-            if (lane > j && lane < p) cf.U[j * p + lane] = cf.G[j * p + lane] * inv;
-            __syncwarp();
-            if (lane > j && lane < p) {
-                const float rb = cf.U[j * p + lane];
-                for (int a = j + 1; a <= lane; ++a) cf.G[a * p + lane] -= cf.U[j * p + a] * rb;
-            }
-            __syncwarp();
-        }
-        if (attempt == 1 || !cf.ill) break;
-        __syncwarp();
-    }
-}
-
-// passes 2/3: deviation Cholesky of G = I + E -> U (R = I + U), Y (R^{-1} = I + Y); warp 0
-__device__ inline void chol32_dev(CholF& cf, const double* G0, int p) {
-    const int lane = threadIdx.x;
-    const int pp = p * p;
-    if (lane == 0) { cf.ill = 0; cf.bad = 0; }
-    for (int o = lane; o < pp; o += 32) {
-        const bool dg = o / p == o % p;
-        cf.G[o] = (float)(G0[o] - (dg ? 1.0 : 0.0));   // E (upper triangle)
-        cf.U[o] = 0.f;
-        cf.Y[o] = 0.f;
-    }
-    __syncwarp();
-    for (int j = 0; j < p; ++j) {
-        if (lane == 0) {
-            if (G0[j * p + j] == 0.0) {
-                cf.U[j * p + j] = -1.f;                  // R_jj = 0: a zero column stays zero
-                cf.rd[j] = 0.f;
-            } else {
-                float x = cf.G[j * p + j];
-                for (int k = 0; k < j; ++k) x -= cf.U[k * p + j] * cf.U[k * p + j];
-                if (!(x > -0.75f) || !isfinite(x)) cf.bad = 1;   // not close to orthonormal
-                if (!(x > -0.75f) || !isfinite(x)) x = 0.f;
-                const float ujj = x / (1.f + sqrtf(1.f + x));
-                cf.U[j * p + j] = ujj;
-                cf.rd[j] = 1.f / (1.f + ujj);
-            }
-        }
-        __syncwarp();
-        if (lane > j && lane < p) {
-            float s = cf.G[j * p + lane];
-            for (int k = 0; k < j; ++k) s -= cf.U[k * p + j] * cf.U[k * p + lane];
-            cf.U[j * p + lane] = s * cf.rd[j];
-        }
-        __syncwarp();
-    }
-    if (lane == 0) {
-        float um = 0.f;
-        for (int o = 0; o < pp; ++o) um = fmaxf(um, fabsf(cf.U[o]));
-        cf.umax = um;
-    }
-    // (I + U) Y = -U, column `lane` by back substitution
-    if (lane < p) {
-        const int c = lane;
-        for (int r = c; r >= 0; --r) {
-            float s = -cf.U[r * p + c];
-            for (int k = r + 1; k <= c; ++k) s -= cf.U[r * p + k] * cf.Y[k * p + c];
-            cf.Y[r * p + c] = (r == c && cf.rd[r] == 0.f) ? -1.f : s * cf.rd[r];
-        }
-    }
-    __syncwarp();
-}
-
-template <int KIND>
-__global__ void __launch_bounds__(NT) k_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int64_t rpb,
-                                                      double* G, double* __restrict__ part, unsigned* ctr,
-                                                      int mode, double* R, double* Rinv, const double* Rtot_in,
-                                                      double* Rtot_out, double* H, int ldH, int hrow, int hcol,
-                                                      double* normsq_out, int* flags, double* out_, int64_t ldo_) {
-    int* extra = flags + 2;
-    if (mode == 2 && *extra == 0) return;
-    __shared__ CholF cf;
-    __shared__ double G0[RP * RP];
-    __shared__ double hn2[RP];
-    __shared__ double Rd[RP * RP];          // KIND 1: R (padded to RP x RP); KIND 2 unused
-    __shared__ double rcp[RP];              // KIND 1: 1 / R_cc (0 for a zero column)
-    __shared__ float Rh[RP * RP], Rl[RP * RP];   // KIND 1: R as float pairs
-    __shared__ float rch[RP], rcl[RP];           // KIND 1: 1 / R_cc as float pairs
-    __shared__ float Yf[RP * RP];           // KIND 2: Y padded to RP x RP
-    __shared__ double red[NT / 32][RG];
-    __shared__ double buf[NT / 32][32 * RP];
-    const int pp = p * p;
-    for (int o = threadIdx.x; o < pp; o += blockDim.x) G0[o] = G[o];
-    const bool last = (mode == 1 && *extra == 0) || mode == 2;
-    const bool lead = blockIdx.x == 0;
-    if (H && last && lead) {
-        const int stripes = NT / p;
-        const int c = threadIdx.x % p, st = threadIdx.x / p;
-        double v2 = 0.0;
-        if (st < stripes)
-            for (int a = st; a < hrow; a += stripes) {
-                const double v = H[(int64_t)(hcol + c) * ldH + a];
-                v2 += v * v;
-            }
-        buf[0][threadIdx.x] = v2;
-    }
-    __syncthreads();
-    if (H && last && lead && threadIdx.x < p) {
-        const int stripes = NT / p;
-        double s2 = 0.0;
-        for (int k = 0; k < stripes; ++k) s2 += buf[0][k * p + threadIdx.x];
-        hn2[threadIdx.x] = s2;
-    }
-    __syncthreads();
-    int kexp = 0;                           // KIND 1: G is factored as G 2^-kexp (kexp even)
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        double tr = 0.0, dmax = 0.0;
-        if (KIND == 1) {
-            for (int c = 0; c < p; ++c) {
-                tr += G0[c * p + c];
-                dmax = fmax(dmax, G0[c * p + c]);
-            }
-            if (dmax > 0.0 && isfinite(dmax)) {
-                frexp(dmax, &kexp);
-                kexp &= ~1;
-            }
-            chol32_full(cf, G0, p, kexp, ldexp(tr, -kexp));
-        } else {
-            chol32_dev(cf, G0, p);
-        }
-        if (lead) {
-            if (KIND == 1 && normsq_out && lane == 0) *normsq_out = tr;
-            if (KIND == 1 && lane == 0) *extra = cf.ill;
-            if (lane < p) {
-                const int c = lane;
-                for (int r = 0; r < p; ++r) {
-                    const int o = r * p + c;
-                    double rt;
-                    if (KIND == 1) {
-                        rt = (r <= c) ? ldexp((double)cf.U[o], kexp / 2) : 0.0;
-                        R[o] = rt;
-                    } else {
-                        // Rtot_out = Rtot_in + U Rtot_in (FP32 correction of the FP64 product)
-                        float corr = 0.f;
-                        for (int k = r; k <= c; ++k) corr = fmaf(cf.U[r * p + k], (float)Rtot_in[k * p + c], corr);
-                        rt = (r <= c) ? Rtot_in[o] + (double)corr : 0.0;
-                        R[o] = (r <= c) ? (double)cf.U[o] + (r == c ? 1.0 : 0.0) : 0.0;
-                        Rinv[o] = (r <= c) ? (double)cf.Y[o] + (r == c ? 1.0 : 0.0) : 0.0;
-                    }
-                    Rtot_out[o] = rt;
-                    if (!isfinite(rt)) cf.bad = 1;
-                    if (H && last) H[(int64_t)(hcol + c) * ldH + hrow + r] = rt;
-                }
-            }
-            __syncwarp();
-            if (H && last && lane < p) {
-                const int c = lane;
-                double n0 = hn2[c], dg = 0.0;
-                for (int a = 0; a <= c; ++a) {
-                    const double v = Rtot_out[a * p + c];
-                    n0 += v * v;
-                    if (a == c) dg = v;
-                }
-                if (dg <= 1e-14 * sqrt(n0)) atomicOr(&flags[1], 1);
-            }
-            __syncwarp();
-            if (lane == 0 && cf.bad) atomicOr(&flags[0], 1);
-        }
-    }
-    __syncthreads();
-    if (KIND == 1) {
-        // kexp as computed by warp 0 (every thread recomputes it from the same G0)
-        double dmax = 0.0;
-        for (int c = 0; c < p; ++c) dmax = fmax(dmax, G0[c * p + c]);
-        kexp = 0;
-        if (dmax > 0.0 && isfinite(dmax)) {
-            frexp(dmax, &kexp);
-            kexp &= ~1;
-        }
-    }
-    // KIND 2 with max|U| above 1e-4 (a pass after the shifted one): the FP32 inverse I + Y
-    // would leave an eps_32 |U| mismatch with the recorded R, so the solve is a forward
-    // substitution with R = I + U in FP64, as in pass 1
-    const bool subst = KIND == 1 || cf.umax > 1e-4f;
-    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
-        const int a = e / RP, c = e % RP;
-        const bool in = a < p && c < p && a <= c;
-        if (KIND == 1) Rd[e] = in ? ldexp((double)cf.U[a * p + c], kexp / 2) : 0.0;
-        else {
-            Yf[e] = in ? cf.Y[a * p + c] : 0.f;
-            Rd[e] = in ? (double)cf.U[a * p + c] + (a == c ? 1.0 : 0.0) : 0.0;
-        }
-    }
-    __syncthreads();
-    if (subst && threadIdx.x < RP) {
-        const double d = Rd[threadIdx.x * RP + threadIdx.x];
-        rcp[threadIdx.x] = (d != 0.0) ? 1.0 / d : 0.0;
-        if (KIND == 1) split_df(rcp[threadIdx.x], rch[threadIdx.x], rcl[threadIdx.x]);
-    }
-    if (KIND == 1)
-        for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) split_df(Rd[e], Rh[e], Rl[e]);
-    __syncthreads();
-    double* out;
-    int64_t ldo;
-    int gram;
-    if (mode == 0) { out = W; ldo = ldw; gram = 1; }
-    else if (mode == 1 && *extra) { out = W; ldo = ldw; gram = 1; }
-    else { out = out_; ldo = ldo_; gram = 0; }
-    double acc0 = 0.0, acc1 = 0.0;
-    float gah[2] = {0.f, 0.f}, gal[2] = {0.f, 0.f};
-    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
-    for (int64_t r0 = rb + (threadIdx.x & ~31); r0 < re; r0 += blockDim.x) {
-        const int64_t r = r0 + (threadIdx.x & 31);
-        const bool ok = r < re;
-        double w[RP], y[RP];
-#pragma unroll
-        for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
-        float yh[RP], yl[RP];
-        if (KIND == 1) {
-            // forward substitution y R = w in double-float: R's entries are exact floats
-            // (pairs Rh + Rl for safety), 1 / R_cc as a pair, y kept as pairs
-#pragma unroll
-            for (int c = 0; c < RP; ++c) {
-                float sh, sl;
-                split_df(w[c], sh, sl);
-#pragma unroll
-                for (int a = 0; a < c; ++a) {
-                    const float r1 = Rh[a * RP + c], r2 = Rl[a * RP + c];
-                    const float pr = yh[a] * r1;
-                    float t = fmaf(yh[a], r1, -pr);
-                    t = fmaf(yh[a], r2, t);
-                    t = fmaf(yl[a], r1, t);
-                    df_add(sh, sl, -pr);
-                    sl -= t;
-                }
-                const float q1 = rch[c], q2 = rcl[c];
-                const float pr = sh * q1;
-                float t = fmaf(sh, q1, -pr);
-                t = fmaf(sh, q2, t);
-                t = fmaf(sl, q1, t);
-                const float s2 = pr + t;
-                yl[c] = t - (s2 - pr);
-                yh[c] = s2;
-                y[c] = (double)yh[c] + (double)yl[c];
-            }
-        } else if (subst) {
-            // forward substitution y R = w (R upper triangular)
-#pragma unroll
-            for (int c = 0; c < RP; ++c) {
-                double s = w[c];
-#pragma unroll
-                for (int a = 0; a < c; ++a) s = fma(-y[a], Rd[a * RP + c], s);
-                y[c] = s * rcp[c];
-            }
-        } else {
-            float wf[RP];
-#pragma unroll
-            for (int c = 0; c < RP; ++c) wf[c] = (float)w[c];
-#pragma unroll
-            for (int c = 0; c < RP; ++c) {
-                float s = 0.f;
-#pragma unroll
-                for (int a = 0; a <= c; ++a) s = fmaf(wf[a], Yf[a * RP + c], s);
-                y[c] = w[c] + (double)s;
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < RP; ++c)
-            if (ok && c < p) out[(int64_t)c * ldo + r] = y[c];
-        if (gram) {
-            if (KIND == 1) {
-#pragma unroll
-                for (int c = 0; c < RP; ++c)
-                    if (!ok || c >= p) { yh[c] = 0.f; yl[c] = 0.f; }
-                warp_gram_rows_df(yh, yl, reinterpret_cast<float*>(buf[threadIdx.x >> 5]), gah, gal);
-            } else {
-                warp_gram_rows(y, buf[threadIdx.x >> 5], acc0, acc1);
-            }
-        }
-    }
-    if (gram) {
-        if (KIND == 1) {
-            acc0 = (double)gah[0] + (double)gal[0];
-            acc1 = (double)gah[1] + (double)gal[1];
-        }
-        cta_gram_write(acc0, acc1, p, red, part);
-        if (take_last_ticket(ctr)) last_cta_sum_df(part, gridDim.x, pp, G, ctr);
-    }
-}
-
-__global__ void __launch_bounds__(NT) k_trsm_rows(double* W, int64_t ldw, int p,
-                                                  int64_t n, int64_t rpb, const double* __restrict__ Rinv,
-                                                  double* out_, int64_t ldo_,
-                                                  double* __restrict__ part, int gram_,
-                                                  const int* extra, int tmode) {
-    const TrsmPass ps = trsm_pass(W, ldw, out_, ldo_, gram_, extra, tmode);
-    if (ps.skip) return;
-    double* out = ps.dest;
-    const int64_t ldo = ps.ldd;
-    const int gram = ps.gram;
-    __shared__ double Ri[RP * RP];
-    __shared__ double red[NT / 32][RG];
-    __shared__ double buf[NT / 32][32 * RP];
-    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
-        const int a = e / RP, c = e % RP;
-        Ri[e] = (a < p && c < p) ? Rinv[a * p + c] : 0.0;
-    }
-    __syncthreads();
-    double acc0 = 0.0, acc1 = 0.0;
-    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
-    // whole warps step through the rows together (rows past the end contribute zeros)
-    for (int64_t r0 = rb + (threadIdx.x & ~31); r0 < re; r0 += blockDim.x) {
-        const int64_t r = r0 + (threadIdx.x & 31);
-        const bool ok = r < re;
-        double w[RP], y[RP];
-#pragma unroll
-        for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
-#pragma unroll
-        for (int c = 0; c < RP; ++c) {
-            double s = 0.0;
-#pragma unroll
-            for (int a = 0; a <= c; ++a) s = fma(w[a], Ri[a * RP + c], s);
-            y[c] = s;
-            if (ok && c < p) out[(int64_t)c * ldo + r] = s;
-        }
-        if (gram) warp_gram_rows(y, buf[threadIdx.x >> 5], acc0, acc1);
-    }
-    if (gram) cta_gram_write(acc0, acc1, p, red, part);
-}
-
-// Row-per-thread, p <= 8: W <- W - V h and the upper-triangular Gram partial of the result.
-// h (cols x p) is broadcast from shared memory.  UPD32 = false: the update in FP64 (the
-// Arnoldi relation stays exact to FP64 rounding).  UPD32 = true (mixed path, second CGS
-// pass only): h is then the O(eps_32) remainder left by the FP32 projection of the first
-// pass, so the correction V h is formed in FP32 and subtracted from the FP64 W; its error,
-// eps_32 |V h| ~ eps_32^2 |W|, stays far below the accuracy the mixed path delivers.
-template <bool UPD32>
-__global__ void __launch_bounds__(NT) k_update_gram_rows(const double* __restrict__ V, int64_t ldv, int cols,
-                                                         double* __restrict__ W, int64_t ldw, int p,
-                                                         int64_t n, int64_t rpb,
-                                                         const double* __restrict__ h,
-                                                         double* __restrict__ part, double* G,
-                                                         unsigned* ctr) {
-    extern __shared__ double hs[];           // cols x RP (zero-padded columns), FP64 or FP32
-    float* hsf = reinterpret_cast<float*>(hs);
-    __shared__ double red[NT / 32][RG];
-    for (int e = threadIdx.x; e < cols * RP; e += blockDim.x) {
-        const int a = e / RP, c = e % RP;
-        const double v = (c < p) ? h[a * p + c] : 0.0;
-        if (UPD32) hsf[e] = (float)v;
-        else hs[e] = v;
-    }
-    __syncthreads();
-    __shared__ double buf[NT / 32][32 * RP];
-    double acc0 = 0.0, acc1 = 0.0;
-    float facc0 = 0.f, facc1 = 0.f;
-    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
-    for (int64_t r0 = rb + (threadIdx.x & ~31); r0 < re; r0 += blockDim.x) {
-        const int64_t r = r0 + (threadIdx.x & 31);
-        const bool ok = r < re;
-        double w[RP];
-#pragma unroll
-        for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
-        if (ok && UPD32) {
-            float corr[RP];
-#pragma unroll
-            for (int c = 0; c < RP; ++c) corr[c] = 0.f;
-#pragma unroll 8
-            for (int a = 0; a < cols; ++a) {
-                const float v = (float)V[(int64_t)a * ldv + r];
-#pragma unroll
-                for (int c = 0; c < RP; ++c) corr[c] = fmaf(v, hsf[a * RP + c], corr[c]);
-            }
-#pragma unroll
-            for (int c = 0; c < RP; ++c) w[c] -= (double)corr[c];
-        } else if (ok) {
-#pragma unroll 8
-            for (int a = 0; a < cols; ++a) {
-                const double v = V[(int64_t)a * ldv + r];
-#pragma unroll
-                for (int c = 0; c < RP; ++c) w[c] = fma(-v, hs[a * RP + c], w[c]);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < RP; ++c)
-            if (ok && c < p) W[(int64_t)c * ldw + r] = w[c];
-        if (UPD32) warp_gram_rows32(w, reinterpret_cast<float*>(buf[threadIdx.x >> 5]), facc0, facc1);
-        else warp_gram_rows(w, buf[threadIdx.x >> 5], acc0, acc1);
-    }
-    if (UPD32) {
-        acc0 = facc0;
-        acc1 = facc1;
-    }
-    cta_gram_write(acc0, acc1, p, red, part);
-    if (G && take_last_ticket(ctr)) {
-        if (UPD32) last_cta_sum<float>(part, gridDim.x, p * p, G, ctr);
-        else last_cta_sum<double>(part, gridDim.x, p * p, G, ctr);
-    }
-}
-
-// Row-per-thread, p <= 8: Z[r, :] += V[r, 0:cols] Wc; restart copy V[r, 0:p] <- V[r, cols-p:cols].
-__global__ void __launch_bounds__(NT) k_update_z_rows(double* __restrict__ V, int64_t ldv, int cols, int p,
-                                                      int64_t n, int64_t rpb,
-                                                      const double* __restrict__ Wc,
-                                                      double* __restrict__ Z, int64_t ldz,
-                                                      int restart_copy) {
-    extern __shared__ double ws[];           // cols x RP
-    for (int e = threadIdx.x; e < cols * RP; e += blockDim.x) {
-        const int a = e / RP, c = e % RP;
-        ws[e] = (c < p) ? Wc[a * p + c] : 0.0;
-    }
-    __syncthreads();
-    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
-    for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
-        double z[RP];
-#pragma unroll
-        for (int c = 0; c < RP; ++c) z[c] = 0.0;
-        for (int a = 0; a < cols; ++a) {
-            const double v = V[(int64_t)a * ldv + r];
-#pragma unroll
-            for (int c = 0; c < RP; ++c) z[c] = fma(v, ws[a * RP + c], z[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < RP; ++c)
-            if (c < p) {
-                Z[(int64_t)c * ldz + r] += z[c];
-                // restart copy: this thread's row only, after all its reads of the row
-                if (restart_copy) V[(int64_t)c * ldv + r] = V[(int64_t)(cols - p + c) * ldv + r];
-            }
-    }
-}
+constexpr int NQ = (RG + 31) / 32;
+constexpr int NTR = 256;
+#include "rows_impl.cuh"
+}  // namespace rows8
+namespace rows16 {
+constexpr int RP = 16;
+constexpr int RG = RP * (RP + 1) / 2;
+constexpr int NQ = (RG + 31) / 32;
+constexpr int NTR = 128;
+#include "rows_impl.cuh"
+}  // namespace rows16
 
 // Z[r, c] += sum_{a < cols} V[r, a] Wc[a][c]; restart: V[:, 0:p] <- V[:, cols-p:cols].
 __global__ void __launch_bounds__(NT) k_update_z(double* __restrict__ V, int64_t ldv, int cols,
@@ -1462,15 +808,19 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
                                  unsigned* ctr, int mode, double* R, double* Rinv, const double* Rtot_in,
                                  double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
                                  int* flags, double* out, int64_t ldo, cudaStream_t s) {
-    if (p > RP) return cudaErrorInvalidValue;
+    if (p > rows16::RP) return cudaErrorInvalidValue;
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
-    if (mode == 0)
-        k_qr_mixed_rows<1><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H,
-                                            ldH, hrow, hcol, normsq_out, flags, out, ldo);
-    else
-        k_qr_mixed_rows<2><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H,
-                                            ldH, hrow, hcol, normsq_out, flags, out, ldo);
+#define EXPM_QR_ROWS(NS)                                                                                          \
+    if (mode == 0)                                                                                              \
+        NS::k_qr_mixed_rows<1><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
+                                                     Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo); \
+    else                                                                                                        \
+        NS::k_qr_mixed_rows<2><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
+                                                     Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo);
+    if (p <= rows8::RP) { EXPM_QR_ROWS(rows8) }
+    else { EXPM_QR_ROWS(rows16) }
+#undef EXPM_QR_ROWS
     return cudaGetLastError();
 }
 
@@ -1483,13 +833,18 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
     if (f32 || upd32) shm += sizeof(float) * (TR * (cols | 1) + TR * p);
     if (upd32) shm += sizeof(float) * (size_t)cols * p;
     const int nout = gram ? p * p : cols * p;
-    if (gram && p <= RP) {
-        if (upd32)
-            k_update_gram_rows<true><<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, W, ldw, p, n,
-                                                                                       rpb, h, part, G, ctr);
-        else
-            k_update_gram_rows<false><<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, W, ldw, p, n,
-                                                                                        rpb, h, part, G, ctr);
+    if (gram && p <= rows16::RP) {
+#define EXPM_UPD_ROWS(NS)                                                                                         \
+    {                                                                                                           \
+        const size_t shr = sizeof(double) * (size_t)cols * NS::RP;                                             \
+        if (upd32)                                                                                              \
+            NS::k_update_gram_rows<true><<<g, NS::NTR, shr, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, G, ctr); \
+        else                                                                                                    \
+            NS::k_update_gram_rows<false><<<g, NS::NTR, shr, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, G, ctr); \
+    }
+        if (p <= rows8::RP) EXPM_UPD_ROWS(rows8)
+        else EXPM_UPD_ROWS(rows16)
+#undef EXPM_UPD_ROWS
         return cudaGetLastError();
     }
     if (upd32 && gram)
@@ -1518,8 +873,12 @@ cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* 
                         const int* extra, int tmode, cudaStream_t s) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
-    if (p <= RP) {
-        k_trsm_rows<<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram, extra, tmode);
+    if (p <= rows8::RP) {
+        rows8::k_trsm_rows<<<g, rows8::NTR, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram, extra, tmode);
+        return cudaGetLastError();
+    }
+    if (p <= rows16::RP) {
+        rows16::k_trsm_rows<<<g, rows16::NTR, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram, extra, tmode);
         return cudaGetLastError();
     }
     EXPM_OPT_DISPATCH(p * p, (k_trsm<O><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram,
@@ -1532,9 +891,14 @@ cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
                             cudaStream_t s, int nblk) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
-    if (p <= RP) {
-        k_update_z_rows<<<g, NT, sizeof(double) * (size_t)cols * RP, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz,
-                                                                         restart_copy);
+    if (p <= rows8::RP) {
+        rows8::k_update_z_rows<<<g, rows8::NTR, sizeof(double) * (size_t)cols * rows8::RP, s>>>(
+            V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy);
+        return cudaGetLastError();
+    }
+    if (p <= rows16::RP) {
+        rows16::k_update_z_rows<<<g, rows16::NTR, sizeof(double) * (size_t)cols * rows16::RP, s>>>(
+            V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy);
         return cudaGetLastError();
     }
     const size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1));
@@ -1602,9 +966,12 @@ cudaError_t krylov_set_smem_limits() {
     EXPM_SET((k_update<16, false, true>)); EXPM_SET((k_update<64, false, true>));
     EXPM_SET(k_update_df<1>); EXPM_SET(k_update_df<4>); EXPM_SET(k_update_df<16>); EXPM_SET(k_update_df<64>);
     EXPM_SET(k_update_z);
-    EXPM_SET(k_update_gram_rows<false>);
-    EXPM_SET(k_update_gram_rows<true>);
-    EXPM_SET(k_update_z_rows);
+    EXPM_SET(rows8::k_update_gram_rows<false>);
+    EXPM_SET(rows8::k_update_gram_rows<true>);
+    EXPM_SET(rows8::k_update_z_rows);
+    EXPM_SET(rows16::k_update_gram_rows<false>);
+    EXPM_SET(rows16::k_update_gram_rows<true>);
+    EXPM_SET(rows16::k_update_z_rows);
 #undef EXPM_SET
     return e;
 }
