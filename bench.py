@@ -215,17 +215,20 @@ def make_plan(w, precision, stream=None, **kw):
     return Plan(w["sides"], w["diff"], w["vel"], **args)
 
 
+def source_digests(paths):
+    return {p: hashlib.sha256(open(os.path.join(ROOT, p), "rb").read()).hexdigest() for p in paths}
+
+
 def traffic_record(kernel):
-    """ncu DRAM bytes per launch recorded in profiles/ncu_traffic.json, or None when the
-    kernel's source changed since the capture (sha256 of the source file)."""
+    """ncu DRAM bytes per launch recorded in profiles/ncu_traffic.json, or None when any of
+    the kernel's source files changed since the capture (sha256 of each)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path))[kernel]
-        src = os.path.join(ROOT, rec["source"])
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+        if source_digests(rec["sources"]) != rec["sources"]:
             return None
         return rec["bytes_per_launch_full"]
-    except (OSError, KeyError, ValueError):
+    except (OSError, KeyError, ValueError, TypeError):
         return None
 
 

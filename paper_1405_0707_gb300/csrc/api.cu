@@ -190,6 +190,11 @@ FftArgs fft_args(const expm_plan* P) {
     a.tw2 = z.tw2;
     a.thi = z.thi;
     a.tlo = z.tlo;
+    a.tw1f = z.tw1f;
+    a.tw2f = z.tw2f;
+    a.thif = z.thif;
+    a.tlof = z.tlof;
+    a.df = z.use_df ? 1 : 0;
     a.lam = z.lam;
     a.mu1 = z.mu1;
     a.mu2 = z.mu2;
@@ -613,6 +618,10 @@ void free_plan(expm_plan* P) {
     cudaFree(P->tz.tw2);
     cudaFree(P->tz.thi);
     cudaFree(P->tz.tlo);
+    cudaFree(P->tz.tw1f);
+    cudaFree(P->tz.tw2f);
+    cudaFree(P->tz.thif);
+    cudaFree(P->tz.tlof);
     cudaFree(P->tz.lam);
     cudaFree(P->tz.Ua);
     cudaFree(P->tz.Ub);
@@ -796,7 +805,26 @@ expm_status toeplitz_setup(expm_plan* P, const expm_op_desc* op, bool want_inver
         launch_fft_cols(a, FFT_COL_FWD_CPLX, 1, s) != cudaSuccess || launch_fft_rows(a, FFT_ROW_FWD, 1, s) != cudaSuccess ||
         launch_real_part(z.Ua, z.lam, N, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
         return EXPM_CUDA_ERROR;
-    if (want_inverse) return toeplitz_generator(P);
+    if (want_inverse) {
+        const expm_status st = toeplitz_generator(P);
+        if (st != EXPM_OK) return st;
+    }
+    // Mixed precision: later products and inverses run their transforms in double-float
+    // (FP32 pairs, ~2^-48 per operation); the spectra and the generator above stay FP64.
+    if (P->opts.precision == EXPM_PREC_MIXED) {
+        const int64_t N = z.f.N;
+        if (!(dalloc(&z.tw1f, 4 * (size_t)z.f.N1) && dalloc(&z.tw2f, 4 * (size_t)z.f.N2) &&
+              dalloc(&z.thif, 4 * (size_t)(N / 64)) && dalloc(&z.tlof, 4 * 64))) {
+            cudaGetLastError();
+            return EXPM_NO_MEMORY;
+        }
+        if (launch_fft_tables_df(z.tw1, z.tw1f, z.f.N1, s) != cudaSuccess ||
+            launch_fft_tables_df(z.tw2, z.tw2f, z.f.N2, s) != cudaSuccess ||
+            launch_fft_tables_df(z.thi, z.thif, N / 64, s) != cudaSuccess ||
+            launch_fft_tables_df(z.tlo, z.tlof, 64, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            return EXPM_CUDA_ERROR;
+        z.use_df = true;
+    }
     return EXPM_OK;
 }
 

@@ -86,6 +86,13 @@ struct FftArgs {
     const double* tw2 = nullptr;   // W_{N2}^k
     const double* thi = nullptr;   // W_N^{64 h}
     const double* tlo = nullptr;   // W_N^l, l < 64
+    // the same tables as float pairs (re_hi, re_lo, im_hi, im_lo); with df set the passes
+    // compute in double-float arithmetic (data stays FP64 in memory)
+    const float* tw1f = nullptr;
+    const float* tw2f = nullptr;
+    const float* thif = nullptr;
+    const float* tlof = nullptr;
+    int df = 0;
 };
 
 // Symmetric Toeplitz operator state (device buffers owned by the plan).
@@ -97,6 +104,11 @@ struct ToeplitzOp {
     double* tw2 = nullptr;
     double* thi = nullptr;
     double* tlo = nullptr;
+    float* tw1f = nullptr;      // float-pair copies of the tables (mixed precision)
+    float* tw2f = nullptr;
+    float* thif = nullptr;
+    float* tlof = nullptr;
+    bool use_df = false;        // products and inverses in double-float (set after setup)
     double* lam = nullptr;      // N real: spectrum of the circulant embedding (transposed order)
     double* Ua = nullptr;       // nseq_max = max(2, ceil(p_max/2)) sequences of N complex
     double* Ub = nullptr;       // (Gohberg-Semencul) 2 nseq_max sequences
@@ -268,6 +280,7 @@ bool fft_geometry_ok(const FftPlan& f);
 cudaError_t fft_set_smem_limits();
 cudaError_t launch_fft_tables(const FftPlan& f, double* tw1, double* tw2, double* thi, double* tlo,
                               cudaStream_t s);
+cudaError_t launch_fft_tables_df(const double* src, float* dst, int64_t count, cudaStream_t s);
 cudaError_t launch_fft_cols(const FftArgs& a, int mode, int nseq, cudaStream_t s);
 cudaError_t launch_fft_rows(const FftArgs& a, int mode, int nseq, cudaStream_t s);
 cudaError_t launch_embed_toeplitz(const double* a, int64_t bw, int64_t N, double* U, cudaStream_t s);

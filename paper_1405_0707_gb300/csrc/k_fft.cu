@@ -38,6 +38,7 @@
 // W_N^e = T_hi[e >> 6] T_lo[e & 63].
 #include <algorithm>
 
+#include "df.cuh"
 #include "internal.h"
 
 namespace expm {
@@ -60,15 +61,97 @@ __device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
 
 constexpr double kRsqrt2 = 0.70710678118654752440;
 
-__device__ __forceinline__ void dft2(c2& a, c2& b) {
-    const c2 t = a;
+// ---- double-float complex numbers (each component a float pair h + l, ~2^-48 relative):
+// the mixed path runs the butterflies on the FP32 pipe, 72x the FP64 rate on this GPU.
+struct df {
+    float h, l;
+};
+struct cdf {
+    df x, y;
+};
+__device__ __forceinline__ df df_of(double v) {
+    df r;
+    split_df(v, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ double df_val(df a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ df dadd(df a, df b) {
+    const float s = a.h + b.h, bp = s - a.h;
+    float e = (a.h - (s - bp)) + (b.h - bp);
+    e += a.l + b.l;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+__device__ __forceinline__ df dneg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df dsub(df a, df b) { return dadd(a, dneg(b)); }
+__device__ __forceinline__ df dmul(df a, df b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float h = p + e;
+    return {h, e - (h - p)};
+}
+__device__ __forceinline__ cdf cadd(cdf a, cdf b) { return {dadd(a.x, b.x), dadd(a.y, b.y)}; }
+__device__ __forceinline__ cdf csub(cdf a, cdf b) { return {dsub(a.x, b.x), dsub(a.y, b.y)}; }
+__device__ __forceinline__ cdf cmul(cdf a, cdf b) {
+    return {dsub(dmul(a.x, b.x), dmul(a.y, b.y)), dadd(dmul(a.x, b.y), dmul(a.y, b.x))};
+}
+__device__ __forceinline__ cdf cmulc(cdf a, cdf b) {
+    return {dadd(dmul(a.x, b.x), dmul(a.y, b.y)), dsub(dmul(a.y, b.x), dmul(a.x, b.y))};
+}
+__device__ __forceinline__ cdf cscale(cdf a, double s) {
+    const df d = df_of(s);
+    return {dmul(a.x, d), dmul(a.y, d)};
+}
+template <bool INV>
+__device__ __forceinline__ cdf mul_mi(cdf a) { return INV ? cdf{dneg(a.y), a.x} : cdf{a.y, dneg(a.x)}; }
+
+// element access for both complex types
+template <class T> __device__ __forceinline__ T czero();
+template <> __device__ __forceinline__ c2 czero<c2>() { return {0.0, 0.0}; }
+template <> __device__ __forceinline__ cdf czero<cdf>() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+template <class T> __device__ __forceinline__ T cmake(double re, double im);
+template <> __device__ __forceinline__ c2 cmake<c2>(double re, double im) { return {re, im}; }
+template <> __device__ __forceinline__ cdf cmake<cdf>(double re, double im) { return {df_of(re), df_of(im)}; }
+__device__ __forceinline__ double cre(c2 a) { return a.x; }
+__device__ __forceinline__ double cim(c2 a) { return a.y; }
+__device__ __forceinline__ double cre(cdf a) { return df_val(a.x); }
+__device__ __forceinline__ double cim(cdf a) { return df_val(a.y); }
+
+// W8^1 o, W8^3 o (W8 = e^{-2 pi i / 8}, conjugated for the inverse)
+template <bool INV>
+__device__ __forceinline__ c2 w8_1(c2 o) {
+    return INV ? c2{(o.x - o.y) * kRsqrt2, (o.x + o.y) * kRsqrt2} : c2{(o.x + o.y) * kRsqrt2, (o.y - o.x) * kRsqrt2};
+}
+template <bool INV>
+__device__ __forceinline__ c2 w8_3(c2 o) {
+    return INV ? c2{-(o.x + o.y) * kRsqrt2, (o.x - o.y) * kRsqrt2} : c2{(o.y - o.x) * kRsqrt2, -(o.x + o.y) * kRsqrt2};
+}
+__device__ __forceinline__ df r2df() { return {0.70710676908493042f, 1.2101617485882343e-08f}; }
+template <bool INV>
+__device__ __forceinline__ cdf w8_1(cdf o) {
+    const df r = r2df();
+    return INV ? cdf{dmul(dsub(o.x, o.y), r), dmul(dadd(o.x, o.y), r)}
+               : cdf{dmul(dadd(o.x, o.y), r), dmul(dsub(o.y, o.x), r)};
+}
+template <bool INV>
+__device__ __forceinline__ cdf w8_3(cdf o) {
+    const df r = r2df();
+    return INV ? cdf{dneg(dmul(dadd(o.x, o.y), r)), dmul(dsub(o.x, o.y), r)}
+               : cdf{dmul(dsub(o.y, o.x), r), dneg(dmul(dadd(o.x, o.y), r))};
+}
+
+template <class T>
+__device__ __forceinline__ void dft2(T& a, T& b) {
+    const T t = a;
     a = cadd(t, b);
     b = csub(t, b);
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft4(c2& x0, c2& x1, c2& x2, c2& x3) {
-    const c2 s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = mul_mi<INV>(csub(x1, x3));
+template <bool INV, class T>
+__device__ __forceinline__ void dft4(T& x0, T& x1, T& x2, T& x3) {
+    const T s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = mul_mi<INV>(csub(x1, x3));
     x0 = cadd(s02, s13);
     x2 = csub(s02, s13);
     x1 = cadd(d02, d13);
@@ -77,18 +160,15 @@ __device__ __forceinline__ void dft4(c2& x0, c2& x1, c2& x2, c2& x3) {
 
 // 8-point DFT in place (natural order in and out): 4-point DFTs E, O of the even and odd
 // samples, then X_k = E_k + W8^k O_k, X_{k+4} = E_k - W8^k O_k.
-template <bool INV>
-__device__ __forceinline__ void dft8(c2* v) {
-    c2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-    c2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+template <bool INV, class T>
+__device__ __forceinline__ void dft8(T* v) {
+    T e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    T o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
     dft4<INV>(e0, e1, e2, e3);
     dft4<INV>(o0, o1, o2, o3);
-    // W8^1 = (1 - i)/sqrt2, W8^2 = -i, W8^3 = (-1 - i)/sqrt2 (conjugates for the inverse)
-    const c2 w1 = INV ? c2{(o1.x - o1.y) * kRsqrt2, (o1.x + o1.y) * kRsqrt2}
-                      : c2{(o1.x + o1.y) * kRsqrt2, (o1.y - o1.x) * kRsqrt2};
-    const c2 w2 = mul_mi<INV>(o2);
-    const c2 w3 = INV ? c2{-(o3.x + o3.y) * kRsqrt2, (o3.x - o3.y) * kRsqrt2}
-                      : c2{(o3.y - o3.x) * kRsqrt2, -(o3.x + o3.y) * kRsqrt2};
+    const T w1 = w8_1<INV>(o1);
+    const T w2 = mul_mi<INV>(o2);
+    const T w3 = w8_3<INV>(o3);
     v[0] = cadd(e0, o0);
     v[4] = csub(e0, o0);
     v[1] = cadd(e1, w1);
@@ -106,14 +186,32 @@ __device__ __forceinline__ c2 ld2(const double* p, int64_t i) {
 __device__ __forceinline__ void st2(double* p, int64_t i, c2 v) {
     reinterpret_cast<double2*>(p)[i] = make_double2(v.x, v.y);
 }
+// complex element i of an interleaved FP64 array, as T
+template <class T> __device__ __forceinline__ T ldc(const double* p, int64_t i);
+template <> __device__ __forceinline__ c2 ldc<c2>(const double* p, int64_t i) { return ld2(p, i); }
+template <> __device__ __forceinline__ cdf ldc<cdf>(const double* p, int64_t i) {
+    const c2 v = ld2(p, i);
+    return {df_of(v.x), df_of(v.y)};
+}
+__device__ __forceinline__ void stc(double* p, int64_t i, c2 v) { st2(p, i, v); }
+__device__ __forceinline__ void stc(double* p, int64_t i, cdf v) { st2(p, i, c2{cre(v), cim(v)}); }
+// twiddle k of a table: interleaved FP64 (c2) or float4 pairs (cdf)
+template <class T> __device__ __forceinline__ T ldtw(const void* tab, int64_t k);
+template <> __device__ __forceinline__ c2 ldtw<c2>(const void* tab, int64_t k) {
+    return ld2(static_cast<const double*>(tab), k);
+}
+template <> __device__ __forceinline__ cdf ldtw<cdf>(const void* tab, int64_t k) {
+    const float4 v = __ldg(static_cast<const float4*>(tab) + k);
+    return {{v.x, v.y}, {v.z, v.w}};
+}
 
 // Stockham FFT of the line s[pad(0..L)) by the L/8 threads q of its group.  Every thread of
 // the block calls this with the same L (the barriers are block-wide); a thread whose group
 // is inactive only takes part in the barriers.  Ends with a barrier.
-template <bool INV>
-__device__ void line_fft(c2* s, int L, int q, const double* __restrict__ tw, bool active) {
+template <bool INV, class T>
+__device__ void line_fft(T* s, int L, int q, const void* tw, bool active) {
     const int G = L >> 3;
-    c2 v[8];
+    T v[8];
     for (int Ns = 1; Ns < L;) {
         const int R = (L / Ns >= 8) ? 8 : L / Ns;
         const int LR = L / R;
@@ -141,7 +239,7 @@ __device__ void line_fft(c2* s, int L, int q, const double* __restrict__ tw, boo
                 if (Ns > 1) {
 #pragma unroll
                     for (int r = 1; r < 8; ++r) {
-                        const c2 t = ld2(tw, r * k * tstep);
+                        const T t = ldtw<T>(tw, r * k * tstep);
                         v[r] = INV ? cmulc(v[r], t) : cmul(v[r], t);
                     }
                 }
@@ -153,11 +251,11 @@ __device__ void line_fft(c2* s, int L, int q, const double* __restrict__ tw, boo
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
                     const int j = q + b * G, k = j & (Ns - 1);
-                    c2* w = v + 4 * b;
+                    T* w = v + 4 * b;
                     if (Ns > 1) {
 #pragma unroll
                         for (int r = 1; r < 4; ++r) {
-                            const c2 t = ld2(tw, r * k * tstep);
+                            const T t = ldtw<T>(tw, r * k * tstep);
                             w[r] = INV ? cmulc(w[r], t) : cmul(w[r], t);
                         }
                     }
@@ -170,9 +268,9 @@ __device__ void line_fft(c2* s, int L, int q, const double* __restrict__ tw, boo
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     const int j = q + b * G, k = j & (Ns - 1);
-                    c2* w = v + 2 * b;
+                    T* w = v + 2 * b;
                     if (Ns > 1) {
-                        const c2 t = ld2(tw, k * tstep);
+                        const T t = ldtw<T>(tw, k * tstep);
                         w[1] = INV ? cmulc(w[1], t) : cmul(w[1], t);
                     }
                     dft2(w[0], w[1]);
@@ -187,74 +285,92 @@ __device__ void line_fft(c2* s, int L, int q, const double* __restrict__ tw, boo
     }
 }
 
+// the twiddle tables of one arithmetic: FP64 (c2) or float pairs (cdf)
+template <class T> __device__ __forceinline__ const void* tab_tw1(const FftArgs& a);
+template <> __device__ __forceinline__ const void* tab_tw1<c2>(const FftArgs& a) { return a.tw1; }
+template <> __device__ __forceinline__ const void* tab_tw1<cdf>(const FftArgs& a) { return a.tw1f; }
+template <class T> __device__ __forceinline__ const void* tab_tw2(const FftArgs& a);
+template <> __device__ __forceinline__ const void* tab_tw2<c2>(const FftArgs& a) { return a.tw2; }
+template <> __device__ __forceinline__ const void* tab_tw2<cdf>(const FftArgs& a) { return a.tw2f; }
+
 // W_N^e from the split tables
-__device__ __forceinline__ c2 twN(const FftArgs& a, int64_t e) {
+template <class T>
+__device__ __forceinline__ T twN(const FftArgs& a, int64_t e);
+template <>
+__device__ __forceinline__ c2 twN<c2>(const FftArgs& a, int64_t e) {
     return cmul(ld2(a.thi, e >> 6), ld2(a.tlo, e & 63));
+}
+template <>
+__device__ __forceinline__ cdf twN<cdf>(const FftArgs& a, int64_t e) {
+    return cmul(ldtw<cdf>(a.thif, e >> 6), ldtw<cdf>(a.tlof, e & 63));
 }
 
 // ------------------------------------------------------------------ column pass
-template <int MODE>
+template <int MODE, class T>
 __global__ void __launch_bounds__(512) k_fft_cols(const FftArgs a) {
-    extern __shared__ c2 sm[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* sm = reinterpret_cast<T*>(sm_raw);
     const int L = a.f.N1, G = L >> 3, C = a.f.C;
     const int N2 = a.f.N2, PL = pad(L);
     const int64_t N = a.f.N;
     const int b = blockIdx.y, c0 = blockIdx.x * C;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int line = tid / G, q = tid - line * G;
-    c2* s = sm + line * PL;
+    T* s = sm + line * PL;
     const int64_t seq = (int64_t)b * N;
     for (int e = tid; e < C * L; e += nthr) {
         const int c = e % C, r = e / C;
         const int64_t g = (int64_t)r * N2 + c0 + c;
-        c2 v{0.0, 0.0};
+        T v = czero<T>();
         if (MODE == FFT_COL_FWD_REAL) {
             if (g < a.nreal) {
-                v.x = a.V[(int64_t)(2 * b) * a.ldv + g];
-                if (2 * b + 1 < a.p) v.y = a.V[(int64_t)(2 * b + 1) * a.ldv + g];
+                const double re = a.V[(int64_t)(2 * b) * a.ldv + g];
+                const double im = (2 * b + 1 < a.p) ? a.V[(int64_t)(2 * b + 1) * a.ldv + g] : 0.0;
+                v = cmake<T>(re, im);
             }
         } else {
-            v = ld2(a.in, seq + g);
+            v = ldc<T>(a.in, seq + g);
         }
         sm[c * PL + pad(r)] = v;
     }
     __syncthreads();
     constexpr bool kInv = (MODE == FFT_COL_INV_REAL || MODE == FFT_COL_INV_CPLX || MODE == FFT_COL_INV_TRUNC_FWD);
-    line_fft<kInv>(s, L, q, a.tw1, true);
+    line_fft<kInv, T>(s, L, q, tab_tw1<T>(a), true);
     if (MODE == FFT_COL_INV_TRUNC_FWD) {
         // keep the first n entries only, then transform forward again
         for (int e = tid; e < C * L; e += nthr) {
             const int c = e % C, r = e / C;
-            if ((int64_t)r * N2 + c0 + c >= a.nreal) sm[c * PL + pad(r)] = c2{0.0, 0.0};
+            if ((int64_t)r * N2 + c0 + c >= a.nreal) sm[c * PL + pad(r)] = czero<T>();
         }
         __syncthreads();
-        line_fft<false>(s, L, q, a.tw1, true);
+        line_fft<false, T>(s, L, q, tab_tw1<T>(a), true);
     }
     for (int e = tid; e < C * L; e += nthr) {
         const int c = e % C, r = e / C;
         const int64_t g = (int64_t)r * N2 + c0 + c;
-        const c2 v = sm[c * PL + pad(r)];
+        const T v = sm[c * PL + pad(r)];
         if (MODE == FFT_COL_INV_REAL) {
             if (g < a.nreal) {
-                a.W[(int64_t)(2 * b) * a.ldw + g] = v.x * a.scale;
-                if (2 * b + 1 < a.p) a.W[(int64_t)(2 * b + 1) * a.ldw + g] = v.y * a.scale;
+                a.W[(int64_t)(2 * b) * a.ldw + g] = cre(v) * a.scale;
+                if (2 * b + 1 < a.p) a.W[(int64_t)(2 * b + 1) * a.ldw + g] = cim(v) * a.scale;
             }
         } else if (MODE == FFT_COL_INV_CPLX) {
-            st2(a.out, seq + g, cscale(v, a.scale));
+            stc(a.out, seq + g, cscale(v, a.scale));
         } else {
-            st2(a.out, seq + g, cmul(v, twN(a, (int64_t)(c0 + c) * r)));
+            stc(a.out, seq + g, cmul(v, twN<T>(a, (int64_t)(c0 + c) * r)));
         }
     }
 }
 
 // ------------------------------------------------------------------ row pass
-template <int MODE, int LPR>
-__device__ __forceinline__ void row_spectral_inverse(const FftArgs& a, c2* sm, c2* s, int L, int Rr, int PL,
+template <int MODE, int LPR, class T>
+__device__ __forceinline__ void row_spectral_inverse(const FftArgs& a, T* sm, T* s, int L, int Rr, int PL,
                                                      int k1_0, int64_t seq, int q, int sub);
 
-template <int MODE>
+template <int MODE, class T>
 __global__ void __launch_bounds__(512) k_fft_rows(const FftArgs a) {
-    extern __shared__ c2 sm[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* sm = reinterpret_cast<T*>(sm_raw);
     constexpr int LPR = (MODE == FFT_ROW_GSF_A || MODE == FFT_ROW_GSF_B) ? 2 : 1;   // lines per row
     const int L = a.f.N2, G = L >> 3, Rr = a.f.Rr;
     const int PL = pad(L);
@@ -262,55 +378,55 @@ __global__ void __launch_bounds__(512) k_fft_rows(const FftArgs a) {
     const int b = blockIdx.y, k1_0 = blockIdx.x * Rr;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int line = tid / G, q = tid - line * G, sub = line % LPR;
-    c2* s = sm + line * PL;
+    T* s = sm + line * PL;
     const int64_t seq = (int64_t)b * N;
     for (int e = tid; e < Rr * LPR * L; e += nthr) {
         const int ln = e / L, i = e - ln * L, row = ln / LPR, sb = ln % LPR;
         if (MODE == FFT_ROW_GSF_A && sb == 1) continue;
         const double* src = sb == 0 ? a.in : a.in2;
-        sm[ln * PL + pad(i)] = ld2(src, seq + (int64_t)(k1_0 + row) * L + i);
+        sm[ln * PL + pad(i)] = ldc<T>(src, seq + (int64_t)(k1_0 + row) * L + i);
     }
     __syncthreads();
-    line_fft<false>(s, L, q, a.tw2, !(MODE == FFT_ROW_GSF_A && sub == 1));
+    line_fft<false, T>(s, L, q, tab_tw2<T>(a), !(MODE == FFT_ROW_GSF_A && sub == 1));
     if constexpr (MODE == FFT_ROW_FWD) {
         for (int e = tid; e < Rr * L; e += nthr) {
             const int row = e / L, i = e - row * L;
-            st2(a.out, seq + (int64_t)(k1_0 + row) * L + i, sm[row * PL + pad(i)]);
+            stc(a.out, seq + (int64_t)(k1_0 + row) * L + i, sm[row * PL + pad(i)]);
         }
         return;
     } else {
-        row_spectral_inverse<MODE, LPR>(a, sm, s, L, Rr, PL, k1_0, seq, q, sub);
+        row_spectral_inverse<MODE, LPR, T>(a, sm, s, L, Rr, PL, k1_0, seq, q, sub);
     }
 }
 
 // The rest of a row pass: pointwise spectral step, inverse row DFT, W_N^{-n2 k1}, store.
-template <int MODE, int LPR>
-__device__ __forceinline__ void row_spectral_inverse(const FftArgs& a, c2* sm, c2* s, int L, int Rr, int PL,
+template <int MODE, int LPR, class T>
+__device__ __forceinline__ void row_spectral_inverse(const FftArgs& a, T* sm, T* s, int L, int Rr, int PL,
                                                      int k1_0, int64_t seq, int q, int sub) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     // pointwise spectral step (the plan's spectra are stored in the same transposed order)
     for (int e = tid; e < Rr * L; e += nthr) {
         const int row = e / L, i = e - row * L;
         const int64_t idx = (int64_t)(k1_0 + row) * L + i;
-        c2* s0 = sm + (row * LPR) * PL + pad(i);
+        T* s0 = sm + (row * LPR) * PL + pad(i);
         if (MODE == FFT_ROW_MATVEC) {
             *s0 = cscale(*s0, a.lam[idx] * a.scale);
         } else if (MODE == FFT_ROW_GSF_A) {
-            const c2 y = *s0;
-            s0[PL] = cscale(cmulc(y, ld2(a.mu2, idx)), a.scale);
-            *s0 = cscale(cmulc(y, ld2(a.mu1, idx)), a.scale);
+            const T y = *s0;
+            s0[PL] = cscale(cmulc(y, ldc<T>(a.mu2, idx)), a.scale);
+            *s0 = cscale(cmulc(y, ldc<T>(a.mu1, idx)), a.scale);
         } else {   // FFT_ROW_GSF_B
-            *s0 = cscale(csub(cmul(*s0, ld2(a.mu1, idx)), cmul(s0[PL], ld2(a.mu2, idx))), a.scale);
+            *s0 = cscale(csub(cmul(*s0, ldc<T>(a.mu1, idx)), cmul(s0[PL], ldc<T>(a.mu2, idx))), a.scale);
         }
     }
     __syncthreads();
-    line_fft<true>(s, L, q, a.tw2, MODE == FFT_ROW_GSF_A || sub == 0);
+    line_fft<true, T>(s, L, q, tab_tw2<T>(a), MODE == FFT_ROW_GSF_A || sub == 0);
     for (int e = tid; e < Rr * LPR * L; e += nthr) {
         const int ln = e / L, i = e - ln * L, row = ln / LPR, sb = ln % LPR;
         if (MODE != FFT_ROW_GSF_A && sb == 1) continue;
         const int k1 = k1_0 + row;
         double* dst = sb == 0 ? a.out : a.out2;
-        st2(dst, seq + (int64_t)k1 * L + i, cmulc(sm[ln * PL + pad(i)], twN(a, (int64_t)i * k1)));
+        stc(dst, seq + (int64_t)k1 * L + i, cmulc(sm[ln * PL + pad(i)], twN<T>(a, (int64_t)i * k1)));
     }
 }
 
@@ -322,6 +438,16 @@ __global__ void k_fft_tables(double* tw1, int N1, double* tw2, int N2, double* t
     if (e < N2) { sincospi(-2.0 * (double)e / N2, &s, &c); st2(tw2, e, c2{c, s}); }
     if (e < N / 64) { sincospi(-2.0 * (double)(64 * e) / (double)N, &s, &c); st2(thi, e, c2{c, s}); }
     if (e < 64) { sincospi(-2.0 * (double)e / (double)N, &s, &c); st2(tlo, e, c2{c, s}); }
+}
+
+// a complex FP64 table as float pairs (re_hi, re_lo, im_hi, im_lo) for the double-float passes
+__global__ void k_tab_df(const double* __restrict__ src, float* __restrict__ dst, int64_t count) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    float4 v;
+    split_df(src[2 * k], v.x, v.y);
+    split_df(src[2 * k + 1], v.z, v.w);
+    reinterpret_cast<float4*>(dst)[k] = v;
 }
 
 // sequence 0: the circulant's first column (Toeplitz embedding), imaginary parts zero
@@ -425,17 +551,23 @@ bool fft_geometry_ok(const FftPlan& f) {
            (size_t)2 * f.Rr * (f.N2 + f.N2 / 8) * 16 <= (size_t)kFftSmemMax;
 }
 
-cudaError_t fft_set_smem_limits() {
-    cudaError_t e = set_smem(k_fft_cols<FFT_COL_FWD_REAL>);
-    if (e == cudaSuccess) e = set_smem(k_fft_cols<FFT_COL_FWD_CPLX>);
-    if (e == cudaSuccess) e = set_smem(k_fft_cols<FFT_COL_INV_REAL>);
-    if (e == cudaSuccess) e = set_smem(k_fft_cols<FFT_COL_INV_CPLX>);
-    if (e == cudaSuccess) e = set_smem(k_fft_cols<FFT_COL_INV_TRUNC_FWD>);
-    if (e == cudaSuccess) e = set_smem(k_fft_rows<FFT_ROW_FWD>);
-    if (e == cudaSuccess) e = set_smem(k_fft_rows<FFT_ROW_MATVEC>);
-    if (e == cudaSuccess) e = set_smem(k_fft_rows<FFT_ROW_GSF_A>);
-    if (e == cudaSuccess) e = set_smem(k_fft_rows<FFT_ROW_GSF_B>);
+template <class T>
+cudaError_t fft_set_smem_limits_t() {
+    cudaError_t e = set_smem(k_fft_cols<FFT_COL_FWD_REAL, T>);
+    if (e == cudaSuccess) e = set_smem(k_fft_cols<FFT_COL_FWD_CPLX, T>);
+    if (e == cudaSuccess) e = set_smem(k_fft_cols<FFT_COL_INV_REAL, T>);
+    if (e == cudaSuccess) e = set_smem(k_fft_cols<FFT_COL_INV_CPLX, T>);
+    if (e == cudaSuccess) e = set_smem(k_fft_cols<FFT_COL_INV_TRUNC_FWD, T>);
+    if (e == cudaSuccess) e = set_smem(k_fft_rows<FFT_ROW_FWD, T>);
+    if (e == cudaSuccess) e = set_smem(k_fft_rows<FFT_ROW_MATVEC, T>);
+    if (e == cudaSuccess) e = set_smem(k_fft_rows<FFT_ROW_GSF_A, T>);
+    if (e == cudaSuccess) e = set_smem(k_fft_rows<FFT_ROW_GSF_B, T>);
     return e;
+}
+
+cudaError_t fft_set_smem_limits() {
+    const cudaError_t e = fft_set_smem_limits_t<c2>();
+    return e == cudaSuccess ? fft_set_smem_limits_t<cdf>() : e;
 }
 
 cudaError_t launch_fft_tables(const FftPlan& f, double* tw1, double* tw2, double* thi, double* tlo,
@@ -445,33 +577,51 @@ cudaError_t launch_fft_tables(const FftPlan& f, double* tw1, double* tw2, double
     return cudaGetLastError();
 }
 
-cudaError_t launch_fft_cols(const FftArgs& a, int mode, int nseq, cudaStream_t s) {
+template <class T>
+cudaError_t launch_fft_cols_t(const FftArgs& a, int mode, int nseq, cudaStream_t s) {
     const dim3 grid((unsigned)(a.f.N2 / a.f.C), (unsigned)nseq);
     const int threads = a.f.C * (a.f.N1 / 8);
-    const size_t smem = (size_t)a.f.C * (a.f.N1 + a.f.N1 / 8) * sizeof(c2);
+    const size_t smem = (size_t)a.f.C * (a.f.N1 + a.f.N1 / 8) * sizeof(T);
     switch (mode) {
-        case FFT_COL_FWD_REAL: k_fft_cols<FFT_COL_FWD_REAL><<<grid, threads, smem, s>>>(a); break;
-        case FFT_COL_FWD_CPLX: k_fft_cols<FFT_COL_FWD_CPLX><<<grid, threads, smem, s>>>(a); break;
-        case FFT_COL_INV_REAL: k_fft_cols<FFT_COL_INV_REAL><<<grid, threads, smem, s>>>(a); break;
-        case FFT_COL_INV_CPLX: k_fft_cols<FFT_COL_INV_CPLX><<<grid, threads, smem, s>>>(a); break;
-        case FFT_COL_INV_TRUNC_FWD: k_fft_cols<FFT_COL_INV_TRUNC_FWD><<<grid, threads, smem, s>>>(a); break;
+        case FFT_COL_FWD_REAL: k_fft_cols<FFT_COL_FWD_REAL, T><<<grid, threads, smem, s>>>(a); break;
+        case FFT_COL_FWD_CPLX: k_fft_cols<FFT_COL_FWD_CPLX, T><<<grid, threads, smem, s>>>(a); break;
+        case FFT_COL_INV_REAL: k_fft_cols<FFT_COL_INV_REAL, T><<<grid, threads, smem, s>>>(a); break;
+        case FFT_COL_INV_CPLX: k_fft_cols<FFT_COL_INV_CPLX, T><<<grid, threads, smem, s>>>(a); break;
+        case FFT_COL_INV_TRUNC_FWD: k_fft_cols<FFT_COL_INV_TRUNC_FWD, T><<<grid, threads, smem, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fft_rows(const FftArgs& a, int mode, int nseq, cudaStream_t s) {
+template <class T>
+cudaError_t launch_fft_rows_t(const FftArgs& a, int mode, int nseq, cudaStream_t s) {
     const int lpr = (mode == FFT_ROW_GSF_A || mode == FFT_ROW_GSF_B) ? 2 : 1;
     const dim3 grid((unsigned)(a.f.N1 / a.f.Rr), (unsigned)nseq);
     const int threads = a.f.Rr * lpr * (a.f.N2 / 8);
-    const size_t smem = (size_t)a.f.Rr * lpr * (a.f.N2 + a.f.N2 / 8) * sizeof(c2);
+    const size_t smem = (size_t)a.f.Rr * lpr * (a.f.N2 + a.f.N2 / 8) * sizeof(T);
     switch (mode) {
-        case FFT_ROW_FWD: k_fft_rows<FFT_ROW_FWD><<<grid, threads, smem, s>>>(a); break;
-        case FFT_ROW_MATVEC: k_fft_rows<FFT_ROW_MATVEC><<<grid, threads, smem, s>>>(a); break;
-        case FFT_ROW_GSF_A: k_fft_rows<FFT_ROW_GSF_A><<<grid, threads, smem, s>>>(a); break;
-        case FFT_ROW_GSF_B: k_fft_rows<FFT_ROW_GSF_B><<<grid, threads, smem, s>>>(a); break;
+        case FFT_ROW_FWD: k_fft_rows<FFT_ROW_FWD, T><<<grid, threads, smem, s>>>(a); break;
+        case FFT_ROW_MATVEC: k_fft_rows<FFT_ROW_MATVEC, T><<<grid, threads, smem, s>>>(a); break;
+        case FFT_ROW_GSF_A: k_fft_rows<FFT_ROW_GSF_A, T><<<grid, threads, smem, s>>>(a); break;
+        case FFT_ROW_GSF_B: k_fft_rows<FFT_ROW_GSF_B, T><<<grid, threads, smem, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// The passes run in FP64, or (a.df, with the float-pair tables set) in double-float.
+cudaError_t launch_fft_cols(const FftArgs& a, int mode, int nseq, cudaStream_t s) {
+    if (a.df && !(a.tw1f && a.thif && a.tlof)) return cudaErrorInvalidValue;
+    return a.df ? launch_fft_cols_t<cdf>(a, mode, nseq, s) : launch_fft_cols_t<c2>(a, mode, nseq, s);
+}
+
+cudaError_t launch_fft_rows(const FftArgs& a, int mode, int nseq, cudaStream_t s) {
+    if (a.df && !(a.tw2f && a.thif && a.tlof)) return cudaErrorInvalidValue;
+    return a.df ? launch_fft_rows_t<cdf>(a, mode, nseq, s) : launch_fft_rows_t<c2>(a, mode, nseq, s);
+}
+
+cudaError_t launch_fft_tables_df(const double* src, float* dst, int64_t count, cudaStream_t s) {
+    k_tab_df<<<blocks_for(count, 256), 256, 0, s>>>(src, dst, count);
     return cudaGetLastError();
 }
 

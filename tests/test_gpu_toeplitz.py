@@ -56,6 +56,25 @@ def test_product_matches_oracle(n, a, p, t):
     assert rel(Wg, Wo) <= 1e-13
 
 
+@pytest.mark.parametrize("n,a,p,t", [(3001, inputs.toeplitz_column(256), 16, 1.0), (700, dense_col(700), 5, 1.0)])
+def test_mixed_transforms_match_oracle(n, a, p, t):
+    """The mixed plan's transforms run in double-float (FP32 pairs, unit roundoff u = 2^-48).
+    A radix-8/4/2 four-step FFT of length N has about log2(N) rounding steps per output and
+    the product three transforms, so with N <= 2^13 here the bound ~ 3 * 13 * u * ||.||
+    stays under 2e-13 relative; the test allows 1e-12.  Products and the Gohberg-Semencul
+    inverse both go through these passes."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    V = inputs.rhs(n, p, 47)
+    plan = Plan.toeplitz(a, n, p_max=p, algorithm=2, precision="mixed")
+    Wg = to_np(plan.op_apply(t, to_dev(V)))
+    Wo = TZ.matvec(full_col(a, n), V, t)
+    assert rel(Wg, Wo) <= 1e-12
+    Ig = to_np(plan.prec_apply(t, to_dev(V)))
+    Io = TZ.gsf_apply(TZ.gsf_generator(full_col(a, n)), V, t)
+    assert rel(Ig, Io) <= 1e-11       # amplified by cond(T) <= 1e2 for these columns
+
+
 @pytest.mark.parametrize("n,a,p,t", [(1000, inputs.toeplitz_column(256), 3, 0.5),
                                      (3001, inputs.toeplitz_column(256), 8, 1.0),
                                      (500, dense_col(500), 2, 1.0)])
