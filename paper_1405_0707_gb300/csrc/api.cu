@@ -327,11 +327,15 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     const int cols = (j + 1) * p;
     const int f32 = P->opts.precision == EXPM_PREC_MIXED ? 1 : 0;
     const int nbc = P->nblk_cgs;
-    LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, nbc, s, f32));
+    // first pass: FP64, or in the mixed path FP32 projection and double-float update (the
+    // row-chunk kernels for p <= 16, else the tile kernels)
+    const bool rows = f32 && cgs_rows_fit(cols, p);
+    if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(0, P->V, ld, cols, P->W, ld, p, n, nullptr, P->part, nbc, s));
+    else LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, nbc, s, f32));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
-    // first pass update: FP64, or double-float on the FP32 pipe in the mixed path (f32 = 2)
-    LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 0, s,
-                                              f32 ? 2 : 0));
+    if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(1, P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, s));
+    else LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 0, s,
+                                                   f32 ? 2 : 0));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
     // second pass: in the mixed path the update is an O(eps_32) correction, formed in FP32;
     // with the fused QR its last CTA also reduces the Gram partials

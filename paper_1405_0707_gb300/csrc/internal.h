@@ -231,6 +231,9 @@ cudaError_t launch_d2f(const double* in, float* out, int64_t n, cudaStream_t s);
 cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const double* W,
                                 int64_t ldw, int p, int64_t n, double* part, int nblk,
                                 cudaStream_t s, int f32 = 0);
+bool cgs_rows_fit(int cols, int p);
+cudaError_t launch_cgs_rows(int upd, const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p,
+                            int64_t n, const double* h, double* part, int nblk, cudaStream_t s);
 cudaError_t launch_reduce_h(const double* part, int nblk, int cols, int p, double* h,
                             double* H, int ldH, int row0, int col0, int accumulate,
                             cudaStream_t s);

@@ -779,6 +779,48 @@ cudaError_t launch_reduce_h(const double* part, int nblk_req, int cols, int p, d
     return cudaGetLastError();
 }
 
+// The first CGS pass of the mixed path by the row-chunk kernels (k_cgs_rows, p <= 16): used
+// when the projection outputs per thread (cols p / NTR) and the staged chunk fit.
+constexpr int kCgsRowsKMax = 20;
+constexpr size_t kCgsRowsSmemMax = 112 * 1024;
+
+bool cgs_rows_fit(int cols, int p) {
+    if (p < 1 || p > rows16::RP || cols < 1) return false;
+    if (p <= rows8::RP)
+        return (cols * p + rows8::NTR - 1) / rows8::NTR <= kCgsRowsKMax &&
+               rows8::cgs_rows_smem(cols, true) <= kCgsRowsSmemMax;
+    return (cols * p + rows16::NTR - 1) / rows16::NTR <= kCgsRowsKMax &&
+           rows16::cgs_rows_smem(cols, true) <= kCgsRowsSmemMax;
+}
+
+cudaError_t launch_cgs_rows(int upd, const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p,
+                            int64_t n, const double* h, double* part, int nblk, cudaStream_t s) {
+    if (!cgs_rows_fit(cols, p) || (upd && !h)) return cudaErrorInvalidValue;
+    const int64_t rpb = rows_per_block(n, nblk);
+    const int g = blocks_for(n, nblk);
+#define EXPM_CGS_K(NS, KK)                                                                                  \
+    {                                                                                                      \
+        constexpr int K_ = KK;                                                                             \
+        const size_t shm = NS::cgs_rows_smem(cols, upd != 0);                                              \
+        if (upd) NS::k_cgs_rows<true, K_><<<g, NS::NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part); \
+        else NS::k_cgs_rows<false, K_><<<g, NS::NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part);   \
+    }
+#define EXPM_CGS_NS(NS)                                          \
+    {                                                            \
+        const int k = (cols * p + NS::NTR - 1) / NS::NTR;        \
+        if (k <= 1) EXPM_CGS_K(NS, 1)                            \
+        else if (k <= 3) EXPM_CGS_K(NS, 3)                       \
+        else if (k <= 6) EXPM_CGS_K(NS, 6)                       \
+        else if (k <= 12) EXPM_CGS_K(NS, 12)                     \
+        else EXPM_CGS_K(NS, 20)                                  \
+    }
+    if (p <= rows8::RP) EXPM_CGS_NS(rows8)
+    else EXPM_CGS_NS(rows16)
+#undef EXPM_CGS_NS
+#undef EXPM_CGS_K
+    return cudaGetLastError();
+}
+
 cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int nblk, double* G, double* part,
                                  unsigned* ctr, int mode, double* R, double* Rinv, const double* Rtot_in,
                                  double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
@@ -947,6 +989,15 @@ cudaError_t krylov_set_smem_limits() {
     EXPM_SET(rows16::k_update_gram_rows<false>);
     EXPM_SET(rows16::k_update_gram_rows<true>);
     EXPM_SET(rows16::k_update_z_rows);
+#define EXPM_SET_CGS(NS)                                                                                    \
+    EXPM_SET((NS::k_cgs_rows<true, 1>)); EXPM_SET((NS::k_cgs_rows<true, 3>)); EXPM_SET((NS::k_cgs_rows<true, 6>)); \
+    EXPM_SET((NS::k_cgs_rows<true, 12>)); EXPM_SET((NS::k_cgs_rows<true, 20>));                               \
+    EXPM_SET((NS::k_cgs_rows<false, 1>)); EXPM_SET((NS::k_cgs_rows<false, 3>));                               \
+    EXPM_SET((NS::k_cgs_rows<false, 6>)); EXPM_SET((NS::k_cgs_rows<false, 12>));                              \
+    EXPM_SET((NS::k_cgs_rows<false, 20>));
+    EXPM_SET_CGS(rows8)
+    EXPM_SET_CGS(rows16)
+#undef EXPM_SET_CGS
 #undef EXPM_SET
     return e;
 }

@@ -699,3 +699,184 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
     }
 }
 
+
+// ---- first block CGS2 pass of the mixed path, in chunks of RB = NTR / 2 rows
+//
+// k_cgs_rows<false>: partial[blk][a][c] = sum over the CTA's rows of V[r, a] W[r, c] (FP32
+// products; the projection of the first pass).
+// k_cgs_rows<true>:  W <- W - V h in double-float arithmetic (as k_update_df: each product
+// v h = vh hh + (err(vh hh) + vl hh + vh hl), the large parts accumulated with TwoSum), then
+// the FP32 partials of V^T W for the second pass.
+// Per chunk the FP32 copy of V (cols x RB) and of W (RB x RP) are staged in shared memory
+// and the cols x p projection outputs are spread over the threads (output o = tid + k NTR);
+// each chunk's FP32 sum is added to a float-pair accumulator, so the CTA's partial carries
+// FP32 products but no growth of the summation error with the number of chunks.  In the
+// update two threads share a row (each takes half of the columns a, the pair sums combine in
+// a fixed order), with no barrier inside the column loop.
+constexpr int RB = NTR / 2;
+constexpr int WS = RP + 1;                  // row stride of the FP32 copy of W
+
+__host__ __device__ constexpr size_t cgs_rows_smem(int cols, bool upd) {
+    return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS + (size_t)cols * (RB + 1));
+}
+
+// one double-float multiply-add: (sh, sl) += (vh + vl)(h1 + h2)
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float vh, float vl, float h1, float h2) {
+    const float pr = vh * h1;
+    float t = fmaf(vh, h1, -pr);
+    t = fmaf(vl, h1, t);
+    t = fmaf(vh, h2, t);
+    df_add(sh, sl, pr);
+    sl += t;
+}
+
+template <int K>
+__device__ __forceinline__ void chunk_project(const float* Vs, const float* Wf, int nout, int p, float* ah,
+                                              float* al) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int o = threadIdx.x + k * NTR;
+        if (o < nout) {
+            const int a = o / p, c = o - a * p;
+            const float* va = Vs + a * (RB + 1);
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+            for (int rr = 0; rr < RB; rr += 2) {
+                s0 = fmaf(va[rr], Wf[rr * WS + c], s0);
+                s1 = fmaf(va[rr + 1], Wf[(rr + 1) * WS + c], s1);
+            }
+            df_add(ah[k], al[k], s0);
+            df_add(ah[k], al[k], s1);
+        }
+    }
+}
+
+template <bool UPD, int K>
+__global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, int64_t ldv, int cols,
+                                                 double* __restrict__ W, int64_t ldw, int p, int64_t n,
+                                                 int64_t rpb, const double* __restrict__ h,
+                                                 double* __restrict__ part) {
+    extern __shared__ __align__(16) float smf[];
+    float* hh = smf;                                   // UPD: cols x RP (zero-padded columns)
+    float* hl = hh + (UPD ? cols * RP : 0);
+    float* Wf = hl + (UPD ? cols * RP : 0);            // RB x WS
+    float* Vs = Wf + RB * WS;                          // cols x (RB + 1)
+    if (UPD) {
+        for (int e = threadIdx.x; e < cols * RP; e += NTR) {
+            const int a = e / RP, c = e - a * RP;
+            float x = 0.f, y = 0.f;
+            if (c < p) split_df(h[a * p + c], x, y);
+            hh[e] = x;
+            hl[e] = y;
+        }
+    }
+    const int nout = cols * p;
+    float ah[K], al[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        ah[k] = 0.f;
+        al[k] = 0.f;
+    }
+    const int rr = threadIdx.x >> 1, hf = threadIdx.x & 1;
+    const int half = (cols + 1) >> 1;
+    const int a0 = hf ? half : 0, a1 = hf ? cols : half;
+    const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
+    for (int64_t r0 = rb; r0 < re; r0 += RB) {
+        const int tr = (int)min((int64_t)RB, re - r0);
+        if (UPD) {
+            __syncthreads();                           // hh/hl written; previous chunk consumed
+            const bool ok = rr < tr;
+            const int64_t r = r0 + rr;
+            float sh[RP], sl[RP];
+#pragma unroll
+            for (int c = 0; c < RP; ++c) {
+                sh[c] = 0.f;
+                sl[c] = 0.f;
+            }
+            int a = a0;
+            for (; a + 4 <= a1; a += 4) {
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = ok ? V[(int64_t)(a + u) * ldv + r] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float vh, vl;
+                    split_df(v[u], vh, vl);
+                    Vs[(a + u) * (RB + 1) + rr] = vh;
+                    const float4* x4 = reinterpret_cast<const float4*>(hh + (a + u) * RP);
+                    const float4* y4 = reinterpret_cast<const float4*>(hl + (a + u) * RP);
+#pragma unroll
+                    for (int q = 0; q < RP / 4; ++q) {
+                        const float4 x = x4[q], y = y4[q];
+                        df_fma(sh[4 * q], sl[4 * q], vh, vl, x.x, y.x);
+                        df_fma(sh[4 * q + 1], sl[4 * q + 1], vh, vl, x.y, y.y);
+                        df_fma(sh[4 * q + 2], sl[4 * q + 2], vh, vl, x.z, y.z);
+                        df_fma(sh[4 * q + 3], sl[4 * q + 3], vh, vl, x.w, y.w);
+                    }
+                }
+            }
+            for (; a < a1; ++a) {
+                const double v = ok ? V[(int64_t)a * ldv + r] : 0.0;
+                float vh, vl;
+                split_df(v, vh, vl);
+                Vs[a * (RB + 1) + rr] = vh;
+                const float4* x4 = reinterpret_cast<const float4*>(hh + a * RP);
+                const float4* y4 = reinterpret_cast<const float4*>(hl + a * RP);
+#pragma unroll
+                for (int q = 0; q < RP / 4; ++q) {
+                    const float4 x = x4[q], y = y4[q];
+                    df_fma(sh[4 * q], sl[4 * q], vh, vl, x.x, y.x);
+                    df_fma(sh[4 * q + 1], sl[4 * q + 1], vh, vl, x.y, y.y);
+                    df_fma(sh[4 * q + 2], sl[4 * q + 2], vh, vl, x.z, y.z);
+                    df_fma(sh[4 * q + 3], sl[4 * q + 3], vh, vl, x.w, y.w);
+                }
+            }
+            // the two halves of the row: (half 0) + (half 1), the same order in both threads
+#pragma unroll
+            for (int c = 0; c < RP; ++c) {
+                const float oh = __shfl_xor_sync(0xffffffffu, sh[c], 1);
+                const float ol = __shfl_xor_sync(0xffffffffu, sl[c], 1);
+                float xh = hf ? oh : sh[c], xl = hf ? ol : sl[c];
+                const float yh = hf ? sh[c] : oh, yl = hf ? sl[c] : ol;
+                df_add(xh, xl, yh);
+                xl += yl;
+                if ((c & 1) == hf) {
+                    float wf = 0.f;
+                    if (ok && c < p) {
+                        const double w = W[(int64_t)c * ldw + r] - ((double)xh + (double)xl);
+                        W[(int64_t)c * ldw + r] = w;
+                        wf = (float)w;
+                    }
+                    Wf[rr * WS + c] = wf;
+                }
+            }
+        } else {
+            __syncthreads();                           // previous chunk consumed
+            const int tot = cols * RB;
+            for (int e0 = threadIdx.x; e0 < tot; e0 += LB * NTR) {
+                double v[LB];
+#pragma unroll
+                for (int k = 0; k < LB; ++k) {
+                    const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
+                    v[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+                }
+#pragma unroll
+                for (int k = 0; k < LB; ++k) {
+                    const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
+                    if (e < tot) Vs[a * (RB + 1) + r2] = (float)v[k];
+                }
+            }
+            for (int e = threadIdx.x; e < RP * RB; e += NTR) {
+                const int c = e / RB, r2 = e - c * RB;
+                Wf[r2 * WS + c] = (c < p && r2 < tr) ? (float)W[(int64_t)c * ldw + r0 + r2] : 0.f;
+            }
+        }
+        __syncthreads();
+        chunk_project<K>(Vs, Wf, nout, p, ah, al);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int o = threadIdx.x + k * NTR;
+        if (o < nout) part[(int64_t)blockIdx.x * nout + o] = (double)ah[k] + (double)al[k];
+    }
+}

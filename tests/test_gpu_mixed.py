@@ -74,3 +74,23 @@ def test_mixed_meets_metric_tolerance_on_bench_workload(tab, t):
     # and against the closed form r(tA)B
     ref = ops.exact_r_of_A_B(w["sides"], w["diff"], w["vel"], t, tab, inputs.rhs(n, w["p"], w["seed"]))
     assert rel(to_np(Z32), ref) <= 1e-8
+
+
+@pytest.mark.parametrize("sides,p", [((70, 66), 1), ((70, 66), 5), ((256, 256), 8), ((97, 83), 12),
+                                     ((97, 83), 16)])
+def test_mixed_arnoldi_relation_is_fp64_exact(sides, p):
+    """The mixed block step (FP32 projections, double-float first update, FP32 second-pass
+    correction, FP32-factor Cholesky-QR applied exactly) keeps the block Arnoldi relation
+    (tA)^{-1} V_m = V_{m+1} H~_m (Section 3) to FP64 rounding, while V is orthonormal only to
+    the FP32 level.  W = (tA)^{-1} V_m comes from the plan's own inverse."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n, m, t = int(np.prod(sides)), 6, 0.05
+    V1, _ = ps.qr_positive(inputs.rhs(n, p, 8))
+    plan = Plan(sides, 0.1, (1.0, -0.5), p_max=p, m=m, precision="mixed")
+    Vg, Hg = plan.arnoldi(t, to_dev(V1))
+    W = np.column_stack([to_np(plan.prec_apply(t, Vg[:, j * p:(j + 1) * p])) for j in range(m)])
+    Vn, Hn = to_np(Vg), to_np(Hg)
+    assert np.linalg.norm(W - Vn @ Hn) <= 1e-12 * np.linalg.norm(W)
+    assert np.linalg.norm(Vn.T @ Vn - np.eye((m + 1) * p)) <= 1e-5
+    assert np.all(Hn[np.tril_indices_from(Hn, -p - 1)] == 0.0)
