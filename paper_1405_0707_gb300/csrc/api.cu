@@ -86,8 +86,11 @@ inline bool fused_qr(const expm_plan* P, int p) {
     return p <= kRowsMaxP && P->opts.precision == EXPM_PREC_MIXED;
 }
 
+// cgs_cols > 0 (mixed path, after the row-chunk CGS kernels): the first pass also applies
+// the second CGS pass's correction W -= V[:, 0:cgs_cols] h, with h followed by the Gram
+// matrix of W before it (k_qr_mixed_rows<3>).
 expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, int hrow, int hcol,
-                     double* normsq, bool gram_done) {
+                     double* normsq, bool gram_done, int cgs_cols = 0) {
     cudaStream_t s = P->stream;
     const int64_t n = P->n, ld = P->ld;
     const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * std::ldexp(1.0, -53);
@@ -103,7 +106,8 @@ expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, 
         }
         LAUNCH(EXPM_STAGE_QR, launch_qr_mixed_rows(P->W, ld, p, n, P->nblk, G, P->part, P->ctr, 0, sm(P, kOffR),
                                                    sm(P, kOffRi), nullptr, sm(P, kOffRt), Hq, P->ldH, hrow, hcol,
-                                                   normsq, flags, P->W, ld, s));
+                                                   normsq, flags, P->W, ld, s, cgs_cols ? P->V : nullptr, ld,
+                                                   cgs_cols, cgs_cols ? sm(P, kOffH) : nullptr));
         LAUNCH(EXPM_STAGE_QR, launch_qr_mixed_rows(P->W, ld, p, n, P->nblk, G, P->part, P->ctr, 1, sm(P, kOffR),
                                                    sm(P, kOffRi), sm(P, kOffRt), sm(P, kOffRt2), Hq, P->ldH, hrow,
                                                    hcol, nullptr, flags, out, ldo, s));
@@ -330,10 +334,17 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     // first pass: FP64, or in the mixed path FP32 projection and double-float update (the
     // row-chunk kernels for p <= 16, else the tile kernels)
     const bool rows = f32 && cgs_rows_fit(cols, p);
-    if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(0, P->V, ld, cols, P->W, ld, p, n, nullptr, P->part, nbc, s));
+    if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(0, P->V, ld, cols, P->W, ld, p, n, nullptr, P->part, nbc, 0, s));
     else LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, nbc, s, f32));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
-    if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(1, P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, s));
+    if (rows && fused_qr(P, p)) {
+        // update, second projection and the Gram matrix of W in one pass; the second pass's
+        // correction is applied by the first Cholesky-QR pass
+        LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(1, P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 1, s));
+        LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols + p, p, h, P->H, P->ldH, 0, j * p, 1, s, cols));
+        return qr_block(P, p, P->V + (int64_t)(j + 1) * p * ld, ld, true, (j + 1) * p, j * p, nullptr, true, cols);
+    }
+    if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(1, P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 0, s));
     else LAUNCH(EXPM_STAGE_CGS, launch_update_proj(P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 0, s,
                                                    f32 ? 2 : 0));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 1, s));
@@ -979,7 +990,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     ok = ok && dalloc(&P->Bst, (size_t)ld * p_max);
     ok = ok && dalloc(&P->Zst, (size_t)ld * p_max);
     ok = ok && dalloc(&P->H, (size_t)P->ldH * mpm);
-    ok = ok && dalloc(&P->part, (size_t)std::max(P->nblk, P->nblk_cgs) * std::max(mpm * p_max, p_max * p_max));
+    ok = ok && dalloc(&P->part, (size_t)std::max(P->nblk, P->nblk_cgs) * (mpm + p_max) * p_max);
     ok = ok && dalloc(&P->small, kSmallDoubles);
     ok = ok && dalloc(&P->S, (size_t)P->npoles * p_max * p_max * 2);
     ok = ok && dalloc(&P->Wc_slots, (size_t)P->npoles * (mpm + p_max) * p_max);

@@ -233,10 +233,11 @@ cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const do
                                 cudaStream_t s, int f32 = 0);
 bool cgs_rows_fit(int cols, int p);
 cudaError_t launch_cgs_rows(int upd, const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p,
-                            int64_t n, const double* h, double* part, int nblk, cudaStream_t s);
+                            int64_t n, const double* h, double* part, int nblk, int gram, cudaStream_t s);
+// hcols < 0: every output row a < cols goes to H; else only a < hcols (the rest to h only)
 cudaError_t launch_reduce_h(const double* part, int nblk, int cols, int p, double* h,
                             double* H, int ldH, int row0, int col0, int accumulate,
-                            cudaStream_t s);
+                            cudaStream_t s, int hcols = -1);
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
                                int p, int64_t n, const double* h, double* part, int nblk,
                                int gram, cudaStream_t s, int f32 = 0, int upd32 = 0, double* G = nullptr,
@@ -246,7 +247,9 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
 cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int nblk, double* G, double* part,
                                  unsigned* ctr, int mode, double* R, double* Rinv, const double* Rtot_in,
                                  double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
-                                 int* flags, double* out, int64_t ldo, cudaStream_t s);
+                                 int* flags, double* out, int64_t ldo, cudaStream_t s,
+                                 const double* Vc = nullptr, int64_t ldvc = 0, int ccols = 0,
+                                 const double* h2 = nullptr);
 constexpr int kRowsMaxP = 16;  // widths handled by the row-per-thread kernels
 // Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
 // third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.

@@ -210,7 +210,7 @@ constexpr int RED_STRIPES = 32;   // threads per output
 // the stripes are added in two fixed-order levels (4 groups of 8, then the 4 groups).
 __global__ void __launch_bounds__(RED_OUT * RED_STRIPES)
 k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p, double* __restrict__ h,
-           double* H, int ldH, int row0, int col0, int accumulate) {
+           double* H, int ldH, int row0, int col0, int accumulate, int hcols) {
     __shared__ double red[RED_STRIPES][RED_OUT];
     __shared__ double red2[4][RED_OUT];
     const int nout = cols * p;
@@ -228,7 +228,7 @@ k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p, double* _
     if (st != 0 || o >= nout) return;
     const double s = (red2[0][ol] + red2[1][ol]) + (red2[2][ol] + red2[3][ol]);
     h[o] = s;
-    if (H) {
+    if (H && o < hcols * p) {
         const int a = o / p, c = o % p;
         double* dst = H + (int64_t)(col0 + c) * ldH + row0 + a;
         *dst = accumulate ? *dst + s : s;
@@ -772,10 +772,10 @@ cudaError_t launch_proj_partial(const double* V, int64_t ldv, int cols, const do
 
 cudaError_t launch_reduce_h(const double* part, int nblk_req, int cols, int p, double* h,
                             double* H, int ldH, int row0, int col0, int accumulate,
-                            cudaStream_t s) {
+                            cudaStream_t s, int hcols) {
     const int nout = cols * p;
     k_reduce_h<<<(nout + RED_OUT - 1) / RED_OUT, RED_OUT * RED_STRIPES, 0, s>>>(
-        part, nblk_req, cols, p, h, H, ldH, row0, col0, accumulate);
+        part, nblk_req, cols, p, h, H, ldH, row0, col0, accumulate, hcols < 0 ? cols : hcols);
     return cudaGetLastError();
 }
 
@@ -787,27 +787,28 @@ constexpr size_t kCgsRowsSmemMax = 112 * 1024;
 bool cgs_rows_fit(int cols, int p) {
     if (p < 1 || p > rows16::RP || cols < 1) return false;
     if (p <= rows8::RP)
-        return (cols * p + rows8::NTR - 1) / rows8::NTR <= kCgsRowsKMax &&
-               rows8::cgs_rows_smem(cols, true) <= kCgsRowsSmemMax;
-    return (cols * p + rows16::NTR - 1) / rows16::NTR <= kCgsRowsKMax &&
-           rows16::cgs_rows_smem(cols, true) <= kCgsRowsSmemMax;
+        return ((cols + p) * p + rows8::NTR - 1) / rows8::NTR <= kCgsRowsKMax &&
+               rows8::cgs_rows_smem(cols, true, p) <= kCgsRowsSmemMax;
+    return ((cols + p) * p + rows16::NTR - 1) / rows16::NTR <= kCgsRowsKMax &&
+           rows16::cgs_rows_smem(cols, true, p) <= kCgsRowsSmemMax;
 }
 
 cudaError_t launch_cgs_rows(int upd, const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p,
-                            int64_t n, const double* h, double* part, int nblk, cudaStream_t s) {
-    if (!cgs_rows_fit(cols, p) || (upd && !h)) return cudaErrorInvalidValue;
+                            int64_t n, const double* h, double* part, int nblk, int gram, cudaStream_t s) {
+    if (!cgs_rows_fit(cols, p) || (upd && !h) || (gram && !upd)) return cudaErrorInvalidValue;
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
+    const int ng = gram ? p : 0;
 #define EXPM_CGS_K(NS, KK)                                                                                  \
     {                                                                                                      \
         constexpr int K_ = KK;                                                                             \
-        const size_t shm = NS::cgs_rows_smem(cols, upd != 0);                                              \
-        if (upd) NS::k_cgs_rows<true, K_><<<g, NS::NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part); \
-        else NS::k_cgs_rows<false, K_><<<g, NS::NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part);   \
+        const size_t shm = NS::cgs_rows_smem(cols, upd != 0, ng);                                          \
+        if (upd) NS::k_cgs_rows<true, K_><<<g, NS::NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng); \
+        else NS::k_cgs_rows<false, K_><<<g, NS::NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, 0);    \
     }
 #define EXPM_CGS_NS(NS)                                          \
     {                                                            \
-        const int k = (cols * p + NS::NTR - 1) / NS::NTR;        \
+        const int k = ((cols + ng) * p + NS::NTR - 1) / NS::NTR; \
         if (k <= 1) EXPM_CGS_K(NS, 1)                            \
         else if (k <= 3) EXPM_CGS_K(NS, 3)                       \
         else if (k <= 6) EXPM_CGS_K(NS, 6)                       \
@@ -824,17 +825,25 @@ cudaError_t launch_cgs_rows(int upd, const double* V, int64_t ldv, int cols, dou
 cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int nblk, double* G, double* part,
                                  unsigned* ctr, int mode, double* R, double* Rinv, const double* Rtot_in,
                                  double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
-                                 int* flags, double* out, int64_t ldo, cudaStream_t s) {
+                                 int* flags, double* out, int64_t ldo, cudaStream_t s, const double* Vc,
+                                 int64_t ldvc, int ccols, const double* h2) {
     if (p > rows16::RP) return cudaErrorInvalidValue;
+    if (Vc && (mode != 0 || !h2 || ccols < 1 || ccols > kMaxMP)) return cudaErrorInvalidValue;
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
 #define EXPM_QR_ROWS(NS)                                                                                          \
-    if (mode == 0)                                                                                              \
+    if (mode == 0 && Vc)                                                                                        \
+        NS::k_qr_mixed_rows<3><<<g, NS::NTR, sizeof(float) * (size_t)ccols * NS::RP, s>>>(                      \
+            W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H, ldH, hrow, hcol, normsq_out,    \
+            flags, out, ldo, Vc, ldvc, ccols, h2);                                                               \
+    else if (mode == 0)                                                                                         \
         NS::k_qr_mixed_rows<1><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
-                                                     Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo); \
+                                                     Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo,  \
+                                                     nullptr, 0, 0, nullptr);                                    \
     else                                                                                                        \
         NS::k_qr_mixed_rows<2><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
-                                                     Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo);
+                                                     Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo,  \
+                                                     nullptr, 0, 0, nullptr);
     if (p <= rows8::RP) { EXPM_QR_ROWS(rows8) }
     else { EXPM_QR_ROWS(rows16) }
 #undef EXPM_QR_ROWS
@@ -997,6 +1006,8 @@ cudaError_t krylov_set_smem_limits() {
     EXPM_SET((NS::k_cgs_rows<false, 20>));
     EXPM_SET_CGS(rows8)
     EXPM_SET_CGS(rows16)
+    EXPM_SET(rows8::k_qr_mixed_rows<3>);
+    EXPM_SET(rows16::k_qr_mixed_rows<3>);
 #undef EXPM_SET_CGS
 #undef EXPM_SET
     return e;

@@ -326,14 +326,25 @@ __device__ inline void chol32_dev(CholF& cf, const double* G0, int p) {
     __syncwarp();
 }
 
+// KIND 1: the first pass (FP32 factor of G, exact double-float application).  KIND 3: the
+// same, fused with the second CGS pass's correction W <- W - Vc h2 (FP32, as
+// k_update_gram_rows<true>): the input Gram matrix Gin = h2 + ccols p (p x p, stored after
+// h2) is then that of W before the correction, and the factor is taken of Gin - h2^T h2 (the
+// Gram matrix after it when V is orthonormal, up to O(eps_32) terms that only the FP32
+// factorisation sees).  Every kind writes the Gram matrix of its result to G (last CTA).
+// KIND 2: the deviation passes.
 template <int KIND>
 __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int64_t rpb,
                                                       double* G, double* __restrict__ part, unsigned* ctr,
                                                       int mode, double* R, double* Rinv, const double* Rtot_in,
                                                       double* Rtot_out, double* H, int ldH, int hrow, int hcol,
-                                                      double* normsq_out, int* flags, double* out_, int64_t ldo_) {
+                                                      double* normsq_out, int* flags, double* out_, int64_t ldo_,
+                                                      const double* __restrict__ Vc, int64_t ldvc, int ccols,
+                                                      const double* __restrict__ h2) {
+    constexpr bool K1 = KIND == 1 || KIND == 3;
     int* extra = flags + 2;
     if (mode == 2 && *extra == 0) return;
+    extern __shared__ float h2f[];          // KIND 3: h2 as FP32, ccols x RP (zero-padded columns)
     __shared__ CholF cf;
     __shared__ double G0[RP * RP];
     __shared__ double hn2[RP];
@@ -345,7 +356,21 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     __shared__ double red[NTR / 32][RG];
     __shared__ double buf[NTR / 32][32 * RP];
     const int pp = p * p;
-    for (int o = threadIdx.x; o < pp; o += blockDim.x) G0[o] = G[o];
+    if (KIND == 3) {
+        for (int e = threadIdx.x; e < ccols * RP; e += blockDim.x) {
+            const int a = e / RP, c = e - a * RP;
+            h2f[e] = (c < p) ? (float)h2[a * p + c] : 0.f;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < pp; o += blockDim.x) {
+            const int i = o / p, k = o - i * p;
+            float s2 = 0.f;
+            for (int a = 0; a < ccols; ++a) s2 = fmaf(h2f[a * RP + i], h2f[a * RP + k], s2);
+            G0[o] = h2[ccols * p + o] - (double)s2;     // the Gram sums follow h2 in memory
+        }
+    } else {
+        for (int o = threadIdx.x; o < pp; o += blockDim.x) G0[o] = G[o];
+    }
     const bool last = (mode == 1 && *extra == 0) || mode == 2;
     const bool lead = blockIdx.x == 0;
     if (H && last && lead) {
@@ -371,7 +396,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         double tr = 0.0, dmax = 0.0;
-        if (KIND == 1) {
+        if (K1) {
             for (int c = 0; c < p; ++c) {
                 tr += G0[c * p + c];
                 dmax = fmax(dmax, G0[c * p + c]);
@@ -385,14 +410,14 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
             chol32_dev(cf, G0, p);
         }
         if (lead) {
-            if (KIND == 1 && normsq_out && lane == 0) *normsq_out = tr;
-            if (KIND == 1 && lane == 0) *extra = cf.ill;
+            if (K1 && normsq_out && lane == 0) *normsq_out = tr;
+            if (K1 && lane == 0) *extra = cf.ill;
             if (lane < p) {
                 const int c = lane;
                 for (int r = 0; r < p; ++r) {
                     const int o = r * p + c;
                     double rt;
-                    if (KIND == 1) {
+                    if (K1) {
                         rt = (r <= c) ? ldexp((double)cf.U[o], kexp / 2) : 0.0;
                         R[o] = rt;
                     } else {
@@ -424,7 +449,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         }
     }
     __syncthreads();
-    if (KIND == 1) {
+    if (K1) {
         // kexp as computed by warp 0 (every thread recomputes it from the same G0)
         double dmax = 0.0;
         for (int c = 0; c < p; ++c) dmax = fmax(dmax, G0[c * p + c]);
@@ -437,11 +462,11 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     // KIND 2 with max|U| above 1e-4 (a pass after the shifted one): the FP32 inverse I + Y
     // would leave an eps_32 |U| mismatch with the recorded R, so the solve is a forward
     // substitution with R = I + U in FP64, as in pass 1
-    const bool subst = KIND == 1 || cf.umax > 1e-4f;
+    const bool subst = K1 || cf.umax > 1e-4f;
     for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
         const int a = e / RP, c = e % RP;
         const bool in = a < p && c < p && a <= c;
-        if (KIND == 1) Rd[e] = in ? ldexp((double)cf.U[a * p + c], kexp / 2) : 0.0;
+        if (K1) Rd[e] = in ? ldexp((double)cf.U[a * p + c], kexp / 2) : 0.0;
         else {
             Yf[e] = in ? cf.Y[a * p + c] : 0.f;
             Rd[e] = in ? (double)cf.U[a * p + c] + (a == c ? 1.0 : 0.0) : 0.0;
@@ -451,9 +476,9 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     if (subst && threadIdx.x < RP) {
         const double d = Rd[threadIdx.x * RP + threadIdx.x];
         rcp[threadIdx.x] = (d != 0.0) ? 1.0 / d : 0.0;
-        if (KIND == 1) split_df(rcp[threadIdx.x], rch[threadIdx.x], rcl[threadIdx.x]);
+        if (K1) split_df(rcp[threadIdx.x], rch[threadIdx.x], rcl[threadIdx.x]);
     }
-    if (KIND == 1)
+    if (K1)
         for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) split_df(Rd[e], Rh[e], Rl[e]);
     __syncthreads();
     double* out;
@@ -477,8 +502,21 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         double w[RP], y[RP];
 #pragma unroll
         for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
+        if (KIND == 3 && ok) {
+            float corr[RP];
+#pragma unroll
+            for (int c = 0; c < RP; ++c) corr[c] = 0.f;
+#pragma unroll 8
+            for (int a = 0; a < ccols; ++a) {
+                const float v = (float)Vc[(int64_t)a * ldvc + r];
+#pragma unroll
+                for (int c = 0; c < RP; ++c) corr[c] = fmaf(v, h2f[a * RP + c], corr[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < RP; ++c) w[c] -= (double)corr[c];
+        }
         float yh[RP], yl[RP];
-        if (KIND == 1) {
+        if (K1) {
             // forward substitution y R = w in double-float: R's entries are exact floats
             // (pairs Rh + Rl for safety), 1 / R_cc as a pair, y kept as pairs
 #pragma unroll
@@ -530,7 +568,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         for (int c = 0; c < RP; ++c)
             if (ok && c < p) out[(int64_t)c * ldo + r] = y[c];
         if (gram) {
-            if (KIND == 1) {
+            if (K1) {
 #pragma unroll
                 for (int c = 0; c < RP; ++c)
                     if (!ok || c >= p) { yh[c] = 0.f; yl[c] = 0.f; }
@@ -541,7 +579,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         }
     }
     if (gram) {
-        if (KIND == 1) {
+        if (K1) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) acc[q] = (double)gah[q] + (double)gal[q];
         }
@@ -706,7 +744,9 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
 // products; the projection of the first pass).
 // k_cgs_rows<true>:  W <- W - V h in double-float arithmetic (as k_update_df: each product
 // v h = vh hh + (err(vh hh) + vl hh + vh hl), the large parts accumulated with TwoSum), then
-// the FP32 partials of V^T W for the second pass.
+// the FP32 partials of V^T W for the second pass; with ng = p also the FP32 Gram partial
+// W^T W (outputs cols p .. (cols + p) p, full p x p), which feeds the FP32 factorisation of
+// the first Cholesky-QR pass.
 // Per chunk the FP32 copy of V (cols x RB) and of W (RB x RP) are staged in shared memory
 // and the cols x p projection outputs are spread over the threads (output o = tid + k NTR);
 // each chunk's FP32 sum is added to a float-pair accumulator, so the CTA's partial carries
@@ -716,8 +756,8 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
 constexpr int RB = NTR / 2;
 constexpr int WS = RP + 1;                  // row stride of the FP32 copy of W
 
-__host__ __device__ constexpr size_t cgs_rows_smem(int cols, bool upd) {
-    return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS + (size_t)cols * (RB + 1));
+__host__ __device__ constexpr size_t cgs_rows_smem(int cols, bool upd, int ng) {
+    return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS + (size_t)(cols + ng) * (RB + 1));
 }
 
 // one double-float multiply-add: (sh, sl) += (vh + vl)(h1 + h2)
@@ -755,12 +795,12 @@ template <bool UPD, int K>
 __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, int64_t ldv, int cols,
                                                  double* __restrict__ W, int64_t ldw, int p, int64_t n,
                                                  int64_t rpb, const double* __restrict__ h,
-                                                 double* __restrict__ part) {
+                                                 double* __restrict__ part, int ng) {
     extern __shared__ __align__(16) float smf[];
     float* hh = smf;                                   // UPD: cols x RP (zero-padded columns)
     float* hl = hh + (UPD ? cols * RP : 0);
     float* Wf = hl + (UPD ? cols * RP : 0);            // RB x WS
-    float* Vs = Wf + RB * WS;                          // cols x (RB + 1)
+    float* Vs = Wf + RB * WS;                          // (cols + ng) x (RB + 1): V, then W
     if (UPD) {
         for (int e = threadIdx.x; e < cols * RP; e += NTR) {
             const int a = e / RP, c = e - a * RP;
@@ -770,7 +810,7 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             hl[e] = y;
         }
     }
-    const int nout = cols * p;
+    const int nout = (cols + (UPD ? ng : 0)) * p;
     float ah[K], al[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -848,6 +888,7 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
                         wf = (float)w;
                     }
                     Wf[rr * WS + c] = wf;
+                    if (c < ng) Vs[(cols + c) * (RB + 1) + rr] = wf;
                 }
             }
         } else {
