@@ -1040,7 +1040,8 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         return EXPM_NO_MEMORY;
     }
     cudaStream_t s = P->stream;
-    bool cuda_ok = krylov_set_smem_limits() == cudaSuccess && poles_set_smem_limits() == cudaSuccess;
+    bool cuda_ok = krylov_set_smem_limits() == cudaSuccess && poles_set_smem_limits() == cudaSuccess &&
+                   operator_set_smem_limits() == cudaSuccess;
     if (!toeplitz) {
         const int64_t nmodes = P->nmodes;
         for (int d = 1; d < P->ndim && cuda_ok; ++d)

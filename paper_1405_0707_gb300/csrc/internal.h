@@ -298,6 +298,7 @@ cudaError_t launch_cg_step(double* x, double* r, const double* p, const double* 
                            cudaStream_t s);
 cudaError_t launch_cg_dir(double* p, const double* r, double beta, int64_t n, cudaStream_t s);
 cudaError_t launch_unit(double* v, int64_t n, cudaStream_t s);
+cudaError_t operator_set_smem_limits();
 cudaError_t krylov_set_smem_limits();
 cudaError_t poles_set_smem_limits();
 size_t poles_smem_bytes(int mp, int p);

@@ -354,6 +354,101 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
         }
 }
 
+// The FP32 line solves with the lines staged in shared memory: a CTA takes TK consecutive
+// modes of one column (16 x L values of f, thm and thc, loaded once with coalesced reads),
+// runs the same segmented affine scans as tridiag_seg from shared memory and writes y back.
+// Each mode's line is stored contiguously with one pad element per segment, so the SEG lanes
+// of a line and the four lines of a warp read distinct banks (row stride L + SEG).
+constexpr int TK = 16;
+constexpr size_t kTridiagTileSmemMax = 110 * 1024;
+__host__ __device__ constexpr size_t tridiag_tile_smem(int L) { return sizeof(float) * 3 * (size_t)TK * (L + TSEG); }
+
+__global__ void __launch_bounds__(TK * TSEG) k_tridiag_tile32(float* y_io, int64_t ld, int L, int64_t nmodes,
+                                                             float l_sub, const float* __restrict__ thm,
+                                                             const float* __restrict__ thc, float inv_t) {
+    extern __shared__ float smt[];
+    const int Lp = L + TSEG;
+    const int seglen = (L + TSEG - 1) / TSEG;
+    float* F = smt;                  // TK x Lp: f, then y in place
+    float* Mt = F + TK * Lp;
+    float* Ct = Mt + TK * Lp;
+    const int c = blockIdx.y;
+    const int64_t k0 = (int64_t)blockIdx.x * TK;
+    float* y = y_io + (int64_t)c * ld;
+    constexpr int NT = TK * TSEG, UB = 8;   // UB elements (3 UB loads) in flight per thread
+    const int tot = L * TK;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += UB * NT) {
+        float fv[UB], mv[UB], cv[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int e = e0 + u * NT, x = e / TK, kk = e - x * TK;
+            const int64_t k = k0 + kk;
+            const bool ok = e < tot && k < nmodes;
+            fv[u] = ok ? y[(int64_t)x * nmodes + k] : 0.f;
+            mv[u] = ok ? thm[(int64_t)x * nmodes + k] : 0.f;
+            cv[u] = ok ? thc[(int64_t)x * nmodes + k] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int e = e0 + u * NT, x = e / TK, kk = e - x * TK;
+            if (e < tot) {
+                const int si = kk * Lp + x + x / seglen;
+                F[si] = fv[u];
+                Mt[si] = mv[u];
+                Ct[si] = cv[u];
+            }
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int seg = lane % TSEG, kk = warp * (32 / TSEG) + lane / TSEG;
+    const int x0 = min(L, seg * seglen), x1 = min(L, x0 + seglen);
+    float* f = F + kk * Lp + seg;          // element x of the line at f[x] (x in this segment)
+    const float* m = Mt + kk * Lp + seg;
+    const float* cc = Ct + kk * Lp + seg;
+    const unsigned full = 0xffffffffu;
+    float A = 1.f, B = 0.f;
+    for (int x = x0; x < x1; ++x) {
+        const float a = -l_sub * m[x];
+        B = a * B + f[x] * inv_t * m[x];
+        A = a * A;
+    }
+    float yin = 0.f;
+    for (int sgi = 1; sgi < TSEG; ++sgi) {
+        const float v = __shfl_up_sync(full, A * yin + B, 1);
+        if (seg == sgi) yin = v;
+    }
+    float prev = yin;
+    for (int x = x0; x < x1; ++x) {
+        prev = (f[x] * inv_t - l_sub * prev) * m[x];
+        f[x] = prev;
+    }
+    A = 1.f;
+    B = 0.f;
+    for (int x = x1 - 1; x >= x0; --x) {
+        const float cv = (x < L - 1) ? cc[x] : 0.f;
+        B = f[x] - cv * B;
+        A = -cv * A;
+    }
+    float zin = 0.f;
+    for (int sgi = TSEG - 2; sgi >= 0; --sgi) {
+        const float v = __shfl_down_sync(full, A * zin + B, 1);
+        if (seg == sgi) zin = v;
+    }
+    float next = zin;
+    for (int x = x1 - 1; x >= x0; --x) {
+        const float cv = (x < L - 1) ? cc[x] : 0.f;
+        next = f[x] - cv * next;
+        f[x] = next;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < L * TK; e += blockDim.x) {
+        const int x = e / TK, kk2 = e - x * TK;
+        const int64_t k = k0 + kk2;
+        if (k < nmodes) y[(int64_t)x * nmodes + k] = F[kk2 * Lp + x + x / seglen];
+    }
+}
+
 __global__ void k_tridiag_lines32(float* y_io, int64_t ld, int p, int L, int64_t nmodes,
                                   float l_sub, const float* __restrict__ thm,
                                   const float* __restrict__ thc, float inv_t) {
@@ -494,10 +589,21 @@ cudaError_t launch_gemm32(const GemmArgsMixed& g, cudaStream_t s) {
 cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t nmodes, float l_sub,
                                    const float* th_m, const float* th_c, float inv_t,
                                    cudaStream_t s) {
+    const size_t shm = tridiag_tile_smem(L);
+    if (shm <= kTridiagTileSmemMax) {
+        const dim3 grid((unsigned)((nmodes + TK - 1) / TK), (unsigned)p);
+        k_tridiag_tile32<<<grid, TK * TSEG, shm, s>>>(y, ld, L, nmodes, l_sub, th_m, th_c, inv_t);
+        return cudaGetLastError();
+    }
     const int64_t lines = nmodes * p, per_block = 128 / TSEG;
     k_tridiag_lines32<<<(unsigned)((lines + per_block - 1) / per_block), 128, 0, s>>>(y, ld, p, L, nmodes, l_sub,
                                                                                    th_m, th_c, inv_t);
     return cudaGetLastError();
+}
+
+cudaError_t operator_set_smem_limits() {
+    return cudaFuncSetAttribute(k_tridiag_tile32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kTridiagTileSmemMax);
 }
 
 int true_resid_blocks(int64_t n) { return (int)((n + 255) / 256); }

@@ -502,18 +502,18 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         double w[RP], y[RP];
 #pragma unroll
         for (int c = 0; c < RP; ++c) w[c] = (ok && c < p) ? W[(int64_t)c * ldw + r] : 0.0;
-        if (KIND == 3 && ok) {
-            float corr[RP];
+        // KIND 3: the FP32 correction V h2, subtracted inside the double-float substitution
+        // below (no FP64 add)
+        float corr[RP];
 #pragma unroll
-            for (int c = 0; c < RP; ++c) corr[c] = 0.f;
+        for (int c = 0; c < RP; ++c) corr[c] = 0.f;
+        if (KIND == 3 && ok) {
 #pragma unroll 8
             for (int a = 0; a < ccols; ++a) {
                 const float v = (float)Vc[(int64_t)a * ldvc + r];
 #pragma unroll
                 for (int c = 0; c < RP; ++c) corr[c] = fmaf(v, h2f[a * RP + c], corr[c]);
             }
-#pragma unroll
-            for (int c = 0; c < RP; ++c) w[c] -= (double)corr[c];
         }
         float yh[RP], yl[RP];
         if (K1) {
@@ -523,6 +523,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
             for (int c = 0; c < RP; ++c) {
                 float sh, sl;
                 split_df(w[c], sh, sl);
+                if (KIND == 3) df_add(sh, sl, -corr[c]);
 #pragma unroll
                 for (int a = 0; a < c; ++a) {
                     const float r1 = Rh[a * RP + c], r2 = Rl[a * RP + c];
