@@ -37,7 +37,7 @@ __device__ inline void cmsub(cplx& x, cplx a, cplx b) {
 }
 
 constexpr size_t kSmemLimit = 200 * 1024;
-constexpr int kPoleThreads = 128;   // four warps per pole
+constexpr int kPoleThreads = 512;   // sixteen warps per pole: four per scheduler to cover FP64 latency
 
 // 1 / d with one scaling division and one reciprocal
 __device__ inline cplx crecip(cplx d) {
@@ -48,7 +48,7 @@ __device__ inline cplx crecip(cplx d) {
     return {dr * k, -di * k};
 }
 
-// One CTA (four warps) per pole.  Shared memory holds M (mp x mp complex, row-major), the
+// One CTA (sixteen warps) per pole.  Shared memory holds M (mp x mp complex, row-major), the
 // right-hand sides / solution X (mp x p complex), the inverses of U's diagonal blocks
 // (mp x p complex) and, when it fits, the real H~ ((mp+p) x mp), staged once with coalesced
 // loads.  Outputs: the restart factor S_i, ||S_i||_F and Y_i = 2 Re(omega_i Z_i) (mp x p
