@@ -230,98 +230,150 @@ struct CholF {
     int ill, bad;
 };
 
+// The p x p factorisations run on warp 0 with lane l holding column l of the working matrix
+// and of the factor in registers; the pivot row's entries reach the other lanes by shuffles
+// (no shared-memory round trips on the serial path).  Every lane of warp 0 must call them.
+
 // pass 1: FP32 Cholesky of G 2^-k (upper triangle) -> U; warp 0
 __device__ inline void chol32_full(CholF& cf, const double* G0, int p, int k, double tr_s) {
     const int lane = threadIdx.x;
-    const int pp = p * p;
-    if (lane == 0) { cf.ill = 0; cf.bad = 0; }
-    __syncwarp();
+    const unsigned full = 0xffffffffu;
+    const bool act = lane < p;
+    float u[RP];                      // u[a] = U[a][lane]
+    int ill = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         const double shift = attempt ? 11.0 * p * (p + 1) * 0x1p-24 * tr_s : 0.0;
-        for (int o = lane; o < pp; o += 32) {
-            cf.G[o] = (float)(ldexp(G0[o], -k) + ((o / p == o % p) ? shift : 0.0));
-            cf.U[o] = 0.f;
+        float g[RP];                  // g[a] = G[a][lane], updated in place
+        float dg = 0.f;
+#pragma unroll
+        for (int a = 0; a < RP; ++a) {
+            g[a] = (act && a < p) ? (float)(ldexp(G0[a * p + lane], -k) + (a == lane ? shift : 0.0)) : 0.f;
+            u[a] = 0.f;
+            if (a == lane) dg = g[a];
         }
-        __syncwarp();
-        float dmax = 0.f;
-        for (int c = 0; c < p; ++c) dmax = fmaxf(dmax, cf.G[c * p + c]);
-        for (int j = 0; j < p; ++j) {
-            if (lane == 0) {
-                float d = cf.G[j * p + j];
+        float dmax = act ? dg : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(full, dmax, o));
+        int ill_l = 0;
+#pragma unroll
+        for (int j = 0; j < RP; ++j) {
+            if (j >= p) break;
+            float inv = 0.f;
+            if (lane == j) {
+                float d = g[j];
                 if (G0[j * p + j] == 0.0) {
-                    cf.U[j * p + j] = 0.f;
-                    cf.rd[j] = 0.f;
+                    u[j] = 0.f;
                 } else {
-                    if (!(d > 0.f) || !isfinite(d) || (attempt == 0 && d < 1e-6f * dmax)) cf.ill = 1;
+                    if (!(d > 0.f) || !isfinite(d) || (attempt == 0 && d < 1e-6f * dmax)) ill_l = 1;
                     if (!(d > 0.f) || !isfinite(d)) d = 1.f;
                     const float rj = sqrtf(d);
-                    cf.U[j * p + j] = rj;
-                    cf.rd[j] = 1.f / rj;
+                    u[j] = rj;
+                    inv = 1.f / rj;
                 }
             }
-            __syncwarp();
-            const float inv = cf.rd[j];
-            if (lane > j && lane < p) cf.U[j * p + lane] = cf.G[j * p + lane] * inv;
-            __syncwarp();
-            if (lane > j && lane < p) {
-                const float rb = cf.U[j * p + lane];
-                for (int a = j + 1; a <= lane; ++a) cf.G[a * p + lane] -= cf.U[j * p + a] * rb;
+            inv = __shfl_sync(full, inv, j);
+            if (act && lane > j) u[j] = g[j] * inv;
+            // trailing update G[a][l] -= U[j][a] U[j][l] for j < a <= l
+#pragma unroll
+            for (int a = j + 1; a < RP; ++a) {
+                const float uja = __shfl_sync(full, u[j], a);
+                if (act && a < p && a <= lane) g[a] -= uja * u[j];
             }
-            __syncwarp();
         }
-        if (attempt == 1 || !cf.ill) break;
-        __syncwarp();
+        if (__any_sync(full, ill_l)) ill = 1;     // sticky: a shifted pass 1 asks for pass 3
+        if (attempt == 1 || !ill) break;
     }
+    if (act)
+#pragma unroll
+        for (int a = 0; a < RP; ++a)
+            if (a < p) cf.U[a * p + lane] = u[a];
+    if (lane == 0) {
+        cf.ill = ill;
+        cf.bad = 0;
+    }
+    __syncwarp();
 }
 
 // passes 2/3: deviation Cholesky of G = I + E -> U (R = I + U), Y (R^{-1} = I + Y); warp 0
 __device__ inline void chol32_dev(CholF& cf, const double* G0, int p) {
     const int lane = threadIdx.x;
-    const int pp = p * p;
-    if (lane == 0) { cf.ill = 0; cf.bad = 0; }
-    for (int o = lane; o < pp; o += 32) {
-        const bool dg = o / p == o % p;
-        cf.G[o] = (float)(G0[o] - (dg ? 1.0 : 0.0));   // E (upper triangle)
-        cf.U[o] = 0.f;
-        cf.Y[o] = 0.f;
+    const unsigned full = 0xffffffffu;
+    const bool act = lane < p;
+    float e[RP], u[RP], y[RP];        // column `lane` of E, U and Y
+#pragma unroll
+    for (int a = 0; a < RP; ++a) {
+        e[a] = (act && a < p) ? (float)(G0[a * p + lane] - (a == lane ? 1.0 : 0.0)) : 0.f;
+        u[a] = 0.f;
+        y[a] = 0.f;
     }
-    __syncwarp();
-    for (int j = 0; j < p; ++j) {
-        if (lane == 0) {
+    int bad = 0;
+    float rdl = 0.f;                  // lane j: 1 / (1 + U_jj)
+#pragma unroll
+    for (int j = 0; j < RP; ++j) {
+        if (j >= p) break;
+        // U[k][j] for k < j from lane j
+        float ucol[RP];
+#pragma unroll
+        for (int k2 = 0; k2 < RP; ++k2) ucol[k2] = (k2 < j) ? __shfl_sync(full, u[k2], j) : 0.f;
+        if (lane == j) {
             if (G0[j * p + j] == 0.0) {
-                cf.U[j * p + j] = -1.f;                  // R_jj = 0: a zero column stays zero
-                cf.rd[j] = 0.f;
+                u[j] = -1.f;                          // R_jj = 0: a zero column stays zero
+                rdl = 0.f;
             } else {
-                float x = cf.G[j * p + j];
-                for (int k = 0; k < j; ++k) x -= cf.U[k * p + j] * cf.U[k * p + j];
-                if (!(x > -0.75f) || !isfinite(x)) cf.bad = 1;   // not close to orthonormal
+                float x = e[j];
+#pragma unroll
+                for (int k2 = 0; k2 < RP; ++k2)
+                    if (k2 < j) x -= u[k2] * u[k2];
+                if (!(x > -0.75f) || !isfinite(x)) bad = 1;   // not close to orthonormal
                 if (!(x > -0.75f) || !isfinite(x)) x = 0.f;
                 const float ujj = x / (1.f + sqrtf(1.f + x));
-                cf.U[j * p + j] = ujj;
-                cf.rd[j] = 1.f / (1.f + ujj);
+                u[j] = ujj;
+                rdl = 1.f / (1.f + ujj);
             }
         }
-        __syncwarp();
-        if (lane > j && lane < p) {
-            float s = cf.G[j * p + lane];
-            for (int k = 0; k < j; ++k) s -= cf.U[k * p + j] * cf.U[k * p + lane];
-            cf.U[j * p + lane] = s * cf.rd[j];
+        const float rdj = __shfl_sync(full, rdl, j);
+        if (act && lane > j) {
+            float s2 = e[j];
+#pragma unroll
+            for (int k2 = 0; k2 < RP; ++k2)
+                if (k2 < j) s2 -= ucol[k2] * u[k2];
+            u[j] = s2 * rdj;
         }
-        __syncwarp();
     }
+    float um = 0.f;
+    if (act)
+#pragma unroll
+        for (int a = 0; a < RP; ++a)
+            if (a < p) um = fmaxf(um, fabsf(u[a]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(full, um, o));
+    // (I + U) Y = -U, column `lane` by back substitution: row r of U comes from lanes k > r
+#pragma unroll
+    for (int r = RP - 1; r >= 0; --r) {
+        const float rdr = __shfl_sync(full, rdl, r);
+        float urow[RP];
+#pragma unroll
+        for (int k2 = 0; k2 < RP; ++k2) urow[k2] = (k2 > r) ? __shfl_sync(full, u[r], k2) : 0.f;
+        if (act && r < p && r <= lane) {
+            float s2 = -u[r];
+#pragma unroll
+            for (int k2 = 0; k2 < RP; ++k2)
+                if (k2 > r && k2 <= lane) s2 -= urow[k2] * y[k2];
+            y[r] = (r == lane && rdr == 0.f) ? -1.f : s2 * rdr;
+        }
+    }
+    if (act)
+#pragma unroll
+        for (int a = 0; a < RP; ++a)
+            if (a < p) {
+                cf.U[a * p + lane] = u[a];
+                cf.Y[a * p + lane] = y[a];
+            }
+    bad = __any_sync(full, bad) ? 1 : 0;
     if (lane == 0) {
-        float um = 0.f;
-        for (int o = 0; o < pp; ++o) um = fmaxf(um, fabsf(cf.U[o]));
+        cf.ill = 0;
+        cf.bad = bad;
         cf.umax = um;
-    }
-    // (I + U) Y = -U, column `lane` by back substitution
-    if (lane < p) {
-        const int c = lane;
-        for (int r = c; r >= 0; --r) {
-            float s = -cf.U[r * p + c];
-            for (int k = r + 1; k <= c; ++k) s -= cf.U[r * p + k] * cf.Y[k * p + c];
-            cf.Y[r * p + c] = (r == c && cf.rd[r] == 0.f) ? -1.f : s * cf.rd[r];
-        }
     }
     __syncwarp();
 }
