@@ -410,7 +410,9 @@ expm_status issue_cycle(expm_plan* P, double t, int p, int alg) {
         LAUNCH(EXPM_STAGE_OTHER, launch_update_z(P->V, ld, mp + p, 2 * P->npoles * p, n, P->Ccert, P->Xcert, ld, 0,
                                                  s, P->nblk));
     }
-    LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk));
+    // mixed path: the product V Wc in double-float on the FP32 pipe (FP64 accumulation into Z)
+    LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk,
+                                              P->opts.precision == EXPM_PREC_MIXED ? 1 : 0));
     CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
     return EXPM_OK;
 }

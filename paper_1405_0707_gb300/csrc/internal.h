@@ -278,7 +278,7 @@ cudaError_t launch_combine2(const double* H, int ldH, int mp, int p, int npoles,
                             const double* Y_slots, double* Wc, int alg, cudaStream_t s);
 cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
                             const double* Wc, double* Z, int64_t ldz, int restart_copy,
-                            cudaStream_t s, int nblk);
+                            cudaStream_t s, int nblk, int df = 0);
 int consistent_blocks(int64_t n, int requested);
 // FFT and Toeplitz pieces (k_fft.cu)
 FftPlan fft_geometry(int64_t nmin);

@@ -914,19 +914,19 @@ cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* 
 
 cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
                             const double* Wc, double* Z, int64_t ldz, int restart_copy,
-                            cudaStream_t s, int nblk) {
+                            cudaStream_t s, int nblk, int df) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
-    if (p <= rows8::RP) {
-        rows8::k_update_z_rows<<<g, rows8::NTR, sizeof(double) * (size_t)cols * rows8::RP, s>>>(
-            V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy);
-        return cudaGetLastError();
+#define EXPM_UPDZ(NS)                                                                                          \
+    {                                                                                                         \
+        const size_t shr = sizeof(double) * (size_t)cols * NS::RP;                                            \
+        if (df) NS::k_update_z_rows<true><<<g, NS::NTR, shr, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy); \
+        else NS::k_update_z_rows<false><<<g, NS::NTR, shr, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy); \
+        return cudaGetLastError();                                                                            \
     }
-    if (p <= rows16::RP) {
-        rows16::k_update_z_rows<<<g, rows16::NTR, sizeof(double) * (size_t)cols * rows16::RP, s>>>(
-            V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy);
-        return cudaGetLastError();
-    }
+    if (p <= rows8::RP) EXPM_UPDZ(rows8)
+    if (p <= rows16::RP) EXPM_UPDZ(rows16)
+#undef EXPM_UPDZ
     const size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1));
     k_update_z<<<g, NT, shm, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy);
     return cudaGetLastError();
@@ -994,10 +994,12 @@ cudaError_t krylov_set_smem_limits() {
     EXPM_SET(k_update_z);
     EXPM_SET(rows8::k_update_gram_rows<false>);
     EXPM_SET(rows8::k_update_gram_rows<true>);
-    EXPM_SET(rows8::k_update_z_rows);
+    EXPM_SET(rows8::k_update_z_rows<false>);
+    EXPM_SET(rows8::k_update_z_rows<true>);
     EXPM_SET(rows16::k_update_gram_rows<false>);
     EXPM_SET(rows16::k_update_gram_rows<true>);
-    EXPM_SET(rows16::k_update_z_rows);
+    EXPM_SET(rows16::k_update_z_rows<false>);
+    EXPM_SET(rows16::k_update_z_rows<true>);
 #define EXPM_SET_CGS(NS)                                                                                    \
     EXPM_SET((NS::k_cgs_rows<true, 1>)); EXPM_SET((NS::k_cgs_rows<true, 3>)); EXPM_SET((NS::k_cgs_rows<true, 6>)); \
     EXPM_SET((NS::k_cgs_rows<true, 12>)); EXPM_SET((NS::k_cgs_rows<true, 20>));                               \

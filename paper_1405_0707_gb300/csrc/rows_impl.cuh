@@ -8,6 +8,16 @@
 // RG = RP (RP + 1) / 2 (Gram entries), NQ = ceil(RG / 32) (entries per lane) and NTR
 // (threads per CTA).
 
+// one double-float multiply-add: (sh, sl) += (vh + vl)(h1 + h2)
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float vh, float vl, float h1, float h2) {
+    const float pr = vh * h1;
+    float t = fmaf(vh, h1, -pr);
+    t = fmaf(vl, h1, t);
+    t = fmaf(vh, h2, t);
+    df_add(sh, sl, pr);
+    sl += t;
+}
+
 __device__ inline double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -758,27 +768,73 @@ __global__ void __launch_bounds__(NTR) k_update_gram_rows(const double* __restri
     }
 }
 
-// Row-per-thread, p <= 8: Z[r, :] += V[r, 0:cols] Wc; restart copy V[r, 0:p] <- V[r, cols-p:cols].
+// Row-per-thread: Z[r, :] += V[r, 0:cols] Wc; restart copy V[r, 0:p] <- V[r, cols-p:cols].
+// DF = false: FP64 products.  DF = true (mixed path): the products in double-float arithmetic
+// on the FP32 pipe (V and Wc split into float pairs, TwoSum accumulation as in the first CGS
+// update, relative error ~ cols 2^-48 of |V Wc|), added to the FP64 Z.
+template <bool DF>
 __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, int64_t ldv, int cols, int p,
                                                       int64_t n, int64_t rpb,
                                                       const double* __restrict__ Wc,
                                                       double* __restrict__ Z, int64_t ldz,
                                                       int restart_copy) {
-    extern __shared__ double ws[];           // cols x RP
+    extern __shared__ __align__(16) double ws[];   // cols x RP (FP64), or 2 cols x RP floats (DF)
+    float* wh = reinterpret_cast<float*>(ws);
+    float* wl = wh + cols * RP;
     for (int e = threadIdx.x; e < cols * RP; e += blockDim.x) {
         const int a = e / RP, c = e % RP;
-        ws[e] = (c < p) ? Wc[a * p + c] : 0.0;
+        const double w = (c < p) ? Wc[a * p + c] : 0.0;
+        if (DF) split_df(w, wh[e], wl[e]);
+        else ws[e] = w;
     }
     __syncthreads();
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
     for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
         double z[RP];
+        if (DF) {
+            float sh[RP], sl[RP];
 #pragma unroll
-        for (int c = 0; c < RP; ++c) z[c] = 0.0;
-        for (int a = 0; a < cols; ++a) {
-            const double v = V[(int64_t)a * ldv + r];
+            for (int c = 0; c < RP; ++c) {
+                sh[c] = 0.f;
+                sl[c] = 0.f;
+            }
+            int a = 0;
+            for (; a + 4 <= cols; a += 4) {
+                double v[4];
 #pragma unroll
-            for (int c = 0; c < RP; ++c) z[c] = fma(v, ws[a * RP + c], z[c]);
+                for (int u = 0; u < 4; ++u) v[u] = V[(int64_t)(a + u) * ldv + r];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float vh, vl;
+                    split_df(v[u], vh, vl);
+                    const float4* x4 = reinterpret_cast<const float4*>(wh + (a + u) * RP);
+                    const float4* y4 = reinterpret_cast<const float4*>(wl + (a + u) * RP);
+#pragma unroll
+                    for (int q = 0; q < RP / 4; ++q) {
+                        const float4 x = x4[q], y = y4[q];
+                        df_fma(sh[4 * q], sl[4 * q], vh, vl, x.x, y.x);
+                        df_fma(sh[4 * q + 1], sl[4 * q + 1], vh, vl, x.y, y.y);
+                        df_fma(sh[4 * q + 2], sl[4 * q + 2], vh, vl, x.z, y.z);
+                        df_fma(sh[4 * q + 3], sl[4 * q + 3], vh, vl, x.w, y.w);
+                    }
+                }
+            }
+            for (; a < cols; ++a) {
+                float vh, vl;
+                split_df(V[(int64_t)a * ldv + r], vh, vl);
+#pragma unroll
+                for (int c = 0; c < RP; ++c) df_fma(sh[c], sl[c], vh, vl, wh[a * RP + c], wl[a * RP + c]);
+            }
+#pragma unroll
+            for (int c = 0; c < RP; ++c) z[c] = (double)sh[c] + (double)sl[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < RP; ++c) z[c] = 0.0;
+            for (int a = 0; a < cols; ++a) {
+                const double v = V[(int64_t)a * ldv + r];
+#pragma unroll
+                for (int c = 0; c < RP; ++c) z[c] = fma(v, ws[a * RP + c], z[c]);
+            }
         }
 #pragma unroll
         for (int c = 0; c < RP; ++c)
@@ -811,16 +867,6 @@ constexpr int WS = RP + 1;                  // row stride of the FP32 copy of W
 
 __host__ __device__ constexpr size_t cgs_rows_smem(int cols, bool upd, int ng) {
     return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS + (size_t)(cols + ng) * (RB + 1));
-}
-
-// one double-float multiply-add: (sh, sl) += (vh + vl)(h1 + h2)
-__device__ __forceinline__ void df_fma(float& sh, float& sl, float vh, float vl, float h1, float h2) {
-    const float pr = vh * h1;
-    float t = fmaf(vh, h1, -pr);
-    t = fmaf(vl, h1, t);
-    t = fmaf(vh, h2, t);
-    df_add(sh, sl, pr);
-    sl += t;
 }
 
 template <int K>
