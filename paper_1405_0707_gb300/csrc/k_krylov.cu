@@ -187,38 +187,39 @@ __global__ void __launch_bounds__(NT) k_proj(const double* __restrict__ V, int64
 }
 
 // Sum of the nblk partials of output o, split over `stripes` threads (stripe s takes
-// b = s, s + stripes, ...) with four independent accumulators; the caller adds the stripes
-// in a fixed order, so the result does not depend on scheduling.
+// b = s, s + stripes, ...) with eight independent accumulators, so eight loads are in flight
+// per thread; the caller adds the stripes in a fixed order, so the result does not depend on
+// scheduling.
 __device__ inline double stripe_sum(const double* __restrict__ part, int nblk, int nout, int o,
                                     int s, int stripes) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 0.0;
     int b = s;
-    for (; b + 3 * stripes < nblk; b += 4 * stripes) {
-        a0 += part[(int64_t)b * nout + o];
-        a1 += part[(int64_t)(b + stripes) * nout + o];
-        a2 += part[(int64_t)(b + 2 * stripes) * nout + o];
-        a3 += part[(int64_t)(b + 3 * stripes) * nout + o];
+    for (; b + 7 * stripes < nblk; b += 8 * stripes) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] += part[(int64_t)(b + k * stripes) * nout + o];
     }
-    for (; b < nblk; b += stripes) a0 += part[(int64_t)b * nout + o];
-    return (a0 + a1) + (a2 + a3);
+    for (; b < nblk; b += stripes) a[0] += part[(int64_t)b * nout + o];
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
-constexpr int RED_OUT = 8;        // outputs per reduction CTA
-constexpr int RED_STRIPES = 32;   // threads per output
+constexpr int RED_OUT = 4;        // outputs per reduction CTA
+constexpr int RED_STRIPES = 64;   // threads per output
 
-// h[o] = sum_b part[b][o]; H[row0 + a, col0 + c] (+)= h[a][c].  CTA = 8 outputs x 32 stripes;
-// the stripes are added in two fixed-order levels (4 groups of 8, then the 4 groups).
+// h[o] = sum_b part[b][o]; H[row0 + a, col0 + c] (+)= h[a][c].  CTA = 4 outputs x 64 stripes;
+// the stripes are added in two fixed-order levels (8 groups of 8, then the 8 groups).
 __global__ void __launch_bounds__(RED_OUT * RED_STRIPES)
 k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p, double* __restrict__ h,
            double* H, int ldH, int row0, int col0, int accumulate, int hcols) {
     __shared__ double red[RED_STRIPES][RED_OUT];
-    __shared__ double red2[4][RED_OUT];
+    __shared__ double red2[8][RED_OUT];
     const int nout = cols * p;
     const int ol = threadIdx.x % RED_OUT, st = threadIdx.x / RED_OUT;
     const int o = blockIdx.x * RED_OUT + ol;
     red[st][ol] = (o < nout) ? stripe_sum(part, nblk, nout, o, st, RED_STRIPES) : 0.0;
     __syncthreads();
-    if (st < 4) {
+    if (st < 8) {
         double g = 0.0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) g += red[st * 8 + k][ol];
@@ -226,7 +227,8 @@ k_reduce_h(const double* __restrict__ part, int nblk, int cols, int p, double* _
     }
     __syncthreads();
     if (st != 0 || o >= nout) return;
-    const double s = (red2[0][ol] + red2[1][ol]) + (red2[2][ol] + red2[3][ol]);
+    const double s = ((red2[0][ol] + red2[1][ol]) + (red2[2][ol] + red2[3][ol])) +
+                     ((red2[4][ol] + red2[5][ol]) + (red2[6][ol] + red2[7][ol]));
     h[o] = s;
     if (H && o < hcols * p) {
         const int a = o / p, c = o % p;
@@ -830,20 +832,24 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
     if (p > rows16::RP) return cudaErrorInvalidValue;
     if (Vc && (mode != 0 || !h2 || ccols < 1 || ccols > kMaxMP)) return cudaErrorInvalidValue;
     const int64_t rpb = rows_per_block(n, nblk);
-    const int g = blocks_for(n, nblk);
+    const int gr = blocks_for(n, nblk);
+    // an extra lead CTA (no rows) when the row CTAs are short; else CTA 0 leads
+    const int NTRp = p <= rows8::RP ? rows8::NTR : rows16::NTR;
+    const bool extra_lead = rpb <= 2 * NTRp;
+    const int g = gr + (extra_lead ? 1 : 0), lead_blk = extra_lead ? gr : 0;
 #define EXPM_QR_ROWS(NS)                                                                                          \
     if (mode == 0 && Vc)                                                                                        \
         NS::k_qr_mixed_rows<3><<<g, NS::NTR, sizeof(float) * (size_t)ccols * NS::RP, s>>>(                      \
             W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H, ldH, hrow, hcol, normsq_out,    \
-            flags, out, ldo, Vc, ldvc, ccols, h2);                                                               \
+            flags, out, ldo, Vc, ldvc, ccols, h2, lead_blk);                                                               \
     else if (mode == 0)                                                                                         \
         NS::k_qr_mixed_rows<1><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
                                                      Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo,  \
-                                                     nullptr, 0, 0, nullptr);                                    \
+                                                     nullptr, 0, 0, nullptr, lead_blk);                                    \
     else                                                                                                        \
         NS::k_qr_mixed_rows<2><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
                                                      Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo,  \
-                                                     nullptr, 0, 0, nullptr);
+                                                     nullptr, 0, 0, nullptr, lead_blk);
     if (p <= rows8::RP) { EXPM_QR_ROWS(rows8) }
     else { EXPM_QR_ROWS(rows16) }
 #undef EXPM_QR_ROWS

@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                                                       double* Rtot_out, double* H, int ldH, int hrow, int hcol,
                                                       double* normsq_out, int* flags, double* out_, int64_t ldo_,
                                                       const double* __restrict__ Vc, int64_t ldvc, int ccols,
-                                                      const double* __restrict__ h2) {
+                                                      const double* __restrict__ h2, int lead_blk) {
     constexpr bool K1 = KIND == 1 || KIND == 3;
     int* extra = flags + 2;
     if (mode == 2 && *extra == 0) return;
@@ -434,7 +434,10 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         for (int o = threadIdx.x; o < pp; o += blockDim.x) G0[o] = G[o];
     }
     const bool last = (mode == 1 && *extra == 0) || mode == 2;
-    const bool lead = blockIdx.x == 0;
+    // the lead CTA writes R, Rtot, the entries of H and the flags: CTA lead_blk, which the
+    // launcher places beyond the rows (an extra CTA that owns none, so the lead work runs
+    // concurrently with the row CTAs) when each CTA holds few rows
+    const bool lead = (int)blockIdx.x == lead_blk;
     if (H && last && lead) {
         const int stripes = NTR / p;
         const int c = threadIdx.x % p, st = threadIdx.x / p;
