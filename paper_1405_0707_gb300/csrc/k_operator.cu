@@ -240,32 +240,38 @@ __global__ void k_axis_setup(double* Qf, double* Qi, double* lam, int N, double 
 
 // W = t (A V) + beta Y, 3/5/7-point stencil with Dirichlet zeros outside the grid.
 // (beta = 0, Y = null: the operator apply; t -> -t, beta = 1: the residual Y - tA V.)
+// Stencil coefficients with t folded in (computed on the host): tc = t (c_x + c_y + c_z),
+// tl[d] = t l_d, tu[d] = t u_d; 5 (2-D) or 7 (3-D) FP64 multiply-adds per point.
+struct StencilT {
+    double tc, tl[3], tu[3];
+};
+
+// W = tA V (+ beta Y): one thread per grid point and column; grid index arithmetic in 32 bits
+// (n < 2^31 is checked by the launcher).
 __global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __restrict__ W,
-                           int64_t ldw, int ndim, int nx, int ny, int nz, Axis ax0, Axis ax1,
-                           Axis ax2, double t, const double* __restrict__ Y, int64_t ldy,
-                           double beta) {
-    const int64_t n = (int64_t)nx * ny * nz;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                           int64_t ldw, int ndim, int nx, int ny, int nz, StencilT k,
+                           const double* __restrict__ Y, int64_t ldy, double beta) {
+    const unsigned n = (unsigned)nx * (unsigned)ny * (unsigned)nz;
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (i >= n) return;
     const double* v = V + c * ldv;
-    const int ix = (int)(i % nx);
-    const int iy = (int)((i / nx) % ny);
-    const int iz = (int)(i / ((int64_t)nx * ny));
-    const double ui = v[i];
-    double acc = (ax0.c + (ndim > 1 ? ax1.c : 0.0) + (ndim > 2 ? ax2.c : 0.0)) * ui;
-    if (ix > 0) acc += ax0.l * v[i - 1];
-    if (ix < nx - 1) acc += ax0.u * v[i + 1];
+    const unsigned q = i / (unsigned)nx;
+    const unsigned ix = i - q * (unsigned)nx;
+    double acc = k.tc * v[i];
+    if (ix > 0) acc = fma(k.tl[0], v[i - 1], acc);
+    if (ix < (unsigned)nx - 1) acc = fma(k.tu[0], v[i + 1], acc);
     if (ndim > 1) {
-        if (iy > 0) acc += ax1.l * v[i - nx];
-        if (iy < ny - 1) acc += ax1.u * v[i + nx];
+        const unsigned iz = q / (unsigned)ny, iy = q - iz * (unsigned)ny;
+        if (iy > 0) acc = fma(k.tl[1], v[i - nx], acc);
+        if (iy < (unsigned)ny - 1) acc = fma(k.tu[1], v[i + nx], acc);
+        if (ndim > 2) {
+            const unsigned st = (unsigned)nx * (unsigned)ny;
+            if (iz > 0) acc = fma(k.tl[2], v[i - st], acc);
+            if (iz < (unsigned)nz - 1) acc = fma(k.tu[2], v[i + st], acc);
+        }
     }
-    if (ndim > 2) {
-        const int64_t s = (int64_t)nx * ny;
-        if (iz > 0) acc += ax2.l * v[i - s];
-        if (iz < nz - 1) acc += ax2.u * v[i + s];
-    }
-    W[c * ldw + i] = t * acc + (Y ? beta * Y[c * ldy + i] : 0.0);
+    W[c * ldw + i] = Y ? fma(beta, Y[c * ldy + i], acc) : acc;
 }
 
 // ---------------------------------------------------------------- mixed precision
@@ -562,9 +568,15 @@ cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw
                             int ndim, int nx, int ny, int nz, const Axis* ax, double t,
                             cudaStream_t s, const double* Y, int64_t ldy, double beta) {
     const int64_t n = (int64_t)nx * ny * nz;
+    if (n >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    StencilT k;
+    k.tc = t * (ax[0].c + (ndim > 1 ? ax[1].c : 0.0) + (ndim > 2 ? ax[2].c : 0.0));
+    for (int d = 0; d < 3; ++d) {
+        k.tl[d] = t * ax[d].l;
+        k.tu[d] = t * ax[d].u;
+    }
     dim3 grid((unsigned)((n + 255) / 256), p);
-    k_cd_apply<<<grid, 256, 0, s>>>(V, ldv, W, ldw, ndim, nx, ny, nz, ax[0], ax[1], ax[2], t, Y,
-                                    ldy, beta);
+    k_cd_apply<<<grid, 256, 0, s>>>(V, ldv, W, ldw, ndim, nx, ny, nz, k, Y, ldy, beta);
     return cudaGetLastError();
 }
 
