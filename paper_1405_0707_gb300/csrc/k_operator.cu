@@ -363,25 +363,26 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
 // The FP32 line solves with the lines staged in shared memory: a CTA takes TK consecutive
 // modes of one column (16 x L values of f, thm and thc, loaded once with coalesced reads),
 // runs the same segmented affine scans as tridiag_seg from shared memory and writes y back.
-// Each mode's line is stored contiguously with one pad element per segment, so the SEG lanes
-// of a line and the four lines of a warp read distinct banks (row stride L + SEG).
+// Each mode's line is stored contiguously with one pad element per segment, so the TSG lanes
+// of a line and the two lines of a warp read distinct banks (row stride L + TSG, L = 256).
 constexpr int TK = 16;
+constexpr int TSG = 16;    // segments per line in the tile kernel (16 lanes per line, 2 lines per warp)
 constexpr size_t kTridiagTileSmemMax = 110 * 1024;
-__host__ __device__ constexpr size_t tridiag_tile_smem(int L) { return sizeof(float) * 3 * (size_t)TK * (L + TSEG); }
+__host__ __device__ constexpr size_t tridiag_tile_smem(int L) { return sizeof(float) * 3 * (size_t)TK * (L + TSG); }
 
-__global__ void __launch_bounds__(TK * TSEG) k_tridiag_tile32(float* y_io, int64_t ld, int L, int64_t nmodes,
+__global__ void __launch_bounds__(TK * TSG) k_tridiag_tile32(float* y_io, int64_t ld, int L, int64_t nmodes,
                                                              float l_sub, const float* __restrict__ thm,
                                                              const float* __restrict__ thc, float inv_t) {
     extern __shared__ float smt[];
-    const int Lp = L + TSEG;
-    const int seglen = (L + TSEG - 1) / TSEG;
+    const int Lp = L + TSG;
+    const int seglen = (L + TSG - 1) / TSG;
     float* F = smt;                  // TK x Lp: f, then y in place
     float* Mt = F + TK * Lp;
     float* Ct = Mt + TK * Lp;
     const int c = blockIdx.y;
     const int64_t k0 = (int64_t)blockIdx.x * TK;
     float* y = y_io + (int64_t)c * ld;
-    constexpr int NT = TK * TSEG, UB = 8;   // UB elements (3 UB loads) in flight per thread
+    constexpr int NT = TK * TSG, UB = 8;   // UB elements (3 UB loads) in flight per thread
     const int tot = L * TK;
     for (int e0 = threadIdx.x; e0 < tot; e0 += UB * NT) {
         float fv[UB], mv[UB], cv[UB];
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(TK * TSEG) k_tridiag_tile32(float* y_io, int64
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int seg = lane % TSEG, kk = warp * (32 / TSEG) + lane / TSEG;
+    const int seg = lane % TSG, kk = warp * (32 / TSG) + lane / TSG;
     const int x0 = min(L, seg * seglen), x1 = min(L, x0 + seglen);
     float* f = F + kk * Lp + seg;          // element x of the line at f[x] (x in this segment)
     const float* m = Mt + kk * Lp + seg;
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(TK * TSEG) k_tridiag_tile32(float* y_io, int64
         A = a * A;
     }
     float yin = 0.f;
-    for (int sgi = 1; sgi < TSEG; ++sgi) {
+    for (int sgi = 1; sgi < TSG; ++sgi) {
         const float v = __shfl_up_sync(full, A * yin + B, 1);
         if (seg == sgi) yin = v;
     }
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(TK * TSEG) k_tridiag_tile32(float* y_io, int64
         A = -cv * A;
     }
     float zin = 0.f;
-    for (int sgi = TSEG - 2; sgi >= 0; --sgi) {
+    for (int sgi = TSG - 2; sgi >= 0; --sgi) {
         const float v = __shfl_down_sync(full, A * zin + B, 1);
         if (seg == sgi) zin = v;
     }
@@ -604,7 +605,7 @@ cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t n
     const size_t shm = tridiag_tile_smem(L);
     if (shm <= kTridiagTileSmemMax) {
         const dim3 grid((unsigned)((nmodes + TK - 1) / TK), (unsigned)p);
-        k_tridiag_tile32<<<grid, TK * TSEG, shm, s>>>(y, ld, L, nmodes, l_sub, th_m, th_c, inv_t);
+        k_tridiag_tile32<<<grid, TK * TSG, shm, s>>>(y, ld, L, nmodes, l_sub, th_m, th_c, inv_t);
         return cudaGetLastError();
     }
     const int64_t lines = nmodes * p, per_block = 128 / TSEG;
