@@ -364,9 +364,9 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
 // modes of one column (16 x L values of f, thm and thc, loaded once with coalesced reads),
 // runs the same segmented affine scans as tridiag_seg from shared memory and writes y back.
 // Each mode's line is stored contiguously with one pad element per segment, so the TSG lanes
-// of a line and the two lines of a warp read distinct banks (row stride L + TSG, L = 256).
+// of a line read distinct banks (segment stride seglen + 1, odd for L = 256).
 constexpr int TK = 16;
-constexpr int TSG = 16;    // segments per line in the tile kernel (16 lanes per line, 2 lines per warp)
+constexpr int TSG = 32;    // segments per line in the tile kernel (one line per warp)
 constexpr size_t kTridiagTileSmemMax = 110 * 1024;
 __host__ __device__ constexpr size_t tridiag_tile_smem(int L) { return sizeof(float) * 3 * (size_t)TK * (L + TSG); }
 
@@ -420,11 +420,19 @@ __global__ void __launch_bounds__(TK * TSG) k_tridiag_tile32(float* y_io, int64_
         B = a * B + f[x] * inv_t * m[x];
         A = a * A;
     }
-    float yin = 0.f;
-    for (int sgi = 1; sgi < TSG; ++sgi) {
-        const float v = __shfl_up_sync(full, A * yin + B, 1);
-        if (seg == sgi) yin = v;
+    // inclusive scan of the segment maps y -> A y + B over the line's TSG lanes (log2 TSG
+    // steps; the composition is associative), then the value entering each segment is the
+    // previous segment's prefix applied to 0
+#pragma unroll
+    for (int d = 1; d < TSG; d <<= 1) {
+        const float Ap = __shfl_up_sync(full, A, d, TSG), Bp = __shfl_up_sync(full, B, d, TSG);
+        if (seg >= d) {
+            B = fmaf(A, Bp, B);
+            A = A * Ap;
+        }
     }
+    float yin = __shfl_up_sync(full, B, 1, TSG);
+    if (seg == 0) yin = 0.f;
     float prev = yin;
     for (int x = x0; x < x1; ++x) {
         prev = (f[x] * inv_t - l_sub * prev) * m[x];
@@ -437,11 +445,16 @@ __global__ void __launch_bounds__(TK * TSG) k_tridiag_tile32(float* y_io, int64_
         B = f[x] - cv * B;
         A = -cv * A;
     }
-    float zin = 0.f;
-    for (int sgi = TSG - 2; sgi >= 0; --sgi) {
-        const float v = __shfl_down_sync(full, A * zin + B, 1);
-        if (seg == sgi) zin = v;
+#pragma unroll
+    for (int d = 1; d < TSG; d <<= 1) {
+        const float An = __shfl_down_sync(full, A, d, TSG), Bn = __shfl_down_sync(full, B, d, TSG);
+        if (seg + d < TSG) {
+            B = fmaf(A, Bn, B);
+            A = A * An;
+        }
     }
+    float zin = __shfl_down_sync(full, B, 1, TSG);
+    if (seg == TSG - 1) zin = 0.f;
     float next = zin;
     for (int x = x1 - 1; x >= x0; --x) {
         const float cv = (x < L - 1) ? cc[x] : 0.f;
