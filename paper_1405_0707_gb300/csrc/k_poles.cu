@@ -22,13 +22,6 @@ struct cplx {
     double re, im;
 };
 __device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
-__device__ inline cplx cdiv(cplx a, cplx b) {
-    const double s = fabs(b.re) + fabs(b.im);
-    const double br = b.re / s, bi = b.im / s, ar = a.re / s, ai = a.im / s;
-    const double d = br * br + bi * bi;
-    return {(ar * br + ai * bi) / d, (ai * br - ar * bi) / d};
-}
 __device__ inline double cabs2(cplx a) { return a.re * a.re + a.im * a.im; }
 // x -= a * b with four fused multiply-adds
 __device__ inline void cmsub(cplx& x, cplx a, cplx b) {
@@ -38,15 +31,6 @@ __device__ inline void cmsub(cplx& x, cplx a, cplx b) {
 
 constexpr size_t kSmemLimit = 200 * 1024;
 constexpr int kPoleThreads = 512;   // sixteen warps per pole: four per scheduler to cover FP64 latency
-
-// 1 / d with one scaling division and one reciprocal
-__device__ inline cplx crecip(cplx d) {
-    const double s = fabs(d.re) + fabs(d.im);
-    const double is = 1.0 / s;
-    const double dr = d.re * is, di = d.im * is;
-    const double k = is / (dr * dr + di * di);
-    return {dr * k, -di * k};
-}
 
 // One CTA (sixteen warps) per pole.  Shared memory holds M (mp x mp complex, row-major), the
 // right-hand sides / solution X (mp x p complex), the inverses of U's diagonal blocks
