@@ -136,14 +136,14 @@ expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, 
 
 // One FP32 application of (tA)^{-1} to R (FP64 in), written (acc = 0) or added (acc = 1)
 // to X (FP64).  Same transforms and layouts as the FP64 path.
-expm_status inv32_apply(expm_plan* P, double t, const double* R, int64_t ldr, int p, double* X,
-                        int64_t ldx, int acc) {
+expm_status inv32_apply(expm_plan* P, double t, const void* R, int64_t ldr, int p, double* X,
+                        int64_t ldx, int acc, int r_f64 = 1) {
     cudaStream_t s = P->stream;
     const int nx = P->ax[0].N, ny = P->ax[1].N, nz = P->ax[2].N;
     const int64_t ld = P->ld;
     const float lsub = (float)P->ax[0].l, inv_t = (float)(1.0 / t);
     if (P->ndim == 2) {
-        GemmArgsMixed g1{R, P->Qf32[1], P->T1f, nx, ny, ny, 1, nx, ldr, 0, ny, 1, ld, 0, ny, p, 1, 1, 0, 0};
+        GemmArgsMixed g1{R, P->Qf32[1], P->T1f, nx, ny, ny, 1, nx, ldr, 0, ny, 1, ld, 0, ny, p, 1, r_f64, 0, 0};
         LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g1, s));
         LAUNCH(EXPM_STAGE_TRIDIAG, launch_tridiag_lines32(P->T1f, ld, p, nx, ny, lsub, P->th_m32, P->th_c32, inv_t, s));
         GemmArgsMixed g2{P->T1f, P->Qi32[1], X, nx, ny, ny, ny, 1, ld, 0, 1, nx, ldx, 0, ny, p, 1, 0, 1, acc};
@@ -151,7 +151,7 @@ expm_status inv32_apply(expm_plan* P, double t, const double* R, int64_t ldr, in
         return EXPM_OK;
     }
     const int64_t nxy = (int64_t)nx * ny;
-    GemmArgsMixed g1{R, P->Qf32[2], P->T2f, (int)nxy, nz, nz, 1, nxy, ldr, 0, 1, nxy, ld, 0, nz, p, 1, 1, 0, 0};
+    GemmArgsMixed g1{R, P->Qf32[2], P->T2f, (int)nxy, nz, nz, 1, nxy, ldr, 0, 1, nxy, ld, 0, nz, p, 1, r_f64, 0, 0};
     LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g1, s));
     GemmArgsMixed g2{P->T2f, P->Qf32[1], P->T1f, nx, ny, ny, 1, nx, ld, nxy, (int64_t)ny * nz, 1, ld, ny, ny, p, nz, 0, 0, 0};
     LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g2, s));
@@ -174,9 +174,12 @@ expm_status prec_apply_mixed(expm_plan* P, double t, const double* V, int64_t ld
     expm_status st = inv32_apply(P, t, V, ldv, p, W, ldw, 0);
     if (st != EXPM_OK) return st;
     for (int k = 0; k < P->refine; ++k) {
-        LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(W, ldw, P->R64, P->ld, p, P->ndim, P->ax[0].N, P->ax[1].N,
-                                                   P->ax[2].N, P->ax, -t, s, V, ldv, 1.0));
-        st = inv32_apply(P, t, P->R64, P->ld, p, W, ldw, 1);
+        // the residual V - tA x in FP64, stored in FP32 (the R64 buffer): the transforms read
+        // it as FP32 either way
+        float* R32 = reinterpret_cast<float*>(P->R64);
+        LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(W, ldw, nullptr, P->ld, p, P->ndim, P->ax[0].N, P->ax[1].N,
+                                                   P->ax[2].N, P->ax, -t, s, V, ldv, 1.0, R32));
+        st = inv32_apply(P, t, R32, P->ld, p, W, ldw, 1, 0);
         if (st != EXPM_OK) return st;
     }
     return EXPM_OK;

@@ -220,7 +220,7 @@ cudaError_t launch_axis_setup(double* Qf, double* Qi, double* lam, int N, double
 cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw, int p,
                             int ndim, int nx, int ny, int nz, const Axis* ax, double t,
                             cudaStream_t s, const double* Y = nullptr, int64_t ldy = 0,
-                            double beta = 0.0);
+                            double beta = 0.0, float* W32 = nullptr);
 cudaError_t launch_gemm32(const GemmArgsMixed& g, cudaStream_t s);
 cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t nmodes, float l_sub,
                                    const float* th_m, const float* th_c, float inv_t,

@@ -247,10 +247,12 @@ struct StencilT {
 };
 
 // W = tA V (+ beta Y): one thread per grid point and column; grid index arithmetic in 32 bits
-// (n < 2^31 is checked by the launcher).
+// (n < 2^31 is checked by the launcher).  With W32 set, the FP64 result is stored rounded to
+// FP32 there (same leading dimension) instead of in W: the refinement residual, which only
+// the FP32 transforms read.
 __global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __restrict__ W,
                            int64_t ldw, int ndim, int nx, int ny, int nz, StencilT k,
-                           const double* __restrict__ Y, int64_t ldy, double beta) {
+                           const double* __restrict__ Y, int64_t ldy, double beta, float* __restrict__ W32) {
     const unsigned n = (unsigned)nx * (unsigned)ny * (unsigned)nz;
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
@@ -271,7 +273,9 @@ __global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __
             if (iz < (unsigned)nz - 1) acc = fma(k.tu[2], v[i + st], acc);
         }
     }
-    W[c * ldw + i] = Y ? fma(beta, Y[c * ldy + i], acc) : acc;
+    const double r = Y ? fma(beta, Y[c * ldy + i], acc) : acc;
+    if (W32) W32[c * ldw + i] = (float)r;
+    else W[c * ldw + i] = r;
 }
 
 // ---------------------------------------------------------------- mixed precision
@@ -580,7 +584,7 @@ cudaError_t launch_axis_setup(double* Qf, double* Qi, double* lam, int N, double
 
 cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw, int p,
                             int ndim, int nx, int ny, int nz, const Axis* ax, double t,
-                            cudaStream_t s, const double* Y, int64_t ldy, double beta) {
+                            cudaStream_t s, const double* Y, int64_t ldy, double beta, float* W32) {
     const int64_t n = (int64_t)nx * ny * nz;
     if (n >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
     StencilT k;
@@ -590,7 +594,7 @@ cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw
         k.tu[d] = t * ax[d].u;
     }
     dim3 grid((unsigned)((n + 255) / 256), p);
-    k_cd_apply<<<grid, 256, 0, s>>>(V, ldv, W, ldw, ndim, nx, ny, nz, k, Y, ldy, beta);
+    k_cd_apply<<<grid, 256, 0, s>>>(V, ldv, W, ldw, ndim, nx, ny, nz, k, Y, ldy, beta, W32);
     return cudaGetLastError();
 }
 
