@@ -1,7 +1,13 @@
-"""Throughput of Z = r(tA) B (preconditioned shifted block FOM, Algorithm 2) on GB300.
+"""Throughput of Z = r(tA) B (the CF rational, solved by the shifted block FOM of Algorithm 2,
+or Algorithm 1 where the norm ratio favours it) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload cd2d-256|tridiag-1d|toeplitz-1m]
+                    [--workload cd2d-256|tridiag-1d|toeplitz-1m|batched3d-64|cd2d-512-grad]
+                    [--component prec|stencil|expm|step --precision fp64|mixed]
+
+The JSON line's value is the mixed-precision path (FP32 and double-float bulk
+arithmetic, FP64 data and projected solves; results within 1e-8 of the FP64 GPU path,
+checked inside the run). The plain FP64 path is timed alongside as "fp64_path".
 
 One step = one pass of the whole hot path over one batch: for the default workload
 (cd2d-256: 2-D convection-diffusion, 256 x 256 interior grid, n = 65536, p = 8 columns
@@ -12,7 +18,8 @@ step a 512 MB buffer is written to flush the 129 MB L2 (the working set, about 6
 would otherwise stay L2-resident across steps), outside the event-timed interval.
 
 --workload toeplitz-1m times the symmetric Toeplitz workload (n = 2^20, bandwidth 256,
-p = 16, t = 1; products by circulant embedding and the four-step FP64 FFT).
+p = 16, t = 1; products by circulant embedding and the four-step FFT, double-float in the
+mixed path).
 
 Multi-GPU: the path does not shard (the block Krylov space couples the p columns), so
 N > 1 runs N independent replicas, one per rank, each on its own seeded batch ("weak"

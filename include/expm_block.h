@@ -57,7 +57,8 @@ typedef enum {
     EXPM_OP_CONV_DIFF = 0,
     /* t * T, T the n x n symmetric Toeplitz matrix with first column (a_0, .., a_bw, 0, ..)
      * (Example 5.4).  Products by circulant embedding (size N = 2^k >= max(n + bw, 2n),
-     * N <= 2^22) and a four-step FP64 FFT; the exact inverse (Algorithm 2's preconditioner)
+     * N <= 2^22) and a four-step FFT (FP64; double-float in mixed plans); the exact inverse
+     * (Algorithm 2's preconditioner)
      * by the Gohberg-Semencul formula (Section 4.1) from the generator x = T^{-1} e_1,
      * computed at plan creation by conjugate gradients with the FFT product.  Requires
      * a_0 < 0 and T negative definite: for bw <= 4096 the plan bounds the largest value of
@@ -79,12 +80,18 @@ typedef struct {
 
 typedef enum {
     EXPM_PREC_FP64 = 0,    /* every step in FP64 (the plain path)                    */
-    /* Mixed: the DST-I transforms of the exact inverse run in FP32 and the inverse is
-     * refined to FP64 accuracy (x += inv32(V - tA x), residual in FP64; Theorem 4.3 makes
-     * the inverse's accuracy the one that matters); the CGS2 projections are FP32 products;
-     * basis storage, the Gram-Schmidt updates, the QR, the projected systems and the
-     * combination stay FP64, so the Arnoldi relation and the collinear restart are exact
-     * to FP64 rounding.  Results agree with EXPM_PREC_FP64 to ~1e-12 relative. */
+    /* Mixed: bulk arithmetic on the FP32 pipe, data and small solves in FP64.
+     * - The DST-I transforms of the exact inverse run in FP32, and the inverse is refined
+     *   to FP64 accuracy (x += inv32(V - tA x), residual in FP64). Theorem 4.3 makes the
+     *   inverse's accuracy the one that matters.
+     * - Symmetric Toeplitz operators run their FFTs in double-float (float pairs, 2^-48).
+     * - The CGS2 projections are FP32 products.
+     * - The first Gram-Schmidt update, the application of each Cholesky-QR factor and the
+     *   Z update run in double-float. Corrections of size O(eps_32) are formed in FP32.
+     * - The basis is stored in FP64, and the projected systems and the combination stay
+     *   FP64.
+     * So the Arnoldi relation and the collinear restart hold to ~1e-14 or better.
+     * Results agree with EXPM_PREC_FP64 to ~1e-12 relative. */
     EXPM_PREC_MIXED = 1
 } expm_precision;
 
@@ -155,7 +162,8 @@ expm_status expm_cf_coeffs(int nu, double* tau_re_im, double* omega_re_im,
  * spectrum of the circulant embedding (one FFT) and, unless opts.algorithm is
  * EXPM_ALG_SBFOM, the Gohberg-Semencul generator (conjugate gradients on the device;
  * EXPM_NOT_CONVERGED if its residual stays above 1e-12).  EXPM_PREC_MIXED on a Toeplitz
- * operator keeps the FFTs in FP64 and runs the Gram-Schmidt projections in FP32.
+ * operator computes the spectra and the generator in FP64 and runs the later products
+ * and inverses in double-float.
  *   op      : host descriptor (read during the call)
  *   p_max   : 1 <= p_max <= 32; m * p_max <= 512
  *   opts    : host options (copied)
