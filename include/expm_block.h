@@ -99,7 +99,7 @@ typedef enum {
  * (tA)^{-1}) pays off when ||tA|| >> |tau_i| (eq. (43), Example 5.2); Algorithm 1 (SBFOM,
  * Krylov operator tA, Section 3) is the better choice when ||tA|| is comparable to the
  * poles.  AUTO picks Algorithm 2 iff the Gershgorin bound of ||tA|| is at least
- * EXPM_AUTO_RATIO * max_i |tau_i| (a build choice). */
+ * EXPM_AUTO_RATIO * max_i |tau_i| (a build choice: the paper gives no rule). */
 typedef enum {
     EXPM_ALG_AUTO = 0,
     EXPM_ALG_SBFOM = 1,     /* Algorithm 1 */

@@ -27,7 +27,7 @@ textbook Chebyshev-CF construction, each step written out:
  4. the CF denominator is the polynomial  q(z) = sum_j v_j z^(K-1-j); exactly nu of
     its roots lie outside the unit disk.  A root z maps to w = (z + 1/z)/2 and then
     to the pole  tau = s (z - 1)^2 / (z + 1)^2  in the x-plane.
- 5. residues (reading, recorded in the design doc): with the poles fixed, omega_0 and the
+ 5. residues (a reading: the paper does not say how): with the poles fixed, omega_0 and the
     omega_i are the linear least-squares fit of e^x on the M Chebyshev points of the
     first kind in w, plus the point w = -1 (x = -inf) where e^x = 0.
 """

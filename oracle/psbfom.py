@@ -20,9 +20,9 @@ Conjugate poles: for real A and B, (A - conj(tau) I)^{-1} B = conj((A - tau I)^{
 the oracle solves the nu/2 poles with Im tau > 0 and adds 2 Re(omega_i X_i) (Section 2,
 last paragraph before Remark 2.1).
 
-Readings of the paper (listed in DESIGN.md): stop when max_i ||R_i||_F <= tol ||B||_F;
+Readings of the paper where it is silent: stop when max_i ||R_i||_F <= tol ||B||_F;
 a block Arnoldi breakdown (new vector norm <= 1e-14 of its norm before orthogonalisation)
-ends the cycle; deflation (Algorithm 1 steps 5-9) is
+ends the cycle; deflation (the deflated restart of Algorithms 1 and 2) is
 ``k`` > 0, Ritz values of H_m chosen as the k smallest in modulus for Algorithm 1 and the
 k largest in modulus for Algorithm 2 (Remark 4.1: those are the smallest |lambda(A)|).
 """
@@ -51,7 +51,7 @@ def matvec(A):
 
 
 def qr_positive(B):
-    """Step 2 of Algorithm 1: B = V_1 R with V_1 orthonormal, R upper triangular with a
+    """The initial block QR of Algorithm 1: B = V_1 R with V_1 orthonormal, R upper triangular with a
     positive diagonal (Householder QR, then column signs fixed)."""
     Q, R = np.linalg.qr(B)
     s = np.sign(np.diag(R))
@@ -65,7 +65,7 @@ def block_arnoldi_ruhe(op, V1, m, start_vectors=None, H0=None):
     Generates v_{p+1}, ..., v_{(m+1)p}: the vector v_j comes from w = op(v_{j-p}),
     orthogonalised against v_1..v_{j-1} (twice), h_{j,j-p} = ||w||, v_j = w / h.
     ``start_vectors``/``H0`` let a deflated restart continue from a given leading basis
-    (Algorithm 1 step 9): columns [0, len0) of the basis and the corresponding leading
+    (the deflated restart of Algorithm 1): columns [0, len0) of the basis and the corresponding leading
     columns of H are taken as given.
 
     Returns (V, H, m_done, breakdown): V is n x (m_done+1)p, H is (m_done+1)p x m_done p.
@@ -123,7 +123,7 @@ def block_arnoldi_ruhe(op, V1, m, start_vectors=None, H0=None):
 
 
 def deflation_basis(Hm, k, largest):
-    """Algorithm 1 steps 5-6: eigenpairs of H_m; keep the k wanted ones (smallest |theta|
+    """The eigenproblem of the deflated restart (Algorithm 1): eigenpairs of H_m; keep the k wanted ones (smallest |theta|
     for Algorithm 1, largest |theta| for Algorithm 2 -- Remark 4.1), split complex
     eigenvectors into real and imaginary parts (a conjugate pair then contributes two
     columns, so k may grow by one), orthonormalise -> P_k (mp x k')."""
@@ -213,7 +213,7 @@ def psbfom(apply_Ainv, B, table, m=10, tol=1e-10, max_cycles=100, k=0, fixed_cyc
         Vnext = V[:, mp_:mp_ + p]
         Snew = [taus[i] * (Hlast @ Zhat[i][mp_ - p:, :]) for i in range(nup)]
         if k > 0:
-            # Steps 5-9 of Algorithm 1 with A^{-1}: deflated restart
+            # the deflated restart of Algorithm 1, with A^{-1} as the operator
             Pk = deflation_basis(Hm, k, largest=True)
             kk = Pk.shape[1]
             Pk1 = np.zeros(((m_done + 1) * p, kk + p))

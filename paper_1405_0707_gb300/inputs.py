@@ -7,7 +7,7 @@ column by column (column c of B is one contiguous draw of n numbers), seed
 20140707 + workload index.
 
 Workloads (the paper's experiments use nu = 14 CF poles, Section 5; the block sizes, grid
-sizes and times below are the synthetic stand-ins described in the design doc):
+sizes and times below are synthetic stand-ins for the paper's own matrices):
   tridiag-1d   A = t (n+1)^2 tridiag(1, -2, 1), n = 2000, t = 1, p = 4, m = 10, tol 1e-10
   cd2d-256     t (0.1 Laplacian_h - (1, 1) . grad_h) on a 256 x 256 interior grid,
                n = 65536, p = 8, t in {1e-3, 1e-2, 1e-1}, m = 10
