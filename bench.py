@@ -50,9 +50,10 @@ L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF = {"gemm": "k_gemm (DST-I transforms of the exact inverse, FP64)",
              "cgs": "k_proj/k_update (block CGS2 row passes, FP64)",
              "cgs_mixed": "k_cgs_rows (first block CGS2 pass: FP32 projection, double-float update fused with "
-                          "the FP32 second projection and the FP32 Gram matrix)",
-             "qr_mixed": "k_qr_mixed_rows (second CGS pass's FP32 correction fused with the first Cholesky-QR "
-                         "pass: FP32 factor applied exactly in double-float; FP32 deviation passes)",
+                          "the FP32 second projection and the double-float Gram matrix)",
+             "qr_mixed": "k_qr_mixed_rows (second CGS pass's FP32 correction fused with one accurate Cholesky-QR "
+                         "pass: double-float factor applied exactly in double-float; FP32 deviation passes only "
+                         "for ill-conditioned blocks)",
              "tridiag_mixed": "k_tridiag_tile32 (FP32 Thomas line solves, segmented affine scans)",
              "gemm_mixed": "k_gemm32 (FP32 DST-I transforms of the exact inverse)",
              "fft_mixed": "k_fft_cols/k_fft_rows (four-step FFT Toeplitz product, double-float)",

@@ -107,7 +107,8 @@ expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, 
         LAUNCH(EXPM_STAGE_QR, launch_qr_mixed_rows(P->W, ld, p, n, P->nblk, G, P->part, P->ctr, 0, sm(P, kOffR),
                                                    sm(P, kOffRi), nullptr, sm(P, kOffRt), Hq, P->ldH, hrow, hcol,
                                                    normsq, flags, P->W, ld, s, cgs_cols ? P->V : nullptr, ld,
-                                                   cgs_cols, cgs_cols ? sm(P, kOffH) : nullptr));
+                                                   cgs_cols, cgs_cols ? sm(P, kOffH) : nullptr,
+                                                   cgs_cols ? out : nullptr, ldo));
         LAUNCH(EXPM_STAGE_QR, launch_qr_mixed_rows(P->W, ld, p, n, P->nblk, G, P->part, P->ctr, 1, sm(P, kOffR),
                                                    sm(P, kOffRi), sm(P, kOffRt), sm(P, kOffRt2), Hq, P->ldH, hrow,
                                                    hcol, nullptr, flags, out, ldo, s));

@@ -249,7 +249,7 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
                                  double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
                                  int* flags, double* out, int64_t ldo, cudaStream_t s,
                                  const double* Vc = nullptr, int64_t ldvc = 0, int ccols = 0,
-                                 const double* h2 = nullptr);
+                                 const double* h2 = nullptr, double* fin = nullptr, int64_t ldfin = 0);
 constexpr int kRowsMaxP = 16;  // widths handled by the row-per-thread kernels
 // Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
 // third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.

@@ -828,7 +828,7 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
                                  unsigned* ctr, int mode, double* R, double* Rinv, const double* Rtot_in,
                                  double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
                                  int* flags, double* out, int64_t ldo, cudaStream_t s, const double* Vc,
-                                 int64_t ldvc, int ccols, const double* h2) {
+                                 int64_t ldvc, int ccols, const double* h2, double* fin, int64_t ldfin) {
     if (p > rows16::RP) return cudaErrorInvalidValue;
     if (Vc && (mode != 0 || !h2 || ccols < 1 || ccols > kMaxMP)) return cudaErrorInvalidValue;
     const int64_t rpb = rows_per_block(n, nblk);
@@ -839,17 +839,17 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
     const int g = gr + (extra_lead ? 1 : 0), lead_blk = extra_lead ? gr : 0;
 #define EXPM_QR_ROWS(NS)                                                                                          \
     if (mode == 0 && Vc)                                                                                        \
-        NS::k_qr_mixed_rows<3><<<g, NS::NTR, sizeof(float) * (size_t)ccols * NS::RP, s>>>(                      \
+        NS::k_qr_mixed_rows<3><<<g, NS::NTR, 2 * sizeof(float) * (size_t)ccols * NS::RP, s>>>(                  \
             W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H, ldH, hrow, hcol, normsq_out,    \
-            flags, out, ldo, Vc, ldvc, ccols, h2, lead_blk);                                                               \
+            flags, out, ldo, Vc, ldvc, ccols, h2, lead_blk, fin, ldfin);                                          \
     else if (mode == 0)                                                                                         \
         NS::k_qr_mixed_rows<1><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
                                                      Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo,  \
-                                                     nullptr, 0, 0, nullptr, lead_blk);                                    \
+                                                     nullptr, 0, 0, nullptr, lead_blk, nullptr, 0);                                    \
     else                                                                                                        \
         NS::k_qr_mixed_rows<2><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
                                                      Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo,  \
-                                                     nullptr, 0, 0, nullptr, lead_blk);
+                                                     nullptr, 0, 0, nullptr, lead_blk, nullptr, 0);
     if (p <= rows8::RP) { EXPM_QR_ROWS(rows8) }
     else { EXPM_QR_ROWS(rows16) }
 #undef EXPM_QR_ROWS

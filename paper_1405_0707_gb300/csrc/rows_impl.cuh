@@ -388,6 +388,120 @@ __device__ inline void chol32_dev(CholF& cf, const double* G0, int p) {
     __syncwarp();
 }
 
+// ---- float-pair (double-float) scalars for the accurate first-pass factor
+struct fp2 {
+    float h, l;
+};
+__device__ __forceinline__ fp2 f2_make(float h, float l) {
+    fp2 r;
+    r.h = h;
+    r.l = l;
+    return r;
+}
+__device__ __forceinline__ fp2 f2_norm(float s, float e) {
+    const float h = s + e;
+    return f2_make(h, e - (h - s));
+}
+__device__ __forceinline__ fp2 f2_add(fp2 a, fp2 b) {
+    const float s = a.h + b.h, bp = s - a.h;
+    const float e = ((a.h - (s - bp)) + (b.h - bp)) + (a.l + b.l);
+    return f2_norm(s, e);
+}
+__device__ __forceinline__ fp2 f2_mul(fp2 a, fp2 b) {
+    const float pr = a.h * b.h;
+    float e = fmaf(a.h, b.h, -pr);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return f2_norm(pr, e);
+}
+// sqrt(a), a > 0: s = sqrtf(a_h), corrected by one Newton step (a - s^2) / (2 s), with s^2
+// formed exactly by an FMA
+__device__ __forceinline__ fp2 f2_sqrt(fp2 a) {
+    const float sq = sqrtf(a.h);
+    const float pr = sq * sq, pe = fmaf(sq, sq, -pr);
+    return f2_norm(sq, (((a.h - pr) - pe) + a.l) / (2.f * sq));
+}
+// 1 / a: x0 = 1 / a_h corrected by x0 (1 - a x0)
+__device__ __forceinline__ fp2 f2_rcp(fp2 a) {
+    const float x0 = 1.f / a.h;
+    float e = fmaf(-a.h, x0, 1.f);
+    e = fmaf(-a.l, x0, e);
+    return f2_norm(x0, x0 * e);
+}
+__device__ __forceinline__ fp2 f2_shfl(fp2 a, int src) {
+    return f2_make(__shfl_sync(0xffffffffu, a.h, src), __shfl_sync(0xffffffffu, a.l, src));
+}
+
+struct CholD {
+    float Uh[RP * RP], Ul[RP * RP];   // the factor of G 2^-k (upper triangle) as float pairs
+    float ih[RP], il[RP];             // 1 / U_cc as float pairs
+    int ok;
+};
+
+// Cholesky factor of G 2^-k in float-pair arithmetic on warp 0, lane l holding column l (as
+// chol32_full).  ok = every pivot is positive and at least rel_min times the largest diagonal
+// entry and no column is zero: then one pass with this factor leaves the block orthonormal to
+// ~kappa^2 2^-48, and the caller skips the deviation pass.  Otherwise the caller discards it.
+__device__ inline void chol_df(CholD& cd, const double* G0, int p, int k, float rel_min) {
+    const int lane = threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    const bool act = lane < p;
+    fp2 g[RP], u[RP];
+    float dg = 0.f;
+#pragma unroll
+    for (int a = 0; a < RP; ++a) {
+        float h = 0.f, l = 0.f;
+        if (act && a < p) split_df(ldexp(G0[a * p + lane], -k), h, l);
+        g[a] = f2_make(h, l);
+        u[a] = f2_make(0.f, 0.f);
+        if (a == lane) dg = h;
+    }
+    float dmax = act ? dg : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(full, dmax, o));
+    int ok_l = 1;
+    fp2 myinv = f2_make(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < RP; ++j) {
+        if (j >= p) break;
+        fp2 inv = f2_make(0.f, 0.f);
+        if (lane == j) {
+            fp2 d = g[j];
+            if (G0[j * p + j] == 0.0 || !(d.h > 0.f) || !isfinite(d.h) || d.h < rel_min * dmax) {
+                ok_l = 0;
+                d = f2_make(1.f, 0.f);
+            }
+            u[j] = f2_sqrt(d);
+            inv = f2_rcp(u[j]);
+            myinv = inv;
+        }
+        inv = f2_shfl(inv, j);
+        if (act && lane > j) u[j] = f2_mul(g[j], inv);
+        // trailing update G[a][l] -= U[j][a] U[j][l] for j < a <= l
+#pragma unroll
+        for (int a = j + 1; a < RP; ++a) {
+            const fp2 uja = f2_shfl(u[j], a);
+            if (act && a < p && a <= lane) {
+                const fp2 pr = f2_mul(uja, u[j]);
+                g[a] = f2_add(g[a], f2_make(-pr.h, -pr.l));
+            }
+        }
+    }
+    const int ok = __all_sync(full, ok_l);
+    if (act) {
+#pragma unroll
+        for (int a = 0; a < RP; ++a)
+            if (a < p) {
+                cd.Uh[a * p + lane] = u[a].h;
+                cd.Ul[a * p + lane] = u[a].l;
+            }
+        cd.ih[lane] = myinv.h;
+        cd.il[lane] = myinv.l;
+    }
+    if (lane == 0) cd.ok = ok;
+    __syncwarp();
+}
+
 // KIND 1: the first pass (FP32 factor of G, exact double-float application).  KIND 3: the
 // same, fused with the second CGS pass's correction W <- W - Vc h2 (FP32, as
 // k_update_gram_rows<true>): the input Gram matrix Gin = h2 + ccols p (p x p, stored after
@@ -402,12 +516,17 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                                                       double* Rtot_out, double* H, int ldH, int hrow, int hcol,
                                                       double* normsq_out, int* flags, double* out_, int64_t ldo_,
                                                       const double* __restrict__ Vc, int64_t ldvc, int ccols,
-                                                      const double* __restrict__ h2, int lead_blk) {
+                                                      const double* __restrict__ h2, int lead_blk, double* fin_,
+                                                      int64_t ldfin_) {
     constexpr bool K1 = KIND == 1 || KIND == 3;
     int* extra = flags + 2;
+    int* done = flags + 3;                  // KIND 3 single pass: the block is final after pass 1
+    if (mode >= 1 && *done) return;
     if (mode == 2 && *extra == 0) return;
-    extern __shared__ float h2f[];          // KIND 3: h2 as FP32, ccols x RP (zero-padded columns)
+    extern __shared__ float h2f[];          // KIND 3: h2 as float pairs (hi, then lo), ccols x RP each
+    float* h2l = h2f + ccols * RP;
     __shared__ CholF cf;
+    __shared__ CholD cd;                    // KIND 3: the float-pair factor of the single pass
     __shared__ double G0[RP * RP];
     __shared__ double hn2[RP];
     __shared__ double Rd[RP * RP];          // KIND 1: R (padded to RP x RP); KIND 2 unused
@@ -421,14 +540,20 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     if (KIND == 3) {
         for (int e = threadIdx.x; e < ccols * RP; e += blockDim.x) {
             const int a = e / RP, c = e - a * RP;
-            h2f[e] = (c < p) ? (float)h2[a * p + c] : 0.f;
+            float hh = 0.f, hl = 0.f;
+            if (c < p) split_df(h2[a * p + c], hh, hl);
+            h2f[e] = hh;
+            h2l[e] = hl;
         }
         __syncthreads();
+        // G - h2^T h2 with the products in float-pair arithmetic (the single pass needs G to
+        // ~2^-48); the Gram sums follow h2 in memory
         for (int o = threadIdx.x; o < pp; o += blockDim.x) {
             const int i = o / p, k = o - i * p;
-            float s2 = 0.f;
-            for (int a = 0; a < ccols; ++a) s2 = fmaf(h2f[a * RP + i], h2f[a * RP + k], s2);
-            G0[o] = h2[ccols * p + o] - (double)s2;     // the Gram sums follow h2 in memory
+            float sh = 0.f, sl = 0.f;
+            for (int a = 0; a < ccols; ++a)
+                df_fma(sh, sl, h2f[a * RP + i], h2l[a * RP + i], h2f[a * RP + k], h2l[a * RP + k]);
+            G0[o] = h2[ccols * p + o] - ((double)sh + (double)sl);
         }
     } else {
         for (int o = threadIdx.x; o < pp; o += blockDim.x) G0[o] = G[o];
@@ -438,7 +563,8 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     // launcher places beyond the rows (an extra CTA that owns none, so the lead work runs
     // concurrently with the row CTAs) when each CTA holds few rows
     const bool lead = (int)blockIdx.x == lead_blk;
-    if (H && last && lead) {
+    const bool need_hn2 = H && lead && (last || (KIND == 3 && fin_));
+    if (need_hn2) {
         const int stripes = NTR / p;
         const int c = threadIdx.x % p, st = threadIdx.x / p;
         double v2 = 0.0;
@@ -450,7 +576,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         buf[0][threadIdx.x] = v2;
     }
     __syncthreads();
-    if (H && last && lead && threadIdx.x < p) {
+    if (need_hn2 && threadIdx.x < p) {
         const int stripes = NTR / p;
         double s2 = 0.0;
         for (int k = 0; k < stripes; ++k) s2 += buf[0][k * p + threadIdx.x];
@@ -470,19 +596,54 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                 frexp(dmax, &kexp);
                 kexp &= ~1;
             }
-            chol32_full(cf, G0, p, kexp, ldexp(tr, -kexp));
+            // KIND 3 with a final destination: the accurate factor first; the FP32 one (and
+            // the deviation passes after it) only when the block is too ill-conditioned for
+            // a single pass
+            int sgl = 0;
+            if (KIND == 3 && fin_) {
+                chol_df(cd, G0, p, kexp, 1e-5f);
+                // the Gram matrix after the correction must keep most of the one before it,
+                // else its relative accuracy is lost to cancellation
+                double tin = 0.0;
+                for (int c = 0; c < p; ++c) tin += h2[ccols * p + c * p + c];
+                sgl = cd.ok && tr >= 1e-4 * tin;
+                if (lane == 0) cd.ok = sgl;
+            } else if (lane == 0) {
+                cd.ok = 0;
+            }
+            __syncwarp();
+            if (sgl) {
+                if (lane == 0) {
+                    cf.ill = 0;
+                    cf.bad = 0;
+                    cf.umax = 0.f;
+                }
+                __syncwarp();
+            } else {
+                chol32_full(cf, G0, p, kexp, ldexp(tr, -kexp));
+            }
         } else {
             chol32_dev(cf, G0, p);
         }
+        const bool sgl_w = K1 && cd.ok;     // warp 0's view of the single-pass decision
+        const bool fin = last || sgl_w;     // this pass writes the final block and H
         if (lead) {
             if (K1 && normsq_out && lane == 0) *normsq_out = tr;
-            if (K1 && lane == 0) *extra = cf.ill;
+            if (K1 && lane == 0) {
+                *extra = cf.ill;
+                *done = sgl_w ? 1 : 0;
+            }
             if (lane < p) {
                 const int c = lane;
                 for (int r = 0; r < p; ++r) {
                     const int o = r * p + c;
                     double rt;
-                    if (K1) {
+                    if (sgl_w) {
+                        float rh = 0.f, rl = 0.f;
+                        if (r <= c) split_df(ldexp((double)cd.Uh[o] + (double)cd.Ul[o], kexp / 2), rh, rl);
+                        rt = (double)rh + (double)rl;   // exactly the R the substitution applies
+                        R[o] = rt;
+                    } else if (K1) {
                         rt = (r <= c) ? ldexp((double)cf.U[o], kexp / 2) : 0.0;
                         R[o] = rt;
                     } else {
@@ -495,11 +656,11 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                     }
                     Rtot_out[o] = rt;
                     if (!isfinite(rt)) cf.bad = 1;
-                    if (H && last) H[(int64_t)(hcol + c) * ldH + hrow + r] = rt;
+                    if (H && fin) H[(int64_t)(hcol + c) * ldH + hrow + r] = rt;
                 }
             }
             __syncwarp();
-            if (H && last && lane < p) {
+            if (H && fin && lane < p) {
                 const int c = lane;
                 double n0 = hn2[c], dg = 0.0;
                 for (int a = 0; a <= c; ++a) {
@@ -527,11 +688,19 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     // KIND 2 with max|U| above 1e-4 (a pass after the shifted one): the FP32 inverse I + Y
     // would leave an eps_32 |U| mismatch with the recorded R, so the solve is a forward
     // substitution with R = I + U in FP64, as in pass 1
+    const bool single = K1 && cd.ok;
     const bool subst = K1 || cf.umax > 1e-4f;
     for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
         const int a = e / RP, c = e % RP;
         const bool in = a < p && c < p && a <= c;
-        if (K1) Rd[e] = in ? ldexp((double)cf.U[a * p + c], kexp / 2) : 0.0;
+        if (single) {
+            // the pair (Rh, Rl) is what the substitution applies and what H records
+            float rh = 0.f, rl = 0.f;
+            if (in) split_df(ldexp((double)cd.Uh[a * p + c] + (double)cd.Ul[a * p + c], kexp / 2), rh, rl);
+            Rh[e] = rh;
+            Rl[e] = rl;
+            Rd[e] = (double)rh + (double)rl;
+        } else if (K1) Rd[e] = in ? ldexp((double)cf.U[a * p + c], kexp / 2) : 0.0;
         else {
             Yf[e] = in ? cf.Y[a * p + c] : 0.f;
             Rd[e] = in ? (double)cf.U[a * p + c] + (a == c ? 1.0 : 0.0) : 0.0;
@@ -539,17 +708,26 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     }
     __syncthreads();
     if (subst && threadIdx.x < RP) {
-        const double d = Rd[threadIdx.x * RP + threadIdx.x];
-        rcp[threadIdx.x] = (d != 0.0) ? 1.0 / d : 0.0;
-        if (K1) split_df(rcp[threadIdx.x], rch[threadIdx.x], rcl[threadIdx.x]);
+        const int c = threadIdx.x;
+        if (single) {
+            // 1 / R_cc from the factor's float-pair reciprocal, scaled back
+            const double ic = (c < p) ? ldexp((double)cd.ih[c] + (double)cd.il[c], -(kexp / 2)) : 0.0;
+            rcp[c] = ic;
+            split_df(ic, rch[c], rcl[c]);
+        } else {
+            const double d = Rd[c * RP + c];
+            rcp[c] = (d != 0.0) ? 1.0 / d : 0.0;
+            if (K1) split_df(rcp[c], rch[c], rcl[c]);
+        }
     }
-    if (K1)
+    if (K1 && !single)
         for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) split_df(Rd[e], Rh[e], Rl[e]);
     __syncthreads();
     double* out;
     int64_t ldo;
     int gram;
-    if (mode == 0) { out = W; ldo = ldw; gram = 1; }
+    if (single) { out = fin_; ldo = ldfin_; gram = 0; }
+    else if (mode == 0) { out = W; ldo = ldw; gram = 1; }
     else if (mode == 1 && *extra) { out = W; ldo = ldw; gram = 1; }
     else { out = out_; ldo = ldo_; gram = 0; }
     double acc[NQ];
@@ -869,17 +1047,31 @@ constexpr int RB = NTR / 2;
 constexpr int WS = RP + 1;                  // row stride of the FP32 copy of W
 
 __host__ __device__ constexpr size_t cgs_rows_smem(int cols, bool upd, int ng) {
-    return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS + (size_t)(cols + ng) * (RB + 1));
+    return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS + (size_t)cols * (RB + 1) +
+                            (ng ? 2 * (size_t)RB * RP : 0));
 }
 
+// Outputs o < cols p: FP32 products V^T W.  Outputs cols p <= o < (cols + p) p (the Gram matrix
+// W^T W, with Wh/Wl set): double-float products of the float pairs of W, so the Gram matrix
+// is accurate to ~2^-48 (it feeds the double-float factorisation of the first QR pass).
 template <int K>
 __device__ __forceinline__ void chunk_project(const float* Vs, const float* Wf, int nout, int p, float* ah,
-                                              float* al) {
+                                              float* al, int cols, const float* Wh, const float* Wl) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int o = threadIdx.x + k * NTR;
         if (o < nout) {
             const int a = o / p, c = o - a * p;
+            if (a >= cols) {
+                const int a2 = a - cols;
+                float sh = 0.f, sl = 0.f;
+#pragma unroll 4
+                for (int rr = 0; rr < RB; ++rr)
+                    df_fma(sh, sl, Wh[rr * RP + a2], Wl[rr * RP + a2], Wh[rr * RP + c], Wl[rr * RP + c]);
+                df_add(ah[k], al[k], sh);
+                al[k] += sl;
+                continue;
+            }
             const float* va = Vs + a * (RB + 1);
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll 8
@@ -902,7 +1094,9 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
     float* hh = smf;                                   // UPD: cols x RP (zero-padded columns)
     float* hl = hh + (UPD ? cols * RP : 0);
     float* Wf = hl + (UPD ? cols * RP : 0);            // RB x WS
-    float* Vs = Wf + RB * WS;                          // (cols + ng) x (RB + 1): V, then W
+    float* Vs = Wf + RB * WS;                          // cols x (RB + 1)
+    float* Wh = Vs + cols * (RB + 1);                  // ng: W as float pairs, RB x RP each
+    float* Wl = Wh + RB * RP;
     if (UPD) {
         for (int e = threadIdx.x; e < cols * RP; e += NTR) {
             const int a = e / RP, c = e - a * RP;
@@ -983,14 +1177,18 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
                 df_add(xh, xl, yh);
                 xl += yl;
                 if ((c & 1) == hf) {
-                    float wf = 0.f;
+                    float wf = 0.f, wh = 0.f, wl = 0.f;
                     if (ok && c < p) {
                         const double w = W[(int64_t)c * ldw + r] - ((double)xh + (double)xl);
                         W[(int64_t)c * ldw + r] = w;
                         wf = (float)w;
+                        if (ng) split_df(w, wh, wl);
                     }
                     Wf[rr * WS + c] = wf;
-                    if (c < ng) Vs[(cols + c) * (RB + 1) + rr] = wf;
+                    if (ng) {
+                        Wh[rr * RP + c] = wh;
+                        Wl[rr * RP + c] = wl;
+                    }
                 }
             }
         } else {
@@ -1015,7 +1213,7 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             }
         }
         __syncthreads();
-        chunk_project<K>(Vs, Wf, nout, p, ah, al);
+        chunk_project<K>(Vs, Wf, nout, p, ah, al, cols, Wh, Wl);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
