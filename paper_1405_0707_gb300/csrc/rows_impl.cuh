@@ -1034,9 +1034,9 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
 // products; the projection of the first pass).
 // k_cgs_rows<true>:  W <- W - V h in double-float arithmetic (as k_update_df: each product
 // v h = vh hh + (err(vh hh) + vl hh + vh hl), the large parts accumulated with TwoSum), then
-// the FP32 partials of V^T W for the second pass; with ng = p also the FP32 Gram partial
-// W^T W (outputs cols p .. (cols + p) p, full p x p), which feeds the FP32 factorisation of
-// the first Cholesky-QR pass.
+// the FP32 partials of V^T W for the second pass; with ng = p also the Gram partial W^T W
+// in double-float (outputs cols p .. (cols + p) p, full p x p), which feeds the double-float
+// factorisation of the single-pass Cholesky-QR.
 // Per chunk the FP32 copy of V (cols x RB) and of W (RB x RP) are staged in shared memory
 // and the cols x p projection outputs are spread over the threads (output o = tid + k NTR);
 // each chunk's FP32 sum is added to a float-pair accumulator, so the CTA's partial carries
