@@ -505,10 +505,13 @@ __device__ inline void chol_df(CholD& cd, const double* G0, int p, int k, float 
 // KIND 1: the first pass (FP32 factor of G, exact double-float application).  KIND 3: the
 // same, fused with the second CGS pass's correction W <- W - Vc h2 (FP32, as
 // k_update_gram_rows<true>): the input Gram matrix Gin = h2 + ccols p (p x p, stored after
-// h2) is then that of W before the correction, and the factor is taken of Gin - h2^T h2 (the
-// Gram matrix after it when V is orthonormal, up to O(eps_32) terms that only the FP32
-// factorisation sees).  Every kind writes the Gram matrix of its result to G (last CTA).
-// KIND 2: the deviation passes.
+// h2, accumulated in double-float) is then that of W before the correction, and the factor
+// is taken of Gin - h2^T h2 (formed in double-float: the Gram matrix after the correction when
+// V is orthonormal).  With a final destination fin_, KIND 3 first factors it in double-float:
+// when the block is well-conditioned (chol_df) that factor is applied, the pass writes the
+// final block and H and sets the done flag, and the later passes return at once; else the
+// FP32 factor and the passes after it run as for KIND 1.  The passes that feed another write
+// the Gram matrix of their result to G (last CTA).  KIND 2: the deviation passes.
 template <int KIND>
 __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int64_t rpb,
                                                       double* G, double* __restrict__ part, unsigned* ctr,
