@@ -43,7 +43,9 @@ typedef enum {
     EXPM_NUMERICAL = 4,        /* NaN/Inf, or a Cholesky pivot <= 0 in the block QR  */
     EXPM_CUDA_ERROR = 5,       /* a CUDA runtime call or kernel launch failed         */
     EXPM_NO_MEMORY = 6,        /* device allocation failed at plan creation           */
-    EXPM_INTERNAL = 7
+    EXPM_INTERNAL = 7,
+    EXPM_TIMEOUT = 8           /* a bounded device-side wait ran out (the kernel returned
+                                  without finishing; the device context stays usable)   */
 } expm_status;
 
 /* Operator families (the problem of Section 1: tA large, sparse, negative definite). */
@@ -117,6 +119,15 @@ typedef struct {
     int32_t algorithm;     /* expm_algorithm                                         */
     int32_t certify;       /* 1: also accumulate every pole's X_i and report the true
                               FP64 residuals ||B - (tA - tau_i I) X_i||_F (eq. (3))   */
+    int32_t nu_cf;         /* even CF degree nu, 2 <= nu <= 2*EXPM_MAX_POLES; 0 = 14, the
+                              degree of the paper's experiments (Section 5)            */
+    int32_t k_defl;        /* deflated restart (the restart of Algorithm 1 with
+                              deflation, used by both algorithms): keep k Ritz vectors of H_m at every restart
+                              (Algorithm 2: largest |mu|, Remark 4.1; Algorithm 1:
+                              smallest |theta|); k is rounded up to a multiple of the
+                              block width p and conjugate pairs are kept together (see
+                              expm_ritz_basis); 0 = plain restart.  Requires
+                              k_defl <= (m - 1) p_max.                                 */
 } expm_opts;
 
 #define EXPM_MAX_POLES 16
@@ -134,6 +145,7 @@ typedef struct {
     int32_t algorithm;           /* 1 or 2: the algorithm that ran                   */
     double  normA_bound;         /* Gershgorin bound of ||tA|| used by AUTO          */
     double  true_resid[EXPM_MAX_POLES]; /* certify: ||B - (tA - tau_i I) X_i||_F in FP64 */
+    int32_t kept;                /* deflated restart: Ritz vectors kept at the last restart */
 } expm_info;
 
 typedef struct expm_plan_s expm_plan;
@@ -154,6 +166,27 @@ typedef struct expm_plan_s expm_plan;
  * ------------------------------------------------------------------------------ */
 expm_status expm_cf_coeffs(int nu, double* tau_re_im, double* omega_re_im,
                            double* omega0, double* sigma);
+
+/* ---------------------------------------------------------------------------------
+ * expm_ritz_basis -- the eigenproblem of the deflated restart (Algorithm 1's restart
+ * with deflation; Algorithm 2 uses it with the Krylov operator A^{-1}): eigenpairs of the mp x mp real
+ * matrix H_m, the wanted Ritz values (largest |mu| when largest != 0, Remark 4.1, else
+ * smallest |theta|), eigenvectors of complex pairs split into real and imaginary parts,
+ * orthonormalised -> P (mp x kept).  Host only (no device work).
+ *   Hm      : host, mp x mp, column-major, leading dimension ldh >= mp (not modified)
+ *   k       : wanted count, 1 <= k <= mp; rounded up to a multiple of align (>= 1)
+ *   P       : host out, mp x kept, column-major, leading dimension ldp >= mp
+ *   kept    : host out: the number of columns written, a multiple of align, <= the rounded k
+ * Selection (a reading: the paper lets k "be increased or decreased"): Ritz values are
+ * walked in wanted order, a conjugate pair as one group of two columns; a group is kept
+ * when it still fits in the rounded k, a pair that does not fit is skipped in favour of
+ * the next real value; if the count is then not a multiple of align, the least wanted
+ * groups are dropped until it is.  Eigenvalues by the Francis double-shift QR algorithm
+ * on the Hessenberg form, eigenvectors by back substitution on the real Schur form.
+ * Errors: EXPM_INVALID_ARG, EXPM_NUMERICAL (no convergence, non-finite input).
+ * ------------------------------------------------------------------------------ */
+expm_status expm_ritz_basis(const double* Hm, int64_t ldh, int mp, int k, int largest,
+                            int align, double* P, int64_t ldp, int* kept);
 
 /* ---------------------------------------------------------------------------------
  * expm_plan_create -- "LU once and for all" (Section 4.1; Section 5): set up the exact

@@ -48,8 +48,13 @@ S_DEFAULT = 9
 K_DEFAULT = 100
 N_DEFAULT = 1024
 M_DEFAULT = 512
-GOLDEN = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                      "tests", "golden", "cf_nu14.json")
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
+GOLDEN = os.path.join(GOLDEN_DIR, "cf_nu14.json")
+
+
+def golden_path(nu):
+    """Stored table of degree nu (written by oracle/make_cf_table.py)."""
+    return os.path.join(GOLDEN_DIR, "cf_nu%d.json" % nu)
 
 
 def _transplant(s, w):
@@ -152,8 +157,11 @@ def cf_table(nu=NU_DEFAULT, s=S_DEFAULT, K=K_DEFAULT, N=N_DEFAULT, M=M_DEFAULT, 
         }
 
 
-def load_table(path=GOLDEN):
-    """Stored table written by ``oracle/make_cf_table.py`` (which calls only this module)."""
+def load_table(path=GOLDEN, nu=None):
+    """Stored table written by ``oracle/make_cf_table.py`` (which calls only this module);
+    ``nu`` picks the stored table of that degree instead of ``path``."""
+    if nu is not None:
+        path = golden_path(nu)
     with open(path) as f:
         d = json.load(f)
     return {
@@ -162,22 +170,5 @@ def load_table(path=GOLDEN):
         "omega": np.array([complex(float(a), float(b)) for a, b in d["omega_str"]]),
         "omega0": float(d["omega0_str"]),
         "sigma": float(d["sigma"]),
+        "tau_str": d["tau_str"], "omega_str": d["omega_str"], "omega0_str": d["omega0_str"],
     }
-
-
-def r_eval(table, x):
-    """r(x) = omega_0 + sum_i 2 Re(omega_i/(x - tau_i)) for real x (numpy, FP64)."""
-    x = np.asarray(x, dtype=np.float64)
-    r = np.full(x.shape, table["omega0"])
-    for t, w in zip(table["tau"], table["omega"]):
-        r = r + 2.0 * np.real(w / (x - t))
-    return r
-
-
-def r_eval_mp(table, x):
-    """The same rational in mpmath at the working precision (for error curves)."""
-    x = mp.mpf(x)
-    r = mp.mpf(table["omega0"])
-    for t, w in zip(table["tau"], table["omega"]):
-        r += 2 * mp.re(mp.mpc(w) / (x - mp.mpc(t)))
-    return r

@@ -122,41 +122,69 @@ def block_arnoldi_ruhe(op, V1, m, start_vectors=None, H0=None):
     return V, H, m_done, breakdown
 
 
-def deflation_basis(Hm, k, largest):
+def deflation_basis(Hm, k, largest, align=None):
     """The eigenproblem of the deflated restart (Algorithm 1): eigenpairs of H_m; keep the k wanted ones (smallest |theta|
     for Algorithm 1, largest |theta| for Algorithm 2 -- Remark 4.1), split complex
     eigenvectors into real and imaginary parts (a conjugate pair then contributes two
-    columns, so k may grow by one), orthonormalise -> P_k (mp x k')."""
+    columns, so k may grow by one), orthonormalise -> P_k (mp x k').
+
+    ``align`` (a reading for a block method: the paper lets k "be increased or decreased"):
+    the kept count is a multiple of align.  k is rounded up to a multiple of align; Ritz
+    values are walked in wanted order with a conjugate pair as one group of two columns; a
+    group is kept only if it still fits, so a pair that does not fit is skipped in favour of
+    the next real value; if the count is then not a multiple of align, the least wanted
+    groups are dropped until it is."""
     theta, Y = np.linalg.eig(Hm)
-    order = list(np.argsort(-np.abs(theta)) if largest else np.argsort(np.abs(theta)))
-    cols, taken = [], set()
+    order = list(np.argsort(-np.abs(theta), kind="stable") if largest else
+                 np.argsort(np.abs(theta), kind="stable"))
+    # groups in wanted order: a real value, or a conjugate pair (its Im > 0 member's vector)
+    groups, taken = [], set()
     for idx in order:
-        if len(cols) >= k:
-            break
         if idx in taken:
             continue
         taken.add(idx)
-        y = Y[:, idx]
         if abs(theta[idx].imag) > 1e-12 * max(abs(theta[idx]), 1e-300):
-            cols += [y.real, y.imag]
             rest = [j for j in order if j not in taken]
             partner = min(rest, key=lambda j: abs(theta[j] - np.conj(theta[idx])))
             taken.add(partner)
+            y = Y[:, idx] if theta[idx].imag > 0 else Y[:, partner]
+            groups.append([y.real, y.imag])
         else:
-            cols.append(y.real)
+            groups.append([Y[:, idx].real])
+    if align is None:
+        cols = []
+        for gcols in groups:
+            if len(cols) >= k:
+                break
+            cols += gcols
+    else:
+        target = min(Hm.shape[0], -(-k // align) * align)
+        sel, count = [], 0
+        for gcols in groups:
+            if count + len(gcols) <= target:
+                sel.append(gcols)
+                count += len(gcols)
+            if count == target:
+                break
+        while count % align != 0 and sel:
+            count -= len(sel.pop())
+        cols = [c for gcols in sel for c in gcols]
+        if not cols:
+            return np.zeros((Hm.shape[0], 0))
     Q, _ = np.linalg.qr(np.column_stack(cols))
     return Q
 
 
 # --------------------------------------------------------------------------- Algorithm 2
 def psbfom(apply_Ainv, B, table, m=10, tol=1e-10, max_cycles=100, k=0, fixed_cycles=None,
-           return_details=False):
+           return_details=False, align=None):
     """Algorithm 2 (PSBFOM[-DR]) for Z ~= e^A B, A already scaled by t.
 
     apply_Ainv : callable, w (n,) -> A^{-1} w  (the right preconditioner M_i = A^{-1})
     B          : (n, p) real
     table      : CF table with 'tau' (Im > 0 poles), 'omega', 'omega0'
     k          : number of deflated Ritz vectors (0 = plain restart)
+    align      : keep a multiple of this many Ritz vectors (see deflation_basis)
     fixed_cycles : run exactly this many cycles (ignores tol), for parity tests
     """
     B = np.asarray(B, dtype=np.float64)
@@ -165,9 +193,9 @@ def psbfom(apply_Ainv, B, table, m=10, tol=1e-10, max_cycles=100, k=0, fixed_cyc
     omegas = np.asarray(table["omega"])
     nup = len(taus)
     normB = np.linalg.norm(B)
-    # Step 1: initial guesses Y_i^0 = O
+    # initial guesses Y_i^0 = O
     Y = [np.zeros((n, p), dtype=complex) for _ in range(nup)]
-    # Step 2: QR of the common initial residual R_i^0 = B
+    # QR of the common initial residual R_i^0 = B
     V1, R = qr_positive(B)
     Rhat = [R.astype(complex) for _ in range(nup)]
     history = []
@@ -180,7 +208,7 @@ def psbfom(apply_Ainv, B, table, m=10, tol=1e-10, max_cycles=100, k=0, fixed_cyc
     details = []
     while True:
         cycles += 1
-        # Step 3: block Arnoldi with the Krylov operator A^{-1}  (eq. (4.5))
+        # block Arnoldi with the Krylov operator A^{-1}  (eq. (4.5))
         V, Ht, m_done, breakdown = block_arnoldi_ruhe(apply_Ainv, V1, m, start_vectors, H0)
         first = p if start_vectors is None else start_vectors.shape[1]
         matvecs += (m_done + 1) * p - first
@@ -188,7 +216,7 @@ def psbfom(apply_Ainv, B, table, m=10, tol=1e-10, max_cycles=100, k=0, fixed_cyc
         Hm = Ht[:mp_, :mp_]
         Hlast = Ht[mp_:mp_ + p, mp_ - p:mp_]           # H_{m+1,m}
         Vm = V[:, :mp_]
-        # Step 4: projected systems (I - tau_i H_m) Z_i = E_1 R_i  (eq. (3236))
+        # projected systems (I - tau_i H_m) Z_i = E_1 R_i  (eq. (3236))
         res = np.zeros(nup)
         Zhat = []
         for i in range(nup):
@@ -212,9 +240,9 @@ def psbfom(apply_Ainv, B, table, m=10, tol=1e-10, max_cycles=100, k=0, fixed_cyc
         # restart: residuals tau_i V_{m+1} H_{m+1,m} E_m^T Z_i are collinear with V_{m+1}
         Vnext = V[:, mp_:mp_ + p]
         Snew = [taus[i] * (Hlast @ Zhat[i][mp_ - p:, :]) for i in range(nup)]
-        if k > 0:
+        Pk = deflation_basis(Hm, k, largest=True, align=align) if k > 0 else None
+        if Pk is not None and Pk.shape[1] > 0:
             # the deflated restart of Algorithm 1, with A^{-1} as the operator
-            Pk = deflation_basis(Hm, k, largest=True)
             kk = Pk.shape[1]
             Pk1 = np.zeros(((m_done + 1) * p, kk + p))
             Pk1[:mp_, :kk] = Pk
@@ -250,8 +278,11 @@ def psbfom(apply_Ainv, B, table, m=10, tol=1e-10, max_cycles=100, k=0, fixed_cyc
 
 
 # --------------------------------------------------------------------------- Algorithm 1
-def sbfom(apply_A, B, table, m=10, tol=1e-10, max_cycles=1000, fixed_cycles=None):
-    """Algorithm 1 (SBFOM, k = 0): the unpreconditioned shifted block FOM."""
+def sbfom(apply_A, B, table, m=10, tol=1e-10, max_cycles=1000, fixed_cycles=None, k=0, align=None):
+    """Algorithm 1 (SBFOM[-DR]): the unpreconditioned shifted block FOM.
+
+    k     : number of deflated Ritz vectors (0 = plain restart): the k smallest |theta| of H_m
+    align : keep a multiple of this many Ritz vectors (see deflation_basis)"""
     B = np.asarray(B, dtype=np.float64)
     n, p = B.shape
     taus = np.asarray(table["tau"])
@@ -263,12 +294,16 @@ def sbfom(apply_A, B, table, m=10, tol=1e-10, max_cycles=1000, fixed_cycles=None
     Rhat = [R.astype(complex) for _ in range(nup)]
     history = []
     cycles = 0
-    block_steps = 0
+    matvecs = 0
     converged = False
+    start_vectors = None
+    H0 = None
+    rhs_row0 = 0
     while True:
         cycles += 1
-        V, Ht, m_done, breakdown = block_arnoldi_ruhe(apply_A, V1, m)
-        block_steps += m_done
+        V, Ht, m_done, breakdown = block_arnoldi_ruhe(apply_A, V1, m, start_vectors, H0)
+        first = p if start_vectors is None else start_vectors.shape[1]
+        matvecs += (m_done + 1) * p - first
         mp_ = m_done * p
         Hm = Ht[:mp_, :mp_]
         Hlast = Ht[mp_:mp_ + p, mp_ - p:mp_]
@@ -276,7 +311,7 @@ def sbfom(apply_A, B, table, m=10, tol=1e-10, max_cycles=1000, fixed_cycles=None
         Snew = []
         for i in range(nup):
             rhs = np.zeros((mp_, p), dtype=complex)
-            rhs[:p, :] = Rhat[i]
+            rhs[rhs_row0:rhs_row0 + p, :] = Rhat[i]
             Zi = np.linalg.solve(Hm - taus[i] * np.eye(mp_), rhs)      # eq. (3.3)
             X[i] = X[i] + V[:, :mp_] @ Zi
             S = -(Hlast @ Zi[mp_ - p:, :])                             # eq. (35)
@@ -289,12 +324,26 @@ def sbfom(apply_A, B, table, m=10, tol=1e-10, max_cycles=1000, fixed_cycles=None
                 break
         elif converged or cycles >= max_cycles or breakdown:
             break
-        V1 = V[:, mp_:mp_ + p]
+        Pk = deflation_basis(Hm, k, largest=False, align=align) if k > 0 else None
+        if Pk is not None and Pk.shape[1] > 0:
+            # the deflated restart: V_new = V_{m+1} blkdiag(P_k, I_p), H_new = its projection;
+            # the residuals stay collinear with V_{m+1}, now the columns kk..kk+p-1
+            kk = Pk.shape[1]
+            Pk1 = np.zeros(((m_done + 1) * p, kk + p))
+            Pk1[:mp_, :kk] = Pk
+            Pk1[mp_:, kk:] = np.eye(p)
+            H0 = Pk1.T @ Ht @ Pk
+            start_vectors = V @ Pk1
+            rhs_row0 = kk
+            V1 = start_vectors[:, kk:kk + p]
+        else:
+            V1 = V[:, mp_:mp_ + p]
+            start_vectors, H0, rhs_row0 = None, None, 0
         Rhat = Snew
     Z = table["omega0"] * B
     for i in range(nup):
         Z = Z + 2.0 * np.real(omegas[i] * X[i])
-    return Z, {"cycles": cycles, "block_steps": block_steps, "matvecs": p * block_steps,
+    return Z, {"cycles": cycles, "block_steps": matvecs / p, "matvecs": matvecs,
                "residuals": history, "converged": converged, "X": X}
 
 

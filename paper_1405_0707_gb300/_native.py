@@ -18,6 +18,7 @@ EXPM_NUMERICAL = 4
 EXPM_CUDA_ERROR = 5
 EXPM_NO_MEMORY = 6
 EXPM_INTERNAL = 7
+EXPM_TIMEOUT = 8
 EXPM_OP_CONV_DIFF = 0
 EXPM_OP_TOEPLITZ_SYM = 1
 EXPM_PREC_FP64 = 0
@@ -31,7 +32,7 @@ EXPM_MAX_POLES = 16
 EXPORTS = ("expm_cf_coeffs", "expm_plan_create", "expm_plan_destroy", "expm_block",
            "expm_block_host", "expm_op_apply", "expm_prec_apply", "expm_arnoldi",
            "expm_plan_profile", "expm_plan_get_profile", "expm_status_str",
-           "expm_prec_apply_noalloc", "expm_block_batched", "expm_block_adjoint")
+           "expm_prec_apply_noalloc", "expm_block_batched", "expm_block_adjoint", "expm_ritz_basis")
 STAGES = ("gemm", "tridiag", "cgs", "reduce", "qr", "poles", "update", "other", "stencil")
 
 
@@ -44,7 +45,7 @@ class expm_op_desc(C.Structure):
 class expm_opts(C.Structure):
     _fields_ = [("m", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double),
                 ("precision", C.c_int32), ("fixed_cycles", C.c_int32), ("algorithm", C.c_int32),
-                ("certify", C.c_int32)]
+                ("certify", C.c_int32), ("nu_cf", C.c_int32), ("k_defl", C.c_int32)]
 
 
 class expm_info(C.Structure):
@@ -52,7 +53,7 @@ class expm_info(C.Structure):
                 ("converged", C.c_int32), ("breakdown", C.c_int32), ("npoles", C.c_int32),
                 ("resid", C.c_double * EXPM_MAX_POLES), ("normB", C.c_double),
                 ("algorithm", C.c_int32), ("normA_bound", C.c_double),
-                ("true_resid", C.c_double * EXPM_MAX_POLES)]
+                ("true_resid", C.c_double * EXPM_MAX_POLES), ("kept", C.c_int32)]
 
 
 _lib = None
@@ -103,6 +104,9 @@ def load(build_if_missing: bool = False):
     lib.expm_arnoldi.argtypes = [p, d, p, i64, i32, p, i64, p, i64]
     lib.expm_prec_apply_noalloc.restype = C.c_int
     lib.expm_prec_apply_noalloc.argtypes = [C.POINTER(expm_op_desc), d, p, i64, i32, p, i64, p]
+    lib.expm_ritz_basis.restype = C.c_int
+    lib.expm_ritz_basis.argtypes = [C.POINTER(d), i64, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(d), i64,
+                                    C.POINTER(C.c_int)]
     lib.expm_plan_profile.restype = C.c_int
     lib.expm_plan_profile.argtypes = [p, C.c_int]
     lib.expm_plan_get_profile.restype = C.c_int
@@ -222,3 +226,17 @@ def expm_prec_apply_noalloc(op, t, dV, ldv, p, dW, ldw, stream=0):
     """Allocation-free W = (tA)^{-1} V (no plan); see include/expm_block.h."""
     check(load().expm_prec_apply_noalloc(C.byref(op), t, C.c_void_p(dV), ldv, p, C.c_void_p(dW), ldw,
                                          C.c_void_p(stream)), "expm_prec_apply_noalloc")
+
+
+def expm_ritz_basis(Hm, k, largest, align):
+    """Host-only: the deflated restart's orthonormal Ritz basis P (mp x kept) of the mp x mp
+    array Hm; see include/expm_block.h."""
+    import numpy as np
+    H = np.asfortranarray(np.asarray(Hm, dtype=np.float64))
+    mp = H.shape[0]
+    P = np.zeros((mp, mp), order="F")
+    kept = C.c_int()
+    check(load().expm_ritz_basis(H.ctypes.data_as(C.POINTER(C.c_double)), mp, mp, int(k), int(bool(largest)),
+                                 int(align), P.ctypes.data_as(C.POINTER(C.c_double)), mp, C.byref(kept)),
+          "expm_ritz_basis")
+    return P[:, :kept.value].copy()

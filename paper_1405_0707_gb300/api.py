@@ -38,7 +38,8 @@ class Plan:
     (``Plan.toeplitz``) for tA = t T with T symmetric Toeplitz."""
 
     def __init__(self, sides, diff, vel, p_max, m=10, tol=1e-10, max_cycles=200,
-                 fixed_cycles=0, stream=None, algorithm=0, precision="fp64", certify=False, _op=None):
+                 fixed_cycles=0, stream=None, algorithm=0, precision="fp64", certify=False, nu=0,
+                 k_defl=0, _op=None):
         import torch
         if _op is None:
             sides = tuple(int(s) for s in sides)
@@ -60,6 +61,8 @@ class Plan:
         opts.fixed_cycles = int(fixed_cycles)
         opts.algorithm = int(algorithm)        # 0 auto, 1 SBFOM (Algorithm 1), 2 PSBFOM (Algorithm 2)
         opts.certify = 1 if certify else 0
+        opts.nu_cf = int(nu)                   # 0: the paper's degree 14
+        opts.k_defl = int(k_defl)              # 0: plain restart
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
         self.tol, self.max_cycles, self.algorithm, self.precision = tol, max_cycles, algorithm, precision

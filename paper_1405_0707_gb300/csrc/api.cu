@@ -1,10 +1,10 @@
 // api.cu -- C ABI entry points and the restart-cycle driver of Algorithm 2 (PSBFOM, k = 0).
 //
 // Host side of one call to expm_block:
-//   Step 1-2 (Algorithm 1, shared by Algorithm 2): X_i^0 = 0, R_i^0 = B = V_1 R  (Cholesky QR)
+//   start (Algorithms 1 and 2 alike): X_i^0 = 0, R_i^0 = B = V_1 R  (Cholesky QR)
 //   per cycle:
-//     Step 3: m block steps W = (tA)^{-1} V_j -> CGS2 -> Cholesky QR -> V_{j+1}, H~_m (eq. (4.5))
-//     Step 4: all projected systems in one launch (eq. (3236)), norms by eq. (49),
+//     block Arnoldi: m block steps W = (tA)^{-1} V_j -> CGS2 -> Cholesky QR -> V_{j+1}, H~_m (eq. (4.5))
+//     projected systems: all poles in one launch (eq. (3236)), norms by eq. (49),
 //             Z += V_{m+1} sum_i 2 Re(omega_i H~_m Z_i); restart V_1 <- V_{m+1}
 //     one device->host copy of the nu/2 residual norms + status flags, then the stop test
 //   Z = omega_0 B + Z_acc   (eq. (11) with the conjugate pairs folded)
@@ -108,7 +108,7 @@ expm_status qr_block(expm_plan* P, int p, double* out, int64_t ldo, bool withH, 
                                                    sm(P, kOffRi), nullptr, sm(P, kOffRt), Hq, P->ldH, hrow, hcol,
                                                    normsq, flags, P->W, ld, s, cgs_cols ? P->V : nullptr, ld,
                                                    cgs_cols, cgs_cols ? sm(P, kOffH) : nullptr,
-                                                   cgs_cols ? out : nullptr, ldo));
+                                                   (cgs_cols && P->qr_single) ? out : nullptr, ldo));
         LAUNCH(EXPM_STAGE_QR, launch_qr_mixed_rows(P->W, ld, p, n, P->nblk, G, P->part, P->ctr, 1, sm(P, kOffR),
                                                    sm(P, kOffRi), sm(P, kOffRt), sm(P, kOffRt2), Hq, P->ldH, hrow,
                                                    hcol, nullptr, flags, out, ldo, s));
@@ -392,13 +392,49 @@ int choose_algorithm(const expm_plan* P, double t) {
     return norm_bound(P, t) >= EXPM_AUTO_RATIO * tmax ? EXPM_ALG_PSBFOM : EXPM_ALG_SBFOM;
 }
 
-// One restart cycle: m block steps, the projected systems, the update and the restart copy,
-// then the device->host copy of the residual norms and flags (no synchronisation).
-expm_status issue_cycle(expm_plan* P, double t, int p, int alg) {
+// Restart prologue of a plan with deflation (the restart copy is then not fused into the
+// Z update): prologue 1 is the plain restart V_1 <- V_{m+1}; prologue 2 the deflated one,
+// V_new = V_{m+1} blkdiag(P_k, I_p): columns 0..kk-1 <- V_m P_k (FP64, in chunks of 16
+// columns), columns kk..kk+p-1 <- V_{m+1}, and H~ <- 0 with the host-formed leading block
+// P_{k+1}^T H~ P_k ((kk + p) x kk) in place.  P_k and that block come from pinned host buffers
+// filled after the previous cycle.
+expm_status restart_prologue(expm_plan* P, int p, int kk, int prologue) {
+    cudaStream_t s = P->stream;
+    const int mp = P->opts.m * p;
+    const int64_t n = P->n, ld = P->ld;
+    double* Vnext = P->V + (int64_t)mp * ld;
+    if (prologue == 1) {
+        LAUNCH(EXPM_STAGE_UPDATE, launch_copy(Vnext, ld, P->V, ld, n, p, s));
+        return EXPM_OK;
+    }
+    CK(cudaMemcpyAsync(P->Pkd, P->hPk, sizeof(double) * (size_t)mp * kk, cudaMemcpyHostToDevice, s));
+    LAUNCH(EXPM_STAGE_UPDATE, launch_zero(P->Vk, ld, n, kk, s));
+    for (int c0 = 0; c0 < kk; c0 += kRowsMaxP) {
+        const int pc = std::min(kRowsMaxP, kk - c0);
+        LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp, pc, n, P->Pkd + (size_t)mp * c0, P->Vk + (int64_t)c0 * ld,
+                                                  ld, 0, s, P->nblk, 0));
+    }
+    LAUNCH(EXPM_STAGE_UPDATE, launch_copy(Vnext, ld, P->V + (int64_t)kk * ld, ld, n, p, s));
+    LAUNCH(EXPM_STAGE_UPDATE, launch_copy(P->Vk, ld, P->V, ld, n, kk, s));
+    CK(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)P->ldH * P->opts.m * P->p_max, s));
+    CK(cudaMemcpy2DAsync(P->H, sizeof(double) * P->ldH, P->hHnew, sizeof(double) * P->ldH,
+                         sizeof(double) * (size_t)(kk + p), kk, cudaMemcpyHostToDevice, s));
+    return EXPM_OK;
+}
+
+// One restart cycle: the restart prologue (plans with deflation), the block steps, the
+// projected systems, the update and the restart copy, then the device->host copy of the
+// residual norms and flags (and of H~ when the next restart may deflate); no synchronisation.
+// kk > 0: the basis starts with kk kept Ritz vectors and the block steps begin at block kk/p.
+expm_status issue_cycle(expm_plan* P, double t, int p, int alg, int kk = 0, int prologue = 0) {
     cudaStream_t s = P->stream;
     const int m = P->opts.m, mp = m * p;
     const int64_t n = P->n, ld = P->ld;
-    for (int j = 0; j < m; ++j) {
+    if (prologue) {
+        expm_status st = restart_prologue(P, p, kk, prologue);
+        if (st != EXPM_OK) return st;
+    }
+    for (int j = kk / p; j < m; ++j) {
         expm_status st = block_step(P, t, j, p, alg);
         if (st != EXPM_OK) return st;
     }
@@ -406,7 +442,7 @@ expm_status issue_cycle(expm_plan* P, double t, int p, int alg) {
     LAUNCH(EXPM_STAGE_POLES, launch_poles(P->H, P->ldH, mp, p, P->npoles, tau_re, tau_re + EXPM_MAX_POLES,
                                           tau_re + 2 * EXPM_MAX_POLES, tau_re + 3 * EXPM_MAX_POLES,
                                           P->S, P->poles, P->Wc_slots, P->stat, flags_of(P->stat), alg, s,
-                                          P->opts.certify ? P->Zcert : nullptr));
+                                          P->opts.certify ? P->Zcert : nullptr, kk));
     LAUNCH(EXPM_STAGE_POLES, launch_combine2(P->H, P->ldH, mp, p, P->npoles, P->Wc_slots, sm(P, kOffWc), alg, s));
     if (P->opts.certify) {
         // every pole's X_i (real and imaginary columns) += V_{m+1} C, before the restart copy
@@ -415,17 +451,20 @@ expm_status issue_cycle(expm_plan* P, double t, int p, int alg) {
                                                  s, P->nblk));
     }
     // mixed path: the product V Wc in double-float on the FP32 pipe (FP64 accumulation into Z)
-    LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, 1, s, P->nblk,
-                                              P->opts.precision == EXPM_PREC_MIXED ? 1 : 0));
+    // (with deflation the restart happens in the next cycle's prologue, after V_m P_k)
+    const bool defl = P->opts.k_defl > 0;
+    LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, defl ? 0 : 1, s,
+                                              P->nblk, P->opts.precision == EXPM_PREC_MIXED ? 1 : 0));
     CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
+    if (defl) CK(cudaMemcpyAsync(P->hH, P->H, sizeof(double) * (size_t)P->ldH * mp, cudaMemcpyDeviceToHost, s));
     return EXPM_OK;
 }
 
 // Capture (once) and return the graph of one cycle for (alg, p, t); nullptr if capture is
 // not possible, in which case the caller launches directly.
-GraphEntry* graph_for(expm_plan* P, double t, int p, int alg) {
+GraphEntry* graph_for(expm_plan* P, double t, int p, int alg, int kk = 0, int prologue = 0) {
     for (auto& g : P->graphs)
-        if (g.alg == alg && g.p == p && g.t == t) return &g;
+        if (g.alg == alg && g.p == p && g.t == t && g.kk == kk && g.prologue == prologue) return &g;
     if (P->graphs.size() >= 16) return nullptr;
     cudaStream_t s = P->stream;
     const int64_t l0 = P->launches;
@@ -435,13 +474,15 @@ GraphEntry* graph_for(expm_plan* P, double t, int p, int alg) {
         cudaGetLastError();
         return nullptr;
     }
-    expm_status st = issue_cycle(P, t, p, alg);
+    expm_status st = issue_cycle(P, t, p, alg, kk, prologue);
     cudaGraph_t graph = nullptr;
     cudaError_t ec = cudaStreamEndCapture(s, &graph);
     GraphEntry e;
     e.alg = alg;
     e.p = p;
     e.t = t;
+    e.kk = kk;
+    e.prologue = prologue;
     e.launches = P->launches - l0;
     for (int k = 0; k < EXPM_NSTAGES; ++k) {
         e.stage_launches[k] = P->stage_launches[k] - sl0[k];
@@ -479,9 +520,12 @@ struct RunState {
     double normB = 0.0;
     expm_status result = EXPM_OK;
     GraphEntry* ge = nullptr;
+    int kk = 0;          // deflated restart: Ritz vectors kept for the next cycle
+    int prologue = 0;    // 0 first cycle, 1 plain restart, 2 deflated restart (plans with k_defl)
+    int steps = 0;       // block applications of the operator so far
 };
 
-// Steps 1-2 of the algorithm: R_i^0 = B = V_1 R for every pole; the cycle graph.
+// Start of the algorithm: R_i^0 = B = V_1 R for every pole; the cycle graph.
 expm_status run_begin(expm_plan* P, RunState& r) {
     cudaStream_t s = P->stream;
     r.alg = choose_algorithm(P, r.t);
@@ -500,9 +544,8 @@ expm_status run_begin(expm_plan* P, RunState& r) {
                                                flags_of(P->stat) + 2));
     else
         LAUNCH(EXPM_STAGE_OTHER, launch_init_S(sm(P, kOffRt), p, P->npoles, P->S, s));
-    // graph of one restart cycle, cached per (algorithm, p, t)
-    r.ge = nullptr;
-    if (P->use_graphs && !P->prof && P->stream != nullptr) r.ge = graph_for(P, r.t, p, r.alg);
+    r.kk = 0;
+    r.prologue = 0;
     return EXPM_OK;
 }
 
@@ -510,16 +553,66 @@ expm_status run_begin(expm_plan* P, RunState& r) {
 expm_status run_issue(expm_plan* P, RunState& r) {
     cudaStream_t s = P->stream;
     ++r.cycles;
+    r.steps += P->opts.m - r.kk / r.p;
+    // graph of one restart cycle, cached per (algorithm, p, t, restart kind)
+    r.ge = nullptr;
+    if (P->use_graphs && !P->prof && P->stream != nullptr) r.ge = graph_for(P, r.t, r.p, r.alg, r.kk, r.prologue);
     if (r.ge) {
         CK(cudaGraphLaunch(r.ge->exec, s));
         P->launches += r.ge->launches;
         for (int k = 0; k < EXPM_NSTAGES; ++k) P->stage_launches[k] += r.ge->stage_launches[k];
     } else {
-        expm_status st = issue_cycle(P, r.t, r.p, r.alg);
+        expm_status st = issue_cycle(P, r.t, r.p, r.alg, r.kk, r.prologue);
         if (st != EXPM_OK) return st;
     }
     CK(cudaEventRecord(P->cycle_ev, s));
     return EXPM_OK;
+}
+
+// The deflated restart's small dense work, on the host after a cycle (H~ is in hH): the
+// orthonormal Ritz basis P_k of H_m (expm_ritz_basis: Algorithm 2 keeps the largest |mu|,
+// Remark 4.1; Algorithm 1 the smallest |theta|; a multiple of p), the new leading block
+// P_{k+1}^T H~ P_k with P_{k+1} = blkdiag(P_k, I_p), and P_k in the chunked layout of the
+// device product.  Without a usable basis the next restart is the plain one.
+void prepare_deflation(expm_plan* P, RunState& r) {
+    const int m = P->opts.m, p = r.p, mp = m * p, ldH = P->ldH;
+    r.kk = 0;
+    r.prologue = 1;
+    const int kreq = std::min(P->opts.k_defl, (m - 1) * p);
+    if (kreq < 1) return;
+    std::vector<double> Pk((size_t)mp * mp);
+    int kept = 0;
+    if (expm_ritz_basis(P->hH, ldH, mp, kreq, r.alg == EXPM_ALG_PSBFOM ? 1 : 0, p, Pk.data(), mp, &kept) != EXPM_OK ||
+        kept < 1 || kept > std::min(P->kdefl_max, (m - 1) * p))
+        return;
+    // T = H~ P_k ((mp + p) x kept), then the leading block: rows < kept are P_k^T T, rows
+    // kept.. kept+p-1 the last block row of T
+    const int rows = mp + p;
+    std::vector<double> T((size_t)rows * kept, 0.0);
+    for (int j = 0; j < kept; ++j)
+        for (int b = 0; b < mp; ++b) {
+            const double pb = Pk[(size_t)j * mp + b];
+            if (pb == 0.0) continue;
+            const double* hc = P->hH + (size_t)b * ldH;
+            for (int a = 0; a < rows; ++a) T[(size_t)j * rows + a] += hc[a] * pb;
+        }
+    for (int j = 0; j < kept; ++j) {
+        double* out = P->hHnew + (size_t)j * ldH;
+        for (int i = 0; i < kept; ++i) {
+            double acc = 0.0;
+            for (int a = 0; a < mp; ++a) acc += Pk[(size_t)i * mp + a] * T[(size_t)j * rows + a];
+            out[i] = acc;
+        }
+        for (int q = 0; q < p; ++q) out[kept + q] = T[(size_t)j * rows + mp + q];
+    }
+    for (int c0 = 0; c0 < kept; c0 += kRowsMaxP) {
+        const int pc = std::min(kRowsMaxP, kept - c0);
+        double* dst = P->hPk + (size_t)mp * c0;
+        for (int a = 0; a < mp; ++a)
+            for (int c = 0; c < pc; ++c) dst[(size_t)a * pc + c] = Pk[(size_t)(c0 + c) * mp + a];
+    }
+    r.kk = kept;
+    r.prologue = 2;
 }
 
 // After a cycle's work has completed: flags, eq. (49) norms, the stop test.
@@ -537,6 +630,7 @@ void run_check(expm_plan* P, RunState& r) {
     r.converged = mx <= P->opts.tol * r.normB;
     r.done = (P->opts.fixed_cycles > 0) ? r.cycles >= P->opts.fixed_cycles
                                         : (r.converged || r.cycles >= P->opts.max_cycles);
+    if (!r.done && P->opts.k_defl > 0) prepare_deflation(P, r);
 }
 
 // Z = omega_0 B + Z_acc (eq. (11) with the conjugate pairs folded), certify, info.
@@ -572,8 +666,6 @@ expm_status run_finish(expm_plan* P, RunState& r, expm_info* info) {
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->cycles = r.cycles;
-        info->block_steps = r.cycles * m;
-        info->matvecs = (int64_t)r.cycles * m * p;
         info->converged = r.converged ? 1 : 0;
         info->npoles = P->npoles;
         info->breakdown = reinterpret_cast<const int*>(P->hpin + 24)[1] ? 1 : 0;
@@ -582,6 +674,10 @@ expm_status run_finish(expm_plan* P, RunState& r, expm_info* info) {
         info->algorithm = r.alg;
         info->normA_bound = norm_bound(P, r.t);
         for (int i = 0; i < P->npoles; ++i) info->true_resid[i] = true_res[i];
+        info->kept = r.kk;
+        // block applications of the operator: a deflated cycle starts at block kk / p
+        info->block_steps = r.steps;
+        info->matvecs = (int64_t)r.steps * p;
     }
     if (r.result != EXPM_OK) return r.result;
     if (P->opts.fixed_cycles > 0) return EXPM_OK;
@@ -661,6 +757,11 @@ void free_plan(expm_plan* P) {
     cudaFree(P->stat);
     cudaFree(P->ctr);
     cudaFree(P->dotpart);
+    cudaFree(P->Vk);
+    cudaFree(P->Pkd);
+    if (P->hH) cudaFreeHost(P->hH);
+    if (P->hPk) cudaFreeHost(P->hPk);
+    if (P->hHnew) cudaFreeHost(P->hHnew);
     if (P->hpin) cudaFreeHost(P->hpin);
     if (P->hdot) cudaFreeHost(P->hdot);
     if (P->cycle_ev) cudaEventDestroy(P->cycle_ev);
@@ -863,6 +964,7 @@ const char* expm_status_str(expm_status s) {
         case EXPM_NUMERICAL: return "numerical failure (NaN/Inf or non-positive Cholesky pivot)";
         case EXPM_CUDA_ERROR: return "CUDA error";
         case EXPM_NO_MEMORY: return "device allocation failed";
+        case EXPM_TIMEOUT: return "a bounded device-side wait ran out";
         default: return "internal error";
     }
 }
@@ -911,6 +1013,9 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         if (shm > 225 * 1024) return EXPM_INVALID_ARG;   // 227 KB opt-in minus static memory
     }
     if (opts->algorithm < EXPM_ALG_AUTO || opts->algorithm > EXPM_ALG_PSBFOM) return EXPM_INVALID_ARG;
+    if (opts->nu_cf != 0 && (opts->nu_cf < 2 || opts->nu_cf > 2 * EXPM_MAX_POLES || opts->nu_cf % 2 != 0))
+        return EXPM_INVALID_ARG;
+    if (opts->k_defl < 0 || (int64_t)opts->k_defl > (int64_t)(opts->m - 1) * p_max) return EXPM_INVALID_ARG;
     expm_plan* P = new (std::nothrow) expm_plan_s();
     if (!P) return EXPM_NO_MEMORY;
     P->op = *op;
@@ -923,6 +1028,10 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     {
         const char* ng = std::getenv("EXPM_DISABLE_GRAPHS");   // debugging switch
         P->use_graphs = !(ng && ng[0] == '1');
+        // test switch: "0" keeps the mixed path on the three-pass FP32 Cholesky-QR for every
+        // block (the fallback of the single accurate pass)
+        const char* sq = std::getenv("EXPM_QR_SINGLE_PASS");
+        P->qr_single = !(sq && sq[0] == '0');
     }
     int64_t n = 1;
     if (toeplitz) {
@@ -951,11 +1060,13 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     }
     P->n = n;
     P->ld = round_up(n, 32);
-    // CF table (Section 2), nu = 14 as in the paper's experiments (Section 5)
+    // CF table (Section 2): degree opts.nu_cf, by default nu = 14 as in the paper's
+    // experiments (Section 5)
     {
         std::vector<std::complex<double>> tau, om;
         double w0 = 0, sg = 0;
-        if (!expm_internal_cf_table(kNu, tau, om, w0, sg)) { delete P; return EXPM_INTERNAL; }
+        const int nu = opts->nu_cf ? opts->nu_cf : kNu;
+        if (!expm_internal_cf_table(nu, tau, om, w0, sg)) { delete P; return EXPM_INTERNAL; }
         P->npoles = (int)tau.size();
         for (int i = 0; i < P->npoles; ++i) {
             P->tau_re[i] = tau[i].real();
@@ -1017,6 +1128,15 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     ok = ok && dalloc(&P->dotpart, (size_t)dot_blocks() * p_max) &&
          cudaMallocHost(reinterpret_cast<void**>(&P->hdot), sizeof(double) * dot_blocks() * p_max) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&P->cycle_ev, cudaEventDisableTiming) == cudaSuccess;
+    if (opts->k_defl > 0) {
+        // the kept count never exceeds k_defl rounded up to a multiple of p, nor (m - 1) p
+        P->kdefl_max = std::min(opts->k_defl + p_max - 1, (m - 1) * p_max);
+        const size_t kd = (size_t)P->kdefl_max;
+        ok = ok && dalloc(&P->Vk, (size_t)ld * kd) && dalloc(&P->Pkd, (size_t)mpm * kd);
+        ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hH), sizeof(double) * (size_t)P->ldH * mpm) == cudaSuccess;
+        ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hPk), sizeof(double) * (size_t)mpm * kd) == cudaSuccess;
+        ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hHnew), sizeof(double) * (size_t)P->ldH * kd) == cudaSuccess;
+    }
     const bool mixed = opts->precision == EXPM_PREC_MIXED;
     if (!toeplitz) {
         // preconditioner tables: every axis but x is transformed

@@ -126,6 +126,7 @@ struct ToeplitzOp {
 struct GraphEntry {
     int alg = 0, p = 0;
     double t = 0.0;
+    int kk = 0, prologue = 0;   // deflated restart: kept Ritz vectors, kind of restart prologue
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;
     int64_t stage_launches[EXPM_NSTAGES] = {};
@@ -203,6 +204,14 @@ struct expm_plan_s {
     int ev_used = 0;
     // CUDA graphs of one restart cycle, keyed by (algorithm, p, t)
     bool use_graphs = false;
+    bool qr_single = true;     // mixed path: try the single accurate Cholesky-QR pass
+    // deflated restart (opts.k_defl > 0)
+    int kdefl_max = 0;         // columns of Vk and Pkd
+    double* Vk = nullptr;      // ld x kdefl_max: V_m P_k
+    double* Pkd = nullptr;     // m p_max x kdefl_max: P_k in chunks of 16 columns, each row-major
+    double* hH = nullptr;      // pinned: H~ after each cycle (ldH x m p_max)
+    double* hPk = nullptr;     // pinned: staging of Pkd
+    double* hHnew = nullptr;   // pinned: the leading (kk + p) x kk block of H~ after the restart
     std::vector<GraphEntry> graphs;
 };
 
@@ -263,7 +272,8 @@ cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* 
 cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          const double* tau_re, const double* tau_im, const double* om_re,
                          const double* om_im, double* S, double* work, double* Wc_slots,
-                         double* res, int* flags, int alg, cudaStream_t s, double* Zout = nullptr);
+                         double* res, int* flags, int alg, cudaStream_t s, double* Zout = nullptr,
+                         int kk = 0);
 cudaError_t launch_certify_coeffs(const double* H, int ldH, int mp, int p, int npoles, const double* Zs,
                                   double* C, int alg, cudaStream_t s);
 int true_resid_blocks(int64_t n);

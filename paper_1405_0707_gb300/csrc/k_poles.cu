@@ -10,7 +10,11 @@
 // Algorithm 1 (alg = 1): (H_m - tau_i I) Z_i = E_1 S_i (eq. (3.3)), S_i <- -H_{m+1,m} E_m^T Z_i
 // (eq. (35)), Wc = [sum_i 2 Re(omega_i Z_i); 0] (X_i - X_i^0 = V_m Z_i).
 // H_m is band upper Hessenberg with p sub-diagonals, so Gaussian elimination with partial
-// pivoting only looks at rows j..j+p of column j (blocked by p x p blocks, see k_poles).  The
+// pivoting only looks at rows j..j+p of column j (blocked by p x p blocks, see k_poles).
+// After a deflated restart that keeps kk Ritz vectors (a multiple of p), the leading kk
+// columns are dense down to row kk+p-1 (the projection of H~ onto the kept vectors) and the
+// right-hand side E S_i sits at rows kk..kk+p-1; the elimination of those columns then looks
+// at rows j..kk+p-1.  The
 // matrix lives in shared memory when (mp)^2 + mp p complex numbers fit, else in a global
 // workspace (L2-resident).
 #include "internal.h"
@@ -58,7 +62,7 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
                                                         double* __restrict__ S, double* __restrict__ work,
                                                         double* __restrict__ Y_slots, double* res,
                                                         int* flags, int use_smem, int h_in_smem, int alg,
-                                                        double* __restrict__ Zout) {
+                                                        double* __restrict__ Zout, int kk) {
     extern __shared__ double sm[];
     __shared__ cplx rdiag[kMaxMP];
     __shared__ double red[kPoleThreads];
@@ -89,15 +93,19 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
             const double d = (r == c ? 1.0 : 0.0);
             M[(size_t)r * mp + c] = (alg == 2) ? cplx{d - tau.re * h, -tau.im * h} : cplx{h - d * tau.re, -d * tau.im};
         }
+    // after a deflated restart the residual coordinates sit at rows kk .. kk+p-1
     for (int e = tid; e < mp * p; e += nt) {
         const int r = e / p, c = e % p;
-        X[e] = (r < p) ? Si[r * p + c] : cplx{0.0, 0.0};
+        X[e] = (r >= kk && r < kk + p) ? Si[(r - kk) * p + c] : cplx{0.0, 0.0};
     }
     __syncthreads();
     const int nbc = mp / p;
     for (int J = 0; J < nbc; ++J) {
         const int r0 = J * p;
-        const int rend = (J + 1 < nbc) ? r0 + 2 * p : r0 + p;   // panel rows r0 .. rend-1
+        // panel rows r0 .. rend-1: the band (one block below the diagonal block); the kk
+        // deflated columns of a deflated restart reach down to the block row of the old
+        // V_{m+1} (rows kk .. kk+p-1: H_{m+1,m} E_m^T P_k)
+        const int rend = min(mp, max(r0 + 2 * p, r0 < kk ? kk + p : 0));
         for (int jj = 0; jj < p; ++jj) {
             const int c = r0 + jj;
             if (warp == 0) {
@@ -165,8 +173,9 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
             }
         }
         __syncthreads();
-        if (rend > r0 + p)
-            for (int e = tid; e < p * ncol; e += nt) {   // M_J+1,c -= L_J+1,J U_J,c
+        const int nbelow = rend - r0 - p;              // rows below the diagonal block
+        if (nbelow > 0)
+            for (int e = tid; e < nbelow * ncol; e += nt) {   // M_below,c -= L_below,J U_J,c
                 const int a = e / ncol, q = e % ncol;
                 cplx* col;
                 size_t ld;
@@ -325,7 +334,7 @@ static size_t poles_h_bytes(int mp, int p) { return (size_t)(mp + p) * mp * size
 cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          const double* tau_re, const double* tau_im, const double* om_re,
                          const double* om_im, double* S, double* work, double* Y_slots,
-                         double* res, int* flags, int alg, cudaStream_t s, double* Zout) {
+                         double* res, int* flags, int alg, cudaStream_t s, double* Zout, int kk) {
     size_t shm = poles_smem_bytes(mp, p);
     int h_in = 0;
     if (shm > 0 && shm + poles_h_bytes(mp, p) <= kSmemLimit) {
@@ -334,7 +343,7 @@ cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
     }
     k_poles<<<npoles, kPoleThreads, shm, s>>>(H, ldH, mp, p, tau_re, tau_im, om_re, om_im, S, work,
                                               Y_slots, res, flags, poles_smem_bytes(mp, p) > 0 ? 1 : 0,
-                                              h_in, alg, Zout);
+                                              h_in, alg, Zout, kk);
     return cudaGetLastError();
 }
 

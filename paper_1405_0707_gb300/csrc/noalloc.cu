@@ -18,6 +18,7 @@
 // the temporary before reading it, so nothing carries over from the previous call and
 // nothing needs clearing.  Calls that overlap on the GPU (two streams, or two host threads
 // on one device) race on the array: the caller must order them.
+#include <cmath>
 #include <mutex>
 
 #include "internal.h"
@@ -58,12 +59,15 @@ extern "C" expm_status expm_prec_apply_noalloc(const expm_op_desc* op, double t,
                                                void* stream) {
     if (!op || !dV || !dW || dV == dW) return EXPM_INVALID_ARG;
     if (op->kind != EXPM_OP_CONV_DIFF || op->ndim < 1 || op->ndim > 2) return EXPM_INVALID_ARG;
-    if (!(op->diff > 0.0) || !(t > 0.0) || p < 1 || p > kMaxP) return EXPM_INVALID_ARG;
+    if (!(op->diff > 0.0) || !std::isfinite(op->diff)) return EXPM_INVALID_ARG;
+    if (!(t > 0.0) || !std::isfinite(t) || p < 1 || p > kMaxP) return EXPM_INVALID_ARG;
     Axis ax[2];
     int64_t n = 1;
     for (int d = 0; d < op->ndim; ++d) {
         const int N = op->side[d];
-        if (N < 1) return EXPM_INVALID_ARG;
+        // every side is bounded by the scratch size before any product is formed, so the
+        // layout arithmetic below stays far from int64 overflow
+        if (N < 1 || N > kScratchDoubles || !std::isfinite(op->vel[d])) return EXPM_INVALID_ARG;
         const double h = 1.0 / (N + 1);
         ax[d].N = N;
         ax[d].l = op->diff / (h * h) + op->vel[d] / (2.0 * h);

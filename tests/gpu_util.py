@@ -30,3 +30,16 @@ def cancellation_floor(tab, X, Z):
     sum (eq. (11)) can differ by this much however accurate each X_i is."""
     s = sum(2 * abs(o) * np.linalg.norm(x) for o, x in zip(tab["omega"], X))
     return np.finfo(float).eps * s / np.linalg.norm(Z)
+
+
+def closed_form_poles(sides, diff, vel, t, tab, B):
+    """X_i = (tA - tau_i I)^{-1} B for every pole with Im tau > 0, by the oracle's closed-form
+    eigen-expansion (diagonal similarity + DST-I; no Krylov iteration involved)."""
+    from oracle import operators as ops
+    return [ops.apply_function(sides, diff, vel, t, lambda lam, z=z: 1.0 / (lam - z), B)
+            for z in tab["tau"]]
+
+
+def closed_form_floor(sides, diff, vel, t, tab, B, Z):
+    """cancellation_floor with the X_i taken from the closed form (cheap at any size)."""
+    return cancellation_floor(tab, closed_form_poles(sides, diff, vel, t, tab, B), Z)

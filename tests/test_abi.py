@@ -121,3 +121,98 @@ def test_toeplitz_descriptor_checks():
     # an unknown operator kind
     op.kind = 7
     assert lib.expm_plan_create(C.byref(op), 2, C.byref(opts), None, C.byref(out)) == N.EXPM_INVALID_ARG
+
+
+def test_noalloc_rejects_bad_arguments_on_host(lib):
+    """The allocation-free apply rejects non-finite t, diff or velocity and sizes beyond its
+    fixed scratch before any device work (the device pointers below are never touched)."""
+    import ctypes as C
+    from paper_1405_0707_gb300 import _native as N
+
+    def call(sides, t=0.1, diff=0.1, vel=(1.0, 1.0), ld=None, p=2):
+        op = N.expm_op_desc()
+        op.kind, op.ndim, op.diff = N.EXPM_OP_CONV_DIFF, len(sides), diff
+        for d in range(3):
+            op.side[d] = sides[d] if d < len(sides) else 1
+            op.vel[d] = vel[d] if d < len(sides) else 0.0
+        n = int(np.prod(sides))
+        ld = n if ld is None else ld
+        return lib.expm_prec_apply_noalloc(C.byref(op), t, C.c_void_p(16), ld, p, C.c_void_p(32), ld, None)
+
+    inf, nan = float("inf"), float("nan")
+    assert call((64, 64), t=inf) == N.EXPM_INVALID_ARG
+    assert call((64, 64), t=nan) == N.EXPM_INVALID_ARG
+    assert call((64, 64), t=-1.0) == N.EXPM_INVALID_ARG
+    assert call((64, 64), diff=inf) == N.EXPM_INVALID_ARG
+    assert call((64, 64), vel=(nan, 0.0)) == N.EXPM_INVALID_ARG
+    assert call((64, 64), p=33) == N.EXPM_INVALID_ARG
+    assert call((1 << 21,), vel=(0.0,)) == N.EXPM_INVALID_ARG          # a side beyond the scratch
+    assert call((1 << 20, 1 << 20), vel=(0.0, 0.0)) == N.EXPM_INVALID_ARG   # tables beyond it
+    assert call((2 ** 31 - 1, 2 ** 31 - 1), vel=(0.0, 0.0)) == N.EXPM_INVALID_ARG
+    assert call((256, 256), p=12) == N.EXPM_INVALID_ARG                # 2 Ny^2 + Ny + 2n + n p > 2^20
+
+
+@pytest.mark.parametrize("largest", [True, False])
+def test_library_ritz_basis_matches_oracle(lib, largest):
+    """The library's host eigen-solver for the deflated restart (Hessenberg reduction, Francis
+    QR, Schur back substitution) against the oracle's deflation_basis (numpy's LAPACK eig),
+    both with the block-aligned selection: the same count and the same subspace.  Matrices: a
+    band Hessenberg H_m from the oracle's block Arnoldi on a nonsymmetric operator (complex
+    Ritz pairs), and a dense random matrix."""
+    from oracle import operators as ops, psbfom as ps
+    from paper_1405_0707_gb300 import _native as N
+    A = ops.cd_matrix((30, 26), 0.1, (3.0, -2.0), 1.0)
+    V1, _ = ps.qr_positive(np.random.default_rng(4).standard_normal((A.shape[0], 4)))
+    _, H, _, _ = ps.block_arnoldi_ruhe(ps.lu_inverse(A), V1, 10)
+    mats = [(H[:40, :40], 4), (np.random.default_rng(5).standard_normal((57, 57)), 3),
+            (np.random.default_rng(6).standard_normal((12, 12)), 1)]
+    for Hm, align in mats:
+        for k in (1, 5, 8, 17):
+            if k > Hm.shape[0]:
+                continue
+            P = N.expm_ritz_basis(Hm, k, largest, align)
+            Po = ps.deflation_basis(Hm, k, largest, align=align)
+            assert P.shape[1] == Po.shape[1], (Hm.shape, k, align, P.shape, Po.shape)
+            if P.shape[1] == 0:
+                continue
+            assert P.shape[1] % align == 0
+            assert np.linalg.norm(P.T @ P - np.eye(P.shape[1])) <= 1e-12
+            # same subspace: the projectors agree
+            assert np.linalg.norm(P @ P.T - Po @ Po.T) <= 1e-8, (Hm.shape, k, align)
+            # invariant under H_m
+            M = P.T @ Hm @ P
+            assert np.linalg.norm(Hm @ P - P @ M) <= 1e-10 * np.linalg.norm(Hm)
+
+
+def test_library_ritz_basis_known_spectrum(lib):
+    """Eigenvalues known by construction (real values and 2 x 2 rotation-scaling blocks under an
+    orthogonal similarity): the kept Ritz values are exactly the wanted ones."""
+    from paper_1405_0707_gb300 import _native as N
+    from tests.test_oracle_deflation import known_spectrum_matrix
+    H, _ = known_spectrum_matrix([9.0, 7.0, 3.0, 1.0], [(8.0, 1.0), (2.0, 5.0), (0.5, 0.5)], 3)
+    for (k, align, largest), want in [((2, 2, True), [9, 7]),
+                                      ((4, 2, True), [9, complex(8, 1), complex(8, -1), 7]),
+                                      ((3, 3, False), [complex(0.5, 0.5), complex(0.5, -0.5), 1])]:
+        P = N.expm_ritz_basis(H, k, largest, align)
+        got = np.sort_complex(np.linalg.eigvals(P.T @ H @ P))
+        assert np.allclose(got, np.sort_complex(np.asarray(want, dtype=complex)), atol=1e-10), got
+    # invalid arguments
+    with pytest.raises(N.ExpmError):
+        N.expm_ritz_basis(H, 0, True, 1)
+    with pytest.raises(N.ExpmError):
+        N.expm_ritz_basis(np.full((4, 4), np.nan), 1, True, 1)
+
+
+@pytest.mark.parametrize("nu", [10, 12, 16])
+def test_library_cf_table_other_degrees(lib, nu):
+    """expm_cf_coeffs for the degrees a plan may choose (opts.nu_cf) against the oracle's
+    stored tables of the same degree (two independent high-precision constructions)."""
+    from paper_1405_0707_gb300 import _native as N
+    tau, om, w0, sig = N.expm_cf_coeffs(nu)
+    tab = cf.load_table(nu=nu)
+    tau, om = np.array(tau), np.array(om)
+    for a, b in ((tau.real, tab["tau"].real), (tau.imag, tab["tau"].imag),
+                 (om.real, tab["omega"].real), (om.imag, tab["omega"].imag)):
+        assert np.all(np.abs(a - b) <= 2 * np.spacing(np.abs(b))), (nu, np.max(np.abs(a - b) / np.spacing(np.abs(b))))
+    assert abs(w0 - tab["omega0"]) <= 2 * np.spacing(abs(tab["omega0"]))
+    assert abs(sig - tab["sigma"]) <= 1e-12 * tab["sigma"]

@@ -204,7 +204,8 @@ def test_invariant_subspace_is_not_an_error(tab):
 def test_certify_true_residual_matches_eq49(tab, precision, sides, diff, vel, t, p, alg):
     """Certify mode recomputes ||B - (tA - tau_i I) X_i||_F in FP64 from the accumulated X_i
     (eq. (3)); it must equal the collinear-residual estimate of eq. (49) / eq. (365) that
-    drives the stop test, for both precisions, and must not change Z."""
+    drives the stop test, for both precisions, must not change Z, and must equal the explicit
+    residual of the oracle's X_i after the same number of cycles."""
     need_gpu()
     from paper_1405_0707_gb300 import Plan
     n = int(np.prod(sides))
@@ -217,6 +218,19 @@ def test_certify_true_residual_matches_eq49(tab, precision, sides, diff, vel, t,
     for i in range(7):
         est, true = ic.resid[i], ic.true_resid[i]
         assert abs(true - est) <= 1e-6 * est + 1e-11 * nb, (i, est, true)
+    # against the oracle: the same fixed cycles of its literal algorithm, then the explicit
+    # residual ||B - (tA - tau_i I) X_i||_F of its own X_i with its own sparse matrix
+    A = ops.cd_matrix(sides, diff, vel, t)
+    if alg == 2:
+        _, io = ps.psbfom(ps.lu_inverse(A), B, tab, m=5, fixed_cycles=3)
+    else:
+        _, io = ps.sbfom(ps.matvec(A), B, tab, m=5, fixed_cycles=3)
+    # the mixed path's FP32 projections perturb its unconverged iterate at the FP32 level,
+    # so its residuals agree with the FP64 oracle's to ~1e-6 rather than to FP64 rounding
+    rtol = 1e-6 if precision == "fp64" else 1e-4
+    for i, (z, X) in enumerate(zip(tab["tau"], io["X"])):
+        ro = np.linalg.norm(B - (A @ X - z * X))
+        assert abs(ic.true_resid[i] - ro) <= rtol * ro + 1e-11 * nb, (i, ic.true_resid[i], ro)
 
 
 def test_example_5_1a_replay_on_gpu(tab):
@@ -233,3 +247,23 @@ def test_example_5_1a_replay_on_gpu(tab):
     assert i2.converged and i1.converged
     assert i2.matvecs <= 123 and rel(to_np(Z2), ex) <= 5.76e-10
     assert i1.matvecs >= 6 * i2.matvecs and rel(to_np(Z1), ex) <= 4.5e-8
+
+
+@pytest.mark.parametrize("nu", [10, 16])
+def test_cf_degree_option(tab, nu):
+    """opts.nu_cf: the plan uses the CF table of that degree.  The result matches r_nu(tA) B
+    from the oracle's table of the same degree, and for nu = 10 it is measurably farther from
+    e^{tA} B than the degree-14 result (sigma_10 ~ 2e-10 against 1.8e-14)."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    tabn = cf.load_table(nu=nu)
+    sides, diff, vel, t, p = (37, 29), 0.1, (1.0, 1.0), 0.1, 3
+    n = int(np.prod(sides))
+    B = inputs.rhs(n, p, 61)
+    Z, info = Plan(sides, diff, vel, p_max=p, m=6, tol=1e-13, max_cycles=400, nu=nu).expm_block(t, to_dev(B))
+    assert info.converged == 1 and info.npoles == nu // 2
+    ref = ops.exact_r_of_A_B(sides, diff, vel, t, tabn, B)
+    assert rel(to_np(Z), ref) <= 1e-10, rel(to_np(Z), ref)
+    if nu == 10:
+        ref14 = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+        assert rel(ref, ref14) > 10 * rel(to_np(Z), ref)

@@ -76,14 +76,18 @@ def test_mixed_meets_metric_tolerance_on_bench_workload(tab, t):
     assert rel(to_np(Z32), ref) <= 1e-8
 
 
+@pytest.mark.parametrize("single_pass", ["1", "0"])
 @pytest.mark.parametrize("sides,p", [((70, 66), 1), ((70, 66), 5), ((256, 256), 8), ((97, 83), 12),
                                      ((97, 83), 16)])
-def test_mixed_arnoldi_relation_is_fp64_exact(sides, p):
+def test_mixed_arnoldi_relation_is_fp64_exact(sides, p, single_pass, monkeypatch):
     """The mixed block step (FP32 projections, double-float first update, FP32 second-pass
     correction, FP32-factor Cholesky-QR applied exactly) keeps the block Arnoldi relation
     (tA)^{-1} V_m = V_{m+1} H~_m (Section 3) to FP64 rounding, while V is orthonormal only to
-    the FP32 level.  W = (tA)^{-1} V_m comes from the plan's own inverse."""
+    the FP32 level.  W = (tA)^{-1} V_m comes from the plan's own inverse.  Both with the single
+    accurate Cholesky-QR pass (taken for these well-conditioned blocks) and with the plan
+    switch that keeps every block on the three-pass FP32 scheme it falls back to."""
     need_gpu()
+    monkeypatch.setenv("EXPM_QR_SINGLE_PASS", single_pass)
     from paper_1405_0707_gb300 import Plan
     n, m, t = int(np.prod(sides)), 6, 0.05
     V1, _ = ps.qr_positive(inputs.rhs(n, p, 8))
@@ -94,3 +98,55 @@ def test_mixed_arnoldi_relation_is_fp64_exact(sides, p):
     assert np.linalg.norm(W - Vn @ Hn) <= 1e-12 * np.linalg.norm(W)
     assert np.linalg.norm(Vn.T @ Vn - np.eye((m + 1) * p)) <= 1e-5
     assert np.all(Hn[np.tril_indices_from(Hn, -p - 1)] == 0.0)
+
+
+@pytest.mark.parametrize("alg", [1, 2])
+def test_mixed_single_pass_on_and_off_agree(tab, alg, monkeypatch):
+    """A converged mixed solve with the single accurate Cholesky-QR pass and with it switched
+    off (every block through the FP32 three-pass fallback): both match r(tA)B and each other."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    sides, diff, vel, t, p = (70, 66), 0.1, (1.0, -0.5), (0.02 if alg == 1 else 1.0), 6
+    n = int(np.prod(sides))
+    B = inputs.rhs(n, p, 81)
+    ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+    out = {}
+    for sp in ("1", "0"):
+        monkeypatch.setenv("EXPM_QR_SINGLE_PASS", sp)
+        Z, info = Plan(sides, diff, vel, p_max=p, m=6, tol=1e-12, max_cycles=400, algorithm=alg,
+                       precision="mixed").expm_block(t, to_dev(B))
+        assert info.converged == 1, sp
+        out[sp] = to_np(Z)
+        assert rel(out[sp], ref) <= 1e-9, (sp, rel(out[sp], ref))
+    assert rel(out["0"], out["1"]) <= 1e-9
+
+
+@pytest.mark.parametrize("delta", [1e-4, 1e-6])
+def test_mixed_block_nearly_dependent_mid_cycle(tab, delta):
+    """B = [b0, b1, (tA)^{-1} b0 + delta b2]: the first block step's W = (tA)^{-1} V_1 then has a
+    direction that lies in span(V_1) up to O(delta), so after the Gram-Schmidt passes its Gram
+    matrix has a pivot far below 1e-5 of the largest diagonal entry.  The mixed path must
+    reject the single accurate Cholesky-QR pass there and finish on the shifted FP32 passes
+    (on real data, in the middle of a cycle), and still match r(tA)B and the FP64 path."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    sides, diff, vel, t = (41, 35), 0.1, (1.0, 1.0), 1.0
+    n = int(np.prod(sides))
+    b = inputs.rhs(n, 3, 82)
+    Ainv = ps.lu_inverse(ops.cd_matrix(sides, diff, vel, t))
+    B = np.column_stack([b[:, 0], b[:, 1], Ainv(b[:, 0]) * 10.0 + delta * b[:, 2]])
+    # the deficiency of the first Krylov block, computed on the host: the smallest singular
+    # value of the projected W relative to its largest
+    V1, _ = ps.qr_positive(B)
+    W = np.column_stack([Ainv(V1[:, c]) for c in range(3)])
+    W = W - V1 @ (V1.T @ W)
+    sv = np.linalg.svd(W, compute_uv=False)
+    assert (sv[-1] / sv[0]) ** 2 < 1e-5
+    ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+    Zm, im = Plan(sides, diff, vel, p_max=3, m=6, tol=1e-12, max_cycles=300, algorithm=2,
+                  precision="mixed").expm_block(t, to_dev(B))
+    Zd, idd = Plan(sides, diff, vel, p_max=3, m=6, tol=1e-12, max_cycles=300,
+                   algorithm=2).expm_block(t, to_dev(B))
+    assert im.converged == 1 and idd.converged == 1
+    assert rel(to_np(Zm), ref) <= 1e-9, rel(to_np(Zm), ref)
+    assert rel(to_np(Zm), to_np(Zd)) <= 1e-9

@@ -96,3 +96,36 @@ def test_planted_mistakes_fail_the_pins(tab):
     for b in bad:
         _, e = _err_curve(b, 20001)
         assert np.abs(e).max() > 100 * tab["sigma"]
+
+
+def _err_curve_strings(tab, npts=400001):
+    """The error curve with the coefficients taken from their stored 25-digit strings in
+    extended precision (for nu = 16 the FP64 rounding of the residues alone is ~1e-14, far
+    above its sigma ~ 3e-16)."""
+    L = np.longdouble
+    w = np.linspace(-1, 1, npts, dtype=L)[1:]
+    x = 9 * (w - 1) / (w + 1)
+    r = np.full(x.shape, L(tab["omega0_str"]))
+    for (tr, ti), (orr, oi) in zip(tab["tau_str"], tab["omega_str"]):
+        dr = x - L(tr)
+        tiL = L(ti)
+        r += 2 * (L(orr) * dr - L(oi) * tiL) / (dr * dr + tiL * tiL)
+    return x, (r - np.exp(x)).astype(np.float64)
+
+
+@pytest.mark.parametrize("nu", [10, 12, 16])
+def test_other_degrees_are_near_best(nu):
+    """The stored tables of the degrees a plan may choose (nu_cf): error at most 1.1 sigma on
+    (-inf, 0], 2 nu + 2 alternations with extrema within 10 % of sigma, nu/2 poles in the upper
+    half-plane."""
+    tab = cf.load_table(nu=nu)
+    assert tab["nu"] == nu and len(tab["tau"]) == nu // 2 and np.all(tab["tau"].imag > 0)
+    _, e = _err_curve_strings(tab)
+    s = tab["sigma"]
+    assert np.abs(e).max() < 1.1 * s, (nu, np.abs(e).max(), s)
+    assert _alternations(e, 0.5 * s) == 2 * nu + 2
+    mask = np.abs(e) > 0.5 * s
+    ev = e[mask]
+    cuts = np.flatnonzero(np.sign(ev[1:]) != np.sign(ev[:-1])) + 1
+    ext = [np.abs(seg).max() for seg in np.split(ev, cuts)]
+    assert min(ext) > 0.9 * s and max(ext) < 1.1 * s

@@ -3,8 +3,9 @@
 Some callers cannot call cudaMalloc (their own pool allocator owns the device memory, or a
 latency-critical loop must not enter the CUDA allocator); this entry point serves them with
 a fixed scratch array inside the library instead of a plan.  Its output must match the
-plan-based expm_prec_apply on two calls in a row (the second call reuses the scratch that
-the first call filled, with a different operator and shape).  Collected last on purpose.
+plan-based expm_prec_apply and the oracle's sparse LU solve on consecutive calls (each call
+reuses the scratch that the one before filled, with a different operator and shape; the
+1-D call follows a larger 2-D one).  Collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -25,14 +26,18 @@ def _desc(sides, diff, vel):
     return op
 
 
-def test_noalloc_matches_plan_apply_on_two_calls():
+def test_noalloc_matches_plan_apply_and_oracle_on_consecutive_calls():
     torch = need_gpu()
+    from oracle import operators as ops, psbfom as ps
     from paper_1405_0707_gb300 import Plan, colmajor
     from paper_1405_0707_gb300 import _native as N
-    calls = [((256, 256), 0.1, (1.0, 1.0), 1e-1, 8), ((37, 29), 0.1, (1.0, -0.5), 1e-2, 3)]
+    # the 1-D call comes after a larger 2-D call has filled the scratch
+    calls = [((256, 256), 0.1, (1.0, 1.0), 1e-1, 8), ((37, 29), 0.1, (1.0, -0.5), 1e-2, 3),
+             ((2000,), 1.0, (0.0,), 1.0, 4)]
     for k, (sides, diff, vel, t, p) in enumerate(calls):
         n = int(np.prod(sides))
-        V = to_dev(inputs.rhs(n, p, 500 + k))
+        Vh = inputs.rhs(n, p, 500 + k)
+        V = to_dev(Vh)
         ref = to_np(Plan(sides, diff, vel, p_max=p, m=2).prec_apply(t, V))
         W = colmajor(n, p)
         W.fill_(float("nan"))
@@ -43,6 +48,16 @@ def test_noalloc_matches_plan_apply_on_two_calls():
         got = to_np(W)
         assert np.all(np.isfinite(got))
         assert rel(got, ref) <= 1e-13, (k, rel(got, ref))
+        # against the oracle's sparse LU solve (the paper's "LU once and for all"); the
+        # transform path's backward error grows with the diagonal similarity's condition
+        # number along the transformed axis
+        Ainv = ps.lu_inverse(ops.cd_matrix(sides, diff, vel, t))
+        lu = np.column_stack([Ainv(Vh[:, c]) for c in range(p)])
+        kappa = 1.0
+        for d in range(1, len(sides)):
+            _, dp, _ = ops.axis_eig(sides[d], diff, vel[d], t)
+            kappa *= dp.max() / dp.min()
+        assert rel(got, lu) <= 1e-13 * max(1.0, kappa) + 1e-13, (k, rel(got, lu))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
