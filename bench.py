@@ -46,6 +46,8 @@ sys.path.insert(0, ROOT)
 METRIC = "e^{tA}B RHS-columns/sec at rel.err≤1e-8 vs plain FP64 GPU path; SpMM HBM GB/s"
 UNIT = "RHS-columns/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070   # SMs x FP64 FMA/clk/SM x flop/FMA x GHz = 1.259e3 GF/s
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x flop/FMA x GHz = 80.5e3 GF/s
+# both reproducible on the device with `python bench.py --component fmapeak` (expm_peak_fma)
 L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF = {"gemm": "k_gemm (DST-I transforms of the exact inverse, FP64)",
              "cgs": "k_proj/k_update (block CGS2 row passes, FP64)",
@@ -151,9 +153,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cd2d-256")
+    ap.add_argument("--workload", default="batched3d-64")
+    ap.add_argument("--k-defl", type=int, default=0, help="deflated restart: Ritz vectors kept (0 = plain)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--component", default=None, choices=[None, "prec", "stencil", "expm", "step"],
+    ap.add_argument("--component", default=None, choices=[None, "prec", "stencil", "expm", "step", "fmapeak"],
                     help="time one entry point of the library on the workload's shapes "
                          "(used for the ncu captures) instead of the full bench")
     ap.add_argument("--reps", type=int, default=5)
@@ -231,6 +234,9 @@ def make_plan(w, precision, stream=None, **kw):
     from paper_1405_0707_gb300 import Plan, inputs
     args = dict(p_max=w["p"], m=w["m"], tol=w["tol"], max_cycles=400, stream=stream, precision=precision)
     args.update(kw)
+    args.setdefault("k_defl", w.get("k_defl", 0))
+    if "frac" in w:
+        return Plan.toeplitz(inputs.fractional_column(w["n"], w["frac"], w["d"]), w["n"], **args)
     if "n" in w:
         return Plan.toeplitz(inputs.toeplitz_column(w["bw"], w["c"]), w["n"], **args)
     return Plan(w["sides"], w["diff"], w["vel"], **args)
@@ -496,9 +502,54 @@ def oracle_instance(d, w, alg=None):
     return time.perf_counter() - t0, d["p"], info
 
 
+def batched_gate(Zm, Z64, Bd):
+    """The metric's criterion per instance: rel.err <= 1e-8 against the plain FP64 GPU path
+    where relative accuracy is meaningful (||Z_64|| >= 1e-6 ||B||); the others (t near 1: the
+    result decays like e^{-3 pi^2 t}, down to ~1e-14 ||B||, where the partial-fraction sum's
+    rounding floor is ~1e-16 ||B||) are held to ||Z - Z_64|| <= 1e-12 ||B|| and listed."""
+    import torch
+    rel, floor = [], []
+    for k, (a, b, B) in enumerate(zip(Zm, Z64, Bd)):
+        nz, nb = float(torch.linalg.norm(b)), float(torch.linalg.norm(B))
+        e = float(torch.linalg.norm(a - b))
+        if nz >= 1e-6 * nb:
+            rel.append((k, e / nz))
+        else:
+            floor.append((k, nz / nb, e / nb))
+    ok = all(e <= 1e-8 for _, e in rel) and all(e <= 1e-12 for _, _, e in floor)
+    return ok, rel, floor
+
+
+def batched_cpu_baseline(inst, w, cycles, algs, budget_s=25.0):
+    """The oracle on a bounded sample of the batched workload: complete solves of instances in
+    order of their estimated oracle cost, while the estimate stays within ~budget_s (at least
+    one).  Algorithm 1 instances first (sparse products only; Algorithm 2's sparse LU of a 3-D
+    operator costs a minute), then by n p x the GPU's cycle count.  Cheap instances first, so
+    the rate flatters the oracle; the sample is named."""
+    import numpy as np
+    order = sorted(range(len(inst)), key=lambda k: (algs[k] == 2, np.prod(inst[k]["sides"]) * inst[k]["p"] * cycles[k]))
+    est_rate = None
+    tot, pc, done = 0.0, 0, []
+    for k in order:
+        d = inst[k]
+        cost = np.prod(d["sides"]) * d["p"] * cycles[k]
+        if done and est_rate and tot + cost / est_rate > budget_s:
+            break
+        dt, p_, info = oracle_instance(d, w, algs[k])
+        tot += dt
+        pc += p_
+        est_rate = sum(np.prod(inst[j]["sides"]) * inst[j]["p"] * cycles[j] for j in [x["k"] for x in done] + [k]) / tot
+        done.append({"k": k, "sides": list(d["sides"]), "t": round(d["t"], 5), "p": p_, "s": round(dt, 2),
+                     "cycles": info["cycles"]})
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": round(pc / tot, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"complete oracle solves (numpy/scipy, default threads) of {len(done)} of the "
+                      f"{len(inst)} instances, cheapest first by n p cycles: {done}"}
+
+
 def run_batched(args):
     """The 64-instance 3-D workload: one expm_block_batched call per step over all instances
-    (each plan on its own stream), mixed precision, gated against the FP64 path."""
+    (each plan on its own stream), mixed precision, gated per instance against the FP64 path."""
     import numpy as np
     import torch
 
@@ -520,7 +571,7 @@ def run_batched(args):
     streams = [torch.cuda.Stream(device=dev) for _ in inst]
     main = torch.cuda.current_stream(dev)
     plans = {prec: [Plan(d["sides"], d["diff"], d["vel"], p_max=d["p"], m=w["m"], tol=w["tol"], max_cycles=400,
-                         stream=st, precision=prec) for d, st in zip(inst, streams)]
+                         stream=st, precision=prec, k_defl=args.k_defl) for d, st in zip(inst, streams)]
              for prec in ("mixed", "fp64")}
     ns = [int(np.prod(d["sides"])) for d in inst]
     ps = [d["p"] for d in inst]
@@ -535,17 +586,6 @@ def run_batched(args):
 
     def step(prec, Z=None):
         return expm_block_batched(plans[prec], ts, Bd, Z if Z is not None else Zd)
-
-    def step_host(prec):
-        for i, st in enumerate(streams):
-            with torch.cuda.stream(st):
-                Bd[i].copy_(hB[i], non_blocking=True)
-        expm_block_batched(plans[prec], ts, Bd, Zd)
-        for i, st in enumerate(streams):
-            with torch.cuda.stream(st):
-                hZ[i].copy_(Zd[i], non_blocking=True)
-        for st in streams:
-            st.synchronize()
 
     def timed(fn, k):
         tot = 0.0
@@ -570,42 +610,44 @@ def run_batched(args):
             pg.barrier()
         return tot, wall
 
-    # accuracy gate (untimed): each mixed instance against the FP64 path
+    # accuracy gate of the metric (untimed): every mixed instance against the FP64 path
     Z64 = [colmajor(n, p, device=dev) for n, p in zip(ns, ps)]
     step("fp64", Z64)
     _, infos = step("mixed")
     torch.cuda.synchronize()
-    errs, floors = [], []
-    for a, b, B in zip(Zd, Z64, Bd):
-        e = float(torch.linalg.norm(a - b))
-        errs.append(e / max(float(torch.linalg.norm(b)), 1e-300))
-        floors.append(e <= 1e-8 * float(torch.linalg.norm(b)) + 1e-12 * float(torch.linalg.norm(B)))
-    mixed_ok = all(floors)
+    mixed_ok, rel_g, floor_g = batched_gate(Zd, Z64, Bd)
+    del Z64
     head = "mixed" if mixed_ok else "fp64"
     res = {}
-    for prec in ("fp64", "mixed"):
-        for _ in range(max(1, args.warmup)):
+    # the headline (mixed) path is timed for exactly --steps steps; the FP64 reference path
+    # (3.5x slower) for min(--steps, 3)
+    for prec, k in ((head, args.steps), ("fp64" if head == "mixed" else "mixed", min(args.steps, 3))):
+        for _ in range(max(1, args.warmup if prec == head else 1)):
             _, infos = step(prec)
         l0 = sum(pl.get_profile()[1] for pl in plans[prec])
         with ClockSampler(local) as clk:
-            ms, wall = timed(lambda: step(prec), args.steps)
+            ms, wall = timed(lambda: step(prec), k)
         l1 = sum(pl.get_profile()[1] for pl in plans[prec])
-        res[prec] = {"ms": ms, "wall": wall, "launches": l1 - l0, "clocks": clk.summary(),
+        res[prec] = {"ms": ms, "wall": wall, "steps": k, "launches": l1 - l0, "clocks": clk.summary(),
                      "cycles": [int(i.cycles) for i in infos], "algs": [int(i.algorithm) for i in infos],
-                     "converged": all(int(i.converged) for i in infos)}
-    ms_e2e, _ = timed(lambda: step_host(head), max(1, args.steps // 2))
-    e2e_steps = max(1, args.steps // 2)
-    # per-stage event timing (graphs off while profiling; the 64 streams overlap, so each
-    # kernel's event-timed duration includes time shared with other instances)
-    for pl in plans[head]:
-        pl.profile(True)
-    step(head)
-    torch.cuda.synchronize()
+                     "converged": all(int(i.converged) for i in infos),
+                     "kept": [int(i.kept) for i in infos]}
+    # end to end through the C ABI with host buffers (expm_block_batched_host: the copies of B
+    # and Z inside the call, overlapped per instance with the other instances' cycles)
+    e2e_steps = max(1, args.steps // 4)
+    expm_block_batched(plans[head], ts, hB, hZ)
+    ms_e2e, _ = timed(lambda: expm_block_batched(plans[head], ts, hB, hZ), e2e_steps)
+    # per-kernel-class event timing: one serial pass (each instance alone on the GPU, graphs off
+    # while profiling), so a class's event time is its own kernels' time
     stages = {}
-    for pl in plans[head]:
+    for pl, t_, B_, Z_ in zip(plans[head], ts, Bd, Zd):
+        pl.profile(True)
+        with torch.cuda.stream(pl.stream):
+            pl.expm_block(t_, B_, Z_)
+        pl.stream.synchronize()
         prof, _ = pl.get_profile()
-        for k, (msk, nk) in prof.items():
-            a_ = stages.setdefault(k, [0.0, 0])
+        for k_, (msk, nk) in prof.items():
+            a_ = stages.setdefault(k_, [0.0, 0])
             a_[0] += msk
             a_[1] += nk
         pl.profile(False)
@@ -619,26 +661,36 @@ def run_batched(args):
     value = world * args.steps * cols / (t_max / 1e3)
     e2e = world * e2e_steps * cols / (t_e2e / 1e3)
     cyc, algs = res[head]["cycles"], res[head]["algs"]
-    # algorithmic work of the dominant stage, summed over instances
+    # algorithmic work of every class, summed over instances
     work = {}
     for d, c, al in zip(inst, cyc, algs):
         wi = dict(sides=d["sides"], diff=d["diff"], vel=d["vel"], p=d["p"], m=w["m"])
-        for k, v in algorithmic_work(wi, d["p"], w["m"], {d["t"]: c}, {d["t"]: al}).items():
-            a_ = work.setdefault(k, [0.0, 0.0])
+        for k_, v in algorithmic_work(wi, d["p"], w["m"], {d["t"]: c}, {d["t"]: al},
+                                      fused=(head == "mixed")).items():
+            a_ = work.setdefault(k_, [0.0, 0.0])
             a_[0] += v[0]
             a_[1] += v[1]
-    dom = max((k for k in stages if k in work and work[k][0] > 0), key=lambda k: stages[k][0])
-    sec = stages[dom][0] / 1e3
-    fl_s, by_s = work[dom][0] / sec, work[dom][1] / sec
-    if fl_s / (FP64_PEAK_TFLOPS * 1e9) >= by_s / (HBM_PEAK_GBS * 1e9):
-        roof = {"kernel": KERNEL_OF[dom], "bound": "alu", "achieved": round(fl_s / 1e12, 4),
-                "peak": round(FP64_PEAK_TFLOPS / 1e3, 4), "unit": "TFLOP/s",
-                "frac": round(fl_s / (FP64_PEAK_TFLOPS * 1e9), 4)}
-    else:
-        roof = {"kernel": KERNEL_OF[dom], "bound": "hbm", "achieved": round(by_s / 1e9, 1), "peak": HBM_PEAK_GBS,
-                "unit": "GB/s", "frac": round(by_s / 1e9 / HBM_PEAK_GBS, 4)}
-    roof.update({"traffic": None, "note": "summed event time of this kernel class over the 64 concurrent "
-                                          "instances (overlapping streams: a conservative rate)"})
+    roofs = {}
+    for k_, (fl, by) in work.items():
+        msk, nk = stages.get(k_, (0.0, 0))
+        if nk == 0 or msk <= 0 or by <= 0:
+            continue
+        sec = msk / 1e3
+        roofs[k_] = {"launches": nk, "ms_serial": round(msk, 3), "launch_ms": msk / nk,
+                     "gbs": by / sec / 1e9, "frac_hbm": by / sec / 1e9 / HBM_PEAK_GBS,
+                     "tflops": fl / sec / 1e12}
+        if head != "mixed" or k_ not in ("cgs", "qr", "update"):
+            roofs[k_]["frac_fp64_alu"] = fl / sec / 1e12 / (FP64_PEAK_TFLOPS / 1e3)
+    dom = max(roofs, key=lambda k_: roofs[k_]["ms_serial"])
+    r = roofs[dom]
+    label = KERNEL_OF.get(dom + "_mixed", KERNEL_OF[dom]) if head == "mixed" else KERNEL_OF[dom]
+    roof = {"kernel": label, "bound": "hbm", "achieved": round(r["gbs"], 1), "peak": HBM_PEAK_GBS,
+            "unit": "GB/s", "frac": round(r["frac_hbm"], 4), "traffic": traffic_record(dom + "_batched"),
+            "bytes_per_launch": work[dom][1] / r["launches"], "launch_ms": r["launch_ms"],
+            "note": "algorithmic bytes of the class summed over the 64 instances (each operand read once "
+                    "per pass) / its event-timed duration in one serial pass over the instances; peak = "
+                    "measured HBM copy rate"}
+    rel_max = max(e for _, e in rel_g) if rel_g else None
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
@@ -646,34 +698,33 @@ def run_batched(args):
         "dtype": "f32+f64" if head == "mixed" else "f64",
         "data": "synthetic (seeded instance list and N(0,1) right-hand sides)",
         "config": {"workload": args.workload, "instances": len(inst), "n_range": [min(ns), max(ns)],
-                   "columns_per_step": cols, "m": w["m"], "tol": w["tol"], "nu": 14, "precision": head,
-                   "max_rel_err_vs_fp64_gpu": max(errs), "all_within_1e-8_or_floor": mixed_ok,
+                   "p_range": [min(ps), max(ps)], "columns_per_step": cols, "m": w["m"], "tol": w["tol"],
+                   "nu": 14, "precision": head, "k_defl": args.k_defl,
+                   "accuracy_vs_fp64_gpu": {
+                       "criterion": "rel.err <= 1e-8 where ||Z_64|| >= 1e-6 ||B||; else ||Z - Z_64|| <= 1e-12 ||B||",
+                       "passed": mixed_ok, "relative_instances": len(rel_g), "max_rel_err": rel_max,
+                       "floor_instances": [{"k": k_, "z_over_b": nzb, "err_over_b": eb} for k_, nzb, eb in floor_g]},
                    "cycles_total": sum(cyc), "algorithm_counts": {"1": algs.count(1), "2": algs.count(2)},
                    "converged": res[head]["converged"], "streams": len(streams),
-                   "l2": "flushed before every timed step (512 MB write)",
+                   "l2": "inputs far larger than L2 (1.3 GB of B); a 512 MB buffer is also written before "
+                         "every timed step",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * sum(n * p for n, p in zip(ns, ps)),
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "steps": e2e_steps,
+                "entry_point": "expm_block_batched_host",
+                "h2d_bytes_per_step": 8 * sum(n * p for n, p in zip(ns, ps)),
                 "d2h_bytes_per_step": 8 * sum(n * p for n, p in zip(ns, ps))},
         "gpu_launches": int(res[head]["launches"]) * world,
         "roofline": roof,
-        "stages": {k: {"ms_summed_over_instances": round(v[0], 3), "launches": v[1]} for k, v in stages.items()},
+        "rooflines": {k_: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                      for k_, v in roofs.items()},
         "clocks": res[head]["clocks"],
         "wall_s_timed": round(res[head]["wall"], 3),
-        "fp64_path": {"value": round(world * args.steps * cols / (t64 / 1e3), 3), "unit": UNIT,
-                      "ms_per_step": round(t64 / args.steps, 4), "clocks": res["fp64"]["clocks"]},
+        "fp64_path": {"value": round(world * res["fp64"]["steps"] * cols / (t64 / 1e3), 3), "unit": UNIT,
+                      "steps": res["fp64"]["steps"], "ms_per_step": round(t64 / res["fp64"]["steps"], 4),
+                      "cycles_total": sum(res["fp64"]["cycles"]), "clocks": res["fp64"]["clocks"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        small = sorted(inst, key=lambda d: np.prod(d["sides"]))[:1]
-        tot, pc, done = 0.0, 0, []
-        for d in small:
-            dt, p_, info = oracle_instance(d, w)
-            tot += dt
-            pc += p_
-            done.append({"sides": d["sides"], "t": d["t"], "p": p_, "s": round(dt, 2), "cycles": info["cycles"]})
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-        line["cpu_baseline"] = {"value": round(pc / tot, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"complete oracle solve of the smallest instance {done} (the others "
-                                          "are larger, so this rate flatters the oracle)"}
+        line["cpu_baseline"] = batched_cpu_baseline(inst, w, cyc, algs)
     elif rank == 0:
         line["cpu_baseline"] = None
     for lst in plans.values():
@@ -884,9 +935,21 @@ def run_reference_toeplitz(args, w, t, alg):
 
 
 def run_component(args):
-    """Time one library entry point on the workload's shapes (for ncu captures)."""
+    """Time one library entry point on the workload's shapes (for ncu captures); fmapeak: the
+    FP64 and FP32 FMA throughput probes behind the ALU roofline peaks."""
     import numpy as np
     import torch
+
+    if args.component == "fmapeak":
+        from paper_1405_0707_gb300 import _native as N
+        N.load()
+        torch.cuda.init()
+        out = {"component": "fmapeak", "fp64_tflops": N.expm_peak_fma(0, 1 << 15),
+               "fp32_tflops": N.expm_peak_fma(1, 1 << 17),
+               "nominal": {"fp64_tflops": round(FP64_PEAK_TFLOPS / 1e3, 4),
+                           "fp32_tflops": round(FP32_PEAK_TFLOPS / 1e3, 2)}}
+        print(json.dumps(out))
+        return
 
     from paper_1405_0707_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]

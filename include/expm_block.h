@@ -258,6 +258,15 @@ expm_status expm_block_batched(expm_plan* const* plans, int count, const double*
                                const double* const* dB, const int64_t* ldb, const int* p,
                                double* const* dZ, const int64_t* ldz, expm_info* info);
 
+/* expm_block_batched_host -- expm_block_batched with HOST buffers: hB[i] (n_i x p[i], ldb[i])
+ * is copied to plans[i]'s device staging buffer on the plan's stream before the instance's
+ * first cycle, and Z back to hZ[i] (ldz[i]) after its last, so one instance's copies overlap
+ * with the others' cycles.  hB[i] and hZ[i] are ordinary (preferably page-locked) host
+ * memory.  Same errors as expm_block_batched. */
+expm_status expm_block_batched_host(expm_plan* const* plans, int count, const double* t,
+                                    const double* const* hB, const int64_t* ldb, const int* p,
+                                    double* const* hZ, const int64_t* ldz, expm_info* info);
+
 /* ---------------------------------------------------------------------------------
  * expm_block_adjoint -- the adjoint of Z = r(tA) B for a loss L with G = dL/dZ:
  *   dGB = dL/dB = r(tA)^T G = r(tA^T) G  (r has real coefficients), computed by the same
@@ -352,6 +361,13 @@ typedef enum {
 expm_status expm_plan_profile(expm_plan* plan, int enable);
 expm_status expm_plan_get_profile(expm_plan* plan, double* stage_ms, int64_t* stage_launches,
                                   int nstages, int64_t* total_launches);
+
+/* expm_peak_fma -- measurement support for the roofline denominators (not part of the
+ * paper's method): the device's FMA throughput, kind 0 = FP64, 1 = FP32, from one launch of
+ * eight independent FMA chains per thread on every SM (iters FMAs per chain), timed with
+ * CUDA events on the stream.  tflops: host out, 2 flops per FMA.  Synchronises the stream.
+ * Errors: EXPM_INVALID_ARG, EXPM_CUDA_ERROR. */
+expm_status expm_peak_fma(int kind, int64_t iters, double* tflops, void* stream);
 
 const char* expm_status_str(expm_status s);
 

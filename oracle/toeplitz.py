@@ -89,3 +89,14 @@ def gsf_apply(x, V, t=1.0):
     u1 = lower_toeplitz_matvec(x, lower_toeplitz_matvec(x, V, transpose=True))
     u2 = lower_toeplitz_matvec(xh, lower_toeplitz_matvec(xh, V, transpose=True))
     return (u1 - u2) / (t * x[0])
+
+
+# --------------------------------------------------------------------------- large-norm regime
+def eig_function(a, B, f, t=1.0):
+    """f(tT) B for the symmetric Toeplitz T with first column a, by the eigendecomposition
+    T = Q diag(lambda) Q^T (scipy eigh; small n only): the exact truth where the Taylor series
+    does not converge (||tT|| ~ 1e9 in Example 5.4's regime).  f maps an eigenvalue array to an
+    array of the same shape."""
+    lam, Q = sl.eigh(sl.toeplitz(a))
+    B = np.asarray(B, dtype=np.float64)
+    return Q @ (np.asarray(f(t * lam))[:, None] * (Q.T @ B))

@@ -32,7 +32,8 @@ EXPM_MAX_POLES = 16
 EXPORTS = ("expm_cf_coeffs", "expm_plan_create", "expm_plan_destroy", "expm_block",
            "expm_block_host", "expm_op_apply", "expm_prec_apply", "expm_arnoldi",
            "expm_plan_profile", "expm_plan_get_profile", "expm_status_str",
-           "expm_prec_apply_noalloc", "expm_block_batched", "expm_block_adjoint", "expm_ritz_basis")
+           "expm_prec_apply_noalloc", "expm_block_batched", "expm_block_adjoint", "expm_ritz_basis",
+           "expm_block_batched_host", "expm_peak_fma")
 STAGES = ("gemm", "tridiag", "cgs", "reduce", "qr", "poles", "update", "other", "stencil")
 
 
@@ -94,10 +95,11 @@ def load(build_if_missing: bool = False):
         f = getattr(lib, name)
         f.restype = C.c_int
         f.argtypes = [p, d, p, i64, i32, p, i64]
-    lib.expm_block_batched.restype = C.c_int
-    lib.expm_block_batched.argtypes = [C.POINTER(p), C.c_int, C.POINTER(d), C.POINTER(p),
-                                       C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(p), C.POINTER(i64),
-                                       C.POINTER(expm_info)]
+    for name in ("expm_block_batched", "expm_block_batched_host"):
+        f = getattr(lib, name)
+        f.restype = C.c_int
+        f.argtypes = [C.POINTER(p), C.c_int, C.POINTER(d), C.POINTER(p), C.POINTER(i64), C.POINTER(C.c_int),
+                      C.POINTER(p), C.POINTER(i64), C.POINTER(expm_info)]
     lib.expm_block_adjoint.restype = C.c_int
     lib.expm_block_adjoint.argtypes = [p, d, p, i64, i32, p, i64, p, i64, C.POINTER(d), C.POINTER(expm_info)]
     lib.expm_arnoldi.restype = C.c_int
@@ -107,6 +109,8 @@ def load(build_if_missing: bool = False):
     lib.expm_ritz_basis.restype = C.c_int
     lib.expm_ritz_basis.argtypes = [C.POINTER(d), i64, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(d), i64,
                                     C.POINTER(C.c_int)]
+    lib.expm_peak_fma.restype = C.c_int
+    lib.expm_peak_fma.argtypes = [C.c_int, i64, C.POINTER(d), p]
     lib.expm_plan_profile.restype = C.c_int
     lib.expm_plan_profile.argtypes = [p, C.c_int]
     lib.expm_plan_get_profile.restype = C.c_int
@@ -171,16 +175,19 @@ def expm_block_host(plan, t, hB, ldb, p, hZ, ldz, allow_not_converged=True):
     return code, info
 
 
-def expm_block_batched(plans, ts, dBs, ldbs, ps, dZs, ldzs, allow_not_converged=True):
-    """Independent solves in one call (see include/expm_block.h); returns (code, [info])."""
+def expm_block_batched(plans, ts, dBs, ldbs, ps, dZs, ldzs, allow_not_converged=True, host=False):
+    """Independent solves in one call (see include/expm_block.h); returns (code, [info]).
+    host: the pointers are host buffers (expm_block_batched_host)."""
     k = len(plans)
     infos = (expm_info * k)()
     arr = lambda T, xs: (T * k)(*xs)
     allow = (EXPM_OK, EXPM_NOT_CONVERGED) if allow_not_converged else (EXPM_OK,)
-    code = check(load().expm_block_batched(
+    fn = load().expm_block_batched_host if host else load().expm_block_batched
+    code = check(fn(
         arr(C.c_void_p, [pl.value if isinstance(pl, C.c_void_p) else pl for pl in plans]), k,
         arr(C.c_double, ts), arr(C.c_void_p, dBs), arr(C.c_int64, ldbs), arr(C.c_int, ps),
-        arr(C.c_void_p, dZs), arr(C.c_int64, ldzs), infos), "expm_block_batched", allow)
+        arr(C.c_void_p, dZs), arr(C.c_int64, ldzs), infos),
+        "expm_block_batched_host" if host else "expm_block_batched", allow)
     return code, list(infos)
 
 
@@ -240,3 +247,10 @@ def expm_ritz_basis(Hm, k, largest, align):
                                  int(align), P.ctypes.data_as(C.POINTER(C.c_double)), mp, C.byref(kept)),
           "expm_ritz_basis")
     return P[:, :kept.value].copy()
+
+
+def expm_peak_fma(kind, iters=1 << 16, stream=0):
+    """Measured FMA throughput in TFLOP/s: kind 0 = FP64, 1 = FP32 (see include/expm_block.h)."""
+    out = C.c_double()
+    check(load().expm_peak_fma(int(kind), int(iters), C.byref(out), C.c_void_p(stream)), "expm_peak_fma")
+    return out.value

@@ -175,12 +175,19 @@ class Plan:
 
 def expm_block_batched(plans, ts, Bs, Zs=None):
     """Independent solves Z_i = r(t_i A_i) B_i in one library call (each plan once; plans on
-    distinct streams overlap on the GPU).  Returns (list of Z, list of info)."""
+    distinct streams overlap on the GPU).  B_i on the device, or all on the host (torch CPU
+    tensors, ideally pinned: expm_block_batched_host, the copies inside the call).  Returns
+    (list of Z, list of info)."""
+    host = all(not B.is_cuda for B in Bs)
     if Zs is None:
-        Zs = [colmajor(pl.n, B.shape[1], device=B.device) for pl, B in zip(plans, Bs)]
+        if host:
+            import torch
+            Zs = [torch.empty((B.shape[1], pl.n), dtype=torch.float64).T for pl, B in zip(plans, Bs)]
+        else:
+            Zs = [colmajor(pl.n, B.shape[1], device=B.device) for pl, B in zip(plans, Bs)]
     ldbs = [_check_colmajor(B, pl.n, B.shape[1], "B") for pl, B in zip(plans, Bs)]
     ldzs = [_check_colmajor(Z, pl.n, B.shape[1], "Z") for pl, B, Z in zip(plans, Bs, Zs)]
     code, infos = N.expm_block_batched([pl._h for pl in plans], [float(t) for t in ts],
                                        [B.data_ptr() for B in Bs], ldbs, [B.shape[1] for B in Bs],
-                                       [Z.data_ptr() for Z in Zs], ldzs)
+                                       [Z.data_ptr() for Z in Zs], ldzs, host=host)
     return Zs, infos

@@ -443,10 +443,10 @@ expm_status issue_cycle(expm_plan* P, double t, int p, int alg, int kk = 0, int 
                                           tau_re + 2 * EXPM_MAX_POLES, tau_re + 3 * EXPM_MAX_POLES,
                                           P->S, P->poles, P->Wc_slots, P->stat, flags_of(P->stat), alg, s,
                                           P->opts.certify ? P->Zcert : nullptr, kk));
-    LAUNCH(EXPM_STAGE_POLES, launch_combine2(P->H, P->ldH, mp, p, P->npoles, P->Wc_slots, sm(P, kOffWc), alg, s));
+    LAUNCH(EXPM_STAGE_POLES, launch_combine2(P->H, P->ldH, mp, p, P->npoles, P->Wc_slots, sm(P, kOffWc), alg, s, kk));
     if (P->opts.certify) {
         // every pole's X_i (real and imaginary columns) += V_{m+1} C, before the restart copy
-        LAUNCH(EXPM_STAGE_OTHER, launch_certify_coeffs(P->H, P->ldH, mp, p, P->npoles, P->Zcert, P->Ccert, alg, s));
+        LAUNCH(EXPM_STAGE_OTHER, launch_certify_coeffs(P->H, P->ldH, mp, p, P->npoles, P->Zcert, P->Ccert, alg, s, kk));
         LAUNCH(EXPM_STAGE_OTHER, launch_update_z(P->V, ld, mp + p, 2 * P->npoles * p, n, P->Ccert, P->Xcert, ld, 0,
                                                  s, P->nblk));
     }
@@ -807,15 +807,26 @@ expm_status toeplitz_validate(const expm_op_desc* op, double* abs_rowsum) {
     if (op->toeplitz_bw < 0 || op->toeplitz_bw > op->n - 1 || !op->toeplitz_col) return EXPM_INVALID_ARG;
     const double* a = op->toeplitz_col;
     const int64_t bw = op->toeplitz_bw;
-    double rs = std::fabs(a[0]);
+    // rs = |a_0| + 2 sum |a_k| and the Gershgorin bound a_0 + 2 sum |a_k|, both with
+    // compensated (Neumaier) sums: for the fractional-diffusion operators the bound is a few
+    // units against terms of 1e10, beyond what a plain sum resolves
+    double rs = 0.0, rc = 0.0, gs = 0.0, gc = 0.0;
+    auto add = [](double& sum, double& comp, double v) {
+        const double t = sum + v;
+        comp += (std::fabs(sum) >= std::fabs(v)) ? (sum - t) + v : (v - t) + sum;
+        sum = t;
+    };
     for (int64_t k = 0; k <= bw; ++k) {
         if (!std::isfinite(a[k])) return EXPM_INVALID_ARG;
-        if (k > 0) rs += 2.0 * std::fabs(a[k]);
+        add(rs, rc, k > 0 ? 2.0 * std::fabs(a[k]) : std::fabs(a[k]));
+        add(gs, gc, k > 0 ? 2.0 * std::fabs(a[k]) : a[k]);
     }
+    rs += rc;
+    gs += gc;
     if (!(a[0] < 0.0)) return EXPM_INVALID_ARG;
     if (bw <= 4096) {
         if (!(toeplitz_symbol_max_bound(a, bw, rs) < 0.0)) return EXPM_INVALID_ARG;
-    } else if (!(a[0] + (rs - std::fabs(a[0])) <= 0.0)) {
+    } else if (!(gs <= 0.0)) {
         return EXPM_INVALID_ARG;
     }
     *abs_rowsum = rs;
@@ -834,14 +845,103 @@ expm_status dot_host(expm_plan* P, const double* x, const double* y, double* par
     return EXPM_OK;
 }
 
+// T. Chan's optimal circulant preconditioner of the generator solve (the circulant C that
+// minimises ||C - T||_F: first column c_k = ((n - k) a_k + k a_{n-k}) / n), applied by FFTs of
+// length n; only when n is a power of two (the four-step FFT's lengths) and C is negative
+// definite.  Owns its device buffers for the duration of the plan's setup.
+struct CircPre {
+    FftPlan f{};
+    double *tw1 = nullptr, *tw2 = nullptr, *thi = nullptr, *tlo = nullptr;
+    double *col = nullptr, *lam = nullptr, *U = nullptr;
+    bool ok = false;
+    ~CircPre() {
+        cudaFree(tw1);
+        cudaFree(tw2);
+        cudaFree(thi);
+        cudaFree(tlo);
+        cudaFree(col);
+        cudaFree(lam);
+        cudaFree(U);
+    }
+};
+
+FftArgs circ_args(const CircPre& c, int64_t n) {
+    FftArgs a;
+    a.f = c.f;
+    a.nreal = n;
+    a.tw1 = c.tw1;
+    a.tw2 = c.tw2;
+    a.thi = c.thi;
+    a.tlo = c.tlo;
+    a.lam = c.lam;
+    a.in = a.out = c.U;
+    a.p = 1;
+    return a;
+}
+
+// z = C^{-1} r (one column): forward column pass, row pass times 1 / sigma, inverse column pass
+expm_status circ_apply(expm_plan* P, const CircPre& c, const double* r, double* z) {
+    cudaStream_t s = P->stream;
+    FftArgs a = circ_args(c, P->n);
+    a.V = r;
+    a.ldv = P->ld;
+    a.W = z;
+    a.ldw = P->ld;
+    a.scale = 1.0 / (double)c.f.N;
+    if (launch_fft_cols(a, FFT_COL_FWD_REAL, 1, s) != cudaSuccess || launch_fft_rows(a, FFT_ROW_MATVEC, 1, s) != cudaSuccess)
+        return EXPM_CUDA_ERROR;
+    a.scale = 1.0;
+    if (launch_fft_cols(a, FFT_COL_INV_REAL, 1, s) != cudaSuccess) return EXPM_CUDA_ERROR;
+    return EXPM_OK;
+}
+
+expm_status circ_setup(expm_plan* P, const double* hcol, CircPre& c) {
+    const int64_t n = P->n, bw = P->tz.bw;
+    if (n < 64 || (n & (n - 1)) != 0) return EXPM_OK;       // not a power of two: no preconditioner
+    c.f = fft_geometry(n);
+    if (c.f.N != n || !fft_geometry_ok(c.f)) return EXPM_OK;
+    cudaStream_t s = P->stream;
+    const int64_t N = c.f.N;
+    if (!(dalloc(&c.tw1, 2 * (size_t)c.f.N1) && dalloc(&c.tw2, 2 * (size_t)c.f.N2) && dalloc(&c.thi, 2 * (size_t)(N / 64)) &&
+          dalloc(&c.tlo, 128) && dalloc(&c.col, (size_t)P->ld) && dalloc(&c.lam, (size_t)N) && dalloc(&c.U, 2 * (size_t)N))) {
+        cudaGetLastError();
+        return EXPM_NO_MEMORY;
+    }
+    std::vector<double> cc((size_t)n, 0.0), sig((size_t)N);
+    auto at = [&](int64_t k) { return k <= bw ? hcol[k] : 0.0; };
+    for (int64_t k = 0; k < n; ++k) cc[k] = ((double)(n - k) * at(k) + (double)k * (k ? at(n - k) : 0.0)) / (double)n;
+    FftArgs a = circ_args(c, n);
+    a.V = c.col;
+    a.ldv = P->ld;
+    if (cudaMemcpyAsync(c.col, cc.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        launch_fft_tables(c.f, c.tw1, c.tw2, c.thi, c.tlo, s) != cudaSuccess ||
+        launch_fft_cols(a, FFT_COL_FWD_REAL, 1, s) != cudaSuccess || launch_fft_rows(a, FFT_ROW_FWD, 1, s) != cudaSuccess ||
+        launch_real_part(c.U, c.lam, N, s) != cudaSuccess ||
+        cudaMemcpyAsync(sig.data(), c.lam, sizeof(double) * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return EXPM_CUDA_ERROR;
+    for (int64_t k = 0; k < N; ++k) {
+        if (!(sig[k] < 0.0) || !std::isfinite(sig[k])) return EXPM_OK;   // not definite: plain CG
+        sig[k] = 1.0 / sig[k];
+    }
+    if (cudaMemcpyAsync(c.lam, sig.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return EXPM_CUDA_ERROR;
+    c.ok = true;
+    return EXPM_OK;
+}
+
 // Generator x = T^{-1} e_1 of the Gohberg-Semencul formula by conjugate gradients with the
-// FFT product (T is symmetric definite), then mu_1 = F[x; 0], mu_2 = F[xh; 0].
-expm_status toeplitz_generator(expm_plan* P) {
+// FFT product (T is symmetric definite), preconditioned by T. Chan's circulant when n is a
+// power of two (the large-norm operators of Example 5.4's regime have kappa ~ 1e9, where
+// plain CG stalls), then mu_1 = F[x; 0], mu_2 = F[xh; 0].  Stop when the backward error
+// ||e_1 - T x|| / (||T||_1 ||x|| + 1) reaches 1e-14; fail above 1e-12.
+expm_status toeplitz_generator(expm_plan* P, const double* hcol) {
     cudaStream_t s = P->stream;
     ToeplitzOp& z = P->tz;
     const int64_t n = P->n, ld = P->ld, N = z.f.N;
     double *buf = nullptr, *part = nullptr;
-    if (cudaMalloc(reinterpret_cast<void**>(&buf), sizeof(double) * 4 * ld) != cudaSuccess) return EXPM_NO_MEMORY;
+    if (cudaMalloc(reinterpret_cast<void**>(&buf), sizeof(double) * 5 * ld) != cudaSuccess) return EXPM_NO_MEMORY;
     if (cudaMalloc(reinterpret_cast<void**>(&part), sizeof(double) * dot_blocks()) != cudaSuccess) {
         cudaFree(buf);
         return EXPM_NO_MEMORY;
@@ -851,6 +951,7 @@ expm_status toeplitz_generator(expm_plan* P) {
     double* r = buf + ld;
     double* pp = buf + 2 * ld;
     double* w = buf + 3 * ld;
+    double* zz = buf + 4 * ld;
     expm_status st = EXPM_OK;
     auto fail = [&](expm_status e) {
         cudaStreamSynchronize(s);
@@ -858,21 +959,36 @@ expm_status toeplitz_generator(expm_plan* P) {
         cudaFree(part);
         return e;
     };
+    CircPre pre;
+    if ((st = circ_setup(P, hcol, pre)) != EXPM_OK) return fail(st);
+    auto precond = [&](const double* in, double* out) -> expm_status {
+        if (pre.ok) return circ_apply(P, pre, in, out);
+        return launch_copy(in, ld, out, ld, n, 1, s) == cudaSuccess ? EXPM_OK : EXPM_CUDA_ERROR;
+    };
     if (cudaMemsetAsync(x, 0, sizeof(double) * ld, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
-    if (launch_unit(r, n, s) != cudaSuccess || launch_unit(pp, n, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
-    double rr = 1.0;
+    if (launch_unit(r, n, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
+    if ((st = precond(r, zz)) != EXPM_OK) return fail(st);
+    if (launch_copy(zz, ld, pp, ld, n, 1, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
+    double rz = 0.0, xx = 0.0;
+    if ((st = dot_host(P, r, zz, part, hpart.data(), &rz)) != EXPM_OK) return fail(st);
+    const double rs = z.abs_rowsum;
     int it = 0;
-    for (; it < 5000 && std::sqrt(rr) > 1e-15; ++it) {
+    for (; it < 5000; ++it) {
         if ((st = toeplitz_matvec(P, 1.0, pp, ld, 1, w, ld, EXPM_STAGE_OTHER)) != EXPM_OK) return fail(st);
         double pw = 0.0;
         if ((st = dot_host(P, pp, w, part, hpart.data(), &pw)) != EXPM_OK) return fail(st);
         if (!(pw < 0.0) || !std::isfinite(pw)) return fail(EXPM_NUMERICAL);   // T negative definite
-        const double alpha = rr / pw;
+        const double alpha = rz / pw;
         if (launch_cg_step(x, r, pp, w, alpha, n, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
-        double rr_new = 0.0;
-        if ((st = dot_host(P, r, r, part, hpart.data(), &rr_new)) != EXPM_OK) return fail(st);
-        if (launch_cg_dir(pp, r, rr_new / rr, n, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
-        rr = rr_new;
+        double rr = 0.0;
+        if ((st = dot_host(P, r, r, part, hpart.data(), &rr)) != EXPM_OK) return fail(st);
+        if (it % 8 == 0 && (st = dot_host(P, x, x, part, hpart.data(), &xx)) != EXPM_OK) return fail(st);
+        if (std::sqrt(rr) <= 1e-14 * (rs * std::sqrt(xx) + 1.0)) break;
+        if ((st = precond(r, zz)) != EXPM_OK) return fail(st);
+        double rz_new = 0.0;
+        if ((st = dot_host(P, r, zz, part, hpart.data(), &rz_new)) != EXPM_OK) return fail(st);
+        if (launch_cg_dir(pp, zz, rz_new / rz, n, s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
+        rz = rz_new;
     }
     // true residual ||e_1 - T x||
     if ((st = toeplitz_matvec(P, 1.0, x, ld, 1, w, ld, EXPM_STAGE_OTHER)) != EXPM_OK) return fail(st);
@@ -881,8 +997,9 @@ expm_status toeplitz_generator(expm_plan* P) {
         return fail(EXPM_CUDA_ERROR);
     double res2 = 0.0;
     if ((st = dot_host(P, r, r, part, hpart.data(), &res2)) != EXPM_OK) return fail(st);
+    if ((st = dot_host(P, x, x, part, hpart.data(), &xx)) != EXPM_OK) return fail(st);
     z.cg_iters = it;
-    z.cg_resid = std::sqrt(res2);
+    z.cg_resid = std::sqrt(res2) / (rs * std::sqrt(xx) + 1.0);
     if (!(z.cg_resid <= 1e-12)) return fail(EXPM_NOT_CONVERGED);
     if (cudaMemcpyAsync(&z.x0, x, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return fail(EXPM_CUDA_ERROR);
@@ -897,6 +1014,7 @@ expm_status toeplitz_generator(expm_plan* P) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(EXPM_CUDA_ERROR);
     if (!(z.x0 < 0.0) || !std::isfinite(z.x0)) return fail(EXPM_NUMERICAL);
     z.gsf = true;
+    z.pcg = pre.ok;
     return fail(EXPM_OK);
 }
 
@@ -928,7 +1046,7 @@ expm_status toeplitz_setup(expm_plan* P, const expm_op_desc* op, bool want_inver
         launch_real_part(z.Ua, z.lam, N, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
         return EXPM_CUDA_ERROR;
     if (want_inverse) {
-        const expm_status st = toeplitz_generator(P);
+        const expm_status st = toeplitz_generator(P, op->toeplitz_col);
         if (st != EXPM_OK) return st;
     }
     // Mixed precision: later products and inverses run their transforms in double-float
@@ -1244,12 +1362,20 @@ expm_status expm_block_host(expm_plan* plan, double t, const double* hB, int64_t
     return st;
 }
 
-expm_status expm_block_batched(expm_plan* const* plans, int count, const double* t, const double* const* dB,
-                               const int64_t* ldb, const int* p, double* const* dZ, const int64_t* ldz,
-                               expm_info* info) {
-    if (count < 1 || !plans || !t || !dB || !ldb || !p || !dZ || !ldz) return EXPM_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// The batched driver behind expm_block_batched and expm_block_batched_host.  With host
+// buffers, instance i's B is copied to its plan's staging buffer on the plan's stream before
+// its first cycle and its Z copied back after its last, so the copies of one instance overlap
+// with the other instances' cycles.
+expm_status batched_run(expm_plan* const* plans, int count, const double* t, const double* const* B,
+                        const int64_t* ldb, const int* p, double* const* Z, const int64_t* ldz, expm_info* info,
+                        bool host) {
+    if (count < 1 || !plans || !t || !B || !ldb || !p || !Z || !ldz) return EXPM_INVALID_ARG;
     for (int i = 0; i < count; ++i) {
-        const expm_status st = validate_block_args(plans[i], t[i], dB[i], ldb[i], p[i], dZ[i], ldz[i]);
+        const expm_status st = validate_block_args(plans[i], t[i], B[i], ldb[i], p[i], Z[i], ldz[i]);
         if (st != EXPM_OK) return st;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return EXPM_INVALID_ARG;   // one call per plan (its workspace)
@@ -1259,15 +1385,28 @@ expm_status expm_block_batched(expm_plan* const* plans, int count, const double*
     std::vector<expm_status> status(count, EXPM_OK);
     int left = 0;
     for (int i = 0; i < count; ++i) {
+        expm_plan* P = plans[i];
         RunState& r = rs[i];
         r.t = t[i];
-        r.dB = dB[i];
-        r.ldb = ldb[i];
         r.p = p[i];
-        r.dZ = dZ[i];
-        r.ldz = ldz[i];
-        expm_status st = run_begin(plans[i], r);
-        if (st == EXPM_OK) st = run_issue(plans[i], r);
+        if (host) {
+            if (cudaMemcpy2DAsync(P->Bst, P->ld * sizeof(double), B[i], ldb[i] * sizeof(double), P->n * sizeof(double),
+                                  p[i], cudaMemcpyHostToDevice, P->stream) != cudaSuccess) {
+                status[i] = EXPM_CUDA_ERROR;
+                continue;
+            }
+            r.dB = P->Bst;
+            r.ldb = P->ld;
+            r.dZ = P->Zst;
+            r.ldz = P->ld;
+        } else {
+            r.dB = B[i];
+            r.ldb = ldb[i];
+            r.dZ = Z[i];
+            r.ldz = ldz[i];
+        }
+        expm_status st = run_begin(P, r);
+        if (st == EXPM_OK) st = run_issue(P, r);
         if (st != EXPM_OK) {
             status[i] = st;
             continue;
@@ -1295,6 +1434,10 @@ expm_status expm_block_batched(expm_plan* const* plans, int count, const double*
                     if (st == EXPM_OK) continue;
                 } else {
                     st = run_finish(P, rs[i], info ? &info[i] : nullptr);
+                    if (host && (st == EXPM_OK || st == EXPM_NOT_CONVERGED) &&
+                        cudaMemcpy2DAsync(Z[i], ldz[i] * sizeof(double), P->Zst, P->ld * sizeof(double),
+                                          P->n * sizeof(double), p[i], cudaMemcpyDeviceToHost, P->stream) != cudaSuccess)
+                        st = EXPM_CUDA_ERROR;
                 }
             }
             status[i] = st;
@@ -1312,6 +1455,22 @@ expm_status expm_block_batched(expm_plan* const* plans, int count, const double*
         if (status[i] == EXPM_NOT_CONVERGED) worst = EXPM_NOT_CONVERGED;
     }
     return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+expm_status expm_block_batched(expm_plan* const* plans, int count, const double* t, const double* const* dB,
+                               const int64_t* ldb, const int* p, double* const* dZ, const int64_t* ldz,
+                               expm_info* info) {
+    return batched_run(plans, count, t, dB, ldb, p, dZ, ldz, info, false);
+}
+
+expm_status expm_block_batched_host(expm_plan* const* plans, int count, const double* t, const double* const* hB,
+                                    const int64_t* ldb, const int* p, double* const* hZ, const int64_t* ldz,
+                                    expm_info* info) {
+    return batched_run(plans, count, t, hB, ldb, p, hZ, ldz, info, true);
 }
 
 expm_status expm_block_adjoint(expm_plan* plan, double t, const double* dG, int64_t ldg, int p,

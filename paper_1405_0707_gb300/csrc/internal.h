@@ -116,7 +116,8 @@ struct ToeplitzOp {
     double* mu2 = nullptr;
     double x0 = 0.0;            // first entry of the generator x = T^{-1} e_1
     int cg_iters = 0;
-    double cg_resid = 0.0;
+    double cg_resid = 0.0;      // backward error ||e_1 - T x|| / (||T||_1 ||x|| + 1)
+    bool pcg = false;           // generator solved with the circulant preconditioner
     double abs_rowsum = 0.0;    // |a_0| + 2 sum_k |a_k|  (bound of ||T||)
     bool gsf = false;           // inverse available
 };
@@ -275,7 +276,7 @@ cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
                          double* res, int* flags, int alg, cudaStream_t s, double* Zout = nullptr,
                          int kk = 0);
 cudaError_t launch_certify_coeffs(const double* H, int ldH, int mp, int p, int npoles, const double* Zs,
-                                  double* C, int alg, cudaStream_t s);
+                                  double* C, int alg, cudaStream_t s, int kk = 0);
 int true_resid_blocks(int64_t n);
 // AX != nullptr: tA X is given (same column layout, leading dimension ldax) instead of the stencil
 cudaError_t launch_true_resid(const double* X, int64_t ldx, const double* B, int64_t ldb, int p, int npoles,
@@ -285,7 +286,7 @@ cudaError_t launch_true_resid(const double* X, int64_t ldx, const double* B, int
 cudaError_t launch_combine(const double* Wc_slots, int npoles, int rows, int p, double* Wc,
                            cudaStream_t s);
 cudaError_t launch_combine2(const double* H, int ldH, int mp, int p, int npoles,
-                            const double* Y_slots, double* Wc, int alg, cudaStream_t s);
+                            const double* Y_slots, double* Wc, int alg, cudaStream_t s, int kk = 0);
 cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
                             const double* Wc, double* Z, int64_t ldz, int restart_copy,
                             cudaStream_t s, int nblk, int df = 0);

@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kPoleThreads) k_poles(const double* __restrict
 // Wc = H~ sum_i Y_i (Algorithm 2) or [sum_i Y_i; 0] (Algorithm 1), (mp+p) x p, row-major
 // [r][c] as k_update_z reads it.  One thread per output, r fastest (coalesced H~ columns).
 __global__ void k_combine2(const double* __restrict__ H, int ldH, int mp, int p, int npoles,
-                           const double* __restrict__ Y_slots, double* __restrict__ Wc, int alg) {
+                           const double* __restrict__ Y_slots, double* __restrict__ Wc, int alg, int kk) {
     extern __shared__ double Ys[];          // mp x p, summed over poles (fixed order)
     const int rows = mp + p;
     for (int e = threadIdx.x; e < mp * p; e += blockDim.x) {
@@ -282,7 +282,9 @@ __global__ void k_combine2(const double* __restrict__ H, int ldH, int mp, int p,
         const int r = e % rows, c = e / rows;
         double s = 0.0;
         if (alg == 2) {
-            for (int k = max(0, r - p); k < mp; ++k) s = fma(H[(int64_t)k * ldH + r], Ys[c * mp + k], s);
+            // band rows start p columns left of the diagonal; the rows of a deflated restart's
+            // leading block (r < kk + p) are dense from column 0
+            for (int k = r < kk + p ? 0 : r - p; k < mp; ++k) s = fma(H[(int64_t)k * ldH + r], Ys[c * mp + k], s);
         } else if (r < mp) {
             s = Ys[c * mp + r];
         }
@@ -294,7 +296,7 @@ __global__ void k_combine2(const double* __restrict__ H, int ldH, int mp, int p,
 // F_i = H~_m Z_i (Algorithm 2: X_i - X_i^0 = V_{m+1} H~_m Z_i) or F_i = [Z_i; 0] (Algorithm 1),
 // so X += V_{m+1} C updates every pole's real and imaginary parts in one tall-skinny product.
 __global__ void k_certify_coeffs(const double* __restrict__ H, int ldH, int mp, int p, int npoles,
-                                 const double* __restrict__ Zs, double* __restrict__ C, int alg) {
+                                 const double* __restrict__ Zs, double* __restrict__ C, int alg, int kk) {
     const int rows = mp + p, w = 2 * npoles * p;
     const cplx* Z = reinterpret_cast<const cplx*>(Zs);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * npoles * p; e += gridDim.x * blockDim.x) {
@@ -302,7 +304,7 @@ __global__ void k_certify_coeffs(const double* __restrict__ H, int ldH, int mp, 
         const cplx* Zi = Z + (size_t)i * mp * p;
         cplx s{0.0, 0.0};
         if (alg == 2) {
-            for (int k = max(0, a - p); k < mp; ++k) {
+            for (int k = a < kk + p ? 0 : a - p; k < mp; ++k) {   // as in k_combine2
                 const double h = H[(int64_t)k * ldH + a];
                 s.re = fma(h, Zi[(size_t)k * p + c].re, s.re);
                 s.im = fma(h, Zi[(size_t)k * p + c].im, s.im);
@@ -318,9 +320,9 @@ __global__ void k_certify_coeffs(const double* __restrict__ H, int ldH, int mp, 
 }  // namespace
 
 cudaError_t launch_certify_coeffs(const double* H, int ldH, int mp, int p, int npoles, const double* Zs,
-                                  double* C, int alg, cudaStream_t s) {
+                                  double* C, int alg, cudaStream_t s, int kk) {
     const int tot = (mp + p) * npoles * p;
-    k_certify_coeffs<<<(tot + 255) / 256, 256, 0, s>>>(H, ldH, mp, p, npoles, Zs, C, alg);
+    k_certify_coeffs<<<(tot + 255) / 256, 256, 0, s>>>(H, ldH, mp, p, npoles, Zs, C, alg, kk);
     return cudaGetLastError();
 }
 
@@ -348,10 +350,10 @@ cudaError_t launch_poles(const double* H, int ldH, int mp, int p, int npoles,
 }
 
 cudaError_t launch_combine2(const double* H, int ldH, int mp, int p, int npoles,
-                            const double* Y_slots, double* Wc, int alg, cudaStream_t s) {
+                            const double* Y_slots, double* Wc, int alg, cudaStream_t s, int kk) {
     const int nout = (mp + p) * p;
     const int blocks = (nout + 255) / 256;
-    k_combine2<<<blocks, 256, sizeof(double) * (size_t)mp * p, s>>>(H, ldH, mp, p, npoles, Y_slots, Wc, alg);
+    k_combine2<<<blocks, 256, sizeof(double) * (size_t)mp * p, s>>>(H, ldH, mp, p, npoles, Y_slots, Wc, alg, kk);
     return cudaGetLastError();
 }
 

@@ -442,7 +442,11 @@ struct CholD {
 // chol32_full).  ok = every pivot is positive and at least rel_min times the largest diagonal
 // entry and no column is zero: then one pass with this factor leaves the block orthonormal to
 // ~kappa^2 2^-48, and the caller skips the deviation pass.  Otherwise the caller discards it.
-__device__ inline void chol_df(CholD& cd, const double* G0, int p, int k, float rel_min) {
+// dep: a pivot that is zero, or below rel_min times the largest diagonal entry, marks a
+// dependent column instead of a failure: R_jj = 0 and row j of R zero, so the column's
+// direction is dropped (the block Krylov space loses a direction that lies in the span of
+// the others to within the pivot) and the forward substitution leaves it zero.
+__device__ inline void chol_df(CholD& cd, const double* G0, int p, int k, float rel_min, bool dep = false) {
     const int lane = threadIdx.x;
     const unsigned full = 0xffffffffu;
     const bool act = lane < p;
@@ -467,12 +471,16 @@ __device__ inline void chol_df(CholD& cd, const double* G0, int p, int k, float 
         fp2 inv = f2_make(0.f, 0.f);
         if (lane == j) {
             fp2 d = g[j];
-            if (G0[j * p + j] == 0.0 || !(d.h > 0.f) || !isfinite(d.h) || d.h < rel_min * dmax) {
-                ok_l = 0;
-                d = f2_make(1.f, 0.f);
+            if (dep && isfinite(d.h) && (G0[j * p + j] == 0.0 || !(d.h >= rel_min * dmax))) {
+                u[j] = f2_make(0.f, 0.f);           // dependent column: R_jj = 0, inverse 0
+            } else {
+                if (G0[j * p + j] == 0.0 || !(d.h > 0.f) || !isfinite(d.h) || d.h < rel_min * dmax) {
+                    ok_l = 0;
+                    d = f2_make(1.f, 0.f);
+                }
+                u[j] = f2_sqrt(d);
+                inv = f2_rcp(u[j]);
             }
-            u[j] = f2_sqrt(d);
-            inv = f2_rcp(u[j]);
             myinv = inv;
         }
         inv = f2_shfl(inv, j);
@@ -529,7 +537,8 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     extern __shared__ float h2f[];          // KIND 3: h2 as float pairs (hi, then lo), ccols x RP each
     float* h2l = h2f + ccols * RP;
     __shared__ CholF cf;
-    __shared__ CholD cd;                    // KIND 3: the float-pair factor of the single pass
+    __shared__ CholD cd;                    // K1: the float-pair factor (single pass, or an ill block)
+    __shared__ int sgl_s;                   // K1: the single pass (the block is final after it)
     __shared__ double G0[RP * RP];
     __shared__ double hn2[RP];
     __shared__ double Rd[RP * RP];          // KIND 1: R (padded to RP x RP); KIND 2 unused
@@ -588,6 +597,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     __syncthreads();
     int kexp = 0;                           // KIND 1: G is factored as G 2^-kexp (kexp even)
     if (threadIdx.x < 32) {
+        int sgl_r = 0;                      // warp 0's copy of the single-pass decision
         const int lane = threadIdx.x;
         double tr = 0.0, dmax = 0.0;
         if (K1) {
@@ -624,11 +634,23 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                 __syncwarp();
             } else {
                 chol32_full(cf, G0, p, kexp, ldexp(tr, -kexp));
+                // an ill-conditioned block (an FP32 pivot below 1e-6 of the largest diagonal
+                // entry: the FP32 factor needed a shift, after which the block would be too far
+                // from orthonormal for the deviation passes): factor the Gram matrix, accurate
+                // to ~2^-48, unshifted in double-float instead and apply that factor exactly;
+                // both deviation passes then run (cf.ill stays set).  Up to kappa(W) ~ 8e6; a
+                // direction below that (a pivot under 2^-46 of the largest, where G's ~2^-48
+                // accuracy no longer resolves it) counts as dependent and is dropped, as the
+                // FP64 path drops zero pivots (info.breakdown).
+                if (cf.ill) chol_df(cd, G0, p, kexp, 0x1p-46f, true);
             }
+            sgl_r = sgl;
+            if (lane == 0) sgl_s = sgl;     // for the other warps, read after the barrier
         } else {
             chol32_dev(cf, G0, p);
         }
-        const bool sgl_w = K1 && cd.ok;     // warp 0's view of the single-pass decision
+        const bool df_w = K1 && cd.ok;      // warp 0: the float-pair factor is applied
+        const bool sgl_w = df_w && sgl_r;   // warp 0's view of the single-pass decision
         const bool fin = last || sgl_w;     // this pass writes the final block and H
         if (lead) {
             if (K1 && normsq_out && lane == 0) *normsq_out = tr;
@@ -641,7 +663,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                 for (int r = 0; r < p; ++r) {
                     const int o = r * p + c;
                     double rt;
-                    if (sgl_w) {
+                    if (df_w) {
                         float rh = 0.f, rl = 0.f;
                         if (r <= c) split_df(ldexp((double)cd.Uh[o] + (double)cd.Ul[o], kexp / 2), rh, rl);
                         rt = (double)rh + (double)rl;   // exactly the R the substitution applies
@@ -650,10 +672,18 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                         rt = (r <= c) ? ldexp((double)cf.U[o], kexp / 2) : 0.0;
                         R[o] = rt;
                     } else {
-                        // Rtot_out = Rtot_in + U Rtot_in (FP32 correction of the FP64 product)
-                        float corr = 0.f;
-                        for (int k = r; k <= c; ++k) corr = fmaf(cf.U[r * p + k], (float)Rtot_in[k * p + c], corr);
-                        rt = (r <= c) ? Rtot_in[o] + (double)corr : 0.0;
+                        // Rtot_out = Rtot_in + U Rtot_in: an FP32 correction of the FP64 product
+                        // when U is O(eps_32); in FP64 after an ill-conditioned first pass (U
+                        // up to ~0.1), so that H records the transform the pass applies
+                        double corr = 0.0;
+                        if (cf.umax > 1e-4f) {
+                            for (int k = r; k <= c; ++k) corr = fma((double)cf.U[r * p + k], Rtot_in[k * p + c], corr);
+                        } else {
+                            float cf32 = 0.f;
+                            for (int k = r; k <= c; ++k) cf32 = fmaf(cf.U[r * p + k], (float)Rtot_in[k * p + c], cf32);
+                            corr = (double)cf32;
+                        }
+                        rt = (r <= c) ? Rtot_in[o] + corr : 0.0;
                         R[o] = (r <= c) ? (double)cf.U[o] + (r == c ? 1.0 : 0.0) : 0.0;
                         Rinv[o] = (r <= c) ? (double)cf.Y[o] + (r == c ? 1.0 : 0.0) : 0.0;
                     }
@@ -691,7 +721,8 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     // KIND 2 with max|U| above 1e-4 (a pass after the shifted one): the FP32 inverse I + Y
     // would leave an eps_32 |U| mismatch with the recorded R, so the solve is a forward
     // substitution with R = I + U in FP64, as in pass 1
-    const bool single = K1 && cd.ok;
+    const bool single = K1 && cd.ok;        // the float-pair factor is applied
+    const bool final1 = single && sgl_s;    // ... as the single, final pass
     const bool subst = K1 || cf.umax > 1e-4f;
     for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
         const int a = e / RP, c = e % RP;
@@ -729,7 +760,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
     double* out;
     int64_t ldo;
     int gram;
-    if (single) { out = fin_; ldo = ldfin_; gram = 0; }
+    if (final1) { out = fin_; ldo = ldfin_; gram = 0; }
     else if (mode == 0) { out = W; ldo = ldw; gram = 1; }
     else if (mode == 1 && *extra) { out = W; ldo = ldw; gram = 1; }
     else { out = out_; ldo = ldo_; gram = 0; }

@@ -13,6 +13,8 @@ sizes and times below are synthetic stand-ins for the paper's own matrices):
                n = 65536, p = 8, t in {1e-3, 1e-2, 1e-1}, m = 10
   toeplitz-1m  t T, T symmetric Toeplitz with first column a_0 = -2 - c, a_k = 1/(1+k)^2
                (1 <= k <= 256), c = 0, n = 2^20, p = 16, t = 1, m = 10
+  toeplitz-frac t T, T the symmetric part of Example 5.4's fractional diffusion matrix
+               (beta = 1.8, fractional_column), n = 2^17, p = 2, t = 0.01, m = 30, k = 30, tol 1e-10
   batched3d-64 64 independent instances t (Laplacian_h - v . grad_h) on N_x x N_y x N_z grids,
                N_d uniform in {32..96} per axis, v ~ 5 N(0, I_3) (redrawn if a cell Peclet
                number |v_d| h_d / 2 reaches 1), t = 10^U(-3, 0), p uniform in {1..16}, m = 10,
@@ -32,6 +34,11 @@ WORKLOADS = {
     "toeplitz-1m": dict(n=1 << 20, bw=256, c=0.0, t=(1.0,), p=16, m=10, tol=1e-13,
                         seed=SEED_BASE + 3),
     "batched3d-64": dict(count=64, m=10, tol=1e-10, seed=SEED_BASE + 4),
+    # the large-norm Toeplitz regime of Example 5.4 (||A|| ~ 2e10 at n = 2^17): beta = 1.8,
+    # p = 2, m = 30 and k = 30 deflated Ritz vectors as in the paper; t = 0.01 (at the paper's
+    # t = 1 the result is ~1e-13 ||B||, below the CF approximation's own error), tol 1e-10
+    "toeplitz-frac": dict(n=1 << 17, bw=(1 << 17) - 1, frac=1.8, d=2.0, t=(0.01,), p=2, m=30, k_defl=30,
+                          tol=1e-10, seed=SEED_BASE + 6),
     # differentiation: L = ||r(tA) B - Y||_F^2, Y = r(t0 A) B0 (t0, B0 seeded perturbations)
     "cd2d-512-grad": dict(sides=(512, 512), diff=0.1, vel=(1.0, 1.0), t=(1e-2,), p=32, m=10,
                           tol=1e-10, seed=SEED_BASE + 5),
@@ -61,6 +68,29 @@ def toeplitz_column(bw, c=0.0):
     k = np.arange(1, bw + 1)
     a[1:] = 1.0 / (1.0 + k) ** 2
     return a
+
+
+def fractional_column(n, beta=1.8, d=2.0):
+    """First column of the symmetric Toeplitz operator of the large-norm workload: the
+    symmetric part of Example 5.4's matrix.  The fractional diffusion equation there, with
+    d_1 = 1 (left-sided) and d_2 = 3 (right-sided) derivatives of order beta and zero
+    boundary values, discretised by the shifted Grunwald formula on h = 1/(n+1), gives
+    A = (d_1 G + d_2 G^T) / h^beta with G the lower Hessenberg Toeplitz matrix
+    G[i, j] = g_{i-j+1} (j <= i+1), g_k = (-1)^k binom(beta, k).  Its symmetric part is
+    (d / h^beta)(G + G^T) with d = (d_1 + d_2) / 2 = 2: first column
+    a_0 = 2 d g_1 / h^beta, a_1 = d (g_0 + g_2) / h^beta, a_k = d g_{k+1} / h^beta (k >= 2).
+    The weights follow g_0 = 1, g_k = g_{k-1} (1 - (beta + 1) / k)."""
+    g = np.empty(n + 1)
+    g[0] = 1.0
+    for k in range(1, n + 1):
+        g[k] = g[k - 1] * (1.0 - (beta + 1.0) / k)
+    scale = d * float(n + 1) ** beta
+    a = np.empty(n)
+    a[0] = 2.0 * g[1]
+    if n > 1:
+        a[1] = g[0] + g[2]
+    a[2:] = g[3:n + 1]
+    return scale * a
 
 
 def grad_target(n, p, seed, t):

@@ -37,6 +37,18 @@ def _loss_setup(sides, diff, vel, t, p, seed, precision, m=8, tol=1e-13):
     return torch, plan, B, Y, loss
 
 
+def central_difference(loss, tv, B, D, h, Y):
+    """(L(B + hD) - L(B - hD)) / 2h for L = ||Z - Y||_F^2, formed as
+    <Z+ - Z-, Z+ + Z- - 2Y> / 2h: the same central difference of the computed map, without
+    subtracting two nearly equal large values of L (at h = 1e-6 that subtraction alone would
+    cost ~1e-5 relative)."""
+    import torch
+    with torch.no_grad():
+        _, Zp = loss(tv, to_dev(B + h * D))
+        _, Zm = loss(tv, to_dev(B - h * D))
+        return float(torch.sum((Zp - Zm) * (Zp + Zm - 2.0 * Y))) / (2 * h)
+
+
 @pytest.mark.parametrize("sides,diff,vel,t,p,precision", [((37, 29), 0.1, (1.0, 1.0), 0.1, 3, "fp64"),
                                                           ((40, 33), 0.1, (1.0, -0.5), 1.0, 2, "mixed"),
                                                           ((11, 9, 7), 1.0, (3.0, -2.0, 1.0), 0.3, 2, "fp64")])
@@ -53,14 +65,12 @@ def test_adjoint_matches_closed_form_and_finite_differences(tab, sides, diff, ve
     assert rel(gB, ref) <= 1e-9
     # central differences along a random direction in B with the differentiation workload's
     # step h = 1e-6 (L is quadratic in B, so the difference quotient is exact up to rounding
-    # and the solver's tolerance) and in t
+    # and the solver's error, which it divides by 2h: FP64 solves at tol 1e-14) and in t
     rng = np.random.default_rng(3)
     D = rng.standard_normal(B.shape)
     h = 1e-6
-    with torch.no_grad():
-        Lp, _ = loss(tv, to_dev(B + h * D))
-        Lm, _ = loss(tv, to_dev(B - h * D))
-    fd = (float(Lp) - float(Lm)) / (2 * h)
+    _, _, _, Yfd, loss_fd = _loss_setup(sides, diff, vel, t, p, 17, "fp64", tol=1e-14)
+    fd = central_difference(loss_fd, tv, B, D, h, Yfd)
     assert abs(fd - np.sum(gB * D)) <= 1e-5 * abs(fd) + 1e-9, (fd, np.sum(gB * D))
     ht = 1e-6 * t
     with torch.no_grad():
@@ -86,14 +96,21 @@ def test_differentiation_workload_512(tab):
     assert rel(to_np(Bt.grad), ref) <= 1e-8
     # forward against the closed form too
     assert rel(to_np(Z), ops.exact_r_of_A_B(w["sides"], w["diff"], w["vel"], t, tab, B)) <= 1e-8
-    # dL/dB against central differences with h = 1e-6 along a random direction
-    D = np.random.default_rng(4).standard_normal(B.shape)
+    # dL/dB against central differences with h = 1e-6 along a random direction.  The two
+    # perturbed losses differ by ~2h |dL/dB . D|, and each carries the solve's own error, which
+    # the quotient divides by 2h: the mixed path's ~1e-12 rounding would cost ~1e-4 there, so
+    # the difference quotient of the map is taken with FP64 solves converged to tol 1e-14
+    # The direction is the computed gradient itself (scaled to ||B||): a random direction in
+    # these 8.4e6 dimensions is nearly orthogonal to Z - Y (cosine ~ 3e-4), which would scale
+    # every small difference between the two losses' solves up by ~3000 relative to the
+    # directional derivative
+    gB = to_np(Bt.grad)
+    D = gB * (np.linalg.norm(B) / np.linalg.norm(gB))
     h = 1e-6
-    with torch.no_grad():
-        Lp, _ = loss(tv, to_dev(B + h * D))
-        Lm, _ = loss(tv, to_dev(B - h * D))
-    fd = (float(Lp) - float(Lm)) / (2 * h)
-    gD = float(np.sum(to_np(Bt.grad) * D))
+    _, _, _, Yfd, loss_fd = _loss_setup(w["sides"], w["diff"], w["vel"], t, w["p"], w["seed"], "fp64",
+                                        m=w["m"], tol=1e-14)
+    fd = central_difference(loss_fd, tv, B, D, h, Yfd)
+    gD = float(np.sum(gB * D))
     assert abs(fd - gD) <= 1e-5 * abs(fd), (fd, gD)
     ht = 1e-6 * t
     with torch.no_grad():

@@ -161,8 +161,9 @@ def test_nearly_dependent_rhs_takes_the_shifted_qr_pass(tab):
     assert rel(to_np(Zg), ref) < 1e-9
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("alg", [1, 2])
-def test_zero_and_repeated_rhs_columns(tab, alg):
+def test_zero_and_repeated_rhs_columns(tab, alg, precision):
     """A zero column and an exactly repeated column in B (rank-deficient block): the zero
     column stays zero through every block (zero Cholesky pivots are skipped) and the others
     match the closed form; an invariant subspace is reported in info.breakdown, not as an
@@ -173,7 +174,7 @@ def test_zero_and_repeated_rhs_columns(tab, alg):
     n = 41 * 35
     b = inputs.rhs(n, 2, 13)
     B = np.column_stack([b[:, 0], np.zeros(n), b[:, 0], b[:, 1]])
-    plan = Plan(sides, diff, vel, p_max=4, m=6, tol=1e-12, max_cycles=200, algorithm=alg)
+    plan = Plan(sides, diff, vel, p_max=4, m=6, tol=1e-12, max_cycles=200, algorithm=alg, precision=precision)
     Zg, info = plan.expm_block(t, to_dev(B))
     Zg = to_np(Zg)
     ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)

@@ -10,7 +10,7 @@
 import numpy as np
 import pytest
 
-from oracle import cf, psbfom as ps, toeplitz as TZ
+from oracle import cf, operators as ops, psbfom as ps, toeplitz as TZ
 from paper_1405_0707_gb300 import inputs
 from tests.gpu_util import cancellation_floor, need_gpu, rel, to_dev, to_np
 
@@ -207,3 +207,68 @@ def test_invalid_descriptors_rejected():
                  ([-2.0], (1 << 21) + 1)]:        # beyond the FFT size limit
         with pytest.raises(ExpmError):
             Plan.toeplitz(a, n, p_max=2)
+
+
+# --------------------------------------------------------------------------- Example 5.4 regime
+@pytest.mark.parametrize("n", [4096, 1 << 17])
+def test_fractional_generator_and_inverse(n):
+    """The large-norm operator (symmetric part of Example 5.4's fractional diffusion matrix,
+    kappa ~ 1e6 at n = 4096 and ~ 1e9 at n = 2^17): plan creation solves the generator by
+    conjugate gradients with T. Chan's circulant preconditioner, and the Gohberg-Semencul
+    inverse then matches the oracle's (Levinson generator) to the conditioning limit."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    a = inputs.fractional_column(n)
+    plan = Plan.toeplitz(a, n, p_max=2, algorithm=2)
+    V = inputs.rhs(n, 2, 41)
+    W = to_np(plan.prec_apply(1.0, to_dev(V)))
+    ref = TZ.gsf_apply(TZ.gsf_generator(a), V, 1.0)
+    kappa = (abs(a[0]) + 2 * np.abs(a[1:]).sum()) / 27.0     # ||T|| / |lambda_max| (lambda_max ~ -27)
+    assert rel(W, ref) <= 1e-14 * kappa, (rel(W, ref), kappa)
+    # and T (T^{-1} V) = V through the oracle's FFT product
+    assert rel(TZ.matvec(a, W), V) <= 1e-14 * kappa
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fractional_expm_matches_eigendecomposition(tab, precision):
+    """Algorithm 2 with the paper's m = 30, k = 30 deflated restart and p = 2 on the fractional
+    operator (n = 2048, ||tA|| ~ 2e5 >> |tau_i|, the regime the preconditioner is for) against
+    the exact r(tA) B and e^{tA} B by the oracle's eigendecomposition."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n, t = 2048, 0.01
+    a = inputs.fractional_column(n)
+    B = inputs.rhs(n, 2, 42)
+    Z, info = Plan.toeplitz(a, n, p_max=2, m=30, k_defl=30, tol=1e-10, precision=precision).expm_block(t, to_dev(B))
+    assert info.converged == 1 and info.algorithm == 2
+    ref = TZ.eig_function(a, B, lambda lam: ops.r_of_lambda_ext(tab, lam), t)
+    assert rel(to_np(Z), ref) <= 1e-9, rel(to_np(Z), ref)
+    ex = TZ.eig_function(a, B, np.exp, t)
+    assert rel(to_np(Z), ex) <= 1e-9 + 1.1 * tab["sigma"] * np.linalg.norm(B) / np.linalg.norm(ex)
+
+
+def test_fractional_workload_full_size(tab):
+    """The toeplitz-frac workload at its size (n = 2^17, ||tA|| ~ 2e8): both precisions converge,
+    the mixed result is within the metric's 1e-8 of the FP64 GPU path, certify mode's true FP64
+    residuals equal the eq. (49) estimates, and the FP64 result agrees with the oracle's
+    literal Algorithm 2 (Levinson generator, its own Gohberg-Semencul products) to the
+    conditioning limit of the inverse (Theorem 4.3)."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    w = inputs.WORKLOADS["toeplitz-frac"]
+    n, p, t = w["n"], w["p"], w["t"][0]
+    a = inputs.fractional_column(n, w["frac"], w["d"])
+    B = inputs.rhs(n, p, w["seed"])
+    kw = dict(p_max=p, m=w["m"], k_defl=w["k_defl"], tol=w["tol"], max_cycles=100)
+    Z64, i64 = Plan.toeplitz(a, n, certify=True, **kw).expm_block(t, to_dev(B))
+    Zm, im = Plan.toeplitz(a, n, precision="mixed", **kw).expm_block(t, to_dev(B))
+    assert i64.converged == 1 and im.converged == 1 and i64.algorithm == 2
+    assert rel(to_np(Zm), to_np(Z64)) <= 1e-8
+    nb = np.linalg.norm(B)
+    for i in range(7):
+        assert abs(i64.true_resid[i] - i64.resid[i]) <= 1e-6 * i64.resid[i] + 1e-11 * nb
+    x = TZ.gsf_generator(a)
+    Zo, io = ps.psbfom(lambda V: TZ.gsf_apply(x, V, t), B, tab, m=w["m"], tol=w["tol"], max_cycles=100,
+                       k=w["k_defl"], align=p)
+    kappa = (abs(a[0]) + 2 * np.abs(a[1:]).sum()) / 27.0
+    assert rel(to_np(Z64), Zo) <= max(1e-10, 1e-15 * kappa), (rel(to_np(Z64), Zo), kappa)

@@ -116,3 +116,67 @@ def test_planted_mistakes_fail():
     # a product that drops the symmetric half (lower triangle only)
     Wl = sl.matmul_toeplitz((a, np.r_[a[0], np.zeros(n - 1)]), V)
     assert np.abs(Wl - TZ.matvec(a, V)).max() > 1e-3
+
+
+# --------------------------------------------------------------------------- Example 5.4 regime
+def test_fractional_column_against_its_definition():
+    """The large-norm workload's column (inputs.fractional_column) against the definition it
+    states, built independently: g_k = (-1)^k binom(beta, k) from scipy's binomial, the shifted
+    Grunwald matrix G[i, j] = g_{i-j+1} assembled entry by entry, A = (d / h^beta)(G + G^T)."""
+    from scipy.special import binom
+    from paper_1405_0707_gb300 import inputs
+    n, beta, d = 200, 1.8, 2.0
+    a = inputs.fractional_column(n, beta, d)
+    g = np.array([(-1.0) ** k * binom(beta, k) for k in range(n + 2)])
+    G = np.zeros((n, n))
+    for i in range(n):
+        for j in range(min(n, i + 2)):
+            G[i, j] = g[i - j + 1]
+    A = d * (n + 1) ** beta * (G + G.T)
+    assert np.allclose(TZ.dense(a), A, rtol=1e-12, atol=1e-12 * np.abs(A).max())
+    # (1 - 1)^beta = 0: the weights sum to zero; with g_1 = -beta the others sum to beta
+    assert abs(g[0] + g[2:].sum() - beta) < 0.05 and abs(g[1] + beta) < 1e-15 and np.all(g[2:] > 0)
+
+
+def test_fractional_operator_is_negative_definite_with_large_norm():
+    """Negative definite (the symbol's largest value a_0 + 2 sum a_k is negative, and so are the
+    eigenvalues of a section), with ||A|| of the order 1e9 at n = 5e4 and 1e10 at n = 2e5 as the
+    paper states for its Example 5.4 matrices."""
+    from paper_1405_0707_gb300 import inputs
+    a = inputs.fractional_column(400)
+    assert np.linalg.eigvalsh(TZ.dense(a)).max() < 0
+    for n, lo, hi in ((50000, 1e9, 1e10), (200000, 1e10, 1e11)):
+        a = inputs.fractional_column(n)
+        norm_bound = abs(a[0]) + 2 * np.abs(a[1:]).sum()       # ||A||_1 = ||A||_inf >= ||A||_2
+        assert lo <= norm_bound < hi, (n, norm_bound)
+        assert a[0] + 2 * np.sort(a[1:])[::-1].sum() < 0
+
+
+def test_eig_function_against_dense_solves_and_expm(table):
+    """The eigendecomposition truth against the partial-fraction sum by dense solves (eq. (11))
+    and against scipy's expm, on a fractional operator small enough for both."""
+    from paper_1405_0707_gb300 import inputs
+    from oracle import psbfom as ps
+    a = inputs.fractional_column(300)
+    B = np.random.default_rng(7).standard_normal((300, 2))
+    t = 1e-3
+    r_eig = TZ.eig_function(a, B, lambda lam: __import__("oracle.operators", fromlist=["x"]).r_of_lambda_ext(table, lam), t)
+    r_dense = ps.dense_r_of_A_B(t * TZ.dense(a), B, table)
+    assert np.linalg.norm(r_eig - r_dense) <= 1e-9 * np.linalg.norm(r_dense)
+    e_eig = TZ.eig_function(a, B, np.exp, t)
+    assert np.linalg.norm(e_eig - sl.expm(t * TZ.dense(a)) @ B) <= 1e-9 * np.linalg.norm(e_eig)
+
+
+def test_gsf_on_a_large_norm_operator():
+    """The Gohberg-Semencul inverse with the Levinson generator on a fractional operator
+    (kappa ~ 1e6 at n = 1024): against a dense solve, to the conditioning limit."""
+    from paper_1405_0707_gb300 import inputs
+    a = inputs.fractional_column(1024)
+    T = TZ.dense(a)
+    V = np.random.default_rng(8).standard_normal((1024, 3))
+    x = TZ.gsf_generator(a)
+    got = TZ.gsf_apply(x, V, 1.0)
+    ref = np.linalg.solve(T, V)
+    kappa = np.linalg.cond(T)
+    assert 1e5 < kappa < 1e8
+    assert np.linalg.norm(got - ref) <= 1e-14 * kappa * np.linalg.norm(ref)
