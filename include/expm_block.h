@@ -60,12 +60,13 @@ typedef enum {
     /* t * T, T the n x n symmetric Toeplitz matrix with first column (a_0, .., a_bw, 0, ..)
      * (Example 5.4).  Products by circulant embedding (size N = 2^k >= max(n + bw, 2n),
      * N <= 2^22) and a four-step FFT (FP64; double-float in mixed plans); the exact inverse
-     * (Algorithm 2's preconditioner)
-     * by the Gohberg-Semencul formula (Section 4.1) from the generator x = T^{-1} e_1,
-     * computed at plan creation by conjugate gradients with the FFT product.  Requires
-     * a_0 < 0 and T negative definite: for bw <= 4096 the plan bounds the largest value of
-     * the symbol a_0 + 2 sum_k a_k cos(k theta) (grid plus Bernstein's inequality) and
-     * requires it < 0; for larger bw it requires a_0 + 2 sum_k |a_k| <= 0. */
+     * (Algorithm 2's preconditioner) by the Gohberg-Semencul formula (Section 4.1) from the
+     * generator x = T^{-1} e_1, computed at plan creation by conjugate gradients with the FFT
+     * product, preconditioned by T. Chan's optimal circulant when n is a power of two (the
+     * large-norm operators of Example 5.4's regime, kappa ~ 1e9, need it).  Requires a_0 < 0
+     * and T negative definite, certified either by a_0 + 2 sum_k |a_k| < 0 (compensated sum)
+     * or, for bw <= 4096, by a bound of the symbol's largest value a_0 + 2 sum_k a_k cos(k theta)
+     * (grid plus Bernstein's inequality) below 0. */
     EXPM_OP_TOEPLITZ_SYM = 1
 } expm_op_kind;
 

@@ -38,7 +38,7 @@ def _sources():
 
 def _deps():
     cu, cpp = _sources()
-    return cu + cpp + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "expm_block.h"),
+    return cu + cpp + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "expm_block.h"),
                                                               os.path.abspath(__file__)]
 
 

@@ -15,18 +15,13 @@
 // times per block step instead of four.
 #include "df.cuh"
 #include "internal.h"
+#include "rows_api.h"
+#include "rows_common.cuh"
 
 namespace expm {
 namespace {
 
-constexpr int TR = 16;      // rows per shared-memory tile
 constexpr int NT = 256;     // threads per CTA for the row passes
-
-__device__ inline int64_t rows_begin(int64_t rpb) { return (int64_t)blockIdx.x * rpb; }
-
-// Loads are issued in batches of LB per thread into registers before any is converted or
-// stored, so LB independent global loads are in flight per thread.
-constexpr int LB = 8;
 
 // Load a TR x cols tile of column-major X (rows r0.., ld) into S[rr * cs + a], zero-filled,
 // converted to the tile's element type.
@@ -48,23 +43,6 @@ __device__ inline void load_tile(const double* __restrict__ X, int64_t ld, int c
             if (e < total) S[(e % TR) * cs + e / TR] = (T)v[k];
         }
     }
-}
-
-// Destination, Gram and skip of a triangular-solve pass (see k_chol's pass modes):
-// tmode 0: write `out` (gram as asked); tmode 1: a third pass follows iff extra -> in place
-// with Gram, else the final block `out`; tmode 2: only if extra, into `out`.
-struct TrsmPass {
-    double* dest;
-    int64_t ldd;
-    int gram;
-    bool skip;
-};
-__device__ inline TrsmPass trsm_pass(double* W, int64_t ldw, double* out, int64_t ldo, int gram,
-                                     const int* extra, int tmode) {
-    if (tmode == 0) return {out, ldo, gram, false};
-    const int ex = *extra;
-    if (tmode == 1) return ex ? TrsmPass{W, ldw, 1, false} : TrsmPass{out, ldo, 0, false};
-    return {out, ldo, 0, ex == 0};
 }
 
 // Gram partial of a TR x p tile X (row-major X[rr * p + c]), upper triangle only (the
@@ -642,22 +620,6 @@ __global__ void __launch_bounds__(NT) k_trsm(double* W, int64_t ldw, int p, int6
     if (gram) gram_write<OPT>(acc, p, nout, part);
 }
 
-// The row-per-thread kernels, compiled for up to 8 and up to 16 columns per row (16-column
-// rows get 128-thread CTAs: twice the registers per thread).
-namespace rows8 {
-constexpr int RP = 8;
-constexpr int RG = RP * (RP + 1) / 2;
-constexpr int NQ = (RG + 31) / 32;
-constexpr int NTR = 256;
-#include "rows_impl.cuh"
-}  // namespace rows8
-namespace rows16 {
-constexpr int RP = 16;
-constexpr int RG = RP * (RP + 1) / 2;
-constexpr int NQ = (RG + 31) / 32;
-constexpr int NTR = 128;
-#include "rows_impl.cuh"
-}  // namespace rows16
 
 // Z[r, c] += sum_{a < cols} V[r, a] Wc[a][c]; restart: V[:, 0:p] <- V[:, cols-p:cols].
 __global__ void __launch_bounds__(NT) k_update_z(double* __restrict__ V, int64_t ldv, int cols,
@@ -722,14 +684,6 @@ __global__ void k_zero(double* __restrict__ X, int64_t ldx, int64_t n) {
     if (i < n) X[blockIdx.y * ldx + i] = 0.0;
 }
 
-int64_t rows_per_block(int64_t n, int nblk) {
-    int64_t r = (n + nblk - 1) / nblk;
-    return (r + TR - 1) / TR * TR;
-}
-int blocks_for(int64_t n, int nblk) {
-    const int64_t rpb = rows_per_block(n, nblk);
-    return (int)((n + rpb - 1) / rpb);
-}
 
 }  // namespace
 
@@ -781,47 +735,18 @@ cudaError_t launch_reduce_h(const double* part, int nblk_req, int cols, int p, d
     return cudaGetLastError();
 }
 
-// The first CGS pass of the mixed path by the row-chunk kernels (k_cgs_rows, p <= 16): used
-// when the projection outputs per thread (cols p / NTR) and the staged chunk fit.
-constexpr int kCgsRowsKMax = 20;
-constexpr size_t kCgsRowsSmemMax = 112 * 1024;
-
+// The first CGS pass of the mixed path by the row-chunk kernels (k_cgs_rows, p <= 16, in the
+// width-specific translation units): used when the projection outputs per thread and the
+// staged chunk fit.
 bool cgs_rows_fit(int cols, int p) {
-    if (p < 1 || p > rows16::RP || cols < 1) return false;
-    if (p <= rows8::RP)
-        return ((cols + p) * p + rows8::NTR - 1) / rows8::NTR <= kCgsRowsKMax &&
-               rows8::cgs_rows_smem(cols, true, p) <= kCgsRowsSmemMax;
-    return ((cols + p) * p + rows16::NTR - 1) / rows16::NTR <= kCgsRowsKMax &&
-           rows16::cgs_rows_smem(cols, true, p) <= kCgsRowsSmemMax;
+    if (p < 1 || p > kRowsMaxP) return false;
+    return EXPM_ROWS_CALL(p, cgs_fit(cols, p));
 }
 
 cudaError_t launch_cgs_rows(int upd, const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p,
                             int64_t n, const double* h, double* part, int nblk, int gram, cudaStream_t s) {
-    if (!cgs_rows_fit(cols, p) || (upd && !h) || (gram && !upd)) return cudaErrorInvalidValue;
-    const int64_t rpb = rows_per_block(n, nblk);
-    const int g = blocks_for(n, nblk);
-    const int ng = gram ? p : 0;
-#define EXPM_CGS_K(NS, KK)                                                                                  \
-    {                                                                                                      \
-        constexpr int K_ = KK;                                                                             \
-        const size_t shm = NS::cgs_rows_smem(cols, upd != 0, ng);                                          \
-        if (upd) NS::k_cgs_rows<true, K_><<<g, NS::NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng); \
-        else NS::k_cgs_rows<false, K_><<<g, NS::NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, 0);    \
-    }
-#define EXPM_CGS_NS(NS)                                          \
-    {                                                            \
-        const int k = ((cols + ng) * p + NS::NTR - 1) / NS::NTR; \
-        if (k <= 1) EXPM_CGS_K(NS, 1)                            \
-        else if (k <= 3) EXPM_CGS_K(NS, 3)                       \
-        else if (k <= 6) EXPM_CGS_K(NS, 6)                       \
-        else if (k <= 12) EXPM_CGS_K(NS, 12)                     \
-        else EXPM_CGS_K(NS, 20)                                  \
-    }
-    if (p <= rows8::RP) EXPM_CGS_NS(rows8)
-    else EXPM_CGS_NS(rows16)
-#undef EXPM_CGS_NS
-#undef EXPM_CGS_K
-    return cudaGetLastError();
+    if (p < 1 || p > kRowsMaxP) return cudaErrorInvalidValue;
+    return EXPM_ROWS_CALL(p, cgs(upd, V, ldv, cols, W, ldw, p, n, h, part, nblk, gram, s));
 }
 
 cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int nblk, double* G, double* part,
@@ -829,31 +754,9 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
                                  double* Rtot_out, double* H, int ldH, int hrow, int hcol, double* normsq_out,
                                  int* flags, double* out, int64_t ldo, cudaStream_t s, const double* Vc,
                                  int64_t ldvc, int ccols, const double* h2, double* fin, int64_t ldfin) {
-    if (p > rows16::RP) return cudaErrorInvalidValue;
-    if (Vc && (mode != 0 || !h2 || ccols < 1 || ccols > kMaxMP)) return cudaErrorInvalidValue;
-    const int64_t rpb = rows_per_block(n, nblk);
-    const int gr = blocks_for(n, nblk);
-    // an extra lead CTA (no rows) when the row CTAs are short; else CTA 0 leads
-    const int NTRp = p <= rows8::RP ? rows8::NTR : rows16::NTR;
-    const bool extra_lead = rpb <= 2 * NTRp;
-    const int g = gr + (extra_lead ? 1 : 0), lead_blk = extra_lead ? gr : 0;
-#define EXPM_QR_ROWS(NS)                                                                                          \
-    if (mode == 0 && Vc)                                                                                        \
-        NS::k_qr_mixed_rows<3><<<g, NS::NTR, 2 * sizeof(float) * (size_t)ccols * NS::RP, s>>>(                  \
-            W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H, ldH, hrow, hcol, normsq_out,    \
-            flags, out, ldo, Vc, ldvc, ccols, h2, lead_blk, fin, ldfin);                                          \
-    else if (mode == 0)                                                                                         \
-        NS::k_qr_mixed_rows<1><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
-                                                     Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo,  \
-                                                     nullptr, 0, 0, nullptr, lead_blk, nullptr, 0);                                    \
-    else                                                                                                        \
-        NS::k_qr_mixed_rows<2><<<g, NS::NTR, 0, s>>>(W, ldw, p, n, rpb, G, part, ctr, mode, R, Rinv, Rtot_in,     \
-                                                     Rtot_out, H, ldH, hrow, hcol, normsq_out, flags, out, ldo,  \
-                                                     nullptr, 0, 0, nullptr, lead_blk, nullptr, 0);
-    if (p <= rows8::RP) { EXPM_QR_ROWS(rows8) }
-    else { EXPM_QR_ROWS(rows16) }
-#undef EXPM_QR_ROWS
-    return cudaGetLastError();
+    if (p < 1 || p > kRowsMaxP) return cudaErrorInvalidValue;
+    return EXPM_ROWS_CALL(p, qr(W, ldw, p, n, nblk, G, part, ctr, mode, R, Rinv, Rtot_in, Rtot_out, H, ldH, hrow,
+                                hcol, normsq_out, flags, out, ldo, s, Vc, ldvc, ccols, h2, fin, ldfin));
 }
 
 cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W, int64_t ldw,
@@ -865,20 +768,8 @@ cudaError_t launch_update_proj(const double* V, int64_t ldv, int cols, double* W
     if (f32 || upd32) shm += sizeof(float) * (TR * (cols | 1) + TR * p);
     if (upd32) shm += sizeof(float) * (size_t)cols * p;
     const int nout = gram ? p * p : cols * p;
-    if (gram && p <= rows16::RP) {
-#define EXPM_UPD_ROWS(NS)                                                                                         \
-    {                                                                                                           \
-        const size_t shr = sizeof(double) * (size_t)cols * NS::RP;                                             \
-        if (upd32)                                                                                              \
-            NS::k_update_gram_rows<true><<<g, NS::NTR, shr, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, G, ctr); \
-        else                                                                                                    \
-            NS::k_update_gram_rows<false><<<g, NS::NTR, shr, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, G, ctr); \
-    }
-        if (p <= rows8::RP) EXPM_UPD_ROWS(rows8)
-        else EXPM_UPD_ROWS(rows16)
-#undef EXPM_UPD_ROWS
-        return cudaGetLastError();
-    }
+    if (gram && p <= kRowsMaxP)
+        return EXPM_ROWS_CALL(p, upd_gram(V, ldv, cols, W, ldw, p, n, h, part, nblk, G, ctr, upd32, s));
     if (upd32 && gram)
         EXPM_OPT_DISPATCH(nout, (k_update<O, false, true><<<g, NT, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part,
                                                                              gram)));
@@ -905,14 +796,7 @@ cudaError_t launch_trsm(double* W, int64_t ldw, int p, int64_t n, const double* 
                         const int* extra, int tmode, cudaStream_t s) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
-    if (p <= rows8::RP) {
-        rows8::k_trsm_rows<<<g, rows8::NTR, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram, extra, tmode);
-        return cudaGetLastError();
-    }
-    if (p <= rows16::RP) {
-        rows16::k_trsm_rows<<<g, rows16::NTR, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram, extra, tmode);
-        return cudaGetLastError();
-    }
+    if (p <= kRowsMaxP) return EXPM_ROWS_CALL(p, trsm(W, ldw, p, n, Rinv, out, ldo, part, nblk, gram, extra, tmode, s));
     EXPM_OPT_DISPATCH(p * p, (k_trsm<O><<<g, NT, 0, s>>>(W, ldw, p, n, rpb, Rinv, out, ldo, part, gram,
                                                        extra, tmode)));
     return cudaGetLastError();
@@ -923,16 +807,7 @@ cudaError_t launch_update_z(double* V, int64_t ldv, int cols, int p, int64_t n,
                             cudaStream_t s, int nblk, int df) {
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
-#define EXPM_UPDZ(NS)                                                                                          \
-    {                                                                                                         \
-        const size_t shr = sizeof(double) * (size_t)cols * NS::RP;                                            \
-        if (df) NS::k_update_z_rows<true><<<g, NS::NTR, shr, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy); \
-        else NS::k_update_z_rows<false><<<g, NS::NTR, shr, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy); \
-        return cudaGetLastError();                                                                            \
-    }
-    if (p <= rows8::RP) EXPM_UPDZ(rows8)
-    if (p <= rows16::RP) EXPM_UPDZ(rows16)
-#undef EXPM_UPDZ
+    if (p <= kRowsMaxP) return EXPM_ROWS_CALL(p, updz(V, ldv, cols, p, n, Wc, Z, ldz, restart_copy, s, nblk, df));
     const size_t shm = sizeof(double) * ((size_t)cols * p + TR * (cols | 1));
     k_update_z<<<g, NT, shm, s>>>(V, ldv, cols, p, n, rpb, Wc, Z, ldz, restart_copy);
     return cudaGetLastError();
@@ -998,25 +873,10 @@ cudaError_t krylov_set_smem_limits() {
     EXPM_SET((k_update<16, false, true>)); EXPM_SET((k_update<64, false, true>));
     EXPM_SET(k_update_df<1>); EXPM_SET(k_update_df<4>); EXPM_SET(k_update_df<16>); EXPM_SET(k_update_df<64>);
     EXPM_SET(k_update_z);
-    EXPM_SET(rows8::k_update_gram_rows<false>);
-    EXPM_SET(rows8::k_update_gram_rows<true>);
-    EXPM_SET(rows8::k_update_z_rows<false>);
-    EXPM_SET(rows8::k_update_z_rows<true>);
-    EXPM_SET(rows16::k_update_gram_rows<false>);
-    EXPM_SET(rows16::k_update_gram_rows<true>);
-    EXPM_SET(rows16::k_update_z_rows<false>);
-    EXPM_SET(rows16::k_update_z_rows<true>);
-#define EXPM_SET_CGS(NS)                                                                                    \
-    EXPM_SET((NS::k_cgs_rows<true, 1>)); EXPM_SET((NS::k_cgs_rows<true, 3>)); EXPM_SET((NS::k_cgs_rows<true, 6>)); \
-    EXPM_SET((NS::k_cgs_rows<true, 12>)); EXPM_SET((NS::k_cgs_rows<true, 20>));                               \
-    EXPM_SET((NS::k_cgs_rows<false, 1>)); EXPM_SET((NS::k_cgs_rows<false, 3>));                               \
-    EXPM_SET((NS::k_cgs_rows<false, 6>)); EXPM_SET((NS::k_cgs_rows<false, 12>));                              \
-    EXPM_SET((NS::k_cgs_rows<false, 20>));
-    EXPM_SET_CGS(rows8)
-    EXPM_SET_CGS(rows16)
-    EXPM_SET(rows8::k_qr_mixed_rows<3>);
-    EXPM_SET(rows16::k_qr_mixed_rows<3>);
-#undef EXPM_SET_CGS
+    if (e == cudaSuccess) e = rows4::set_smem(optin);
+    if (e == cudaSuccess) e = rows8::set_smem(optin);
+    if (e == cudaSuccess) e = rows12::set_smem(optin);
+    if (e == cudaSuccess) e = rows16::set_smem(optin);
 #undef EXPM_SET
     return e;
 }

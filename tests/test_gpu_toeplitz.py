@@ -264,9 +264,12 @@ def test_fractional_workload_full_size(tab):
     Zm, im = Plan.toeplitz(a, n, precision="mixed", **kw).expm_block(t, to_dev(B))
     assert i64.converged == 1 and im.converged == 1 and i64.algorithm == 2
     assert rel(to_np(Zm), to_np(Z64)) <= 1e-8
+    # the true FP64 residuals ||B - (tA - tau_i I) X_i||_F of every pole: forming tA X_i alone
+    # rounds at eps ||tA|| ||X_i|| ~ 1e-9 ||B|| here (||tA|| ~ 2e8), far above the eq. (49)
+    # estimate of a converged solve, so the check is against ||B||
     nb = np.linalg.norm(B)
     for i in range(7):
-        assert abs(i64.true_resid[i] - i64.resid[i]) <= 1e-6 * i64.resid[i] + 1e-11 * nb
+        assert i64.true_resid[i] <= 1e-8 * nb, (i, i64.true_resid[i] / nb)
     x = TZ.gsf_generator(a)
     Zo, io = ps.psbfom(lambda V: TZ.gsf_apply(x, V, t), B, tab, m=w["m"], tol=w["tol"], max_cycles=100,
                        k=w["k_defl"], align=p)
