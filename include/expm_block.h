@@ -269,6 +269,32 @@ expm_status expm_block_batched_host(expm_plan* const* plans, int count, const do
                                     double* const* hZ, const int64_t* ldz, expm_info* info);
 
 /* ---------------------------------------------------------------------------------
+ * expm_batch_create / expm_batch_run / expm_batch_destroy -- many independent solves as ONE
+ * CUDA graph launch (a serving variant; the paper solves one problem at a time).  Instance i
+ * computes dZ[i] = r(t[i] A_i) dB[i] with plans[i] as expm_block would; every instance is one
+ * branch of the graph: its start, a device-side WHILE loop of restart cycles whose stop test
+ * (eq. (49) / eq. (365), max_cycles, fixed_cycles) runs in a kernel and sets the loop's
+ * condition, and its finish.  The branches run concurrently and no host work happens between
+ * cycles.  The graph is built once (create) and replayed by every run with the same
+ * arguments; the buffers dB, dZ must stay valid and in place for the batch's lifetime.
+ *   plans  : distinct plans, each with a stream other than the legacy default stream, no
+ *            deflated restart (opts.k_defl = 0: its eigenproblem runs on the host) and no
+ *            certify mode
+ *   t, dB, ldb, p, dZ, ldz : as expm_block_batched
+ *   stream : cudaStream_t on which expm_batch_run launches the graph
+ *   out    : host, receives the batch (free with expm_batch_destroy)
+ * expm_batch_run launches the graph, synchronises the stream and fills info[i] (may be NULL);
+ * it returns the first hard error, else EXPM_NOT_CONVERGED if any instance stopped
+ * unconverged, else EXPM_OK.  While a batch runs, its plans must not be used by other calls.
+ * Errors: EXPM_INVALID_ARG, EXPM_NO_MEMORY, EXPM_CUDA_ERROR, and those of expm_block. */
+typedef struct expm_batch_s expm_batch;
+expm_status expm_batch_create(expm_plan* const* plans, int count, const double* t,
+                              const double* const* dB, const int64_t* ldb, const int* p,
+                              double* const* dZ, const int64_t* ldz, void* stream, expm_batch** out);
+expm_status expm_batch_run(expm_batch* batch, expm_info* info);
+void expm_batch_destroy(expm_batch* batch);
+
+/* ---------------------------------------------------------------------------------
  * expm_block_adjoint -- the adjoint of Z = r(tA) B for a loss L with G = dL/dZ:
  *   dGB = dL/dB = r(tA)^T G = r(tA^T) G  (r has real coefficients), computed by the same
  *         method on A^T: for EXPM_OP_CONV_DIFF the stencil with the velocity negated

@@ -33,7 +33,8 @@ EXPORTS = ("expm_cf_coeffs", "expm_plan_create", "expm_plan_destroy", "expm_bloc
            "expm_block_host", "expm_op_apply", "expm_prec_apply", "expm_arnoldi",
            "expm_plan_profile", "expm_plan_get_profile", "expm_status_str",
            "expm_prec_apply_noalloc", "expm_block_batched", "expm_block_adjoint", "expm_ritz_basis",
-           "expm_block_batched_host", "expm_peak_fma")
+           "expm_block_batched_host", "expm_peak_fma", "expm_batch_create", "expm_batch_run",
+           "expm_batch_destroy")
 STAGES = ("gemm", "tridiag", "cgs", "reduce", "qr", "poles", "update", "other", "stencil")
 
 
@@ -109,6 +110,13 @@ def load(build_if_missing: bool = False):
     lib.expm_ritz_basis.restype = C.c_int
     lib.expm_ritz_basis.argtypes = [C.POINTER(d), i64, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(d), i64,
                                     C.POINTER(C.c_int)]
+    lib.expm_batch_create.restype = C.c_int
+    lib.expm_batch_create.argtypes = [C.POINTER(p), C.c_int, C.POINTER(d), C.POINTER(p), C.POINTER(i64),
+                                      C.POINTER(C.c_int), C.POINTER(p), C.POINTER(i64), p, C.POINTER(p)]
+    lib.expm_batch_run.restype = C.c_int
+    lib.expm_batch_run.argtypes = [p, C.POINTER(expm_info)]
+    lib.expm_batch_destroy.restype = None
+    lib.expm_batch_destroy.argtypes = [p]
     lib.expm_peak_fma.restype = C.c_int
     lib.expm_peak_fma.argtypes = [C.c_int, i64, C.POINTER(d), p]
     lib.expm_plan_profile.restype = C.c_int
@@ -254,3 +262,26 @@ def expm_peak_fma(kind, iters=1 << 16, stream=0):
     out = C.c_double()
     check(load().expm_peak_fma(int(kind), int(iters), C.byref(out), C.c_void_p(stream)), "expm_peak_fma")
     return out.value
+
+
+def expm_batch_create(plans, ts, dBs, ldbs, ps, dZs, ldzs, stream=0):
+    """One CUDA graph for many independent solves (see include/expm_block.h); returns the handle."""
+    k = len(plans)
+    arr = lambda T, xs: (T * k)(*xs)
+    out = C.c_void_p()
+    check(load().expm_batch_create(arr(C.c_void_p, [pl.value if isinstance(pl, C.c_void_p) else pl for pl in plans]),
+                                   k, arr(C.c_double, ts), arr(C.c_void_p, dBs), arr(C.c_int64, ldbs),
+                                   arr(C.c_int, ps), arr(C.c_void_p, dZs), arr(C.c_int64, ldzs), C.c_void_p(stream),
+                                   C.byref(out)), "expm_batch_create")
+    return out
+
+
+def expm_batch_run(batch, count, allow_not_converged=True):
+    infos = (expm_info * count)()
+    allow = (EXPM_OK, EXPM_NOT_CONVERGED) if allow_not_converged else (EXPM_OK,)
+    code = check(load().expm_batch_run(batch, infos), "expm_batch_run", allow)
+    return code, list(infos)
+
+
+def expm_batch_destroy(batch):
+    load().expm_batch_destroy(batch)

@@ -191,3 +191,36 @@ def expm_block_batched(plans, ts, Bs, Zs=None):
                                        [B.data_ptr() for B in Bs], ldbs, [B.shape[1] for B in Bs],
                                        [Z.data_ptr() for Z in Zs], ldzs, host=host)
     return Zs, infos
+
+
+class Batch:
+    """Many independent solves Z_i = r(t_i A_i) B_i as one CUDA graph launch with device-side
+    stop tests (expm_batch_create / expm_batch_run).  The buffers stay in place: build once,
+    call run() as often as needed (each run recomputes every Z_i from the current B_i)."""
+
+    def __init__(self, plans, ts, Bs, Zs=None, stream=None):
+        import torch
+        self.plans, self.Bs = list(plans), list(Bs)
+        self.Zs = Zs if Zs is not None else [colmajor(pl.n, B.shape[1], device=B.device) for pl, B in zip(plans, Bs)]
+        ldbs = [_check_colmajor(B, pl.n, B.shape[1], "B") for pl, B in zip(plans, Bs)]
+        ldzs = [_check_colmajor(Z, pl.n, B.shape[1], "Z") for pl, B, Z in zip(plans, Bs, self.Zs)]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = N.expm_batch_create([pl._h for pl in plans], [float(t) for t in ts], [B.data_ptr() for B in Bs],
+                                      ldbs, [B.shape[1] for B in Bs], [Z.data_ptr() for Z in self.Zs], ldzs,
+                                      self.stream.cuda_stream)
+
+    def run(self):
+        """Launch the graph; returns (list of Z, list of info)."""
+        code, infos = N.expm_batch_run(self._h, len(self.plans))
+        return self.Zs, infos
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.expm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -343,9 +343,17 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
     if (rows && fused_qr(P, p)) {
         // update, second projection and the Gram matrix of W in one pass; the second pass's
-        // correction is applied by the first Cholesky-QR pass
-        LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(1, P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 1, s));
-        LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols + p, p, h, P->H, P->ldH, 0, j * p, 1, s, cols));
+        // correction is applied by the first Cholesky-QR pass.  On the tensor cores (exact bf16
+        // slicing, k_cgs_tc) when the plan chose it, else on the FP32 pipe (double-float)
+        if (P->cgs_tc && cgs_tc_fit(cols, p)) {
+            int g = 0;
+            LAUNCH(EXPM_STAGE_CGS, launch_cgs_tc(P->V, ld, cols, P->W, ld, p, n, h, P->part, &g, flags_of(P->stat),
+                                                 P->tc_spin, s));
+            LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, g, cols + p, p, h, P->H, P->ldH, 0, j * p, 1, s, cols));
+        } else {
+            LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(1, P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 1, s));
+            LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols + p, p, h, P->H, P->ldH, 0, j * p, 1, s, cols));
+        }
         return qr_block(P, p, P->V + (int64_t)(j + 1) * p * ld, ld, true, (j + 1) * p, j * p, nullptr, true, cols);
     }
     if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(1, P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 0, s));
@@ -362,6 +370,7 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
 
 expm_status check_flags(const double* hstat) {
     const int* f = reinterpret_cast<const int*>(hstat + 24);
+    if (f[0] & 16) return EXPM_TIMEOUT;   // a bounded device-side wait ran out
     if (f[0]) return EXPM_NUMERICAL;
     return EXPM_OK;
 }
@@ -426,7 +435,7 @@ expm_status restart_prologue(expm_plan* P, int p, int kk, int prologue) {
 // projected systems, the update and the restart copy, then the device->host copy of the
 // residual norms and flags (and of H~ when the next restart may deflate); no synchronisation.
 // kk > 0: the basis starts with kk kept Ritz vectors and the block steps begin at block kk/p.
-expm_status issue_cycle(expm_plan* P, double t, int p, int alg, int kk = 0, int prologue = 0) {
+expm_status issue_cycle(expm_plan* P, double t, int p, int alg, int kk = 0, int prologue = 0, bool d2h = true) {
     cudaStream_t s = P->stream;
     const int m = P->opts.m, mp = m * p;
     const int64_t n = P->n, ld = P->ld;
@@ -455,6 +464,7 @@ expm_status issue_cycle(expm_plan* P, double t, int p, int alg, int kk = 0, int 
     const bool defl = P->opts.k_defl > 0;
     LAUNCH(EXPM_STAGE_UPDATE, launch_update_z(P->V, ld, mp + p, p, n, sm(P, kOffWc), P->Zacc, ld, defl ? 0 : 1, s,
                                               P->nblk, P->opts.precision == EXPM_PREC_MIXED ? 1 : 0));
+    if (!d2h) return EXPM_OK;   // the batch graph's stop test reads the status on the device
     CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, s));
     if (defl) CK(cudaMemcpyAsync(P->hH, P->H, sizeof(double) * (size_t)P->ldH * mp, cudaMemcpyDeviceToHost, s));
     return EXPM_OK;
@@ -1071,6 +1081,48 @@ expm_status toeplitz_setup(expm_plan* P, const expm_op_desc* op, bool want_inver
 
 }  // namespace
 
+// A batch: the instances' arguments and the instantiated graph (see expm_batch_create).
+struct expm_batch_s {
+    std::vector<expm_plan*> plans;
+    std::vector<RunState> rs;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int* dctl = nullptr;              // per instance: cycles run, converged
+    int* hctl = nullptr;              // pinned host mirror
+    std::vector<int64_t> fixed_launches, cycle_launches;
+};
+
+namespace {
+
+void batch_free(expm_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->dctl);
+    if (b->hctl) cudaFreeHost(b->hctl);
+    delete b;
+}
+
+// capture fn's stream work on P's stream into a child graph node of G with the given dependency
+template <class F>
+expm_status capture_child(expm_plan* P, cudaGraph_t G, const cudaGraphNode_t* dep, cudaGraphNode_t* out, F fn) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return EXPM_CUDA_ERROR;
+    const expm_status st = fn();
+    const cudaError_t ec = cudaStreamEndCapture(P->stream, &g);
+    if (st != EXPM_OK || ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != EXPM_OK ? st : EXPM_CUDA_ERROR;
+    }
+    const cudaError_t ea = cudaGraphAddChildGraphNode(out, G, dep, dep ? 1 : 0, g);
+    cudaGraphDestroy(g);
+    return ea == cudaSuccess ? EXPM_OK : EXPM_CUDA_ERROR;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* expm_status_str(expm_status s) {
@@ -1150,6 +1202,14 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         // block (the fallback of the single accurate pass)
         const char* sq = std::getenv("EXPM_QR_SINGLE_PASS");
         P->qr_single = !(sq && sq[0] == '0');
+        // the first CGS pass on the tensor cores (k_cgs_tc): "1" selects it for mixed plans.
+        // Off by default: measured on the batched workload it is still slower than the
+        // double-float pass (one 8-warp CTA per SM, see k_cgs_tc.cu)
+        const char* tc = std::getenv("EXPM_CGS_TC");
+        P->cgs_tc = opts->precision == EXPM_PREC_MIXED && tc && tc[0] == '1';
+        // test switch: the bound of the tensor-core kernel's waits (0 makes every wait run out)
+        const char* sl = std::getenv("EXPM_TC_SPIN_LIMIT");
+        if (sl) P->tc_spin = std::strtol(sl, nullptr, 10);
     }
     int64_t n = 1;
     if (toeplitz) {
@@ -1285,7 +1345,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     }
     cudaStream_t s = P->stream;
     bool cuda_ok = krylov_set_smem_limits() == cudaSuccess && poles_set_smem_limits() == cudaSuccess &&
-                   operator_set_smem_limits() == cudaSuccess;
+                   operator_set_smem_limits() == cudaSuccess && cgs_tc_set_smem_limits() == cudaSuccess;
     if (!toeplitz) {
         const int64_t nmodes = P->nmodes;
         for (int d = 1; d < P->ndim && cuda_ok; ++d)
@@ -1457,6 +1517,27 @@ expm_status batched_run(expm_plan* const* plans, int count, const double* t, con
     return worst;
 }
 
+// ---- the batched form as one CUDA graph with device-side stop tests
+//
+// Every instance is one branch of the graph: its start (R^0 = B = V_1 R for every pole), a
+// WHILE conditional node whose body is one restart cycle followed by k_stop, and its finish
+// (Z = omega_0 B + Z_acc and the status back to the host).  k_stop applies the stop test of
+// eq. (49) / eq. (365) on the device and sets the loop's condition, so the whole batched solve
+// is a single graph launch with no host round trip per cycle; the branches run concurrently.
+__global__ void k_stop(const double* __restrict__ stat, int npoles, double tol, int fixed, int max_cycles,
+                       int* ctl, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int c = ctl[0] + 1;
+    ctl[0] = c;
+    double mx = 0.0;
+    for (int i = 0; i < npoles; ++i) mx = fmax(mx, stat[i]);
+    const int flags = reinterpret_cast<const int*>(stat + 24)[0];
+    const bool conv = mx <= tol * sqrt(stat[16]);
+    ctl[1] = conv ? 1 : 0;
+    const bool more = flags == 0 && (fixed > 0 ? c < fixed : (!conv && c < max_cycles));
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1471,6 +1552,150 @@ expm_status expm_block_batched_host(expm_plan* const* plans, int count, const do
                                     const int64_t* ldb, const int* p, double* const* hZ, const int64_t* ldz,
                                     expm_info* info) {
     return batched_run(plans, count, t, hB, ldb, p, hZ, ldz, info, true);
+}
+
+expm_status expm_batch_create(expm_plan* const* plans, int count, const double* t, const double* const* dB,
+                              const int64_t* ldb, const int* p, double* const* dZ, const int64_t* ldz, void* stream,
+                              expm_batch** out) {
+    if (!out || count < 1 || !plans || !t || !dB || !ldb || !p || !dZ || !ldz) return EXPM_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        const expm_status st = validate_block_args(plans[i], t[i], dB[i], ldb[i], p[i], dZ[i], ldz[i]);
+        if (st != EXPM_OK) return st;
+        const expm_plan* P = plans[i];
+        // the device-side loop needs no host work between cycles: no deflated restart (host
+        // eigenproblem), no certify accumulation, a capturable stream
+        if (P->opts.k_defl > 0 || P->opts.certify || !P->stream) return EXPM_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return EXPM_INVALID_ARG;
+    }
+    expm_batch* b = new (std::nothrow) expm_batch_s();
+    if (!b) return EXPM_NO_MEMORY;
+    b->plans.assign(plans, plans + count);
+    b->rs.resize(count);
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    b->fixed_launches.assign(count, 0);
+    b->cycle_launches.assign(count, 0);
+    if (cudaMalloc(reinterpret_cast<void**>(&b->dctl), sizeof(int) * 2 * count) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&b->hctl), sizeof(int) * 2 * count) != cudaSuccess ||
+        cudaGraphCreate(&b->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return EXPM_NO_MEMORY;
+    }
+    for (int i = 0; i < count; ++i) {
+        expm_plan* P = plans[i];
+        RunState& r = b->rs[i];
+        r.t = t[i];
+        r.dB = dB[i];
+        r.ldb = ldb[i];
+        r.p = p[i];
+        r.dZ = dZ[i];
+        r.ldz = ldz[i];
+        int* ctl = b->dctl + 2 * i;
+        const int64_t l0 = P->launches;
+        cudaGraphNode_t nb = nullptr, nc = nullptr, nf = nullptr;
+        expm_status st = capture_child(P, b->graph, nullptr, &nb, [&]() -> expm_status {
+            CK(cudaMemsetAsync(ctl, 0, sizeof(int) * 2, P->stream));
+            return run_begin(P, r);
+        });
+        const int64_t l1 = P->launches;
+        cudaGraphConditionalHandle hdl;
+        cudaGraphNodeParams cp = {};
+        if (st == EXPM_OK) {
+            if (cudaGraphConditionalHandleCreate(&hdl, b->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+                st = EXPM_CUDA_ERROR;
+            } else {
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = hdl;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                if (cudaGraphAddNode(&nc, b->graph, &nb, nullptr, 1, &cp) != cudaSuccess) st = EXPM_CUDA_ERROR;
+            }
+        }
+        if (st == EXPM_OK) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+                cudaSuccess) {
+                st = EXPM_CUDA_ERROR;
+            } else {
+                st = issue_cycle(P, r.t, r.p, r.alg, 0, 0, false);
+                if (st == EXPM_OK) {
+                    k_stop<<<1, 32, 0, P->stream>>>(P->stat, P->npoles, P->opts.tol, P->opts.fixed_cycles,
+                                                     P->opts.max_cycles, ctl, hdl);
+                    if (cudaGetLastError() != cudaSuccess) st = EXPM_CUDA_ERROR;
+                }
+                cudaGraph_t g2 = body;
+                if (cudaStreamEndCapture(P->stream, &g2) != cudaSuccess && st == EXPM_OK) st = EXPM_CUDA_ERROR;
+            }
+        }
+        const int64_t l2 = P->launches;
+        if (st == EXPM_OK)
+            st = capture_child(P, b->graph, &nc, &nf, [&]() -> expm_status {
+                LAUNCH(EXPM_STAGE_OTHER, launch_axpby(P->omega0, r.dB, r.ldb, 1.0, P->Zacc, P->ld, r.dZ, r.ldz, P->n,
+                                                      r.p, P->stream));
+                CK(cudaMemcpyAsync(P->hpin, P->stat, sizeof(double) * kStatDoubles, cudaMemcpyDeviceToHost, P->stream));
+                CK(cudaMemcpyAsync(b->hctl + 2 * i, ctl, sizeof(int) * 2, cudaMemcpyDeviceToHost, P->stream));
+                return EXPM_OK;
+            });
+        // launch accounting: the start and the finish once, the cycle body once per cycle
+        b->fixed_launches[i] = (l1 - l0) + (P->launches - l2);
+        b->cycle_launches[i] = (l2 - l1) + 1;
+        P->launches = l0;
+        if (st != EXPM_OK) {
+            cudaGetLastError();
+            batch_free(b);
+            return st;
+        }
+    }
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return EXPM_CUDA_ERROR;
+    }
+    *out = b;
+    return EXPM_OK;
+}
+
+expm_status expm_batch_run(expm_batch* b, expm_info* info) {
+    if (!b || !b->exec) return EXPM_INVALID_ARG;
+    CK(cudaGraphLaunch(b->exec, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    expm_status worst = EXPM_OK;
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        expm_plan* P = b->plans[i];
+        RunState& r = b->rs[i];
+        r.cycles = b->hctl[2 * i];
+        r.steps = r.cycles * P->opts.m;
+        r.converged = b->hctl[2 * i + 1] != 0;
+        r.normB = std::sqrt(P->hpin[16]);
+        r.result = check_flags(P->hpin);
+        P->launches += b->fixed_launches[i] + (int64_t)r.cycles * b->cycle_launches[i];
+        if (info) {
+            expm_info& f = info[i];
+            std::memset(&f, 0, sizeof(f));
+            f.cycles = r.cycles;
+            f.block_steps = r.steps;
+            f.matvecs = (int64_t)r.steps * r.p;
+            f.converged = r.converged ? 1 : 0;
+            f.npoles = P->npoles;
+            f.breakdown = reinterpret_cast<const int*>(P->hpin + 24)[1] ? 1 : 0;
+            for (int k = 0; k < P->npoles; ++k) f.resid[k] = P->hpin[k];
+            f.normB = r.normB;
+            f.algorithm = r.alg;
+            f.normA_bound = norm_bound(P, r.t);
+        }
+        expm_status st = r.result;
+        if (st == EXPM_OK && P->opts.fixed_cycles == 0 && !r.converged) st = EXPM_NOT_CONVERGED;
+        if (st != EXPM_OK && st != EXPM_NOT_CONVERGED) return st;
+        if (st == EXPM_NOT_CONVERGED) worst = st;
+    }
+    return worst;
+}
+
+void expm_batch_destroy(expm_batch* b) {
+    if (b && b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
 }
 
 expm_status expm_block_adjoint(expm_plan* plan, double t, const double* dG, int64_t ldg, int p,

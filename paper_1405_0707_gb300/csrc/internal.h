@@ -206,6 +206,8 @@ struct expm_plan_s {
     // CUDA graphs of one restart cycle, keyed by (algorithm, p, t)
     bool use_graphs = false;
     bool qr_single = true;     // mixed path: try the single accurate Cholesky-QR pass
+    bool cgs_tc = false;       // mixed path: first CGS pass on the tensor cores (k_cgs_tc)
+    long tc_spin = 1L << 24;   // bound of the tensor-core kernel's mbarrier waits (iterations)
     // deflated restart (opts.k_defl > 0)
     int kdefl_max = 0;         // columns of Vk and Pkd
     double* Vk = nullptr;      // ld x kdefl_max: V_m P_k
@@ -261,6 +263,11 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
                                  const double* Vc = nullptr, int64_t ldvc = 0, int ccols = 0,
                                  const double* h2 = nullptr, double* fin = nullptr, int64_t ldfin = 0);
 constexpr int kRowsMaxP = 16;  // widths handled by the row-per-thread kernels
+// First CGS pass of the mixed path on the tensor cores (k_cgs_tc.cu): p <= 16, cols <= 192.
+bool cgs_tc_fit(int cols, int p);
+cudaError_t launch_cgs_tc(const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p, int64_t n,
+                          const double* h, double* part, int* grid_out, int* flags, long spin_limit, cudaStream_t s);
+cudaError_t cgs_tc_set_smem_limits();
 // Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
 // third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.
 cudaError_t launch_chol(const double* part, int nblk, int p, double shift_rel, double* R,

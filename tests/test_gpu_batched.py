@@ -66,3 +66,57 @@ def test_batched_rejects_repeated_plan():
     B = to_dev(inputs.rhs(50, 1, 1))
     with pytest.raises(ExpmError):
         expm_block_batched([pl, pl], [0.1, 0.2], [B, B])
+
+
+
+def test_batch_graph_matches_batched_call(tab):
+    """The batched solve as one CUDA graph (a device-side WHILE loop of restart cycles per
+    instance, the stop test in a kernel): the same Z, bit for bit, and the same cycle counts as
+    the host-driven expm_block_batched, on a mix of families, orders, widths and precisions;
+    replaying the graph gives the same result again; each Z matches its closed form."""
+    torch = need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    from paper_1405_0707_gb300.api import Batch, expm_block_batched
+    rng = np.random.default_rng(62)
+    specs = [("cd", (41, 35), 0.1, (1.0, 1.0), 0.1, 3, "fp64"),
+             ("cd", (16, 13, 11), 1.0, (2.0, -3.0, 1.5), 0.02, 5, "mixed"),
+             ("cd", (300,), 1.0, (0.0,), 1.0, 1, "fp64"),
+             ("toe", 2500, None, None, 1.0, 4, "mixed"),
+             ("cd", (60, 58, 57), 1.0, (-4.0, 1.0, 2.0), 0.05, 12, "mixed")]
+    plans, Bs, ts = [], [], []
+    for kind, shape, diff, vel, t, p, prec in specs:
+        stream = torch.cuda.Stream()
+        if kind == "cd":
+            pl = Plan(shape, diff, vel, p_max=p, m=8, tol=1e-12, max_cycles=300, stream=stream, precision=prec)
+            n = int(np.prod(shape))
+        else:
+            pl = Plan.toeplitz(inputs.toeplitz_column(256), shape, p_max=p, m=8, tol=1e-13, stream=stream, precision=prec)
+            n = shape
+        plans.append(pl)
+        Bs.append(inputs.rhs(n, p, int(rng.integers(1 << 30))))
+        ts.append(t)
+    Bd = [to_dev(B) for B in Bs]
+    torch.cuda.synchronize()
+    Zr, ir = expm_block_batched(plans, ts, Bd)
+    Zr = [to_np(Z) for Z in Zr]
+    batch = Batch(plans, ts, Bd)
+    for rep in range(2):
+        Zg, ig = batch.run()
+        for (kind, shape, diff, vel, t, p, prec), B, Z, Z0, i_g, i_r in zip(specs, Bs, Zg, Zr, ig, ir):
+            assert i_g.converged == 1 and i_g.cycles == i_r.cycles, (rep, shape, i_g.cycles, i_r.cycles)
+            assert np.array_equal(to_np(Z), Z0), (rep, shape)
+            if kind == "cd":
+                assert rel(Z0, ops.exact_r_of_A_B(shape, diff, vel, t, tab, B)) <= 1e-9
+    batch.close()
+
+
+def test_batch_graph_rejects_host_work_between_cycles():
+    torch = need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    from paper_1405_0707_gb300._native import ExpmError
+    from paper_1405_0707_gb300.api import Batch
+    B = to_dev(inputs.rhs(400, 2, 3))
+    for kw in (dict(k_defl=2), dict(certify=True)):
+        pl = Plan((20, 20), 0.1, (1.0, 1.0), p_max=2, m=4, stream=torch.cuda.Stream(), **kw)
+        with pytest.raises(ExpmError):
+            Batch([pl], [0.1], [B])
