@@ -155,6 +155,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched3d-64")
     ap.add_argument("--k-defl", type=int, default=0, help="deflated restart: Ritz vectors kept (0 = plain)")
+    ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_1405_0707_gb300", "tuning", "batched3d-64.json"),
+                    help="autotuner table of launch shapes (paper_1405_0707_gb300/autotune.py); '' = defaults")
+    ap.add_argument("--graph", type=int, default=1,
+                    help="batched workload: 1 = one CUDA graph launch per step (expm_batch_run), 0 = the "
+                         "host-driven expm_block_batched")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--component", default=None, choices=[None, "prec", "stencil", "expm", "step", "fmapeak"],
                     help="time one entry point of the library on the workload's shapes "
@@ -555,7 +560,7 @@ def run_batched(args):
 
     from paper_1405_0707_gb300 import Plan, inputs
     from paper_1405_0707_gb300 import _native as N
-    from paper_1405_0707_gb300.api import colmajor, expm_block_batched
+    from paper_1405_0707_gb300.api import Batch, colmajor, expm_block_batched
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -570,8 +575,18 @@ def run_batched(args):
     N.load()
     streams = [torch.cuda.Stream(device=dev) for _ in inst]
     main = torch.cuda.current_stream(dev)
+    from paper_1405_0707_gb300 import autotune
+    table = autotune.load(args.tuning)
+    taus, _, _, _ = N.expm_cf_coeffs(14)
+    tmax = max(abs(z) for z in taus)
+
+    def tuned(d, prec):
+        bound = d["t"] * sum(4.0 * d["diff"] * (s_ + 1) ** 2 for s_ in d["sides"])
+        alg = 2 if bound >= 50.0 * tmax else 1
+        return autotune.options_for(table, len(d["sides"]), int(np.prod(d["sides"])), d["p"], prec, alg)
     plans = {prec: [Plan(d["sides"], d["diff"], d["vel"], p_max=d["p"], m=w["m"], tol=w["tol"], max_cycles=400,
-                         stream=st, precision=prec, k_defl=args.k_defl) for d, st in zip(inst, streams)]
+                         stream=st, precision=prec, k_defl=min(args.k_defl, (w["m"] - 1) * d["p"]), **tuned(d, prec))
+                    for d, st in zip(inst, streams)]
              for prec in ("mixed", "fp64")}
     ns = [int(np.prod(d["sides"])) for d in inst]
     ps = [d["p"] for d in inst]
@@ -584,8 +599,14 @@ def run_batched(args):
     hZ = [torch.empty((p, n), dtype=torch.float64).pin_memory().T for n, p in zip(ns, ps)]
     torch.cuda.synchronize()
 
+    graphs = {}
+
     def step(prec, Z=None):
-        return expm_block_batched(plans[prec], ts, Bd, Z if Z is not None else Zd)
+        if Z is not None or not args.graph or args.k_defl:
+            return expm_block_batched(plans[prec], ts, Bd, Z if Z is not None else Zd)
+        if prec not in graphs:   # one CUDA graph per precision, built once (its buffers stay in place)
+            graphs[prec] = Batch(plans[prec], ts, Bd, Zd, stream=main)
+        return graphs[prec].run()
 
     def timed(fn, k):
         tot = 0.0
@@ -706,6 +727,10 @@ def run_batched(args):
                        "floor_instances": [{"k": k_, "z_over_b": nzb, "err_over_b": eb} for k_, nzb, eb in floor_g]},
                    "cycles_total": sum(cyc), "algorithm_counts": {"1": algs.count(1), "2": algs.count(2)},
                    "converged": res[head]["converged"], "streams": len(streams),
+                   "launch": ("one CUDA graph launch per step (expm_batch_run: a device-side loop of restart "
+                              "cycles per instance)" if args.graph and not args.k_defl else
+                              "expm_block_batched (host-driven cycles on per-instance streams)"),
+                   "tuning": (os.path.relpath(args.tuning, ROOT) if table else "library defaults"),
                    "l2": "inputs far larger than L2 (1.3 GB of B); a 512 MB buffer is also written before "
                          "every timed step",
                    "parallelism": f"replicas x{world}"},
@@ -727,6 +752,8 @@ def run_batched(args):
         line["cpu_baseline"] = batched_cpu_baseline(inst, w, cyc, algs)
     elif rank == 0:
         line["cpu_baseline"] = None
+    for g_ in graphs.values():
+        g_.close()
     for lst in plans.values():
         for pl in lst:
             pl.close()

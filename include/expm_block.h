@@ -129,6 +129,11 @@ typedef struct {
                               block width p and conjugate pairs are kept together (see
                               expm_ritz_basis); 0 = plain restart.  Requires
                               k_defl <= (m - 1) p_max.                                 */
+    int32_t row_ctas_per_sm;  /* launch shape of the row-parallel passes (Cholesky-QR, Z
+                                 update, reductions): CTAs per SM, 1..8; 0 = 2          */
+    int32_t cgs_ctas_per_sm;  /* ... of the first Gram-Schmidt pass: 1..8; 0 = twice
+                                 row_ctas_per_sm.  Both are what the autotuner of the
+                                 Python package chooses per problem class.             */
 } expm_opts;
 
 #define EXPM_MAX_POLES 16

@@ -47,7 +47,8 @@ class expm_op_desc(C.Structure):
 class expm_opts(C.Structure):
     _fields_ = [("m", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double),
                 ("precision", C.c_int32), ("fixed_cycles", C.c_int32), ("algorithm", C.c_int32),
-                ("certify", C.c_int32), ("nu_cf", C.c_int32), ("k_defl", C.c_int32)]
+                ("certify", C.c_int32), ("nu_cf", C.c_int32), ("k_defl", C.c_int32),
+                ("row_ctas_per_sm", C.c_int32), ("cgs_ctas_per_sm", C.c_int32)]
 
 
 class expm_info(C.Structure):

@@ -39,7 +39,7 @@ class Plan:
 
     def __init__(self, sides, diff, vel, p_max, m=10, tol=1e-10, max_cycles=200,
                  fixed_cycles=0, stream=None, algorithm=0, precision="fp64", certify=False, nu=0,
-                 k_defl=0, _op=None):
+                 k_defl=0, row_ctas=0, cgs_ctas=0, _op=None):
         import torch
         if _op is None:
             sides = tuple(int(s) for s in sides)
@@ -63,6 +63,8 @@ class Plan:
         opts.certify = 1 if certify else 0
         opts.nu_cf = int(nu)                   # 0: the paper's degree 14
         opts.k_defl = int(k_defl)              # 0: plain restart
+        opts.row_ctas_per_sm = int(row_ctas)   # launch shape (0: library defaults; see autotune)
+        opts.cgs_ctas_per_sm = int(cgs_ctas)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
         self.tol, self.max_cycles, self.algorithm, self.precision = tol, max_cycles, algorithm, precision

@@ -1186,6 +1186,8 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     if (opts->nu_cf != 0 && (opts->nu_cf < 2 || opts->nu_cf > 2 * EXPM_MAX_POLES || opts->nu_cf % 2 != 0))
         return EXPM_INVALID_ARG;
     if (opts->k_defl < 0 || (int64_t)opts->k_defl > (int64_t)(opts->m - 1) * p_max) return EXPM_INVALID_ARG;
+    if (opts->row_ctas_per_sm < 0 || opts->row_ctas_per_sm > 8 || opts->cgs_ctas_per_sm < 0 || opts->cgs_ctas_per_sm > 8)
+        return EXPM_INVALID_ARG;
     expm_plan* P = new (std::nothrow) expm_plan_s();
     if (!P) return EXPM_NO_MEMORY;
     P->op = *op;
@@ -1261,15 +1263,13 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         return EXPM_CUDA_ERROR;
     }
     {
-        // CTAs of the row-parallel passes: blocks_per_sm x SMs, at least 64 rows each
-        int per_sm = 2;
-        const char* bs = std::getenv("EXPM_BLOCKS_PER_SM");   // tuning knob (1..8)
-        if (bs && bs[0] >= '1' && bs[0] <= '8' && bs[1] == 0) per_sm = bs[0] - '0';
+        // CTAs of the row-parallel passes: blocks_per_sm x SMs, at least 64 rows each (the
+        // plan options, as an autotuner picks them; else 2, and twice that for the first CGS
+        // pass, measured best on the 256 x 256 workload)
+        int per_sm = opts->row_ctas_per_sm > 0 ? opts->row_ctas_per_sm : 2;
         P->nblk = consistent_blocks(n, std::max(1, std::min<int>(per_sm * sms, (int)((n + 63) / 64))));
         // the first CGS pass (projection, update) may use more CTAs than the other row passes
-        int per_sm_cgs = 2 * per_sm;   // measured best for the 256 x 256 workload
-        const char* bc = std::getenv("EXPM_CGS_BLOCKS_PER_SM");   // tuning knob (1..8)
-        if (bc && bc[0] >= '1' && bc[0] <= '8' && bc[1] == 0) per_sm_cgs = bc[0] - '0';
+        const int per_sm_cgs = opts->cgs_ctas_per_sm > 0 ? opts->cgs_ctas_per_sm : 2 * per_sm;
         P->nblk_cgs = consistent_blocks(n, std::max(1, std::min<int>(per_sm_cgs * sms, (int)((n + 63) / 64))));
     }
     const int m = opts->m;

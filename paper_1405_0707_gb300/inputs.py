@@ -34,6 +34,9 @@ WORKLOADS = {
     "toeplitz-1m": dict(n=1 << 20, bw=256, c=0.0, t=(1.0,), p=16, m=10, tol=1e-13,
                         seed=SEED_BASE + 3),
     "batched3d-64": dict(count=64, m=10, tol=1e-10, seed=SEED_BASE + 4),
+    # one instance of the batched workload's largest class (96^3 grid, p = 16), for profiling
+    "cd3d-96": dict(sides=(96, 96, 96), diff=1.0, vel=(1.0, -1.0, 0.5), t=(0.01,), p=16, m=10, tol=1e-10,
+                    seed=SEED_BASE + 7),
     # the large-norm Toeplitz regime of Example 5.4 (||A|| ~ 2e10 at n = 2^17): beta = 1.8,
     # p = 2, m = 30 and k = 30 deflated Ritz vectors as in the paper; t = 0.01 (at the paper's
     # t = 1 the result is ~1e-13 ||B||, below the CF approximation's own error), tol 1e-10
