@@ -767,7 +767,8 @@ def run_batched(args):
 # --------------------------------------------------------------------------- oracle arm
 def auto_algorithm(workload, t):
     """The library's AUTO rule, restated on the host: Algorithm 2 iff the Gershgorin bound
-    of ||tA|| is >= 50 max|tau| (eq. (43)).  The pole modulus comes from the stored table."""
+    of ||tA|| is >= EXPM_AUTO_RATIO max|tau| (eq. (43)).  The pole modulus comes from the stored
+    table."""
     import numpy as np
 
     from oracle import cf
@@ -778,7 +779,8 @@ def auto_algorithm(workload, t):
     else:
         bound = t * sum(4.0 * w["diff"] * (s + 1) ** 2 for s in w["sides"])
     taumax = max(abs(z) for z in cf.load_table()["tau"])
-    return 2 if bound >= 50.0 * taumax else 1
+    from paper_1405_0707_gb300 import _native as N
+    return 2 if bound >= N.EXPM_AUTO_RATIO * taumax else 1
 
 
 TOEPLITZ_SAMPLE_ROWS = 1 << 17

@@ -19,6 +19,7 @@ EXPM_CUDA_ERROR = 5
 EXPM_NO_MEMORY = 6
 EXPM_INTERNAL = 7
 EXPM_TIMEOUT = 8
+EXPM_AUTO_RATIO = 36.0     # the AUTO rule's ratio (include/expm_block.h)
 EXPM_OP_CONV_DIFF = 0
 EXPM_OP_TOEPLITZ_SYM = 1
 EXPM_PREC_FP64 = 0

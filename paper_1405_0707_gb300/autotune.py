@@ -117,17 +117,15 @@ def main():
     taus, _, _, _ = N.expm_cf_coeffs(14)
     tmax = max(abs(z) for z in taus)
 
-    def auto_alg(d):   # the library's AUTO rule: Algorithm 2 iff the Gershgorin bound >= 50 max|tau|
+    def auto_alg(d):   # the library's AUTO rule: Algorithm 2 iff the Gershgorin bound >= ratio max|tau|
         bound = d["t"] * sum(4.0 * d["diff"] * (s + 1) ** 2 for s in d["sides"])
-        return 2 if bound >= N_AUTO_RATIO * tmax else 1
+        return 2 if bound >= N.EXPM_AUTO_RATIO * tmax else 1
     table = tune_batched(inst, w["m"], a.precision, auto_alg, a.reps, load(a.out))
     with open(a.out, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
     wins = sum(1 for v in table.values() if v["best"] != list(DEFAULT))
     print(json.dumps({"classes": len(table), "tuned_differently": wins, "out": a.out}))
 
-
-N_AUTO_RATIO = 50.0   # EXPM_AUTO_RATIO of include/expm_block.h
 
 if __name__ == "__main__":
     main()

@@ -41,6 +41,19 @@ def test_exports_every_declared_symbol(lib):
     assert set(N.EXPORTS) <= names
 
 
+def test_binding_constants_match_the_header():
+    """The binding's status codes and AUTO ratio mirror include/expm_block.h's values."""
+    from paper_1405_0707_gb300 import _native as N
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "expm_block.h")).read(), flags=re.S)
+    ratio = re.search(r"#define\s+EXPM_AUTO_RATIO\s+([0-9.]+)", src)
+    assert ratio and float(ratio.group(1)) == N.EXPM_AUTO_RATIO
+    codes = dict(re.findall(r"\b(EXPM_(?:OK|INVALID_ARG|NOT_CONVERGED|BREAKDOWN|NUMERICAL|CUDA_ERROR|NO_MEMORY|"
+                            r"INTERNAL|TIMEOUT))\s*=\s*(\d+)", src))
+    assert len(codes) == 9
+    for name, v in codes.items():
+        assert getattr(N, name) == int(v), name
+
+
 def test_library_cf_table_matches_oracle(lib):
     from paper_1405_0707_gb300 import _native as N
     tau, om, w0, sig = N.expm_cf_coeffs(14)

@@ -124,10 +124,11 @@ def test_algorithm1_parity_with_oracle(tab, sides, diff, vel, t, p, m):
 
 
 def test_auto_selection_follows_norm_ratio(tab):
-    """AUTO runs Algorithm 2 only when the Gershgorin bound of ||tA|| is >= 50 max|tau|
+    """AUTO runs Algorithm 2 only when the Gershgorin bound of ||tA|| is >= EXPM_AUTO_RATIO max|tau|
     (eq. (43)); both choices converge to the closed form here."""
     need_gpu()
     from paper_1405_0707_gb300 import Plan
+    from paper_1405_0707_gb300 import _native as N
     sides, diff, vel, p = (48, 40), 0.1, (1.0, 1.0), 2
     n = 48 * 40
     B = inputs.rhs(n, p, 5)
@@ -138,7 +139,7 @@ def test_auto_selection_follows_norm_ratio(tab):
         h2 = [1.0 / (s + 1) ** 2 for s in sides]
         bound = t * sum(4 * diff / h for h in h2)
         assert abs(info.normA_bound - bound) <= 1e-12 * bound
-        assert info.algorithm == (2 if bound >= 50 * taumax else 1)
+        assert info.algorithm == (2 if bound >= N.EXPM_AUTO_RATIO * taumax else 1)
         ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
         assert info.converged == 1 and rel(to_np(Zg), ref) < 1e-9, (t, rel(to_np(Zg), ref))
 
