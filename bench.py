@@ -165,6 +165,7 @@ def parse():
                     help="time one entry point of the library on the workload's shapes "
                          "(used for the ncu captures) instead of the full bench")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--instance", type=int, default=0, help="--component on a batched workload: the instance")
     ap.add_argument("--t", type=float, default=None)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the --component run")
@@ -980,11 +981,23 @@ def run_component(args):
         print(json.dumps(out))
         return
 
-    from paper_1405_0707_gb300 import inputs
+    from paper_1405_0707_gb300 import autotune, inputs
     w = inputs.WORKLOADS[args.workload]
+    kw = {}
+    if "count" in w:   # one instance of a batched workload (--instance), with its tuned launch shape
+        d = inputs.batched3d_instances(w["count"], w["seed"])[args.instance]
+        w = dict(sides=d["sides"], diff=d["diff"], vel=d["vel"], t=(d["t"],), p=d["p"], m=w["m"], tol=w["tol"],
+                 seed=d["seed"])
+        if args.precision == "mixed":
+            from paper_1405_0707_gb300 import _native as N
+            N.load()
+            taus = N.expm_cf_coeffs(14)[0]
+            bound = d["t"] * sum(4.0 * d["diff"] * (s_ + 1) ** 2 for s_ in d["sides"])
+            alg = 2 if bound >= N.EXPM_AUTO_RATIO * max(abs(z) for z in taus) else 1
+            kw = autotune.options_for(autotune.load(args.tuning), 3, workload_n(w), d["p"], "mixed", alg)
     n, p = workload_n(w), w["p"]
     t = args.t if args.t is not None else max(w["t"])
-    plan = make_plan(w, args.precision, algorithm=2 if args.component == "prec" else 0)
+    plan = make_plan(w, args.precision, algorithm=2 if args.component == "prec" else 0, **kw)
     B = inputs.to_device_colmajor(inputs.rhs(n, p, w["seed"]))
     Wd = torch.empty((p, n), dtype=torch.float64, device="cuda").T
     def whole_step():   # one bench step: every t of the workload

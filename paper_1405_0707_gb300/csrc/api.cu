@@ -154,11 +154,14 @@ expm_status inv32_apply(expm_plan* P, double t, const void* R, int64_t ldr, int 
     const int64_t nxy = (int64_t)nx * ny;
     GemmArgsMixed g1{R, P->Qf32[2], P->T2f, (int)nxy, nz, nz, 1, nxy, ldr, 0, 1, nxy, ld, 0, nz, p, 1, r_f64, 0, 0};
     LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g1, s));
-    GemmArgsMixed g2{P->T2f, P->Qf32[1], P->T1f, nx, ny, ny, 1, nx, ld, nxy, (int64_t)ny * nz, 1, ld, ny, ny, p, nz, 0, 0, 0};
+    // the y transforms take (x, z) as one row index of nx nz rows (no padding per x line)
+    GemmArgsMixed g2{P->T2f, P->Qf32[1], P->T1f, nx * nz, ny, ny, 1, nx, ld, 0, (int64_t)ny * nz, 1, ld, 0, ny, p, 1,
+                     0, 0, 0, nx, nxy, ny};
     LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g2, s));
     LAUNCH(EXPM_STAGE_TRIDIAG, launch_tridiag_lines32(P->T1f, ld, p, nx, (int64_t)ny * nz, lsub, P->th_m32,
                                                       P->th_c32, inv_t, s));
-    GemmArgsMixed g3{P->T1f, P->Qi32[1], P->T2f, nx, ny, ny, (int64_t)ny * nz, 1, ld, ny, 1, nx, ld, nxy, ny, p, nz, 0, 0, 0};
+    GemmArgsMixed g3{P->T1f, P->Qi32[1], P->T2f, nx * nz, ny, ny, (int64_t)ny * nz, 1, ld, 0, 1, nx, ld, 0, ny, p, 1,
+                     0, 0, 0, nx, ny, nxy};
     LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g3, s));
     GemmArgsMixed g4{P->T2f, P->Qi32[2], X, (int)nxy, nz, nz, 1, nxy, ld, 0, 1, nxy, ldx, 0, nz, p, 1, 0, 1, acc};
     LAUNCH(EXPM_STAGE_GEMM, launch_gemm32(g4, s));

@@ -44,6 +44,10 @@ struct GemmArgsMixed {
     int ldb;
     int nb1, nb2;
     int a_f64, c_f64, accumulate;
+    // ms > 0: the row index m is a pair (m % ms, m / ms) with strides (a_rs, a_ms2) in A and
+    // (c_rs, c_ms2) in C, so two grid axes form one long M dimension (no padding per line)
+    int ms = 0;
+    int64_t a_ms2 = 0, c_ms2 = 0;
 };
 
 // Four-step FFT geometry: N = N1 N2 (powers of two), C adjacent columns per block in the

@@ -8,6 +8,7 @@
 // the shift lambda_y + lambda_z, transform back.  The transforms are small dense GEMMs
 // (DST-I for N + 1 prime or odd has no cheap power-of-two FFT), the line solves use a
 // Thomas factorisation built once per mode at plan creation.
+#include "df.cuh"
 #include "internal.h"
 
 namespace expm {
@@ -286,7 +287,30 @@ constexpr int BK32 = 32;   // k-depth of one FP32 tile
 
 // FP32 tiles of 64 x 64 outputs, 4 x 4 per thread; the next k-tile's global loads are
 // issued into registers before the current tile's FMAs (software pipelining), so each
-// barrier round overlaps its loads with arithmetic.
+// barrier round overlaps its loads with arithmetic.  FP64 operands are converted from the
+// bit pattern (f32_rn_i) and FP64 results formed with an exact float -> double widening,
+// keeping the transforms off GB300's FP64 pipe except for the one accumulating add.
+__device__ __forceinline__ int64_t gemm_row_off(int m, int ms, int64_t rs, int64_t ms2) {
+    return ms ? (int64_t)(m % ms) * rs + (int64_t)(m / ms) * ms2 : (int64_t)m * rs;
+}
+
+__device__ __forceinline__ float gemm_in(double x) { return f32_rn_i(x); }
+__device__ __forceinline__ float gemm_in(float x) { return x; }
+
+// exact float -> double from the bit pattern (normal floats and zero; others by hardware)
+__device__ __forceinline__ double f64_of_f32_i(float x) {
+    const unsigned u = __float_as_uint(x), ex = (u >> 23) & 0xFFu;
+    if (ex == 0u || ex == 0xFFu) return (u & 0x7FFFFFFFu) ? (double)x : __longlong_as_double((long long)(u >> 31) << 63);
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(ex + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+template <typename TC>
+__device__ __forceinline__ void gemm_out(TC* dst, float v, int acc) {
+    if constexpr (sizeof(TC) == 8) *dst = acc ? *dst + f64_of_f32_i(v) : f64_of_f32_i(v);
+    else *dst = acc ? *dst + v : v;
+}
+
 template <bool CM, typename TA, typename TC>
 __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
     // rows padded to BM + 4 floats: 16-byte aligned rows for the float4 operand loads
@@ -304,16 +328,21 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     constexpr int NQ = BK32 * BM / 256;   // elements of each tile per thread (8)
+    // A-row offset of each of this thread's fetched elements (-1 past M), fixed over k
+    int64_t aoff[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int e = tid + q * 256;
+        const int gm = m0 + (a_mfast ? e % BM : e / BK32);
+        aoff[q] = gm < g.M ? gemm_row_off(gm, g.ms, g.a_rs, g.a_ms2) : -1;
+    }
     float ra[NQ], rb[NQ];
     auto fetch = [&](int k0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int e = tid + q * 256;
-            int mm, kk;
-            if (a_mfast) { mm = e % BM; kk = e / BM; }
-            else { kk = e % BK32; mm = e / BK32; }
-            const int gm = m0 + mm, gk = k0 + kk;
-            ra[q] = (gm < g.M && gk < g.K) ? (float)A[(int64_t)gm * g.a_rs + (int64_t)gk * g.a_cs] : 0.f;
+            const int gk = k0 + (a_mfast ? e / BM : e % BK32);
+            ra[q] = (aoff[q] >= 0 && gk < g.K) ? gemm_in(A[aoff[q] + (int64_t)gk * g.a_cs]) : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -353,15 +382,16 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
     }
     const int mi = 4 * (CM ? tx : ty), nj = 4 * (CM ? ty : tx);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + mi + i;
+        if (m >= g.M) continue;
+        TC* crow = C + gemm_row_off(m, g.ms, g.c_rs, g.c_ms2);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int m = m0 + mi + i, nn = n0 + nj + j;
-            if (m < g.M && nn < g.N) {
-                TC* dst = C + (int64_t)m * g.c_rs + (int64_t)nn * g.c_cs;
-                *dst = g.accumulate ? (TC)(*dst + (TC)acc[i][j]) : (TC)acc[i][j];
-            }
+            const int nn = n0 + nj + j;
+            if (nn < g.N) gemm_out(crow + (int64_t)nn * g.c_cs, acc[i][j], g.accumulate);
         }
+    }
 }
 
 // The FP32 line solves with the lines staged in shared memory: a CTA takes TK consecutive
@@ -470,6 +500,35 @@ __global__ void __launch_bounds__(TK * TSG) k_tridiag_tile32(float* y_io, int64_
         const int x = e / TK, kk2 = e - x * TK;
         const int64_t k = k0 + kk2;
         if (k < nmodes) y[(int64_t)x * nmodes + k] = F[kk2 * Lp + x + x / seglen];
+    }
+}
+
+// Short lines with many modes (the x lines of a 3-D grid, L <= 128, ny nz modes): one thread
+// per (mode, column) runs both sweeps of the factored solve over its line, consecutive
+// threads on consecutive modes (coalesced: the layout is mode-fastest).  The sweeps' loads
+// do not depend on the recurrence, so unrolling keeps several of them in flight; the forward
+// sweep's results stay in place (in L2) for the backward sweep.
+__global__ void __launch_bounds__(256) k_tridiag_thread32(float* y_io, int64_t ld, int L, int64_t nmodes,
+                                                          float l_sub, const float* __restrict__ thm,
+                                                          const float* __restrict__ thc, float inv_t) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nmodes) return;
+    float* y = y_io + (int64_t)blockIdx.y * ld + k;
+    const float* m = thm + k;
+    const float* cc = thc + k;
+    float prev = 0.f;
+#pragma unroll 8
+    for (int x = 0; x < L; ++x) {
+        const int64_t o = (int64_t)x * nmodes;
+        prev = (y[o] * inv_t - l_sub * prev) * m[o];
+        y[o] = prev;
+    }
+    float next = prev;                               // x = L - 1: no coupling above
+#pragma unroll 8
+    for (int x = L - 2; x >= 0; --x) {
+        const int64_t o = (int64_t)x * nmodes;
+        next = y[o] - cc[o] * next;
+        y[o] = next;
     }
 }
 
@@ -619,6 +678,11 @@ cudaError_t launch_gemm32(const GemmArgsMixed& g, cudaStream_t s) {
 cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t nmodes, float l_sub,
                                    const float* th_m, const float* th_c, float inv_t,
                                    cudaStream_t s) {
+    if (L <= 128 && nmodes >= 1024) {
+        const dim3 grid((unsigned)((nmodes + 255) / 256), (unsigned)p);
+        k_tridiag_thread32<<<grid, 256, 0, s>>>(y, ld, L, nmodes, l_sub, th_m, th_c, inv_t);
+        return cudaGetLastError();
+    }
     const size_t shm = tridiag_tile_smem(L);
     if (shm <= kTridiagTileSmemMax) {
         const dim3 grid((unsigned)((nmodes + TK - 1) / TK), (unsigned)p);

@@ -54,7 +54,7 @@ __device__ inline void warp_gram_rows(const double* y, double* buf, double* acc)
 __device__ inline void warp_gram_rows32(const double* y, float* buf, float* acc) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int c = 0; c < RP; ++c) buf[lane * RP + c] = (float)y[c];
+    for (int c = 0; c < RP; ++c) buf[lane * RP + c] = f32_rn_i(y[c]);
     __syncwarp();
     for (int q = 0; q < NQ; ++q) {
         const int kk = lane + 32 * q;
@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         if (KIND == 3 && ok) {
 #pragma unroll 8
             for (int a = 0; a < ccols; ++a) {
-                const float v = (float)Vc[(int64_t)a * ldvc + r];
+                const float v = f32_rn_i(Vc[(int64_t)a * ldvc + r]);
 #pragma unroll
                 for (int c = 0; c < RP; ++c) corr[c] = fmaf(v, h2f[a * RP + c], corr[c]);
             }
@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
 #pragma unroll
             for (int c = 0; c < RP; ++c) {
                 float sh, sl;
-                split_df(w[c], sh, sl);
+                split_df_i(w[c], sh, sl);
                 if (KIND == 3) df_add(sh, sl, -corr[c]);
 #pragma unroll
                 for (int a = 0; a < c; ++a) {
@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         } else {
             float wf[RP];
 #pragma unroll
-            for (int c = 0; c < RP; ++c) wf[c] = (float)w[c];
+            for (int c = 0; c < RP; ++c) wf[c] = f32_rn_i(w[c]);
 #pragma unroll
             for (int c = 0; c < RP; ++c) {
                 float s = 0.f;
@@ -952,7 +952,7 @@ __global__ void __launch_bounds__(NTR) k_update_gram_rows(const double* __restri
             for (int c = 0; c < RP; ++c) corr[c] = 0.f;
 #pragma unroll 8
             for (int a = 0; a < cols; ++a) {
-                const float v = (float)V[(int64_t)a * ldv + r];
+                const float v = f32_rn_i(V[(int64_t)a * ldv + r]);
 #pragma unroll
                 for (int c = 0; c < RP; ++c) corr[c] = fmaf(v, hsf[a * RP + c], corr[c]);
             }
@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     float vh, vl;
-                    split_df(v[u], vh, vl);
+                    split_df_i(v[u], vh, vl);
                     const float4* x4 = reinterpret_cast<const float4*>(wh + (a + u) * RP);
                     const float4* y4 = reinterpret_cast<const float4*>(wl + (a + u) * RP);
 #pragma unroll
@@ -1036,7 +1036,7 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
             }
             for (; a < cols; ++a) {
                 float vh, vl;
-                split_df(V[(int64_t)a * ldv + r], vh, vl);
+                split_df_i(V[(int64_t)a * ldv + r], vh, vl);
 #pragma unroll
                 for (int c = 0; c < RP; ++c) df_fma(sh[c], sl[c], vh, vl, wh[a * RP + c], wl[a * RP + c]);
             }
@@ -1066,60 +1066,126 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
 //
 // k_cgs_rows<false>: partial[blk][a][c] = sum over the CTA's rows of V[r, a] W[r, c] (FP32
 // products; the projection of the first pass).
-// k_cgs_rows<true>:  W <- W - V h in double-float arithmetic (as k_update_df: each product
+// k_cgs_rows<true>:  W <- W - V h in double-float arithmetic (each product
 // v h = vh hh + (err(vh hh) + vl hh + vh hl), the large parts accumulated with TwoSum), then
 // the FP32 partials of V^T W for the second pass; with ng = p also the Gram partial W^T W
 // in double-float (outputs cols p .. (cols + p) p, full p x p), which feeds the double-float
 // factorisation of the single-pass Cholesky-QR.
-// Per chunk the FP32 copy of V (cols x RB) and of W (RB x RP) are staged in shared memory
-// and the cols x p projection outputs are spread over the threads (output o = tid + k NTR);
-// each chunk's FP32 sum is added to a float-pair accumulator, so the CTA's partial carries
-// FP32 products but no growth of the summation error with the number of chunks.  In the
-// update two threads share a row (each takes half of the columns a, the pair sums combine in
-// a fixed order), with no barrier inside the column loop.
+// Per chunk the FP32 copy of V (cols x RB) and of W (RB x RP) are staged in shared memory.
+// The projection is register-blocked: a thread owns blocks of 2 basis columns x 4 block
+// columns and per pair of rows reads two float4 of W and four floats of V for 32 FMAs, so
+// the shared-memory pipe is no longer the bound (one load per FMA without blocking).  Each
+// chunk's FP32 sums (two chains per output, even and odd rows) are added to float-pair
+// accumulators, so the CTA's partial carries FP32 products but no growth of the summation
+// error with the number of chunks.  In the update two threads share a row, each owning half
+// of the block's columns for every basis column a; both threads of a pair then read the same
+// h entries in lockstep (one broadcast per load) and each finishes its own columns of W.
+// Conversions from FP64 are built from the bit pattern (split_df_i, f32_rn_i): a hardware
+// double -> float conversion issues to the FP64 pipe.
 constexpr int RB = NTR / 2;
-constexpr int WS = RP + 1;                  // row stride of the FP32 copy of W
+constexpr int VS = RB + 1;                  // row stride of the FP32 copy of V (per basis column)
+constexpr int WS4 = RP + 4;                 // row stride of the FP32 copy of W (float4 rows)
+constexpr int WG = RP + 1;                  // row stride of the float pairs of W (Gram)
+constexpr int HP = RP / 2;                  // columns of W per thread in the update
+constexpr int KG = (RG + NTR - 1) / NTR;    // Gram entries (upper triangle) per thread
+
+__host__ __device__ constexpr int cgs_nblk(int cols, int p) { return ((cols + 1) / 2) * ((p + 3) / 4); }
 
 __host__ __device__ constexpr size_t cgs_rows_smem(int cols, bool upd, int ng) {
-    return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS + (size_t)cols * (RB + 1) +
-                            (ng ? 2 * (size_t)RB * RP : 0));
+    return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS4 + (size_t)((cols + 1) & ~1) * VS +
+                            (ng ? 2 * (size_t)RB * WG : 0));
 }
 
-// Outputs o < cols p: FP32 products V^T W.  Outputs cols p <= o < (cols + p) p (the Gram matrix
-// W^T W, with Wh/Wl set): double-float products of the float pairs of W, so the Gram matrix
-// is accurate to ~2^-48 (it feeds the double-float factorisation of the first QR pass).
-template <int K>
-__device__ __forceinline__ void chunk_project(const float* Vs, const float* Wf, int nout, int p, float* ah,
-                                              float* al, int cols, const float* Wh, const float* Wl) {
+// The projection blocks of one chunk: block b = ab ncb + cb covers basis columns 2ab, 2ab + 1
+// and block columns 4cb .. 4cb + 3 (columns past p read zeros and are not written).
+template <int KB>
+__device__ __forceinline__ void chunk_project(const float* Vs, const float* Wf, int nblk, int ncb, float (*ah)[8],
+                                              float (*al)[8]) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int o = threadIdx.x + k * NTR;
-        if (o < nout) {
-            const int a = o / p, c = o - a * p;
-            if (a >= cols) {
-                const int a2 = a - cols;
-                float sh = 0.f, sl = 0.f;
+    for (int k = 0; k < KB; ++k) {
+        const int b = threadIdx.x + k * NTR;
+        if (b < nblk) {
+            const int ab = b / ncb, cb = b - ab * ncb;
+            const float* v0 = Vs + 2 * ab * VS;
+            const float* v1 = v0 + VS;
+            const float* wp = Wf + 4 * cb;
+            float se[8], so[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                se[q] = 0.f;
+                so[q] = 0.f;
+            }
 #pragma unroll 4
-                for (int rr = 0; rr < RB; ++rr)
-                    df_fma(sh, sl, Wh[rr * RP + a2], Wl[rr * RP + a2], Wh[rr * RP + c], Wl[rr * RP + c]);
-                df_add(ah[k], al[k], sh);
-                al[k] += sl;
-                continue;
-            }
-            const float* va = Vs + a * (RB + 1);
-            float s0 = 0.f, s1 = 0.f;
-#pragma unroll 8
             for (int rr = 0; rr < RB; rr += 2) {
-                s0 = fmaf(va[rr], Wf[rr * WS + c], s0);
-                s1 = fmaf(va[rr + 1], Wf[(rr + 1) * WS + c], s1);
+                const float4 w0 = *reinterpret_cast<const float4*>(wp + rr * WS4);
+                const float4 w1 = *reinterpret_cast<const float4*>(wp + (rr + 1) * WS4);
+                const float x0 = v0[rr], x1 = v1[rr], y0 = v0[rr + 1], y1 = v1[rr + 1];
+                se[0] = fmaf(x0, w0.x, se[0]);
+                se[1] = fmaf(x0, w0.y, se[1]);
+                se[2] = fmaf(x0, w0.z, se[2]);
+                se[3] = fmaf(x0, w0.w, se[3]);
+                se[4] = fmaf(x1, w0.x, se[4]);
+                se[5] = fmaf(x1, w0.y, se[5]);
+                se[6] = fmaf(x1, w0.z, se[6]);
+                se[7] = fmaf(x1, w0.w, se[7]);
+                so[0] = fmaf(y0, w1.x, so[0]);
+                so[1] = fmaf(y0, w1.y, so[1]);
+                so[2] = fmaf(y0, w1.z, so[2]);
+                so[3] = fmaf(y0, w1.w, so[3]);
+                so[4] = fmaf(y1, w1.x, so[4]);
+                so[5] = fmaf(y1, w1.y, so[5]);
+                so[6] = fmaf(y1, w1.z, so[6]);
+                so[7] = fmaf(y1, w1.w, so[7]);
             }
-            df_add(ah[k], al[k], s0);
-            df_add(ah[k], al[k], s1);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                df_add(ah[k][q], al[k][q], se[q]);
+                df_add(ah[k][q], al[k][q], so[q]);
+            }
         }
     }
 }
 
-template <bool UPD, int K>
+// The Gram entries (i <= j) of one chunk in double-float from the float pairs of W.
+__device__ __forceinline__ void chunk_gram(const float* Wh, const float* Wl, const int* gi, const int* gj, int ngu,
+                                           float* gh, float* gl) {
+#pragma unroll
+    for (int k = 0; k < KG; ++k) {
+        if ((int)threadIdx.x + k * NTR < ngu) {
+            const int i = gi[k], j = gj[k];
+            float sh = 0.f, sl = 0.f;
+#pragma unroll 4
+            for (int rr = 0; rr < RB; ++rr)
+                df_fma(sh, sl, Wh[rr * WG + i], Wl[rr * WG + i], Wh[rr * WG + j], Wl[rr * WG + j]);
+            df_add(gh[k], gl[k], sh);
+            gl[k] += sl;
+        }
+    }
+}
+
+// h entries of the thread's HP columns (four floats per load when HP is a multiple of 4, else
+// two; the rows of hh and hl and the thread's offset keep those loads aligned)
+__device__ __forceinline__ void df_row_update(float* sh, float* sl, float vh, float vl, const float* x, const float* y) {
+    if constexpr (HP % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < HP / 4; ++q) {
+            const float4 a = reinterpret_cast<const float4*>(x)[q], b = reinterpret_cast<const float4*>(y)[q];
+            df_fma(sh[4 * q], sl[4 * q], vh, vl, a.x, b.x);
+            df_fma(sh[4 * q + 1], sl[4 * q + 1], vh, vl, a.y, b.y);
+            df_fma(sh[4 * q + 2], sl[4 * q + 2], vh, vl, a.z, b.z);
+            df_fma(sh[4 * q + 3], sl[4 * q + 3], vh, vl, a.w, b.w);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < HP / 2; ++q) {
+            const float2 a = reinterpret_cast<const float2*>(x)[q], b = reinterpret_cast<const float2*>(y)[q];
+            df_fma(sh[2 * q], sl[2 * q], vh, vl, a.x, b.x);
+            df_fma(sh[2 * q + 1], sl[2 * q + 1], vh, vl, a.y, b.y);
+        }
+    }
+}
+
+template <bool UPD, int KB>
 __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, int64_t ldv, int cols,
                                                  double* __restrict__ W, int64_t ldw, int p, int64_t n,
                                                  int64_t rpb, const double* __restrict__ h,
@@ -1127,10 +1193,10 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
     extern __shared__ __align__(16) float smf[];
     float* hh = smf;                                   // UPD: cols x RP (zero-padded columns)
     float* hl = hh + (UPD ? cols * RP : 0);
-    float* Wf = hl + (UPD ? cols * RP : 0);            // RB x WS
-    float* Vs = Wf + RB * WS;                          // cols x (RB + 1)
-    float* Wh = Vs + cols * (RB + 1);                  // ng: W as float pairs, RB x RP each
-    float* Wl = Wh + RB * RP;
+    float* Wf = hl + (UPD ? cols * RP : 0);            // RB x WS4
+    float* Vs = Wf + RB * WS4;                         // ((cols + 1) & ~1) x VS
+    float* Wh = Vs + ((cols + 1) & ~1) * VS;           // ng: W as float pairs, RB x WG each
+    float* Wl = Wh + RB * WG;
     if (UPD) {
         for (int e = threadIdx.x; e < cols * RP; e += NTR) {
             const int a = e / RP, c = e - a * RP;
@@ -1140,16 +1206,33 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             hl[e] = y;
         }
     }
-    const int nout = (cols + (UPD ? ng : 0)) * p;
-    float ah[K], al[K];
+    if (cols & 1)                                      // the padding column of the last block
+        for (int e = threadIdx.x; e < VS; e += NTR) Vs[cols * VS + e] = 0.f;
+    const int ncb = (p + 3) >> 2, nblk = cgs_nblk(cols, p);
+    const int gp = UPD ? ng : 0, ngu = gp * (gp + 1) / 2;
+    float ah[KB][8], al[KB][8], gh[KG], gl[KG];
+    int gi[KG], gj[KG];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        ah[k] = 0.f;
-        al[k] = 0.f;
+    for (int k = 0; k < KB; ++k)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            ah[k][q] = 0.f;
+            al[k][q] = 0.f;
+        }
+#pragma unroll
+    for (int k = 0; k < KG; ++k) {
+        gh[k] = 0.f;
+        gl[k] = 0.f;
+        int i = 0, rem = threadIdx.x + k * NTR;        // upper-triangle entry -> (i, j), i <= j
+        if (rem < ngu)
+            while (rem >= gp - i) {
+                rem -= gp - i;
+                ++i;
+            }
+        gi[k] = i;
+        gj[k] = i + rem;
     }
-    const int rr = threadIdx.x >> 1, hf = threadIdx.x & 1;
-    const int half = (cols + 1) >> 1;
-    const int a0 = hf ? half : 0, a1 = hf ? cols : half;
+    const int rr = threadIdx.x >> 1, hf = threadIdx.x & 1, c0 = hf * HP;
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
     for (int64_t r0 = rb; r0 < re; r0 += RB) {
         const int tr = (int)min((int64_t)RB, re - r0);
@@ -1157,72 +1240,61 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             __syncthreads();                           // hh/hl written; previous chunk consumed
             const bool ok = rr < tr;
             const int64_t r = r0 + rr;
-            float sh[RP], sl[RP];
+            float sh[HP], sl[HP];
 #pragma unroll
-            for (int c = 0; c < RP; ++c) {
+            for (int c = 0; c < HP; ++c) {
                 sh[c] = 0.f;
                 sl[c] = 0.f;
             }
-            int a = a0;
-            for (; a + 4 <= a1; a += 4) {
-                double v[4];
+            // groups of 8 basis columns: each thread of the pair loads and splits the 4 of its
+            // parity (a = 8g + 2q + hf) and takes the other 4 from its partner by a shuffle;
+            // the next group's loads are issued before this group's products
+            const int ng8 = cols >> 3;
+            double nx[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = ok ? V[(int64_t)(a + u) * ldv + r] : 0.0;
+            for (int q = 0; q < 4; ++q) nx[q] = (ok && ng8 > 0) ? V[(int64_t)(2 * q + hf) * ldv + r] : 0.0;
+            for (int g = 0; g < ng8; ++g) {
+                float mh[4], ml[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    float vh, vl;
-                    split_df(v[u], vh, vl);
-                    Vs[(a + u) * (RB + 1) + rr] = vh;
-                    const float4* x4 = reinterpret_cast<const float4*>(hh + (a + u) * RP);
-                    const float4* y4 = reinterpret_cast<const float4*>(hl + (a + u) * RP);
+                for (int q = 0; q < 4; ++q) {
+                    split_df_i(nx[q], mh[q], ml[q]);
+                    Vs[(8 * g + 2 * q + hf) * VS + rr] = mh[q];
+                }
+                if (g + 1 < ng8) {
 #pragma unroll
-                    for (int q = 0; q < RP / 4; ++q) {
-                        const float4 x = x4[q], y = y4[q];
-                        df_fma(sh[4 * q], sl[4 * q], vh, vl, x.x, y.x);
-                        df_fma(sh[4 * q + 1], sl[4 * q + 1], vh, vl, x.y, y.y);
-                        df_fma(sh[4 * q + 2], sl[4 * q + 2], vh, vl, x.z, y.z);
-                        df_fma(sh[4 * q + 3], sl[4 * q + 3], vh, vl, x.w, y.w);
-                    }
+                    for (int q = 0; q < 4; ++q) nx[q] = ok ? V[(int64_t)(8 * (g + 1) + 2 * q + hf) * ldv + r] : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, mh[q], 1);
+                    const float ol = __shfl_xor_sync(0xffffffffu, ml[q], 1);
+                    const int a = 8 * g + 2 * q;
+                    df_row_update(sh, sl, hf ? oh : mh[q], hf ? ol : ml[q], hh + a * RP + c0, hl + a * RP + c0);
+                    df_row_update(sh, sl, hf ? mh[q] : oh, hf ? ml[q] : ol, hh + (a + 1) * RP + c0,
+                                  hl + (a + 1) * RP + c0);
                 }
             }
-            for (; a < a1; ++a) {
+            for (int a = 8 * ng8; a < cols; ++a) {
                 const double v = ok ? V[(int64_t)a * ldv + r] : 0.0;
                 float vh, vl;
-                split_df(v, vh, vl);
-                Vs[a * (RB + 1) + rr] = vh;
-                const float4* x4 = reinterpret_cast<const float4*>(hh + a * RP);
-                const float4* y4 = reinterpret_cast<const float4*>(hl + a * RP);
-#pragma unroll
-                for (int q = 0; q < RP / 4; ++q) {
-                    const float4 x = x4[q], y = y4[q];
-                    df_fma(sh[4 * q], sl[4 * q], vh, vl, x.x, y.x);
-                    df_fma(sh[4 * q + 1], sl[4 * q + 1], vh, vl, x.y, y.y);
-                    df_fma(sh[4 * q + 2], sl[4 * q + 2], vh, vl, x.z, y.z);
-                    df_fma(sh[4 * q + 3], sl[4 * q + 3], vh, vl, x.w, y.w);
-                }
+                split_df_i(v, vh, vl);
+                if ((a & 1) == hf) Vs[a * VS + rr] = vh;
+                df_row_update(sh, sl, vh, vl, hh + a * RP + c0, hl + a * RP + c0);
             }
-            // the two halves of the row: (half 0) + (half 1), the same order in both threads
 #pragma unroll
-            for (int c = 0; c < RP; ++c) {
-                const float oh = __shfl_xor_sync(0xffffffffu, sh[c], 1);
-                const float ol = __shfl_xor_sync(0xffffffffu, sl[c], 1);
-                float xh = hf ? oh : sh[c], xl = hf ? ol : sl[c];
-                const float yh = hf ? sh[c] : oh, yl = hf ? sl[c] : ol;
-                df_add(xh, xl, yh);
-                xl += yl;
-                if ((c & 1) == hf) {
-                    float wf = 0.f, wh = 0.f, wl = 0.f;
-                    if (ok && c < p) {
-                        const double w = W[(int64_t)c * ldw + r] - ((double)xh + (double)xl);
-                        W[(int64_t)c * ldw + r] = w;
-                        wf = (float)w;
-                        if (ng) split_df(w, wh, wl);
-                    }
-                    Wf[rr * WS + c] = wf;
-                    if (ng) {
-                        Wh[rr * RP + c] = wh;
-                        Wl[rr * RP + c] = wl;
-                    }
+            for (int q = 0; q < HP; ++q) {
+                const int c = c0 + q;
+                float wf = 0.f, wh = 0.f, wl = 0.f;
+                if (ok && c < p) {
+                    const double w = W[(int64_t)c * ldw + r] - ((double)sh[q] + (double)sl[q]);
+                    W[(int64_t)c * ldw + r] = w;
+                    wf = f32_rn_i(w);
+                    if (ng) split_df_i(w, wh, wl);
+                }
+                Wf[rr * WS4 + c] = wf;
+                if (ng) {
+                    Wh[rr * WG + c] = wh;
+                    Wl[rr * WG + c] = wl;
                 }
             }
         } else {
@@ -1238,20 +1310,38 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
 #pragma unroll
                 for (int k = 0; k < LB; ++k) {
                     const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
-                    if (e < tot) Vs[a * (RB + 1) + r2] = (float)v[k];
+                    if (e < tot) Vs[a * VS + r2] = f32_rn_i(v[k]);
                 }
             }
             for (int e = threadIdx.x; e < RP * RB; e += NTR) {
                 const int c = e / RB, r2 = e - c * RB;
-                Wf[r2 * WS + c] = (c < p && r2 < tr) ? (float)W[(int64_t)c * ldw + r0 + r2] : 0.f;
+                Wf[r2 * WS4 + c] = (c < p && r2 < tr) ? f32_rn_i(W[(int64_t)c * ldw + r0 + r2]) : 0.f;
             }
         }
         __syncthreads();
-        chunk_project<K>(Vs, Wf, nout, p, ah, al, cols, Wh, Wl);
+        chunk_project<KB>(Vs, Wf, nblk, ncb, ah, al);
+        if (UPD && ngu) chunk_gram(Wh, Wl, gi, gj, ngu, gh, gl);
+    }
+    const int nout = (cols + gp) * p;
+    double* out = part + (int64_t)blockIdx.x * nout;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+        const int b = threadIdx.x + k * NTR;
+        if (b < nblk) {
+            const int ab = b / ncb, cb = b - ab * ncb;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int a = 2 * ab + (q >> 2), c = 4 * cb + (q & 3);
+                if (a < cols && c < p) out[a * p + c] = (double)ah[k][q] + (double)al[k][q];
+            }
+        }
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int o = threadIdx.x + k * NTR;
-        if (o < nout) part[(int64_t)blockIdx.x * nout + o] = (double)ah[k] + (double)al[k];
+    for (int k = 0; k < KG; ++k) {
+        if ((int)threadIdx.x + k * NTR < ngu) {
+            const double g = (double)gh[k] + (double)gl[k];
+            out[(cols + gi[k]) * p + gj[k]] = g;
+            out[(cols + gj[k]) * p + gi[k]] = g;
+        }
     }
 }

@@ -2,13 +2,13 @@
 // rows_impl.cuh inside the width's namespace; see rows_api.h).
 
 // The first CGS pass of the mixed path by the row-chunk kernels (k_cgs_rows): used when the
-// projection outputs per thread ((cols + p) p / NTR) and the staged chunk fit.
-constexpr int kCgsRowsKMax = 20;
+// projection blocks per thread and the staged chunk fit.
+constexpr int kCgsRowsKMax = 5;
 constexpr size_t kCgsRowsSmemMax = 112 * 1024;
 
 bool cgs_fit(int cols, int p) {
     if (p < 1 || p > RP || cols < 1) return false;
-    return ((cols + p) * p + NTR - 1) / NTR <= kCgsRowsKMax && cgs_rows_smem(cols, true, p) <= kCgsRowsSmemMax;
+    return (cgs_nblk(cols, p) + NTR - 1) / NTR <= kCgsRowsKMax && cgs_rows_smem(cols, true, p) <= kCgsRowsSmemMax;
 }
 
 cudaError_t cgs(int upd, const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p, int64_t n,
@@ -23,12 +23,11 @@ cudaError_t cgs(int upd, const double* V, int64_t ldv, int cols, double* W, int6
         if (upd) k_cgs_rows<true, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng); \
         else k_cgs_rows<false, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, 0);     \
     }
-    const int k = ((cols + ng) * p + NTR - 1) / NTR;
+    const int k = (cgs_nblk(cols, p) + NTR - 1) / NTR;
     if (k <= 1) EXPM_CGS_K(1)
+    else if (k <= 2) EXPM_CGS_K(2)
     else if (k <= 3) EXPM_CGS_K(3)
-    else if (k <= 6) EXPM_CGS_K(6)
-    else if (k <= 12) EXPM_CGS_K(12)
-    else EXPM_CGS_K(20)
+    else EXPM_CGS_K(5)
 #undef EXPM_CGS_K
     return cudaGetLastError();
 }
@@ -105,10 +104,10 @@ cudaError_t set_smem(int optin) {
     EXPM_SET(k_update_gram_rows<true>);
     EXPM_SET(k_update_z_rows<false>);
     EXPM_SET(k_update_z_rows<true>);
-    EXPM_SET((k_cgs_rows<true, 1>)); EXPM_SET((k_cgs_rows<true, 3>)); EXPM_SET((k_cgs_rows<true, 6>));
-    EXPM_SET((k_cgs_rows<true, 12>)); EXPM_SET((k_cgs_rows<true, 20>));
-    EXPM_SET((k_cgs_rows<false, 1>)); EXPM_SET((k_cgs_rows<false, 3>)); EXPM_SET((k_cgs_rows<false, 6>));
-    EXPM_SET((k_cgs_rows<false, 12>)); EXPM_SET((k_cgs_rows<false, 20>));
+    EXPM_SET((k_cgs_rows<true, 1>)); EXPM_SET((k_cgs_rows<true, 2>)); EXPM_SET((k_cgs_rows<true, 3>));
+    EXPM_SET((k_cgs_rows<true, 5>));
+    EXPM_SET((k_cgs_rows<false, 1>)); EXPM_SET((k_cgs_rows<false, 2>)); EXPM_SET((k_cgs_rows<false, 3>));
+    EXPM_SET((k_cgs_rows<false, 5>));
     EXPM_SET(k_qr_mixed_rows<3>);
 #undef EXPM_SET
     return e;
