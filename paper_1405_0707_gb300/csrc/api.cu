@@ -182,7 +182,7 @@ expm_status prec_apply_mixed(expm_plan* P, double t, const double* V, int64_t ld
         // it as FP32 either way
         float* R32 = reinterpret_cast<float*>(P->R64);
         LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(W, ldw, nullptr, P->ld, p, P->ndim, P->ax[0].N, P->ax[1].N,
-                                                   P->ax[2].N, P->ax, -t, s, V, ldv, 1.0, R32));
+                                                   P->ax[2].N, P->ax, -t, s, V, ldv, 1.0, R32, P->stencil_df & 2));
         st = inv32_apply(P, t, R32, P->ld, p, W, ldw, 1, 0);
         if (st != EXPM_OK) return st;
     }
@@ -279,7 +279,7 @@ expm_status op_apply_internal(expm_plan* P, double t, const double* V, int64_t l
                               int64_t ldw) {
     if (P->toeplitz) return toeplitz_matvec(P, t, V, ldv, p, W, ldw, EXPM_STAGE_STENCIL);
     LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(V, ldv, W, ldw, p, P->ndim, P->ax[0].N, P->ax[1].N, P->ax[2].N,
-                                               P->ax, t, P->stream));
+                                               P->ax, t, P->stream, nullptr, 0, 0.0, nullptr, P->stencil_df & 1));
     return EXPM_OK;
 }
 
@@ -1215,6 +1215,11 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         // test switch: the bound of the tensor-core kernel's waits (0 makes every wait run out)
         const char* sl = std::getenv("EXPM_TC_SPIN_LIMIT");
         if (sl) P->tc_spin = std::strtol(sl, nullptr, 10);
+        // mixed plans apply the stencil in double-float: bit 0 Algorithm 1's operator, bit 1
+        // the refinement residual of the FP32 inverse.  Test switch: "1" keeps both on the
+        // FP64 stencil, "2" only the residual
+        const char* sf = std::getenv("EXPM_STENCIL_FP64");
+        P->stencil_df = opts->precision != EXPM_PREC_MIXED ? 0 : !sf ? 3 : sf[0] == '1' ? 0 : sf[0] == '2' ? 1 : 3;
     }
     int64_t n = 1;
     if (toeplitz) {

@@ -62,4 +62,30 @@ __device__ __forceinline__ void df_add(float& s, float& c, float x) {
     c += err;
 }
 
+// exact float -> double from the bit pattern with integer operations only (a hardware
+// float -> double conversion also issues to the FP64 pipe): normal floats, zeros, subnormals
+// (normalised with a leading-zero count), inf and NaN.
+__device__ __forceinline__ double f64_of_f32_i(float x) {
+    const unsigned u = __float_as_uint(x), ex = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    const unsigned long long sg = (unsigned long long)(u >> 31) << 63;
+    unsigned long long b = sg | ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)m << 29);
+    if (ex == 0xFFu) b = sg | (0x7FFull << 52) | ((unsigned long long)m << 29);
+    if (ex == 0u) {
+        const int lead = 31 - __clz((int)(m | 1u));          // position of m's leading one
+        const unsigned long long frac = ((unsigned long long)m << (52 - lead)) & 0xFFFFFFFFFFFFFull;
+        b = m ? (sg | ((unsigned long long)(lead + 874) << 52) | frac) : sg;
+    }
+    return __longlong_as_double((long long)b);
+}
+
+// one double-float multiply-add: (sh, sl) += (vh + vl)(h1 + h2)
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float vh, float vl, float h1, float h2) {
+    const float pr = vh * h1;
+    float t = fmaf(vh, h1, -pr);
+    t = fmaf(vl, h1, t);
+    t = fmaf(vh, h2, t);
+    df_add(sh, sl, pr);
+    sl += t;
+}
+
 }  // namespace expm

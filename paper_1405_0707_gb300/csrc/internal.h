@@ -211,6 +211,7 @@ struct expm_plan_s {
     bool use_graphs = false;
     bool qr_single = true;     // mixed path: try the single accurate Cholesky-QR pass
     bool cgs_tc = false;       // mixed path: first CGS pass on the tensor cores (k_cgs_tc)
+    int stencil_df = 0;        // mixed path: the stencil in double-float (k_cd_apply_df)
     long tc_spin = 1L << 24;   // bound of the tensor-core kernel's mbarrier waits (iterations)
     // deflated restart (opts.k_defl > 0)
     int kdefl_max = 0;         // columns of Vk and Pkd
@@ -236,7 +237,7 @@ cudaError_t launch_axis_setup(double* Qf, double* Qi, double* lam, int N, double
 cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw, int p,
                             int ndim, int nx, int ny, int nz, const Axis* ax, double t,
                             cudaStream_t s, const double* Y = nullptr, int64_t ldy = 0,
-                            double beta = 0.0, float* W32 = nullptr);
+                            double beta = 0.0, float* W32 = nullptr, int df = 0);
 cudaError_t launch_gemm32(const GemmArgsMixed& g, cudaStream_t s);
 cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t nmodes, float l_sub,
                                    const float* th_m, const float* th_c, float inv_t,

@@ -279,6 +279,56 @@ __global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __
     else W[c * ldw + i] = r;
 }
 
+// The same stencil in double-float arithmetic on the FP32 pipe, for mixed-precision plans:
+// coefficients as float pairs (host-split), every value split from its bit pattern
+// (split_df_i), products and sums as in the double-float row kernels.  GB300 retires about two
+// FP64 FMAs per SM per clock, so the FP64 stencil (5 or 7 per point) is bound by the FP64
+// pipe, not by memory; the pair arithmetic is ~2^-48 accurate, the level of the mixed path's
+// other double-float kernels.  Y (the refinement's right-hand side) enters with beta = 1.
+struct StencilDF {
+    float ch, cl, lh[3], ll[3], uh[3], ul[3];
+};
+
+__device__ __forceinline__ void df_term(float& sh, float& sl, double v, float ch, float cl) {
+    float vh, vl;
+    split_df_i(v, vh, vl);
+    df_fma(sh, sl, vh, vl, ch, cl);
+}
+
+__global__ void k_cd_apply_df(const double* __restrict__ V, int64_t ldv, double* __restrict__ W,
+                              int64_t ldw, int ndim, int nx, int ny, int nz, StencilDF k,
+                              const double* __restrict__ Y, int64_t ldy, float* __restrict__ W32) {
+    const unsigned n = (unsigned)nx * (unsigned)ny * (unsigned)nz;
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= n) return;
+    const double* v = V + c * ldv;
+    const unsigned q = i / (unsigned)nx;
+    const unsigned ix = i - q * (unsigned)nx;
+    float sh = 0.f, sl = 0.f;
+    df_term(sh, sl, v[i], k.ch, k.cl);
+    if (ix > 0) df_term(sh, sl, v[i - 1], k.lh[0], k.ll[0]);
+    if (ix < (unsigned)nx - 1) df_term(sh, sl, v[i + 1], k.uh[0], k.ul[0]);
+    if (ndim > 1) {
+        const unsigned iz = q / (unsigned)ny, iy = q - iz * (unsigned)ny;
+        if (iy > 0) df_term(sh, sl, v[i - nx], k.lh[1], k.ll[1]);
+        if (iy < (unsigned)ny - 1) df_term(sh, sl, v[i + nx], k.uh[1], k.ul[1]);
+        if (ndim > 2) {
+            const unsigned st = (unsigned)nx * (unsigned)ny;
+            if (iz > 0) df_term(sh, sl, v[i - st], k.lh[2], k.ll[2]);
+            if (iz < (unsigned)nz - 1) df_term(sh, sl, v[i + st], k.uh[2], k.ul[2]);
+        }
+    }
+    if (Y) {
+        float yh, yl;
+        split_df_i(Y[c * ldy + i], yh, yl);
+        df_add(sh, sl, yh);
+        sl += yl;
+    }
+    if (W32) W32[c * ldw + i] = sh + sl;
+    else W[c * ldw + i] = f64_of_f32_i(sh) + f64_of_f32_i(sl);
+}
+
 // ---------------------------------------------------------------- mixed precision
 // FP32 arithmetic for the DST-I transforms of the exact inverse; the result is refined
 // in FP64 by the caller (residual with the FP64 stencil, Theorem 4.3 bounds what an
@@ -296,14 +346,6 @@ __device__ __forceinline__ int64_t gemm_row_off(int m, int ms, int64_t rs, int64
 
 __device__ __forceinline__ float gemm_in(double x) { return f32_rn_i(x); }
 __device__ __forceinline__ float gemm_in(float x) { return x; }
-
-// exact float -> double from the bit pattern (normal floats and zero; others by hardware)
-__device__ __forceinline__ double f64_of_f32_i(float x) {
-    const unsigned u = __float_as_uint(x), ex = (u >> 23) & 0xFFu;
-    if (ex == 0u || ex == 0xFFu) return (u & 0x7FFFFFFFu) ? (double)x : __longlong_as_double((long long)(u >> 31) << 63);
-    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(ex + 896u) << 52) |
-                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
 
 template <typename TC>
 __device__ __forceinline__ void gemm_out(TC* dst, float v, int acc) {
@@ -390,6 +432,116 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
         for (int j = 0; j < 4; ++j) {
             const int nn = n0 + nj + j;
             if (nn < g.N) gemm_out(crow + (int64_t)nn * g.c_cs, acc[i][j], g.accumulate);
+        }
+    }
+}
+
+// Transforms along a short axis (K, N <= 96: every axis of the 3-D grids): the whole K x N
+// DST matrix and a slab of SBM rows of A (all K) sit in shared memory, so one barrier
+// separates staging from arithmetic and no k-tile padding is read.  A thread owns 8 rows
+// (two runs of 4 consecutive rows, 64 apart) and NJ columns (16 apart): per k two float4 of
+// A and NJ floats of B feed 8 NJ FMAs.  The row runs (CM: C's contiguous dimension is m) or
+// the columns (otherwise) walk consecutive threads, so the stores coalesce.
+constexpr int SBM = 128, SMAX = 96;
+constexpr int SAS = SBM + 4;   // row stride of the staged A (float4-aligned)
+__host__ __device__ constexpr size_t gemm_small_smem(int K, int NJ) {
+    return sizeof(float) * ((size_t)K * 16 * NJ + (size_t)K * SAS);
+}
+
+template <bool CM, typename TA, typename TC, int NJ>
+__global__ void __launch_bounds__(256) k_gemm_small(GemmArgsMixed g) {
+    extern __shared__ __align__(16) float sgm[];
+    constexpr int NP = 16 * NJ;
+    const int K = g.K;
+    float* Bs = sgm;                  // K x NP, columns past N zero
+    float* As = Bs + K * NP;          // K x SAS: As[k * SAS + mm]
+    const int b1 = blockIdx.y % g.nb1, b2 = blockIdx.y / g.nb1;
+    const TA* A = reinterpret_cast<const TA*>(g.A) + b1 * g.a_b1 + b2 * g.a_b2;
+    TC* C = reinterpret_cast<TC*>(g.C) + b1 * g.c_b1 + b2 * g.c_b2;
+    const int m0 = blockIdx.x * SBM, tid = threadIdx.x;
+    // staging: the loads of each thread are issued in batches into registers before any is
+    // stored, so a batch's latencies overlap (a plain loop would wait for every load in turn)
+    for (int e0 = tid; e0 < K * NP; e0 += 8 * 256) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + 256 * u, k = e / NP, n = e - k * NP;
+            v[u] = (e < K * NP && n < g.N) ? g.B[(int64_t)k * g.ldb + n] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (e0 + 256 * u < K * NP) Bs[e0 + 256 * u] = v[u];
+    }
+    if (g.a_rs == 1) {
+        // m fastest in memory: thread t keeps row mm = t % SBM (one row offset) and walks k
+        const int mm = tid & (SBM - 1), m = m0 + mm;
+        const bool ok = m < g.M;
+        const int64_t ro = ok ? gemm_row_off(m, g.ms, g.a_rs, g.a_ms2) : 0;
+        for (int k0 = tid >> 7; k0 < K; k0 += 16) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + 2 * u;
+                v[u] = (ok && k < K) ? gemm_in(A[ro + (int64_t)k * g.a_cs]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k0 + 2 * u < K) As[(k0 + 2 * u) * SAS + mm] = v[u];
+        }
+    } else {
+        // k fastest in memory: a warp takes 4 rows at a time, lane l the entries k = l + 32 j
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int mm0 = warp; mm0 < SBM; mm0 += 32) {
+            float v[4][3];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int m = m0 + mm0 + 8 * r;
+                const bool ok = m < g.M;
+                const int64_t ro = ok ? gemm_row_off(m, g.ms, g.a_rs, g.a_ms2) : 0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int k = lane + 32 * j;
+                    v[r][j] = (ok && k < K) ? gemm_in(A[ro + (int64_t)k * g.a_cs]) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (lane + 32 * j < K) As[(lane + 32 * j) * SAS + mm0 + 8 * r] = v[r][j];
+        }
+    }
+    __syncthreads();
+    const int tm = CM ? (tid & 15) : (tid >> 4), tn = CM ? (tid >> 4) : (tid & 15);
+    float acc[8][NJ];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) acc[i][j] = 0.f;
+    const float* ap = As + 4 * tm;
+    const float* bp = Bs + tn;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(ap + k * SAS);
+        const float4 a1 = *reinterpret_cast<const float4*>(ap + k * SAS + 64);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float b[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) b[j] = bp[k * NP + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + 4 * tm + (i & 3) + 64 * (i >> 2);
+        if (m >= g.M) continue;
+        TC* crow = C + gemm_row_off(m, g.ms, g.c_rs, g.c_ms2);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int n = tn + 16 * j;
+            if (n < g.N) gemm_out(crow + (int64_t)n * g.c_cs, acc[i][j], g.accumulate);
         }
     }
 }
@@ -505,9 +657,11 @@ __global__ void __launch_bounds__(TK * TSG) k_tridiag_tile32(float* y_io, int64_
 
 // Short lines with many modes (the x lines of a 3-D grid, L <= 128, ny nz modes): one thread
 // per (mode, column) runs both sweeps of the factored solve over its line, consecutive
-// threads on consecutive modes (coalesced: the layout is mode-fastest).  The sweeps' loads
-// do not depend on the recurrence, so unrolling keeps several of them in flight; the forward
-// sweep's results stay in place (in L2) for the backward sweep.
+// threads on consecutive modes (coalesced: the layout is mode-fastest).  The sweeps' loads do
+// not depend on the recurrence, but they may alias the stores as far as the compiler knows,
+// so each sweep reads its line in explicit batches of TB elements into registers and issues
+// the next batch's loads before it stores the current one.
+constexpr int TB = 8;
 __global__ void __launch_bounds__(256) k_tridiag_thread32(float* y_io, int64_t ld, int L, int64_t nmodes,
                                                           float l_sub, const float* __restrict__ thm,
                                                           const float* __restrict__ thc, float inv_t) {
@@ -516,19 +670,57 @@ __global__ void __launch_bounds__(256) k_tridiag_thread32(float* y_io, int64_t l
     float* y = y_io + (int64_t)blockIdx.y * ld + k;
     const float* m = thm + k;
     const float* cc = thc + k;
-    float prev = 0.f;
-#pragma unroll 8
-    for (int x = 0; x < L; ++x) {
-        const int64_t o = (int64_t)x * nmodes;
-        prev = (y[o] * inv_t - l_sub * prev) * m[o];
-        y[o] = prev;
+    float yv[TB], mv[TB], out[TB];
+    // forward sweep, x ascending
+#pragma unroll
+    for (int u = 0; u < TB; ++u) {
+        yv[u] = u < L ? y[(int64_t)u * nmodes] : 0.f;
+        mv[u] = u < L ? m[(int64_t)u * nmodes] : 0.f;
     }
-    float next = prev;                               // x = L - 1: no coupling above
-#pragma unroll 8
-    for (int x = L - 2; x >= 0; --x) {
-        const int64_t o = (int64_t)x * nmodes;
-        next = y[o] - cc[o] * next;
-        y[o] = next;
+    float prev = 0.f;
+    for (int x0 = 0; x0 < L; x0 += TB) {
+#pragma unroll
+        for (int u = 0; u < TB; ++u) {
+            if (x0 + u < L) prev = (yv[u] * inv_t - l_sub * prev) * mv[u];
+            out[u] = prev;
+        }
+        if (x0 + TB < L) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+                const int x = x0 + TB + u;
+                yv[u] = x < L ? y[(int64_t)x * nmodes] : 0.f;
+                mv[u] = x < L ? m[(int64_t)x * nmodes] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TB; ++u)
+            if (x0 + u < L) y[(int64_t)(x0 + u) * nmodes] = out[u];
+    }
+    // backward sweep, x descending from L - 1 (whose value the forward sweep left final)
+    int xb = L - 2;
+#pragma unroll
+    for (int u = 0; u < TB; ++u) {
+        yv[u] = xb - u >= 0 ? y[(int64_t)(xb - u) * nmodes] : 0.f;
+        mv[u] = xb - u >= 0 ? cc[(int64_t)(xb - u) * nmodes] : 0.f;
+    }
+    float next = prev;
+    for (; xb >= 0; xb -= TB) {
+#pragma unroll
+        for (int u = 0; u < TB; ++u) {
+            next = yv[u] - mv[u] * next;
+            out[u] = next;
+        }
+        if (xb - TB >= 0) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+                const int x = xb - TB - u;
+                yv[u] = x >= 0 ? y[(int64_t)x * nmodes] : 0.f;
+                mv[u] = x >= 0 ? cc[(int64_t)x * nmodes] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TB; ++u)
+            if (xb - u >= 0) y[(int64_t)(xb - u) * nmodes] = out[u];
     }
 }
 
@@ -641,11 +833,28 @@ cudaError_t launch_axis_setup(double* Qf, double* Qi, double* lam, int N, double
     return cudaGetLastError();
 }
 
+static void split_host(double x, float& h, float& l) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
 cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw, int p,
                             int ndim, int nx, int ny, int nz, const Axis* ax, double t,
-                            cudaStream_t s, const double* Y, int64_t ldy, double beta, float* W32) {
+                            cudaStream_t s, const double* Y, int64_t ldy, double beta, float* W32, int df) {
     const int64_t n = (int64_t)nx * ny * nz;
     if (n >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    if (df) {
+        if (Y && beta != 1.0) return cudaErrorInvalidValue;
+        StencilDF k;
+        split_host(t * (ax[0].c + (ndim > 1 ? ax[1].c : 0.0) + (ndim > 2 ? ax[2].c : 0.0)), k.ch, k.cl);
+        for (int d = 0; d < 3; ++d) {
+            split_host(t * ax[d].l, k.lh[d], k.ll[d]);
+            split_host(t * ax[d].u, k.uh[d], k.ul[d]);
+        }
+        dim3 grid((unsigned)((n + 255) / 256), p);
+        k_cd_apply_df<<<grid, 256, 0, s>>>(V, ldv, W, ldw, ndim, nx, ny, nz, k, Y, ldy, W32);
+        return cudaGetLastError();
+    }
     StencilT k;
     k.tc = t * (ax[0].c + (ndim > 1 ? ax[1].c : 0.0) + (ndim > 2 ? ax[2].c : 0.0));
     for (int d = 0; d < 3; ++d) {
@@ -657,7 +866,34 @@ cudaError_t launch_cd_apply(const double* V, int64_t ldv, double* W, int64_t ldw
     return cudaGetLastError();
 }
 
+template <typename TA, typename TC, int NJ>
+static void launch_gemm_small_nj(const GemmArgsMixed& g, bool cm, cudaStream_t s) {
+    const dim3 grid((unsigned)((g.M + SBM - 1) / SBM), (unsigned)(g.nb1 * g.nb2));
+    const size_t shm = gemm_small_smem(g.K, NJ);
+    if (cm) k_gemm_small<true, TA, TC, NJ><<<grid, 256, shm, s>>>(g);
+    else k_gemm_small<false, TA, TC, NJ><<<grid, 256, shm, s>>>(g);
+}
+
+template <typename TA, typename TC>
+static void launch_gemm_small_t(const GemmArgsMixed& g, bool cm, cudaStream_t s) {
+    const int nj = (g.N + 15) / 16;
+    if (nj <= 2) launch_gemm_small_nj<TA, TC, 2>(g, cm, s);
+    else if (nj == 3) launch_gemm_small_nj<TA, TC, 3>(g, cm, s);
+    else if (nj == 4) launch_gemm_small_nj<TA, TC, 4>(g, cm, s);
+    else if (nj == 5) launch_gemm_small_nj<TA, TC, 5>(g, cm, s);
+    else launch_gemm_small_nj<TA, TC, 6>(g, cm, s);
+}
+
 cudaError_t launch_gemm32(const GemmArgsMixed& g, cudaStream_t s) {
+    const bool small = g.K <= SMAX && g.N <= SMAX;
+    if (small) {
+        const bool cm = (g.c_rs == 1);
+        if (g.a_f64 && !g.c_f64) launch_gemm_small_t<double, float>(g, cm, s);
+        else if (!g.a_f64 && !g.c_f64) launch_gemm_small_t<float, float>(g, cm, s);
+        else if (!g.a_f64 && g.c_f64) launch_gemm_small_t<float, double>(g, cm, s);
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, g.nb1 * g.nb2);
     const bool cm = (g.c_rs == 1);
     if (g.a_f64 && !g.c_f64) {
@@ -695,9 +931,32 @@ cudaError_t launch_tridiag_lines32(float* y, int64_t ld, int p, int L, int64_t n
     return cudaGetLastError();
 }
 
+template <typename TA, typename TC, int NJ>
+static cudaError_t set_gemm_small_smem() {
+    const int mx = (int)gemm_small_smem(SMAX, NJ);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_small<true, TA, TC, NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gemm_small<false, TA, TC, NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+}
+
+template <typename TA, typename TC>
+static cudaError_t set_gemm_small_smem_t() {
+    cudaError_t e = set_gemm_small_smem<TA, TC, 2>();
+    if (e == cudaSuccess) e = set_gemm_small_smem<TA, TC, 3>();
+    if (e == cudaSuccess) e = set_gemm_small_smem<TA, TC, 4>();
+    if (e == cudaSuccess) e = set_gemm_small_smem<TA, TC, 5>();
+    if (e == cudaSuccess) e = set_gemm_small_smem<TA, TC, 6>();
+    return e;
+}
+
 cudaError_t operator_set_smem_limits() {
-    return cudaFuncSetAttribute(k_tridiag_tile32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kTridiagTileSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(k_tridiag_tile32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTridiagTileSmemMax);
+    if (e == cudaSuccess) e = set_gemm_small_smem_t<double, float>();
+    if (e == cudaSuccess) e = set_gemm_small_smem_t<float, float>();
+    if (e == cudaSuccess) e = set_gemm_small_smem_t<float, double>();
+    return e;
 }
 
 int true_resid_blocks(int64_t n) { return (int)((n + 255) / 256); }

@@ -8,16 +8,6 @@
 // RG = RP (RP + 1) / 2 (Gram entries), NQ = ceil(RG / 32) (entries per lane) and NTR
 // (threads per CTA).
 
-// one double-float multiply-add: (sh, sl) += (vh + vl)(h1 + h2)
-__device__ __forceinline__ void df_fma(float& sh, float& sl, float vh, float vl, float h1, float h2) {
-    const float pr = vh * h1;
-    float t = fmaf(vh, h1, -pr);
-    t = fmaf(vl, h1, t);
-    t = fmaf(vh, h2, t);
-    df_add(sh, sl, pr);
-    sl += t;
-}
-
 __device__ inline double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -37,6 +37,49 @@ def test_refined_fp32_inverse_matches_fp64(sides, diff, vel, t, p):
     assert rel(W32, W64) <= 1e-13 * max(1.0, kappa)
 
 
+# 3-D grids that take each transform and line-solve kernel of the FP32 inverse: every axis
+# <= 96 (shared-memory transform, N padded to 48/80/96), an axis of 100 (tiled transform with
+# merged (x, z) rows), x lines <= 128 with >= 1024 modes (thread-per-line solve) and x = 130
+# (shared-memory line solve), with ragged 128-row slabs throughout
+CASES_3D = [((45, 37, 33), 1.0, (2.0, -1.0, 0.5), 0.05, 3),
+            ((97, 33, 35), 1.0, (1.0, 1.0, -1.0), 0.02, 2),
+            ((40, 100, 30), 1.0, (-1.5, 0.5, 1.0), 0.05, 2),
+            ((130, 20, 60), 1.0, (0.5, -0.5, 2.0), 0.02, 1)]
+
+
+@pytest.mark.parametrize("sides,diff,vel,t,p", CASES_3D)
+def test_refined_fp32_inverse_3d_transform_paths(sides, diff, vel, t, p):
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n = int(np.prod(sides))
+    V = inputs.rhs(n, p, 78)
+    W64 = to_np(Plan(sides, diff, vel, p_max=p, m=2).prec_apply(t, to_dev(V)))
+    W32 = to_np(Plan(sides, diff, vel, p_max=p, m=2, precision="mixed").prec_apply(t, to_dev(V)))
+    kappa = 1.0
+    for d in range(1, len(sides)):
+        _, dp, _ = ops.axis_eig(sides[d], diff, vel[d], t)
+        kappa *= dp.max() / dp.min()
+    assert rel(W32, W64) <= 1e-13 * max(1.0, kappa)
+    # and A (A^{-1} V) = V through the oracle's independent sparse matrix
+    assert rel(ops.cd_matrix(sides, diff, vel, t) @ W32, V) <= 1e-11 * max(1.0, kappa)
+
+
+@pytest.mark.parametrize("sides,diff,vel,t,p", CASES + CASES_3D[:2] + [((517,), 1.0, (0.0,), 1.0, 3)])
+def test_double_float_stencil_matches_sparse_matrix(sides, diff, vel, t, p):
+    """Mixed plans apply tA in double-float (pairs of floats from the bit pattern): every entry
+    within 2^-45 of the sum of the magnitudes of its terms, |tA| |V| (the pair arithmetic's
+    ~2^-48 per term, with room for 7 terms)."""
+    need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    n = int(np.prod(sides))
+    V = inputs.rhs(n, p, 4321)
+    W = to_np(Plan(sides, diff, vel, p_max=p, m=2, precision="mixed").op_apply(t, to_dev(V)))
+    A = ops.cd_matrix(sides, diff, vel, t)
+    ref = A @ V
+    bound = abs(A) @ np.abs(V)
+    assert np.all(np.abs(W - ref) <= 2.0 ** -45 * bound)
+
+
 @pytest.mark.parametrize("sides,diff,vel,t,p", CASES[:3])
 def test_mixed_converged_matches_fp64_and_closed_form(tab, sides, diff, vel, t, p):
     """Converged to tol 1e-12, the mixed path agrees with the FP64 path and with r(tA)B.
