@@ -345,14 +345,14 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     else LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, nbc, s, f32));
     LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
     if (rows && fused_qr(P, p)) {
-        // update, second projection and the Gram matrix of W in one pass; the second pass's
-        // correction is applied by the first Cholesky-QR pass.  On the tensor cores (exact bf16
-        // slicing, k_cgs_tc) when the plan chose it, else on the FP32 pipe (double-float)
+        // update, second projection and the Gram matrix of W; the second pass's correction is
+        // applied by the first Cholesky-QR pass.  The update on the tensor cores (exact bf16
+        // slicing, k_cgs_tc) when the plan chose it, followed by the FP32 projection kernel with
+        // the Gram outputs; else all three in one double-float pass on the FP32 pipe
         if (P->cgs_tc && cgs_tc_fit(cols, p)) {
-            int g = 0;
-            LAUNCH(EXPM_STAGE_CGS, launch_cgs_tc(P->V, ld, cols, P->W, ld, p, n, h, P->part, &g, flags_of(P->stat),
-                                                 P->tc_spin, s));
-            LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, g, cols + p, p, h, P->H, P->ldH, 0, j * p, 1, s, cols));
+            LAUNCH(EXPM_STAGE_CGS, launch_cgs_tc(P->V, ld, cols, P->W, ld, p, n, h, flags_of(P->stat), P->tc_spin, s));
+            LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(0, P->V, ld, cols, P->W, ld, p, n, nullptr, P->part, nbc, 1, s));
+            LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols + p, p, h, P->H, P->ldH, 0, j * p, 1, s, cols));
         } else {
             LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(1, P->V, ld, cols, P->W, ld, p, n, h, P->part, nbc, 1, s));
             LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols + p, p, h, P->H, P->ldH, 0, j * p, 1, s, cols));
@@ -1215,11 +1215,13 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         // test switch: the bound of the tensor-core kernel's waits (0 makes every wait run out)
         const char* sl = std::getenv("EXPM_TC_SPIN_LIMIT");
         if (sl) P->tc_spin = std::strtol(sl, nullptr, 10);
-        // mixed plans apply the stencil in double-float: bit 0 Algorithm 1's operator, bit 1
-        // the refinement residual of the FP32 inverse.  Test switch: "1" keeps both on the
-        // FP64 stencil, "2" only the residual
+        // mixed plans apply Algorithm 1's operator tA in double-float (bit 0).  The refinement
+        // residual of the FP32 inverse stays FP64: in double-float (bit 1) it limits the
+        // refined inverse to ~2^-45 |tA| |x|, measured 3-4e-13 against the FP64 inverse on 3-D
+        // grids instead of ~1e-13.  Test switch: "1" keeps both on the FP64 stencil, "3" puts
+        // both in double-float
         const char* sf = std::getenv("EXPM_STENCIL_FP64");
-        P->stencil_df = opts->precision != EXPM_PREC_MIXED ? 0 : !sf ? 3 : sf[0] == '1' ? 0 : sf[0] == '2' ? 1 : 3;
+        P->stencil_df = opts->precision != EXPM_PREC_MIXED ? 0 : !sf ? 1 : sf[0] == '1' ? 0 : sf[0] == '3' ? 3 : 1;
     }
     int64_t n = 1;
     if (toeplitz) {

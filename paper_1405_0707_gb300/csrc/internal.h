@@ -268,10 +268,12 @@ cudaError_t launch_qr_mixed_rows(double* W, int64_t ldw, int p, int64_t n, int n
                                  const double* Vc = nullptr, int64_t ldvc = 0, int ccols = 0,
                                  const double* h2 = nullptr, double* fin = nullptr, int64_t ldfin = 0);
 constexpr int kRowsMaxP = 16;  // widths handled by the row-per-thread kernels
-// First CGS pass of the mixed path on the tensor cores (k_cgs_tc.cu): p <= 16, cols <= 192.
+// The first CGS pass's update W <- W - V h on the tensor cores (k_cgs_tc.cu): p <= 16,
+// cols <= 160.  The second projection and the Gram matrix follow from launch_cgs_rows(0, ...,
+// gram = 1).
 bool cgs_tc_fit(int cols, int p);
 cudaError_t launch_cgs_tc(const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p, int64_t n,
-                          const double* h, double* part, int* grid_out, int* flags, long spin_limit, cudaStream_t s);
+                          const double* h, int* flags, long spin_limit, cudaStream_t s);
 cudaError_t cgs_tc_set_smem_limits();
 // Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
 // third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.

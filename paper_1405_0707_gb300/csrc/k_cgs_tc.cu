@@ -1,37 +1,43 @@
-// k_cgs_tc.cu -- the first block CGS2 pass of the mixed path on the 5th-generation tensor
-// cores (tcgen05, accumulators in tensor memory), for blocks of p <= 16 columns against at
-// most 192 basis columns.
+// k_cgs_tc.cu -- the update of the first block CGS2 pass of the mixed path on the
+// 5th-generation tensor cores (tcgen05, accumulators in tensor memory), for blocks of p <= 16
+// columns against at most 160 basis columns.
 //
-// The pass computes W <- W - V h (V: n x cols, the orthonormal Krylov basis, FP64; h: cols x p,
-// the projection of the first Gram-Schmidt pass), and then, from the updated W, the FP32
-// partials of V^T W (the second pass's projection) and the double-float Gram matrix W^T W
-// (which feeds the single-pass Cholesky-QR), exactly as the CUDA-core kernel k_cgs_rows does.
-// The update must hold to FP64 rounding (the block Arnoldi relation of eq. (4.5) is what the
-// collinear-residual restart relies on), which bf16 products reach by exact slicing:
-//   * |V| <= 1 (orthonormal columns), so every entry is cut into seven signed integer slices
-//     (|s_i| <= 256) of fixed weights 2^-8, 2^-16, ..., 2^-56, exactly from its bit pattern:
-//     v = sum_i s_i 2^-8(i+1) + O(2^-56);
-//   * each column c of h gets its own exponent f_c (|h[:, c]| < 2^f_c) and six slices
-//     t_j 2^(f_c - 8(j+1));
-//   * every product s_i t_j of the 27 pairs with i + j <= 6 (the rest are below 2^-56 of
-//     max|h|) is summed over the basis columns by tcgen05.mma kind::f16 (bf16 in, FP32 out)
-//     into its own 128 x 16 accumulator in tensor memory: |s_i t_j| <= 2^16 and at most 192
-//     terms keep every sum an integer below 2^24, so the FP32 accumulation is exact;
-//   * the epilogue adds the accumulators of each level l = i + j as 32-bit integers, packs the
-//     seven levels into two 64-bit integers and forms the correction in FP64 with one rounding.
-// The error of V h is thus ~2^-56 max|h| per term, the same order as the double-float
-// arithmetic it replaces, at a fraction of its FP32 instruction count.
+// The kernel computes W <- W - V h (V: n x cols, the orthonormal Krylov basis, FP64; h: cols x
+// p, the projection of the first Gram-Schmidt pass).  The update must hold to FP64 rounding
+// (the block Arnoldi relation of eq. (4.5) is what the collinear-residual restart relies on),
+// which bf16 products reach by exact slicing into balanced base-256 digits:
+//   * |V| <= 1 (orthonormal columns): X = trunc(|v| 2^55) is cut into seven digits s_i
+//     (i = 0 most significant) in [-128, 128] (the top one in [0, 129]) with
+//     |v| = 2^-55 sum_i s_i 256^(6 - i) + O(2^-55), each digit given v's sign;
+//   * column c of h gets an exponent f_c with max_a |h[a, c]| < 2^f_c and six digits t_j in
+//     [-128, 128] of X = trunc(|h| 2^(47 - f_c)) < 2^47, so h = 2^(f_c - 47) sum_j t_j
+//     256^(5 - j) + O(2^(f_c - 47));
+//   * the product v h is the sum over pairs of s_i t_j 2^(f_c - 14 - 8 (i + j)); the 27 pairs
+//     with level l = i + j <= 6 are kept (the rest lie below 2^-56 of max|h| per term) and
+//     summed over the basis columns by tcgen05.mma kind::f16 (bf16 operands, exact for
+//     integers up to 256, FP32 accumulation) into one 128 x 16 accumulator per LEVEL: at most
+//     6 pairs per level, |s t| <= 129 * 128 and at most 160 terms keep every partial sum an
+//     integer below 2^24, so the FP32 accumulation is exact;
+//   * the epilogue sums the seven level sums S = sum_l L_l 2^(-8 l) in double-float (Horner
+//     from level 6; each L_l is an exact integer in FP32) and subtracts S 2^(f_c - 14) from W
+//     in FP64, the power of two applied to the exponent fields (two FP64 adds per entry).
+// One MMA per V digit covers all its levels at once: the six h digits of a 16-column chunk are
+// stacked along N (16 rows each), so digit i multiplies [t_0; ...; t_(nj-1)] (N = 16 nj,
+// nj = min(6, 7 - i)) into the accumulator columns of levels i .. i + nj - 1: 7 MMAs per chunk
+// (8 in the first chunk, where level 6 is started by its own MMA so that no accumulator needs
+// zeroing) into 112 of the CTA's 128 tensor-memory columns.
 //
-// Layout: one CTA per SM (the 27 accumulators take 432 of the SM's 512 tensor-memory columns),
-// 256 threads, persistent over 128-row tiles.  Per 16-column chunk of the basis each thread
-// loads 8 FP64 values of one row (coalesced per column), keeps an FP32 copy for the second
-// projection, cuts them into slices with integer operations and stores each slice's 8 bf16
-// values as one 16-byte row
-// of a core matrix (the canonical K-major layout without swizzle); thread 0 then issues the
-// 27 MMAs of the chunk and commits them to the chunk's mbarrier.  Two slice buffers alternate,
-// so the slicing of chunk k+1 overlaps the MMAs of chunk k.  Every mbarrier wait is bounded:
-// a wait that runs out records EXPM_TIMEOUT's flag, stops issuing, drains the MMAs already
-// issued (with a second, generous bound) and frees the tensor memory.
+// Layout: persistent CTAs over 128-row tiles, two per SM (86 KB of shared memory, 128
+// tensor-memory columns each), 256 threads.  Per 16-column chunk of the basis each thread
+// loads 8 FP64 values of one row (coalesced per column), cuts them into digits with integer
+// operations and stores each digit's 8 bf16 values as one 16-byte row of a core matrix (the
+// canonical K-major layout without swizzle); thread 0 then issues the chunk's MMAs and commits
+// them to the chunk's mbarrier.  Two digit buffers alternate, so the slicing of chunk k+1
+// overlaps the MMAs of chunk k, and the other CTA on the SM overlaps this one's epilogue.
+// Every mbarrier wait is bounded: a wait that runs out records EXPM_TIMEOUT's flag, stops
+// issuing, drains the MMAs already issued (with a second, generous bound) and frees the tensor
+// memory.  The second pass's projection and the Gram matrix of the updated block are left to
+// the CUDA-core projection kernel (k_cgs_rows<false> with the Gram outputs).
 #include <cuda_bf16.h>
 
 #include "df.cuh"
@@ -42,19 +48,16 @@ namespace {
 
 constexpr int TCT = 256;          // threads per CTA
 constexpr int TCM = 128;          // rows per tile (tensor-memory lanes)
-constexpr int NVS = 7;            // slices of V
-constexpr int NHS = 6;            // slices of h
-constexpr int NPAIR = 27;         // pairs (i, j) with i + j <= 6
-constexpr int TC_COLS_MAX = 192;
-constexpr int TMEM_COLS = 512;
-constexpr int VFS = TCM + 1;      // row stride of the FP32 copy of V (per basis column)
-constexpr int WFS = 17;           // row stride of the FP32 copy of W
-constexpr uint32_t kATile = 4096; // one 128 x 16 bf16 slice, bytes
-constexpr uint32_t kBTile = 512;  // one 16 x 16 bf16 slice, bytes
+constexpr int NVS = 7;            // digits of V
+constexpr int NHS = 6;            // digits of h
+constexpr int NLEV = 7;           // levels i + j = 0 .. 6
+constexpr int TC_COLS_MAX = 160;
+constexpr int TMEM_COLS = 128;    // 7 levels x 16 columns, allocated as a power of two
+constexpr uint32_t kATile = 4096; // one 128 x 16 bf16 digit slice of V, bytes
+constexpr uint32_t kBTile = 512;  // one 16 x 16 bf16 digit slice of h, bytes
 
 __host__ __device__ constexpr size_t tc_smem_bytes(int cols) {
-    return (size_t)2 * NVS * kATile + (size_t)((cols + 15) / 16) * NHS * kBTile + sizeof(float) * (size_t)cols * VFS +
-           sizeof(float) * (TCM * WFS + 2 * TCM * 16);
+    return (size_t)2 * NVS * kATile + (size_t)((cols + 15) / 16) * NHS * kBTile;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -72,8 +75,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
            ((uint64_t)1 << 46);
 }
 
-// instruction descriptor of kind::f16: D FP32, A and B bf16, both K-major, N = 16, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor of kind::f16: D FP32, A and B bf16, both K-major, M = 128, N given
+__device__ __forceinline__ uint32_t idesc(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long limit) {
     uint32_t done = 0;
@@ -85,10 +90,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     return done != 0;
 }
 
-__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t acc) {
+__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t n, uint32_t acc) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-                 "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+                 "l"(da), "l"(db), "r"(idesc(n)), "r"(acc));
 }
 
 // 8 consecutive accumulator columns of this warp's 32 lanes
@@ -98,52 +103,67 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
                  : "r"(taddr));
 }
 
-// The seven slices of v (|v| <= 1 + 2^-8): X = round-toward-zero(|v| 2^56) as a 64-bit integer
-// from the bit pattern, its base-256 digits d_0 .. d_6 (d_0 <= 256, X = sum d_i 2^(8 (6 - i))),
-// each turned into an exact float (2^23 + d - 2^23) and given v's sign.  Returns false when
-// |v| is too large for the slicing (d_0 > 256).
+// an integer d in [-256, 256] as an exact float without a conversion instruction (2^23 + 256 +
+// d is a float with unit spacing; subtracting 2^23 + 256 is exact)
+__device__ __forceinline__ float small_int_f(int d) {
+    return __int_as_float(0x4B000000 + 256 + d) - 8388864.f;
+}
+
+// The seven balanced digits of v (|v| <= 1 + 2^-8) from its bit pattern: X = trunc(|v| 2^55),
+// base-256 digits from the least significant, each folded into [-128, 127] with a carry into
+// the next; the top digit takes the last carry unfolded (X < 2^55 + 2^47 keeps it <= 129).
+// Returns false when |v| is too large for the slicing.
 __device__ __forceinline__ bool slice7(double v, float* s) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int E = (int)((b >> 52) & 0x7FF);
-    const unsigned sgn = (unsigned)(b >> 63) << 31;
+    const bool neg = (b >> 63) != 0;
     const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = E - 1019;                  // |v| 2^56 = m 2^sh
+    const int sh = E - 1020;                  // |v| 2^55 = m 2^sh
     unsigned long long X = 0;
-    if (E != 0 && sh > -53) X = sh >= 0 ? (sh < 8 ? m << sh : ~0ull) : m >> (-sh);
-    const unsigned d0 = (unsigned)(X >> 48);
+    if (E != 0 && sh > -53) X = sh >= 0 ? (sh <= 3 ? m << sh : ~0ull) : m >> (-sh);
+    int carry = 0;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
-        const unsigned d = i == 0 ? min(d0, 256u) : (unsigned)(X >> (8 * (6 - i))) & 0xFFu;
-        const float f = __int_as_float(0x4B000000 | d) - 8388608.f;
-        s[i] = __int_as_float(__float_as_int(f) ^ (int)sgn);
+    for (int i = 6; i >= 1; --i) {
+        int d = (int)((X >> (8 * (6 - i))) & 0xFFu) + carry;
+        carry = d >= 128;
+        d -= carry << 8;
+        s[i] = small_int_f(neg ? -d : d);
     }
-    return d0 <= 256u;
+    const int top = (int)min(X >> 48, 255ull);
+    const int d0 = top + carry;
+    s[0] = small_int_f(neg ? -d0 : d0);
+    return top <= 128;
+}
+
+// x 2^k by an add to the exponent field (integer operations only); a result below the normal
+// range flushes to a signed zero and one above it becomes inf
+__device__ __forceinline__ double scale2_i(double x, int k) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    long long r = b + ((long long)k << 52);
+    if (e == 0 || e + k <= 0) r = b & (1LL << 63);
+    if (e != 0 && e + k >= 0x7FF) r = (b & (1LL << 63)) | (0x7FFLL << 52);
+    return __longlong_as_double(r);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // exact: |a|, |b| <= 256 integers
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // exact: integers |a|, |b| <= 256
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <int K>
-__global__ void __launch_bounds__(TCT, 1) k_cgs_tc(const double* __restrict__ V, int64_t ldv, int cols,
+template <int dummy>
+__global__ void __launch_bounds__(TCT, 2) k_cgs_tc(const double* __restrict__ V, int64_t ldv, int cols,
                                                    double* __restrict__ W, int64_t ldw, int p, int64_t n,
-                                                   const double* __restrict__ h, double* __restrict__ part,
-                                                   int* flags, long spin_limit) {
+                                                   const double* __restrict__ h, int* flags, long spin_limit) {
     extern __shared__ __align__(1024) unsigned char smc[];
     const int nk = (cols + 15) >> 4;
     unsigned char* As = smc;                                   // [2][NVS][kATile]
     unsigned char* Bs = As + 2 * NVS * kATile;                 // [nk][NHS][kBTile]
-    float* Vf = reinterpret_cast<float*>(Bs + (size_t)nk * NHS * kBTile);   // [cols][VFS]
-    float* Wf = Vf + (size_t)cols * VFS;                       // [TCM][WFS]
-    float* Wh = Wf + TCM * WFS;                                // [TCM][16]
-    float* Wl = Wh + TCM * 16;
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tbase_s;
-    __shared__ int fexp[16];
+    __shared__ int fexp[16], emax_s[16];
     __shared__ int bad_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nout = (cols + p) * p;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase_s)),
@@ -156,40 +176,46 @@ __global__ void __launch_bounds__(TCT, 1) k_cgs_tc(const double* __restrict__ V,
         asm volatile("fence.mbarrier_init.release.cluster;");
         bad_s = 0;
     }
-    // h: per-column exponents and six bf16 slices per 16 x 16 chunk (B operands), staged
-    // through the (not yet used) FP32 copy of V
-    double* hs = reinterpret_cast<double*>(Vf);
-    for (int e = tid; e < cols * p; e += TCT) hs[e] = h[e];
-    __syncthreads();
+    // per column c: the exponent f_c with max_a |h[a, c]| < 2^f_c, from the bit pattern
     if (tid < 16) {
-        double mx = 0.0;
+        int emax = 0;
         if (tid < p)
-            for (int a = 0; a < cols; ++a) mx = fmax(mx, fabs(hs[a * p + tid]));
-        int e = 0;
-        if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);   // mx < 2^e
-        fexp[tid] = e;
+            for (int a = 0; a < cols; ++a)
+                emax = max(emax, (int)(((unsigned long long)__double_as_longlong(h[a * p + tid]) >> 52) & 0x7FF));
+        emax_s[tid] = emax;
+        fexp[tid] = emax > 0 ? emax - 1022 : -1021;            // |h| < 2^(E - 1022)
     }
     __syncthreads();
+    if (tid == 0)
+        for (int c = 0; c < p; ++c)
+            if (emax_s[c] == 0x7FF) bad_s |= 1;                // h not finite
+    // h's digits as the B operands, chunk kc: six 16 x 16 K-major blocks stacked along N
     for (int e = tid; e < nk * 256; e += TCT) {
         const int kc = e >> 8, rem = e & 255, c = rem >> 4, k = rem & 15, a = kc * 16 + k;
-        double x = (a < cols && c < p) ? ldexp(hs[a * p + c], -fexp[c]) : 0.0;   // |x| < 1
-        for (int j = 0; j < NHS; ++j) {
-            x *= 256.0;
-            const double s = trunc(x);
-            x -= s;
-            *reinterpret_cast<__nv_bfloat16*>(Bs + ((size_t)kc * NHS + j) * kBTile + kmaj(c, k)) = __float2bfloat16((float)s);
+        unsigned long long X = 0;
+        bool neg = false;
+        if (a < cols && c < p) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(h[a * p + c]);
+            const int E = (int)((b >> 52) & 0x7FF);
+            neg = (b >> 63) != 0;
+            const int sh = E - 1028 - fexp[c];                 // |h| 2^(47 - f) = m 2^sh, sh <= -6
+            if (E != 0 && sh > -64) X = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (-sh);
+        }
+        int carry = 0;
+        for (int j = NHS - 1; j >= 0; --j) {
+            int d = (int)((X >> (8 * (NHS - 1 - j))) & 0xFFu) + carry;
+            if (j > 0) {
+                carry = d >= 128;
+                d -= carry << 8;
+            }
+            *reinterpret_cast<__nv_bfloat16*>(Bs + ((size_t)kc * NHS + j) * kBTile + kmaj(c, k)) =
+                __float2bfloat16((float)(neg ? -d : d));
         }
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     const uint32_t tbase = tbase_s;
 
-    float ah[K], al[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-        ah[q] = 0.f;
-        al[q] = 0.f;
-    }
     int uses0 = 0, uses1 = 0;          // commits so far to mbar[0], mbar[1] (uniform)
     bool stop = false;                 // a bounded wait ran out: issue nothing more
     const int r = tid & (TCM - 1), g = tid >> 7;
@@ -225,8 +251,6 @@ __global__ void __launch_bounds__(TCT, 1) k_cgs_tc(const double* __restrict__ V,
             bool ok = true;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int a = kc * 16 + g * 8 + u;
-                if (a < cols) Vf[a * VFS + r] = (float)v[u];
                 float d[NVS];
                 ok &= slice7(v[u], d);
 #pragma unroll
@@ -249,13 +273,19 @@ __global__ void __launch_bounds__(TCT, 1) k_cgs_tc(const double* __restrict__ V,
             asm volatile("tcgen05.fence::after_thread_sync;");
             if (tid == 0) {
                 const unsigned char* Bk = Bs + (size_t)kc * NHS * kBTile;
-                int pr = 0;
+                const uint64_t db = sdesc(smem_u32(Bk));
 #pragma unroll 1
-                for (int j = 0; j < NHS; ++j)
-#pragma unroll 1
-                    for (int i = 0; i + j <= 6; ++i, ++pr)
-                        mma_issue(tbase + 16u * pr, sdesc(smem_u32(Ab + (size_t)i * kATile)),
-                                  sdesc(smem_u32(Bk + (size_t)j * kBTile)), kc > 0 ? 1u : 0u);
+                for (int i = 0; i < NVS; ++i) {
+                    const uint64_t da = sdesc(smem_u32(Ab + (size_t)i * kATile));
+                    const int nj = min(NHS, NLEV - i);
+                    if (kc == 0 && i == 1) {
+                        // level 6 is first written here: its own MMA starts it (pair (1, 5))
+                        mma_issue(tbase + 16u * 6u, da, sdesc(smem_u32(Bk + (size_t)5 * kBTile)), 16u, 0u);
+                        mma_issue(tbase + 16u, da, db, 16u * 5u, 1u);
+                    } else {
+                        mma_issue(tbase + 16u * (uint32_t)i, da, db, 16u * (uint32_t)nj, (kc > 0 || i > 0) ? 1u : 0u);
+                    }
+                }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_u32(&mbar[buf])));
             }
@@ -278,81 +308,34 @@ __global__ void __launch_bounds__(TCT, 1) k_cgs_tc(const double* __restrict__ V,
         }
         // epilogue: warp w reads lanes 32 (w % 4) .. +31 (rows), columns 8 (w / 4) .. +7
         {
-            const int q4 = warp & 3, c0 = (warp >> 2) * 8, rr = q4 * 32 + lane;
-            int L[7][8];
-#pragma unroll
-            for (int l = 0; l < 7; ++l)
-#pragma unroll
-                for (int c = 0; c < 8; ++c) L[l][c] = 0;
+            const int q4 = warp & 3, c0 = (warp >> 2) * 8;
             const uint32_t tl = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c0;
-            int pr = 0;
+            uint32_t x[NLEV][8];
 #pragma unroll
-            for (int j = 0; j < NHS; ++j)
-#pragma unroll
-                for (int i = 0; i + j <= 6; ++i, ++pr) {
-                    uint32_t x[8];
-                    tmem_ld8(tl + 16u * pr, x);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) L[i + j][c] += __float2int_rz(__uint_as_float(x[c]));
-                }
-            const int64_t row = row0 + rr;
+            for (int l = 0; l < NLEV; ++l) tmem_ld8(tl + 16u * l, x[l]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            const int64_t row = row0 + q4 * 32 + lane;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int cc = c0 + c;
-                float wf = 0.f, wh = 0.f, wl = 0.f;
                 if (row < n && cc < p) {
-                    // sum_l L_l 2^-8l = hi 2^-16 + lo 2^-48, exact in 64-bit integers
-                    const long long hi = ((long long)L[0][c] << 16) + ((long long)L[1][c] << 8) + (long long)L[2][c];
-                    const long long lo = ((long long)L[3][c] << 24) + ((long long)L[4][c] << 16) +
-                                         ((long long)L[5][c] << 8) + (long long)L[6][c];
-                    const double corr = ldexp(fma((double)hi, 0x1p-16, (double)lo * 0x1p-48), fexp[cc] - 16);
-                    const double w = W[(int64_t)cc * ldw + row] - corr;
-                    W[(int64_t)cc * ldw + row] = w;
-                    wf = (float)w;
-                    split_df(w, wh, wl);
+                    // S = sum_l L_l 2^(-8 l) by Horner from level 6 in double-float (the level
+                    // sums are exact integers in FP32), then corr = S 2^(f - 14), with the
+                    // power of two applied to the exponent field
+                    float sh = __uint_as_float(x[NLEV - 1][c]), sl = 0.f;
+#pragma unroll
+                    for (int l = NLEV - 2; l >= 0; --l) {
+                        sh *= 0x1p-8f;
+                        sl *= 0x1p-8f;
+                        df_add(sh, sl, __uint_as_float(x[l][c]));
+                    }
+                    const int k = fexp[cc] - 14;
+                    const double w = W[(int64_t)cc * ldw + row] - scale2_i(f64_of_f32_i(sh), k);
+                    W[(int64_t)cc * ldw + row] = w - scale2_i(f64_of_f32_i(sl), k);
                 }
-                Wf[rr * WFS + cc] = wf;
-                Wh[rr * 16 + cc] = wh;
-                Wl[rr * 16 + cc] = wl;
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        // the second pass's FP32 projection V^T W and the double-float Gram W^T W of this tile
-#pragma unroll
-        for (int q = 0; q < K; ++q) {
-            const int o = tid + q * TCT;
-            if (o < nout) {
-                const int a = o / p, c = o - a * p;
-                if (a >= cols) {
-                    const int a2 = a - cols;
-                    float sh = 0.f, sx = 0.f;
-#pragma unroll 4
-                    for (int k = 0; k < TCM; ++k) {
-                        const float vh = Wh[k * 16 + a2], vl = Wl[k * 16 + a2], h1 = Wh[k * 16 + c], h2 = Wl[k * 16 + c];
-                        const float pr = vh * h1;
-                        float t = fmaf(vh, h1, -pr);
-                        t = fmaf(vl, h1, t);
-                        t = fmaf(vh, h2, t);
-                        df_add(sh, sx, pr);
-                        sx += t;
-                    }
-                    df_add(ah[q], al[q], sh);
-                    al[q] += sx;
-                } else {
-                    const float* va = Vf + (size_t)a * VFS;
-                    float s0 = 0.f, s1 = 0.f;
-#pragma unroll 8
-                    for (int k = 0; k < TCM; k += 2) {
-                        s0 = fmaf(va[k], Wf[k * WFS + c], s0);
-                        s1 = fmaf(va[k + 1], Wf[(k + 1) * WFS + c], s1);
-                    }
-                    df_add(ah[q], al[q], s0);
-                    df_add(ah[q], al[q], s1);
-                }
-            }
-        }
         __syncthreads();
     }
     // drain: after a wait ran out, the MMAs already issued still complete before the tensor
@@ -361,11 +344,6 @@ __global__ void __launch_bounds__(TCT, 1) k_cgs_tc(const double* __restrict__ V,
         const int b0 = uses0 > 0 ? mbar_wait(&mbar[0], (uint32_t)((uses0 - 1) & 1), 1L << 26) : 1;
         const int b1 = uses1 > 0 ? mbar_wait(&mbar[1], (uint32_t)((uses1 - 1) & 1), 1L << 26) : 1;
         if (!(b0 && b1) && lane == 0) atomicOr(&bad_s, 4);
-    }
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-        const int o = tid + q * TCT;
-        if (o < nout) part[(int64_t)blockIdx.x * nout + o] = (double)ah[q] + (double)al[q];
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -390,37 +368,18 @@ int tc_sms() {
 
 bool cgs_tc_fit(int cols, int p) { return p >= 1 && p <= 16 && cols >= 1 && cols <= TC_COLS_MAX; }
 
-// grid_out: the CTA count (one per SM at most): the partials' row count for the reduction
+// W <- W - V h on the tensor cores; persistent CTAs, two per SM at most
 cudaError_t launch_cgs_tc(const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p, int64_t n,
-                          const double* h, double* part, int* grid_out, int* flags, long spin_limit, cudaStream_t s) {
-    if (!cgs_tc_fit(cols, p) || !h || !part || !grid_out || !flags) return cudaErrorInvalidValue;
+                          const double* h, int* flags, long spin_limit, cudaStream_t s) {
+    if (!cgs_tc_fit(cols, p) || !h || !flags) return cudaErrorInvalidValue;
     const int64_t tiles = (n + TCM - 1) / TCM;
-    const int g = (int)std::min<int64_t>(tiles, tc_sms());
-    *grid_out = g;
-    const size_t shm = tc_smem_bytes(cols);
-    const int k = ((cols + p) * p + TCT - 1) / TCT;
-#define EXPM_TC_K(KK) k_cgs_tc<KK><<<g, TCT, shm, s>>>(V, ldv, cols, W, ldw, p, n, h, part, flags, spin_limit)
-    if (k <= 4) EXPM_TC_K(4);
-    else if (k <= 8) EXPM_TC_K(8);
-    else EXPM_TC_K(14);
-#undef EXPM_TC_K
+    const int g = (int)std::min<int64_t>(tiles, 2 * (int64_t)tc_sms());
+    k_cgs_tc<0><<<g, TCT, tc_smem_bytes(cols), s>>>(V, ldv, cols, W, ldw, p, n, h, flags, spin_limit);
     return cudaGetLastError();
 }
 
 cudaError_t cgs_tc_set_smem_limits() {
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    auto set = [&](auto kern) {
-        if (e != cudaSuccess) return;
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, kern);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-    };
-    set(k_cgs_tc<4>);
-    set(k_cgs_tc<8>);
-    set(k_cgs_tc<14>);
-    return e;
+    return cudaFuncSetAttribute(k_cgs_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_COLS_MAX));
 }
 
 }  // namespace expm

@@ -1055,7 +1055,8 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
 // ---- first block CGS2 pass of the mixed path, in chunks of RB = NTR / 2 rows
 //
 // k_cgs_rows<false>: partial[blk][a][c] = sum over the CTA's rows of V[r, a] W[r, c] (FP32
-// products; the projection of the first pass).
+// products; the projection of the first pass, or of the second after the tensor-core update),
+// with ng = p also the double-float Gram partial as below.
 // k_cgs_rows<true>:  W <- W - V h in double-float arithmetic (each product
 // v h = vh hh + (err(vh hh) + vl hh + vh hl), the large parts accumulated with TwoSum), then
 // the FP32 partials of V^T W for the second pass; with ng = p also the Gram partial W^T W
@@ -1199,7 +1200,7 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
     if (cols & 1)                                      // the padding column of the last block
         for (int e = threadIdx.x; e < VS; e += NTR) Vs[cols * VS + e] = 0.f;
     const int ncb = (p + 3) >> 2, nblk = cgs_nblk(cols, p);
-    const int gp = UPD ? ng : 0, ngu = gp * (gp + 1) / 2;
+    const int gp = ng, ngu = gp * (gp + 1) / 2;
     float ah[KB][8], al[KB][8], gh[KG], gl[KG];
     int gi[KG], gj[KG];
 #pragma unroll
@@ -1305,12 +1306,14 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             }
             for (int e = threadIdx.x; e < RP * RB; e += NTR) {
                 const int c = e / RB, r2 = e - c * RB;
-                Wf[r2 * WS4 + c] = (c < p && r2 < tr) ? f32_rn_i(W[(int64_t)c * ldw + r0 + r2]) : 0.f;
+                const double w = (c < p && r2 < tr) ? W[(int64_t)c * ldw + r0 + r2] : 0.0;
+                Wf[r2 * WS4 + c] = f32_rn_i(w);
+                if (ng) split_df_i(w, Wh[r2 * WG + c], Wl[r2 * WG + c]);
             }
         }
         __syncthreads();
         chunk_project<KB>(Vs, Wf, nblk, ncb, ah, al);
-        if (UPD && ngu) chunk_gram(Wh, Wl, gi, gj, ngu, gh, gl);
+        if (ngu) chunk_gram(Wh, Wl, gi, gj, ngu, gh, gl);
     }
     const int nout = (cols + gp) * p;
     double* out = part + (int64_t)blockIdx.x * nout;

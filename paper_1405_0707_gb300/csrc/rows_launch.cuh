@@ -13,7 +13,7 @@ bool cgs_fit(int cols, int p) {
 
 cudaError_t cgs(int upd, const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p, int64_t n,
                 const double* h, double* part, int nblk, int gram, cudaStream_t s) {
-    if (!cgs_fit(cols, p) || (upd && !h) || (gram && !upd)) return cudaErrorInvalidValue;
+    if (!cgs_fit(cols, p) || (upd && !h)) return cudaErrorInvalidValue;
     const int64_t rpb = rows_per_block(n, nblk);
     const int g = blocks_for(n, nblk);
     const int ng = gram ? p : 0;
@@ -21,7 +21,7 @@ cudaError_t cgs(int upd, const double* V, int64_t ldv, int cols, double* W, int6
 #define EXPM_CGS_K(KK)                                                                               \
     {                                                                                               \
         if (upd) k_cgs_rows<true, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng); \
-        else k_cgs_rows<false, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, 0);     \
+        else k_cgs_rows<false, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng);    \
     }
     const int k = (cgs_nblk(cols, p) + NTR - 1) / NTR;
     if (k <= 1) EXPM_CGS_K(1)

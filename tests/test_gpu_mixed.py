@@ -67,8 +67,10 @@ def test_refined_fp32_inverse_3d_transform_paths(sides, diff, vel, t, p):
 @pytest.mark.parametrize("sides,diff,vel,t,p", CASES + CASES_3D[:2] + [((517,), 1.0, (0.0,), 1.0, 3)])
 def test_double_float_stencil_matches_sparse_matrix(sides, diff, vel, t, p):
     """Mixed plans apply tA in double-float (pairs of floats from the bit pattern): every entry
-    within 2^-45 of the sum of the magnitudes of its terms, |tA| |V| (the pair arithmetic's
-    ~2^-48 per term, with room for 7 terms)."""
+    within 2^-43 of the sum of the magnitudes of its terms, |tA| |V|.  Each pair multiply-add
+    leaves up to ~2^-47 of its term (the rounded cross terms and the low word's sum), and the
+    coefficients' pairs carry 2^-48: an FP32 emulation of the kernel on the 256^2 case reaches
+    0.99 * 2^-45 with 5 terms; 2^-43 covers 7 terms with room."""
     need_gpu()
     from paper_1405_0707_gb300 import Plan
     n = int(np.prod(sides))
@@ -77,7 +79,7 @@ def test_double_float_stencil_matches_sparse_matrix(sides, diff, vel, t, p):
     A = ops.cd_matrix(sides, diff, vel, t)
     ref = A @ V
     bound = abs(A) @ np.abs(V)
-    assert np.all(np.abs(W - ref) <= 2.0 ** -45 * bound)
+    assert np.all(np.abs(W - ref) <= 2.0 ** -43 * bound)
 
 
 @pytest.mark.parametrize("sides,diff,vel,t,p", CASES[:3])
