@@ -103,36 +103,31 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
                  : "r"(taddr));
 }
 
-// an integer d in [-256, 256] as an exact float without a conversion instruction (2^23 + 256 +
-// d is a float with unit spacing; subtracting 2^23 + 256 is exact)
-__device__ __forceinline__ float small_int_f(int d) {
-    return __int_as_float(0x4B000000 + 256 + d) - 8388864.f;
-}
-
-// The seven balanced digits of v (|v| <= 1 + 2^-8) from its bit pattern: X = trunc(|v| 2^55),
-// base-256 digits from the least significant, each folded into [-128, 127] with a carry into
-// the next; the top digit takes the last carry unfolded (X < 2^55 + 2^47 keeps it <= 129).
-// Returns false when |v| is too large for the slicing.
+// The seven balanced digits of v (|v| <= 1 + 2^-8) from its bit pattern: X = trunc(|v| 2^55)
+// in base 256 with the six low digits in [-128, 127] and the top one taking the last carry
+// (X < 2^55 + 2^47 keeps it <= 129).  Adding 128 at each low byte position, Y = X + 0x80..80,
+// turns those digits into the plain bytes of Y (d = byte - 128), so no carry chain is run:
+// each byte is placed into the float 2^23 + byte by one byte permute and the digit, with v's
+// sign, follows from one FMA.  Returns false when |v| is too large for the slicing.
 __device__ __forceinline__ bool slice7(double v, float* s) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int E = (int)((b >> 52) & 0x7FF);
-    const bool neg = (b >> 63) != 0;
     const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     const int sh = E - 1020;                  // |v| 2^55 = m 2^sh
     unsigned long long X = 0;
     if (E != 0 && sh > -53) X = sh >= 0 ? (sh <= 3 ? m << sh : ~0ull) : m >> (-sh);
-    int carry = 0;
-#pragma unroll
-    for (int i = 6; i >= 1; --i) {
-        int d = (int)((X >> (8 * (6 - i))) & 0xFFu) + carry;
-        carry = d >= 128;
-        d -= carry << 8;
-        s[i] = small_int_f(neg ? -d : d);
-    }
-    const int top = (int)min(X >> 48, 255ull);
-    const int d0 = top + carry;
-    s[0] = small_int_f(neg ? -d0 : d0);
-    return top <= 128;
+    const unsigned long long Y = X + 0x808080808080ull;
+    const unsigned lo = (unsigned)Y, hi = (unsigned)(Y >> 32);
+    const float sg = (b >> 63) ? -1.f : 1.f, off = -8388736.f * sg, off0 = -8388608.f * sg;
+    // byte k of Y (k = 6 - i for digit i) as the float 2^23 + byte
+    s[6] = fmaf(__uint_as_float(__byte_perm(0x4B000000u, lo, 0x3214u)), sg, off);
+    s[5] = fmaf(__uint_as_float(__byte_perm(0x4B000000u, lo, 0x3215u)), sg, off);
+    s[4] = fmaf(__uint_as_float(__byte_perm(0x4B000000u, lo, 0x3216u)), sg, off);
+    s[3] = fmaf(__uint_as_float(__byte_perm(0x4B000000u, lo, 0x3217u)), sg, off);
+    s[2] = fmaf(__uint_as_float(__byte_perm(0x4B000000u, hi, 0x3214u)), sg, off);
+    s[1] = fmaf(__uint_as_float(__byte_perm(0x4B000000u, hi, 0x3215u)), sg, off);
+    s[0] = fmaf(__uint_as_float(__byte_perm(0x4B000000u, hi, 0x3216u)), sg, off0);
+    return (X >> 48) <= 128;
 }
 
 // x 2^k by an add to the exponent field (integer operations only); a result below the normal

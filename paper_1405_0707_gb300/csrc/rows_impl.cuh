@@ -1176,7 +1176,9 @@ __device__ __forceinline__ void df_row_update(float* sh, float* sl, float vh, fl
     }
 }
 
-template <bool UPD, int KB>
+// GR: the Gram outputs are compiled in (the update always; the projection only in its Gram
+// variant, so the plain projection keeps its lower register count)
+template <bool UPD, bool GR, int KB>
 __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, int64_t ldv, int cols,
                                                  double* __restrict__ W, int64_t ldw, int p, int64_t n,
                                                  int64_t rpb, const double* __restrict__ h,
@@ -1200,7 +1202,7 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
     if (cols & 1)                                      // the padding column of the last block
         for (int e = threadIdx.x; e < VS; e += NTR) Vs[cols * VS + e] = 0.f;
     const int ncb = (p + 3) >> 2, nblk = cgs_nblk(cols, p);
-    const int gp = ng, ngu = gp * (gp + 1) / 2;
+    const int gp = GR ? ng : 0, ngu = gp * (gp + 1) / 2;
     float ah[KB][8], al[KB][8], gh[KG], gl[KG];
     int gi[KG], gj[KG];
 #pragma unroll
@@ -1290,25 +1292,37 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             }
         } else {
             __syncthreads();                           // previous chunk consumed
+            // batches of LB loads per thread, the next batch issued before the current one is
+            // converted and stored, so two batches are in flight
             const int tot = cols * RB;
-            for (int e0 = threadIdx.x; e0 < tot; e0 += LB * NTR) {
-                double v[LB];
+            double v[LB], vn[LB];
 #pragma unroll
-                for (int k = 0; k < LB; ++k) {
-                    const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
-                    v[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+            for (int k = 0; k < LB; ++k) {
+                const int e = threadIdx.x + k * NTR, a = e / RB, r2 = e - a * RB;
+                v[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+            }
+            for (int e0 = threadIdx.x; e0 < tot; e0 += LB * NTR) {
+                const int e1 = e0 + LB * NTR;
+                if (e1 < tot) {
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) {
+                        const int e = e1 + k * NTR, a = e / RB, r2 = e - a * RB;
+                        vn[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+                    }
                 }
 #pragma unroll
                 for (int k = 0; k < LB; ++k) {
                     const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
                     if (e < tot) Vs[a * VS + r2] = f32_rn_i(v[k]);
                 }
+#pragma unroll
+                for (int k = 0; k < LB; ++k) v[k] = vn[k];
             }
             for (int e = threadIdx.x; e < RP * RB; e += NTR) {
                 const int c = e / RB, r2 = e - c * RB;
                 const double w = (c < p && r2 < tr) ? W[(int64_t)c * ldw + r0 + r2] : 0.0;
                 Wf[r2 * WS4 + c] = f32_rn_i(w);
-                if (ng) split_df_i(w, Wh[r2 * WG + c], Wl[r2 * WG + c]);
+                if (GR && ng) split_df_i(w, Wh[r2 * WG + c], Wl[r2 * WG + c]);
             }
         }
         __syncthreads();

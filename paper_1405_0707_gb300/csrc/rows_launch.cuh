@@ -20,8 +20,9 @@ cudaError_t cgs(int upd, const double* V, int64_t ldv, int cols, double* W, int6
     const size_t shm = cgs_rows_smem(cols, upd != 0, ng);
 #define EXPM_CGS_K(KK)                                                                               \
     {                                                                                               \
-        if (upd) k_cgs_rows<true, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng); \
-        else k_cgs_rows<false, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng);    \
+        if (upd) k_cgs_rows<true, true, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng); \
+        else if (ng) k_cgs_rows<false, true, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, ng); \
+        else k_cgs_rows<false, false, KK><<<g, NTR, shm, s>>>(V, ldv, cols, W, ldw, p, n, rpb, h, part, 0);    \
     }
     const int k = (cgs_nblk(cols, p) + NTR - 1) / NTR;
     if (k <= 1) EXPM_CGS_K(1)
@@ -104,10 +105,12 @@ cudaError_t set_smem(int optin) {
     EXPM_SET(k_update_gram_rows<true>);
     EXPM_SET(k_update_z_rows<false>);
     EXPM_SET(k_update_z_rows<true>);
-    EXPM_SET((k_cgs_rows<true, 1>)); EXPM_SET((k_cgs_rows<true, 2>)); EXPM_SET((k_cgs_rows<true, 3>));
-    EXPM_SET((k_cgs_rows<true, 5>));
-    EXPM_SET((k_cgs_rows<false, 1>)); EXPM_SET((k_cgs_rows<false, 2>)); EXPM_SET((k_cgs_rows<false, 3>));
-    EXPM_SET((k_cgs_rows<false, 5>));
+    EXPM_SET((k_cgs_rows<true, true, 1>)); EXPM_SET((k_cgs_rows<true, true, 2>));
+    EXPM_SET((k_cgs_rows<true, true, 3>)); EXPM_SET((k_cgs_rows<true, true, 5>));
+    EXPM_SET((k_cgs_rows<false, true, 1>)); EXPM_SET((k_cgs_rows<false, true, 2>));
+    EXPM_SET((k_cgs_rows<false, true, 3>)); EXPM_SET((k_cgs_rows<false, true, 5>));
+    EXPM_SET((k_cgs_rows<false, false, 1>)); EXPM_SET((k_cgs_rows<false, false, 2>));
+    EXPM_SET((k_cgs_rows<false, false, 3>)); EXPM_SET((k_cgs_rows<false, false, 5>));
     EXPM_SET(k_qr_mixed_rows<3>);
 #undef EXPM_SET
     return e;
