@@ -349,7 +349,7 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
         // applied by the first Cholesky-QR pass.  The update on the tensor cores (exact bf16
         // slicing, k_cgs_tc) when the plan chose it, followed by the FP32 projection kernel with
         // the Gram outputs; else all three in one double-float pass on the FP32 pipe
-        if (P->cgs_tc && cgs_tc_fit(cols, p)) {
+        if (P->cgs_tc && cgs_tc_fit(cols, p) && (P->cgs_tc == 1 || (p >= 12 && cols >= 64))) {
             LAUNCH(EXPM_STAGE_CGS, launch_cgs_tc(P->V, ld, cols, P->W, ld, p, n, h, flags_of(P->stat), P->tc_spin, s));
             LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(0, P->V, ld, cols, P->W, ld, p, n, nullptr, P->part, nbc, 1, s));
             LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols + p, p, h, P->H, P->ldH, 0, j * p, 1, s, cols));
@@ -1207,11 +1207,13 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         // block (the fallback of the single accurate pass)
         const char* sq = std::getenv("EXPM_QR_SINGLE_PASS");
         P->qr_single = !(sq && sq[0] == '0');
-        // the first CGS pass on the tensor cores (k_cgs_tc): "1" selects it for mixed plans.
-        // Off by default: measured on the batched workload it is still slower than the
-        // double-float pass (one 8-warp CTA per SM, see k_cgs_tc.cu)
+        // the first CGS pass's update on the tensor cores (k_cgs_tc, then the projection kernel
+        // for the second pass and the Gram matrix) for mixed plans: by default for block
+        // steps with p >= 12 and at least 64 basis columns, where it measured faster than the
+        // double-float pass (whose cost grows with p, the tensor-core pass's with the basis
+        // alone).  Test switch: "1" for every block step it fits, "0" never
         const char* tc = std::getenv("EXPM_CGS_TC");
-        P->cgs_tc = opts->precision == EXPM_PREC_MIXED && tc && tc[0] == '1';
+        P->cgs_tc = opts->precision != EXPM_PREC_MIXED ? 0 : !tc ? 2 : tc[0] == '1' ? 1 : 0;
         // test switch: the bound of the tensor-core kernel's waits (0 makes every wait run out)
         const char* sl = std::getenv("EXPM_TC_SPIN_LIMIT");
         if (sl) P->tc_spin = std::strtol(sl, nullptr, 10);

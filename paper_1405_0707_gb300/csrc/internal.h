@@ -210,7 +210,7 @@ struct expm_plan_s {
     // CUDA graphs of one restart cycle, keyed by (algorithm, p, t)
     bool use_graphs = false;
     bool qr_single = true;     // mixed path: try the single accurate Cholesky-QR pass
-    bool cgs_tc = false;       // mixed path: first CGS pass on the tensor cores (k_cgs_tc)
+    int cgs_tc = 0;            // mixed path, first CGS update on the tensor cores: 0 never, 1 always, 2 by shape
     int stencil_df = 0;        // mixed path: the stencil in double-float (k_cd_apply_df)
     long tc_spin = 1L << 24;   // bound of the tensor-core kernel's mbarrier waits (iterations)
     // deflated restart (opts.k_defl > 0)

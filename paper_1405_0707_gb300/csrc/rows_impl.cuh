@@ -1292,31 +1292,49 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             }
         } else {
             __syncthreads();                           // previous chunk consumed
-            // batches of LB loads per thread, the next batch issued before the current one is
-            // converted and stored, so two batches are in flight
+            // batches of LB loads per thread.  With many basis columns (KB >= 3) the next batch
+            // is issued before the current one is converted and stored, so two batches are in
+            // flight (measured faster at 160 columns, 96^3; slower with few columns, where the
+            // extra registers cost a resident CTA)
             const int tot = cols * RB;
-            double v[LB], vn[LB];
-#pragma unroll
-            for (int k = 0; k < LB; ++k) {
-                const int e = threadIdx.x + k * NTR, a = e / RB, r2 = e - a * RB;
-                v[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
-            }
-            for (int e0 = threadIdx.x; e0 < tot; e0 += LB * NTR) {
-                const int e1 = e0 + LB * NTR;
-                if (e1 < tot) {
-#pragma unroll
-                    for (int k = 0; k < LB; ++k) {
-                        const int e = e1 + k * NTR, a = e / RB, r2 = e - a * RB;
-                        vn[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
-                    }
-                }
+            if constexpr (KB >= 3) {
+                double v[LB], vn[LB];
 #pragma unroll
                 for (int k = 0; k < LB; ++k) {
-                    const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
-                    if (e < tot) Vs[a * VS + r2] = f32_rn_i(v[k]);
+                    const int e = threadIdx.x + k * NTR, a = e / RB, r2 = e - a * RB;
+                    v[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
                 }
+                for (int e0 = threadIdx.x; e0 < tot; e0 += LB * NTR) {
+                    const int e1 = e0 + LB * NTR;
+                    if (e1 < tot) {
 #pragma unroll
-                for (int k = 0; k < LB; ++k) v[k] = vn[k];
+                        for (int k = 0; k < LB; ++k) {
+                            const int e = e1 + k * NTR, a = e / RB, r2 = e - a * RB;
+                            vn[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) {
+                        const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
+                        if (e < tot) Vs[a * VS + r2] = f32_rn_i(v[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) v[k] = vn[k];
+                }
+            } else {
+                for (int e0 = threadIdx.x; e0 < tot; e0 += LB * NTR) {
+                    double v[LB];
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) {
+                        const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
+                        v[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) {
+                        const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
+                        if (e < tot) Vs[a * VS + r2] = f32_rn_i(v[k]);
+                    }
+                }
             }
             for (int e = threadIdx.x; e < RP * RB; e += NTR) {
                 const int c = e / RB, r2 = e - c * RB;
