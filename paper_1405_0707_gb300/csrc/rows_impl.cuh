@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                 const float s2 = pr + t;
                 yl[c] = t - (s2 - pr);
                 yh[c] = s2;
-                y[c] = (double)yh[c] + (double)yl[c];
+                y[c] = f64_of_f32_i(yh[c]) + f64_of_f32_i(yl[c]);
             }
         } else if (subst) {
             // forward substitution y R = w (R upper triangular)
@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                 float s = 0.f;
 #pragma unroll
                 for (int a = 0; a <= c; ++a) s = fmaf(wf[a], Yf[a * RP + c], s);
-                y[c] = w[c] + (double)s;
+                y[c] = w[c] + f64_of_f32_i(s);
             }
         }
 #pragma unroll
@@ -1031,7 +1031,7 @@ __global__ void __launch_bounds__(NTR) k_update_z_rows(double* __restrict__ V, i
                 for (int c = 0; c < RP; ++c) df_fma(sh[c], sl[c], vh, vl, wh[a * RP + c], wl[a * RP + c]);
             }
 #pragma unroll
-            for (int c = 0; c < RP; ++c) z[c] = (double)sh[c] + (double)sl[c];
+            for (int c = 0; c < RP; ++c) z[c] = f64_of_f32_i(sh[c]) + f64_of_f32_i(sl[c]);
         } else {
 #pragma unroll
             for (int c = 0; c < RP; ++c) z[c] = 0.0;
@@ -1279,7 +1279,7 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
                 const int c = c0 + q;
                 float wf = 0.f, wh = 0.f, wl = 0.f;
                 if (ok && c < p) {
-                    const double w = W[(int64_t)c * ldw + r] - ((double)sh[q] + (double)sl[q]);
+                    const double w = W[(int64_t)c * ldw + r] - (f64_of_f32_i(sh[q]) + f64_of_f32_i(sl[q]));
                     W[(int64_t)c * ldw + r] = w;
                     wf = f32_rn_i(w);
                     if (ng) split_df_i(w, wh, wl);
