@@ -67,7 +67,22 @@ typedef enum {
      * and T negative definite, certified either by a_0 + 2 sum_k |a_k| < 0 (compensated sum)
      * or, for bw <= 4096, by a bound of the symbol's largest value a_0 + 2 sum_k a_k cos(k theta)
      * (grid plus Bernstein's inequality) below 0. */
-    EXPM_OP_TOEPLITZ_SYM = 1
+    EXPM_OP_TOEPLITZ_SYM = 1,
+    /* t * A, A a general real n x n sparse matrix in CSR form (host arrays, copied at plan
+     * creation; column indices need not be sorted).  The Krylov operator of Algorithm 1 is
+     * the sparse product; Algorithm 2's (tA)^{-1} is applied INEXACTLY by an inner iterative
+     * solve, the alternative Section 4.1 names for matrices too large for a direct solver:
+     * BiCGStab with the Jacobi preconditioner on every column of the block at once, to the
+     * relative residual opts.inner_tol.  Theorem 4.3 bounds what the inexact inverse costs:
+     *   ||X_i - X~_i|| / ||X_i|| <~ kappa(A) ||(I - tau_i A^{-1})^{-1}|| ||A~^{-1} - A^{-1}|| / ||A^{-1}||,
+     * so inner_tol must sit below the wanted accuracy by about kappa(A).  Requires every
+     * diagonal entry negative and every row weakly diagonally dominant,
+     * sum_{j != i} |a_ij| <= |a_ii| (a Gershgorin certificate that the spectrum of A lies in
+     * the closed left half-plane, where the CF approximation of Section 2 applies, and that
+     * the Jacobi-preconditioned inner solve is well posed).  Restart cycles of these plans are
+     * not captured as CUDA graphs (the inner solve's stop test reads residual norms on the
+     * host), and certify mode, the adjoint and the one-graph batch do not take them. */
+    EXPM_OP_CSR = 2
 } expm_op_kind;
 
 typedef struct {
@@ -79,6 +94,9 @@ typedef struct {
     int64_t n;             /* TOEPLITZ_SYM: order n >= 2                             */
     const double* toeplitz_col; /* TOEPLITZ_SYM: host, a_0 .. a_bw (read at plan creation) */
     int64_t toeplitz_bw;   /* TOEPLITZ_SYM: bandwidth, 0 <= bw <= n - 1              */
+    const int64_t* csr_rowptr;  /* CSR: host, n + 1 offsets, rowptr[0] = 0, nondecreasing */
+    const int32_t* csr_colind;  /* CSR: host, rowptr[n] column indices in [0, n)          */
+    const double*  csr_val;     /* CSR: host, rowptr[n] values (n from the field n)       */
 } expm_op_desc;
 
 typedef enum {
@@ -137,6 +155,9 @@ typedef struct {
     int32_t cgs_ctas_per_sm;  /* ... of the first Gram-Schmidt pass: 1..8; 0 = twice
                                  row_ctas_per_sm.  Both are what the autotuner of the
                                  Python package chooses per problem class.             */
+    double  inner_tol;     /* CSR operators, Algorithm 2: relative residual of the inner
+                              solve of A y = v, per column; 0 = 1e-12                  */
+    int32_t inner_maxit;   /* ... and its iteration cap per application; 0 = 2000      */
 } expm_opts;
 
 #define EXPM_MAX_POLES 16
@@ -155,6 +176,8 @@ typedef struct {
     double  normA_bound;         /* Gershgorin bound of ||tA|| used by AUTO          */
     double  true_resid[EXPM_MAX_POLES]; /* certify: ||B - (tA - tau_i I) X_i||_F in FP64 */
     int32_t kept;                /* deflated restart: Ritz vectors kept at the last restart */
+    int64_t inner_iters;         /* CSR operators: inner solver iterations, summed over the
+                                    block applications of the call                      */
 } expm_info;
 
 typedef struct expm_plan_s expm_plan;

@@ -22,6 +22,7 @@ EXPM_TIMEOUT = 8
 EXPM_AUTO_RATIO = 36.0     # the AUTO rule's ratio (include/expm_block.h)
 EXPM_OP_CONV_DIFF = 0
 EXPM_OP_TOEPLITZ_SYM = 1
+EXPM_OP_CSR = 2
 EXPM_PREC_FP64 = 0
 EXPM_PREC_MIXED = 1
 EXPM_ALG_AUTO = 0
@@ -42,14 +43,17 @@ STAGES = ("gemm", "tridiag", "cgs", "reduce", "qr", "poles", "update", "other", 
 class expm_op_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("ndim", C.c_int32), ("side", C.c_int32 * 3),
                 ("diff", C.c_double), ("vel", C.c_double * 3), ("n", C.c_int64),
-                ("toeplitz_col", C.POINTER(C.c_double)), ("toeplitz_bw", C.c_int64)]
+                ("toeplitz_col", C.POINTER(C.c_double)), ("toeplitz_bw", C.c_int64),
+                ("csr_rowptr", C.POINTER(C.c_int64)), ("csr_colind", C.POINTER(C.c_int32)),
+                ("csr_val", C.POINTER(C.c_double))]
 
 
 class expm_opts(C.Structure):
     _fields_ = [("m", C.c_int32), ("max_cycles", C.c_int32), ("tol", C.c_double),
                 ("precision", C.c_int32), ("fixed_cycles", C.c_int32), ("algorithm", C.c_int32),
                 ("certify", C.c_int32), ("nu_cf", C.c_int32), ("k_defl", C.c_int32),
-                ("row_ctas_per_sm", C.c_int32), ("cgs_ctas_per_sm", C.c_int32)]
+                ("row_ctas_per_sm", C.c_int32), ("cgs_ctas_per_sm", C.c_int32),
+                ("inner_tol", C.c_double), ("inner_maxit", C.c_int32)]
 
 
 class expm_info(C.Structure):
@@ -57,7 +61,8 @@ class expm_info(C.Structure):
                 ("converged", C.c_int32), ("breakdown", C.c_int32), ("npoles", C.c_int32),
                 ("resid", C.c_double * EXPM_MAX_POLES), ("normB", C.c_double),
                 ("algorithm", C.c_int32), ("normA_bound", C.c_double),
-                ("true_resid", C.c_double * EXPM_MAX_POLES), ("kept", C.c_int32)]
+                ("true_resid", C.c_double * EXPM_MAX_POLES), ("kept", C.c_int32),
+                ("inner_iters", C.c_int64)]
 
 
 _lib = None

@@ -39,7 +39,7 @@ class Plan:
 
     def __init__(self, sides, diff, vel, p_max, m=10, tol=1e-10, max_cycles=200,
                  fixed_cycles=0, stream=None, algorithm=0, precision="fp64", certify=False, nu=0,
-                 k_defl=0, row_ctas=0, cgs_ctas=0, _op=None):
+                 k_defl=0, row_ctas=0, cgs_ctas=0, inner_tol=0.0, inner_maxit=0, _op=None):
         import torch
         if _op is None:
             sides = tuple(int(s) for s in sides)
@@ -65,6 +65,8 @@ class Plan:
         opts.k_defl = int(k_defl)              # 0: plain restart
         opts.row_ctas_per_sm = int(row_ctas)   # launch shape (0: library defaults; see autotune)
         opts.cgs_ctas_per_sm = int(cgs_ctas)
+        opts.inner_tol = float(inner_tol)      # CSR operators: inner solve (0: library default)
+        opts.inner_maxit = int(inner_maxit)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
         self.tol, self.max_cycles, self.algorithm, self.precision = tol, max_cycles, algorithm, precision
@@ -92,6 +94,34 @@ class Plan:
         op.toeplitz_bw = len(a) - 1
         plan = cls(None, 0.0, None, p_max, _op=op, **kw)
         plan.toeplitz_col = a
+        return plan
+
+    @classmethod
+    def csr(cls, A, p_max, **kw):
+        """Plan for t A, A a general sparse n x n matrix (anything scipy.sparse.csr_matrix
+        accepts), whose diagonal is negative and whose rows are weakly diagonally dominant.
+        Algorithm 2 applies (tA)^{-1} inexactly by an inner iterative solve (inner_tol,
+        inner_maxit)."""
+        import numpy as np
+        import scipy.sparse as sp
+        M = sp.csr_matrix(A)
+        n = M.shape[0]
+        if M.shape != (n, n):
+            raise ValueError("A must be square")
+        rowptr = np.ascontiguousarray(M.indptr, dtype=np.int64)
+        colind = np.ascontiguousarray(M.indices, dtype=np.int32)
+        val = np.ascontiguousarray(M.data, dtype=np.float64)
+        op = N.expm_op_desc()
+        op.kind = N.EXPM_OP_CSR
+        op.ndim = 1
+        for d in range(3):
+            op.side[d] = 1
+        op.n = int(n)
+        op.csr_rowptr = rowptr.ctypes.data_as(C.POINTER(C.c_int64))
+        op.csr_colind = colind.ctypes.data_as(C.POINTER(C.c_int32))
+        op.csr_val = val.ctypes.data_as(C.POINTER(C.c_double))
+        plan = cls(None, 0.0, None, p_max, _op=op, **kw)
+        plan.csr_arrays = (rowptr, colind, val)
         return plan
 
     def close(self):

@@ -278,6 +278,10 @@ expm_status toeplitz_inverse(expm_plan* P, double t, const double* V, int64_t ld
 expm_status op_apply_internal(expm_plan* P, double t, const double* V, int64_t ldv, int p, double* W,
                               int64_t ldw) {
     if (P->toeplitz) return toeplitz_matvec(P, t, V, ldv, p, W, ldw, EXPM_STAGE_STENCIL);
+    if (P->csr) {
+        LAUNCH(EXPM_STAGE_STENCIL, launch_csr_spmm(P->cs, t, V, ldv, p, W, ldw, P->stream));
+        return EXPM_OK;
+    }
     LAUNCH(EXPM_STAGE_STENCIL, launch_cd_apply(V, ldv, W, ldw, p, P->ndim, P->ax[0].N, P->ax[1].N, P->ax[2].N,
                                                P->ax, t, P->stream, nullptr, 0, 0.0, nullptr, P->stencil_df & 1));
     return EXPM_OK;
@@ -289,6 +293,17 @@ expm_status prec_apply_internal(expm_plan* P, double t, const double* V, int64_t
     if (P->toeplitz) {
         if (!P->tz.gsf) return EXPM_INVALID_ARG;
         return toeplitz_inverse(P, t, V, ldv, p, W, ldw, EXPM_STAGE_GEMM);
+    }
+    if (P->csr) {
+        // the inexact inverse of Section 4.1 (inner BiCGStab to opts.inner_tol, k_csr.cu);
+        // its stop test synchronises the stream, so these plans run without cycle graphs
+        int iters = 0, conv = 0;
+        const double eta = P->opts.inner_tol > 0.0 ? P->opts.inner_tol : 1e-12;
+        const int maxit = P->opts.inner_maxit > 0 ? P->opts.inner_maxit : 2000;
+        ++P->launches;
+        CK(csr_inverse(P->cs, t, V, ldv, p, W, ldw, eta, maxit, s, &iters, &conv));
+        P->inner_iters += iters;
+        return conv ? EXPM_OK : EXPM_NOT_CONVERGED;
     }
     if (P->opts.precision == EXPM_PREC_MIXED && P->ndim > 1) return prec_apply_mixed(P, t, V, ldv, p, W, ldw);
     const double inv_t = 1.0 / t;
@@ -391,6 +406,7 @@ expm_status validate_block_args(expm_plan* P, double t, const void* B, int64_t l
 // Gershgorin bound of ||tA||_inf for the convection-diffusion operator.
 double norm_bound(const expm_plan* P, double t) {
     if (P->toeplitz) return t * P->tz.abs_rowsum;
+    if (P->csr) return t * P->cs.abs_rowsum;
     double s = 0.0;
     for (int d = 0; d < P->ndim; ++d) s += std::fabs(P->ax[d].l) + std::fabs(P->ax[d].c) + std::fabs(P->ax[d].u);
     return t * s;
@@ -688,6 +704,7 @@ expm_status run_finish(expm_plan* P, RunState& r, expm_info* info) {
         info->normA_bound = norm_bound(P, r.t);
         for (int i = 0; i < P->npoles; ++i) info->true_resid[i] = true_res[i];
         info->kept = r.kk;
+        info->inner_iters = P->inner_iters;
         // block applications of the operator: a deflated cycle starts at block kk / p
         info->block_steps = r.steps;
         info->matvecs = (int64_t)r.steps * p;
@@ -706,6 +723,7 @@ expm_status run_block(expm_plan* P, double t, const double* dB, int64_t ldb, int
     r.p = p;
     r.dZ = dZ;
     r.ldz = ldz;
+    P->inner_iters = 0;
     expm_status st = run_begin(P, r);
     if (st != EXPM_OK) return st;
     while (!r.done) {
@@ -743,6 +761,15 @@ void free_plan(expm_plan* P) {
     cudaFree(P->Zst);
     cudaFree(P->Xcert);
     cudaFree(P->Acert);
+    cudaFree(P->cs.rowptr);
+    cudaFree(P->cs.colind);
+    cudaFree(P->cs.val);
+    cudaFree(P->cs.dinv);
+    cudaFree(P->cs.work);
+    cudaFree(P->cs.part);
+    cudaFree(P->cs.frz);
+    cudaFree(P->cs.norms);
+    if (P->cs.hnorms) cudaFreeHost(P->cs.hnorms);
     cudaFree(P->tz.col);
     cudaFree(P->tz.tw1);
     cudaFree(P->tz.tw2);
@@ -813,6 +840,38 @@ double toeplitz_symbol_max_bound(const double* a, int64_t bw, double abs_rowsum)
         if (mx >= 0.0 || bound < 0.0 || 4 * M * bw > 1000000000) break;
     }
     return bound;
+}
+
+// A general sparse operator's descriptor: the CSR structure (offsets from 0, nondecreasing,
+// column indices in range, finite values) and the Gershgorin certificate of the operator
+// kind's contract: every diagonal entry negative (duplicates summed) and every row weakly
+// diagonally dominant, so the spectrum lies in the closed left half-plane.  abs_rowsum:
+// max_i sum_j |a_ij|, the bound of ||A||_inf behind AUTO.
+expm_status csr_validate(const expm_op_desc* op, double* abs_rowsum) {
+    const int64_t n = op->n;
+    if (n < 1 || n > INT32_MAX || !op->csr_rowptr) return EXPM_INVALID_ARG;
+    const int64_t* rp = op->csr_rowptr;
+    if (rp[0] != 0) return EXPM_INVALID_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return EXPM_INVALID_ARG;
+    const int64_t nnz = rp[n];
+    if (nnz > 0 && (!op->csr_colind || !op->csr_val)) return EXPM_INVALID_ARG;
+    double mx = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double dg = 0.0, off = 0.0, tot = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int64_t j = op->csr_colind[k];
+            const double a = op->csr_val[k];
+            if (j < 0 || j >= n || !std::isfinite(a)) return EXPM_INVALID_ARG;
+            if (j == i) dg += a;
+            else off += std::fabs(a);
+            tot += std::fabs(a);
+        }
+        if (!(dg < 0.0) || off > -dg * (1.0 + 1e-12)) return EXPM_INVALID_ARG;
+        mx = std::max(mx, tot);
+    }
+    *abs_rowsum = mx;
+    return EXPM_OK;
 }
 
 expm_status toeplitz_validate(const expm_op_desc* op, double* abs_rowsum) {
@@ -1165,10 +1224,15 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     if (!op || !opts || !out) return EXPM_INVALID_ARG;
     *out = nullptr;
     const bool toeplitz = op->kind == EXPM_OP_TOEPLITZ_SYM;
+    const bool csr = op->kind == EXPM_OP_CSR;
     double abs_rowsum = 0.0;
     if (toeplitz) {
         const expm_status vs = toeplitz_validate(op, &abs_rowsum);
         if (vs != EXPM_OK) return vs;
+    } else if (csr) {
+        const expm_status vs = csr_validate(op, &abs_rowsum);
+        if (vs != EXPM_OK) return vs;
+        if (opts->certify) return EXPM_INVALID_ARG;
     } else {
         if (op->kind != EXPM_OP_CONV_DIFF) return EXPM_INVALID_ARG;
         if (op->ndim < 1 || op->ndim > 3) return EXPM_INVALID_ARG;
@@ -1195,14 +1259,18 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     if (!P) return EXPM_NO_MEMORY;
     P->op = *op;
     P->op.toeplitz_col = nullptr;   // host memory of the caller: not kept
+    P->op.csr_rowptr = nullptr;
+    P->op.csr_colind = nullptr;
+    P->op.csr_val = nullptr;
     P->opts = *opts;
     P->toeplitz = toeplitz;
-    P->ndim = toeplitz ? 1 : op->ndim;
+    P->csr = csr;
+    P->ndim = (toeplitz || csr) ? 1 : op->ndim;
     P->p_max = p_max;
     P->stream = reinterpret_cast<cudaStream_t>(stream);
     {
         const char* ng = std::getenv("EXPM_DISABLE_GRAPHS");   // debugging switch
-        P->use_graphs = !(ng && ng[0] == '1');
+        P->use_graphs = !(ng && ng[0] == '1') && !csr;
         // test switch: "0" keeps the mixed path on the three-pass FP32 Cholesky-QR for every
         // block (the fallback of the single accurate pass)
         const char* sq = std::getenv("EXPM_QR_SINGLE_PASS");
@@ -1231,6 +1299,11 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         P->tz.n = op->n;
         P->tz.bw = op->toeplitz_bw;
         P->tz.abs_rowsum = abs_rowsum;
+    } else if (csr) {
+        n = op->n;
+        P->cs.n = op->n;
+        P->cs.nnz = op->csr_rowptr[op->n];
+        P->cs.abs_rowsum = abs_rowsum;
     } else {
         for (int d = 0; d < 3; ++d) {
             Axis& a = P->ax[d];
@@ -1328,7 +1401,19 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         ok = ok && cudaMallocHost(reinterpret_cast<void**>(&P->hHnew), sizeof(double) * (size_t)P->ldH * kd) == cudaSuccess;
     }
     const bool mixed = opts->precision == EXPM_PREC_MIXED;
-    if (!toeplitz) {
+    if (csr) {
+        CsrOp& c = P->cs;
+        c.ld = ld;
+        c.pmax = p_max;
+        const size_t nb = (size_t)csr_blocks(n);
+        ok = ok && cudaMalloc(reinterpret_cast<void**>(&c.rowptr), sizeof(int64_t) * (size_t)(n + 1)) == cudaSuccess;
+        ok = ok && cudaMalloc(reinterpret_cast<void**>(&c.colind), sizeof(int) * (size_t)std::max<int64_t>(c.nnz, 1)) == cudaSuccess;
+        ok = ok && dalloc(&c.val, (size_t)std::max<int64_t>(c.nnz, 1)) && dalloc(&c.dinv, (size_t)n);
+        ok = ok && dalloc(&c.work, (size_t)9 * ld * p_max) && dalloc(&c.part, 7 * nb * p_max);
+        ok = ok && cudaMalloc(reinterpret_cast<void**>(&c.frz), sizeof(int) * (size_t)p_max) == cudaSuccess;
+        ok = ok && dalloc(&c.norms, 2 * (size_t)p_max);
+        ok = ok && cudaMallocHost(reinterpret_cast<void**>(&c.hnorms), sizeof(double) * 2 * (size_t)p_max) == cudaSuccess;
+    } else if (!toeplitz) {
         // preconditioner tables: every axis but x is transformed
         int64_t nmodes = 1;
         for (int d = 1; d < P->ndim; ++d) {
@@ -1358,7 +1443,14 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     cudaStream_t s = P->stream;
     bool cuda_ok = krylov_set_smem_limits() == cudaSuccess && poles_set_smem_limits() == cudaSuccess &&
                    operator_set_smem_limits() == cudaSuccess && cgs_tc_set_smem_limits() == cudaSuccess;
-    if (!toeplitz) {
+    if (csr && cuda_ok) {
+        CsrOp& c = P->cs;
+        cuda_ok = cudaMemcpyAsync(c.rowptr, op->csr_rowptr, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                  (c.nnz == 0 || (cudaMemcpyAsync(c.colind, op->csr_colind, sizeof(int) * (size_t)c.nnz, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                                  cudaMemcpyAsync(c.val, op->csr_val, sizeof(double) * (size_t)c.nnz, cudaMemcpyHostToDevice, s) == cudaSuccess)) &&
+                  launch_csr_dinv(c, s) == cudaSuccess;
+    }
+    if (!toeplitz && !csr) {
         const int64_t nmodes = P->nmodes;
         for (int d = 1; d < P->ndim && cuda_ok; ++d)
             cuda_ok = launch_axis_setup(P->Qf[d], P->Qi[d], P->lam[d], P->ax[d].N, P->ax[d].l,
@@ -1577,7 +1669,7 @@ expm_status expm_batch_create(expm_plan* const* plans, int count, const double* 
         const expm_plan* P = plans[i];
         // the device-side loop needs no host work between cycles: no deflated restart (host
         // eigenproblem), no certify accumulation, a capturable stream
-        if (P->opts.k_defl > 0 || P->opts.certify || !P->stream) return EXPM_INVALID_ARG;
+        if (P->opts.k_defl > 0 || P->opts.certify || P->csr || !P->stream) return EXPM_INVALID_ARG;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return EXPM_INVALID_ARG;
     }
@@ -1718,6 +1810,7 @@ expm_status expm_block_adjoint(expm_plan* plan, double t, const double* dG, int6
                                          dGB ? ldgb : ldz);
     if (st != EXPM_OK) return st;
     if (hGt && (ldz < plan->n || dZ == dGB)) return EXPM_INVALID_ARG;
+    if (plan->csr) return EXPM_INVALID_ARG;   // the adjoint needs A^T's plan (stencils, Toeplitz)
     expm_plan* P = plan;
     cudaStream_t s = P->stream;
     const int64_t n = P->n, ld = P->ld;

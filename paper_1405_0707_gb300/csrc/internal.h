@@ -126,6 +126,23 @@ struct ToeplitzOp {
     bool gsf = false;           // inverse available
 };
 
+// A general sparse operator (EXPM_OP_CSR): the matrix on the device, its inverted diagonal
+// (the inner solve's Jacobi preconditioner) and the inner solver's workspace.
+struct CsrOp {
+    int64_t n = 0, nnz = 0, ld = 0;
+    int pmax = 0;
+    int64_t* rowptr = nullptr;
+    int* colind = nullptr;
+    double* val = nullptr;
+    double* dinv = nullptr;
+    double abs_rowsum = 0.0;    // max_i sum_j |a_ij| (bound of ||A||_inf)
+    double* work = nullptr;     // 9 x ld x pmax: the inner solver's vectors
+    double* part = nullptr;     // 7 x csr_blocks(n) x pmax partial sums
+    int* frz = nullptr;         // pmax
+    double* norms = nullptr;    // 2 pmax: squared residual and right-hand-side norms
+    double* hnorms = nullptr;   // pinned host mirror of norms
+};
+
 }  // namespace expm
 
 struct GraphEntry {
@@ -144,6 +161,9 @@ struct expm_plan_s {
     expm::Axis ax[3];
     bool toeplitz = false;     // EXPM_OP_TOEPLITZ_SYM
     expm::ToeplitzOp tz;
+    bool csr = false;          // EXPM_OP_CSR
+    expm::CsrOp cs;
+    int64_t inner_iters = 0;   // CSR: inner solver iterations of the current call
     int64_t n = 0, ld = 0;
     int p_max = 0;
     cudaStream_t stream = nullptr;
@@ -225,6 +245,13 @@ struct expm_plan_s {
 
 // ---------------------------------------------------------------- launchers
 namespace expm {
+// general sparse operators (k_csr.cu)
+int csr_blocks(int64_t n);
+cudaError_t launch_csr_spmm(const CsrOp& a, double alpha, const double* X, int64_t ldx, int p, double* Y,
+                            int64_t ldy, cudaStream_t s);
+cudaError_t launch_csr_dinv(CsrOp& a, cudaStream_t s);
+cudaError_t csr_inverse(const CsrOp& a, double t, const double* V, int64_t ldv, int p, double* W, int64_t ldw,
+                        double eta, int maxit, cudaStream_t s, int* iters, int* converged);
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_tridiag_lines(const double* in, int64_t ld_in, double* out, int64_t ld_out,
                                  int p, int L, int64_t nmodes, double l_sub, const double* th_m,

@@ -105,6 +105,34 @@ def grad_target(n, p, seed, t):
     return t0, B0
 
 
+def sparse_dd_matrix(n, nnz_row=8, seed=SEED_BASE + 9, margin=(0.05, 0.5), scale=1.0e4):
+    """A seeded nonsymmetric sparse n x n matrix for the general sparse operator: nnz_row - 1
+    off-diagonal entries per row at random columns (N(0, 1) values), and a negative diagonal
+    exceeding the row's off-diagonal magnitude by a factor 1 + U(margin), all times `scale`
+    (rows weakly diagonally dominant with a negative diagonal, the operator's contract).
+    Returns (indptr, indices, data) of the CSR form, column indices sorted within a row."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    k = max(0, nnz_row - 1)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        js = rng.choice(n - 1, size=min(k, n - 1), replace=False)
+        js = np.where(js >= i, js + 1, js)                      # off-diagonal columns
+        v = rng.standard_normal(len(js))
+        d = -(np.abs(v).sum() + 1e-3) * (1.0 + rng.uniform(*margin))
+        js = np.concatenate([js, [i]])
+        v = np.concatenate([v, [d]])
+        order = np.argsort(js)
+        rows.append(np.full(len(js), i))
+        cols.append(js[order])
+        vals.append(v[order] * scale)
+    indices = np.concatenate(cols).astype(np.int32)
+    data = np.concatenate(vals)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    indptr[1:] = np.cumsum([len(c) for c in cols])
+    return indptr, indices, data
+
+
 def rhs(n, p, seed):
     """B (n x p), i.i.d. N(0, 1), returned as a Fortran-ordered (column-major) array."""
     rng = np.random.Generator(np.random.PCG64(seed))

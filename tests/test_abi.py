@@ -95,6 +95,56 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.expm_status_str(N.EXPM_BREAKDOWN) == b"block Arnoldi breakdown"
 
 
+def test_csr_descriptor_checks(lib):
+    """General sparse descriptors are validated on the host before any device work: the CSR
+    structure, finite values, and the Gershgorin certificate of the operator's contract (a
+    negative diagonal, weakly diagonally dominant rows).  Every case below is rejected."""
+    import ctypes as C
+    from paper_1405_0707_gb300 import _native as N
+    from paper_1405_0707_gb300 import inputs
+    n = 40
+    ip0, ix0, d0 = inputs.sparse_dd_matrix(n, nnz_row=5, seed=3)
+    opts = N.expm_opts()
+    opts.m, opts.max_cycles, opts.tol, opts.precision = 4, 10, 1e-10, 0
+    out = C.c_void_p()
+
+    def create(ip, ix, d, nn=n, certify=0):
+        op = N.expm_op_desc()
+        op.kind, op.ndim, op.n = N.EXPM_OP_CSR, 1, nn
+        for k in range(3):
+            op.side[k] = 1
+        ip = np.ascontiguousarray(ip, dtype=np.int64)
+        ix = np.ascontiguousarray(ix, dtype=np.int32)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        op.csr_rowptr = ip.ctypes.data_as(C.POINTER(C.c_int64))
+        op.csr_colind = ix.ctypes.data_as(C.POINTER(C.c_int32))
+        op.csr_val = d.ctypes.data_as(C.POINTER(C.c_double))
+        opts.certify = certify
+        return lib.expm_plan_create(C.byref(op), 2, C.byref(opts), None, C.byref(out))
+
+    diag = ix0 == np.repeat(np.arange(n), np.diff(ip0))
+    bad = d0.copy()
+    bad[np.flatnonzero(diag)[3]] *= 0.3            # row 3 no longer diagonally dominant
+    assert create(ip0, ix0, bad) == N.EXPM_INVALID_ARG
+    bad = d0.copy()
+    bad[np.flatnonzero(diag)[7]] *= -1.0           # positive diagonal entry
+    assert create(ip0, ix0, bad) == N.EXPM_INVALID_ARG
+    bad = d0.copy()
+    bad[5] = np.nan
+    assert create(ip0, ix0, bad) == N.EXPM_INVALID_ARG
+    bix = ix0.copy()
+    bix[9] = n                                     # column index out of range
+    assert create(ip0, bix, d0) == N.EXPM_INVALID_ARG
+    bip = ip0.copy()
+    bip[10], bip[11] = bip[11], bip[10]            # decreasing offsets
+    assert create(bip, ix0, d0) == N.EXPM_INVALID_ARG
+    bip = ip0.copy()
+    bip[0] = 1
+    assert create(bip, ix0, d0) == N.EXPM_INVALID_ARG
+    assert create(ip0, ix0, d0, nn=0) == N.EXPM_INVALID_ARG
+    assert create(ip0, ix0, d0, certify=1) == N.EXPM_INVALID_ARG   # certify mode takes no CSR
+
+
 def test_toeplitz_descriptor_checks():
     """Toeplitz descriptors are validated on the host before any device work (Example 5.4's
     operator must be symmetric negative definite): every case below is rejected."""
