@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                 const float s2 = pr + t;
                 yl[c] = t - (s2 - pr);
                 yh[c] = s2;
-                y[c] = f64_of_f32_i(yh[c]) + f64_of_f32_i(yl[c]);
+                y[c] = (double)yh[c] + (double)yl[c];
             }
         } else if (subst) {
             // forward substitution y R = w (R upper triangular)
@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
                 float s = 0.f;
 #pragma unroll
                 for (int a = 0; a <= c; ++a) s = fmaf(wf[a], Yf[a * RP + c], s);
-                y[c] = w[c] + f64_of_f32_i(s);
+                y[c] = w[c] + (double)s;
             }
         }
 #pragma unroll
