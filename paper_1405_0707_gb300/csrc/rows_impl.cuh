@@ -1082,29 +1082,9 @@ constexpr int KG = (RG + NTR - 1) / NTR;    // Gram entries (upper triangle) per
 
 __host__ __device__ constexpr int cgs_nblk(int cols, int p) { return ((cols + 1) / 2) * ((p + 3) / 4); }
 
-// the projection (not upd) also holds the raw FP64 chunk of V that the asynchronous copies
-// fill while the previous chunk is projected: cols x RB doubles after the float arrays
-__host__ __device__ constexpr size_t cgs_rows_raw_off(int cols, bool upd, int ng) {
-    return ((sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS4 + (size_t)((cols + 1) & ~1) * VS +
-                              (ng ? 2 * (size_t)RB * WG : 0))) + 15) / 16 * 16;
-}
 __host__ __device__ constexpr size_t cgs_rows_smem(int cols, bool upd, int ng) {
-    return cgs_rows_raw_off(cols, upd, ng) + (upd ? 0 : sizeof(double) * (size_t)cols * RB);
-}
-
-// asynchronous copies (cp.async, 16 bytes, zero-filled past src_bytes) of one chunk of V
-// (rows r0 .. r0 + tr - 1 of every basis column) into the raw buffer, one commit group
-__device__ __forceinline__ void cgs_issue_chunk(double* raw, const double* __restrict__ V, int64_t ldv, int cols,
-                                                int64_t r0, int tr) {
-    const int per = RB / 2;
-    for (int e = threadIdx.x; e < cols * per; e += NTR) {
-        const int a = e / per, r2 = 2 * (e - a * per);
-        const int nb = r2 < tr ? (r2 + 1 < tr ? 16 : 8) : 0;
-        const double* src = nb ? V + (int64_t)a * ldv + r0 + r2 : V;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + a * RB + r2);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(nb) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    return sizeof(float) * ((upd ? 2 * (size_t)cols * RP : 0) + (size_t)RB * WS4 + (size_t)((cols + 1) & ~1) * VS +
+                            (ng ? 2 * (size_t)RB * WG : 0));
 }
 
 // The projection blocks of one chunk: block b = ab ncb + cb covers basis columns 2ab, 2ab + 1
@@ -1210,8 +1190,6 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
     float* Vs = Wf + RB * WS4;                         // ((cols + 1) & ~1) x VS
     float* Wh = Vs + ((cols + 1) & ~1) * VS;           // ng: W as float pairs, RB x WG each
     float* Wl = Wh + RB * WG;
-    double* raw = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(smf) +
-                                            cgs_rows_raw_off(cols, UPD, GR ? ng : 0));   // !UPD: cols x RB
     if (UPD) {
         for (int e = threadIdx.x; e < cols * RP; e += NTR) {
             const int a = e / RP, c = e - a * RP;
@@ -1249,7 +1227,6 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
     }
     const int rr = threadIdx.x >> 1, hf = threadIdx.x & 1, c0 = hf * HP;
     const int64_t rb = rows_begin(rpb), re = min(n, rb + rpb);
-    if (!UPD && rb < re) cgs_issue_chunk(raw, V, ldv, cols, rb, (int)min((int64_t)RB, re - rb));
     for (int64_t r0 = rb; r0 < re; r0 += RB) {
         const int tr = (int)min((int64_t)RB, re - r0);
         if (UPD) {
@@ -1315,13 +1292,49 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             }
         } else {
             __syncthreads();                           // previous chunk consumed
-            // the chunk's V arrived in raw by asynchronous copies, issued while the previous
-            // chunk was projected: convert it to the FP32 copy (rows past the chunk are zero)
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncthreads();
-            for (int e = threadIdx.x; e < cols * RB; e += NTR) {
-                const int a = e / RB, r2 = e - a * RB;
-                Vs[a * VS + r2] = r2 < tr ? f32_rn_i(raw[e]) : 0.f;
+            // batches of LB loads per thread.  With many basis columns (KB >= 3) the next batch
+            // is issued before the current one is converted and stored, so two batches are in
+            // flight (measured faster at 160 columns, 96^3; slower with few columns, where the
+            // extra registers cost a resident CTA)
+            const int tot = cols * RB;
+            if constexpr (KB >= 3) {
+                double v[LB], vn[LB];
+#pragma unroll
+                for (int k = 0; k < LB; ++k) {
+                    const int e = threadIdx.x + k * NTR, a = e / RB, r2 = e - a * RB;
+                    v[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+                }
+                for (int e0 = threadIdx.x; e0 < tot; e0 += LB * NTR) {
+                    const int e1 = e0 + LB * NTR;
+                    if (e1 < tot) {
+#pragma unroll
+                        for (int k = 0; k < LB; ++k) {
+                            const int e = e1 + k * NTR, a = e / RB, r2 = e - a * RB;
+                            vn[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) {
+                        const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
+                        if (e < tot) Vs[a * VS + r2] = f32_rn_i(v[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) v[k] = vn[k];
+                }
+            } else {
+                for (int e0 = threadIdx.x; e0 < tot; e0 += LB * NTR) {
+                    double v[LB];
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) {
+                        const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
+                        v[k] = (e < tot && r2 < tr) ? V[(int64_t)a * ldv + r0 + r2] : 0.0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < LB; ++k) {
+                        const int e = e0 + k * NTR, a = e / RB, r2 = e - a * RB;
+                        if (e < tot) Vs[a * VS + r2] = f32_rn_i(v[k]);
+                    }
+                }
             }
             for (int e = threadIdx.x; e < RP * RB; e += NTR) {
                 const int c = e / RB, r2 = e - c * RB;
@@ -1331,8 +1344,6 @@ __global__ void __launch_bounds__(NTR) k_cgs_rows(const double* __restrict__ V, 
             }
         }
         __syncthreads();
-        // the next chunk's copies run while this one is projected (raw is free again)
-        if (!UPD && r0 + RB < re) cgs_issue_chunk(raw, V, ldv, cols, r0 + RB, (int)min((int64_t)RB, re - r0 - RB));
         chunk_project<KB>(Vs, Wf, nblk, ncb, ah, al);
         if (ngu) chunk_gram(Wh, Wl, gi, gj, ngu, gh, gl);
     }

@@ -5,12 +5,10 @@
 // projection blocks per thread and the staged chunk fit.
 constexpr int kCgsRowsKMax = 5;
 constexpr size_t kCgsRowsSmemMax = 112 * 1024;
-constexpr size_t kCgsProjSmemMax = 220 * 1024;    // the projection with its raw FP64 chunk
 
 bool cgs_fit(int cols, int p) {
     if (p < 1 || p > RP || cols < 1) return false;
-    return (cgs_nblk(cols, p) + NTR - 1) / NTR <= kCgsRowsKMax && cgs_rows_smem(cols, true, p) <= kCgsRowsSmemMax &&
-           cgs_rows_smem(cols, false, p) <= kCgsProjSmemMax;
+    return (cgs_nblk(cols, p) + NTR - 1) / NTR <= kCgsRowsKMax && cgs_rows_smem(cols, true, p) <= kCgsRowsSmemMax;
 }
 
 cudaError_t cgs(int upd, const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p, int64_t n,
