@@ -82,7 +82,7 @@ def workload_n(w):
     if "n" in w:
         return int(w["n"])
     n = 1
-    for s_ in w["sides"]:
+    for s_ in w.get("sides", w.get("csr_sides", ())):
         n *= s_
     return n
 
@@ -241,6 +241,11 @@ def make_plan(w, precision, stream=None, **kw):
     args = dict(p_max=w["p"], m=w["m"], tol=w["tol"], max_cycles=400, stream=stream, precision=precision)
     args.update(kw)
     args.setdefault("k_defl", w.get("k_defl", 0))
+    if "csr_sides" in w:
+        import scipy.sparse as sp
+        ip, ix, dv = inputs.sparse_stencil_matrix(w["csr_sides"])
+        n = workload_n(w)
+        return Plan.csr(sp.csr_matrix((dv, ix, ip), shape=(n, n)), **args)
     if "frac" in w:
         return Plan.toeplitz(inputs.fractional_column(w["n"], w["frac"], w["d"]), w["n"], **args)
     if "n" in w:

@@ -37,6 +37,9 @@ WORKLOADS = {
     # one instance of the batched workload's largest class (96^3 grid, p = 16), for profiling
     "cd3d-96": dict(sides=(96, 96, 96), diff=1.0, vel=(1.0, -1.0, 0.5), t=(0.01,), p=16, m=10, tol=1e-10,
                     seed=SEED_BASE + 7),
+    # a general sparse operator of the same size: the 96^3 grid's 7-point pattern with random
+    # values (sparse_stencil_matrix), p = 16, for the sparse product and the inexact inverse
+    "csr3d-96": dict(csr_sides=(96, 96, 96), t=(0.2,), p=16, m=10, tol=1e-10, seed=SEED_BASE + 11),
     # the large-norm Toeplitz regime of Example 5.4 (||A|| ~ 2e10 at n = 2^17): beta = 1.8,
     # p = 2, m = 30 and k = 30 deflated Ritz vectors as in the paper; t = 0.01 (at the paper's
     # t = 1 the result is ~1e-13 ||B||, below the CF approximation's own error), tol 1e-10
@@ -131,6 +134,44 @@ def sparse_dd_matrix(n, nnz_row=8, seed=SEED_BASE + 9, margin=(0.05, 0.5), scale
     indptr = np.zeros(n + 1, dtype=np.int64)
     indptr[1:] = np.cumsum([len(c) for c in cols])
     return indptr, indices, data
+
+
+def sparse_stencil_matrix(sides, seed=SEED_BASE + 10, margin=(0.05, 0.5)):
+    """A seeded sparse matrix with the 2-D/3-D grid's 5/7-point pattern (neighbours along each
+    axis, x fastest, no wrap-around) but random N(0, 1) off-diagonal values, and a negative
+    diagonal exceeding the row's off-diagonal magnitude by a factor 1 + U(margin) (rows weakly
+    diagonally dominant with a negative diagonal, the general sparse operator's contract).
+    Returns (indptr, indices, data) of the CSR form, columns sorted within a row."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sides = tuple(int(s_) for s_ in sides)
+    n = int(np.prod(sides))
+    idx = np.arange(n, dtype=np.int64)
+    coords = []
+    rem = idx.copy()
+    for s_ in sides:
+        coords.append(rem % s_)
+        rem //= s_
+    rows, cols = [], []
+    stride = 1
+    for d, s_ in enumerate(sides):
+        for sgn in (-1, 1):
+            ok = (coords[d] + sgn >= 0) & (coords[d] + sgn < s_)
+            rows.append(idx[ok])
+            cols.append(idx[ok] + sgn * stride)
+        stride *= s_
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = rng.standard_normal(len(r))
+    off = np.bincount(r, weights=np.abs(v), minlength=n)
+    dg = -(off + 1e-3) * (1.0 + rng.uniform(*margin, size=n))
+    r = np.concatenate([r, idx])
+    c = np.concatenate([c, idx])
+    v = np.concatenate([v, dg])
+    order = np.lexsort((c, r))
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    indptr[1:] = np.cumsum(np.bincount(r, minlength=n))
+    return indptr, c[order].astype(np.int32), v[order]
 
 
 def rhs(n, p, seed):
