@@ -81,7 +81,8 @@ typedef enum {
      * the closed left half-plane, where the CF approximation of Section 2 applies, and that
      * the Jacobi-preconditioned inner solve is well posed).  Restart cycles of these plans are
      * not captured as CUDA graphs (the inner solve's stop test reads residual norms on the
-     * host), and certify mode, the adjoint and the one-graph batch do not take them. */
+     * host), and certify mode, the adjoint and the one-graph batch do not take them.
+     * Block width p_max <= 16. */
     EXPM_OP_CSR = 2
 } expm_op_kind;
 

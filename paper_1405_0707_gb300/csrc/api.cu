@@ -767,7 +767,7 @@ void free_plan(expm_plan* P) {
     cudaFree(P->cs.dinv);
     cudaFree(P->cs.work);
     cudaFree(P->cs.part);
-    cudaFree(P->cs.frz);
+    cudaFree(P->cs.scal);
     cudaFree(P->cs.norms);
     if (P->cs.hnorms) cudaFreeHost(P->cs.hnorms);
     cudaFree(P->tz.col);
@@ -1232,7 +1232,7 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     } else if (csr) {
         const expm_status vs = csr_validate(op, &abs_rowsum);
         if (vs != EXPM_OK) return vs;
-        if (opts->certify) return EXPM_INVALID_ARG;
+        if (opts->certify || p_max > 16) return EXPM_INVALID_ARG;   // the sparse kernels take p <= 16
     } else {
         if (op->kind != EXPM_OP_CONV_DIFF) return EXPM_INVALID_ARG;
         if (op->ndim < 1 || op->ndim > 3) return EXPM_INVALID_ARG;
@@ -1409,8 +1409,8 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         ok = ok && cudaMalloc(reinterpret_cast<void**>(&c.rowptr), sizeof(int64_t) * (size_t)(n + 1)) == cudaSuccess;
         ok = ok && cudaMalloc(reinterpret_cast<void**>(&c.colind), sizeof(int) * (size_t)std::max<int64_t>(c.nnz, 1)) == cudaSuccess;
         ok = ok && dalloc(&c.val, (size_t)std::max<int64_t>(c.nnz, 1)) && dalloc(&c.dinv, (size_t)n);
-        ok = ok && dalloc(&c.work, (size_t)9 * ld * p_max) && dalloc(&c.part, 7 * nb * p_max);
-        ok = ok && cudaMalloc(reinterpret_cast<void**>(&c.frz), sizeof(int) * (size_t)p_max) == cudaSuccess;
+        ok = ok && dalloc(&c.work, (size_t)9 * ld * p_max) && dalloc(&c.part, 2 * nb * p_max);
+        ok = ok && dalloc(&c.scal, 8 * (size_t)p_max);
         ok = ok && dalloc(&c.norms, 2 * (size_t)p_max);
         ok = ok && cudaMallocHost(reinterpret_cast<void**>(&c.hnorms), sizeof(double) * 2 * (size_t)p_max) == cudaSuccess;
     } else if (!toeplitz) {

@@ -137,8 +137,8 @@ struct CsrOp {
     double* dinv = nullptr;
     double abs_rowsum = 0.0;    // max_i sum_j |a_ij| (bound of ||A||_inf)
     double* work = nullptr;     // 9 x ld x pmax: the inner solver's vectors
-    double* part = nullptr;     // 7 x csr_blocks(n) x pmax partial sums
-    int* frz = nullptr;         // pmax
+    double* part = nullptr;     // csr_blocks(n) x 2 x pmax partial sums
+    double* scal = nullptr;     // pmax x 8: the columns' solver scalars
     double* norms = nullptr;    // 2 pmax: squared residual and right-hand-side norms
     double* hnorms = nullptr;   // pinned host mirror of norms
 };

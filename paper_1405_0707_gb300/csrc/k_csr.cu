@@ -4,234 +4,272 @@
 // error that the inexactness costs).
 //
 // The inner solve is BiCGStab with the Jacobi preconditioner (right preconditioning, M =
-// diag(A)) on every column of the block at once, each column with its own scalars.  Every
-// step is a kernel over (row blocks) x (columns); the reductions are deterministic: each CTA
-// writes one partial per column and dot, and the CTAs of the next kernel each re-add all the
-// partials of their column in the same fixed order, so every CTA derives the same alpha,
-// beta, omega without a separate reduction launch.  A column whose relative residual has
-// reached the tolerance (or whose recurrence broke down: a zero denominator) is frozen: its
-// iterate and residual no longer change.
+// diag(A)) on every column of the block at once, each column with its own scalars.  The
+// vector steps are kernels with a thread per row over all p columns, so the sparse products
+// read each matrix row once for the whole block; each reduction writes one partial per CTA,
+// column and dot, and a one-CTA scalar step adds them in a fixed order (deterministic) and
+// updates the columns' alpha, omega, rho, beta.  A column whose relative residual has reached
+// the tolerance (or whose recurrence broke down: a zero denominator) is frozen: its iterate
+// and residual no longer change.
 #include "internal.h"
 
 namespace expm {
 namespace {
 
 constexpr int CT = 256;     // threads per CTA
+constexpr int PMAX = 16;    // columns per block (p_max limit of the row kernels)
+constexpr int NSC = 8;      // scalars per column: rho, rho_old, alpha, omega, rr, bb, beta, frozen
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+enum { S_RHO = 0, S_RHO0, S_ALPHA, S_OMEGA, S_RR, S_BB, S_BETA, S_FRZ };
+
+// Y[:, c] = alpha A X[:, c] for every column: a thread per row reads the row's entries once and
+// applies them to all p columns (the matrix is read once, not once per column)
+template <int NC>
+__device__ __forceinline__ void row_apply(const int64_t* __restrict__ rp, const int* __restrict__ ci,
+                                          const double* __restrict__ va, const double* __restrict__ X, int64_t ldx,
+                                          int p, int64_t r, double* acc) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < CT / 32; ++k) s += sh[k];
-    return s;   // valid in thread 0
-}
-
-// y = alpha A x for one row (thread per row and column)
-__device__ __forceinline__ double row_dot(const int64_t* __restrict__ rp, const int* __restrict__ ci,
-                                          const double* __restrict__ va, const double* __restrict__ x, int64_t r) {
-    double s = 0.0;
-    for (int64_t k = rp[r]; k < rp[r + 1]; ++k) s = fma(va[k], x[ci[k]], s);
-    return s;
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    const int64_t k1 = rp[r + 1];
+    for (int64_t k = rp[r]; k < k1; ++k) {
+        const double a = va[k];
+        const double* xc = X + ci[k];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (c < p) acc[c] = fma(a, xc[c * ldx], acc[c]);
+    }
 }
 
 __global__ void __launch_bounds__(CT) k_csr_spmm(const int64_t* __restrict__ rp, const int* __restrict__ ci,
                                                  const double* __restrict__ va, int64_t n, double alpha,
                                                  const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
-                                                 int64_t ldy) {
-    const int c = blockIdx.y;
-    const double* x = X + c * ldx;
-    for (int64_t r = (int64_t)blockIdx.x * CT + threadIdx.x; r < n; r += (int64_t)gridDim.x * CT)
-        Y[c * ldy + r] = alpha * row_dot(rp, ci, va, x, r);
+                                                 int64_t ldy, int p) {
+    double acc[PMAX];
+    for (int64_t r = (int64_t)blockIdx.x * CT + threadIdx.x; r < n; r += (int64_t)gridDim.x * CT) {
+        row_apply<PMAX>(rp, ci, va, X, ldx, p, r, acc);
+#pragma unroll
+        for (int c = 0; c < PMAX; ++c)
+            if (c < p) Y[c * ldy + r] = alpha * acc[c];
+    }
 }
 
 // The inner solver's vectors, column c at offset c * ld of each: x, r, rh (the shadow
-// residual r^_0), q (search direction p), qh = M^-1 q, v = A qh, s, sh = M^-1 s, u = A sh.
+// residual r^_0), q (search direction), qh = M^-1 q, v = A qh, s, sh = M^-1 s, u = A sh.
 struct Bicg {
     const int64_t* rp;
     const int* ci;
     const double* va;
     const double* dinv;      // 1 / a_ii
     int64_t n, ld;
+    int p, nb;
     double *x, *r, *rh, *q, *qh, *v, *s, *sh, *u;
-    // partials [nb][p] each: d1 = (rh, v), d2 = (u, s), d3 = (u, u), d4 = (rh, r) (two
-    // buffers by iteration parity), d5 = (r, r), b2 = (b, b)
-    double *d1, *d2, *d3, *d4a, *d4b, *d5, *b2;
-    int* frz;                // per column: frozen this iteration (written by k_bicg_dir)
+    double* part;            // [nb][2][p]: the CTAs' partials of the phase's one or two dots
+    double* sc;              // [p][NSC]: the columns' scalars
+    double* norms;           // [2p]: rr and bb per column, for the host's stop test
     double eta2;             // squared relative tolerance
 };
 
-__device__ __forceinline__ double sum_part(const double* part, int nb, int p, int c) {
+// The CTA's per-column partials of up to two dot products: per-warp sums through shared
+// memory, then thread c adds the warps' sums in a fixed order (deterministic).
+__device__ __forceinline__ void cta_partials(const Bicg& g, const double* d1, const double* d2, int nd) {
+    __shared__ double sh[CT / 32][2][PMAX];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int k = 0; k < nd; ++k) {
+        const double* d = k ? d2 : d1;
+#pragma unroll
+        for (int c = 0; c < PMAX; ++c) {
+            double v = c < g.p ? d[c] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (l == 0) sh[w][k][c] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < g.p * nd) {
+        const int k = threadIdx.x / g.p, c = threadIdx.x - k * g.p;
+        double s = 0.0;
+        for (int ww = 0; ww < CT / 32; ++ww) s += sh[ww][k][c];
+        g.part[((size_t)blockIdx.x * 2 + k) * g.p + c] = s;
+    }
+}
+
+// the elementwise steps loop over columns (one column's rows at a time, coalesced) and leave
+// each warp's sums in shared memory, indexed by column; cta_partials_sh then writes the
+// CTA's partials in a fixed order
+__device__ __forceinline__ void warp_put(double (*sh)[2][PMAX], int k, int c, double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][k][c] = v;
+}
+
+__device__ __forceinline__ void cta_partials_sh(const Bicg& g, double (*sh)[2][PMAX], int nd) {
+    __syncthreads();
+    if (threadIdx.x < g.p * nd) {
+        const int k = threadIdx.x / g.p, c = threadIdx.x - k * g.p;
+        double s = 0.0;
+        for (int ww = 0; ww < CT / 32; ++ww) s += sh[ww][k][c];
+        g.part[((size_t)blockIdx.x * 2 + k) * g.p + c] = s;
+    }
+}
+
+__device__ __forceinline__ double sum_part(const Bicg& g, int k, int c) {
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += __ldcg(part + (int64_t)b * p + c);
+    for (int b = 0; b < g.nb; ++b) s += g.part[((size_t)b * 2 + k) * g.p + c];
     return s;
 }
 
-// the scalars of column c at the start of iteration it (it >= 1), from the partials of the
-// previous iteration: rho_new = (rh, r), rho_old, alpha, omega, and whether the column is
-// frozen (converged at the previous check of (r, r), or a denominator vanished)
-struct Scal {
-    double rho, alpha, omega, beta;
-    bool frozen;
-};
-
-__device__ Scal scalars(const Bicg& g, int it, int nb, int p, int c) {
-    const double* d4cur = (it & 1) ? g.d4b : g.d4a;   // written by iteration it - 1
-    const double* d4old = (it & 1) ? g.d4a : g.d4b;   // written by iteration it - 2 (or the start)
-    Scal z;
-    const double rho = sum_part(d4cur, nb, p, c), rho_old = sum_part(d4old, nb, p, c);
-    const double dd1 = sum_part(g.d1, nb, p, c), dd2 = sum_part(g.d2, nb, p, c), dd3 = sum_part(g.d3, nb, p, c);
-    const double rr = sum_part(g.d5, nb, p, c), bb = sum_part(g.b2, nb, p, c);
-    const double alpha = dd1 != 0.0 ? rho_old / dd1 : 0.0;
-    const double omega = dd3 != 0.0 ? dd2 / dd3 : 0.0;
-    z.rho = rho;
-    z.alpha = alpha;
-    z.omega = omega;
-    z.frozen = !(rr > g.eta2 * bb) || dd1 == 0.0 || dd3 == 0.0 || omega == 0.0 || rho_old == 0.0;
-    z.beta = z.frozen ? 0.0 : (rho / rho_old) * (alpha / omega);
-    return z;
-}
-
-// start: x = 0, r = rh = b, q = 0 (the first direction is r), partials (b, b) and (rh, r)
-__global__ void __launch_bounds__(CT) k_bicg_start(Bicg g, const double* __restrict__ B, int64_t ldb, int p) {
-    __shared__ double sh[CT / 32];
-    const int c = blockIdx.y, nb = gridDim.x;
-    double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)nb * CT) {
-        const double b = B[c * ldb + i];
-        const int64_t o = c * g.ld + i;
-        g.x[o] = 0.0;
-        g.r[o] = b;
-        g.rh[o] = b;
-        g.q[o] = 0.0;
-        g.v[o] = 0.0;
-        acc = fma(b, b, acc);
-    }
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-        const int64_t o = (int64_t)blockIdx.x * p + c;
-        g.b2[o] = s;
-        g.d4a[o] = s;      // rho_0 = (rh, r_0)
-        g.d4b[o] = 1.0;    // (rho of iteration 1 is written by iteration 0 before any read)
-        g.d5[o] = s;
-    }
-}
-
-// q = r + beta (q - omega v), qh = M^-1 q  (iteration 0: q = r).  Every CTA derives the
-// column's scalars and frozen state from the same partials; CTA 0 records the state for the
-// iteration's other kernels (which overwrite some of those partials).
-__global__ void __launch_bounds__(CT) k_bicg_dir(Bicg g, int it, int p) {
-    const int c = blockIdx.y, nb = gridDim.x;
-    Scal z;
-    if (it > 0) z = scalars(g, it, nb, p, c);
-    else z = Scal{0.0, 0.0, 0.0, 0.0, !(sum_part(g.b2, nb, p, c) > 0.0)};
-    if (blockIdx.x == 0 && threadIdx.x == 0) g.frz[c] = z.frozen ? 1 : 0;
-    if (z.frozen) return;
-    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)nb * CT) {
-        const int64_t o = c * g.ld + i;
-        const double q = it > 0 ? fma(z.beta, fma(-z.omega, g.v[o], g.q[o]), g.r[o]) : g.r[o];
-        g.q[o] = q;
-        g.qh[o] = q * g.dinv[i];
-    }
-}
-
-// v = A qh, partial (rh, v)
-__global__ void __launch_bounds__(CT) k_bicg_av(Bicg g, int it, int p) {
-    __shared__ double sh[CT / 32];
-    const int c = blockIdx.y, nb = gridDim.x;
-    const bool frozen = g.frz[c] != 0;
-    double acc = 0.0;
-    if (!frozen)
-        for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)nb * CT) {
+// start: x = 0, r = rh = b, q = v = 0; partials (b, b)
+__global__ void __launch_bounds__(CT) k_bicg_start(Bicg g, const double* __restrict__ B, int64_t ldb) {
+    __shared__ double sh[CT / 32][2][PMAX];
+    for (int c = 0; c < g.p; ++c) {
+        double bb = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * CT) {
+            const double b = B[c * ldb + i];
             const int64_t o = c * g.ld + i;
-            const double v = row_dot(g.rp, g.ci, g.va, g.qh + c * g.ld, i);
-            g.v[o] = v;
-            acc = fma(g.rh[o], v, acc);
+            g.x[o] = 0.0;
+            g.r[o] = b;
+            g.rh[o] = b;
+            g.q[o] = 0.0;
+            g.v[o] = 0.0;
+            bb = fma(b, b, bb);
         }
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0 && !frozen) g.d1[(int64_t)blockIdx.x * p + c] = s;
+        warp_put(sh, 0, c, bb);
+    }
+    cta_partials_sh(g, sh, 1);
 }
 
-// alpha = rho / (rh, v); s = r - alpha v, sh = M^-1 s
-__global__ void __launch_bounds__(CT) k_bicg_s(Bicg g, int it, int p) {
-    const int c = blockIdx.y, nb = gridDim.x;
-    if (g.frz[c]) return;
-    const double* d4cur = (it & 1) ? g.d4b : g.d4a;
-    const double dd1 = sum_part(g.d1, nb, p, c);
-    const double alpha = dd1 != 0.0 ? sum_part(d4cur, nb, p, c) / dd1 : 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)nb * CT) {
-        const int64_t o = c * g.ld + i;
-        const double s = fma(-alpha, g.v[o], g.r[o]);
-        g.s[o] = s;
-        g.sh[o] = s * g.dinv[i];
+// The scalar steps (one CTA, a thread per column), after each reduction:
+//   phase 0 (start): bb = rho = rr = (b, b); frozen iff b = 0
+//   phase 1 (after v = A qh): alpha = rho / (rh, v)
+//   phase 2 (after u = A sh): omega = (u, s) / (u, u)
+//   phase 3 (after the update): rho_old = rho, rho = (rh, r), rr = (r, r),
+//           beta = (rho / rho_old) (alpha / omega); frozen once rr <= eta^2 bb or a
+//           denominator vanished (then the column's iterate stays as it is)
+__global__ void k_bicg_scal(Bicg g, int phase) {
+    const int c = threadIdx.x;
+    if (c >= g.p) return;
+    double* z = g.sc + c * NSC;
+    if (phase == 0) {
+        const double bb = sum_part(g, 0, c);
+        z[S_BB] = bb;
+        z[S_RHO] = bb;
+        z[S_RR] = bb;
+        z[S_FRZ] = bb > 0.0 ? 0.0 : 1.0;
+    } else if (phase == 1) {
+        const double d = sum_part(g, 0, c);
+        if (d != 0.0) z[S_ALPHA] = z[S_RHO] / d;
+        else z[S_FRZ] = 1.0;
+    } else if (phase == 2) {
+        const double us = sum_part(g, 0, c), uu = sum_part(g, 1, c);
+        if (uu != 0.0 && us != 0.0) z[S_OMEGA] = us / uu;
+        else z[S_FRZ] = 1.0;
+    } else {
+        const double rho = sum_part(g, 0, c), rr = sum_part(g, 1, c);
+        if (z[S_FRZ] == 0.0) {
+            z[S_RHO0] = z[S_RHO];
+            z[S_RHO] = rho;
+            z[S_RR] = rr;
+            z[S_BETA] = (rho / z[S_RHO0]) * (z[S_ALPHA] / z[S_OMEGA]);
+            if (!(rr > g.eta2 * z[S_BB]) || rho == 0.0) z[S_FRZ] = 1.0;
+        }
+    }
+    g.norms[c] = z[S_RR];
+    g.norms[g.p + c] = z[S_BB];
+}
+
+// q = r + beta (q - omega v) (iteration 0: q = r), qh = M^-1 q
+__global__ void __launch_bounds__(CT) k_bicg_dir(Bicg g, int it) {
+    for (int c = 0; c < g.p; ++c) {
+        const double* z = g.sc + c * NSC;
+        if (z[S_FRZ] != 0.0) continue;
+        const double beta = z[S_BETA], omega = z[S_OMEGA];
+        for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * CT) {
+            const int64_t o = c * g.ld + i;
+            const double q = it > 0 ? fma(beta, fma(-omega, g.v[o], g.q[o]), g.r[o]) : g.r[o];
+            g.q[o] = q;
+            g.qh[o] = q * g.dinv[i];
+        }
+    }
+}
+
+// v = A qh, partials (rh, v)
+__global__ void __launch_bounds__(CT) k_bicg_av(Bicg g) {
+    double acc[PMAX], d1[PMAX];
+#pragma unroll
+    for (int c = 0; c < PMAX; ++c) d1[c] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * CT) {
+        row_apply<PMAX>(g.rp, g.ci, g.va, g.qh, g.ld, g.p, i, acc);
+#pragma unroll
+        for (int c = 0; c < PMAX; ++c)
+            if (c < g.p) {
+                const int64_t o = c * g.ld + i;
+                g.v[o] = acc[c];
+                d1[c] = fma(g.rh[o], acc[c], d1[c]);
+            }
+    }
+    cta_partials(g, d1, nullptr, 1);
+}
+
+// s = r - alpha v, sh = M^-1 s
+__global__ void __launch_bounds__(CT) k_bicg_s(Bicg g) {
+    for (int c = 0; c < g.p; ++c) {
+        const double* z = g.sc + c * NSC;
+        if (z[S_FRZ] != 0.0) continue;
+        const double alpha = z[S_ALPHA];
+        for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * CT) {
+            const int64_t o = c * g.ld + i;
+            const double s = fma(-alpha, g.v[o], g.r[o]);
+            g.s[o] = s;
+            g.sh[o] = s * g.dinv[i];
+        }
     }
 }
 
 // u = A sh, partials (u, s) and (u, u)
-__global__ void __launch_bounds__(CT) k_bicg_au(Bicg g, int it, int p) {
-    __shared__ double sh[CT / 32];
-    const int c = blockIdx.y, nb = gridDim.x;
-    const bool frozen = g.frz[c] != 0;
-    double a2 = 0.0, a3 = 0.0;
-    if (!frozen)
-        for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)nb * CT) {
+__global__ void __launch_bounds__(CT) k_bicg_au(Bicg g) {
+    double acc[PMAX], d2[PMAX], d3[PMAX];
+#pragma unroll
+    for (int c = 0; c < PMAX; ++c) {
+        d2[c] = 0.0;
+        d3[c] = 0.0;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * CT) {
+        row_apply<PMAX>(g.rp, g.ci, g.va, g.sh, g.ld, g.p, i, acc);
+#pragma unroll
+        for (int c = 0; c < PMAX; ++c)
+            if (c < g.p) {
+                const int64_t o = c * g.ld + i;
+                g.u[o] = acc[c];
+                d2[c] = fma(acc[c], g.s[o], d2[c]);
+                d3[c] = fma(acc[c], acc[c], d3[c]);
+            }
+    }
+    cta_partials(g, d2, d3, 2);
+}
+
+// x += alpha qh + omega sh, r = s - omega u; partials (rh, r) and (r, r)
+__global__ void __launch_bounds__(CT) k_bicg_x(Bicg g) {
+    __shared__ double sh[CT / 32][2][PMAX];
+    for (int c = 0; c < g.p; ++c) {
+        const double* z = g.sc + c * NSC;
+        const bool frz = z[S_FRZ] != 0.0;
+        const double alpha = z[S_ALPHA], omega = z[S_OMEGA];
+        double d4 = 0.0, d5 = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * CT) {
             const int64_t o = c * g.ld + i;
-            const double u = row_dot(g.rp, g.ci, g.va, g.sh + c * g.ld, i);
-            g.u[o] = u;
-            a2 = fma(u, g.s[o], a2);
-            a3 = fma(u, u, a3);
+            double r = g.r[o];
+            if (!frz) {
+                g.x[o] = fma(omega, g.sh[o], fma(alpha, g.qh[o], g.x[o]));
+                r = fma(-omega, g.u[o], g.s[o]);
+                g.r[o] = r;
+            }
+            d4 = fma(g.rh[o], r, d4);
+            d5 = fma(r, r, d5);
         }
-    const double s2 = block_sum(a2, sh);
-    const double s3 = block_sum(a3, sh);
-    if (threadIdx.x == 0 && !frozen) {
-        g.d2[(int64_t)blockIdx.x * p + c] = s2;
-        g.d3[(int64_t)blockIdx.x * p + c] = s3;
+        warp_put(sh, 0, c, d4);
+        warp_put(sh, 1, c, d5);
     }
-}
-
-// omega = (u, s) / (u, u); x += alpha qh + omega sh; r = s - omega u; partials (rh, r), (r, r)
-__global__ void __launch_bounds__(CT) k_bicg_x(Bicg g, int it, int p) {
-    __shared__ double sh[CT / 32];
-    const int c = blockIdx.y, nb = gridDim.x;
-    const bool frozen = g.frz[c] != 0;
-    const double* d4cur = (it & 1) ? g.d4b : g.d4a;
-    double* d4next = (it & 1) ? g.d4a : g.d4b;
-    const double dd1 = sum_part(g.d1, nb, p, c), dd2 = sum_part(g.d2, nb, p, c), dd3 = sum_part(g.d3, nb, p, c);
-    const double alpha = dd1 != 0.0 ? sum_part(d4cur, nb, p, c) / dd1 : 0.0;
-    const double omega = dd3 != 0.0 ? dd2 / dd3 : 0.0;
-    double a4 = 0.0, a5 = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)nb * CT) {
-        const int64_t o = c * g.ld + i;
-        double r = g.r[o];
-        if (!frozen) {
-            g.x[o] = fma(omega, g.sh[o], fma(alpha, g.qh[o], g.x[o]));
-            r = fma(-omega, g.u[o], g.s[o]);
-            g.r[o] = r;
-        }
-        a4 = fma(g.rh[o], r, a4);
-        a5 = fma(r, r, a5);
-    }
-    const double s4 = block_sum(a4, sh);
-    const double s5 = block_sum(a5, sh);
-    if (threadIdx.x == 0) {
-        const int64_t o = (int64_t)blockIdx.x * p + c;
-        // a frozen column keeps its partials, so its scalars and its frozen state stay put
-        d4next[o] = frozen ? d4cur[o] : s4;
-        g.d5[o] = s5;
-    }
-}
-
-// squared residual norms and (b, b) per column, for the host's stop test
-__global__ void k_bicg_norms(Bicg g, int nb, int p, double* out) {
-    const int c = threadIdx.x;
-    if (c < p) {
-        out[c] = sum_part(g.d5, nb, p, c);
-        out[p + c] = sum_part(g.b2, nb, p, c);
-    }
+    cta_partials_sh(g, sh, 2);
 }
 
 __global__ void __launch_bounds__(CT) k_csr_scale_out(const double* __restrict__ x, int64_t ldx, int64_t n,
@@ -260,13 +298,13 @@ int csr_blocks(int64_t n) {
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             sms = 1;
     }
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n + CT - 1) / CT, 2 * (int64_t)sms));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + CT - 1) / CT, 4 * (int64_t)sms));
 }
 
 cudaError_t launch_csr_spmm(const CsrOp& a, double alpha, const double* X, int64_t ldx, int p, double* Y, int64_t ldy,
                             cudaStream_t s) {
-    const dim3 grid((unsigned)csr_blocks(a.n), (unsigned)p);
-    k_csr_spmm<<<grid, CT, 0, s>>>(a.rowptr, a.colind, a.val, a.n, alpha, X, ldx, Y, ldy);
+    if (p < 1 || p > PMAX) return cudaErrorInvalidValue;
+    k_csr_spmm<<<(unsigned)csr_blocks(a.n), CT, 0, s>>>(a.rowptr, a.colind, a.val, a.n, alpha, X, ldx, Y, ldy, p);
     return cudaGetLastError();
 }
 
@@ -277,11 +315,12 @@ cudaError_t launch_csr_dinv(CsrOp& a, cudaStream_t s) {
 
 // W = (tA)^{-1} V approximately: A y = V by BiCGStab to ||r|| <= eta ||v|| per column, then
 // W = y / t.  The host reads the residual norms every `check` iterations (a stream
-// synchronisation).  Returns cudaSuccess and *iters (iterations run); *converged = 0 when
-// maxit ran out first.
+// synchronisation).  *iters: iterations run; *converged = 0 when maxit ran out first.
 cudaError_t csr_inverse(const CsrOp& a, double t, const double* V, int64_t ldv, int p, double* W, int64_t ldw,
                         double eta, int maxit, cudaStream_t s, int* iters, int* converged) {
-    const int nb = csr_blocks(a.n);
+    *iters = 0;
+    *converged = 0;
+    if (p < 1 || p > PMAX) return cudaErrorInvalidValue;
     Bicg g;
     g.rp = a.rowptr;
     g.ci = a.colind;
@@ -289,36 +328,32 @@ cudaError_t csr_inverse(const CsrOp& a, double t, const double* V, int64_t ldv, 
     g.dinv = a.dinv;
     g.n = a.n;
     g.ld = a.ld;
+    g.p = p;
+    g.nb = csr_blocks(a.n);
     double* w = a.work;
     double** vecs[9] = {&g.x, &g.r, &g.rh, &g.q, &g.qh, &g.v, &g.s, &g.sh, &g.u};
     for (int k = 0; k < 9; ++k) *vecs[k] = w + (size_t)k * a.ld * a.pmax;
-    double* pp = a.part;
-    const size_t ps = (size_t)nb * p;
-    g.d1 = pp; g.d2 = pp + ps; g.d3 = pp + 2 * ps; g.d4a = pp + 3 * ps; g.d4b = pp + 4 * ps;
-    g.d5 = pp + 5 * ps; g.b2 = pp + 6 * ps;
-    g.frz = a.frz;
+    g.part = a.part;
+    g.sc = a.scal;
+    g.norms = a.norms;
     g.eta2 = eta * eta;
-    // the partials of the dots before their first write: zero (a frozen check in iteration
-    // 0 is skipped, and iteration 1 reads only what iteration 0 wrote)
-    cudaError_t e = cudaMemsetAsync(pp, 0, sizeof(double) * 7 * ps, s);
-    const dim3 grid((unsigned)nb, (unsigned)p);
-    if (e == cudaSuccess) {
-        k_bicg_start<<<grid, CT, 0, s>>>(g, V, ldv, p);
-        e = cudaGetLastError();
-    }
-    *iters = 0;
-    *converged = 0;
+    const unsigned nb = (unsigned)g.nb;
+    k_bicg_start<<<nb, CT, 0, s>>>(g, V, ldv);
+    k_bicg_scal<<<1, PMAX, 0, s>>>(g, 0);
+    cudaError_t e = cudaGetLastError();
     const int check = 8;
     for (int it = 0; it < maxit && e == cudaSuccess; ++it) {
-        k_bicg_dir<<<grid, CT, 0, s>>>(g, it, p);
-        k_bicg_av<<<grid, CT, 0, s>>>(g, it, p);
-        k_bicg_s<<<grid, CT, 0, s>>>(g, it, p);
-        k_bicg_au<<<grid, CT, 0, s>>>(g, it, p);
-        k_bicg_x<<<grid, CT, 0, s>>>(g, it, p);
+        k_bicg_dir<<<nb, CT, 0, s>>>(g, it);
+        k_bicg_av<<<nb, CT, 0, s>>>(g);
+        k_bicg_scal<<<1, PMAX, 0, s>>>(g, 1);
+        k_bicg_s<<<nb, CT, 0, s>>>(g);
+        k_bicg_au<<<nb, CT, 0, s>>>(g);
+        k_bicg_scal<<<1, PMAX, 0, s>>>(g, 2);
+        k_bicg_x<<<nb, CT, 0, s>>>(g);
+        k_bicg_scal<<<1, PMAX, 0, s>>>(g, 3);
         e = cudaGetLastError();
         *iters = it + 1;
         if (e == cudaSuccess && ((it + 1) % check == 0 || it + 1 == maxit)) {
-            k_bicg_norms<<<1, 32, 0, s>>>(g, nb, p, a.norms);
             e = cudaMemcpyAsync(a.hnorms, a.norms, sizeof(double) * 2 * p, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) break;
@@ -331,6 +366,7 @@ cudaError_t csr_inverse(const CsrOp& a, double t, const double* V, int64_t ldv, 
         }
     }
     if (e == cudaSuccess) {
+        const dim3 grid(nb, (unsigned)p);
         k_csr_scale_out<<<grid, CT, 0, s>>>(g.x, a.ld, a.n, 1.0 / t, W, ldw);
         e = cudaGetLastError();
     }
