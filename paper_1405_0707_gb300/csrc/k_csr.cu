@@ -19,6 +19,7 @@ namespace {
 constexpr int CT = 256;     // threads per CTA
 constexpr int PMAX = 16;    // columns per block (p_max limit of the row kernels)
 constexpr int NSC = 8;      // scalars per column: rho, rho_old, alpha, omega, rr, bb, beta, frozen
+constexpr int SPG = 4;      // columns per thread in the sparse products
 
 enum { S_RHO = 0, S_RHO0, S_ALPHA, S_OMEGA, S_RR, S_BB, S_BETA, S_FRZ };
 
@@ -40,16 +41,24 @@ __device__ __forceinline__ void row_apply(const int64_t* __restrict__ rp, const 
     }
 }
 
+// thread per row and group of SPG columns (blockIdx.y): each row's entries are read once per
+// group, from L2 after the first group (measured: one group of all 16 columns ran
+// load-throttled at 0.24 ms on 96^3, p = 16; one column per CTA column re-read the matrix
+// from DRAM 2.85 times)
 __global__ void __launch_bounds__(CT) k_csr_spmm(const int64_t* __restrict__ rp, const int* __restrict__ ci,
                                                  const double* __restrict__ va, int64_t n, double alpha,
                                                  const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
                                                  int64_t ldy, int p) {
-    double acc[PMAX];
+    const int c0 = blockIdx.y * SPG;
+    const int pc = min(SPG, p - c0);
+    X += c0 * ldx;
+    Y += c0 * ldy;
+    double acc[SPG];
     for (int64_t r = (int64_t)blockIdx.x * CT + threadIdx.x; r < n; r += (int64_t)gridDim.x * CT) {
-        row_apply<PMAX>(rp, ci, va, X, ldx, p, r, acc);
+        row_apply<SPG>(rp, ci, va, X, ldx, pc, r, acc);
 #pragma unroll
-        for (int c = 0; c < PMAX; ++c)
-            if (c < p) Y[c * ldy + r] = alpha * acc[c];
+        for (int c = 0; c < SPG; ++c)
+            if (c < pc) Y[c * ldy + r] = alpha * acc[c];
     }
 }
 
@@ -69,27 +78,30 @@ struct Bicg {
     double eta2;             // squared relative tolerance
 };
 
-// The CTA's per-column partials of up to two dot products: per-warp sums through shared
-// memory, then thread c adds the warps' sums in a fixed order (deterministic).
-__device__ __forceinline__ void cta_partials(const Bicg& g, const double* d1, const double* d2, int nd) {
-    __shared__ double sh[CT / 32][2][PMAX];
+// The CTA's partials of up to two dot products for its SPG columns c0 .. c0 + SPG - 1: per-warp
+// sums through shared memory, then thread (k, c) adds the warps' sums in a fixed order
+// (deterministic).
+__device__ __forceinline__ void cta_partials(const Bicg& g, int c0, const double* d1, const double* d2, int nd) {
+    __shared__ double sh[CT / 32][2][SPG];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (int k = 0; k < nd; ++k) {
         const double* d = k ? d2 : d1;
 #pragma unroll
-        for (int c = 0; c < PMAX; ++c) {
-            double v = c < g.p ? d[c] : 0.0;
+        for (int c = 0; c < SPG; ++c) {
+            double v = d[c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (l == 0) sh[w][k][c] = v;
         }
     }
     __syncthreads();
-    if (threadIdx.x < g.p * nd) {
-        const int k = threadIdx.x / g.p, c = threadIdx.x - k * g.p;
-        double s = 0.0;
-        for (int ww = 0; ww < CT / 32; ++ww) s += sh[ww][k][c];
-        g.part[((size_t)blockIdx.x * 2 + k) * g.p + c] = s;
+    if (threadIdx.x < SPG * nd) {
+        const int k = threadIdx.x / SPG, c = threadIdx.x - k * SPG;
+        if (c0 + c < g.p) {
+            double s = 0.0;
+            for (int ww = 0; ww < CT / 32; ++ww) s += sh[ww][k][c];
+            g.part[((size_t)blockIdx.x * 2 + k) * g.p + c0 + c] = s;
+        }
     }
 }
 
@@ -192,22 +204,23 @@ __global__ void __launch_bounds__(CT) k_bicg_dir(Bicg g, int it) {
     }
 }
 
-// v = A qh, partials (rh, v)
+// v = A qh, partials (rh, v); blockIdx.y: the group of SPG columns
 __global__ void __launch_bounds__(CT) k_bicg_av(Bicg g) {
-    double acc[PMAX], d1[PMAX];
+    const int c0 = blockIdx.y * SPG, pc = min(SPG, g.p - c0);
+    double acc[SPG], d1[SPG];
 #pragma unroll
-    for (int c = 0; c < PMAX; ++c) d1[c] = 0.0;
+    for (int c = 0; c < SPG; ++c) d1[c] = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * CT) {
-        row_apply<PMAX>(g.rp, g.ci, g.va, g.qh, g.ld, g.p, i, acc);
+        row_apply<SPG>(g.rp, g.ci, g.va, g.qh + c0 * g.ld, g.ld, pc, i, acc);
 #pragma unroll
-        for (int c = 0; c < PMAX; ++c)
-            if (c < g.p) {
-                const int64_t o = c * g.ld + i;
+        for (int c = 0; c < SPG; ++c)
+            if (c < pc) {
+                const int64_t o = (c0 + c) * g.ld + i;
                 g.v[o] = acc[c];
                 d1[c] = fma(g.rh[o], acc[c], d1[c]);
             }
     }
-    cta_partials(g, d1, nullptr, 1);
+    cta_partials(g, c0, d1, nullptr, 1);
 }
 
 // s = r - alpha v, sh = M^-1 s
@@ -225,26 +238,27 @@ __global__ void __launch_bounds__(CT) k_bicg_s(Bicg g) {
     }
 }
 
-// u = A sh, partials (u, s) and (u, u)
+// u = A sh, partials (u, s) and (u, u); blockIdx.y: the group of SPG columns
 __global__ void __launch_bounds__(CT) k_bicg_au(Bicg g) {
-    double acc[PMAX], d2[PMAX], d3[PMAX];
+    const int c0 = blockIdx.y * SPG, pc = min(SPG, g.p - c0);
+    double acc[SPG], d2[SPG], d3[SPG];
 #pragma unroll
-    for (int c = 0; c < PMAX; ++c) {
+    for (int c = 0; c < SPG; ++c) {
         d2[c] = 0.0;
         d3[c] = 0.0;
     }
     for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * CT) {
-        row_apply<PMAX>(g.rp, g.ci, g.va, g.sh, g.ld, g.p, i, acc);
+        row_apply<SPG>(g.rp, g.ci, g.va, g.sh + c0 * g.ld, g.ld, pc, i, acc);
 #pragma unroll
-        for (int c = 0; c < PMAX; ++c)
-            if (c < g.p) {
-                const int64_t o = c * g.ld + i;
+        for (int c = 0; c < SPG; ++c)
+            if (c < pc) {
+                const int64_t o = (c0 + c) * g.ld + i;
                 g.u[o] = acc[c];
                 d2[c] = fma(acc[c], g.s[o], d2[c]);
                 d3[c] = fma(acc[c], acc[c], d3[c]);
             }
     }
-    cta_partials(g, d2, d3, 2);
+    cta_partials(g, c0, d2, d3, 2);
 }
 
 // x += alpha qh + omega sh, r = s - omega u; partials (rh, r) and (r, r)
@@ -304,7 +318,8 @@ int csr_blocks(int64_t n) {
 cudaError_t launch_csr_spmm(const CsrOp& a, double alpha, const double* X, int64_t ldx, int p, double* Y, int64_t ldy,
                             cudaStream_t s) {
     if (p < 1 || p > PMAX) return cudaErrorInvalidValue;
-    k_csr_spmm<<<(unsigned)csr_blocks(a.n), CT, 0, s>>>(a.rowptr, a.colind, a.val, a.n, alpha, X, ldx, Y, ldy, p);
+    const dim3 grid((unsigned)csr_blocks(a.n), (unsigned)((p + SPG - 1) / SPG));
+    k_csr_spmm<<<grid, CT, 0, s>>>(a.rowptr, a.colind, a.val, a.n, alpha, X, ldx, Y, ldy, p);
     return cudaGetLastError();
 }
 
@@ -338,16 +353,17 @@ cudaError_t csr_inverse(const CsrOp& a, double t, const double* V, int64_t ldv, 
     g.norms = a.norms;
     g.eta2 = eta * eta;
     const unsigned nb = (unsigned)g.nb;
+    const dim3 gsp(nb, (unsigned)((p + SPG - 1) / SPG));
     k_bicg_start<<<nb, CT, 0, s>>>(g, V, ldv);
     k_bicg_scal<<<1, PMAX, 0, s>>>(g, 0);
     cudaError_t e = cudaGetLastError();
     const int check = 8;
     for (int it = 0; it < maxit && e == cudaSuccess; ++it) {
         k_bicg_dir<<<nb, CT, 0, s>>>(g, it);
-        k_bicg_av<<<nb, CT, 0, s>>>(g);
+        k_bicg_av<<<gsp, CT, 0, s>>>(g);
         k_bicg_scal<<<1, PMAX, 0, s>>>(g, 1);
         k_bicg_s<<<nb, CT, 0, s>>>(g);
-        k_bicg_au<<<nb, CT, 0, s>>>(g);
+        k_bicg_au<<<gsp, CT, 0, s>>>(g);
         k_bicg_scal<<<1, PMAX, 0, s>>>(g, 2);
         k_bicg_x<<<nb, CT, 0, s>>>(g);
         k_bicg_scal<<<1, PMAX, 0, s>>>(g, 3);
