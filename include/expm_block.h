@@ -109,7 +109,11 @@ typedef enum {
      * - Symmetric Toeplitz operators run their FFTs in double-float (float pairs, 2^-48).
      * - The CGS2 projections are FP32 products.
      * - The first Gram-Schmidt update, the application of each Cholesky-QR factor and the
-     *   Z update run in double-float. Corrections of size O(eps_32) are formed in FP32.
+     *   Z update run in double-float. Corrections of size O(eps_32) are formed in FP32. For
+     *   blocks of p >= 12 against at least 64 basis columns the first update runs on the
+     *   tensor cores instead, on exact bf16 digit slices with FP32 accumulation.
+     * - Algorithm 1's operator tA (stencils) is applied in double-float; the refinement
+     *   residual of the inverse stays FP64.
      * - The basis is stored in FP64, and the projected systems and the combination stay
      *   FP64.
      * So the Arnoldi relation and the collinear restart hold to ~1e-14 or better.
