@@ -114,6 +114,27 @@ def test_csr_inexact_inverse_error_follows_theorem_4_3(tab):
     assert errs[1e-13] < errs[1e-6]
 
 
+def test_csr_full_size_product_and_inner_solve():
+    """At the benchmarked size (csr3d-96: the 96^3 7-point pattern with random values, p = 16):
+    the product against scipy's entry by entry, and the inner solve's stopping rule per column
+    with the residual formed on the host by scipy."""
+    need_gpu()
+    import scipy.sparse as sp
+    from paper_1405_0707_gb300 import Plan
+    w = inputs.WORKLOADS["csr3d-96"]
+    ip, ix, dv = inputs.sparse_stencil_matrix(w["csr_sides"])
+    n, p, t = 96 ** 3, w["p"], w["t"][0]
+    A = sp.csr_matrix((dv, ix, ip), shape=(n, n))
+    V = inputs.rhs(n, p, w["seed"])
+    plan = Plan.csr(A, p_max=p, m=2, inner_tol=1e-12)
+    W = to_np(plan.op_apply(t, to_dev(V)))
+    assert np.all(np.abs(W - t * (A @ V)) <= 16 * 2.0 ** -53 * t * (abs(A) @ np.abs(V)))
+    X = to_np(plan.prec_apply(t, to_dev(V)))
+    R = V - t * (A @ X)
+    for c in range(p):
+        assert np.linalg.norm(R[:, c]) <= 1.05e-12 * np.linalg.norm(V[:, c]), c
+
+
 def test_csr_plans_reject_what_they_do_not_support():
     torch = need_gpu()
     from paper_1405_0707_gb300 import Plan
