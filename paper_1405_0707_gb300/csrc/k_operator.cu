@@ -275,7 +275,7 @@ __global__ void k_cd_apply(const double* __restrict__ V, int64_t ldv, double* __
         }
     }
     const double r = Y ? fma(beta, Y[c * ldy + i], acc) : acc;
-    if (W32) W32[c * ldw + i] = (float)r;
+    if (W32) W32[c * ldw + i] = f32_rn_i(r);   // integer rounding: no FP64-pipe conversion
     else W[c * ldw + i] = r;
 }
 
