@@ -585,18 +585,6 @@ __global__ void __launch_bounds__(NTR) k_qr_mixed_rows(double* W, int64_t ldw, i
         hn2[threadIdx.x] = s2;
     }
     __syncthreads();
-    // the CTA's rows of W (and, KIND 3, of the basis for the correction) are prefetched into
-    // L2 while warp 0 factors the Gram matrix below, so the row pass after the barrier starts
-    // from L2 instead of HBM (a CTA holds only a few rows per thread: the factor's latency
-    // would otherwise stand in front of every load)
-    {
-        const int64_t rb0 = rows_begin(rpb), re0 = min(n, rb0 + rpb);
-        for (int64_t r = rb0 + threadIdx.x; r < re0; r += blockDim.x) {
-            for (int c = 0; c < p; ++c) asm volatile("prefetch.global.L2 [%0];" ::"l"(W + (int64_t)c * ldw + r));
-            if (KIND == 3)
-                for (int a = 0; a < ccols; ++a) asm volatile("prefetch.global.L2 [%0];" ::"l"(Vc + (int64_t)a * ldvc + r));
-        }
-    }
     int kexp = 0;                           // KIND 1: G is factored as G 2^-kexp (kexp even)
     if (threadIdx.x < 32) {
         int sgl_r = 0;                      // warp 0's copy of the single-pass decision
