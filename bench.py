@@ -70,12 +70,14 @@ KERNEL_OF = {"gemm": "k_gemm (DST-I transforms of the exact inverse, FP64)",
 
 def _hbm_peak():
     try:
-        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        return (float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]),
+                "measured copy rate (MEASURED_PEAKS.json hbm_gbs)")
     except (OSError, KeyError, ValueError):
-        return 6800.0      # fallback figure of the profiling recipe
+        # no measured figure at hand: an earlier GB300 copy measurement, 6.8 TB/s
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
 
 
-HBM_PEAK_GBS = _hbm_peak()
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _hbm_peak()
 
 
 def workload_n(w):
@@ -161,6 +163,9 @@ def parse():
                     help="batched workload: 1 = one CUDA graph launch per step (expm_batch_run), 0 = the "
                          "host-driven expm_block_batched")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extra", default="cd2d-256,toeplitz-1m",
+                    help="batched line only: single-instance workloads also timed (a few steps each) "
+                         "and reported under 'extra'; '' = none")
     ap.add_argument("--component", default=None, choices=[None, "prec", "stencil", "expm", "step", "fmapeak"],
                     help="time one entry point of the library on the workload's shapes "
                          "(used for the ncu captures) instead of the full bench")
@@ -414,10 +419,10 @@ def run_ours(args):
                  "bytes_per_launch": by_launch,
                  "launch_ms": r["ms_per_step"] / max(1, r["launches_per_step"]),
                  "peak_note": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz = 1.259 TF/s (the higher of two "
-                              "probes; 1.01 and 1.26 TF/s measured); HBM: measured copy GB/s"})
+                              "probes; 1.01 and 1.26 TF/s measured); HBM: " + HBM_PEAK_SOURCE})
     if head == "mixed":
         roof["note"] = ("mixed path: achieved = the stage's algorithmic bytes (each operand read once per "
-                        "pass) / its event time, against the measured HBM copy rate.  The basis (n x (m+1)p "
+                        "pass) / its event time, against the HBM peak.  The basis (n x (m+1)p "
                         "FP64) stays L2-resident within a step, and these passes are latency-bound (short "
                         "dependent passes of 293-586 CTAs, serial p x p factorisations in every CTA, last-CTA "
                         "reductions), so the fraction is low; fp64_path.roofline is the same stage of the pure "
@@ -530,6 +535,58 @@ def batched_gate(Zm, Z64, Bd):
     ok = all(e <= 1e-8 for _, e in rel) and all(e <= 1e-12 for _, _, e in floor)
     return ok, rel, floor
 
+
+
+def extra_workload(name, dev, steps=3, warmup=2):
+    """One single-instance workload timed briefly beside the batched line: the mixed and the
+    FP64 plan over all of its t, device-resident inputs, a 512 MB L2 flush before each step,
+    CUDA events on the plans' stream.  Returns RHS-columns/s of both paths and the mixed
+    path's relative error against the FP64 one."""
+    import torch
+
+    from paper_1405_0707_gb300 import inputs
+    w = inputs.WORKLOADS[name]
+    p, n, times = w["p"], workload_n(w), w["t"]
+    stream = torch.cuda.Stream(device=dev)
+    plans = {prec: make_plan(w, prec, stream) for prec in ("mixed", "fp64")}
+    with torch.cuda.stream(stream):
+        B = inputs.to_device_colmajor(inputs.rhs(n, p, w["seed"]), device=dev)
+        Z = torch.empty((p, n), dtype=torch.float64, device=dev).T
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    out = {"unit": UNIT, "steps": steps, "t": list(times), "p": p, "n": n}
+    err = 0.0
+    for t in times:
+        Z64, _ = plans["fp64"].expm_block(t, B)
+        Zm, _ = plans["mixed"].expm_block(t, B)
+        err = max(err, float(torch.linalg.norm(Zm - Z64) / torch.linalg.norm(Z64)))
+    for prec in ("mixed", "fp64"):
+        def step():
+            for t in times:
+                plans[prec].expm_block(t, B, Z)
+        for _ in range(warmup):
+            step()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize()
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i)
+                ev[i][0].record(stream)
+            step()
+            with torch.cuda.stream(stream):
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        key = "value" if prec == "mixed" else "fp64_value"
+        out[key] = round(steps * len(times) * p / (ms / 1e3), 3)
+        out["ms_per_step" if prec == "mixed" else "fp64_ms_per_step"] = round(ms / steps, 3)
+    out["mixed_rel_err_vs_fp64"] = err
+    for pl in plans.values():
+        pl.close()
+    del B, Z, flush
+    torch.cuda.synchronize()
+    return out
 
 def batched_cpu_baseline(inst, w, cycles, algs, budget_s=25.0):
     """The oracle on a bounded sample of the batched workload: complete solves of instances in
@@ -715,8 +772,8 @@ def run_batched(args):
             "unit": "GB/s", "frac": round(r["frac_hbm"], 4), "traffic": traffic_record(dom + "_batched"),
             "bytes_per_launch": work[dom][1] / r["launches"], "launch_ms": r["launch_ms"],
             "note": "algorithmic bytes of the class summed over the 64 instances (each operand read once "
-                    "per pass) / its event-timed duration in one serial pass over the instances; peak = "
-                    "measured HBM copy rate"}
+                    "per pass) / its event-timed duration in one serial pass over the instances",
+            "peak_source": HBM_PEAK_SOURCE}
     rel_max = max(e for _, e in rel_g) if rel_g else None
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -763,6 +820,8 @@ def run_batched(args):
     for lst in plans.values():
         for pl in lst:
             pl.close()
+    if rank == 0 and world == 1 and args.extra:
+        line["extra"] = {name: extra_workload(name, dev) for name in args.extra.split(",") if name}
     if pg:
         import torch.distributed as dist
         dist.destroy_process_group()
