@@ -232,28 +232,53 @@ bool gauss_dd(std::vector<dd> A, std::vector<dd> b, int n, std::vector<dd>& x) {
     return true;
 }
 
+// Complex double arithmetic written out with the basic IEEE operations only (no libm, no
+// libgcc complex division), so that the root finder takes the same path on every host.
+struct cx {
+    double re, im;
+};
+inline cx operator+(cx a, cx b) { return {a.re + b.re, a.im + b.im}; }
+inline cx operator-(cx a, cx b) { return {a.re - b.re, a.im - b.im}; }
+inline cx operator*(cx a, cx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+inline cx operator/(cx a, cx b) {   // Smith's algorithm
+    if (std::fabs(b.re) >= std::fabs(b.im)) {
+        const double r = b.im / b.re, d = b.re + b.im * r;
+        return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+    }
+    const double r = b.re / b.im, d = b.im + b.re * r;
+    return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+}
+inline double cx_abs(cx a) { return std::sqrt(a.re * a.re + a.im * a.im); }
+
 // All roots of sum_j v_j z^(deg-j), deg = v.size()-1, by the Aberth-Ehrlich iteration in
-// complex double.
-std::vector<std::complex<double>> aberth(const std::vector<double>& v) {
-    int deg = (int)v.size() - 1;
-    using C = std::complex<double>;
-    double r0 = std::pow(std::fabs(v[deg] / v[0]), 1.0 / deg);
-    std::vector<C> z(deg);
-    for (int k = 0; k < deg; ++k) z[k] = std::polar(r0, 2.0 * M_PI * (k + 0.25) / deg + 0.4);
+// complex double.  Starting points: a circle of radius 2^e with |v_deg / v_0| ~ 2^(e deg),
+// at the angles pi m / Q (cos and sin from the double-double series above).
+std::vector<cx> aberth(const std::vector<double>& v) {
+    const int deg = (int)v.size() - 1;
+    int e = 0;
+    std::frexp(std::fabs(v[deg] / v[0]), &e);
+    const double r0 = std::ldexp(1.0, e / deg);
+    const long Q = 4000L * deg;                    // angle 2 pi (k + 1/4) / deg + 0.127 pi
+    std::vector<cx> z(deg);
+    for (int k = 0; k < deg; ++k) {
+        const long m = 8000L * k + 2000L + 508L * deg;
+        z[k] = {r0 * cospi_frac(m, Q).hi, r0 * cospi_frac(m - Q / 2, Q).hi};
+    }
+    const cx one{1.0, 0.0};
     for (int it = 0; it < 2000; ++it) {
         double maxrel = 0;
         for (int k = 0; k < deg; ++k) {
-            C p = v[0], dp = 0;
+            cx p{v[0], 0.0}, dp{0.0, 0.0};
             for (int j = 1; j <= deg; ++j) {
                 dp = dp * z[k] + p;
-                p = p * z[k] + v[j];
+                p = p * z[k] + cx{v[j], 0.0};
             }
-            C ratio = p / dp, sum = 0;
+            cx ratio = p / dp, sum{0.0, 0.0};
             for (int j = 0; j < deg; ++j)
-                if (j != k) sum += 1.0 / (z[k] - z[j]);
-            C w = ratio / (1.0 - ratio * sum);
-            z[k] -= w;
-            maxrel = std::max(maxrel, std::abs(w) / std::max(std::abs(z[k]), 1e-300));
+                if (j != k) sum = sum + one / (z[k] - z[j]);
+            const cx w = ratio / (one - ratio * sum);
+            z[k] = z[k] - w;
+            maxrel = std::max(maxrel, cx_abs(w) / std::max(cx_abs(z[k]), 1e-300));
         }
         if (maxrel < 1e-15) break;
     }
@@ -261,9 +286,9 @@ std::vector<std::complex<double>> aberth(const std::vector<double>& v) {
 }
 
 // Newton refinement of one root in complex dd.
-cdd newton_dd(const std::vector<dd>& v, std::complex<double> z0) {
+cdd newton_dd(const std::vector<dd>& v, cx z0) {
     int deg = (int)v.size() - 1;
-    cdd z{mk(z0.real()), mk(z0.imag())};
+    cdd z{mk(z0.re), mk(z0.im)};
     for (int it = 0; it < 6; ++it) {
         cdd p{v[0], mk(0.0)}, dp{mk(0.0), mk(0.0)};
         for (int j = 1; j <= deg; ++j) {
@@ -338,7 +363,7 @@ Table build(int nu) {
     auto roots = aberth(vd);
     std::vector<cdd> outside;
     for (auto& z : roots)
-        if (std::abs(z) > 1.0) outside.push_back(newton_dd(x, z));
+        if (cx_abs(z) > 1.0) outside.push_back(newton_dd(x, z));
     if ((int)outside.size() != nu) return T;
     std::vector<cdd> up;
     for (auto& z : outside) {

@@ -78,7 +78,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     opts.m, opts.max_cycles, opts.tol, opts.precision = 4, 10, 1e-10, 0
     import ctypes as C
     out = C.c_void_p()
-    # p_max out of range, m p too large, bad ndim, cell Peclet >= 1, bad nu
+    # p_max out of range, m p too large, bad ndim, cell Peclet >= 1, negative grid_sms, bad nu
     assert lib.expm_plan_create(C.byref(op), 0, C.byref(opts), None, C.byref(out)) == N.EXPM_INVALID_ARG
     assert lib.expm_plan_create(C.byref(op), 33, C.byref(opts), None, C.byref(out)) == N.EXPM_INVALID_ARG
     opts.m = 200
@@ -89,6 +89,10 @@ def test_invalid_arguments_rejected_on_host(lib):
     op.ndim = 2
     op.vel[0] = 100.0      # cell Peclet 100/(17*0.2) > 1
     assert lib.expm_plan_create(C.byref(op), 8, C.byref(opts), None, C.byref(out)) == N.EXPM_INVALID_ARG
+    op.vel[0] = 1.0
+    opts.grid_sms = -1     # a negative share of the SMs
+    assert lib.expm_plan_create(C.byref(op), 8, C.byref(opts), None, C.byref(out)) == N.EXPM_INVALID_ARG
+    opts.grid_sms = 0
     d = (C.c_double * 32)()
     assert lib.expm_cf_coeffs(13, d, d, d, d) == N.EXPM_INVALID_ARG
     assert lib.expm_block(None, 1.0, None, 1, 1, None, 1, None) == N.EXPM_INVALID_ARG
@@ -277,5 +281,9 @@ def test_library_cf_table_other_degrees(lib, nu):
     for a, b in ((tau.real, tab["tau"].real), (tau.imag, tab["tau"].imag),
                  (om.real, tab["omega"].real), (om.imag, tab["omega"].imag)):
         assert np.all(np.abs(a - b) <= 2 * np.spacing(np.abs(b))), (nu, np.max(np.abs(a - b) / np.spacing(np.abs(b))))
-    assert abs(w0 - tab["omega0"]) <= 2 * np.spacing(abs(tab["omega0"]))
+    # omega_0 = r(-inf) comes out of the same least-squares solve as the residues: the
+    # library solves it in double-double on O(1) entries, so each component carries an
+    # absolute error of some units of 2^-106.  At nu = 16, omega_0 ~ 2e-16 lies far below
+    # that scale and only the absolute accuracy (2^-96, ~1e-29) is meaningful.
+    assert abs(w0 - tab["omega0"]) <= 2 * np.spacing(abs(tab["omega0"])) + 2.0 ** -96
     assert abs(sig - tab["sigma"]) <= 1e-12 * tab["sigma"]
