@@ -162,6 +162,9 @@ def parse():
     ap.add_argument("--graph", type=int, default=1,
                     help="batched workload: 1 = one CUDA graph launch per step (expm_batch_run), 0 = the "
                          "host-driven expm_block_batched")
+    ap.add_argument("--grid-share", type=float, default=0.5,
+                    help="batched workload: share of the SMs that each plan's row-pass grids are sized for "
+                         "(the plans' grid_sms option; the instances run concurrently)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extra", default="cd2d-256,toeplitz-1m",
                     help="batched line only: single-instance workloads also timed (a few steps each) "
@@ -645,10 +648,13 @@ def run_batched(args):
 
     def tuned(d, prec):
         bound = d["t"] * sum(4.0 * d["diff"] * (s_ + 1) ** 2 for s_ in d["sides"])
-        alg = 2 if bound >= 50.0 * tmax else 1
+        alg = 2 if bound >= N.EXPM_AUTO_RATIO * tmax else 1
         return autotune.options_for(table, len(d["sides"]), int(np.prod(d["sides"])), d["p"], prec, alg)
+    # the instances' solves run concurrently: each plan's row passes get a share of the SMs
+    grid_sms = max(1, round(args.grid_share * torch.cuda.get_device_properties(dev).multi_processor_count))
     plans = {prec: [Plan(d["sides"], d["diff"], d["vel"], p_max=d["p"], m=w["m"], tol=w["tol"], max_cycles=400,
-                         stream=st, precision=prec, k_defl=min(args.k_defl, (w["m"] - 1) * d["p"]), **tuned(d, prec))
+                         stream=st, precision=prec, k_defl=min(args.k_defl, (w["m"] - 1) * d["p"]),
+                         grid_sms=grid_sms, **tuned(d, prec))
                     for d, st in zip(inst, streams)]
              for prec in ("mixed", "fp64")}
     ns = [int(np.prod(d["sides"])) for d in inst]
@@ -781,7 +787,8 @@ def run_batched(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if head == "mixed" else "f64",
         "data": "synthetic (seeded instance list and N(0,1) right-hand sides)",
-        "config": {"workload": args.workload, "instances": len(inst), "n_range": [min(ns), max(ns)],
+        "config": {"workload": args.workload, "instances": len(inst), "grid_sms": grid_sms,
+                   "n_range": [min(ns), max(ns)],
                    "p_range": [min(ps), max(ps)], "columns_per_step": cols, "m": w["m"], "tol": w["tol"],
                    "nu": 14, "precision": head, "k_defl": args.k_defl,
                    "accuracy_vs_fp64_gpu": {

@@ -163,6 +163,16 @@ typedef struct {
     double  inner_tol;     /* CSR operators, Algorithm 2: relative residual of the inner
                               solve of A y = v, per column; 0 = 1e-12                  */
     int32_t inner_maxit;   /* ... and its iteration cap per application; 0 = 2000      */
+    int32_t grid_sms;      /* SMs that the grids of the row-parallel passes after the
+                              first Gram-Schmidt pass (Cholesky-QR, Z update, reductions)
+                              are sized for: CTAs = row_ctas_per_sm x grid_sms; 0 = all of
+                              the device's.  The first Gram-Schmidt pass always spans the
+                              device.  Plans whose solves run at the same time
+                              (expm_block_batched, expm_batch_*) can each take a share:
+                              those passes are latency-bound (a serial p x p
+                              factorisation in every CTA), and fewer CTAs with more rows
+                              each leave SMs to the other instances' kernels.  Results do
+                              not depend on it beyond the order of the row partial sums. */
 } expm_opts;
 
 #define EXPM_MAX_POLES 16

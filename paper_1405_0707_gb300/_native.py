@@ -53,7 +53,8 @@ class expm_opts(C.Structure):
                 ("precision", C.c_int32), ("fixed_cycles", C.c_int32), ("algorithm", C.c_int32),
                 ("certify", C.c_int32), ("nu_cf", C.c_int32), ("k_defl", C.c_int32),
                 ("row_ctas_per_sm", C.c_int32), ("cgs_ctas_per_sm", C.c_int32),
-                ("inner_tol", C.c_double), ("inner_maxit", C.c_int32)]
+                ("inner_tol", C.c_double), ("inner_maxit", C.c_int32),
+                ("grid_sms", C.c_int32)]
 
 
 class expm_info(C.Structure):

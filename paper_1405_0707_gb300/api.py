@@ -39,7 +39,8 @@ class Plan:
 
     def __init__(self, sides, diff, vel, p_max, m=10, tol=1e-10, max_cycles=200,
                  fixed_cycles=0, stream=None, algorithm=0, precision="fp64", certify=False, nu=0,
-                 k_defl=0, row_ctas=0, cgs_ctas=0, inner_tol=0.0, inner_maxit=0, _op=None):
+                 k_defl=0, row_ctas=0, cgs_ctas=0, inner_tol=0.0, inner_maxit=0, grid_sms=0,
+                 _op=None):
         import torch
         if _op is None:
             sides = tuple(int(s) for s in sides)
@@ -67,6 +68,7 @@ class Plan:
         opts.cgs_ctas_per_sm = int(cgs_ctas)
         opts.inner_tol = float(inner_tol)      # CSR operators: inner solve (0: library default)
         opts.inner_maxit = int(inner_maxit)
+        opts.grid_sms = int(grid_sms)          # 0: row-pass grids sized for the whole device
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.sides, self.diff, self.vel, self.p_max, self.m = sides, diff, vel, p_max, m
         self.tol, self.max_cycles, self.algorithm, self.precision = tol, max_cycles, algorithm, precision

@@ -1253,7 +1253,8 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     if (opts->nu_cf != 0 && (opts->nu_cf < 2 || opts->nu_cf > 2 * EXPM_MAX_POLES || opts->nu_cf % 2 != 0))
         return EXPM_INVALID_ARG;
     if (opts->k_defl < 0 || (int64_t)opts->k_defl > (int64_t)(opts->m - 1) * p_max) return EXPM_INVALID_ARG;
-    if (opts->row_ctas_per_sm < 0 || opts->row_ctas_per_sm > 8 || opts->cgs_ctas_per_sm < 0 || opts->cgs_ctas_per_sm > 8)
+    if (opts->row_ctas_per_sm < 0 || opts->row_ctas_per_sm > 8 || opts->cgs_ctas_per_sm < 0 || opts->cgs_ctas_per_sm > 8 ||
+        opts->grid_sms < 0)
         return EXPM_INVALID_ARG;
     expm_plan* P = new (std::nothrow) expm_plan_s();
     if (!P) return EXPM_NO_MEMORY;
@@ -1350,9 +1351,11 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
     {
         // CTAs of the row-parallel passes: blocks_per_sm x SMs, at least 64 rows each (the
         // plan options, as an autotuner picks them; else 2, and twice that for the first CGS
-        // pass, measured best on the 256 x 256 workload)
+        // pass, measured best on the 256 x 256 workload).  SMs = the device's count for the
+        // first CGS pass; for the other row passes, the share of it that the plan was given.
         int per_sm = opts->row_ctas_per_sm > 0 ? opts->row_ctas_per_sm : 2;
-        P->nblk = consistent_blocks(n, std::max(1, std::min<int>(per_sm * sms, (int)((n + 63) / 64))));
+        const int sms_rows = opts->grid_sms > 0 ? std::min(sms, (int)opts->grid_sms) : sms;
+        P->nblk = consistent_blocks(n, std::max(1, std::min<int>(per_sm * sms_rows, (int)((n + 63) / 64))));
         // the first CGS pass (projection, update) may use more CTAs than the other row passes
         const int per_sm_cgs = opts->cgs_ctas_per_sm > 0 ? opts->cgs_ctas_per_sm : 2 * per_sm;
         P->nblk_cgs = consistent_blocks(n, std::max(1, std::min<int>(per_sm_cgs * sms, (int)((n + 63) / 64))));

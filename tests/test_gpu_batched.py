@@ -120,3 +120,28 @@ def test_batch_graph_rejects_host_work_between_cycles():
         pl = Plan((20, 20), 0.1, (1.0, 1.0), p_max=2, m=4, stream=torch.cuda.Stream(), **kw)
         with pytest.raises(ExpmError):
             Batch([pl], [0.1], [B])
+
+
+@pytest.mark.parametrize("alg", [1, 2])
+def test_row_grid_share_changes_only_the_summation_order(tab, alg):
+    """grid_sms sizes the grids of the row passes after the first Gram-Schmidt pass for a
+    share of the SMs (fewer CTAs, more rows each).  The solve is the same up to the order of
+    the per-CTA partial sums: Z agrees with the whole-device plan to rounding, takes the same
+    number of cycles, and meets the closed form."""
+    torch = need_gpu()
+    from paper_1405_0707_gb300 import Plan
+    sides, diff, vel, t, p = (37, 31, 29), 1.0, (1.0, -2.0, 0.5), (0.004 if alg == 1 else 0.05), 6
+    B = inputs.rhs(int(np.prod(sides)), p, 77)
+    out = {}
+    for share in (0, 3, 40):
+        pl = Plan(sides, diff, vel, p_max=p, m=10, tol=1e-11, max_cycles=300, algorithm=alg, precision="mixed",
+                  grid_sms=share, row_ctas=2)
+        Z, info = pl.expm_block(t, to_dev(B))
+        assert info.converged == 1 and info.algorithm == alg
+        out[share] = (to_np(Z), int(info.cycles))
+        pl.close()
+    ref = ops.exact_r_of_A_B(sides, diff, vel, t, tab, B)
+    for share in (3, 40):
+        assert out[share][1] == out[0][1]
+        assert rel(out[share][0], out[0][0]) <= 1e-12
+        assert rel(out[share][0], ref) <= 1e-9
