@@ -444,6 +444,15 @@ __global__ void __launch_bounds__(256) k_gemm32(GemmArgsMixed g) {
 // the columns (otherwise) walk consecutive threads, so the stores coalesce.
 constexpr int SBM = 128, SMAX = 96;
 constexpr int SAS = SBM + 4;   // row stride of the staged A (float4-aligned)
+
+// one 4-byte asynchronous global -> shared copy (zero-filled when !ok: no bytes are read,
+// and src is then any valid address)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __host__ __device__ constexpr size_t gemm_small_smem(int K, int NJ) {
     return sizeof(float) * ((size_t)K * 16 * NJ + (size_t)K * SAS);
 }
@@ -459,20 +468,39 @@ __global__ void __launch_bounds__(256) k_gemm_small(GemmArgsMixed g) {
     const TA* A = reinterpret_cast<const TA*>(g.A) + b1 * g.a_b1 + b2 * g.a_b2;
     TC* C = reinterpret_cast<TC*>(g.C) + b1 * g.c_b1 + b2 * g.c_b2;
     const int m0 = blockIdx.x * SBM, tid = threadIdx.x;
-    // staging: the loads of each thread are issued in batches into registers before any is
-    // stored, so a batch's latencies overlap (a plain loop would wait for every load in turn)
-    for (int e0 = tid; e0 < K * NP; e0 += 8 * 256) {
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + 256 * u, k = e / NP, n = e - k * NP;
-            v[u] = (e < K * NP && n < g.N) ? g.B[(int64_t)k * g.ldb + n] : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (e0 + 256 * u < K * NP) Bs[e0 + 256 * u] = v[u];
+    // staging: every float operand is copied with cp.async, so all of a thread's copies are in
+    // flight at once and the CTA waits for one round trip; an FP64 A is converted on the way
+    // and goes through registers, in batches of loads issued before any is stored
+    for (int e = tid; e < K * NP; e += 256) {
+        const int k = e / NP, n = e - k * NP;
+        const bool ok = n < g.N;
+        cp_async4(Bs + e, ok ? g.B + (int64_t)k * g.ldb + n : g.B, ok);
     }
-    if (g.a_rs == 1) {
+    if constexpr (sizeof(TA) == 4) {
+        if (g.a_rs == 1) {
+            const int mm = tid & (SBM - 1), m = m0 + mm;
+            const bool ok = m < g.M;
+            const int64_t ro = ok ? gemm_row_off(m, g.ms, g.a_rs, g.a_ms2) : 0;
+            for (int k = tid >> 7; k < K; k += 2)
+                cp_async4(As + k * SAS + mm, ok ? (const float*)A + ro + (int64_t)k * g.a_cs : (const float*)A, ok);
+        } else {
+            const int warp = tid >> 5, lane = tid & 31;
+            for (int mm0 = warp; mm0 < SBM; mm0 += 32)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int m = m0 + mm0 + 8 * r;
+                    const bool ok = m < g.M;
+                    const int64_t ro = ok ? gemm_row_off(m, g.ms, g.a_rs, g.a_ms2) : 0;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int k = lane + 32 * j;
+                        if (k < K)
+                            cp_async4(As + k * SAS + mm0 + 8 * r,
+                                      ok ? (const float*)A + ro + (int64_t)k * g.a_cs : (const float*)A, ok);
+                    }
+                }
+        }
+    } else if (g.a_rs == 1) {
         // m fastest in memory: thread t keeps row mm = t % SBM (one row offset) and walks k
         const int mm = tid & (SBM - 1), m = m0 + mm;
         const bool ok = m < g.M;
@@ -511,6 +539,7 @@ __global__ void __launch_bounds__(256) k_gemm_small(GemmArgsMixed g) {
                     if (lane + 32 * j < K) As[(lane + 32 * j) * SAS + mm0 + 8 * r] = v[r][j];
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     const int tm = CM ? (tid & 15) : (tid >> 4), tn = CM ? (tid >> 4) : (tid & 15);
     float acc[8][NJ];
