@@ -68,6 +68,23 @@ KERNEL_OF = {"gemm": "k_gemm (DST-I transforms of the exact inverse, FP64)",
              "gsf": "k_fft_cols/k_fft_rows (Gohberg-Semencul inverse, FP64)"}
 
 
+# arithmetic pipe of each class's kernels in a mixed plan.  FP32 classes are measured against
+# the FP32 FMA peak; double-float classes (several FP32 instructions per algorithmic FP64 flop)
+# and classes that mix pipes only against HBM.  An FP64 plan's classes run on the FP64 pipe.
+MIXED_PIPE = {"gemm": "fp32", "tridiag": "fp32", "cgs": "fp32-pair", "qr": "fp32-pair",
+              "update": "fp32-pair", "fft": "fp32-pair", "gsf": "fp32-pair", "stencil": "fp64+fp32-pair"}
+
+
+def alu_fracs(cls, head, tflops):
+    if head != "mixed":
+        return {"pipe": "fp64", "frac_fp64_alu": tflops / (FP64_PEAK_TFLOPS / 1e3)}
+    pipe = MIXED_PIPE.get(cls, "mixed")
+    out = {"pipe": pipe}
+    if pipe == "fp32":
+        out["frac_fp32_alu"] = tflops / (FP32_PEAK_TFLOPS / 1e3)
+    return out
+
+
 def _hbm_peak():
     try:
         return (float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]),
@@ -398,23 +415,20 @@ def run_ours(args):
         sec = ms_k / 1e3
         fl_s, by_s = fl * args.steps / sec, by * args.steps / sec
         roofs[k] = {"launches_per_step": n_k // args.steps, "ms_per_step": ms_k / args.steps,
-                    "tflops": fl_s / 1e12, "gbs": by_s / 1e9,
-                    "frac_fp64_alu": fl_s / 1e12 / (FP64_PEAK_TFLOPS / 1e3),
-                    "frac_hbm": by_s / 1e9 / HBM_PEAK_GBS}
+                    "tflops": fl_s / 1e12, "gbs": by_s / 1e9, "frac_hbm": by_s / 1e9 / HBM_PEAK_GBS}
+        roofs[k].update(alu_fracs(k, head, fl_s / 1e12))
     dom = max(roofs, key=lambda k: roofs[k]["ms_per_step"])
     r = roofs[dom]
     fl_launch = alg_work[dom][0] / max(1, r["launches_per_step"])
     by_launch = alg_work[dom][1] / max(1, r["launches_per_step"])
     label = KERNEL_OF.get(dom + "_mixed", KERNEL_OF[dom]) if head == "mixed" else KERNEL_OF[dom]
-    if head == "mixed" and dom in ("cgs", "qr", "update"):
-        # row passes over FP64 data whose arithmetic runs on the FP32 pipe (FP32 products,
-        # double-float sums): their ceiling is memory bandwidth, not the FP64 ALU
-        roof = {"kernel": label, "bound": "hbm", "achieved": round(r["gbs"], 1),
-                "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": round(r["frac_hbm"], 4)}
-    elif r["frac_fp64_alu"] >= r["frac_hbm"]:
+    # double-float row passes (FP32 products, double-float sums over FP64 data) have no ALU
+    # fraction: their ceiling is memory bandwidth
+    fa = r.get("frac_fp64_alu", r.get("frac_fp32_alu"))
+    if fa is not None and fa >= r["frac_hbm"]:
+        pk = FP64_PEAK_TFLOPS if "frac_fp64_alu" in r else FP32_PEAK_TFLOPS
         roof = {"kernel": label, "bound": "alu", "achieved": round(r["tflops"], 4),
-                "peak": round(FP64_PEAK_TFLOPS / 1e3, 4), "unit": "TFLOP/s",
-                "frac": round(r["frac_fp64_alu"], 4)}
+                "peak": round(pk / 1e3, 4), "unit": "TFLOP/s", "frac": round(fa, 4)}
     else:
         roof = {"kernel": label, "bound": "hbm", "achieved": round(r["gbs"], 1),
                 "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": round(r["frac_hbm"], 4)}
@@ -769,8 +783,7 @@ def run_batched(args):
         roofs[k_] = {"launches": nk, "ms_serial": round(msk, 3), "launch_ms": msk / nk,
                      "gbs": by / sec / 1e9, "frac_hbm": by / sec / 1e9 / HBM_PEAK_GBS,
                      "tflops": fl / sec / 1e12}
-        if head != "mixed" or k_ not in ("cgs", "qr", "update"):
-            roofs[k_]["frac_fp64_alu"] = fl / sec / 1e12 / (FP64_PEAK_TFLOPS / 1e3)
+        roofs[k_].update(alu_fracs(k_, head, fl / sec / 1e12))
     dom = max(roofs, key=lambda k_: roofs[k_]["ms_serial"])
     r = roofs[dom]
     label = KERNEL_OF.get(dom + "_mixed", KERNEL_OF[dom]) if head == "mixed" else KERNEL_OF[dom]

@@ -67,3 +67,17 @@ def test_auto_rule_on_the_workloads():
 
 def test_toeplitz_fft_length():
     assert bench.fft_size(inputs.WORKLOADS["toeplitz-1m"]) == 2 ** 21
+
+
+def test_alu_fractions_follow_the_pipe_of_each_class():
+    """A class's ALU fraction is taken against the peak of the pipe its kernels run on: FP64
+    plans against the FP64 FMA peak; in mixed plans the FP32 transforms and line solves
+    against the FP32 peak, and the double-float classes against none (HBM only)."""
+    import bench
+    g = bench.alu_fracs("gemm", "mixed", 4.025)
+    assert g["pipe"] == "fp32" and abs(g["frac_fp32_alu"] - 4.025e3 / bench.FP32_PEAK_TFLOPS) < 1e-15
+    for cls in ("cgs", "qr", "update", "fft", "gsf", "stencil"):
+        f = bench.alu_fracs(cls, "mixed", 4.0)
+        assert "frac_fp64_alu" not in f and "frac_fp32_alu" not in f, cls
+    d = bench.alu_fracs("gemm", "fp64", bench.FP64_PEAK_TFLOPS / 2e3)     # half the FP64 peak
+    assert d["pipe"] == "fp64" and abs(d["frac_fp64_alu"] - 0.5) < 1e-12
