@@ -356,9 +356,19 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     // first pass: FP64, or in the mixed path FP32 projection and double-float update (the
     // row-chunk kernels for p <= 16, else the tile kernels)
     const bool rows = f32 && cgs_rows_fit(cols, p);
-    if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(0, P->V, ld, cols, P->W, ld, p, n, nullptr, P->part, nbc, 0, s));
+    // the projection on the tensor cores (TF32 hi/lo products) when the plan chose it: by
+    // default for p >= 8 and 48 <= cols <= 128 (one M tile), where it measured faster than
+    // the FP32 kernel (whose cost grows with p; the tensor-core pass has a fixed cost per
+    // 16-row chunk)
+    const bool ptc = rows && P->proj_tc && proj_tc_fit(cols, p) &&
+                     (P->proj_tc == 1 || (p >= 8 && cols >= 48 && cols <= 128));
+    const int nb1 = ptc ? proj_tc_blocks(n, cols, nbc) : nbc;
+    if (ptc)
+        LAUNCH(EXPM_STAGE_CGS, launch_proj_tc(P->V, ld, cols, P->W, ld, p, n, P->part, nb1, flags_of(P->stat),
+                                              P->tc_spin, s));
+    else if (rows) LAUNCH(EXPM_STAGE_CGS, launch_cgs_rows(0, P->V, ld, cols, P->W, ld, p, n, nullptr, P->part, nbc, 0, s));
     else LAUNCH(EXPM_STAGE_CGS, launch_proj_partial(P->V, ld, cols, P->W, ld, p, n, P->part, nbc, s, f32));
-    LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nbc, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
+    LAUNCH(EXPM_STAGE_REDUCE, launch_reduce_h(P->part, nb1, cols, p, h, P->H, P->ldH, 0, j * p, 0, s));
     if (rows && fused_qr(P, p)) {
         // update, second projection and the Gram matrix of W; the second pass's correction is
         // applied by the first Cholesky-QR pass.  The update on the tensor cores (exact bf16
@@ -1283,6 +1293,10 @@ expm_status expm_plan_create(const expm_op_desc* op, int p_max, const expm_opts*
         // alone).  Test switch: "1" for every block step it fits, "0" never
         const char* tc = std::getenv("EXPM_CGS_TC");
         P->cgs_tc = opts->precision != EXPM_PREC_MIXED ? 0 : !tc ? 2 : tc[0] == '1' ? 1 : 0;
+        // the first CGS pass's projection on the tensor cores (k_proj_tc) for mixed plans, by
+        // shape (see block_step).  Test switch: "1" for every block step it fits, "0" never
+        const char* ptc = std::getenv("EXPM_PROJ_TC");
+        P->proj_tc = opts->precision != EXPM_PREC_MIXED ? 0 : !ptc ? 2 : ptc[0] == '1' ? 1 : 0;
         // test switch: the bound of the tensor-core kernel's waits (0 makes every wait run out)
         const char* sl = std::getenv("EXPM_TC_SPIN_LIMIT");
         if (sl) P->tc_spin = std::strtol(sl, nullptr, 10);

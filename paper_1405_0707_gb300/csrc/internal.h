@@ -231,6 +231,7 @@ struct expm_plan_s {
     bool use_graphs = false;
     bool qr_single = true;     // mixed path: try the single accurate Cholesky-QR pass
     int cgs_tc = 0;            // mixed path, first CGS update on the tensor cores: 0 never, 1 always, 2 by shape
+    int proj_tc = 0;           // mixed path, first CGS projection on the tensor cores: 0 never, 1 always, 2 by shape
     int stencil_df = 0;        // mixed path: the stencil in double-float (k_cd_apply_df)
     long tc_spin = 1L << 24;   // bound of the tensor-core kernel's mbarrier waits (iterations)
     // deflated restart (opts.k_defl > 0)
@@ -301,6 +302,14 @@ constexpr int kRowsMaxP = 16;  // widths handled by the row-per-thread kernels
 bool cgs_tc_fit(int cols, int p);
 cudaError_t launch_cgs_tc(const double* V, int64_t ldv, int cols, double* W, int64_t ldw, int p, int64_t n,
                           const double* h, int* flags, long spin_limit, cudaStream_t s);
+// The first CGS pass's projection h = V^T W on the tensor cores (k_cgs_tc.cu, kind::tf32 with
+// a hi/lo split): partial[blk][a][c] for blk < nb as the FP32 projection kernel writes them;
+// p <= 16, cols <= 160; nb = proj_tc_blocks(n, cols, max) CTAs looping over 256-row tiles.  A bounded wait that runs
+// out sets bit 4 of flags[0].
+bool proj_tc_fit(int cols, int p);
+int proj_tc_blocks(int64_t n, int cols, int max_blocks);
+cudaError_t launch_proj_tc(const double* V, int64_t ldv, int cols, const double* W, int64_t ldw, int p, int64_t n,
+                           double* part, int nb, int* flags, long spin_limit, cudaStream_t s);
 cudaError_t cgs_tc_set_smem_limits();
 // Cholesky-QR passes: mode 0 (unshifted, shifted on ill-conditioning, sets flags[2] when a
 // third pass is needed), mode 1, mode 2 (no-op unless flags[2]); see k_krylov.cu.

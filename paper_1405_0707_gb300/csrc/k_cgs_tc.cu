@@ -349,6 +349,226 @@ __global__ void __launch_bounds__(TCT, 2) k_cgs_tc(const double* __restrict__ V,
     }
 }
 
+// ---- the first CGS pass's projection h = V^T W on the tensor cores (tcgen05.mma kind::tf32)
+//
+// partial[blk][a][c] = sum over the CTA's rows r of V[r, a] W[r, c]: the output of the FP32
+// projection kernel (k_cgs_rows<false>), for the same reduction.  This projection only seeds
+// the second Gram-Schmidt pass, which removes whatever it leaves, so FP32-level accuracy is
+// enough: each FP64 operand is rounded to FP32 (integer operations) and split x = x_hi + x_lo,
+// x_hi its top 11 significant bits (a TF32 value) and x_lo = x - x_hi (exact in FP32, read
+// by the MMA as TF32: its top 11 bits).  v w is taken as v_hi w_hi + v_hi w_lo + v_lo w_hi,
+// about 2^-21 relative per product.  Both operands are K-major with K = the rows, contiguous
+// in the column-major V and W: A = V^T (M = the basis columns, one or two 128-row M tiles),
+// B = W^T (N = 16; block columns past p are zero).
+// Layout: persistent CTAs of 128 threads over 256-row tiles of 16 chunks of 16 rows.  Per
+// chunk each thread converts its tasks (4 consecutive rows of one column) and stores x_hi and
+// x_lo as one 16-byte core-matrix row each into one of two stages; thread 0 then issues the
+// chunk's MMAs (per M tile and 8-row K block: hi.lo, lo.hi, hi.hi) into the tile's
+// accumulator (16 tensor-memory columns per M tile) and commits them to the stage's mbarrier.
+// The next chunk's loads are in flight in registers while the current chunk is stored.  At
+// the end of a tile the FP32 accumulators (sums over 256 rows) are read back and added into
+// float-pair sums per thread (thread = accumulator lane = basis column), so the summation
+// error does not grow with the number of tiles.  Every mbarrier wait is bounded as in
+// k_cgs_tc.
+constexpr int PT = 128;              // threads per M tile (its tensor-memory lanes)
+constexpr int PKC = 16;              // rows per chunk
+constexpr int PCH = 16;              // chunks per tile
+constexpr int PTILE = PKC * PCH;     // rows per tile
+constexpr int PCOLS_MAX = 160;       // basis columns (the second M tile partly used)
+constexpr uint32_t kPA = 4096;       // one 128 x 8 TF32 block of A
+constexpr uint32_t kPB = 512;        // one 16 x 8 TF32 block of B
+constexpr int PTMEM = 32;            // two M tiles x 16 accumulator columns
+
+__host__ __device__ constexpr size_t ptc_stage_bytes(int mt) { return (size_t)mt * 4 * kPA + 4 * kPB; }
+__host__ __device__ constexpr size_t ptc_smem_bytes(int mt) { return 2 * ptc_stage_bytes(mt); }
+
+// byte offset of element (row, k) of a K-major block with 8 TF32 per row: core matrices of
+// 8 rows x 16 bytes, adjacent along K 128 bytes apart (LBO), along the rows 256 bytes (SBO)
+__device__ __forceinline__ uint32_t kmaj32(int row, int k) {
+    return (uint32_t)((row >> 3) * 256 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, M = 128, N = 16
+__device__ __forceinline__ uint32_t idesc_tf32() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+                 "l"(da), "l"(db), "r"(idesc_tf32()), "r"(acc));
+}
+
+// x as the pair (hi, lo): FP32 rounding by integer operations, hi = its top 11 significant
+// bits, lo = the rest (exact)
+__device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
+    const float f = f32_rn_i(x);
+    hi = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+    lo = f - hi;
+}
+
+template <int MT>
+__global__ void __launch_bounds__(PT * MT) k_proj_tc(const double* __restrict__ V, int64_t ldv, int cols,
+                                                const double* __restrict__ W, int64_t ldw, int p, int64_t n,
+                                                double* __restrict__ part, int* flags, long spin_limit) {
+    extern __shared__ __align__(1024) unsigned char smp[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tbase_s;
+    __shared__ int bad_s;
+    constexpr uint32_t SB = (uint32_t)ptc_stage_bytes(MT);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase_s)),
+                     "r"(PTMEM));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        bad_s = 0;
+    }
+    // both stages zeroed once: rows of the last M tile past cols are never written
+    for (uint32_t o = (uint32_t)tid * 16u; o < 2u * SB; o += PT * MT * 16u)
+        *reinterpret_cast<uint4*>(smp + o) = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    const uint32_t tbase = tbase_s;
+
+    constexpr int NTH = PT * MT;                     // threads: warp w reads M tile w / 4
+    constexpr int PTASK = (4 * (MT == 1 ? 128 : PCOLS_MAX) + NTH - 1) / NTH;   // V tasks per thread, at most
+    const int ntask = 4 * cols;                      // V tasks per chunk: (column, 4-row group)
+    const int64_t ntiles = (n + PTILE - 1) / PTILE;
+    const int mt_own = warp >> 2;                    // the M tile whose sums this thread keeps
+    float sh[16], sl[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        sh[c] = 0.f;
+        sl[c] = 0.f;
+    }
+    double pv[PTASK][4], pw[4];
+    auto load = [&](int64_t r0) {
+#pragma unroll
+        for (int t = 0; t < PTASK; ++t) {
+            const int task = tid + t * NTH;
+            const int a = task >> 2;
+            const int64_t r = r0 + 4 * (task & 3);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                pv[t][u] = (task < ntask && r + u < n) ? V[(int64_t)a * ldv + r + u] : 0.0;
+        }
+        const int c = tid >> 2;
+        const int64_t r = r0 + 4 * (tid & 3);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pw[u] = (tid < 64 && c < p && r + u < n) ? W[(int64_t)c * ldw + r + u] : 0.0;
+    };
+
+    int uses0 = 0, uses1 = 0, gch = 0;   // commits to mbar[0], mbar[1]; chunks issued (uniform)
+    bool stop = false;
+    if ((int64_t)blockIdx.x < ntiles) load((int64_t)blockIdx.x * PTILE);
+    for (int64_t tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+        for (int kc = 0; kc < PCH; ++kc) {
+            const int buf = gch & 1;
+            const int uses = buf ? uses1 : uses0;
+            if (uses > 0 && !mbar_wait(&mbar[buf], (uint32_t)((uses - 1) & 1), spin_limit)) {
+                if (lane == 0) atomicOr(&bad_s, 2);
+            }
+            __syncthreads();
+            if (bad_s & 2) {
+                stop = true;
+                break;
+            }
+            unsigned char* S = smp + (size_t)buf * SB;
+#pragma unroll
+            for (int t = 0; t < PTASK; ++t) {
+                const int task = tid + t * NTH;
+                if (task < ntask) {
+                    const int a = task >> 2, g = task & 3;
+                    float hi[4], lo[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) split_tf32(pv[t][u], hi[u], lo[u]);
+                    const uint32_t o = (uint32_t)(((a >> 7) * 2 + (g >> 1)) * 2) * kPA + kmaj32(a & 127, (g & 1) * 4);
+                    *reinterpret_cast<float4*>(S + o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<float4*>(S + o + kPA) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+            if (tid < 64) {
+                const int c = tid >> 2, g = tid & 3;
+                float hi[4], lo[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) split_tf32(pw[u], hi[u], lo[u]);
+                const uint32_t o = (uint32_t)MT * 4u * kPA + (uint32_t)((g >> 1) * 2) * kPB + kmaj32(c, (g & 1) * 4);
+                *reinterpret_cast<float4*>(S + o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<float4*>(S + o + kPB) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            }
+            // the next chunk's loads (possibly of the CTA's next tile) while this one is used
+            if (kc + 1 < PCH) load(tile * PTILE + (int64_t)(kc + 1) * PKC);
+            else if (tile + gridDim.x < ntiles) load((tile + gridDim.x) * PTILE);
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0) {
+                const uint32_t sa = smem_u32(S), sb = sa + (uint32_t)MT * 4u * kPA;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int kb = 0; kb < 2; ++kb) {
+                        const uint32_t ah = sa + (uint32_t)((mt * 2 + kb) * 2) * kPA, bh = sb + (uint32_t)(kb * 2) * kPB;
+                        const uint32_t d = tbase + 16u * (uint32_t)mt;
+                        mma_tf32(d, sdesc(ah), sdesc(bh + kPB), (kc > 0 || kb > 0) ? 1u : 0u);   // hi . lo
+                        mma_tf32(d, sdesc(ah + kPA), sdesc(bh), 1u);                              // lo . hi
+                        mma_tf32(d, sdesc(ah), sdesc(bh), 1u);                                    // hi . hi
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&mbar[buf])));
+            }
+            if (buf) ++uses1;
+            else ++uses0;
+            ++gch;
+        }
+        if (stop) break;
+        // the tile's sums: every MMA of the tile is tracked by its last commit
+        const int lbuf = (gch - 1) & 1, luses = lbuf ? uses1 : uses0;
+        if (!mbar_wait(&mbar[lbuf], (uint32_t)((luses - 1) & 1), spin_limit)) {
+            if (lane == 0) atomicOr(&bad_s, 2);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (bad_s & 2) {
+            stop = true;
+            break;
+        }
+        {
+            // warp w reads lanes 32 (w % 4) .. + 31 of M tile w / 4 (its accumulator columns)
+            uint32_t x[16];
+            const uint32_t ta = tbase + ((uint32_t)((warp & 3) * 32) << 16) + 16u * (uint32_t)mt_own;
+            tmem_ld8(ta, x);
+            tmem_ld8(ta + 8u, x + 8);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int c = 0; c < 16; ++c) df_add(sh[c], sl[c], __uint_as_float(x[c]));
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+    }
+    if (stop) {
+        const int b0 = uses0 > 0 ? mbar_wait(&mbar[0], (uint32_t)((uses0 - 1) & 1), 1L << 26) : 1;
+        const int b1 = uses1 > 0 ? mbar_wait(&mbar[1], (uint32_t)((uses1 - 1) & 1), 1L << 26) : 1;
+        if (!(b0 && b1) && lane == 0) atomicOr(&bad_s, 4);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(PTMEM));
+    double* out = part + (int64_t)blockIdx.x * cols * p;
+    if (tid < cols)     // thread tid holds basis column a = 128 (tid / 128) + tid % 128 = tid
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < p) out[tid * p + c] = (double)sh[c] + (double)sl[c];
+    if (tid == 0 && (bad_s & 6)) atomicOr(&flags[0], 16);   // a bounded wait ran out (EXPM_TIMEOUT)
+}
+
 int tc_sms() {
     static int sms = 0;
     if (!sms) {
@@ -373,8 +593,35 @@ cudaError_t launch_cgs_tc(const double* V, int64_t ldv, int cols, double* W, int
     return cudaGetLastError();
 }
 
+// The projection of the first CGS pass on the tensor cores: persistent CTAs, one partial each
+// (max_blocks of them, or one per 256-row tile when there are fewer tiles: a grid capped at
+// one wave by the occupancy calculator measured slower than the plan's CGS grid)
+int proj_tc_blocks(int64_t n, int cols, int max_blocks) {
+    (void)cols;
+    const int64_t tiles = (n + PTILE - 1) / PTILE;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, max_blocks));
+}
+
+bool proj_tc_fit(int cols, int p) { return p >= 1 && p <= 16 && cols >= 1 && cols <= PCOLS_MAX; }
+
+cudaError_t launch_proj_tc(const double* V, int64_t ldv, int cols, const double* W, int64_t ldw, int p, int64_t n,
+                           double* part, int nb, int* flags, long spin_limit, cudaStream_t s) {
+    if (!proj_tc_fit(cols, p) || nb < 1 || !part || !flags) return cudaErrorInvalidValue;
+    if (cols <= 128)
+        k_proj_tc<1><<<nb, PT, ptc_smem_bytes(1), s>>>(V, ldv, cols, W, ldw, p, n, part, flags, spin_limit);
+    else
+        k_proj_tc<2><<<nb, 2 * PT, ptc_smem_bytes(2), s>>>(V, ldv, cols, W, ldw, p, n, part, flags, spin_limit);
+    return cudaGetLastError();
+}
+
 cudaError_t cgs_tc_set_smem_limits() {
-    return cudaFuncSetAttribute(k_cgs_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_COLS_MAX));
+    cudaError_t e = cudaFuncSetAttribute(k_cgs_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes(TC_COLS_MAX));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_proj_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ptc_smem_bytes(1));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_proj_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ptc_smem_bytes(2));
+    return e;
 }
 
 }  // namespace expm
