@@ -359,9 +359,10 @@ expm_status block_step(expm_plan* P, double t, int j, int p, int alg) {
     // the projection on the tensor cores (TF32 hi/lo products) when the plan chose it: by
     // default for p >= 8 and 48 <= cols <= 128 (one M tile), where it measured faster than
     // the FP32 kernel (whose cost grows with p; the tensor-core pass has a fixed cost per
-    // 16-row chunk)
+    // 16-row chunk), and with at least one 256-row tile per CTA of the plan's CGS grid (its
+    // set-up and per-tile read-back are amortised only then: on 256 x 256 it was slower)
     const bool ptc = rows && P->proj_tc && proj_tc_fit(cols, p) &&
-                     (P->proj_tc == 1 || (p >= 8 && cols >= 48 && cols <= 128));
+                     (P->proj_tc == 1 || (p >= 8 && cols >= 48 && cols <= 128 && n >= (int64_t)256 * nbc));
     const int nb1 = ptc ? proj_tc_blocks(n, cols, nbc) : nbc;
     if (ptc)
         LAUNCH(EXPM_STAGE_CGS, launch_proj_tc(P->V, ld, cols, P->W, ld, p, n, P->part, nb1, flags_of(P->stat),
