@@ -1,6 +1,7 @@
-// k_cgs_tc.cu -- the update of the first block CGS2 pass of the mixed path on the
-// 5th-generation tensor cores (tcgen05, accumulators in tensor memory), for blocks of p <= 16
-// columns against at most 160 basis columns.
+// k_cgs_tc.cu -- the first block CGS2 pass of the mixed path on the 5th-generation tensor
+// cores (tcgen05, accumulators in tensor memory), for blocks of p <= 16 columns against at
+// most 160 basis columns: the update (k_cgs_tc, below) and the projection (k_proj_tc, further
+// down).
 //
 // The kernel computes W <- W - V h (V: n x cols, the orthonormal Krylov basis, FP64; h: cols x
 // p, the projection of the first Gram-Schmidt pass).  The update must hold to FP64 rounding
