@@ -51,8 +51,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x flop/FMA x GHz = 
 L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF = {"gemm": "k_gemm (DST-I transforms of the exact inverse, FP64)",
              "cgs": "k_proj/k_update (block CGS2 row passes, FP64)",
-             "cgs_mixed": "k_cgs_rows (first block CGS2 pass: FP32 projection, double-float update fused with "
-                          "the FP32 second projection and the double-float Gram matrix)",
+             "cgs_mixed": "k_cgs_rows / k_proj_tc / k_cgs_tc (first block CGS2 pass: projection in FP32, or TF32 "
+                          "hi/lo products on the tensor cores; update in double-float fused with the FP32 second "
+                          "projection and the double-float Gram matrix, or exact bf16 slices on the tensor cores)",
              "qr_mixed": "k_qr_mixed_rows (second CGS pass's FP32 correction fused with one accurate Cholesky-QR "
                          "pass: double-float factor applied exactly in double-float; FP32 deviation passes only "
                          "for ill-conditioned blocks)",
